@@ -1,0 +1,395 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by the mathematics.
+
+Each test checks the oracle against something other than itself: textbook closed forms, the
+closed-form Fourier symbol of the tensor-product elements, exact laminate results, invariants
+(homogeneous material, symmetry, Voigt/Reuss bounds, Hill-Mandel energy identity, element-by-
+element eigenvalue bounds of Sec. 4.3), one-iteration convergence for C = s C_ref (Sec. 4.3) and
+brute force on tiny grids.  No GPU needed.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fem, solvers
+from paper_2203_02962_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _rand_spd(m, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, m))
+    return scale * (A @ A.T + m * np.eye(m))
+
+
+def _mandel_tensor(C):
+    """Full 4th-order tensor C_ijkl (3-D or 2-D) from a Mandel matrix, written out for the test."""
+    m = C.shape[0]
+    d = 3 if m == 6 else 2
+    pairs = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)] if d == 3 else [(0, 0), (1, 1), (0, 1)]
+    w = [1.0 if i == j else math.sqrt(2.0) for i, j in pairs]
+    T = np.zeros((d, d, d, d))
+    for I_, (i, j) in enumerate(pairs):
+        for J_, (k, l) in enumerate(pairs):
+            v = C[I_, J_] / (w[I_] * w[J_])
+            for a, b in ((i, j), (j, i)):
+                for c, e in ((k, l), (l, k)):
+                    T[a, b, c, e] = v
+    return T
+
+
+def _mandel_vec(E):
+    d = E.shape[0]
+    s2 = math.sqrt(2.0)
+    if d == 2:
+        return np.array([E[0, 0], E[1, 1], s2 * E[0, 1]])
+    return np.array([E[0, 0], E[1, 1], E[2, 2], s2 * E[1, 2], s2 * E[0, 2], s2 * E[0, 1]])
+
+
+# ------------------------------------------------------------------------------------------------
+# element level: closed forms and patch tests
+# ------------------------------------------------------------------------------------------------
+def test_p1_scalar_is_five_point_laplacian():
+    """Two P1 triangles per pixel, isotropic k: the assembled stencil is k * (4, -1, -1, -1, -1)."""
+    k = 2.5
+    g = fem.Grid((6, 6), "p1tri2_2d", "scalar")
+    K = fem.assemble_K(g, np.zeros(g.N, int), [k * np.eye(2)]).toarray()
+    for node in (0, 7, 35):
+        i, j = node % 6, node // 6
+        expect = np.zeros(g.N)
+        expect[node] = 4 * k
+        for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            expect[((i + di) % 6) + 6 * ((j + dj) % 6)] -= k
+        np.testing.assert_allclose(K[node], expect, atol=1e-13)
+
+
+def test_hex8_scalar_element_closed_form():
+    """Q1 3-D Laplacian element matrix: h*k*(1/3 diag, 0 edge, -1/12 face/body diagonal)."""
+    n, k = 4, 3.0
+    g = fem.Grid((n, n, n), "hex8_3d", "scalar")
+    Ke = fem.element_stiffness(g, k * np.eye(3))
+    h = 1.0 / n
+    for a, oa in enumerate(g.corners):
+        for b, ob in enumerate(g.corners):
+            dist = sum(x != y for x, y in zip(oa, ob))
+            expect = {0: 1 / 3, 1: 0.0, 2: -1 / 12, 3: -1 / 12}[dist] * h * k
+            assert abs(Ke[a, b] - expect) < 1e-14
+
+
+def test_q1_2d_scalar_element_closed_form():
+    """Q1 2-D Laplacian element: (1/6) * [4 -1 -2 -1] pattern (diag, edge, diagonal), h-free."""
+    g = fem.Grid((5, 5), "q1_2d", "scalar")
+    Ke = fem.element_stiffness(g, np.eye(2))
+    for a, oa in enumerate(g.corners):
+        for b, ob in enumerate(g.corners):
+            dist = sum(x != y for x, y in zip(oa, ob))
+            assert abs(Ke[a, b] - {0: 4 / 6, 1: -1 / 6, 2: -2 / 6}[dist]) < 1e-14
+
+
+@pytest.mark.parametrize("elem,shape", [("hex8_3d", (3, 4, 5)), ("q1_2d", (4, 5)), ("p1tri2_2d", (4, 5))])
+@pytest.mark.parametrize("physics", ["scalar", "elastic"])
+def test_patch_linear_field(elem, shape, physics):
+    """A linear nodal field has the exact constant gradient / Mandel strain at every quadrature point,
+    and its element energy is V * eps^T C eps (patch test; pins D and the Mandel sqrt(2) factors)."""
+    g = fem.Grid(shape, elem, physics)
+    rng = np.random.default_rng(1)
+    d = g.dim
+    h = g.h
+    X = np.array([[off[ax] * h[ax] for ax in range(d)] for off in g.corners])  # (ne, d)
+    if physics == "scalar":
+        gvec = rng.standard_normal(d)
+        ue = X @ gvec
+        target = gvec
+    else:
+        G = rng.standard_normal((d, d))       # u_i = sum_j G_ij x_j
+        ue = np.concatenate([X @ G[i] for i in range(d)])
+        E = 0.5 * (G + G.T)
+        target = _mandel_vec(E)
+    for B, w in fem.element_B(g):
+        np.testing.assert_allclose(B @ ue, target, atol=1e-12)
+    C = _rand_spd(g.m, 3)
+    Ke = fem.element_stiffness(g, C)
+    np.testing.assert_allclose(ue @ Ke @ ue, g.vp * target @ C @ target, rtol=1e-12)
+    # constant fields (translations) are in the kernel
+    for j in range(g.c):
+        t = np.zeros(g.c * g.ne)
+        t[j * g.ne:(j + 1) * g.ne] = 1.0
+        np.testing.assert_allclose(Ke @ t, 0.0, atol=1e-12)
+
+
+def test_hex8_elastic_rigid_rotations():
+    """Infinitesimal rotations u = W x (W skew) produce zero strain: 6 null modes of K_e in 3-D."""
+    g = fem.Grid((3, 3, 3), "hex8_3d", "elastic")
+    Ke = fem.element_stiffness(g, I.isotropic_elastic_mandel(1.0, 0.3))
+    ev = np.linalg.eigvalsh(Ke)
+    assert np.sum(np.abs(ev) < 1e-12 * ev.max()) == 6
+
+
+# ------------------------------------------------------------------------------------------------
+# Algorithm 2: symbol of K_ref against its closed form; pseudo-inverse action
+# ------------------------------------------------------------------------------------------------
+def _closed_form_hex8(shape, A4, h):
+    """K_hat_ab(k) = sum_ij A_{i a j b} S_ij, S_ii = k_i prod m_j, S_ij = sin_i sin_j prod m_k.
+
+    1-D factors on a periodic line of spacing h: stiffness (2 - 2 cos t)/h, mass h (2 + cos t)/3,
+    first-derivative coupling sin t (up to a sign that cancels in S_ij)."""
+    d = len(shape)
+    th = np.meshgrid(*[2 * np.pi * np.arange(n) / n for n in shape], indexing="ij")  # (z, y, x) order
+    th = th[::-1]                                      # x, y, z
+    hh = h
+    kf = [(2 - 2 * np.cos(t)) / hh[i] for i, t in enumerate(th)]
+    mf = [hh[i] * (2 + np.cos(t)) / 3 for i, t in enumerate(th)]
+    sf = [np.sin(t) for t in th]
+    S = np.empty((d, d) + tuple(shape))
+    for i in range(d):
+        for j in range(d):
+            if i == j:
+                val = kf[i].copy()
+                for l in range(d):
+                    if l != i:
+                        val = val * mf[l]
+            else:
+                val = sf[i] * sf[j]
+                for l in range(d):
+                    if l not in (i, j):
+                        val = val * mf[l]
+            S[i, j] = val
+    if A4.ndim == 2:       # scalar conductivity A_ij
+        return np.einsum("ij,ij...->...", A4, S)[None, None]
+    return np.einsum("iajb,ij...->ab...", A4, S)
+
+
+def test_symbol_hex8_scalar_closed_form():
+    shape = (4, 6, 8)  # (z, y, x)
+    g = fem.Grid(shape, "hex8_3d", "scalar")
+    A = _rand_spd(3, 5)
+    Kh = solvers.kref_symbol(g, A)
+    assert np.max(np.abs(Kh.imag)) < 1e-13 * np.max(np.abs(Kh.real))
+    ref = _closed_form_hex8(shape, A, g.h)
+    np.testing.assert_allclose(Kh.real, ref, atol=1e-12 * np.abs(ref).max())
+
+
+def test_symbol_hex8_elastic_closed_form():
+    shape = (4, 4, 6)
+    g = fem.Grid(shape, "hex8_3d", "elastic")
+    C = _rand_spd(6, 7)
+    Kh = solvers.kref_symbol(g, C)
+    assert np.max(np.abs(Kh.imag)) < 1e-13 * np.max(np.abs(Kh.real))
+    ref = _closed_form_hex8(shape, _mandel_tensor(C), g.h)
+    np.testing.assert_allclose(Kh.real, ref, atol=1e-12 * np.abs(ref).max())
+    # k = 0 block is the zero matrix: d null eigenvalues (Sec. 5.3)
+    assert np.max(np.abs(Kh[:, :, 0, 0, 0])) < 1e-12 * np.abs(ref).max()
+
+
+def test_symbol_p1_isotropic_closed_form():
+    shape = (6, 8)
+    g = fem.Grid(shape, "p1tri2_2d", "scalar")
+    k = 1.7
+    Kh = solvers.kref_symbol(g, k * np.eye(2))[0, 0]
+    t1 = 2 * np.pi * np.arange(8) / 8
+    t2 = 2 * np.pi * np.arange(6) / 6
+    hx, hy = 1 / 8, 1 / 6       # rectangular pixels: edge couplings scale with h_y/h_x and h_x/h_y
+    ref = k * ((hy / hx) * (2 - 2 * np.cos(t1))[None, :] + (hx / hy) * (2 - 2 * np.cos(t2))[:, None])
+    np.testing.assert_allclose(Kh, ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("elem,shape,physics", [("hex8_3d", (4, 6, 4), "elastic"),
+                                                 ("hex8_3d", (6, 4, 8), "scalar"),
+                                                 ("p1tri2_2d", (6, 8), "elastic"),
+                                                 ("q1_2d", (6, 4), "scalar")])
+def test_precond_is_pseudo_inverse(elem, shape, physics):
+    """K_ref (K_ref^+ r) = r minus its mean per component, for a random r (Eq. M_inverse)."""
+    g = fem.Grid(shape, elem, physics)
+    C = _rand_spd(g.m, 11)
+    Kref = fem.assemble_K(g, np.zeros(g.N, int), [C])
+    Kinv = solvers.kref_pinv_symbol(solvers.kref_symbol(g, C))
+    r = np.random.default_rng(2).standard_normal(g.c * g.N)
+    z = solvers.apply_precond(g, Kinv, r)
+    np.testing.assert_allclose(Kref @ z, solvers.project_mean_zero(g, r), atol=1e-11 * np.abs(r).max())
+    # z is mean-zero per component (pseudo-inverse at k = 0)
+    np.testing.assert_allclose(solvers.project_mean_zero(g, z), z, atol=1e-12)
+
+
+# ------------------------------------------------------------------------------------------------
+# invariants and exact results of the homogenised problem
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("elem,shape,physics", [("hex8_3d", (4, 4, 4), "elastic"),
+                                                 ("p1tri2_2d", (8, 8), "scalar"),
+                                                 ("q1_2d", (6, 6), "elastic")])
+def test_homogeneous_material(elem, shape, physics):
+    g = fem.Grid(shape, elem, physics)
+    C = _rand_spd(g.m, 4)
+    ids = np.zeros(g.N, int)
+    for e in np.eye(g.m):
+        np.testing.assert_allclose(fem.assemble_rhs(g, ids, [C], e), 0.0, atol=1e-13)
+    res = solvers.homogenise(g, ids, [C], np.eye(g.m), method="dense")
+    np.testing.assert_allclose(res["fields"], 0.0, atol=1e-12)
+    np.testing.assert_allclose(res["C_eff"], C, rtol=1e-13, atol=1e-13)
+
+
+def test_laminate_scalar_exact():
+    """Layers normal to x: C_eff = diag(harmonic, arithmetic[, arithmetic]) exactly (FE space holds the solution)."""
+    layers = [0, 0, 1, 1, 1, 0, 2, 2]
+    ks = [1.0, 10.0, 3.0]
+    for elem, shape in (("hex8_3d", (2, 3, 8)), ("p1tri2_2d", (4, 8)), ("q1_2d", (4, 8))):
+        g = fem.Grid(shape, elem, "scalar")
+        ids = I.laminate(shape, layers).ravel()
+        mod = [k * np.eye(g.dim) for k in ks]
+        res = solvers.homogenise(g, ids, mod, np.eye(g.dim), method="dense")
+        kk = np.array([ks[p] for p in layers])
+        expect = np.diag([1.0 / np.mean(1.0 / kk)] + [np.mean(kk)] * (g.dim - 1))
+        np.testing.assert_allclose(res["C_eff"], expect, rtol=1e-11, atol=1e-12)
+
+
+def test_laminate_elastic_exact():
+    """Exact laminate formula derived here for layers normal to x, in Mandel coordinates.
+
+    The fluctuation only produces the strain components that involve the normal (n-set: 11, 13,
+    12); the t-set strains equal the macro strain and the n-set stresses are continuous, which gives
+    C_eff = <C> - <C_:n C_nn^-1 C_n:> + <C_:n C_nn^-1> <C_nn^-1>^-1 <C_nn^-1 C_n:>."""
+    layers = [0, 1, 1, 0, 0, 2]
+    Cs = [_rand_spd(6, 20), _rand_spd(6, 21, 5.0), I.isotropic_elastic_mandel(7.0, 0.25)]
+    g = fem.Grid((2, 2, 6), "hex8_3d", "elastic")
+    ids = I.laminate((2, 2, 6), layers).ravel()
+    res = solvers.homogenise(g, ids, Cs, np.eye(6), method="dense")
+    nset = [0, 4, 5]
+    f = np.bincount(layers, minlength=3) / len(layers)
+    avg = lambda fn: sum(f[p] * fn(Cs[p]) for p in range(3))
+    inv_nn = lambda C: np.linalg.inv(C[np.ix_(nset, nset)])
+    A = avg(lambda C: C)
+    Bm = avg(lambda C: C[:, nset] @ inv_nn(C) @ C[nset, :])
+    L = avg(lambda C: C[:, nset] @ inv_nn(C))
+    M = avg(inv_nn)
+    R = avg(lambda C: inv_nn(C) @ C[nset, :])
+    expect = A - Bm + L @ np.linalg.inv(M) @ R
+    np.testing.assert_allclose(res["C_eff"], expect, rtol=1e-10, atol=1e-10)
+
+
+def _voigt_reuss_check(C_eff, moduli, ids):
+    f = np.bincount(np.asarray(ids).ravel(), minlength=len(moduli)) / np.asarray(ids).size
+    voigt = sum(fp * C for fp, C in zip(f, moduli))
+    reuss = np.linalg.inv(sum(fp * np.linalg.inv(C) for fp, C in zip(f, moduli)))
+    sym = 0.5 * (C_eff + C_eff.T)
+    assert np.linalg.eigvalsh(voigt - sym).min() > -1e-10
+    assert np.linalg.eigvalsh(sym - reuss).min() > -1e-10
+
+
+def test_circle2d_invariants_and_solver_agreement():
+    """32^2 P1 disc cell: dense-equivalent sparse LU, CG and PCG agree; C_eff symmetric, inside
+    the Voigt/Reuss bounds; Hill-Mandel: e^T <sigma> = <(e + Du)^T C (e + Du)>."""
+    w = I.workload_circle2d_32()
+    g = fem.Grid((32, 32), "p1tri2_2d", "scalar")
+    r_lu = solvers.homogenise(g, w["ids"], w["moduli"], w["loads"], method="sparse")
+    r_cg = solvers.homogenise(g, w["ids"], w["moduli"], w["loads"], method="cg", tol=1e-14)
+    r_pcg = solvers.homogenise(g, w["ids"], w["moduli"], w["loads"], method="pcg", tol=1e-13)
+    np.testing.assert_allclose(r_cg["C_eff"], r_lu["C_eff"], rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(r_pcg["C_eff"], r_lu["C_eff"], rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(r_pcg["fields"], r_lu["fields"], atol=1e-11)
+    C = r_lu["C_eff"]
+    assert abs(C[0, 1]) < 1e-12 and abs(C[0, 0] - C[1, 1]) < 1e-12   # square symmetry of the disc
+    _voigt_reuss_check(C, w["moduli"], w["ids"])
+    # Hill-Mandel energy identity
+    ids = w["ids"].ravel()
+    dofs = g.element_dofs()
+    for li, e in enumerate(w["loads"]):
+        u = r_lu["fields"][li]
+        energy = 0.0
+        for B, wq in fem.element_B(g):
+            strain = e[None, :] + u[dofs] @ B.T
+            Cq = np.asarray(w["moduli"])[ids]
+            energy += wq * np.einsum("ni,nij,nj->", strain, Cq, strain)
+        assert abs(energy - e @ r_lu["mean_flux"][li]) < 1e-11
+
+
+@pytest.mark.parametrize("elem,shape,physics", [("hex8_3d", (3, 2, 4), "elastic"),
+                                                 ("hex8_3d", (2, 3, 4), "scalar"),
+                                                 ("p1tri2_2d", (4, 6), "elastic"),
+                                                 ("q1_2d", (3, 4), "scalar")])
+def test_brute_force_tiny(elem, shape, physics):
+    """Tiny random grids: dense bordered solve == CG == PCG; residual K u - b vanishes."""
+    g = fem.Grid(shape, elem, physics)
+    rng = np.random.default_rng(9)
+    ids = rng.integers(0, 3, g.N)
+    mod = [_rand_spd(g.m, 30 + p, 10.0 ** p) for p in range(3)]
+    K = fem.assemble_K(g, ids, mod)
+    e = rng.standard_normal(g.m)
+    b = fem.assemble_rhs(g, ids, mod, e)
+    u_d = solvers.solve_dense(g, K, b)
+    np.testing.assert_allclose(K @ u_d, b, atol=1e-11 * np.abs(b).max())
+    u_c, _, _ = solvers.cg(K, b, tol=1e-15)
+    Kinv = solvers.kref_pinv_symbol(solvers.kref_symbol(g, fem.mean_material(g, ids, mod)))
+    res = solvers.pcg(lambda v: K @ v, lambda v: solvers.apply_precond(g, Kinv, v), b, 1e-14)
+    scale = np.abs(u_d).max()
+    np.testing.assert_allclose(solvers.project_mean_zero(g, u_c), u_d, atol=1e-10 * scale)
+    np.testing.assert_allclose(solvers.project_mean_zero(g, res["x"]), u_d, atol=1e-10 * scale)
+    # element-by-element stiffness rows agree with the assembled matrix
+    rows = rng.integers(0, g.c * g.N, 17)
+    np.testing.assert_allclose(fem.stiffness_rows(g, ids, mod, u_d, rows), (K @ u_d)[rows], atol=1e-12 * scale)
+
+
+def test_one_iteration_when_reference_equals_material():
+    """C = s * C_ref everywhere: M^-1 K = s I on the range, PCG converges in one step (Sec. 4.3)."""
+    g = fem.Grid((4, 6, 4), "hex8_3d", "elastic")
+    C_ref = _rand_spd(6, 40)
+    K = fem.assemble_K(g, np.zeros(g.N, int), [3.5 * C_ref])
+    Kinv = solvers.kref_pinv_symbol(solvers.kref_symbol(g, C_ref))
+    b = solvers.project_mean_zero(g, np.random.default_rng(3).standard_normal(g.c * g.N))
+    res = solvers.pcg(lambda v: K @ v, lambda v: solvers.apply_precond(g, Kinv, v), b, 1e-12)
+    assert res["iters"] == 1
+    np.testing.assert_allclose(res["alphas"][0], 1 / 3.5, rtol=1e-12)
+
+
+def test_ritz_values_inside_element_bounds():
+    """Sec. 4.3: the spectrum of K_ref^-1 K lies in [min_e lambda_min(C_ref^-1 C_e), max_e lambda_max];
+    the CG-Lanczos Ritz values from the PCG coefficients must lie there too."""
+    g = fem.Grid((6, 6, 6), "hex8_3d", "elastic")
+    rng = np.random.default_rng(5)
+    ids = rng.integers(0, 2, g.N)
+    mod = [I.isotropic_elastic_mandel(1.0, 0.3), I.isotropic_elastic_mandel(20.0, 0.2)]
+    C_ref = fem.mean_material(g, ids, mod)
+    K = fem.assemble_K(g, ids, mod)
+    Kinv = solvers.kref_pinv_symbol(solvers.kref_symbol(g, C_ref))
+    b = fem.assemble_rhs(g, ids, mod, np.eye(6)[0])
+    res = solvers.pcg(lambda v: K @ v, lambda v: solvers.apply_precond(g, Kinv, v), b, 1e-10)
+    ritz = solvers.lanczos_ritz(res["alphas"], res["betas"])
+    lam = [np.linalg.eigvals(np.linalg.solve(C_ref, C)).real for C in mod]
+    lo, hi = min(l.min() for l in lam), max(l.max() for l in lam)
+    assert ritz.min() >= lo * (1 - 1e-8) and ritz.max() <= hi * (1 + 1e-8)
+
+
+def test_iterations_flat_under_refinement():
+    """h-independent conditioning (Sec. 4.3): PCG iterations for the disc cell at fixed contrast
+    stay within +-20 % when the grid is refined 32 -> 64 -> 128 (tol 1e-8)."""
+    its = []
+    for n in (32, 64, 128):
+        g = fem.Grid((n, n), "p1tri2_2d", "scalar")
+        ids = I.circle2d(n, 0.3)
+        mod = [np.eye(2), 10.0 * np.eye(2)]
+        res = solvers.homogenise(g, ids, mod, np.eye(2)[:1], method="pcg", tol=1e-8)
+        its.append(res["iters"][0])
+    assert max(its) <= 1.2 * min(its), its
+
+
+def test_coated_sphere_bulk_modulus_golden():
+    """Sec. 6.2 coated sphere (golden parameters): the neutral coated inclusion leaves the
+    hydrostatic response of the K_eff matrix unchanged, so the cell bulk modulus is ~K_eff = 1.0
+    (exact in the continuum, up to the voxelisation of the two spheres here)."""
+    with open(os.path.join(HERE, "golden", "hashin_coated_sphere.json")) as fh:
+        gd = json.load(fh)
+    n = 16
+    g = fem.Grid((n, n, n), "hex8_3d", "elastic")
+    ids = I.coated_sphere(n, gd["r1"], gd["r2"]).ravel()
+    mod = [I.bulk_shear_mandel(gd["K1"], gd["G1"]), I.bulk_shear_mandel(gd["K2"], gd["G2"]),
+           I.bulk_shear_mandel(gd["K_eff"], gd["G_eff"])]
+    e = np.array([1.0, 1.0, 1.0, 0, 0, 0]) / 3.0          # hydrostatic strain, trace 1
+    res = solvers.homogenise(g, ids, mod, e[None, :], method="pcg", tol=1e-10)
+    sig = res["mean_flux"][0]
+    K_cell = sig[:3].mean()                                # mean normal stress / trace(e) = K
+    assert abs(K_cell - gd["K_eff"]) < 0.1, K_cell
+    # without the coating balance (core material everywhere inside r2) the response moves far away
+    mod_bad = [mod[0], mod[0], mod[2]]
+    sig_bad = solvers.homogenise(g, ids, mod_bad, e[None, :], method="pcg", tol=1e-8)["mean_flux"][0]
+    assert abs(sig_bad[:3].mean() - gd["K_eff"]) > 0.3
