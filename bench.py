@@ -1,0 +1,293 @@
+"""Benchmark: PCG of the periodic FE homogenisation cell problem on one GB300.
+
+Workload (one "step"): 128^3 trilinear-hexahedron small-strain elasticity, 60 seeded periodic
+spheres (E = 100, nu = 0.2) in a matrix (E = 1, nu = 0.3), reference material = volume mean,
+the 6 unit Mandel strains solved as one batch with plain FP64 PCG to a relative K_ref^-1-norm
+residual of 1e-6.  A step runs the whole hot path through the C ABI: Algorithm 2 (preconditioner
+build), right-hand sides, PCG iterations (stiffness apply, FFT preconditioner, fused updates and
+reductions) and the volume averages giving C_eff.
+
+value = PCG DOF*iterations/s = sum over loads of (3 * 128^3 * iterations) / step time (device
+time, inputs resident in HBM).  e2e = the same through fehom_setup with host phase ids, with the
+fluctuation fields read back to pinned host memory, host<->device copies inside the timed region.
+The mixed-precision form (FP32 stiffness/FFT in FP64 iterative refinement) is timed on the same
+workload and reported under "mixed".  The inputs (fields of 50 MB per load and component set)
+are larger than L2, and every step rewrites them, so no L2 flush is added.
+
+--impl reference runs the FP64 CPU oracle (assembled CSR + unpreconditioned CG) on a bounded
+sample of the same workload statistics on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG DOF*iter/s + time-to-1e-6 (128^3 elastic), % HBM peak; mixed vs FP64"
+UNIT = "DOF*iter/s"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 FMA throughput from unit counts: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (max clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                           "--format=csv,noheader,nounits", "-lms", "100"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self._proc = None
+        return self
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.samples.append(parts)
+
+    def __exit__(self, *exc):
+        if self._proc:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons}
+
+
+def workload():
+    from paper_2203_02962_gb300 import inputs
+    return inputs.workload_spheres_elastic(128, seed=0)
+
+
+def run_ours(args):
+    import torch
+    from paper_2203_02962_gb300 import fehom
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = workload()
+    n = w["n"]
+    N = n[0] * n[1] * n[2]
+    c = 3
+    loads = w["loads"]
+    ids_dev = torch.tensor(w["ids"].ravel(), device=dev)
+    stream = torch.cuda.current_stream()
+
+    def make(precision):
+        return fehom.Solver("hex8_3d", "elastic", n, ids_dev, w["moduli"], precision=precision, stream=stream)
+
+    def step(s):
+        s.precond_build()
+        return s.solve(loads, tol=w["tol"], fields=None)
+
+    results = {}
+    for prec in ("fp64", "mixed"):
+        s = make(prec)
+        for _ in range(args.warmup):
+            step(s)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters = []
+        with ClockSampler(0) as clk:
+            ev0.record(stream)
+            outs = [step(s) for _ in range(args.steps)]
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        its = [sum(i["iterations"] for i in o["info"]) for o in outs]
+        results[prec] = dict(ms=ms, iters=its[-1], out=outs[-1], clocks=clk.summary(), solver=s)
+
+    # e2e: host phase ids -> setup -> build -> solve -> fields back to pinned host memory
+    ids_host = np.ascontiguousarray(w["ids"].ravel())
+    fields_host = torch.empty((len(loads), c, N), dtype=torch.float64).pin_memory()
+    import ctypes
+    lib = fehom.load_library()
+
+    def e2e_step():
+        s = fehom.Solver("hex8_3d", "elastic", n, ids_host, w["moduli"], stream=stream)
+        s.precond_build()
+        flux = np.zeros((len(loads), 6))
+        ceff = np.zeros((6, 6))
+        info = (fehom.SolveInfo * len(loads))()
+        st = lib.fehom_solve(s.ctx, len(loads), fehom._dptr(np.ascontiguousarray(loads)), w["tol"], None,
+                             ctypes.c_void_p(fields_host.data_ptr()), 0, fehom._dptr(flux), fehom._dptr(ceff), info)
+        assert st == 0, st
+        s.close()
+        return sum(info[l].iterations for l in range(len(loads)))
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_iters = [e2e_step() for _ in range(max(1, args.steps))]
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
+
+    # dominant kernel: the FP64 stiffness apply, timed with CUDA events on the solver's stream
+    s64 = results["fp64"]["solver"]
+    x = torch.randn(c * N, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        s64.apply_stiffness(x)
+    reps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        s64.apply_stiffness(x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    k_ms = e0.elapsed_time(e1) / reps
+    flop_per_voxel = ISO_HEX8_ELASTIC_FLOPS
+    achieved_tf = flop_per_voxel * N / (k_ms * 1e-3) / 1e12
+
+    r64, rmx = results["fp64"], results["mixed"]
+    dof_iter_64 = c * N * r64["iters"]
+    value = dof_iter_64 / (r64["ms"] * 1e-3)
+    hbm, hbm_src = peaks()
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": r64["ms"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "128^3 hex8 elasticity, 60 periodic spheres E100/nu0.2 in E1/nu0.3, 6 unit Mandel "
+                               "strains batched, C_ref = volume mean, FP64 PCG to 1e-6",
+                   "dof": c * N, "loads": len(loads), "tol": w["tol"],
+                   "l2": "inputs > L2 (50 MB per field, 1.5 GB working set); no flush"},
+        "time_to_tol_s": r64["ms"] * 1e-3,
+        "pcg_iterations": r64["iters"],
+        "C_eff_diag": [float(v) for v in np.diag(r64["out"]["C_eff"])],
+        "e2e": {"value": c * N * (e_iters[-1]) / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(N + w["moduli"].nbytes + loads.nbytes),
+                "d2h_bytes_per_step": int(len(loads) * c * N * 8 + 6 * 6 * 8 + len(loads) * 6 * 8),
+                "ms_per_step": e2e_ms},
+        "mixed": {"value": c * N * rmx["iters"] / (rmx["ms"] * 1e-3), "ms_per_step": rmx["ms"],
+                  "time_to_tol_s": rmx["ms"] * 1e-3, "inner_iterations": rmx["iters"],
+                  "speedup_vs_fp64": r64["ms"] / rmx["ms"],
+                  "C_eff_rel_diff_vs_fp64": float(np.abs(rmx["out"]["C_eff"] - r64["out"]["C_eff"]).max()
+                                                  / np.abs(r64["out"]["C_eff"]).max()),
+                  "clocks": rmx["clocks"]},
+        "roofline": {"bound": "alu", "kernel": "hex8_apply_kernel<double> (FP64 stiffness apply)",
+                     "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                     "hbm_frac": (2 * c * N * 8 + N) / (k_ms * 1e-3) / 1e9 / hbm, "hbm_peak_gbs": hbm,
+                     "hbm_peak_source": hbm_src, "kernel_ms": k_ms},
+        "clocks": r64["clocks"],
+        "gpu_launches": None,
+    }
+    out["cpu_baseline"] = cpu_baseline(short=True)
+    print(json.dumps(out))
+
+
+# FP64 operations per voxel of the isotropic hex8 elasticity apply (modal formulation): counted from
+# the element code, FMA = 2 flop
+ISO_HEX8_ELASTIC_FLOPS = 420
+
+
+def cpu_baseline(short=False):
+    """The oracle (assembled CSR + unpreconditioned CG, FP64) on a bounded sample of the workload
+    statistics: a 32^3 cell with radii scaled by 1/4, 6 loads, a fixed number of CG iterations."""
+    from oracle import fem, solvers
+    from paper_2203_02962_gb300 import inputs
+    import scipy.sparse  # noqa: F401
+
+    n = 32
+    ids = inputs.spheres3d(n, count=60, rmin=2.0, rmax=4.0, seed=0)
+    mod = np.stack([inputs.isotropic_elastic_mandel(1.0, 0.3), inputs.isotropic_elastic_mandel(100.0, 0.2)])
+    g = fem.Grid((n, n, n), "hex8_3d", "elastic")
+    K = fem.assemble_K(g, ids.ravel(), mod)
+    iters = 40 if short else 200
+    t0 = time.perf_counter()
+    total = 0
+    for e in np.eye(6):
+        b = fem.assemble_rhs(g, ids.ravel(), mod, e)
+        _, it, _ = solvers.cg(K, b, tol=1e-30, maxiter=iters)
+        total += it
+    dt = time.perf_counter() - t0
+    return {"value": g.c * g.N * total / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"32^3 elastic spheres (radii 2-4), 6 loads x {iters} unpreconditioned CG iterations "
+                      f"(scipy CSR SpMV, 1 thread), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(short=True)
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(short=True))
+    v = statistics.median(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "oracle sample: 32^3 elastic spheres, 6 loads, CG"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[-1]["sample"], "value": v},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

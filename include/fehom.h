@@ -1,0 +1,183 @@
+/*
+ * fehom.h -- C ABI of the GB300 (sm_103a) FFT-preconditioned matrix-free finite-element
+ * homogenisation solver.
+ *
+ * The library solves the periodic cell problem of small-strain elasticity (Sec. 2, Eq. weak_form)
+ * or scalar conduction (App. A, Eq. weak_form_scalar) discretised on a regular grid of one-node
+ * stencils (Sec. 3, Fig. 3): K u = b with K = D^T W C D and b = -D^T W C e (Sec. 3.1,
+ * Eq. lin_system, one Newton step from u = 0, which is exact for linear materials).  It uses
+ * preconditioned CG with the reference-material preconditioner K_ref = D^T W C_ref D (Sec. 4.1,
+ * Eq. Kref), applied in Fourier space as a per-wavevector block (pseudo-)inverse (Sec. 4.2,
+ * Eq. M_inverse; Sec. 5.3, Eq. block_inversion) whose blocks are built matrix-free by
+ * Algorithm 2 (Sec. 5.2).
+ *
+ * Conventions shared by every call:
+ *   - Unit cell [0, l_x] x [0, l_y] (x [0, l_z]); n[a] nodes (= pixels/voxels) per axis; node
+ *     (i, j, k) at (i h_x, j h_y, k h_z), h_a = l_a / n[a]; voxel (i, j, k) has the corner nodes
+ *     (i + a, j + b, k + c) mod n.  Flat node index i + n_x (j + n_y k) (x fastest).
+ *   - Fields are component-blocked ("SoA"): entry comp * N + node, N = n_x n_y n_z, the ordering
+ *     u = [u_1; u_2; ...] of Eq. Du_mat.  c = 1 DOF per node for FEHOM_SCALAR, c = d for
+ *     FEHOM_ELASTIC.
+ *   - Flux / stress / gradient / strain vectors have m entries: m = d for FEHOM_SCALAR; Mandel
+ *     form (Eq. mandel_grad) for FEHOM_ELASTIC with m = 3, order (11, 22, 12) in 2-D and m = 6,
+ *     order (11, 22, 33, 23, 13, 12) in 3-D, sqrt(2) on shear strains.
+ *   - Material matrices are m x m, row-major, symmetric positive definite.
+ *   - Supported sizes: every n[a] is 2^k or 3 * 2^k with 2 <= n[a] <= 1024; n_x even.
+ *   - Device pointers are CUDA device (or managed) addresses on the context's device; the caller
+ *     owns every buffer it passes; the context owns everything it allocates.
+ *   - No call aborts or throws: each returns a status; fehom_last_error() describes the last
+ *     failure of a context.  A failed CUDA call returns FEHOM_E_CUDA and leaves the context
+ *     unusable for further solves (destroy it).
+ */
+#ifndef FEHOM_H
+#define FEHOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fehom_ctx fehom_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  FEHOM_OK = 0,
+  FEHOM_E_INVALID = 1,          /* bad argument (NULL, non-finite or non-SPD moduli, bad enum) */
+  FEHOM_E_UNSUPPORTED_SIZE = 2, /* grid size outside 2^k / 3*2^k, odd n_x, or too large */
+  FEHOM_E_OOM = 3,              /* device allocation failed */
+  FEHOM_E_CUDA = 4,             /* a CUDA runtime call failed */
+  FEHOM_E_NOT_CONVERGED = 5,    /* max_iter reached; outputs and info are still written */
+  FEHOM_E_BREAKDOWN = 6,        /* PCG breakdown: non-positive or non-finite curvature */
+  FEHOM_E_STATE = 7             /* call order violated (solve before precond_build, ...) */
+} fehom_status;
+
+typedef enum {
+  FEHOM_P1TRI2_2D = 1, /* two linear triangles per pixel, split along (0,0)-(1,1), 1 QP each (Fig. 3 b) */
+  FEHOM_HEX8_3D = 2,   /* trilinear hexahedron, 2x2x2 Gauss points (3-D analogue of Fig. 3 a) */
+  FEHOM_Q1_2D = 3      /* bilinear quadrilateral, 2x2 Gauss points (Fig. 3 a) */
+} fehom_elem;
+
+typedef enum { FEHOM_SCALAR = 1, FEHOM_ELASTIC = 2 } fehom_physics;
+
+typedef enum {
+  FEHOM_FP64 = 0,  /* every step in FP64 */
+  FEHOM_MIXED = 1  /* FP32 stiffness apply, FFT and vectors inside an FP64 iterative-refinement loop;
+                      FP64 dots, alpha/beta, true residual and volume averages */
+} fehom_precision;
+
+typedef struct {
+  int precision;     /* fehom_precision (default FEHOM_FP64) */
+  int max_iter;      /* PCG iteration cap per load (default 10000); mixed: cap on inner iterations in total */
+  double inner_tol;  /* mixed only: relative K_ref^-1-norm reduction per inner FP32 solve (default 1e-3) */
+  void* stream;      /* cudaStream_t for every launch and copy; NULL = a blocking stream the context creates */
+  int use_graph;     /* 1 (default): replay PCG iterations from a captured CUDA graph; 0: plain launches */
+} fehom_options;
+
+typedef struct {
+  int iterations;          /* PCG iterations (mixed: inner FP32 iterations summed over refinements) */
+  int refinements;         /* mixed: outer FP64 refinement steps (FP64: 0) */
+  int converged;           /* 1 if sqrt(<r, K_ref^+ r>) <= tol * sqrt(<b, K_ref^+ b>) in FP64 */
+  double rel_residual_M;   /* final sqrt(<r, K_ref^+ r> / <b, K_ref^+ b>), r the recursive (FP64) or true (mixed) residual */
+  double rel_residual_2;   /* final true ||b - K u||_2 / ||b||_2, computed in FP64 */
+  double solve_ms;         /* device time of this load's share of the solve (the batch time for batched loads) */
+} fehom_solve_info;
+
+/* Default options (precision FP64, max_iter 10000, inner_tol 1e-3, default stream, graphs on). */
+void fehom_default_options(fehom_options* opt);
+
+/*
+ * fehom_setup -- create a context for one periodic cell (Sec. 3, Fig. 3; Sec. 4.1, Eq. Kref).
+ *   out            receives the new context (set to NULL on failure).
+ *   elem, physics  fehom_elem / fehom_physics; FEHOM_HEX8_3D needs n[2] > 1, the 2-D elements n[2] == 1.
+ *   n              nodes per axis (x, y, z), see the size rule above.
+ *   cell           cell edge lengths l_x, l_y, l_z (host, 3 doubles), or NULL for the unit cell.
+ *   phase_ids      N uint8 phase ids, one per pixel/voxel, x fastest (host or device, per ids_on_device);
+ *                  copied, the caller may free it after the call.  Every id must be < n_phases.
+ *   n_phases       1..256.
+ *   phase_moduli   host, n_phases x m x m doubles: the material matrix C of each phase (Sec. 3.1; the
+ *                  conductivity matrix of App. A for FEHOM_SCALAR).  Copied.
+ *   ref_material   host m x m C_ref, or NULL for the volume mean C_mean = (1/|Y|) sum_Q C(x_Q) w_Q
+ *                  (Sec. 6.2).  Copied.
+ *   opt            NULL for the defaults.
+ * Allocates the device work buffers of one load; fehom_solve grows them for more loads.
+ * Errors: FEHOM_E_INVALID, FEHOM_E_UNSUPPORTED_SIZE, FEHOM_E_OOM, FEHOM_E_CUDA.
+ */
+fehom_status fehom_setup(fehom_ctx** out, int elem, int physics, const int64_t n[3], const double* cell,
+                         const uint8_t* phase_ids, int ids_on_device, int n_phases,
+                         const double* phase_moduli, const double* ref_material, const fehom_options* opt);
+
+/*
+ * fehom_precond_build -- Algorithm 2 (Sec. 5.2) and the block (pseudo-)inversion of Sec. 5.3.
+ * For each DOF type beta it applies K_ref (the stiffness kernel with the uniform material C_ref)
+ * to the unit impulse at node 0, forward-FFTs the c result components into the diagonals of the
+ * Fourier blocks K_hat[alpha, beta](k), checks that the blocks are real symmetric, inverts them per
+ * wavevector and stores the Moore-Penrose pseudo-inverse of the k = 0 block (the zero matrix for
+ * one-node stencils).  The table is kept in FP64 (and FP32 for the mixed path), half spectrum.
+ * Errors: FEHOM_E_STATE (no setup), FEHOM_E_INVALID (a block that is not real symmetric positive
+ * definite away from k = 0), FEHOM_E_OOM, FEHOM_E_CUDA.
+ */
+fehom_status fehom_precond_build(fehom_ctx* ctx);
+
+/*
+ * fehom_solve -- solve the cell problem for n_loads macroscopic gradients / strains e_l
+ * (Eq. lin_system with u_(0) = 0 and Eq. prec_lin_system_FFT), all loads as one batch.
+ *   loads          host, n_loads x m doubles (row l = e_l).
+ *   tol            PCG stop: sqrt(<r, K_ref^+ r>) <= tol * sqrt(<b, K_ref^+ b>) (Sec. 6, termination
+ *                  criteria, normalised by b).  0 < tol < 1.
+ *   x0             NULL (zero initial guess) or a device array of n_loads x c x N FP64 initial guesses;
+ *                  their mean per component is removed before use.
+ *   fluct_out      NULL, or n_loads x c x N FP64 fluctuation fields u~ (mean zero per component),
+ *                  host or device per fluct_on_device.
+ *   mean_flux_out  NULL or host n_loads x m: <sigma>_l = (1/|Y|) sum_Q w_Q C_Q (e_l + (D u~_l)_Q).
+ *   c_eff_out      NULL or host m x m: C_eff = S E^-1 (S, E: mean fluxes and loads as columns), written
+ *                  only when n_loads == m and E is invertible (the unit loads give C_eff[:, l] = <sigma>_l).
+ *   info           NULL or host array of n_loads fehom_solve_info.
+ * Errors: FEHOM_E_STATE (before fehom_precond_build), FEHOM_E_INVALID, FEHOM_E_NOT_CONVERGED
+ * (outputs written), FEHOM_E_BREAKDOWN, FEHOM_E_OOM, FEHOM_E_CUDA.
+ */
+fehom_status fehom_solve(fehom_ctx* ctx, int n_loads, const double* loads, double tol, const double* x0,
+                         double* fluct_out, int fluct_on_device, double* mean_flux_out, double* c_eff_out,
+                         fehom_solve_info* info);
+
+/* Release every device and host resource of the context (NULL is ignored). */
+void fehom_destroy(fehom_ctx* ctx);
+
+/* Text of the context's last error ("" if none); owned by the context, valid until the next call.  With
+ * ctx == NULL: the message of the last failed fehom_setup on the calling thread. */
+const char* fehom_last_error(const fehom_ctx* ctx);
+
+/* Grid facts of a context: c (DOF per node), m (flux components), N (nodes), nxh (n_x / 2 + 1). */
+fehom_status fehom_query(const fehom_ctx* ctx, int* c, int* m, int64_t* N, int64_t* nxh);
+
+/* ---------------------------------------------------------------------------------------------
+ * Operator-level entry points: single steps of the solve, exposed so that each can be checked on
+ * its own.  All arrays are device arrays of the context's device; `precision` selects FP64
+ * (double arrays) or FEHOM_MIXED (float arrays).  They run on the context's stream and return
+ * after the work is complete.
+ * ------------------------------------------------------------------------------------------- */
+
+/* y = K x = D^T W C D x, matrix-free (Sec. 5.1, the gradient as a short convolution and the
+ * weighted divergence D^T W).  x, y: c x N.  Needs fehom_setup. */
+fehom_status fehom_apply_stiffness(fehom_ctx* ctx, const void* x, void* y, int precision);
+
+/* b = -D^T W C e for one macroscopic gradient / strain e (host, m doubles); b: c x N FP64. */
+fehom_status fehom_rhs(fehom_ctx* ctx, const double* e, double* b);
+
+/* z = K_ref^+ r = F^-1 K_hat^+ F r (Eq. M_inverse); r, z: c x N.  Needs fehom_precond_build. */
+fehom_status fehom_apply_precond(fehom_ctx* ctx, const void* r, void* z, int precision);
+
+/* Copy the FP64 inverse symbol table to the host: out[e * Nh + (kz * n_y + ky) * nxh + kx] for the
+ * packed symmetric entries e of K_hat^+(k) (c = 1: (00); c = 2: (00, 11, 01); c = 3: (00, 11, 22,
+ * 12, 02, 01)), half spectrum kx = 0..n_x/2, Nh = nxh n_y n_z.  The stored values include the
+ * inverse-DFT factor 1/N.  out holds c(c+1)/2 * Nh doubles.  Needs fehom_precond_build. */
+fehom_status fehom_get_symbol_inverse(fehom_ctx* ctx, double* out);
+
+/* <sigma> = (1/|Y|) sum_Q w_Q C_Q (e + (D u)_Q) for a device FP64 field u (c x N) and host load e. */
+fehom_status fehom_mean_flux(fehom_ctx* ctx, const double* e, const double* u, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEHOM_H */

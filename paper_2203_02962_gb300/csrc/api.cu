@@ -1,0 +1,1086 @@
+// Host runtime of libfehom.so: the C ABI declared in include/fehom.h.
+//
+// fehom_setup        validates the grid and materials, uploads the phase ids, forms the reference
+//                    material (volume mean C_mean of Sec. 6.2 unless given) and the gradient-space
+//                    material tables used by the stiffness kernel.
+// fehom_precond_build Algorithm 2 (Sec. 5.2) on the device + the block (pseudo-)inverse (Sec. 5.3).
+// fehom_solve        PCG of Sec. 4.1 (symmetric form) for a batch of loads, each iteration one
+//                    stiffness launch and the FFT passes, with alpha, beta and the stopping test kept
+//                    in device memory; iterations replayed from a captured CUDA graph.  The mixed
+//                    precision variant wraps an FP32 PCG in FP64 iterative refinement.
+#include "fehom_internal.cuh"
+#include "../../include/fehom.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace fehom;
+
+struct fehom_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  fehom_options opt{};
+  Dims d{};
+  int physics = 0, m = 0, D = 0;  // D: gradient-space size c * dim
+  double h[3] = {1, 1, 1};
+  double vol = 1.0;
+  int n_phases = 0;
+  std::vector<double> moduli;     // [phase][m*m]
+  std::vector<double> cref;       // [m*m]
+  std::vector<double> frac;       // volume fractions
+  bool iso = false;               // isotropic phases on a cubic grid (fast stiffness path)
+  bool iso_ref = false;
+  // device
+  uint8_t* ids = nullptr;
+  double* mats64 = nullptr; float* mats32 = nullptr;   // [phase][D*D]
+  double* iso64 = nullptr; float* iso32 = nullptr;     // [phase][2]
+  double* rmats64 = nullptr; double* riso64 = nullptr;  // reference material (one phase)
+  double* moduli_d = nullptr;                           // [phase][m*m]
+  double2* tw64[3] = {nullptr, nullptr, nullptr};
+  float2* tw32[3] = {nullptr, nullptr, nullptr};
+  double* sym64 = nullptr; float* sym32 = nullptr;
+  bool built = false;
+  // work buffers (grown on demand)
+  int cap64 = 0, cap32 = 0;
+  double *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *ap64 = nullptr, *b64 = nullptr;
+  double2* spec64 = nullptr;
+  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *ap32 = nullptr;
+  float2* spec32 = nullptr;
+  PcgState* st = nullptr;
+  RedScratch red{};
+  double* tau = nullptr;       // [load][phase][D]
+  double* loads_d = nullptr;   // [load][m]
+  double* partial = nullptr;   // general reduction scratch
+  size_t partial_cap = 0;
+  // captured iteration graphs
+  cudaGraphExec_t graph_exec = nullptr;
+  long long graph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_setup_error;  // message of the last failed fehom_setup on this thread
+
+constexpr int kRedBlocks = 1 << 16;
+constexpr int kChunk = 8;  // PCG iterations per graph replay / convergence poll
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);              \
+      return e_ == cudaErrorMemoryAllocation ? FEHOM_E_OOM : FEHOM_E_CUDA;        \
+    }                                                                             \
+  } while (0)
+
+#define FAIL(code, msg)      \
+  do {                       \
+    ctx->err = (msg);        \
+    return (code);           \
+  } while (0)
+
+bool size_ok(long long n) {
+  if (n < 2 || n > 1024) return false;
+  while (n % 2 == 0) n /= 2;
+  return n == 1 || n == 3;
+}
+
+template <typename P> void dfree(P*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+// symmetric positive definite check (Cholesky) of an m x m row-major matrix
+bool spd(const double* A, int m) {
+  std::vector<double> L(m * m, 0.0);
+  double mx = 0;
+  for (int i = 0; i < m * m; ++i) {
+    if (!std::isfinite(A[i])) return false;
+    mx = std::max(mx, std::fabs(A[i]));
+  }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j)
+      if (std::fabs(A[i * m + j] - A[j * m + i]) > 1e-12 * mx) return false;
+  for (int j = 0; j < m; ++j) {
+    double s = A[j * m + j];
+    for (int k = 0; k < j; ++k) s -= L[j * m + k] * L[j * m + k];
+    if (!(s > 1e-14 * mx)) return false;
+    L[j * m + j] = std::sqrt(s);
+    for (int i = j + 1; i < m; ++i) {
+      double t = A[i * m + j];
+      for (int k = 0; k < j; ++k) t -= L[i * m + k] * L[j * m + k];
+      L[i * m + j] = t / L[j * m + j];
+    }
+  }
+  return true;
+}
+
+// P: flux vector (m) <- gradient vector (D, index comp * dim + deriv for elasticity, deriv for scalar)
+std::vector<double> grad_to_flux(int dim, int physics) {
+  if (physics == FEHOM_SCALAR) {
+    std::vector<double> P(dim * dim, 0.0);
+    for (int i = 0; i < dim; ++i) P[i * dim + i] = 1.0;
+    return P;
+  }
+  const int m = dim * (dim + 1) / 2, D = dim * dim;
+  std::vector<double> P(m * D, 0.0);
+  for (int a = 0; a < dim; ++a) P[a * D + a * dim + a] = 1.0;
+  const double r2 = 1.0 / std::sqrt(2.0);
+  const int pairs3[3][2] = {{1, 2}, {0, 2}, {0, 1}};
+  const int pairs2[1][2] = {{0, 1}};
+  const int np = dim == 3 ? 3 : 1;
+  for (int s = 0; s < np; ++s) {
+    const int a = dim == 3 ? pairs3[s][0] : pairs2[s][0];
+    const int b = dim == 3 ? pairs3[s][1] : pairs2[s][1];
+    const int I = dim + s;
+    P[I * D + a * dim + b] = r2;
+    P[I * D + b * dim + a] = r2;
+  }
+  return P;
+}
+
+// element weight and per-direction gradient scale of the stiffness kernel's gradient coordinates
+void kernel_scales(const fehom_ctx* ctx, double* w, double s[3]) {
+  for (int i = 0; i < 3; ++i) {
+    if (ctx->d.elem == HEX8_3D) s[i] = 1.0 / (4.0 * ctx->h[i]);        // d/dx = (2/h) d/dxi, modal sums carry 8
+    else if (ctx->d.elem == Q1_2D) s[i] = 1.0 / (2.0 * ctx->h[i]);     // (2/h) / 4
+    else s[i] = 1.0 / ctx->h[i];                                       // raw differences of P1
+  }
+  *w = (ctx->d.elem == P1TRI2_2D) ? 0.5 * ctx->vol : ctx->vol;
+}
+
+// Chat = w S P^T C P S  (D x D) for one material C (m x m)
+void grad_material(const fehom_ctx* ctx, const double* C, double* out) {
+  const int dim = ctx->d.dim, m = ctx->m, D = ctx->D;
+  const std::vector<double> P = grad_to_flux(dim, ctx->physics);
+  double w, s[3];
+  kernel_scales(ctx, &w, s);
+  std::vector<double> sc(D);
+  for (int k = 0; k < D; ++k) sc[k] = s[k % dim];
+  for (int a = 0; a < D; ++a)
+    for (int b = 0; b < D; ++b) {
+      double acc = 0.0;
+      for (int I = 0; I < m; ++I)
+        for (int J = 0; J < m; ++J) acc += P[I * D + a] * C[I * m + J] * P[J * D + b];
+      out[a * D + b] = w * sc[a] * sc[b] * acc;
+    }
+}
+
+// tau = w S P^T C e (D)
+void grad_prestress(const fehom_ctx* ctx, const double* C, const double* e, double* out) {
+  const int dim = ctx->d.dim, m = ctx->m, D = ctx->D;
+  const std::vector<double> P = grad_to_flux(dim, ctx->physics);
+  double w, s[3];
+  kernel_scales(ctx, &w, s);
+  for (int a = 0; a < D; ++a) {
+    double acc = 0.0;
+    for (int I = 0; I < m; ++I)
+      for (int J = 0; J < m; ++J) acc += P[I * D + a] * C[I * m + J] * e[J];
+    out[a] = w * s[a % dim] * acc;
+  }
+}
+
+// isotropic elastic Mandel matrix C = lam J + 2 mu I ?
+bool iso_elastic(const double* C, int dim, double* lam, double* mu) {
+  const int m = dim * (dim + 1) / 2;
+  double mx = 0;
+  for (int i = 0; i < m * m; ++i) mx = std::max(mx, std::fabs(C[i]));
+  const double l = C[0 * m + 1], mu2 = C[(m - 1) * m + (m - 1)];
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      double v = 0;
+      if (i < dim && j < dim) v = l;
+      if (i == j) v += mu2;
+      if (std::fabs(C[i * m + j] - v) > 1e-13 * mx) return false;
+    }
+  *lam = l;
+  *mu = 0.5 * mu2;
+  return true;
+}
+
+// symmetric Jacobi eigen-decomposition (small n), for the k = 0 pseudo-inverse
+void jacobi_eig(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& ev) {
+  V.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += A[p * n + q] * A[p * n + q];
+    if (off < 1e-300) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double theta = (A[q * n + q] - A[p * n + p]) / (2 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1));
+        const double c = 1 / std::sqrt(t * t + 1), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  ev.resize(n);
+  for (int i = 0; i < n; ++i) ev[i] = A[i * n + i];
+}
+
+void fill_dims_args(fehom_ctx* ctx, FftArgs& f, bool fp32, int n_loads) {
+  f.d = ctx->d;
+  f.n_loads = n_loads;
+  f.load_stride_f = (long long)ctx->d.c * ctx->d.N;
+  f.load_stride_s = (long long)ctx->d.c * ctx->d.Nh;
+  if (fp32) {
+    f.tw = Twiddles{ctx->tw32[0], ctx->tw32[1], ctx->tw32[2]};
+    f.sym = ctx->sym32;
+  } else {
+    f.tw = Twiddles{ctx->tw64[0], ctx->tw64[1], ctx->tw64[2]};
+    f.sym = ctx->sym64;
+  }
+  f.st = nullptr;
+  f.red = ctx->red;
+  f.init = 0;
+  f.mode = FX_PLAIN;
+  f.f0 = nullptr;
+  f.f1 = nullptr;
+  f.f2 = nullptr;
+  f.spec = fp32 ? (void*)ctx->spec32 : (void*)ctx->spec64;
+}
+
+StencilArgs stencil_args(fehom_ctx* ctx, bool fp32, int n_loads) {
+  StencilArgs a{};
+  a.d = ctx->d;
+  a.ids = ctx->ids;
+  a.mats = fp32 ? (const void*)ctx->mats32 : (const void*)ctx->mats64;
+  a.iso = ctx->iso ? (fp32 ? (const void*)ctx->iso32 : (const void*)ctx->iso64) : nullptr;
+  a.tau = nullptr;
+  a.n_phases = ctx->n_phases;
+  a.n_loads = n_loads;
+  a.load_stride = (long long)ctx->d.c * ctx->d.N;
+  a.y_scale = 1.0;
+  a.st = nullptr;
+  a.red = ctx->red;
+  return a;
+}
+
+fehom_status grow64(fehom_ctx* ctx, int n) {
+  if (n <= ctx->cap64) return FEHOM_OK;
+  dfree(ctx->x64); dfree(ctx->r64); dfree(ctx->p64); dfree(ctx->ap64); dfree(ctx->b64); dfree(ctx->spec64);
+  ctx->graph_key[0] = 0;
+  const size_t f = (size_t)n * ctx->d.c * ctx->d.N, sp = (size_t)n * ctx->d.c * ctx->d.Nh;
+  CK(cudaMalloc(&ctx->x64, f * sizeof(double)));
+  CK(cudaMalloc(&ctx->r64, f * sizeof(double)));
+  CK(cudaMalloc(&ctx->p64, f * sizeof(double)));
+  CK(cudaMalloc(&ctx->ap64, f * sizeof(double)));
+  CK(cudaMalloc(&ctx->b64, f * sizeof(double)));
+  CK(cudaMalloc(&ctx->spec64, sp * sizeof(double2)));
+  ctx->cap64 = n;
+  return FEHOM_OK;
+}
+
+fehom_status grow32(fehom_ctx* ctx, int n) {
+  if (n <= ctx->cap32) return FEHOM_OK;
+  dfree(ctx->x32); dfree(ctx->r32); dfree(ctx->p32); dfree(ctx->ap32); dfree(ctx->spec32);
+  ctx->graph_key[0] = 0;
+  const size_t f = (size_t)n * ctx->d.c * ctx->d.N, sp = (size_t)n * ctx->d.c * ctx->d.Nh;
+  CK(cudaMalloc(&ctx->x32, f * sizeof(float)));
+  CK(cudaMalloc(&ctx->r32, f * sizeof(float)));
+  CK(cudaMalloc(&ctx->p32, f * sizeof(float)));
+  CK(cudaMalloc(&ctx->ap32, f * sizeof(float)));
+  CK(cudaMalloc(&ctx->spec32, sp * sizeof(float2)));
+  ctx->cap32 = n;
+  return FEHOM_OK;
+}
+
+fehom_status ensure_partial(fehom_ctx* ctx, size_t n) {
+  if (n <= ctx->partial_cap) return FEHOM_OK;
+  dfree(ctx->partial);
+  CK(cudaMalloc(&ctx->partial, n * sizeof(double)));
+  ctx->partial_cap = n;
+  return FEHOM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// preconditioner passes
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+cudaError_t fft_forward(fehom_ctx* ctx, FftArgs f, cudaStream_t s) {
+  cudaError_t e = launch_fft_x_fwd<T>(f, s);
+  if (e != cudaSuccess) return e;
+  if (ctx->d.dim == 3 && (e = launch_fft_y<T>(f, 0, s)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t precond_passes(fehom_ctx* ctx, FftArgs f, int fwd_mode, int inv_mode, void* fwd_field,
+                           const void* fwd_ap, void* inv_f0, void* inv_f2, cudaStream_t s) {
+  cudaError_t e;
+  f.mode = fwd_mode;
+  f.f0 = fwd_field;
+  f.f1 = fwd_ap;
+  if ((e = launch_fft_x_fwd<T>(f, s)) != cudaSuccess) return e;
+  if (ctx->d.dim == 3 && (e = launch_fft_y<T>(f, 0, s)) != cudaSuccess) return e;
+  if ((e = launch_fft_last_solve<T>(f, s)) != cudaSuccess) return e;
+  if (ctx->d.dim == 3 && (e = launch_fft_y<T>(f, 1, s)) != cudaSuccess) return e;
+  f.mode = inv_mode;
+  f.f0 = inv_f0;
+  f.f2 = inv_f2;
+  return launch_fft_x_inv<T>(f, s);
+}
+
+// one PCG iteration for every active load
+template <typename T>
+cudaError_t pcg_iteration(fehom_ctx* ctx, int n_loads, T* x, T* r, T* p, T* ap, cudaStream_t s) {
+  const bool fp32 = sizeof(T) == 4;
+  StencilArgs a = stencil_args(ctx, fp32, n_loads);
+  a.x = p;
+  a.y = ap;
+  a.st = ctx->st;
+  cudaError_t e = launch_stiffness<T>(a, s);
+  if (e != cudaSuccess) return e;
+  FftArgs f;
+  fill_dims_args(ctx, f, fp32, n_loads);
+  f.st = ctx->st;
+  return precond_passes<T>(ctx, f, FX_PCG, FX_PCG, r, ap, x, p, s);
+}
+
+template <typename T>
+fehom_status run_iterations(fehom_ctx* ctx, int n_loads, T* x, T* r, T* p, T* ap, int max_iter,
+                            std::vector<PcgState>& hs) {
+  cudaStream_t s = ctx->stream;
+  const long long key[8] = {1, (long long)n_loads, (long long)(size_t)x, (long long)(size_t)r, (long long)(size_t)p,
+                            (long long)(size_t)ap, (long long)sizeof(T), (long long)(size_t)ctx->st};
+  bool use_graph = ctx->opt.use_graph != 0;
+  if (use_graph && std::memcmp(key, ctx->graph_key, sizeof(key)) != 0) {
+    if (ctx->graph_exec) {
+      cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+    }
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kChunk && e == cudaSuccess; ++i) e = pcg_iteration<T>(ctx, n_loads, x, r, p, ap, s);
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    CK(e);
+    CK(e2);
+    CK(cudaGraphInstantiate(&ctx->graph_exec, g, 0));
+    cudaGraphDestroy(g);
+    std::memcpy(ctx->graph_key, key, sizeof(key));
+  }
+  hs.resize(n_loads);
+  for (int done = 0; done < max_iter + kChunk;) {
+    if (use_graph) {
+      CK(cudaGraphLaunch(ctx->graph_exec, s));
+    } else {
+      for (int i = 0; i < kChunk; ++i) CK(pcg_iteration<T>(ctx, n_loads, x, r, p, ap, s));
+    }
+    done += kChunk;
+    CK(cudaMemcpyAsync(hs.data(), ctx->st, sizeof(PcgState) * n_loads, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int l = 0; l < n_loads; ++l)
+      if (hs[l].state == ST_RUN || hs[l].state == ST_CONV || hs[l].state == ST_FIN_MAX) all = false;
+    if (all) break;
+  }
+  return FEHOM_OK;
+}
+
+// initial preconditioner apply of PCG: z0 = K_ref^+ r0, p0 = z0, rz0, bnorm2
+template <typename T>
+fehom_status pcg_init(fehom_ctx* ctx, int n_loads, T* r, T* p) {
+  FftArgs f;
+  fill_dims_args(ctx, f, sizeof(T) == 4, n_loads);
+  f.st = ctx->st;
+  f.init = 1;
+  CK(precond_passes<T>(ctx, f, FX_PLAIN, FX_PCG_INIT, r, nullptr, nullptr, p, ctx->stream));
+  return FEHOM_OK;
+}
+
+fehom_status set_states(fehom_ctx* ctx, int n_loads, double tol_rel, int max_iter, double bnorm2) {
+  std::vector<PcgState> hs(n_loads);
+  for (auto& s : hs) {
+    std::memset(&s, 0, sizeof(s));
+    s.bnorm2 = bnorm2;
+    s.tol2_rel = tol_rel * tol_rel;
+    s.state = ST_RUN;
+    s.max_iter = max_iter;
+  }
+  CK(cudaMemcpyAsync(ctx->st, hs.data(), sizeof(PcgState) * n_loads, cudaMemcpyHostToDevice, ctx->stream));
+  return FEHOM_OK;
+}
+
+// b = -D^T W C e for every load (FP64) into `b`
+fehom_status compute_rhs(fehom_ctx* ctx, int n_loads, const double* loads, double* b) {
+  const int P = ctx->n_phases, D = ctx->D;
+  std::vector<double> tau((size_t)n_loads * P * D);
+  for (int l = 0; l < n_loads; ++l)
+    for (int ph = 0; ph < P; ++ph)
+      grad_prestress(ctx, &ctx->moduli[(size_t)ph * ctx->m * ctx->m], loads + (size_t)l * ctx->m,
+                     &tau[((size_t)l * P + ph) * D]);
+  dfree(ctx->tau);
+  CK(cudaMalloc(&ctx->tau, tau.size() * sizeof(double)));
+  CK(cudaMemcpyAsync(ctx->tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  StencilArgs a = stencil_args(ctx, false, n_loads);
+  a.x = nullptr;
+  a.y = b;
+  a.tau = ctx->tau;
+  a.y_scale = -1.0;
+  CK(launch_stiffness<double>(a, ctx->stream));
+  return FEHOM_OK;
+}
+
+fehom_status mean_flux(fehom_ctx* ctx, int n_loads, const double* loads_host, const double* u, double* out) {
+  dfree(ctx->loads_d);
+  CK(cudaMalloc(&ctx->loads_d, sizeof(double) * n_loads * ctx->m));
+  CK(cudaMemcpyAsync(ctx->loads_d, loads_host, sizeof(double) * n_loads * ctx->m, cudaMemcpyHostToDevice, ctx->stream));
+  const int blocks_max = 4 * 152;
+  fehom_status st = ensure_partial(ctx, (size_t)n_loads * blocks_max * ctx->m);
+  if (st != FEHOM_OK) return st;
+  MeanFluxArgs a{};
+  a.d = ctx->d;
+  a.u = u;
+  a.ids = ctx->ids;
+  a.moduli = ctx->moduli_d;
+  a.loads = ctx->loads_d;
+  a.n_loads = n_loads;
+  a.m = ctx->m;
+  a.load_stride = (long long)ctx->d.c * ctx->d.N;
+  for (int i = 0; i < 3; ++i) a.h[i] = ctx->h[i];
+  a.partial = ctx->partial;
+  int blocks = 0;
+  CK(launch_mean_flux(a, &blocks, ctx->stream));
+  std::vector<double> hp((size_t)n_loads * blocks * ctx->m);
+  CK(cudaMemcpyAsync(hp.data(), ctx->partial, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  double cell_vol = 1.0;
+  for (int i = 0; i < ctx->d.dim; ++i) cell_vol *= ctx->h[i] * (i == 0 ? ctx->d.nx : i == 1 ? ctx->d.ny : ctx->d.nz);
+  for (int l = 0; l < n_loads; ++l)
+    for (int r = 0; r < ctx->m; ++r) {
+      double acc = 0.0;
+      for (int b = 0; b < blocks; ++b) acc += hp[((size_t)l * blocks + b) * ctx->m + r];
+      out[l * ctx->m + r] = acc / cell_vol;
+    }
+  return FEHOM_OK;
+}
+
+fehom_status norms2(fehom_ctx* ctx, int n_loads, const double* v, std::vector<double>& out) {
+  fehom_status st = ensure_partial(ctx, (size_t)n_loads * 256);
+  if (st != FEHOM_OK) return st;
+  int blocks = 0;
+  const long long n = (long long)ctx->d.c * ctx->d.N;
+  CK(launch_norm2(v, n, n_loads, n, ctx->partial, &blocks, ctx->stream));
+  std::vector<double> hp((size_t)n_loads * blocks);
+  CK(cudaMemcpyAsync(hp.data(), ctx->partial, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  out.assign(n_loads, 0.0);
+  for (int l = 0; l < n_loads; ++l)
+    for (int b = 0; b < blocks; ++b) out[l] += hp[(size_t)l * blocks + b];
+  return FEHOM_OK;
+}
+
+#define TRY(x)                          \
+  do {                                  \
+    fehom_status s_ = (x);              \
+    if (s_ != FEHOM_OK) return s_;      \
+  } while (0)
+
+}  // namespace
+
+// ==================================================================================================
+// C ABI
+// ==================================================================================================
+extern "C" {
+
+void fehom_default_options(fehom_options* opt) {
+  if (!opt) return;
+  opt->precision = FEHOM_FP64;
+  opt->max_iter = 10000;
+  opt->inner_tol = 1e-3;
+  opt->stream = nullptr;
+  opt->use_graph = 1;
+}
+
+const char* fehom_last_error(const fehom_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
+
+fehom_status fehom_query(const fehom_ctx* ctx, int* c, int* m, int64_t* N, int64_t* nxh) {
+  if (!ctx) return FEHOM_E_INVALID;
+  if (c) *c = ctx->d.c;
+  if (m) *m = ctx->m;
+  if (N) *N = ctx->d.N;
+  if (nxh) *nxh = ctx->d.nxh;
+  return FEHOM_OK;
+}
+
+void fehom_destroy(fehom_ctx* ctx) {
+  if (!ctx) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  dfree(ctx->ids); dfree(ctx->mats64); dfree(ctx->mats32); dfree(ctx->iso64); dfree(ctx->iso32);
+  dfree(ctx->rmats64); dfree(ctx->riso64); dfree(ctx->moduli_d);
+  for (int i = 0; i < 3; ++i) { dfree(ctx->tw64[i]); dfree(ctx->tw32[i]); }
+  dfree(ctx->sym64); dfree(ctx->sym32);
+  dfree(ctx->x64); dfree(ctx->r64); dfree(ctx->p64); dfree(ctx->ap64); dfree(ctx->b64); dfree(ctx->spec64);
+  dfree(ctx->x32); dfree(ctx->r32); dfree(ctx->p32); dfree(ctx->ap32); dfree(ctx->spec32);
+  dfree(ctx->st); dfree(ctx->red.partial); dfree(ctx->red.count);
+  dfree(ctx->tau); dfree(ctx->loads_d); dfree(ctx->partial);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  cudaSetDevice(prev);
+  delete ctx;
+}
+
+static fehom_status setup_impl(fehom_ctx* ctx, int elem, int physics, const int64_t n[3], const double* cell,
+                               const uint8_t* phase_ids, int ids_on_device, int n_phases, const double* phase_moduli,
+                               const double* ref_material, const fehom_options* opt) {
+  if (opt) ctx->opt = *opt;
+  else fehom_default_options(&ctx->opt);
+  if (ctx->opt.max_iter <= 0) ctx->opt.max_iter = 10000;
+  if (!(ctx->opt.inner_tol > 0.0 && ctx->opt.inner_tol < 1.0)) ctx->opt.inner_tol = 1e-3;
+  if (elem != FEHOM_P1TRI2_2D && elem != FEHOM_HEX8_3D && elem != FEHOM_Q1_2D) FAIL(FEHOM_E_INVALID, "unknown element type");
+  if (physics != FEHOM_SCALAR && physics != FEHOM_ELASTIC) FAIL(FEHOM_E_INVALID, "unknown physics");
+  if (!n || !phase_ids || !phase_moduli) FAIL(FEHOM_E_INVALID, "NULL argument");
+  if (n_phases < 1 || n_phases > kMaxPhases) FAIL(FEHOM_E_INVALID, "n_phases must be in 1..256");
+  const int dim = (elem == FEHOM_HEX8_3D) ? 3 : 2;
+  if (dim == 2 && n[2] != 1) FAIL(FEHOM_E_UNSUPPORTED_SIZE, "2-D elements need n[2] == 1");
+  for (int i = 0; i < dim; ++i)
+    if (!size_ok(n[i])) FAIL(FEHOM_E_UNSUPPORTED_SIZE, "each grid size must be 2^k or 3*2^k in [2, 1024]");
+  if (n[0] % 2) FAIL(FEHOM_E_UNSUPPORTED_SIZE, "n_x must be even");
+  ctx->d.dim = dim;
+  ctx->d.nx = (int)n[0];
+  ctx->d.ny = (int)n[1];
+  ctx->d.nz = dim == 3 ? (int)n[2] : 1;
+  ctx->d.nxh = ctx->d.nx / 2 + 1;
+  ctx->d.N = (long long)ctx->d.nx * ctx->d.ny * ctx->d.nz;
+  ctx->d.Nh = (long long)ctx->d.nxh * ctx->d.ny * ctx->d.nz;
+  ctx->d.c = physics == FEHOM_SCALAR ? 1 : dim;
+  ctx->d.elem = elem;
+  ctx->physics = physics;
+  ctx->m = physics == FEHOM_SCALAR ? dim : dim * (dim + 1) / 2;
+  ctx->D = ctx->d.c * dim;
+  ctx->vol = 1.0;
+  for (int i = 0; i < 3; ++i) {
+    const double l = (cell && i < dim) ? cell[i] : 1.0;
+    if (!(l > 0.0) || !std::isfinite(l)) FAIL(FEHOM_E_INVALID, "cell lengths must be positive");
+    ctx->h[i] = i < dim ? l / (double)n[i] : 1.0;
+    if (i < dim) ctx->vol *= ctx->h[i];
+  }
+  const int m = ctx->m;
+  ctx->n_phases = n_phases;
+  ctx->moduli.assign(phase_moduli, phase_moduli + (size_t)n_phases * m * m);
+  for (int p = 0; p < n_phases; ++p)
+    if (!spd(&ctx->moduli[(size_t)p * m * m], m)) FAIL(FEHOM_E_INVALID, "phase moduli must be finite, symmetric, positive definite");
+
+  CK(cudaGetDevice(&ctx->device));
+  if (ctx->opt.stream) {
+    ctx->stream = (cudaStream_t)ctx->opt.stream;
+  } else {
+    CK(cudaStreamCreate(&ctx->stream));  // blocking stream: ordered with the legacy default stream
+    ctx->own_stream = true;
+  }
+  cudaStream_t s = ctx->stream;
+  const long long N = ctx->d.N;
+  CK(cudaMalloc(&ctx->ids, N));
+  CK(cudaMemcpyAsync(ctx->ids, phase_ids, N, ids_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  // phase histogram: id range check and volume fractions
+  unsigned long long* hist;
+  CK(cudaMalloc(&hist, 256 * sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), s));
+  CK(launch_phase_histogram(ctx->ids, N, hist, s));
+  std::vector<unsigned long long> hh(256);
+  CK(cudaMemcpyAsync(hh.data(), hist, 256 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  cudaFree(hist);
+  for (int p = n_phases; p < 256; ++p)
+    if (hh[p]) FAIL(FEHOM_E_INVALID, "phase id >= n_phases in phase_ids");
+  ctx->frac.assign(n_phases, 0.0);
+  for (int p = 0; p < n_phases; ++p) ctx->frac[p] = (double)hh[p] / (double)N;
+  // reference material: given, or the volume mean (Sec. 6.2)
+  ctx->cref.assign((size_t)m * m, 0.0);
+  if (ref_material) {
+    ctx->cref.assign(ref_material, ref_material + (size_t)m * m);
+  } else {
+    for (int p = 0; p < n_phases; ++p)
+      for (int i = 0; i < m * m; ++i) ctx->cref[i] += ctx->frac[p] * ctx->moduli[(size_t)p * m * m + i];
+  }
+  if (!spd(ctx->cref.data(), m)) FAIL(FEHOM_E_INVALID, "reference material must be symmetric positive definite");
+  // gradient-space materials
+  const int D = ctx->D;
+  std::vector<double> mats((size_t)n_phases * D * D);
+  for (int p = 0; p < n_phases; ++p) grad_material(ctx, &ctx->moduli[(size_t)p * m * m], &mats[(size_t)p * D * D]);
+  std::vector<float> mats32(mats.begin(), mats.end());
+  CK(cudaMalloc(&ctx->mats64, mats.size() * sizeof(double)));
+  CK(cudaMalloc(&ctx->mats32, mats.size() * sizeof(float)));
+  CK(cudaMemcpyAsync(ctx->mats64, mats.data(), mats.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->mats32, mats32.data(), mats32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  std::vector<double> rm((size_t)D * D);
+  grad_material(ctx, ctx->cref.data(), rm.data());
+  CK(cudaMalloc(&ctx->rmats64, rm.size() * sizeof(double)));
+  CK(cudaMemcpyAsync(ctx->rmats64, rm.data(), rm.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMalloc(&ctx->moduli_d, ctx->moduli.size() * sizeof(double)));
+  CK(cudaMemcpyAsync(ctx->moduli_d, ctx->moduli.data(), ctx->moduli.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  // isotropic fast path (hex8 elasticity on a cubic grid)
+  if (elem == FEHOM_HEX8_3D && physics == FEHOM_ELASTIC && ctx->h[0] == ctx->h[1] && ctx->h[1] == ctx->h[2]) {
+    bool all = true;
+    std::vector<double> iso(2 * n_phases);
+    double w, sc[3];
+    kernel_scales(ctx, &w, sc);
+    for (int p = 0; p < n_phases && all; ++p) {
+      double lam, mu;
+      all = iso_elastic(&ctx->moduli[(size_t)p * m * m], 3, &lam, &mu);
+      iso[2 * p] = w * sc[0] * sc[0] * lam;
+      iso[2 * p + 1] = w * sc[0] * sc[0] * mu;
+    }
+    if (all) {
+      ctx->iso = true;
+      std::vector<float> iso32(iso.begin(), iso.end());
+      CK(cudaMalloc(&ctx->iso64, iso.size() * sizeof(double)));
+      CK(cudaMalloc(&ctx->iso32, iso.size() * sizeof(float)));
+      CK(cudaMemcpyAsync(ctx->iso64, iso.data(), iso.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(ctx->iso32, iso32.data(), iso32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+    double lam, mu;
+    if (iso_elastic(ctx->cref.data(), 3, &lam, &mu)) {
+      ctx->iso_ref = true;
+      const double ri[2] = {w * sc[0] * sc[0] * lam, w * sc[0] * sc[0] * mu};
+      CK(cudaMalloc(&ctx->riso64, 2 * sizeof(double)));
+      CK(cudaMemcpyAsync(ctx->riso64, ri, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+  }
+  // twiddles
+  const int lens[3] = {ctx->d.nx, ctx->d.ny, ctx->d.nz};
+  for (int i = 0; i < dim; ++i) CK(make_twiddles(lens[i], &ctx->tw64[i], &ctx->tw32[i]));
+  // PCG state and reduction scratch
+  CK(cudaMalloc(&ctx->st, sizeof(PcgState) * kMaxLoads));
+  ctx->red.max_blocks = kRedBlocks;
+  CK(cudaMalloc(&ctx->red.partial, sizeof(double) * (size_t)kMaxLoads * kRedBlocks));
+  CK(cudaMalloc(&ctx->red.count, sizeof(unsigned) * kMaxLoads));
+  CK(cudaMemsetAsync(ctx->red.count, 0, sizeof(unsigned) * kMaxLoads, s));
+  TRY(grow64(ctx, 1));
+  CK(cudaStreamSynchronize(s));
+  return FEHOM_OK;
+}
+
+fehom_status fehom_setup(fehom_ctx** out, int elem, int physics, const int64_t n[3], const double* cell,
+                         const uint8_t* phase_ids, int ids_on_device, int n_phases, const double* phase_moduli,
+                         const double* ref_material, const fehom_options* opt) {
+  if (!out) return FEHOM_E_INVALID;
+  *out = nullptr;
+  fehom_ctx* ctx = new (std::nothrow) fehom_ctx();
+  if (!ctx) return FEHOM_E_OOM;
+  const fehom_status st = setup_impl(ctx, elem, physics, n, cell, phase_ids, ids_on_device, n_phases, phase_moduli,
+                                     ref_material, opt);
+  if (st != FEHOM_OK) {
+    g_setup_error = ctx->err;  // readable through fehom_last_error(NULL)
+    fehom_destroy(ctx);
+    return st;
+  }
+  g_setup_error.clear();
+  *out = ctx;
+  return FEHOM_OK;
+}
+
+fehom_status fehom_precond_build(fehom_ctx* ctx) {
+  if (!ctx) return FEHOM_E_INVALID;
+  const int c = ctx->d.c;
+  cudaStream_t s = ctx->stream;
+  TRY(grow64(ctx, c));
+  const long long cN = (long long)c * ctx->d.N;
+  // Algorithm 2: impulses i^beta at node 0 of component beta (one "load" per beta)
+  CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * c, s));
+  const double one = 1.0;
+  for (int be = 0; be < c; ++be)
+    CK(cudaMemcpyAsync(ctx->x64 + be * cN + (long long)be * ctx->d.N, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+  StencilArgs a{};
+  a.d = ctx->d;
+  a.x = ctx->x64;
+  a.y = ctx->ap64;
+  a.ids = nullptr;  // uniform reference material
+  a.mats = ctx->rmats64;
+  a.iso = (ctx->iso_ref && ctx->iso) ? ctx->riso64 : nullptr;
+  a.n_phases = 1;
+  a.n_loads = c;
+  a.load_stride = cN;
+  a.y_scale = 1.0;
+  a.red = ctx->red;
+  CK(launch_stiffness<double>(a, s));
+  // forward FFT of every component of every column -> spec64[beta][alpha][Nh]
+  FftArgs f;
+  fill_dims_args(ctx, f, false, c);
+  f.sym = nullptr;
+  f.mode = FX_PLAIN;
+  f.f0 = ctx->ap64;
+  CK(launch_fft_x_fwd<double>(f, s));
+  if (ctx->d.dim == 3) CK(launch_fft_y<double>(f, 0, s));
+  CK(launch_fft_last_solve<double>(f, s));
+  // per-wavevector inverse
+  const long long Nh = ctx->d.Nh;
+  const int ne = c * (c + 1) / 2;
+  if (!ctx->sym64) {
+    CK(cudaMalloc(&ctx->sym64, sizeof(double) * ne * Nh));
+    CK(cudaMalloc(&ctx->sym32, sizeof(float) * ne * Nh));
+  }
+  TRY(ensure_partial(ctx, 4 * 2 * 152));
+  SymbolArgs sa{};
+  sa.d = ctx->d;
+  sa.spec = ctx->spec64;
+  sa.sym64 = ctx->sym64;
+  sa.sym32 = ctx->sym32;
+  sa.partial = ctx->partial;
+  sa.zero_tol = 1e-12;
+  int blocks = 0;
+  CK(launch_symbol_build(sa, &blocks, s));
+  std::vector<double> hp(4 * blocks);
+  CK(cudaMemcpyAsync(hp.data(), ctx->partial, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  // the k = 0 block
+  std::vector<double2> k0(c * c);
+  for (int be = 0; be < c; ++be)
+    for (int al = 0; al < c; ++al)
+      CK(cudaMemcpyAsync(&k0[be * c + al], ctx->spec64 + ((long long)be * c + al) * Nh, sizeof(double2),
+                         cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double mx_im = 0, mx_asym = 0, mx_abs = 0, mn_piv = 1e300;
+  for (int b = 0; b < blocks; ++b) {
+    mx_im = std::max(mx_im, hp[4 * b]);
+    mx_asym = std::max(mx_asym, hp[4 * b + 1]);
+    mx_abs = std::max(mx_abs, hp[4 * b + 2]);
+    mn_piv = std::min(mn_piv, hp[4 * b + 3]);
+  }
+  char msg[256];
+  if (!(mx_abs > 0) || mx_im > 1e-9 * mx_abs || mx_asym > 1e-9 * mx_abs) {
+    std::snprintf(msg, sizeof msg, "reference symbol not real symmetric: max|Im| %.3e, asym %.3e, max %.3e", mx_im,
+                  mx_asym, mx_abs);
+    FAIL(FEHOM_E_INVALID, msg);
+  }
+  if (ctx->d.Nh > 1 && !(mn_piv > 1e-13 * mx_abs)) {
+    std::snprintf(msg, sizeof msg, "reference symbol singular away from k = 0 (min pivot %.3e)", mn_piv);
+    FAIL(FEHOM_E_INVALID, msg);
+  }
+  // Moore-Penrose pseudo-inverse of the k = 0 block, singular values cut relative to max |K_hat|
+  std::vector<double> A(c * c), V, ev;
+  for (int al = 0; al < c; ++al)
+    for (int be = 0; be < c; ++be) A[al * c + be] = 0.5 * (k0[be * c + al].x + k0[al * c + be].x);
+  jacobi_eig(c, A, V, ev);
+  std::vector<double> pinv(c * c, 0.0);
+  for (int k = 0; k < c; ++k) {
+    if (std::fabs(ev[k]) <= 1e-12 * mx_abs) continue;
+    for (int i = 0; i < c; ++i)
+      for (int j = 0; j < c; ++j) pinv[i * c + j] += V[i * c + k] * V[j * c + k] / ev[k];
+  }
+  const int pi3[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+  const int pi2[3][2] = {{0, 0}, {1, 1}, {0, 1}};
+  const double invN = 1.0 / (double)ctx->d.N;
+  for (int e = 0; e < ne; ++e) {
+    const int i = c == 3 ? pi3[e][0] : (c == 2 ? pi2[e][0] : 0);
+    const int j = c == 3 ? pi3[e][1] : (c == 2 ? pi2[e][1] : 0);
+    const double v = pinv[i * c + j] * invN;
+    const float vf = (float)v;
+    CK(cudaMemcpyAsync(ctx->sym64 + (long long)e * Nh, &v, sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->sym32 + (long long)e * Nh, &vf, sizeof(float), cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  ctx->built = true;
+  return FEHOM_OK;
+}
+
+fehom_status fehom_apply_stiffness(fehom_ctx* ctx, const void* x, void* y, int precision) {
+  if (!ctx || !x || !y) return FEHOM_E_INVALID;
+  StencilArgs a = stencil_args(ctx, precision == FEHOM_MIXED, 1);
+  a.x = x;
+  a.y = y;
+  if (precision == FEHOM_MIXED) CK(launch_stiffness<float>(a, ctx->stream));
+  else CK(launch_stiffness<double>(a, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FEHOM_OK;
+}
+
+fehom_status fehom_rhs(fehom_ctx* ctx, const double* e, double* b) {
+  if (!ctx || !e || !b) return FEHOM_E_INVALID;
+  TRY(compute_rhs(ctx, 1, e, b));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FEHOM_OK;
+}
+
+fehom_status fehom_apply_precond(fehom_ctx* ctx, const void* r, void* z, int precision) {
+  if (!ctx || !r || !z) return FEHOM_E_INVALID;
+  if (!ctx->built) FAIL(FEHOM_E_STATE, "fehom_apply_precond before fehom_precond_build");
+  const bool fp32 = precision == FEHOM_MIXED;
+  if (fp32) TRY(grow32(ctx, 1));
+  FftArgs f;
+  fill_dims_args(ctx, f, fp32, 1);
+  if (fp32) CK(precond_passes<float>(ctx, f, FX_PLAIN, FX_PLAIN, const_cast<void*>(r), nullptr, z, nullptr, ctx->stream));
+  else CK(precond_passes<double>(ctx, f, FX_PLAIN, FX_PLAIN, const_cast<void*>(r), nullptr, z, nullptr, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FEHOM_OK;
+}
+
+fehom_status fehom_get_symbol_inverse(fehom_ctx* ctx, double* out) {
+  if (!ctx || !out) return FEHOM_E_INVALID;
+  if (!ctx->built) FAIL(FEHOM_E_STATE, "fehom_get_symbol_inverse before fehom_precond_build");
+  const int ne = ctx->d.c * (ctx->d.c + 1) / 2;
+  CK(cudaMemcpyAsync(out, ctx->sym64, sizeof(double) * ne * ctx->d.Nh, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FEHOM_OK;
+}
+
+fehom_status fehom_mean_flux(fehom_ctx* ctx, const double* e, const double* u, double* out) {
+  if (!ctx || !e || !u || !out) return FEHOM_E_INVALID;
+  return mean_flux(ctx, 1, e, u, out);
+}
+
+static fehom_status finish_outputs(fehom_ctx* ctx, int n_loads, const double* loads, double* fluct_out,
+                                   int fluct_on_device, double* mean_flux_out, double* c_eff_out,
+                                   std::vector<double>& rel2) {
+  cudaStream_t s = ctx->stream;
+  const long long cN = (long long)ctx->d.c * ctx->d.N;
+  CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, s));
+  // true FP64 residual b - K x
+  TRY(compute_rhs(ctx, n_loads, loads, ctx->b64));
+  std::vector<double> bn;
+  TRY(norms2(ctx, n_loads, ctx->b64, bn));
+  StencilArgs a = stencil_args(ctx, false, n_loads);
+  a.x = ctx->x64;
+  a.y = ctx->ap64;
+  CK(launch_stiffness<double>(a, s));
+  CK(launch_axpby_d(ctx->ap64, ctx->b64, -1.0, 1.0, cN * n_loads, s));
+  std::vector<double> rn;
+  TRY(norms2(ctx, n_loads, ctx->b64, rn));
+  rel2.resize(n_loads);
+  for (int l = 0; l < n_loads; ++l) rel2[l] = bn[l] > 0 ? std::sqrt(rn[l] / bn[l]) : 0.0;
+  std::vector<double> flux((size_t)n_loads * ctx->m);
+  TRY(mean_flux(ctx, n_loads, loads, ctx->x64, flux.data()));
+  if (mean_flux_out) std::memcpy(mean_flux_out, flux.data(), flux.size() * sizeof(double));
+  if (c_eff_out && n_loads == ctx->m) {
+    // C_eff = S E^-1 with S[:, l] = flux_l, E[:, l] = e_l  ->  solve E^T C_eff^T = S^T
+    const int m = ctx->m;
+    std::vector<double> Et(m * m), St(m * m);
+    for (int l = 0; l < m; ++l)
+      for (int i = 0; i < m; ++i) {
+        Et[l * m + i] = loads[l * m + i];  // row l of E^T = e_l
+        St[l * m + i] = flux[l * m + i];
+      }
+    // Gaussian elimination with partial pivoting on [Et | St]
+    bool ok = true;
+    for (int col = 0; col < m && ok; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < m; ++r)
+        if (std::fabs(Et[r * m + col]) > std::fabs(Et[piv * m + col])) piv = r;
+      if (std::fabs(Et[piv * m + col]) < 1e-300) { ok = false; break; }
+      for (int k = 0; k < m; ++k) {
+        std::swap(Et[col * m + k], Et[piv * m + k]);
+        std::swap(St[col * m + k], St[piv * m + k]);
+      }
+      for (int r = 0; r < m; ++r) {
+        if (r == col) continue;
+        const double f = Et[r * m + col] / Et[col * m + col];
+        for (int k = 0; k < m; ++k) {
+          Et[r * m + k] -= f * Et[col * m + k];
+          St[r * m + k] -= f * St[col * m + k];
+        }
+      }
+    }
+    if (ok) {
+      // row l of C_eff^T = St[l] / Et[l][l]  ->  C_eff[i][l] = St[l][i] / Et[l][l]
+      for (int l = 0; l < m; ++l)
+        for (int i = 0; i < m; ++i) c_eff_out[i * m + l] = St[l * m + i] / Et[l * m + l];
+    }
+  }
+  if (fluct_out) {
+    CK(cudaMemcpyAsync(fluct_out, ctx->x64, sizeof(double) * cN * n_loads,
+                       fluct_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return FEHOM_OK;
+}
+
+static fehom_status solve_fp64(fehom_ctx* ctx, int n_loads, const double* loads, double tol, const double* x0,
+                               std::vector<PcgState>& hs) {
+  cudaStream_t s = ctx->stream;
+  const long long cN = (long long)ctx->d.c * ctx->d.N;
+  TRY(compute_rhs(ctx, n_loads, loads, ctx->r64));
+  double bn = -1.0;
+  if (x0) {
+    // <b, K_ref^+ b> first (normalisation of the stopping test), then r0 = b - K x0
+    TRY(set_states(ctx, n_loads, tol, ctx->opt.max_iter, -1.0));
+    CK(cudaMemcpyAsync(ctx->b64, ctx->r64, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
+    TRY(pcg_init<double>(ctx, n_loads, ctx->b64, ctx->p64));
+    std::vector<PcgState> h0(n_loads);
+    CK(cudaMemcpyAsync(h0.data(), ctx->st, sizeof(PcgState) * n_loads, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
+    CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, s));
+    StencilArgs a = stencil_args(ctx, false, n_loads);
+    a.x = ctx->x64;
+    a.y = ctx->ap64;
+    CK(launch_stiffness<double>(a, s));
+    CK(launch_axpby_d(ctx->ap64, ctx->r64, -1.0, 1.0, cN * n_loads, s));
+    std::vector<PcgState> hs0(n_loads);
+    for (int l = 0; l < n_loads; ++l) {
+      std::memset(&hs0[l], 0, sizeof(PcgState));
+      hs0[l].bnorm2 = h0[l].bnorm2;
+      hs0[l].tol2_rel = tol * tol;
+      hs0[l].state = ST_RUN;
+      hs0[l].max_iter = ctx->opt.max_iter;
+    }
+    CK(cudaMemcpyAsync(ctx->st, hs0.data(), sizeof(PcgState) * n_loads, cudaMemcpyHostToDevice, s));
+  } else {
+    CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * n_loads, s));
+    TRY(set_states(ctx, n_loads, tol, ctx->opt.max_iter, bn));
+  }
+  TRY(pcg_init<double>(ctx, n_loads, ctx->r64, ctx->p64));
+  return run_iterations<double>(ctx, n_loads, ctx->x64, ctx->r64, ctx->p64, ctx->ap64, ctx->opt.max_iter, hs);
+}
+
+// FP32 PCG inside FP64 iterative refinement: r = b - K x (FP64), K d = r in FP32 to inner_tol, x += d.
+static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads, double tol, const double* x0,
+                                std::vector<PcgState>& hs, std::vector<int>& outer_it, std::vector<int>& inner_it,
+                                std::vector<double>& relM) {
+  cudaStream_t s = ctx->stream;
+  TRY(grow32(ctx, n_loads));
+  const long long cN = (long long)ctx->d.c * ctx->d.N;
+  TRY(compute_rhs(ctx, n_loads, loads, ctx->b64));
+  if (x0) {
+    CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
+    CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, s));
+  } else {
+    CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * n_loads, s));
+  }
+  std::vector<double> bnorm2(n_loads, -1.0);
+  std::vector<bool> done(n_loads, false);
+  outer_it.assign(n_loads, 0);
+  inner_it.assign(n_loads, 0);
+  relM.assign(n_loads, 1.0);
+  hs.assign(n_loads, PcgState{});
+  int total_inner = 0;
+  const int max_outer = 60;
+  for (int outer = 0; outer < max_outer; ++outer) {
+    // r = b - K x in FP64
+    CK(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
+    if (outer > 0 || x0) {
+      StencilArgs a = stencil_args(ctx, false, n_loads);
+      a.x = ctx->x64;
+      a.y = ctx->ap64;
+      CK(launch_stiffness<double>(a, s));
+      CK(launch_axpby_d(ctx->ap64, ctx->r64, -1.0, 1.0, cN * n_loads, s));
+    }
+    if (outer == 0 && x0) {
+      // normalisation <b, K_ref^+ b> from b itself
+      CK(launch_cast_d2f(ctx->b64, ctx->r32, 1.0, cN * n_loads, s));
+      TRY(set_states(ctx, n_loads, ctx->opt.inner_tol, 1, -1.0));
+      TRY(pcg_init<float>(ctx, n_loads, ctx->r32, ctx->p32));
+      std::vector<PcgState> h0(n_loads);
+      CK(cudaMemcpyAsync(h0.data(), ctx->st, sizeof(PcgState) * n_loads, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int l = 0; l < n_loads; ++l) bnorm2[l] = h0[l].rz_init;
+    }
+    CK(launch_cast_d2f(ctx->r64, ctx->r32, 1.0, cN * n_loads, s));
+    CK(cudaMemsetAsync(ctx->x32, 0, sizeof(float) * cN * n_loads, s));
+    const int remaining = std::max(1, ctx->opt.max_iter - total_inner);
+    TRY(set_states(ctx, n_loads, ctx->opt.inner_tol, remaining, -1.0));
+    TRY(pcg_init<float>(ctx, n_loads, ctx->r32, ctx->p32));
+    std::vector<PcgState> h(n_loads);
+    CK(cudaMemcpyAsync(h.data(), ctx->st, sizeof(PcgState) * n_loads, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int l = 0; l < n_loads; ++l) {
+      if (done[l]) {
+        h[l].state = ST_DONE;
+        continue;
+      }
+      if (bnorm2[l] < 0) bnorm2[l] = h[l].rz_init;
+      relM[l] = bnorm2[l] > 0 ? std::sqrt(std::max(h[l].rz_init, 0.0) / bnorm2[l]) : 0.0;
+      if (bnorm2[l] <= 0 || h[l].rz_init <= tol * tol * bnorm2[l]) {
+        done[l] = true;
+        h[l].state = ST_DONE;
+      } else {
+        all = false;
+        outer_it[l] += 1;
+        if (h[l].state != ST_RUN) h[l].state = ST_RUN;  // inner criterion met at start: still do >= 1 step
+      }
+    }
+    if (all || total_inner >= ctx->opt.max_iter) break;
+    CK(cudaMemcpyAsync(ctx->st, h.data(), sizeof(PcgState) * n_loads, cudaMemcpyHostToDevice, s));
+    TRY(run_iterations<float>(ctx, n_loads, ctx->x32, ctx->r32, ctx->p32, ctx->ap32, remaining, hs));
+    int mx = 0;
+    for (int l = 0; l < n_loads; ++l) {
+      if (!done[l]) inner_it[l] += hs[l].iter;
+      mx = std::max(mx, hs[l].iter);
+    }
+    total_inner += mx;
+    CK(launch_add_f2d(ctx->x32, ctx->x64, 1.0, cN * n_loads, s));
+  }
+  for (int l = 0; l < n_loads; ++l) {
+    hs[l].iter = inner_it[l];
+    hs[l].state = done[l] ? ST_DONE : ST_MAXIT;
+  }
+  return FEHOM_OK;
+}
+
+fehom_status fehom_solve(fehom_ctx* ctx, int n_loads, const double* loads, double tol, const double* x0,
+                         double* fluct_out, int fluct_on_device, double* mean_flux_out, double* c_eff_out,
+                         fehom_solve_info* info) {
+  if (!ctx) return FEHOM_E_INVALID;
+  if (!ctx->built) FAIL(FEHOM_E_STATE, "fehom_solve before fehom_precond_build");
+  if (n_loads < 1 || n_loads > kMaxLoads || !loads) FAIL(FEHOM_E_INVALID, "n_loads must be in 1..64 with loads given");
+  if (!(tol > 0.0 && tol < 1.0)) FAIL(FEHOM_E_INVALID, "tol must be in (0, 1)");
+  for (int i = 0; i < n_loads * ctx->m; ++i)
+    if (!std::isfinite(loads[i])) FAIL(FEHOM_E_INVALID, "non-finite load");
+  TRY(grow64(ctx, n_loads));
+  cudaStream_t s = ctx->stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  std::vector<PcgState> hs;
+  std::vector<int> outer_it(n_loads, 0), inner_it;
+  std::vector<double> relM(n_loads, 0.0);
+  fehom_status st;
+  const bool mixed = ctx->opt.precision == FEHOM_MIXED;
+  if (mixed) st = solve_mixed(ctx, n_loads, loads, tol, x0, hs, outer_it, inner_it, relM);
+  else st = solve_fp64(ctx, n_loads, loads, tol, x0, hs);
+  if (st != FEHOM_OK) return st;
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::vector<double> rel2;
+  TRY(finish_outputs(ctx, n_loads, loads, fluct_out, fluct_on_device, mean_flux_out, c_eff_out, rel2));
+  bool brk = false, notconv = false;
+  for (int l = 0; l < n_loads; ++l) {
+    if (hs[l].state == ST_BREAK) brk = true;
+    if (hs[l].state != ST_DONE) notconv = true;
+    if (info) {
+      info[l].iterations = hs[l].iter;
+      info[l].refinements = mixed ? outer_it[l] : 0;
+      info[l].converged = hs[l].state == ST_DONE;
+      info[l].rel_residual_M = mixed ? relM[l] : (hs[l].bnorm2 > 0 ? std::sqrt(std::max(hs[l].rz, 0.0) / hs[l].bnorm2) : 0.0);
+      info[l].rel_residual_2 = rel2[l];
+      info[l].solve_ms = ms;
+    }
+  }
+  if (brk) FAIL(FEHOM_E_BREAKDOWN, "PCG breakdown (non-positive or non-finite curvature)");
+  if (notconv) FAIL(FEHOM_E_NOT_CONVERGED, "PCG did not reach the tolerance within max_iter");
+  ctx->err.clear();
+  return FEHOM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// Internal declarations shared by the translation units of libfehom.so.
+//
+// Layout in device memory (one context = one periodic cell):
+//   fields   T[load][comp][N]            x fastest inside a component (N = nx ny nz)
+//   spectra  complex<T>[load][comp][Nh]   half spectrum, kx = 0..nx/2 fastest (Nh = nxh ny nz)
+//   symbol   T[entry][Nh]                packed symmetric K_hat^+(k) / N (Sec. 5.3)
+//   ids      uint8[N]                    phase id per pixel/voxel
+//   mats     T[phase][D*D]               gradient-space material (see stencil.cu)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fehom {
+
+constexpr int kMaxLoads = 64;      // loads solved as one batch
+constexpr int kMaxPhases = 256;
+
+enum Elem { P1TRI2_2D = 1, HEX8_3D = 2, Q1_2D = 3 };
+
+struct Dims {
+  int dim;        // 2 or 3
+  int nx, ny, nz; // nz == 1 in 2-D
+  int nxh;        // nx / 2 + 1
+  long long N;    // nx ny nz
+  long long Nh;   // nxh ny nz
+  int c;          // DOF per node
+  int elem;
+};
+
+// Per-load PCG scalars, resident in device memory (written by the last CTA of a reduction).
+struct PcgState {
+  double rz;       // <r, z> of the current iterate
+  double pAp;      // <p, K p>
+  double alpha, beta;
+  double bnorm2;   // <b, K_ref^+ b>; negative = take <r0, z0> (zero initial guess)
+  double tol2_rel; // tol^2
+  double tol2;     // tol^2 * bnorm2
+  double rz_init;  // <r0, z0>
+  int state;       // see ST_*
+  int iter;
+  int max_iter;
+  int pad;
+};
+
+// RUN: iterating; CONV / FIN_MAX: converged / out of iterations, finishing the current iteration
+// (x update still due); DONE / MAXIT: finished; BREAK: breakdown (non-positive or non-finite curvature).
+enum { ST_RUN = 0, ST_CONV = 1, ST_DONE = 2, ST_BREAK = 3, ST_MAXIT = 4, ST_FIN_MAX = 5 };
+
+// Reduction scratch: per-load partial sums written by each CTA, plus per-load arrival counters.
+struct RedScratch {
+  double* partial;   // [kMaxLoads][max_blocks]
+  unsigned* count;   // [kMaxLoads] arrival counters (self-resetting)
+  int max_blocks;
+};
+
+// ------------------------------------------------------------------------------------------------
+// stencil.cu
+// ------------------------------------------------------------------------------------------------
+struct StencilArgs {
+  Dims d;
+  const void* x;        // [load][c][N] or nullptr (treated as zero)
+  void* y;              // [load][c][N]
+  const uint8_t* ids;   // [N]; nullptr = every voxel is phase 0 (uniform material)
+  const void* mats;     // [phase][D*D] gradient-space material, T
+  const void* iso;      // [phase][2] (lambda', mu') for the isotropic cubic fast path, or nullptr
+  const double* tau;    // [load][phase][D] prestress of the macroscopic load (FP64), or nullptr
+  int n_phases;
+  int n_loads;
+  long long load_stride;  // elements between loads in x / y
+  double y_scale;         // y = y_scale * D^T W C (D x + e)
+  // fused PCG reduction <x, y> -> pAp, alpha = rz / pAp (nullptr = off)
+  PcgState* st;
+  RedScratch red;
+};
+
+// Launches y = D^T W C (D x + e) for every load (blockIdx.z).  T = double or float.
+template <typename T>
+cudaError_t launch_stiffness(const StencilArgs& a, cudaStream_t s);
+
+struct MeanFluxArgs {
+  Dims d;
+  const double* u;      // [load][c][N] or nullptr
+  const uint8_t* ids;
+  const double* moduli; // [phase][m*m] Mandel / conductivity matrices (FP64)
+  const double* loads;  // [load][m] (device)
+  int n_loads, m;
+  long long load_stride;
+  double h[3];
+  double* partial;      // [load][blocks][m]
+};
+cudaError_t launch_mean_flux(const MeanFluxArgs& a, int* blocks_out, cudaStream_t s);
+
+cudaError_t launch_phase_histogram(const uint8_t* ids, long long N, unsigned long long* hist,
+                                   cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------------
+// fft.cu
+// ------------------------------------------------------------------------------------------------
+struct Twiddles {  // W_L^m = exp(-2 pi i m / L) for the x (length nx), y, z axes
+  const void* x;
+  const void* y;
+  const void* z;
+};
+
+enum FxMode {
+  FX_PLAIN = 0,     // forward: spectrum of the field; inverse: write the field
+  FX_PCG = 1,       // forward: r -= alpha Ap first; inverse: x += alpha p, p = z + beta p
+  FX_PCG_INIT = 2   // inverse only: p = z (first preconditioner apply of PCG)
+};
+
+struct FftArgs {
+  Dims d;
+  int n_loads;
+  long long load_stride_f;  // field stride between loads (c * N)
+  long long load_stride_s;  // spectrum stride between loads (c * Nh), in complex elements
+  void* spec;               // complex<T>
+  Twiddles tw;
+  // x-pass operands
+  void* f0;          // forward: r (in/out); inverse: x (in/out) or output z (FX_PLAIN)
+  const void* f1;    // forward: Ap; inverse: unused
+  void* f2;          // inverse: p (in/out)
+  int mode;
+  // solve pass
+  const void* sym;   // [entry][Nh] packed K_hat^+ / N (T)
+  PcgState* st;      // nullptr = no PCG bookkeeping
+  RedScratch red;
+  int init;          // solve pass: 1 = first apply (sets rz, bnorm2)
+};
+
+template <typename T> cudaError_t launch_fft_x_fwd(const FftArgs& a, cudaStream_t s);
+template <typename T> cudaError_t launch_fft_x_inv(const FftArgs& a, cudaStream_t s);
+template <typename T> cudaError_t launch_fft_y(const FftArgs& a, int inverse, cudaStream_t s);
+// last axis (z in 3-D, y in 2-D): forward FFT, z^ = K_hat^+ r^ / N, <r, z>, inverse FFT.
+// sym == nullptr: forward only (used by Algorithm 2).
+template <typename T> cudaError_t launch_fft_last_solve(const FftArgs& a, cudaStream_t s);
+
+// Algorithm 2 tail: spectra of the c impulse responses -> packed FP64 K_hat blocks, with the
+// largest |Im| and largest asymmetry recorded; then per-wavevector inverse.
+struct SymbolArgs {
+  Dims d;
+  const void* spec;  // complex<double>[beta][alpha][Nh]: spectrum of component alpha of K_ref i^beta
+  double* sym64;     // [entry][Nh] output K_hat^+ / N
+  float* sym32;      // [entry][Nh] output (float copy) or nullptr
+  double* diag;      // [4]: max |Im|, max asymmetry, max |K_hat|, min eigenvalue ratio (atomic max/min via partials)
+  double* partial;   // [blocks][4]
+  double zero_tol;   // relative cut for the k = 0 pseudo-inverse
+};
+cudaError_t launch_symbol_build(const SymbolArgs& a, int* blocks_out, cudaStream_t s);
+
+cudaError_t make_twiddles(int L, double2** d64, float2** d32);
+
+// ------------------------------------------------------------------------------------------------
+// vec.cu: small vector kernels used by the solve driver
+// ------------------------------------------------------------------------------------------------
+cudaError_t launch_fill(void* p, long long n, int bytes_per_elem, cudaStream_t s);  // zero
+cudaError_t launch_axpby_d(const double* x, double* y, double a, double b, long long n, cudaStream_t s);
+cudaError_t launch_cast_d2f(const double* x, float* y, double scale, long long n, cudaStream_t s);
+cudaError_t launch_add_f2d(const float* x, double* y, double scale, long long n, cudaStream_t s);
+cudaError_t launch_sub_mean(double* x, int c, long long N, int n_loads, long long load_stride, cudaStream_t s);
+// per-load sum of squares and sum (FP64 partials -> host)
+cudaError_t launch_norm2(const double* x, long long n, int n_loads, long long load_stride, double* partial,
+                         int* blocks_out, cudaStream_t s);
+
+}  // namespace fehom

@@ -1,0 +1,792 @@
+// Fourier-space application of the reference-material preconditioner (Sec. 4.2, Eq. M_inverse) and
+// the Fourier part of Algorithm 2 (Sec. 5.2), as shared-memory Stockham FFT passes.
+//
+// Transform convention: unnormalised forward DFT exp(-2 pi i k.x / n); the inverse DFT's 1/N is
+// folded into the stored symbol K_hat^+ / N.  A real field is stored as its half spectrum
+// (kx = 0 .. nx/2) per component.
+//
+// Passes (3-D; in 2-D the last axis is y and there is no middle pass):
+//   x forward  : two real lines packed into one complex line (re = line 2q, im = line 2q+1), one
+//                complex FFT of length nx, split into the two half spectra.  Fused PCG update
+//                r <- r - alpha Ap in front (FX_PCG).
+//   y forward / inverse : complex FFT along y of a tile of TC consecutive half-spectrum columns.
+//   last axis  : forward FFT, per-wavevector block solve z^ = K_hat^+ r^ / N (c x c real symmetric,
+//                Sec. 5.3, Eq. block_inversion), Parseval partial sum <r, z>, inverse FFT, for all c
+//                components of the same columns in one CTA.  Without a symbol: forward only.
+//   x inverse  : two half spectra -> one complex line (Hermitian completion), inverse FFT, split into
+//                the two real lines.  Fused PCG update x <- x + alpha p, p <- z + beta p (FX_PCG).
+//
+// Stockham autosort stages in shared memory: a stage of radix R with span Ns reads butterfly j's
+// inputs at j + r L/R, multiplies input r by W^(r (j mod Ns)) of the length-(Ns R) transform, does
+// an R-point DFT in registers and writes output r to (j / Ns) Ns R + (j mod Ns) + r Ns.  Radices
+// 3 (once, for 3 * 2^k), 8, 4, 2.  Twiddles come from a per-axis table W_L^m = exp(-2 pi i m / L)
+// computed on the host in long double from octant symmetry.
+#include "fehom_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace fehom {
+namespace {
+
+template <typename T> struct V2;
+template <> struct V2<double> { using t = double2; };
+template <> struct V2<float> { using t = float2; };
+
+template <typename C> __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) { C r; r.x = a; r.y = b; return r; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk<C>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {  // a * conj(b)
+  return mk<C>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+// multiply by -i (forward) or +i (inverse)
+template <typename C, bool INV> __device__ __forceinline__ C rot(C a) {
+  return INV ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
+}
+
+// R-point DFT in registers (sign -1 forward, +1 inverse), natural order in and out.
+template <typename C, int R, bool INV> __device__ __forceinline__ void dft(C (&v)[R]);
+
+template <typename C, bool INV> __device__ __forceinline__ void dft2(C& a, C& b) {
+  const C t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <typename C, bool INV> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+  const C a = cadd(v0, v2), b = csub(v0, v2), c = cadd(v1, v3), d = rot<C, INV>(csub(v1, v3));
+  v0 = cadd(a, c);
+  v2 = csub(a, c);
+  v1 = cadd(b, d);
+  v3 = csub(b, d);
+}
+
+template <typename C, int R, bool INV> struct Dft;
+template <typename C, bool INV> struct Dft<C, 2, INV> {
+  __device__ static void run(C (&v)[2]) { dft2<C, INV>(v[0], v[1]); }
+};
+template <typename C, bool INV> struct Dft<C, 4, INV> {
+  __device__ static void run(C (&v)[4]) { dft4<C, INV>(v[0], v[1], v[2], v[3]); }
+};
+template <typename C, bool INV> struct Dft<C, 8, INV> {
+  // one radix-2 decimation-in-frequency step, then two 4-point DFTs
+  __device__ static void run(C (&v)[8]) {
+    using T = decltype(C::x);
+    const T r2 = T(0.70710678118654752440);
+    C a[4], b[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      a[n] = cadd(v[n], v[n + 4]);
+      b[n] = csub(v[n], v[n + 4]);
+    }
+    // b[n] *= W_8^n  (forward W_8 = (1 - i)/sqrt 2; inverse: conjugate)
+    b[1] = INV ? mk<C>(r2 * (b[1].x - b[1].y), r2 * (b[1].x + b[1].y))
+               : mk<C>(r2 * (b[1].x + b[1].y), r2 * (b[1].y - b[1].x));
+    b[2] = rot<C, INV>(b[2]);
+    b[3] = INV ? mk<C>(-r2 * (b[3].x + b[3].y), r2 * (b[3].x - b[3].y))
+               : mk<C>(r2 * (b[3].y - b[3].x), -r2 * (b[3].x + b[3].y));
+    dft4<C, INV>(a[0], a[1], a[2], a[3]);
+    dft4<C, INV>(b[0], b[1], b[2], b[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] = a[k];
+      v[2 * k + 1] = b[k];
+    }
+  }
+};
+template <typename C, bool INV> struct Dft<C, 3, INV> {
+  __device__ static void run(C (&v)[3]) {
+    using T = decltype(C::x);
+    const T s3 = T(0.86602540378443864676);  // sin(2 pi / 3)
+    const C t1 = cadd(v[1], v[2]);
+    const C d = csub(v[1], v[2]);
+    const C m = mk<C>(fma(T(-0.5), t1.x, v[0].x), fma(T(-0.5), t1.y, v[0].y));
+    // t2 = (v1 - v2) * (-i sin(2 pi/3)) forward, (+i ...) inverse
+    const C t2 = INV ? mk<C>(-s3 * d.y, s3 * d.x) : mk<C>(s3 * d.y, -s3 * d.x);
+    v[0] = cadd(v[0], t1);
+    v[1] = cadd(m, t2);
+    v[2] = csub(m, t2);
+  }
+};
+
+// One Stockham stage over `ncols` independent lines.  COLS: element-major layout (addr e*ld + col),
+// otherwise line-major (addr col*ld + e).
+template <typename C, int R, bool INV, bool COLS>
+__device__ __forceinline__ void stage(const C* __restrict__ in, C* __restrict__ out, int L, int Ns, int ncols, int ld,
+                                      const C* __restrict__ tw) {
+  const int nb = L / R;
+  const int tstride = L / (Ns * R);
+  for (int w = threadIdx.x; w < ncols * nb; w += blockDim.x) {
+    int col, j;
+    if (COLS) {
+      col = w % ncols;
+      j = w / ncols;
+    } else {
+      j = w % nb;
+      col = w / nb;
+    }
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = COLS ? in[(j + r * nb) * ld + col] : in[col * ld + j + r * nb];
+    const int kk = j % Ns;
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const C w_ = __ldg(tw + kk * r * tstride);
+        v[r] = INV ? cmulc(v[r], w_) : cmul(v[r], w_);
+      }
+    }
+    Dft<C, R, INV>::run(v);
+    const int base = (j - kk) * R + kk;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = base + r * Ns;
+      if (COLS) out[e * ld + col] = v[r];
+      else out[col * ld + e] = v[r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full length-L transform of `ncols` lines held in b0; returns the buffer holding the result.
+template <typename C, bool INV, bool COLS>
+__device__ C* fft_smem(C* b0, C* b1, int L, int ncols, int ld, const C* tw) {
+  int Ns = 1, rem = L;
+  C* in = b0;
+  C* out = b1;
+  if (rem % 3 == 0) {
+    stage<C, 3, INV, COLS>(in, out, L, Ns, ncols, ld, tw);
+    Ns *= 3; rem /= 3;
+    C* t = in; in = out; out = t;
+  }
+  while (rem % 8 == 0 && rem != 16) {  // 16 = 4 * 4 is cheaper than 8 * 2
+    stage<C, 8, INV, COLS>(in, out, L, Ns, ncols, ld, tw);
+    Ns *= 8; rem /= 8;
+    C* t = in; in = out; out = t;
+  }
+  while (rem % 4 == 0) {
+    stage<C, 4, INV, COLS>(in, out, L, Ns, ncols, ld, tw);
+    Ns *= 4; rem /= 4;
+    C* t = in; in = out; out = t;
+  }
+  if (rem % 2 == 0) {
+    stage<C, 2, INV, COLS>(in, out, L, Ns, ncols, ld, tw);
+    Ns *= 2; rem /= 2;
+    C* t = in; in = out; out = t;
+  }
+  return in;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double t = 0.0;
+  if (w == 0) {
+    t = (l < nw) ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (l == 0) sh[0] = t;
+  }
+  __syncthreads();
+  t = sh[0];
+  __syncthreads();
+  return t;
+}
+
+__device__ bool finish_reduction(double part, double* partial, unsigned* counter, int nblk, int bid, double* sh,
+                                 double* total) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partial[bid] = part;
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    last = (prev == (unsigned)nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += ((volatile double*)partial)[b];
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    *total = t;
+    *counter = 0u;
+  }
+  return true;
+}
+
+__device__ __forceinline__ bool first_half_active(const PcgState* st, int load) {
+  return st == nullptr || st[load].state == ST_RUN;
+}
+__device__ __forceinline__ bool second_half_active(const PcgState* st, int load) {
+  if (st == nullptr) return true;
+  const int s = st[load].state;
+  return s == ST_RUN || s == ST_CONV || s == ST_FIN_MAX;
+}
+
+constexpr int XT = 256;  // threads of the x passes
+constexpr int ST = 256;  // threads of the strided passes
+
+// ------------------------------------------------------------------------------------------------
+// x passes
+// ------------------------------------------------------------------------------------------------
+template <typename T, bool UPDATE>
+__global__ void __launch_bounds__(XT) fft_x_fwd_kernel(FftArgs a, int P) {
+  using C = typename V2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims d = a.d;
+  const int nx = d.nx, nxh = d.nxh;
+  C* b0 = reinterpret_cast<C*>(smem_raw);
+  C* b1 = b0 + P * nx;
+  const int comp = blockIdx.y, load = blockIdx.z;
+  if (UPDATE && !first_half_active(a.st, load)) return;
+  const long long nlines = (long long)d.ny * d.nz;
+  const long long foff = (long long)load * a.load_stride_f + (long long)comp * d.N;
+  T* r = reinterpret_cast<T*>(a.f0) + foff;
+  const T* ap = UPDATE ? reinterpret_cast<const T*>(a.f1) + foff : nullptr;
+  C* spec = reinterpret_cast<C*>(a.spec) + (long long)load * a.load_stride_s + (long long)comp * d.Nh;
+  const T alpha = UPDATE ? T(a.st[load].alpha) : T(0);
+  const long long line_base = 2LL * blockIdx.x * P;
+  for (int idx = threadIdx.x; idx < P * nx; idx += XT) {
+    const int q = idx / nx, xx = idx - q * nx;
+    const long long l0 = line_base + 2 * q;
+    T v0 = T(0), v1 = T(0);
+    if (l0 < nlines) {
+      const bool has1 = l0 + 1 < nlines;  // an odd line count leaves the last line unpaired
+      const long long g0 = l0 * nx + xx, g1 = g0 + nx;
+      v0 = r[g0];
+      if (has1) v1 = r[g1];
+      if (UPDATE) {
+        v0 = fma(-alpha, ap[g0], v0);
+        r[g0] = v0;
+        if (has1) {
+          v1 = fma(-alpha, ap[g1], v1);
+          r[g1] = v1;
+        }
+      }
+    }
+    b0[q * nx + xx] = mk<C>(v0, v1);
+  }
+  __syncthreads();
+  const C* res = fft_smem<C, false, false>(b0, b1, nx, P, nx, reinterpret_cast<const C*>(a.tw.x));
+  for (int idx = threadIdx.x; idx < P * nxh; idx += XT) {
+    const int q = idx / nxh, k = idx - q * nxh;
+    const long long l0 = line_base + 2 * q;
+    if (l0 >= nlines) continue;
+    const C zk = res[q * nx + k];
+    const C zn = res[q * nx + (k == 0 ? 0 : nx - k)];
+    const T h = T(0.5);
+    const C A = mk<C>(h * (zk.x + zn.x), h * (zk.y - zn.y));
+    const C B = mk<C>(h * (zk.y + zn.y), h * (zn.x - zk.x));
+    spec[l0 * nxh + k] = A;
+    if (l0 + 1 < nlines) spec[(l0 + 1) * nxh + k] = B;
+  }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(XT) fft_x_inv_kernel(FftArgs a, int P) {
+  using C = typename V2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_sh[32];
+  const Dims d = a.d;
+  const int nx = d.nx, nxh = d.nxh, half = nx / 2;
+  C* b0 = reinterpret_cast<C*>(smem_raw);
+  C* b1 = b0 + P * nx;
+  const int comp = blockIdx.y, load = blockIdx.z;
+  if (MODE != FX_PLAIN && !second_half_active(a.st, load)) return;
+  const long long nlines = (long long)d.ny * d.nz;
+  const long long foff = (long long)load * a.load_stride_f + (long long)comp * d.N;
+  const C* spec = reinterpret_cast<const C*>(a.spec) + (long long)load * a.load_stride_s + (long long)comp * d.Nh;
+  const long long line_base = 2LL * blockIdx.x * P;
+  for (int idx = threadIdx.x; idx < P * nx; idx += XT) {
+    const int q = idx / nx, k = idx - q * nx;
+    const long long l0 = line_base + 2 * q;
+    C z = mk<C>(T(0), T(0));
+    if (l0 < nlines) {
+      const bool has1 = l0 + 1 < nlines;
+      C A, B = mk<C>(T(0), T(0));
+      if (k <= half) {
+        A = spec[l0 * nxh + k];
+        if (has1) B = spec[(l0 + 1) * nxh + k];
+        if (k == 0 || k == half) {
+          A.y = T(0);
+          B.y = T(0);
+        }
+      } else {
+        const C a0 = spec[l0 * nxh + nx - k];
+        A = mk<C>(a0.x, -a0.y);
+        if (has1) {
+          const C b0_ = spec[(l0 + 1) * nxh + nx - k];
+          B = mk<C>(b0_.x, -b0_.y);
+        }
+      }
+      z = mk<C>(A.x - B.y, A.y + B.x);  // A + i B
+    }
+    b0[q * nx + k] = z;
+  }
+  __syncthreads();
+  const C* res = fft_smem<C, true, false>(b0, b1, nx, P, nx, reinterpret_cast<const C*>(a.tw.x));
+  T* f0 = reinterpret_cast<T*>(a.f0) + foff;
+  T* f2 = (MODE != FX_PLAIN) ? reinterpret_cast<T*>(a.f2) + foff : nullptr;
+  const T alpha = (MODE == FX_PCG) ? T(a.st[load].alpha) : T(0);
+  const T beta = (MODE == FX_PCG) ? T(a.st[load].beta) : T(0);
+  for (int idx = threadIdx.x; idx < P * nx; idx += XT) {
+    const int q = idx / nx, xx = idx - q * nx;
+    const long long l0 = line_base + 2 * q;
+    if (l0 >= nlines) continue;
+    const C zc = res[q * nx + xx];
+    const bool has1 = l0 + 1 < nlines;
+    const long long g0 = l0 * nx + xx, g1 = g0 + nx;
+    if (MODE == FX_PLAIN) {
+      f0[g0] = zc.x;
+      if (has1) f0[g1] = zc.y;
+    } else if (MODE == FX_PCG_INIT) {
+      f2[g0] = zc.x;
+      if (has1) f2[g1] = zc.y;
+    } else {
+      const T p0 = f2[g0];
+      f0[g0] = fma(alpha, p0, f0[g0]);
+      f2[g0] = fma(beta, p0, zc.x);
+      if (has1) {
+        const T p1 = f2[g1];
+        f0[g1] = fma(alpha, p1, f0[g1]);
+        f2[g1] = fma(beta, p1, zc.y);
+      }
+    }
+  }
+  if (MODE != FX_PLAIN && a.st != nullptr) {
+    // the last CTA over all components finalises the iteration bookkeeping
+    const int nblk = gridDim.x * gridDim.y;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    double total;
+    __syncthreads();
+    if (finish_reduction(0.0, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load, nblk, bid,
+                         red_sh, &total)) {
+      if (threadIdx.x == 0) {
+        PcgState& s = a.st[load];
+        if (MODE == FX_PCG) s.iter += 1;
+        if (s.state == ST_CONV) s.state = ST_DONE;
+        else if (s.state == ST_FIN_MAX) s.state = ST_MAXIT;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// strided passes: columns cf = 0..ncols-1 of the half spectrum; element e of column cf at
+//   (cf / nxh) * outer + e * estride + (cf % nxh)
+// ------------------------------------------------------------------------------------------------
+struct ColMap {
+  int L;             // transform length (axis size)
+  int ncols;         // number of columns
+  long long outer;   // stride of cf / nxh
+  long long estride; // stride along the axis
+};
+
+template <typename T, bool INV>
+__global__ void __launch_bounds__(ST) fft_strided_kernel(FftArgs a, ColMap m, int TC, const typename V2<T>::t* tw) {
+  using C = typename V2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* b0 = reinterpret_cast<C*>(smem_raw);
+  C* b1 = b0 + m.L * TC;
+  const int comp = blockIdx.y, load = blockIdx.z;
+  if (a.st != nullptr) {
+    if (!INV && !first_half_active(a.st, load)) return;
+    if (INV && !second_half_active(a.st, load)) return;
+  }
+  C* spec = reinterpret_cast<C*>(a.spec) + (long long)load * a.load_stride_s + (long long)comp * a.d.Nh;
+  const int nxh = a.d.nxh;
+  const int cf0 = blockIdx.x * TC;
+  for (int idx = threadIdx.x; idx < m.L * TC; idx += ST) {
+    const int e = idx / TC, t = idx - e * TC;
+    const int cf = cf0 + t;
+    C v = mk<C>(T(0), T(0));
+    if (cf < m.ncols) v = spec[(long long)(cf / nxh) * m.outer + (long long)e * m.estride + (cf % nxh)];
+    b0[idx] = v;
+  }
+  __syncthreads();
+  const C* res = fft_smem<C, INV, true>(b0, b1, m.L, TC, TC, tw);
+  for (int idx = threadIdx.x; idx < m.L * TC; idx += ST) {
+    const int e = idx / TC, t = idx - e * TC;
+    const int cf = cf0 + t;
+    if (cf < m.ncols) spec[(long long)(cf / nxh) * m.outer + (long long)e * m.estride + (cf % nxh)] = res[idx];
+  }
+}
+
+// Last axis with the block solve.  3-D: axis z, columns cf = ky * nxh + kx.  2-D: axis y, cf = kx.
+template <typename T, int NC, bool SOLVE>
+__global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, int TC, const typename V2<T>::t* tw) {
+  using C = typename V2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_sh[32];
+  const int W = NC * TC;  // columns held by the CTA (component-major)
+  C* b0 = reinterpret_cast<C*>(smem_raw);
+  C* b1 = b0 + m.L * W;
+  const int load = blockIdx.z;
+  if (!first_half_active(a.st, load)) return;
+  C* spec = reinterpret_cast<C*>(a.spec) + (long long)load * a.load_stride_s;
+  const long long Nh = a.d.Nh;
+  const int nxh = a.d.nxh, half = a.d.nx / 2;
+  const int cf0 = blockIdx.x * TC;
+  for (int idx = threadIdx.x; idx < m.L * W; idx += ST) {
+    const int e = idx / W, rem = idx - e * W, comp = rem / TC, t = rem - comp * TC;
+    const int cf = cf0 + t;
+    C v = mk<C>(T(0), T(0));
+    if (cf < m.ncols) v = spec[comp * Nh + (long long)(cf / nxh) * m.outer + (long long)e * m.estride + (cf % nxh)];
+    b0[idx] = v;
+  }
+  __syncthreads();
+  C* res = fft_smem<C, false, true>(b0, b1, m.L, W, W, tw);
+  C* other = (res == b0) ? b1 : b0;
+  if (!SOLVE) {
+    for (int idx = threadIdx.x; idx < m.L * W; idx += ST) {
+      const int e = idx / W, rem = idx - e * W, comp = rem / TC, t = rem - comp * TC;
+      const int cf = cf0 + t;
+      if (cf < m.ncols) spec[comp * Nh + (long long)(cf / nxh) * m.outer + (long long)e * m.estride + (cf % nxh)] = res[idx];
+    }
+    return;
+  }
+  const T* sym = reinterpret_cast<const T*>(a.sym);
+  double dot = 0.0;
+  for (int idx = threadIdx.x; idx < m.L * TC; idx += ST) {
+    const int e = idx / TC, t = idx - e * TC;
+    const int cf = cf0 + t;
+    if (cf >= m.ncols) continue;
+    const long long ti = (long long)(cf / nxh) * m.outer + (long long)e * m.estride + (cf % nxh);
+    const int kx = cf % nxh;
+    const double wgt = (kx == 0 || kx == half) ? 1.0 : 2.0;
+    C r[NC], z[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) r[c] = res[e * W + c * TC + t];
+    if constexpr (NC == 1) {
+      const T k00 = sym[ti];
+      z[0] = mk<C>(k00 * r[0].x, k00 * r[0].y);
+    } else if constexpr (NC == 2) {
+      const T k00 = sym[ti], k11 = sym[Nh + ti], k01 = sym[2 * Nh + ti];
+      z[0] = mk<C>(fma(k00, r[0].x, k01 * r[1].x), fma(k00, r[0].y, k01 * r[1].y));
+      z[1] = mk<C>(fma(k01, r[0].x, k11 * r[1].x), fma(k01, r[0].y, k11 * r[1].y));
+    } else {
+      const T k00 = sym[ti], k11 = sym[Nh + ti], k22 = sym[2 * Nh + ti];
+      const T k12 = sym[3 * Nh + ti], k02 = sym[4 * Nh + ti], k01 = sym[5 * Nh + ti];
+      z[0] = mk<C>(fma(k00, r[0].x, fma(k01, r[1].x, k02 * r[2].x)), fma(k00, r[0].y, fma(k01, r[1].y, k02 * r[2].y)));
+      z[1] = mk<C>(fma(k01, r[0].x, fma(k11, r[1].x, k12 * r[2].x)), fma(k01, r[0].y, fma(k11, r[1].y, k12 * r[2].y)));
+      z[2] = mk<C>(fma(k02, r[0].x, fma(k12, r[1].x, k22 * r[2].x)), fma(k02, r[0].y, fma(k12, r[1].y, k22 * r[2].y)));
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      acc = fma((double)r[c].x, (double)z[c].x, acc);
+      acc = fma((double)r[c].y, (double)z[c].y, acc);
+      res[e * W + c * TC + t] = z[c];
+    }
+    dot = fma(wgt, acc, dot);
+  }
+  __syncthreads();
+  const C* out = fft_smem<C, true, true>(res, other, m.L, W, W, tw);
+  for (int idx = threadIdx.x; idx < m.L * W; idx += ST) {
+    const int e = idx / W, rem = idx - e * W, comp = rem / TC, t = rem - comp * TC;
+    const int cf = cf0 + t;
+    if (cf < m.ncols) spec[comp * Nh + (long long)(cf / nxh) * m.outer + (long long)e * m.estride + (cf % nxh)] = out[idx];
+  }
+  if (a.st != nullptr) {
+    const double part = block_sum(dot, red_sh);
+    double total;
+    if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load, gridDim.x,
+                         blockIdx.x, red_sh, &total)) {
+      if (threadIdx.x == 0) {
+        PcgState& s = a.st[load];
+        if (a.init) {
+          s.rz = total;
+          s.rz_init = total;
+          if (s.bnorm2 < 0.0) s.bnorm2 = total;  // zero initial guess: <b, K_ref^+ b> = <r0, z0>
+          s.tol2 = s.tol2_rel * s.bnorm2;
+          s.alpha = 0.0;
+          s.beta = 0.0;
+          if (!isfinite(total)) s.state = ST_BREAK;
+          else if (total <= s.tol2) s.state = ST_CONV;
+        } else {
+          s.beta = (s.rz > 0.0) ? total / s.rz : 0.0;
+          s.rz = total;
+          if (!isfinite(total)) s.state = ST_BREAK;
+          else if (total <= s.tol2) s.state = ST_CONV;
+          else if (s.iter + 1 >= s.max_iter) s.state = ST_FIN_MAX;
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Algorithm 2 tail: packed symbol, checks and per-wavevector inverse
+// ------------------------------------------------------------------------------------------------
+template <int NC>
+__global__ void symbol_kernel(SymbolArgs a) {
+  const long long Nh = a.d.Nh;
+  const double2* sp = reinterpret_cast<const double2*>(a.spec);
+  const double invN = 1.0 / (double)a.d.N;
+  double mx_im = 0.0, mx_asym = 0.0, mx_abs = 0.0, mn_piv = 1e300;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Nh; k += (long long)gridDim.x * blockDim.x) {
+    double K[NC][NC];
+#pragma unroll
+    for (int al = 0; al < NC; ++al)
+#pragma unroll
+      for (int be = 0; be < NC; ++be) {
+        const double2 v = sp[((long long)be * NC + al) * Nh + k];  // spectrum of comp alpha of K_ref i^beta
+        K[al][be] = v.x;
+        mx_im = fmax(mx_im, fabs(v.y));
+        mx_abs = fmax(mx_abs, fabs(v.x));
+      }
+#pragma unroll
+    for (int al = 0; al < NC; ++al)
+#pragma unroll
+      for (int be = al + 1; be < NC; ++be) {
+        mx_asym = fmax(mx_asym, fabs(K[al][be] - K[be][al]));
+        const double s = 0.5 * (K[al][be] + K[be][al]);
+        K[al][be] = s;
+        K[be][al] = s;
+      }
+    double inv[6] = {0, 0, 0, 0, 0, 0};  // packed (00, 11, 22, 12, 02, 01) / (00, 11, 01) / (00)
+    if (k != 0) {
+      if (NC == 1) {
+        mn_piv = fmin(mn_piv, K[0][0]);
+        inv[0] = 1.0 / K[0][0];
+      } else if (NC == 2) {
+        const double det = K[0][0] * K[1][1] - K[0][1] * K[0][1];
+        mn_piv = fmin(mn_piv, fmin(K[0][0], det / K[0][0]));
+        inv[0] = K[1][1] / det;
+        inv[1] = K[0][0] / det;
+        inv[2] = -K[0][1] / det;
+      } else {
+        const double A = K[0][0], B = K[1][1], Cc = K[2][2], D = K[1][2], E = K[0][2], F = K[0][1];
+        const double c00 = B * Cc - D * D, c11 = A * Cc - E * E, c22 = A * B - F * F;
+        const double c12 = E * F - A * D, c02 = D * F - B * E, c01 = D * E - Cc * F;
+        const double det = A * c00 + F * c01 + E * c02;
+        mn_piv = fmin(mn_piv, fmin(A, fmin(c22 / A, det / c22)));
+        inv[0] = c00 / det; inv[1] = c11 / det; inv[2] = c22 / det;
+        inv[3] = c12 / det; inv[4] = c02 / det; inv[5] = c01 / det;
+      }
+    }
+    constexpr int NE_ = NC * (NC + 1) / 2;
+#pragma unroll
+    for (int e = 0; e < NE_; ++e) {
+      a.sym64[e * Nh + k] = inv[e] * invN;
+      if (a.sym32) a.sym32[e * Nh + k] = (float)(inv[e] * invN);
+    }
+  }
+  // block maxima -> partials (host reduces)
+  __shared__ double sh[4][256];
+  sh[0][threadIdx.x] = mx_im;
+  sh[1][threadIdx.x] = mx_asym;
+  sh[2][threadIdx.x] = mx_abs;
+  sh[3][threadIdx.x] = mn_piv;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sh[0][threadIdx.x] = fmax(sh[0][threadIdx.x], sh[0][threadIdx.x + s]);
+      sh[1][threadIdx.x] = fmax(sh[1][threadIdx.x], sh[1][threadIdx.x + s]);
+      sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + s]);
+      sh[3][threadIdx.x] = fmin(sh[3][threadIdx.x], sh[3][threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 4; ++i) a.partial[blockIdx.x * 4 + i] = sh[i][0];
+}
+
+template <typename K>
+cudaError_t set_smem(K kern, size_t bytes) {
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+constexpr size_t kSmemBudget = 112 * 1024;  // two CTAs per SM
+
+// pairs of x lines per CTA: as many as fit (power of two), at most 8
+template <typename T> int x_pairs(const Dims& d) {
+  using C = typename V2<T>::t;
+  const long long pairs = ((long long)d.ny * d.nz + 1) / 2;
+  int P = 8;
+  while (P > 1 && (2ull * P * d.nx * sizeof(C) > kSmemBudget || P > pairs)) P >>= 1;
+  return P;
+}
+
+template <typename T> int tile_cols(int L, int nc) {
+  using C = typename V2<T>::t;
+  int TC = 16;
+  while (TC > 1 && 2ull * L * nc * TC * sizeof(C) > kSmemBudget) TC >>= 1;
+  return TC;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_fft_x_fwd(const FftArgs& a, cudaStream_t s) {
+  using C = typename V2<T>::t;
+  const int P = x_pairs<T>(a.d);
+  const long long pairs = ((long long)a.d.ny * a.d.nz + 1) / 2;
+  dim3 grid((unsigned)((pairs + P - 1) / P), a.d.c, a.n_loads);
+  const size_t smem = 2ull * P * a.d.nx * sizeof(C);
+  if (a.mode == FX_PCG) {
+    auto k = fft_x_fwd_kernel<T, true>;
+    cudaError_t e = set_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, XT, smem, s>>>(a, P);
+  } else {
+    auto k = fft_x_fwd_kernel<T, false>;
+    cudaError_t e = set_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, XT, smem, s>>>(a, P);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fft_x_inv(const FftArgs& a, cudaStream_t s) {
+  using C = typename V2<T>::t;
+  const int P = x_pairs<T>(a.d);
+  const long long pairs = ((long long)a.d.ny * a.d.nz + 1) / 2;
+  dim3 grid((unsigned)((pairs + P - 1) / P), a.d.c, a.n_loads);
+  if (a.st != nullptr && (long long)grid.x * grid.y > a.red.max_blocks) return cudaErrorInvalidConfiguration;
+  const size_t smem = 2ull * P * a.d.nx * sizeof(C);
+  cudaError_t e;
+  if (a.mode == FX_PCG) {
+    auto k = fft_x_inv_kernel<T, FX_PCG>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<grid, XT, smem, s>>>(a, P);
+  } else if (a.mode == FX_PCG_INIT) {
+    auto k = fft_x_inv_kernel<T, FX_PCG_INIT>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<grid, XT, smem, s>>>(a, P);
+  } else {
+    auto k = fft_x_inv_kernel<T, FX_PLAIN>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<grid, XT, smem, s>>>(a, P);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fft_y(const FftArgs& a, int inverse, cudaStream_t s) {
+  using C = typename V2<T>::t;
+  // 3-D middle axis: columns (z, kx), element e = ky
+  ColMap m{a.d.ny, a.d.nz * a.d.nxh, (long long)a.d.ny * a.d.nxh, (long long)a.d.nxh};
+  const int TC = tile_cols<T>(m.L, 1);
+  dim3 grid((m.ncols + TC - 1) / TC, a.d.c, a.n_loads);
+  const size_t smem = 2ull * m.L * TC * sizeof(C);
+  const C* tw = reinterpret_cast<const C*>(a.tw.y);
+  cudaError_t e;
+  if (inverse) {
+    auto k = fft_strided_kernel<T, true>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<grid, ST, smem, s>>>(a, m, TC, tw);
+  } else {
+    auto k = fft_strided_kernel<T, false>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<grid, ST, smem, s>>>(a, m, TC, tw);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int NC>
+static cudaError_t launch_last_nc(const FftArgs& a, cudaStream_t s) {
+  using C = typename V2<T>::t;
+  ColMap m;
+  const C* tw;
+  if (a.d.dim == 3) {
+    m = ColMap{a.d.nz, a.d.ny * a.d.nxh, (long long)a.d.nxh, (long long)a.d.ny * a.d.nxh};
+    tw = reinterpret_cast<const C*>(a.tw.z);
+  } else {
+    m = ColMap{a.d.ny, a.d.nxh, 0LL, (long long)a.d.nxh};
+    tw = reinterpret_cast<const C*>(a.tw.y);
+  }
+  const int TC = tile_cols<T>(m.L, NC);
+  dim3 grid((m.ncols + TC - 1) / TC, 1, a.n_loads);
+  if (a.st != nullptr && (long long)grid.x > a.red.max_blocks) return cudaErrorInvalidConfiguration;
+  const size_t smem = 2ull * m.L * NC * TC * sizeof(C);
+  cudaError_t e;
+  if (a.sym) {
+    auto k = fft_last_kernel<T, NC, true>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<grid, ST, smem, s>>>(a, m, TC, tw);
+  } else {
+    auto k = fft_last_kernel<T, NC, false>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<grid, ST, smem, s>>>(a, m, TC, tw);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fft_last_solve(const FftArgs& a, cudaStream_t s) {
+  if (a.d.c == 1) return launch_last_nc<T, 1>(a, s);
+  if (a.d.c == 2) return launch_last_nc<T, 2>(a, s);
+  if (a.d.c == 3) return launch_last_nc<T, 3>(a, s);
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_fft_x_fwd<double>(const FftArgs&, cudaStream_t);
+template cudaError_t launch_fft_x_fwd<float>(const FftArgs&, cudaStream_t);
+template cudaError_t launch_fft_x_inv<double>(const FftArgs&, cudaStream_t);
+template cudaError_t launch_fft_x_inv<float>(const FftArgs&, cudaStream_t);
+template cudaError_t launch_fft_y<double>(const FftArgs&, int, cudaStream_t);
+template cudaError_t launch_fft_y<float>(const FftArgs&, int, cudaStream_t);
+template cudaError_t launch_fft_last_solve<double>(const FftArgs&, cudaStream_t);
+template cudaError_t launch_fft_last_solve<float>(const FftArgs&, cudaStream_t);
+
+cudaError_t launch_symbol_build(const SymbolArgs& a, int* blocks_out, cudaStream_t s) {
+  const int blocks = (int)std::min<long long>(2 * 152, (a.d.Nh + 255) / 256);
+  *blocks_out = blocks;
+  if (a.d.c == 1) symbol_kernel<1><<<blocks, 256, 0, s>>>(a);
+  else if (a.d.c == 2) symbol_kernel<2><<<blocks, 256, 0, s>>>(a);
+  else symbol_kernel<3><<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// W_L^m = exp(-2 pi i m / L), m = 0..L-1, from cos/sin of the first octant in long double.
+cudaError_t make_twiddles(int L, double2** d64, float2** d32) {
+  std::vector<double2> h64(L);
+  std::vector<float2> h32(L);
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int m = 0; m < L; ++m) {
+    // angle = 2 pi m / L reduced to [0, pi/4] by octant symmetry: exact at multiples of L/8
+    long long num = (long long)m * 8;  // angle in units of (2 pi / (8 L)) * 8 = octants * L
+    const int oct = (int)(num / L);    // 0..7
+    long long rem = num - (long long)oct * L;  // 0..L-1, angle within the octant = (2 pi / 8) * rem / L
+    // within-octant angle phi in [0, pi/4); use the reflected angle on odd octants
+    long double phi = two_pi / 8.0L * (long double)rem / (long double)L;
+    long double c = cosl(phi), sn = sinl(phi);
+    long double cr = cosl(two_pi / 8.0L - phi), sr = sinl(two_pi / 8.0L - phi);
+    long double cosv = 0, sinv = 0;
+    switch (oct) {  // theta = oct * pi/4 + phi
+      case 0: cosv = c; sinv = sn; break;
+      case 1: cosv = sr; sinv = cr; break;          // theta = pi/2 - (pi/4 - phi)
+      case 2: cosv = -sn; sinv = c; break;          // theta = pi/2 + phi
+      case 3: cosv = -cr; sinv = sr; break;         // theta = pi - (pi/4 - phi)
+      case 4: cosv = -c; sinv = -sn; break;         // theta = pi + phi
+      case 5: cosv = -sr; sinv = -cr; break;        // theta = 3pi/2 - (pi/4 - phi)
+      case 6: cosv = sn; sinv = -c; break;          // theta = 3pi/2 + phi
+      default: cosv = cr; sinv = -sr; break;        // theta = 2pi - (pi/4 - phi)
+    }
+    h64[m] = make_double2((double)cosv, (double)(-sinv));
+    h32[m] = make_float2((float)cosv, (float)(-sinv));
+  }
+  cudaError_t e = cudaMalloc(d64, sizeof(double2) * L);
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(d32, sizeof(float2) * L);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(*d64, h64.data(), sizeof(double2) * L, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*d32, h32.data(), sizeof(float2) * L, cudaMemcpyHostToDevice);
+}
+
+}  // namespace fehom

@@ -1,0 +1,713 @@
+// Matrix-free stiffness apply y = s * D^T W C (D x + e) on the periodic grid (Sec. 5.1; Eq. lin_system).
+//
+// Voxel-wise constant material C_e = C[phase(e)] is looked up by phase id (Sec. 3.1: the tangent
+// is diagonal per quadrature point; here it is constant per voxel as in Sec. 6.1).
+//
+// Trilinear hexahedron (HEX8_3D), 2x2x2 Gauss points.  The element field is written in the modal
+// basis {1, xi, eta, zeta, xi eta, eta zeta, xi zeta, xi eta zeta} on [-1, 1]^3, obtained from the
+// 8 nodal values by three butterfly stages (a Hadamard transform).  Its gradient is a sum of the
+// seven mutually orthogonal monomials {1, xi, eta, zeta, eta zeta, xi zeta, xi eta}; since 2-point
+// Gauss rules integrate their products exactly, the element energy is
+//     a_e(u, u) = sum_m mu_m g_m^T Chat g_m,   mu = 1 (m = 1), 1/3 (linear), 1/9 (bilinear),
+// where g_m holds the modal coefficients that multiply monomial m in each derivative and
+// Chat = V_e S P^T C P S is the material in gradient coordinates (P: gradient -> Mandel strain,
+// S: d/dxi -> d/dx scaling, V_e: voxel volume).  This is the same bilinear form as the quadrature
+// sum of Eq. global_sum, evaluated with 7 small contractions instead of 8 quadrature points.
+// The element forces follow from the transposed butterflies.
+//
+// 2-D pixels: P1TRI2_2D (two triangles with constant gradients, w = V_p/2 each, Fig. 3 b) and
+// Q1_2D (bilinear, modal basis {1, xi, eta, xi eta}, 2x2 Gauss, Fig. 3 a).
+//
+// Tiling.  A CTA owns BX x BY output nodes of the x-y plane and marches along z through a slab of
+// KZ planes.  Per element layer it stages the next node plane (with a periodic halo of one node)
+// in shared memory, computes the (BX+1) x (BY+1) elements of the layer once each, writes their
+// corner forces to shared memory, and lets each node thread gather the four bottom corners that
+// complete its node plane (the four top corners are carried to the next layer in registers).
+// No atomics; fixed summation order.
+#include "fehom_internal.cuh"
+
+#include <algorithm>
+#include <cstdio>
+
+namespace fehom {
+namespace {
+
+constexpr int BX = 32;
+constexpr int BY = 8;
+constexpr int PX = BX + 2;
+constexpr int PY = BY + 2;
+constexpr int EX = BX + 1;
+constexpr int EY = BY + 1;
+constexpr int NE = EX * EY;              // elements per layer per CTA (297)
+constexpr int NT = ((NE + 31) / 32) * 32; // threads (320)
+
+__device__ __forceinline__ int wrap(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// Block-wide FP64 sum; every thread gets the result. `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double t = 0.0;
+  if (w == 0) {
+    t = (l < nw) ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (l == 0) sh[0] = t;
+  }
+  __syncthreads();
+  t = sh[0];
+  __syncthreads();
+  return t;
+}
+
+// Deterministic reduction finalisation: CTA partials -> last-arriving CTA sums them in index order.
+// Returns true in the (single) CTA that must finalise; `total` is valid there.
+__device__ bool finish_reduction(double part, double* partial, unsigned* counter, int nblk, int bid,
+                                 double* sh, double* total) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partial[bid] = part;
+    __threadfence();
+    unsigned prev = atomicAdd(counter, 1u);
+    last = (prev == (unsigned)nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double acc = 0.0;
+  // fixed order: thread t sums blocks t, t + NT, ...; then a fixed-shape tree
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += ((volatile double*)partial)[b];
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    *total = t;
+    *counter = 0u;  // self-reset for the next launch
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------------------------------------
+// element kernels: modal contractions
+// ------------------------------------------------------------------------------------------------
+// General material: T[j][i] = sum_{l,k active} Ch[(j*3+i)*D + l*3+k] * g[l][k], active dirs = MASK.
+template <int MASK, int C, typename T>
+__device__ __forceinline__ void contract_gen(const T* __restrict__ Ch, const T (&g)[C][3], T wgt, T (&out)[C][3]) {
+  constexpr int D = 3 * C;
+#pragma unroll
+  for (int j = 0; j < C; ++j)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (!((MASK >> i) & 1)) continue;
+      const int kk = (C == 1) ? i : (j * 3 + i);
+      T acc = T(0);
+#pragma unroll
+      for (int l = 0; l < C; ++l)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if (!((MASK >> k) & 1)) continue;
+          const int ll = (C == 1) ? k : (l * 3 + k);
+          acc = fma(__ldg(Ch + kk * D + ll), g[l][k], acc);
+        }
+      out[j][i] = acc * wgt;
+    }
+}
+
+// Isotropic material on a cubic grid: T_ij = lam tr(g) delta_ij + mu (g_ij + g_ji) (entries in MASK).
+template <int MASK, typename T>
+__device__ __forceinline__ void contract_iso(const T (&g)[3][3], T lam, T mu, T (&out)[3][3]) {
+  // g[j][i]: derivative i of component j; entries outside MASK are zero
+  T tr = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if ((MASK >> i) & 1) tr += g[i][i];
+  const T lt = lam * tr;
+  const T mu2 = mu + mu;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (!((MASK >> i) & 1)) continue;
+      if (i == j) {
+        out[j][i] = fma(mu2, g[j][j], lt);
+      } else {
+        // g[i][j] (derivative j of component i) is nonzero only when direction j is active
+        out[j][i] = ((MASK >> j) & 1) ? mu * (g[j][i] + g[i][j]) : mu * g[j][i];
+      }
+    }
+}
+
+// Hex8 element: nodal values u[j][corner] (corner = a + 2b + 4c) -> forces f[j][corner].
+template <typename T, int C, bool ISO, bool HAS_E>
+__device__ __forceinline__ void hex8_element(const T (&u)[C][8], const T* __restrict__ Ch,
+                                             const T* __restrict__ iso, const double* __restrict__ tau,
+                                             T (&f)[C][8]) {
+  // forward butterflies: q[j][n], n = 1..7 (xi, eta, zeta, xi eta, eta zeta, xi zeta, xi eta zeta)
+  T q1[C], q2[C], q3[C], q4[C], q5[C], q6[C], q7[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    T s[4], d[4];
+#pragma unroll
+    for (int bc = 0; bc < 4; ++bc) {  // bc = b + 2c
+      s[bc] = u[j][2 * bc + 1] + u[j][2 * bc];
+      d[bc] = u[j][2 * bc + 1] - u[j][2 * bc];
+    }
+    // along y (b): index bc = b + 2c
+    const T ss0 = s[1] + s[0], sd0 = s[1] - s[0], ss1 = s[3] + s[2], sd1 = s[3] - s[2];
+    const T ds0 = d[1] + d[0], dd0 = d[1] - d[0], ds1 = d[3] + d[2], dd1 = d[3] - d[2];
+    // along z (c)
+    q3[j] = ss1 - ss0;
+    q2[j] = sd1 + sd0;
+    q5[j] = sd1 - sd0;
+    q1[j] = ds1 + ds0;
+    q6[j] = ds1 - ds0;
+    q4[j] = dd1 + dd0;
+    q7[j] = dd1 - dd0;
+  }
+  // gradient coefficients per monomial, g[j][dir]
+  T g1[C][3], gx[C][3], gy[C][3], gz[C][3], gyz[C][3], gxz[C][3], gxy[C][3];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    g1[j][0] = q1[j]; g1[j][1] = q2[j]; g1[j][2] = q3[j];
+    gx[j][0] = T(0);  gx[j][1] = q4[j]; gx[j][2] = q6[j];   // monomial xi
+    gy[j][0] = q4[j]; gy[j][1] = T(0);  gy[j][2] = q5[j];   // eta
+    gz[j][0] = q6[j]; gz[j][1] = q5[j]; gz[j][2] = T(0);    // zeta
+    gyz[j][0] = q7[j]; gyz[j][1] = T(0); gyz[j][2] = T(0);  // eta zeta
+    gxz[j][0] = T(0); gxz[j][1] = q7[j]; gxz[j][2] = T(0);  // xi zeta
+    gxy[j][0] = T(0); gxy[j][1] = T(0); gxy[j][2] = q7[j];  // xi eta
+  }
+  T t1[C][3], tx[C][3], ty[C][3], tz[C][3], tyz[C][3], txz[C][3], txy[C][3];
+  constexpr double third = 1.0 / 3.0, ninth = 1.0 / 9.0;
+  if constexpr (ISO && C == 3) {
+    const T lam = iso[0], mu = iso[1];
+    contract_iso<7>(g1, lam, mu, t1);
+    const T l3 = lam * T(third), m3 = mu * T(third), l9 = lam * T(ninth), m9 = mu * T(ninth);
+    contract_iso<6>(gx, l3, m3, tx);
+    contract_iso<5>(gy, l3, m3, ty);
+    contract_iso<3>(gz, l3, m3, tz);
+    contract_iso<1>(gyz, l9, m9, tyz);
+    contract_iso<2>(gxz, l9, m9, txz);
+    contract_iso<4>(gxy, l9, m9, txy);
+  } else {
+    contract_gen<7>(Ch, g1, T(1), t1);
+    contract_gen<6>(Ch, gx, T(third), tx);
+    contract_gen<5>(Ch, gy, T(third), ty);
+    contract_gen<3>(Ch, gz, T(third), tz);
+    contract_gen<1>(Ch, gyz, T(ninth), tyz);
+    contract_gen<2>(Ch, gxz, T(ninth), txz);
+    contract_gen<4>(Ch, gxy, T(ninth), txy);
+  }
+  if constexpr (HAS_E) {
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) t1[j][i] += T(tau[j * 3 + i]);
+  }
+  // dual modal forces and transposed butterflies
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const T Q1 = t1[j][0], Q2 = t1[j][1], Q3 = t1[j][2];
+    const T Q4 = tx[j][1] + ty[j][0];
+    const T Q5 = ty[j][2] + tz[j][1];
+    const T Q6 = tx[j][2] + tz[j][0];
+    const T Q7 = tyz[j][0] + txz[j][1] + txy[j][2];
+    // z stage (transposed)
+    const T ds0 = Q1 - Q6, ds1 = Q1 + Q6;
+    const T dd0 = Q4 - Q7, dd1 = Q4 + Q7;
+    const T sd0 = Q2 - Q5, sd1 = Q2 + Q5;
+    const T ss0 = -Q3, ss1 = Q3;
+    // y stage (transposed): s[b + 2c], d[b + 2c]
+    T s[4], d[4];
+    s[0] = ss0 - sd0; s[1] = ss0 + sd0; s[2] = ss1 - sd1; s[3] = ss1 + sd1;
+    d[0] = ds0 - dd0; d[1] = ds0 + dd0; d[2] = ds1 - dd1; d[3] = ds1 + dd1;
+    // x stage (transposed)
+#pragma unroll
+    for (int bc = 0; bc < 4; ++bc) {
+      f[j][2 * bc] = s[bc] - d[bc];
+      f[j][2 * bc + 1] = s[bc] + d[bc];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// 3-D hex8 kernel
+// ------------------------------------------------------------------------------------------------
+template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, bool DOT>
+__global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* pl = reinterpret_cast<T*>(smem_raw);                 // [2][C][PY][PX]
+  T* F = pl + 2 * C * PY * PX;                             // [4 bottom + 4 top][C][EY][EX]
+  __shared__ double red_sh[32];
+
+  const Dims d = a.d;
+  const int load = blockIdx.z;
+  if (DOT && a.st != nullptr && a.st[load].state != ST_RUN) return;
+
+  const int tiles_x = (d.nx + BX - 1) / BX;
+  const int i0 = (blockIdx.x % tiles_x) * BX;
+  const int j0 = (blockIdx.x / tiles_x) * BY;
+  const int k0 = blockIdx.y * kz_per_cta;
+  const int k1 = min(k0 + kz_per_cta, d.nz);
+  const int tid = threadIdx.x;
+
+  const T* x = HAS_X ? reinterpret_cast<const T*>(a.x) + (long long)load * a.load_stride : nullptr;
+  T* y = reinterpret_cast<T*>(a.y) + (long long)load * a.load_stride;
+  const T* mats = reinterpret_cast<const T*>(a.mats);
+  const T* isot = reinterpret_cast<const T*>(a.iso);
+  const double* tau = HAS_E ? a.tau + (long long)load * a.n_phases * (3 * C) : nullptr;
+  const long long plane = (long long)d.nx * d.ny;
+
+  auto load_plane = [&](int slot, int k) {
+    if (!HAS_X) return;
+    const int kk = wrap(k, d.nz);
+    for (int idx = tid; idx < C * PY * PX; idx += NT) {
+      const int px = idx % PX;
+      const int py = (idx / PX) % PY;
+      const int j = idx / (PX * PY);
+      const int gi = wrap(i0 - 1 + px, d.nx);
+      const int gj = wrap(j0 - 1 + py, d.ny);
+      pl[((slot * C + j) * PY + py) * PX + px] = x[(long long)j * d.N + kk * plane + (long long)gj * d.nx + gi];
+    }
+  };
+
+  // node-thread state: top-corner contributions carried to the next plane
+  const int ni = tid % BX, nj = tid / BX;  // valid node thread when tid < BX * BY
+  const bool node_thread = tid < BX * BY && (i0 + ni) < d.nx && (j0 + nj) < d.ny;
+  T carry[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) carry[j] = T(0);
+  double dot = 0.0;
+
+  const int ei = tid % EX, ej = tid / EX;  // element thread
+  const bool elem_thread = tid < NE;
+  const int gie = wrap(i0 - 1 + ei, d.nx);
+  const int gje = wrap(j0 - 1 + ej, d.ny);
+
+  int cur = 0;
+  load_plane(cur, k0 - 1);
+  for (int k = k0 - 1; k < k1; ++k) {
+    // element layer k spans node planes k (slot cur) and k + 1 (slot cur ^ 1)
+    load_plane(cur ^ 1, k + 1);
+    __syncthreads();
+    if (elem_thread) {
+      T u[C][8];
+#pragma unroll
+      for (int j = 0; j < C; ++j)
+#pragma unroll
+        for (int cn = 0; cn < 8; ++cn) {
+          const int aa = cn & 1, bb = (cn >> 1) & 1, cc = cn >> 2;
+          u[j][cn] = HAS_X ? pl[(((cur ^ cc) * C + j) * PY + ej + bb) * PX + ei + aa] : T(0);
+        }
+      const int kk = wrap(k, d.nz);
+      const int ph = a.ids ? a.ids[(long long)kk * plane + (long long)gje * d.nx + gie] : 0;
+      T f[C][8];
+      hex8_element<T, C, ISO, HAS_E>(u, mats + (long long)ph * (9 * C * C), isot + 2 * ph,
+                                     HAS_E ? tau + ph * (3 * C) : nullptr, f);
+#pragma unroll
+      for (int j = 0; j < C; ++j)
+#pragma unroll
+        for (int cn = 0; cn < 8; ++cn) F[((cn * C + j) * EY + ej) * EX + ei] = f[j][cn];
+    }
+    __syncthreads();
+    if (node_thread) {
+      // node (i, j) of plane k: bottom corners (c = 0) of layer k from elements (i-1..i, j-1..j)
+      // plus the carried top corners of layer k-1; then carry the top corners of layer k.
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        T bot = F[((3 * C + j) * EY + nj) * EX + ni]          // corner (1,1,0) of element (i-1, j-1)
+              + F[((2 * C + j) * EY + nj) * EX + ni + 1]      // corner (0,1,0) of element (i, j-1)
+              + F[((1 * C + j) * EY + nj + 1) * EX + ni]      // corner (1,0,0) of element (i-1, j)
+              + F[((0 * C + j) * EY + nj + 1) * EX + ni + 1]; // corner (0,0,0) of element (i, j)
+        T top = F[((7 * C + j) * EY + nj) * EX + ni]
+              + F[((6 * C + j) * EY + nj) * EX + ni + 1]
+              + F[((5 * C + j) * EY + nj + 1) * EX + ni]
+              + F[((4 * C + j) * EY + nj + 1) * EX + ni + 1];
+        if (k >= k0) {
+          const T val = T(a.y_scale) * (carry[j] + bot);
+          const long long gidx = (long long)j * d.N + (long long)k * plane + (long long)(j0 + nj) * d.nx + i0 + ni;
+          y[gidx] = val;
+          if (DOT) dot += (double)val * (double)pl[((cur * C + j) * PY + nj + 1) * PX + ni + 1];
+        }
+        carry[j] = top;
+      }
+    }
+    cur ^= 1;
+    // the next iteration overwrites slot cur^1 (old plane k) only after its __syncthreads
+    __syncthreads();
+  }
+  if (DOT) {
+    const double part = block_sum(dot, red_sh);
+    const int nblk = gridDim.x * gridDim.y;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    double total;
+    if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load, nblk,
+                         bid, red_sh, &total)) {
+      if (threadIdx.x == 0) {
+        PcgState& s = a.st[load];
+        s.pAp = total;
+        if (!(total > 0.0) || !isfinite(total)) {
+          s.state = ST_BREAK;
+          s.alpha = 0.0;
+        } else {
+          s.alpha = s.rz / total;
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// 2-D pixel kernels (P1 triangles, Q1)
+// ------------------------------------------------------------------------------------------------
+template <typename T, int C, int ELEM, bool HAS_E>
+__device__ __forceinline__ void pixel_element(const T (&u)[C][4], const T* __restrict__ Ch,
+                                              const double* __restrict__ tau, T (&f)[C][4]) {
+  constexpr int D = 2 * C;
+  // corners: 0 = (0,0), 1 = (1,0), 2 = (0,1), 3 = (1,1); g[j][dir] = raw difference / modal coefficient
+  auto contract = [&](const T (&g)[C][2], T w, T (&out)[C][2], int mask) {
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int l = 0; l < C; ++l)
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+            if ((mask >> k) & 1) acc = fma(__ldg(Ch + (j * 2 + i) * D + l * 2 + k), g[l][k], acc);
+        out[j][i] = acc * w;
+      }
+  };
+  if constexpr (ELEM == P1TRI2_2D) {
+    // triangle A (0,0),(1,0),(1,1): gx = u1 - u0, gy = u3 - u1; triangle B (0,0),(1,1),(0,1): gx = u3 - u2, gy = u2 - u0
+    T gA[C][2], gB[C][2], tA[C][2], tB[C][2];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      gA[j][0] = u[j][1] - u[j][0];
+      gA[j][1] = u[j][3] - u[j][1];
+      gB[j][0] = u[j][3] - u[j][2];
+      gB[j][1] = u[j][2] - u[j][0];
+    }
+    contract(gA, T(1), tA, 3);
+    contract(gB, T(1), tB, 3);
+    if constexpr (HAS_E) {
+#pragma unroll
+      for (int j = 0; j < C; ++j)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          tA[j][i] += T(tau[j * 2 + i]);
+          tB[j][i] += T(tau[j * 2 + i]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      f[j][0] = -tA[j][0] - tB[j][1];
+      f[j][1] = tA[j][0] - tA[j][1];
+      f[j][2] = tB[j][1] - tB[j][0];
+      f[j][3] = tA[j][1] + tB[j][0];
+    }
+  } else {
+    // Q1: modal q1 (xi), q2 (eta), q3 (xi eta); monomials 1: (q1, q2), xi: (0, q3), eta: (q3, 0)
+    T g1[C][2], gx[C][2], gy[C][2], t1[C][2], tx[C][2], ty[C][2];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const T s0 = u[j][1] + u[j][0], d0 = u[j][1] - u[j][0];
+      const T s1 = u[j][3] + u[j][2], d1 = u[j][3] - u[j][2];
+      const T q1 = d1 + d0, q2 = s1 - s0, q3 = d1 - d0;
+      g1[j][0] = q1; g1[j][1] = q2;
+      gx[j][0] = T(0); gx[j][1] = q3;
+      gy[j][0] = q3; gy[j][1] = T(0);
+    }
+    constexpr double third = 1.0 / 3.0;
+    contract(g1, T(1), t1, 3);
+    contract(gx, T(third), tx, 2);
+    contract(gy, T(third), ty, 1);
+    if constexpr (HAS_E) {
+#pragma unroll
+      for (int j = 0; j < C; ++j)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) t1[j][i] += T(tau[j * 2 + i]);
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const T Q1 = t1[j][0], Q2 = t1[j][1], Q3 = tx[j][1] + ty[j][0];
+      // transposed: d0 = Q1 - Q3, d1 = Q1 + Q3, s0 = -Q2, s1 = Q2
+      const T d0 = Q1 - Q3, d1 = Q1 + Q3, s0 = -Q2, s1 = Q2;
+      f[j][0] = s0 - d0;
+      f[j][1] = s0 + d0;
+      f[j][2] = s1 - d1;
+      f[j][3] = s1 + d1;
+    }
+  }
+}
+
+constexpr int BY2 = 8;  // 2-D tile: BX x BY2 nodes
+constexpr int PY2 = BY2 + 2, EY2 = BY2 + 1, NE2 = EX * EY2, NT2 = ((NE2 + 31) / 32) * 32;
+
+template <typename T, int C, int ELEM, bool HAS_X, bool HAS_E, bool DOT>
+__global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* pl = reinterpret_cast<T*>(smem_raw);  // [C][PY2][PX]
+  T* F = pl + C * PY2 * PX;                // [4][C][EY2][EX]
+  __shared__ double red_sh[32];
+  const Dims d = a.d;
+  const int load = blockIdx.z;
+  if (DOT && a.st != nullptr && a.st[load].state != ST_RUN) return;
+  const int tiles_x = (d.nx + BX - 1) / BX;
+  const int i0 = (blockIdx.x % tiles_x) * BX;
+  const int j0 = (blockIdx.x / tiles_x) * BY2;
+  const int tid = threadIdx.x;
+  const T* x = HAS_X ? reinterpret_cast<const T*>(a.x) + (long long)load * a.load_stride : nullptr;
+  T* y = reinterpret_cast<T*>(a.y) + (long long)load * a.load_stride;
+  const T* mats = reinterpret_cast<const T*>(a.mats);
+  const double* tau = HAS_E ? a.tau + (long long)load * a.n_phases * (2 * C) : nullptr;
+  if (HAS_X) {
+    for (int idx = tid; idx < C * PY2 * PX; idx += NT2) {
+      const int px = idx % PX, py = (idx / PX) % PY2, j = idx / (PX * PY2);
+      pl[idx] = x[(long long)j * d.N + (long long)wrap(j0 - 1 + py, d.ny) * d.nx + wrap(i0 - 1 + px, d.nx)];
+    }
+  }
+  __syncthreads();
+  const int ei = tid % EX, ej = tid / EX;
+  if (tid < NE2) {
+    T u[C][4];
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+#pragma unroll
+      for (int cn = 0; cn < 4; ++cn)
+        u[j][cn] = HAS_X ? pl[(j * PY2 + ej + (cn >> 1)) * PX + ei + (cn & 1)] : T(0);
+    const int ph = a.ids ? a.ids[(long long)wrap(j0 - 1 + ej, d.ny) * d.nx + wrap(i0 - 1 + ei, d.nx)] : 0;
+    T f[C][4];
+    pixel_element<T, C, ELEM, HAS_E>(u, mats + (long long)ph * (4 * C * C), HAS_E ? tau + ph * (2 * C) : nullptr, f);
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+#pragma unroll
+      for (int cn = 0; cn < 4; ++cn) F[((cn * C + j) * EY2 + ej) * EX + ei] = f[j][cn];
+  }
+  __syncthreads();
+  double dot = 0.0;
+  const int ni = tid % BX, nj = tid / BX;
+  if (tid < BX * BY2 && i0 + ni < d.nx && j0 + nj < d.ny) {
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const T v = F[((3 * C + j) * EY2 + nj) * EX + ni] + F[((2 * C + j) * EY2 + nj) * EX + ni + 1] +
+                  F[((1 * C + j) * EY2 + nj + 1) * EX + ni] + F[((0 * C + j) * EY2 + nj + 1) * EX + ni + 1];
+      const T val = T(a.y_scale) * v;
+      y[(long long)j * d.N + (long long)(j0 + nj) * d.nx + i0 + ni] = val;
+      if (DOT) dot += (double)val * (double)pl[(j * PY2 + nj + 1) * PX + ni + 1];
+    }
+  }
+  if (DOT) {
+    const double part = block_sum(dot, red_sh);
+    double total;
+    if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load,
+                         gridDim.x, blockIdx.x, red_sh, &total)) {
+      if (threadIdx.x == 0) {
+        PcgState& s = a.st[load];
+        s.pAp = total;
+        if (!(total > 0.0) || !isfinite(total)) {
+          s.state = ST_BREAK;
+          s.alpha = 0.0;
+        } else {
+          s.alpha = s.rz / total;
+        }
+      }
+    }
+  }
+}
+
+template <typename K>
+cudaError_t set_smem(K kern, size_t bytes) {
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, bool DOT>
+cudaError_t launch_hex8_t(const StencilArgs& a, cudaStream_t s) {
+  const Dims& d = a.d;
+  const int tiles = ((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
+  // z slabs: enough CTAs to fill 2 waves of 152 SMs, at least 8 planes per slab
+  int slabs = (2 * 152 + tiles - 1) / tiles;
+  slabs = max(1, min(slabs, d.nz / 8 > 0 ? d.nz / 8 : 1));
+  const int kz = (d.nz + slabs - 1) / slabs;
+  slabs = (d.nz + kz - 1) / kz;
+  if (DOT && tiles * slabs > a.red.max_blocks) return cudaErrorInvalidConfiguration;
+  const size_t smem = sizeof(T) * (2 * C * PY * PX + 8 * C * EY * EX);
+  auto kern = hex8_apply_kernel<T, C, ISO, HAS_X, HAS_E, DOT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(tiles, slabs, a.n_loads);
+  kern<<<grid, NT, smem, s>>>(a, kz);
+  return cudaGetLastError();
+}
+
+template <typename T, int C, int ELEM, bool HAS_X, bool HAS_E, bool DOT>
+cudaError_t launch_pixel_t(const StencilArgs& a, cudaStream_t s) {
+  const Dims& d = a.d;
+  const int tiles = ((d.nx + BX - 1) / BX) * ((d.ny + BY2 - 1) / BY2);
+  if (DOT && tiles > a.red.max_blocks) return cudaErrorInvalidConfiguration;
+  const size_t smem = sizeof(T) * (C * PY2 * PX + 4 * C * EY2 * EX);
+  auto kern = pixel_apply_kernel<T, C, ELEM, HAS_X, HAS_E, DOT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(tiles, 1, a.n_loads);
+  kern<<<grid, NT2, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int C, bool ISO>
+cudaError_t dispatch_hex8(const StencilArgs& a, cudaStream_t s) {
+  const bool hx = a.x != nullptr, he = a.tau != nullptr, dot = a.st != nullptr;
+  if (dot) {
+    if (!hx || he) return cudaErrorInvalidValue;
+    return launch_hex8_t<T, C, ISO, true, false, true>(a, s);
+  }
+  if (hx && he) return launch_hex8_t<T, C, ISO, true, true, false>(a, s);
+  if (hx) return launch_hex8_t<T, C, ISO, true, false, false>(a, s);
+  if (he) return launch_hex8_t<T, C, ISO, false, true, false>(a, s);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int C, int ELEM>
+cudaError_t dispatch_pixel(const StencilArgs& a, cudaStream_t s) {
+  const bool hx = a.x != nullptr, he = a.tau != nullptr, dot = a.st != nullptr;
+  if (dot) {
+    if (!hx || he) return cudaErrorInvalidValue;
+    return launch_pixel_t<T, C, ELEM, true, false, true>(a, s);
+  }
+  if (hx && he) return launch_pixel_t<T, C, ELEM, true, true, false>(a, s);
+  if (hx) return launch_pixel_t<T, C, ELEM, true, false, false>(a, s);
+  if (he) return launch_pixel_t<T, C, ELEM, false, true, false>(a, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_stiffness(const StencilArgs& a, cudaStream_t s) {
+  const Dims& d = a.d;
+  if (d.elem == HEX8_3D) {
+    if (d.c == 1) return dispatch_hex8<T, 1, false>(a, s);
+    if (a.iso) return dispatch_hex8<T, 3, true>(a, s);
+    return dispatch_hex8<T, 3, false>(a, s);
+  }
+  if (d.elem == P1TRI2_2D) return d.c == 1 ? dispatch_pixel<T, 1, P1TRI2_2D>(a, s) : dispatch_pixel<T, 2, P1TRI2_2D>(a, s);
+  if (d.elem == Q1_2D) return d.c == 1 ? dispatch_pixel<T, 1, Q1_2D>(a, s) : dispatch_pixel<T, 2, Q1_2D>(a, s);
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_stiffness<double>(const StencilArgs&, cudaStream_t);
+template cudaError_t launch_stiffness<float>(const StencilArgs&, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------------
+// volume average of flux / stress: <sigma> = (1/|Y|) sum_e V_e C_e (e + mean strain of element e)
+// ------------------------------------------------------------------------------------------------
+namespace {
+constexpr int MF_T = 256;
+
+__device__ __forceinline__ void grad_to_flux_vec(int dim, int c, const double (&G)[3][3], double (&eps)[6]) {
+  // G[i][j]: derivative i of component j.  Scalar: eps = grad; elastic: Mandel strain
+  if (c == 1) {
+    for (int i = 0; i < dim; ++i) eps[i] = G[i][0];
+    return;
+  }
+  const double r2 = 0.70710678118654752440;  // 1 / sqrt(2)
+  if (dim == 2) {
+    eps[0] = G[0][0];
+    eps[1] = G[1][1];
+    eps[2] = r2 * (G[0][1] + G[1][0]);
+  } else {
+    eps[0] = G[0][0];
+    eps[1] = G[1][1];
+    eps[2] = G[2][2];
+    eps[3] = r2 * (G[1][2] + G[2][1]);
+    eps[4] = r2 * (G[0][2] + G[2][0]);
+    eps[5] = r2 * (G[0][1] + G[1][0]);
+  }
+}
+
+__global__ void __launch_bounds__(MF_T) mean_flux_kernel(MeanFluxArgs a) {
+  const Dims d = a.d;
+  const int load = blockIdx.y;
+  const double* u = a.u ? a.u + (long long)load * a.load_stride : nullptr;
+  const double* e = a.loads + load * a.m;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const double vol = a.h[0] * a.h[1] * (d.dim == 3 ? a.h[2] : 1.0);
+  for (long long v = blockIdx.x * (long long)MF_T + threadIdx.x; v < d.N; v += (long long)gridDim.x * MF_T) {
+    const int i = (int)(v % d.nx);
+    const int j = (int)((v / d.nx) % d.ny);
+    const int k = (int)(v / ((long long)d.nx * d.ny));
+    // element-mean gradient G[i][j] (derivative i of component j) from the corner values
+    double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (u) {
+      const int ncorner = d.dim == 3 ? 8 : 4;
+      for (int comp = 0; comp < d.c; ++comp) {
+        double uc[8];
+        for (int cn = 0; cn < ncorner; ++cn) {
+          const int ii = (i + (cn & 1)) % d.nx, jj = (j + ((cn >> 1) & 1)) % d.ny;
+          const int kk = d.dim == 3 ? (k + (cn >> 2)) % d.nz : 0;
+          uc[cn] = u[(long long)comp * d.N + ((long long)kk * d.ny + jj) * d.nx + ii];
+        }
+        if (d.dim == 3) {
+          // mean of d/dxi over the voxel: (1/4) sum over the 4 x-edges, divided by h
+          G[0][comp] = ((uc[1] - uc[0]) + (uc[3] - uc[2]) + (uc[5] - uc[4]) + (uc[7] - uc[6])) / (4.0 * a.h[0]);
+          G[1][comp] = ((uc[2] - uc[0]) + (uc[3] - uc[1]) + (uc[6] - uc[4]) + (uc[7] - uc[5])) / (4.0 * a.h[1]);
+          G[2][comp] = ((uc[4] - uc[0]) + (uc[5] - uc[1]) + (uc[6] - uc[2]) + (uc[7] - uc[3])) / (4.0 * a.h[2]);
+        } else if (d.elem == Q1_2D) {
+          G[0][comp] = ((uc[1] - uc[0]) + (uc[3] - uc[2])) / (2.0 * a.h[0]);
+          G[1][comp] = ((uc[2] - uc[0]) + (uc[3] - uc[1])) / (2.0 * a.h[1]);
+        } else {
+          // mean of the two triangles: A: (u1 - u0, u3 - u1), B: (u3 - u2, u2 - u0)
+          G[0][comp] = 0.5 * ((uc[1] - uc[0]) + (uc[3] - uc[2])) / a.h[0];
+          G[1][comp] = 0.5 * ((uc[3] - uc[1]) + (uc[2] - uc[0])) / a.h[1];
+        }
+      }
+    }
+    double eps[6] = {0, 0, 0, 0, 0, 0};
+    grad_to_flux_vec(d.dim, d.c, G, eps);
+    const int ph = a.ids ? a.ids[v] : 0;
+    const double* C = a.moduli + (long long)ph * a.m * a.m;
+    for (int r = 0; r < a.m; ++r) {
+      double s = 0.0;
+      for (int q = 0; q < a.m; ++q) s += C[r * a.m + q] * (e[q] + eps[q]);
+      acc[r] += vol * s;
+    }
+  }
+  __shared__ double sh[32];
+  for (int r = 0; r < a.m; ++r) {
+    const double t = block_sum(acc[r], sh);
+    if (threadIdx.x == 0) a.partial[((long long)load * gridDim.x + blockIdx.x) * a.m + r] = t;
+  }
+}
+
+__global__ void phase_hist_kernel(const uint8_t* ids, long long N, unsigned long long* hist) {
+  __shared__ unsigned int h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N; v += (long long)gridDim.x * blockDim.x)
+    atomicAdd(&h[ids[v]], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+}  // namespace
+
+cudaError_t launch_mean_flux(const MeanFluxArgs& a, int* blocks_out, cudaStream_t s) {
+  const int blocks = (int)std::min<long long>(4 * 152, (a.d.N + MF_T - 1) / MF_T);
+  *blocks_out = blocks;
+  dim3 grid(blocks, a.n_loads);
+  mean_flux_kernel<<<grid, MF_T, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_histogram(const uint8_t* ids, long long N, unsigned long long* hist, cudaStream_t s) {
+  const int blocks = (int)std::min<long long>(2 * 152, (N + 255) / 256);
+  phase_hist_kernel<<<blocks, 256, 0, s>>>(ids, N, hist);
+  return cudaGetLastError();
+}
+
+}  // namespace fehom

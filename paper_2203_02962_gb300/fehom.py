@@ -1,0 +1,224 @@
+"""ctypes binding of libfehom.so (include/fehom.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module passes pointers, sizes and
+the CUDA stream, and uses torch tensors for device memory.  There is no CPU fallback: loading
+fails loudly when the library is missing.
+
+    s = Solver("hex8_3d", "elastic", (128, 128, 128), ids, moduli)
+    s.precond_build()
+    out = s.solve(loads, tol=1e-6)        # out["C_eff"], out["mean_flux"], out["fields"], out["info"]
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfehom.so")
+
+ELEM = {"p1tri2_2d": 1, "hex8_3d": 2, "q1_2d": 3}
+PHYSICS = {"scalar": 1, "elastic": 2}
+PRECISION = {"fp64": 0, "mixed": 1}
+STATUS = {0: "FEHOM_OK", 1: "FEHOM_E_INVALID", 2: "FEHOM_E_UNSUPPORTED_SIZE", 3: "FEHOM_E_OOM",
+          4: "FEHOM_E_CUDA", 5: "FEHOM_E_NOT_CONVERGED", 6: "FEHOM_E_BREAKDOWN", 7: "FEHOM_E_STATE"}
+
+# every entry point declared in include/fehom.h
+EXPORTS = ("fehom_default_options", "fehom_setup", "fehom_precond_build", "fehom_solve", "fehom_destroy",
+           "fehom_last_error", "fehom_query", "fehom_apply_stiffness", "fehom_rhs", "fehom_apply_precond",
+           "fehom_get_symbol_inverse", "fehom_mean_flux")
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("max_iter", C.c_int), ("inner_tol", C.c_double),
+                ("stream", C.c_void_p), ("use_graph", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("converged", C.c_int),
+                ("rel_residual_M", C.c_double), ("rel_residual_2", C.c_double), ("solve_ms", C.c_double)]
+
+
+class FehomError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfehom.so (raises when it has not been built) and declare the signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfehom.so not found at {path}; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    vp, i, d, i64p = C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_int64)
+    dp = C.POINTER(C.c_double)
+    lib.fehom_default_options.argtypes = [C.POINTER(Options)]
+    lib.fehom_default_options.restype = None
+    lib.fehom_setup.argtypes = [C.POINTER(vp), i, i, i64p, dp, vp, i, i, dp, dp, C.POINTER(Options)]
+    lib.fehom_setup.restype = i
+    lib.fehom_precond_build.argtypes = [vp]
+    lib.fehom_precond_build.restype = i
+    lib.fehom_solve.argtypes = [vp, i, dp, d, vp, vp, i, dp, dp, C.POINTER(SolveInfo)]
+    lib.fehom_solve.restype = i
+    lib.fehom_destroy.argtypes = [vp]
+    lib.fehom_destroy.restype = None
+    lib.fehom_last_error.argtypes = [vp]
+    lib.fehom_last_error.restype = C.c_char_p
+    lib.fehom_query.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), i64p, i64p]
+    lib.fehom_query.restype = i
+    lib.fehom_apply_stiffness.argtypes = [vp, vp, vp, i]
+    lib.fehom_apply_stiffness.restype = i
+    lib.fehom_rhs.argtypes = [vp, dp, vp]
+    lib.fehom_rhs.restype = i
+    lib.fehom_apply_precond.argtypes = [vp, vp, vp, i]
+    lib.fehom_apply_precond.restype = i
+    lib.fehom_get_symbol_inverse.argtypes = [vp, dp]
+    lib.fehom_get_symbol_inverse.restype = i
+    lib.fehom_mean_flux.argtypes = [vp, dp, vp, dp]
+    lib.fehom_mean_flux.restype = i
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("fehom needs a CUDA GPU")
+    return torch
+
+
+class Solver:
+    """One periodic cell: fehom_setup on construction, fehom_destroy on close()."""
+
+    def __init__(self, elem, physics, n, ids, moduli, ref_material=None, precision="fp64", max_iter=10000,
+                 inner_tol=1e-3, cell=None, use_graph=True, stream=None):
+        torch = _torch()
+        self.lib = load_library()
+        self.elem, self.physics = elem, physics
+        n = tuple(int(v) for v in n) + (1,) * (3 - len(n))
+        self.n = n
+        self.N = n[0] * n[1] * n[2]
+        opt = Options()
+        self.lib.fehom_default_options(C.byref(opt))
+        opt.precision = PRECISION[precision]
+        opt.max_iter = int(max_iter)
+        opt.inner_tol = float(inner_tol)
+        opt.use_graph = 1 if use_graph else 0
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        opt.stream = C.c_void_p(self.stream.cuda_stream)
+        self._opt = opt
+        moduli = np.ascontiguousarray(np.asarray(moduli, dtype=np.float64))
+        nn = (C.c_int64 * 3)(*n)
+        cellp = _dptr(np.ascontiguousarray(np.asarray(cell, np.float64))) if cell is not None else None
+        refp = None
+        if ref_material is not None:
+            self._ref = np.ascontiguousarray(np.asarray(ref_material, np.float64))
+            refp = _dptr(self._ref)
+        if isinstance(ids, np.ndarray):
+            ids_h = np.ascontiguousarray(ids.astype(np.uint8).ravel())
+            ids_ptr, on_dev = ids_h.ctypes.data, 0
+        else:  # torch uint8 tensor on the GPU
+            ids_t = ids.contiguous().view(-1)
+            ids_ptr, on_dev = ids_t.data_ptr(), 1 if ids_t.is_cuda else 0
+            if not ids_t.is_cuda:
+                ids_h = ids_t.numpy()
+        ctx = C.c_void_p()
+        st = self.lib.fehom_setup(C.byref(ctx), ELEM[elem], PHYSICS[physics], nn, cellp, C.c_void_p(ids_ptr), on_dev,
+                                  int(moduli.shape[0]), _dptr(moduli), refp, C.byref(opt))
+        if st != 0:
+            raise FehomError(st, self.lib.fehom_last_error(None).decode())
+        self.ctx = ctx
+        c, m, Nq, nxh = C.c_int(), C.c_int(), C.c_int64(), C.c_int64()
+        self.lib.fehom_query(ctx, C.byref(c), C.byref(m), C.byref(Nq), C.byref(nxh))
+        self.c, self.m, self.nxh = c.value, m.value, nxh.value
+        self.Nh = self.nxh * n[1] * n[2]
+
+    # -- lifetime -------------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.fehom_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            raise FehomError(st, self.lib.fehom_last_error(self.ctx).decode())
+
+    # -- the three calls ------------------------------------------------------------------------
+    def precond_build(self):
+        self._check(self.lib.fehom_precond_build(self.ctx))
+
+    def solve(self, loads, tol, x0=None, fields="device", raise_on_failure=True):
+        """Solve for every row of ``loads``; returns mean fluxes, C_eff, fields and per-load info."""
+        torch = _torch()
+        loads = np.ascontiguousarray(np.atleast_2d(np.asarray(loads, np.float64)))
+        L = loads.shape[0]
+        flux = np.zeros((L, self.m))
+        ceff = np.full((self.m, self.m), np.nan)
+        info = (SolveInfo * L)()
+        out = None
+        out_ptr, on_dev = None, 1
+        if fields == "device":
+            out = torch.empty((L, self.c, self.N), dtype=torch.float64, device="cuda")
+            out_ptr = C.c_void_p(out.data_ptr())
+        elif fields == "host":
+            out = torch.empty((L, self.c, self.N), dtype=torch.float64).pin_memory()
+            out_ptr, on_dev = C.c_void_p(out.data_ptr()), 0
+        x0p = C.c_void_p(x0.data_ptr()) if x0 is not None else None
+        st = self.lib.fehom_solve(self.ctx, L, _dptr(loads), float(tol), x0p, out_ptr, on_dev, _dptr(flux), _dptr(ceff),
+                                  info)
+        if st != 0 and raise_on_failure:
+            self._check(st)
+        infos = [{k: getattr(info[l], k) for k, _ in SolveInfo._fields_} for l in range(L)]
+        return dict(status=st, mean_flux=flux, C_eff=ceff if L == self.m else None, fields=out, info=infos)
+
+    # -- operator-level entry points ------------------------------------------------------------
+    def apply_stiffness(self, x, precision="fp64"):
+        torch = _torch()
+        y = torch.empty_like(x)
+        self._check(self.lib.fehom_apply_stiffness(self.ctx, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                                   PRECISION[precision]))
+        return y
+
+    def rhs(self, e):
+        torch = _torch()
+        e = np.ascontiguousarray(np.asarray(e, np.float64))
+        b = torch.empty((self.c * self.N,), dtype=torch.float64, device="cuda")
+        self._check(self.lib.fehom_rhs(self.ctx, _dptr(e), C.c_void_p(b.data_ptr())))
+        return b
+
+    def apply_precond(self, r, precision="fp64"):
+        torch = _torch()
+        z = torch.empty_like(r)
+        self._check(self.lib.fehom_apply_precond(self.ctx, C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr()),
+                                                 PRECISION[precision]))
+        return z
+
+    def symbol_inverse(self):
+        ne = self.c * (self.c + 1) // 2
+        out = np.zeros(ne * self.Nh)
+        self._check(self.lib.fehom_get_symbol_inverse(self.ctx, _dptr(out)))
+        return out.reshape(ne, self.n[2], self.n[1], self.nxh)
+
+    def mean_flux(self, e, u):
+        e = np.ascontiguousarray(np.asarray(e, np.float64))
+        out = np.zeros(self.m)
+        self._check(self.lib.fehom_mean_flux(self.ctx, _dptr(e), C.c_void_p(u.data_ptr()), _dptr(out)))
+        return out

@@ -1,0 +1,338 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 CPU oracle.
+
+Operator level: stiffness apply (S1/S3), right-hand side (S2), Algorithm 2 symbol (S4), the FFT
+preconditioner (S5-S7), volume averages (S9), on grids that span several tiles with ragged tails.
+Solve level (S8 + everything): C_eff and fields against the oracle's direct solve, iteration counts
+against the oracle's PCG, batched vs one-by-one loads, mixed vs FP64.  Error paths return status
+codes.  Tolerances: FP64 operators 1e-12 relative to the largest entry; FP32 operators 2e-5;
+solves at tol 1e-12: C_eff 1e-10 relative, fields 1e-9 relative max-norm.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import fem, solvers  # noqa: E402
+from paper_2203_02962_gb300 import inputs as I  # noqa: E402
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _fehom():
+    from paper_2203_02962_gb300 import fehom
+    return fehom
+
+
+def _rand_spd(m, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, m))
+    return scale * (A @ A.T + m * np.eye(m))
+
+
+def _solver(elem, physics, shape, ids, moduli, **kw):
+    return _fehom().Solver(elem, physics, tuple(shape[::-1]), ids, moduli, **kw)
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+OPERATOR_CASES = [
+    # elem, physics, shape (z, y, x) or (y, x), materials, cell
+    ("hex8_3d", "elastic", (12, 6, 48), "aniso", None),
+    ("hex8_3d", "elastic", (12, 12, 48), "iso", (4.0, 1.0, 1.0)),     # cubic voxels -> isotropic fast path
+    ("hex8_3d", "elastic", (24, 24, 24), "iso", None),
+    ("hex8_3d", "scalar", (6, 12, 48), "aniso", None),
+    ("hex8_3d", "scalar", (8, 8, 8), "iso", None),
+    ("p1tri2_2d", "scalar", (24, 48), "aniso", None),
+    ("p1tri2_2d", "elastic", (12, 96), "aniso", None),
+    ("q1_2d", "scalar", (16, 48), "iso", None),
+    ("q1_2d", "elastic", (6, 64), "aniso", None),
+]
+
+
+def _materials(physics, dim, kind, seed=0):
+    m = dim if physics == "scalar" else dim * (dim + 1) // 2
+    if kind == "aniso":
+        return np.stack([_rand_spd(m, seed + p, 10.0 ** p) for p in range(3)])
+    if physics == "scalar":
+        return np.stack([I.isotropic_conductivity(k, dim) for k in (1.0, 30.0, 1000.0)])
+    return np.stack([I.isotropic_elastic_mandel(E, nu, dim) for E, nu in ((1.0, 0.3), (100.0, 0.2), (7.0, 0.45))])
+
+
+@pytest.mark.parametrize("elem,physics,shape,kind,cell", OPERATOR_CASES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_stiffness_apply(elem, physics, shape, kind, cell, precision):
+    torch = _torch()
+    g = fem.Grid(shape, elem, physics)
+    if cell is not None:  # the oracle's grid is the unit cell: scale h by hand
+        g.h = np.array(cell, float)[: g.dim] / np.array(g.n_xyz, float)
+        g.vp = float(np.prod(g.h))
+    rng = np.random.default_rng(1)
+    ids = rng.integers(0, 3, size=shape).astype(np.uint8)
+    mod = _materials(physics, g.dim, kind)
+    K = fem.assemble_K(g, ids.ravel(), mod)
+    x = rng.standard_normal(g.c * g.N)
+    y_ref = K @ x
+    s = _solver(elem, physics, shape, ids, mod, cell=cell)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    y = s.apply_stiffness(torch.tensor(x, dtype=dt, device="cuda"), precision).double().cpu().numpy()
+    tol = 1e-12 if precision == "fp64" else 2e-5
+    scale = np.abs(K).max() * np.abs(x).max() if precision == "mixed" else np.abs(y_ref).max()
+    assert np.abs(y - y_ref).max() <= tol * scale
+    s.close()
+
+
+@pytest.mark.parametrize("elem,physics,shape,kind,cell", OPERATOR_CASES[::2])
+def test_rhs_and_mean_flux(elem, physics, shape, kind, cell):
+    torch = _torch()
+    g = fem.Grid(shape, elem, physics)
+    if cell is not None:
+        g.h = np.array(cell, float)[: g.dim] / np.array(g.n_xyz, float)
+        g.vp = float(np.prod(g.h))
+    rng = np.random.default_rng(2)
+    ids = rng.integers(0, 3, size=shape).astype(np.uint8)
+    mod = _materials(physics, g.dim, kind)
+    s = _solver(elem, physics, shape, ids, mod, cell=cell)
+    e = rng.standard_normal(g.m)
+    b = s.rhs(e).cpu().numpy()
+    b_ref = fem.assemble_rhs(g, ids.ravel(), mod, e)
+    assert _rel(b, b_ref) < 1e-12
+    u = rng.standard_normal(g.c * g.N)
+    fl = s.mean_flux(e, torch.tensor(u, device="cuda"))
+    fl_ref = fem.mean_flux(g, ids.ravel(), mod, e, u) / (g.vp * g.N)
+    assert _rel(fl, fl_ref) < 1e-12
+    s.close()
+
+
+PRECOND_CASES = [
+    ("hex8_3d", "elastic", (6, 12, 24)),
+    ("hex8_3d", "scalar", (12, 6, 48)),
+    ("hex8_3d", "elastic", (16, 8, 32)),
+    ("p1tri2_2d", "scalar", (24, 48)),
+    ("q1_2d", "elastic", (3, 8)),
+    ("p1tri2_2d", "elastic", (96, 12)),
+]
+
+
+@pytest.mark.parametrize("elem,physics,shape", PRECOND_CASES)
+def test_symbol_and_preconditioner(elem, physics, shape):
+    """Algorithm 2 table (half spectrum, packed, times 1/N) and z = K_ref^+ r against the oracle."""
+    torch = _torch()
+    g = fem.Grid(shape, elem, physics)
+    rng = np.random.default_rng(3)
+    ids = rng.integers(0, 2, size=shape).astype(np.uint8)
+    mod = _materials(physics, g.dim, "aniso")[:2]
+    C_ref = fem.mean_material(g, ids.ravel(), mod)
+    s = _solver(elem, physics, shape, ids, mod)
+    s.precond_build()
+    Kinv = solvers.kref_pinv_symbol(solvers.kref_symbol(g, C_ref))   # (c, c, *shape) complex
+    assert np.abs(Kinv.imag).max() < 1e-12 * np.abs(Kinv).max()
+    tab = s.symbol_inverse()                                          # (ne, nz, ny, nxh)
+    c = g.c
+    pairs = {1: [(0, 0)], 2: [(0, 0), (1, 1), (0, 1)], 3: [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]}[c]
+    nxh = g.n_xyz[0] // 2 + 1
+    for e_, (i, j) in enumerate(pairs):
+        ref = Kinv[i, j].real / g.N
+        ref = ref.reshape((1,) * (3 - g.dim) + ref.shape)[..., :nxh]
+        assert _rel(tab[e_], ref) < 1e-12
+    r = rng.standard_normal(g.c * g.N)
+    z_ref = solvers.apply_precond(g, Kinv, r)
+    z = s.apply_precond(torch.tensor(r, device="cuda")).cpu().numpy()
+    assert _rel(z, z_ref) < 1e-12
+    z32 = s.apply_precond(torch.tensor(r, dtype=torch.float32, device="cuda"), "mixed").double().cpu().numpy()
+    assert _rel(z32, z_ref) < 2e-5
+    s.close()
+
+
+def _small_elastic(n=16, seed=3):
+    ids = I.spheres3d(n, count=8, rmin=2.0, rmax=3.5, seed=seed)
+    mod = np.stack([I.isotropic_elastic_mandel(1.0, 0.3), I.isotropic_elastic_mandel(100.0, 0.2)])
+    return ids, mod
+
+
+def test_solve_circle2d_matches_oracle():
+    w = I.workload_circle2d_32()
+    g = fem.Grid((32, 32), "p1tri2_2d", "scalar")
+    ref = solvers.homogenise(g, w["ids"], w["moduli"], w["loads"], method="sparse")
+    s = _solver("p1tri2_2d", "scalar", (32, 32), w["ids"], w["moduli"])
+    s.precond_build()
+    out = s.solve(w["loads"], tol=1e-12)
+    assert _rel(out["C_eff"], ref["C_eff"]) < 1e-10
+    assert _rel(out["fields"].cpu().numpy(), ref["fields"]) < 1e-9
+    assert _rel(out["mean_flux"], ref["mean_flux"]) < 1e-10
+    assert all(i["converged"] for i in out["info"])
+    s.close()
+
+
+@pytest.mark.parametrize("physics", ["elastic", "scalar"])
+def test_solve_3d_matches_oracle(physics):
+    n = 16
+    if physics == "elastic":
+        ids, mod = _small_elastic(n)
+    else:
+        ids = I.grf_threshold((n, n, n), ell=3.0, seed=4)
+        mod = np.stack([I.isotropic_conductivity(1.0, 3), I.isotropic_conductivity(1000.0, 3)])
+    g = fem.Grid((n, n, n), "hex8_3d", physics)
+    loads = np.eye(g.m)
+    ref = solvers.homogenise(g, ids, mod, loads, method="sparse")
+    s = _solver("hex8_3d", physics, (n, n, n), ids, mod)
+    s.precond_build()
+    out = s.solve(loads, tol=1e-12)
+    assert _rel(out["C_eff"], ref["C_eff"]) < 1e-10
+    assert _rel(out["fields"].cpu().numpy(), ref["fields"]) < 1e-9
+    s.close()
+
+
+def test_iteration_counts_match_oracle_pcg():
+    """Same algorithm, same stopping test: the GPU and oracle PCG stop at the same iteration (+-1)."""
+    n = 16
+    ids, mod = _small_elastic(n, seed=5)
+    g = fem.Grid((n, n, n), "hex8_3d", "elastic")
+    loads = np.eye(6)
+    ref = solvers.homogenise(g, ids, mod, loads, method="pcg", tol=1e-6)
+    s = _solver("hex8_3d", "elastic", (n, n, n), ids, mod)
+    s.precond_build()
+    out = s.solve(loads, tol=1e-6)
+    its = [i["iterations"] for i in out["info"]]
+    assert all(abs(a - b) <= 1 for a, b in zip(its, ref["iters"])), (its, ref["iters"])
+    s.close()
+
+
+def test_batched_loads_equal_one_by_one():
+    n = 16
+    ids, mod = _small_elastic(n, seed=6)
+    s = _solver("hex8_3d", "elastic", (n, n, n), ids, mod)
+    s.precond_build()
+    loads = np.eye(6) + 0.1
+    batch = s.solve(loads, tol=1e-8)
+    for l in range(6):
+        one = s.solve(loads[l:l + 1], tol=1e-8)
+        assert one["info"][0]["iterations"] == batch["info"][l]["iterations"]
+        assert _rel(one["fields"][0].cpu().numpy(), batch["fields"][l].cpu().numpy()) < 1e-13
+    s.close()
+
+
+def test_mixed_precision_matches_fp64():
+    n = 16
+    ids, mod = _small_elastic(n, seed=7)
+    s64 = _solver("hex8_3d", "elastic", (n, n, n), ids, mod)
+    s64.precond_build()
+    o64 = s64.solve(np.eye(6), tol=1e-10)
+    s32 = _solver("hex8_3d", "elastic", (n, n, n), ids, mod, precision="mixed")
+    s32.precond_build()
+    o32 = s32.solve(np.eye(6), tol=1e-10)
+    assert _rel(o32["C_eff"], o64["C_eff"]) < 1e-7
+    for inf in o32["info"]:
+        assert inf["converged"] and inf["refinements"] >= 1
+        assert inf["rel_residual_M"] <= 1e-10
+    s64.close()
+    s32.close()
+
+
+def test_graph_and_plain_launches_agree():
+    n = 16
+    ids, mod = _small_elastic(n, seed=8)
+    a = _solver("hex8_3d", "elastic", (n, n, n), ids, mod, use_graph=True)
+    b = _solver("hex8_3d", "elastic", (n, n, n), ids, mod, use_graph=False)
+    a.precond_build()
+    b.precond_build()
+    oa, ob = a.solve(np.eye(6), tol=1e-8), b.solve(np.eye(6), tol=1e-8)
+    assert [i["iterations"] for i in oa["info"]] == [i["iterations"] for i in ob["info"]]
+    assert _rel(oa["fields"].cpu().numpy(), ob["fields"].cpu().numpy()) == 0.0
+    a.close()
+    b.close()
+
+
+def test_warm_start_with_solution_converges_immediately():
+    torch = _torch()
+    n = 16
+    ids, mod = _small_elastic(n, seed=9)
+    s = _solver("hex8_3d", "elastic", (n, n, n), ids, mod)
+    s.precond_build()
+    o = s.solve(np.eye(6), tol=1e-10)
+    w = s.solve(np.eye(6), tol=1e-8, x0=o["fields"].contiguous())
+    assert all(i["iterations"] <= 1 for i in w["info"])
+    assert _rel(w["C_eff"], o["C_eff"]) < 1e-9
+    s.close()
+
+
+def test_homogeneous_and_zero_load():
+    C = _rand_spd(6, 12)
+    ids = np.zeros((8, 8, 8), np.uint8)
+    s = _solver("hex8_3d", "elastic", (8, 8, 8), ids, C[None])
+    s.precond_build()
+    out = s.solve(np.eye(6), tol=1e-10)
+    assert _rel(out["C_eff"], C) < 1e-13
+    assert np.abs(out["fields"].cpu().numpy()).max() < 1e-13
+    z = s.solve(np.zeros((1, 6)), tol=1e-6)
+    assert z["info"][0]["iterations"] == 0 and z["info"][0]["converged"]
+    s.close()
+
+
+def test_error_paths_return_status():
+    fehom = _fehom()
+    ids = np.zeros((8, 8, 8), np.uint8)
+    mod = I.isotropic_elastic_mandel(1.0, 0.3)[None]
+    with pytest.raises(fehom.FehomError) as e:
+        _solver("hex8_3d", "elastic", (8, 8, 10), np.zeros((8, 8, 10), np.uint8), mod)
+    assert e.value.status == 2
+    with pytest.raises(fehom.FehomError) as e:
+        _solver("hex8_3d", "elastic", (8, 8, 8), ids + 1, mod)            # id 1 >= n_phases
+    assert e.value.status == 1
+    bad = mod.copy()
+    bad[0, 0, 0] = -5.0
+    with pytest.raises(fehom.FehomError) as e:
+        _solver("hex8_3d", "elastic", (8, 8, 8), ids, bad)
+    assert e.value.status == 1
+    s = _solver("hex8_3d", "elastic", (8, 8, 8), ids, mod)
+    with pytest.raises(fehom.FehomError) as e:
+        s.solve(np.eye(6), tol=1e-6)                                      # before precond_build
+    assert e.value.status == 7
+    s.close()
+    ids2, mod2 = _small_elastic(16, seed=10)
+    s = _solver("hex8_3d", "elastic", (16, 16, 16), ids2, mod2, max_iter=2)
+    s.precond_build()
+    out = s.solve(np.eye(6), tol=1e-10, raise_on_failure=False)
+    assert out["status"] == 5
+    assert all(i["iterations"] == 2 and not i["converged"] for i in out["info"])
+    assert np.isfinite(out["C_eff"]).all()
+    s.close()
+
+
+def test_full_size_bench_config_sampled():
+    """128^3 elastic spheres (the benchmark workload): sampled stiffness rows against the oracle's
+    element-by-element rows; the FP64 solve's outputs satisfy properties that hold at any size."""
+    torch = _torch()
+    w = I.workload_spheres_elastic(128, seed=0)
+    shape = (128, 128, 128)
+    g = fem.Grid(shape, "hex8_3d", "elastic")
+    s = _solver("hex8_3d", "elastic", shape, w["ids"], w["moduli"])
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(g.c * g.N)
+    y = s.apply_stiffness(torch.tensor(x, device="cuda")).cpu().numpy()
+    rows = rng.integers(0, g.c * g.N, 3000)
+    y_ref = fem.stiffness_rows(g, w["ids"].ravel(), w["moduli"], x, rows)
+    assert np.abs(y[rows] - y_ref).max() <= 1e-12 * np.abs(y_ref).max()
+    s.precond_build()
+    out = s.solve(w["loads"], tol=1e-6)
+    C = out["C_eff"]
+    assert all(i["converged"] for i in out["info"])
+    assert np.abs(C - C.T).max() <= 1e-4 * np.abs(C).max()
+    f = np.bincount(w["ids"].ravel(), minlength=2) / g.N
+    voigt = sum(fp * Cp for fp, Cp in zip(f, w["moduli"]))
+    reuss = np.linalg.inv(sum(fp * np.linalg.inv(Cp) for fp, Cp in zip(f, w["moduli"])))
+    sym = 0.5 * (C + C.T)
+    assert np.linalg.eigvalsh(voigt - sym).min() > 0 and np.linalg.eigvalsh(sym - reuss).min() > 0
+    # the oracle's volume average of the GPU fields reproduces the GPU's mean stress
+    u0 = out["fields"][0].reshape(-1).cpu().numpy()
+    fl_ref = fem.mean_flux(g, w["ids"].ravel(), w["moduli"], w["loads"][0], u0) / (g.vp * g.N)
+    assert _rel(out["mean_flux"][0], fl_ref) < 1e-12
+    # true residual from the oracle at sampled DOFs: |b - K u| small relative to |b|
+    b_rows = fem.assemble_rhs(g, w["ids"].ravel(), w["moduli"], w["loads"][0])
+    r_rows = b_rows[rows] - fem.stiffness_rows(g, w["ids"].ravel(), w["moduli"], u0, rows)
+    assert np.abs(r_rows).max() < 1e-3 * np.abs(b_rows).max()
+    s.close()
