@@ -602,7 +602,7 @@ __global__ void symbol_kernel(SymbolArgs a) {
 
 template <typename K>
 cudaError_t set_smem(K kern, size_t bytes) {
-  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes > 32 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return cudaSuccess;
 }
 

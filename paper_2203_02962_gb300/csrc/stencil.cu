@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
 
 template <typename K>
 cudaError_t set_smem(K kern, size_t bytes) {
-  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes > 32 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return cudaSuccess;
 }
 
