@@ -46,8 +46,6 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# FP64 FMA throughput from unit counts: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (max clock)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 class ClockSampler:
@@ -102,6 +100,27 @@ def workload():
     return inputs.workload_spheres_elastic(128, seed=0)
 
 
+# Algorithmic work per voxel and load of each PCG kernel class on the 128^3 elastic workload
+# (c = 3 DOF per voxel).  Bytes: fields read + written once (s bytes per scalar), half spectra
+# nxh / nx = 65/128 complex per real voxel per component, phase ids 1 byte.  FP64 operations: counted
+# from the kernels' arithmetic (one FP64 instruction = add, mul or fma), see the design doc section 6.
+def kernel_model(s):
+    c, hs = 3, 65.0 / 128.0
+    spec = c * hs * 2 * s              # one half-spectrum pass over the c components
+    sym = 6 * s * hs                   # packed 3x3 symmetric K_hat^+ per half-spectrum k
+    return {
+        "stiffness": {"bytes": 2 * c * s + 1, "fp64_ops": 250},
+        "fft_x_fwd": {"bytes": 3 * c * s + spec, "fp64_ops": 3 * 4.0 * 7 * 3.5 / 2 * 2},
+        "fft_y_fwd": {"bytes": 2 * spec, "fp64_ops": 3 * hs * 7 * 3.5},
+        "fft_last": {"bytes": 2 * spec + sym, "fp64_ops": 3 * hs * 2 * 7 * 3.5 + hs * 18},
+        "fft_y_inv": {"bytes": 2 * spec, "fp64_ops": 3 * hs * 7 * 3.5},
+        "fft_x_inv": {"bytes": spec + 4 * c * s, "fp64_ops": 3 * 4.0 * 7 * 3.5 / 2 * 2},
+    }
+
+
+FP64_INSTR_PEAK = 152 * 2 * 2.07e9     # FP64 instructions/s: 152 SMs x 2 FP64 lanes-per-clock x max clock
+
+
 def run_ours(args):
     import torch
     from paper_2203_02962_gb300 import fehom
@@ -114,10 +133,7 @@ def run_ours(args):
     c = 3
     loads = w["loads"]
     ids_dev = torch.tensor(w["ids"].ravel(), device=dev)
-    stream = torch.cuda.current_stream()
-
-    def make(precision):
-        return fehom.Solver("hex8_3d", "elastic", n, ids_dev, w["moduli"], precision=precision, stream=stream)
+    stream = torch.cuda.Stream(device=dev)   # the library launches on this stream; events are recorded on it
 
     def step(s):
         s.precond_build()
@@ -125,20 +141,26 @@ def run_ours(args):
 
     results = {}
     for prec in ("fp64", "mixed"):
-        s = make(prec)
+        s = fehom.Solver("hex8_3d", "elastic", n, ids_dev, w["moduli"], precision=prec, stream=stream,
+                         profile=True)
         for _ in range(args.warmup):
             step(s)
+        t_before = s.kernel_times(prec)
+        l_before = s.launch_count()
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        iters = []
         with ClockSampler(0) as clk:
             ev0.record(stream)
             outs = [step(s) for _ in range(args.steps)]
             ev1.record(stream)
             torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / args.steps
-        its = [sum(i["iterations"] for i in o["info"]) for o in outs]
-        results[prec] = dict(ms=ms, iters=its[-1], out=outs[-1], clocks=clk.summary(), solver=s)
+        t_after = s.kernel_times(prec)
+        kt = {k: (t_after[k][0] - t_before[k][0], t_after[k][1] - t_before[k][1]) for k in t_after}
+        load_iters = sum(sum(i["iterations"] for i in o["info"]) for o in outs)
+        results[prec] = dict(ms=ms, iters=load_iters / args.steps, out=outs[-1], clocks=clk.summary(), kt=kt,
+                             load_iters=load_iters, launches=s.launch_count() - l_before)
+        s.close()
 
     # e2e: host phase ids -> setup -> build -> solve -> fields back to pinned host memory
     ids_host = np.ascontiguousarray(w["ids"].ravel())
@@ -165,26 +187,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
 
-    # dominant kernel: the FP64 stiffness apply, timed with CUDA events on the solver's stream
-    s64 = results["fp64"]["solver"]
-    x = torch.randn(c * N, dtype=torch.float64, device=dev)
-    for _ in range(3):
-        s64.apply_stiffness(x)
-    reps = 20
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        s64.apply_stiffness(x)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    k_ms = e0.elapsed_time(e1) / reps
-    flop_per_voxel = ISO_HEX8_ELASTIC_FLOPS
-    achieved_tf = flop_per_voxel * N / (k_ms * 1e-3) / 1e12
-
     r64, rmx = results["fp64"], results["mixed"]
-    dof_iter_64 = c * N * r64["iters"]
-    value = dof_iter_64 / (r64["ms"] * 1e-3)
+    value = c * N * r64["iters"] / (r64["ms"] * 1e-3)
     hbm, hbm_src = peaks()
+    # dominant kernel of the FP64 step, from the CUDA events recorded around every launch
+    dom = max(r64["kt"], key=lambda k: r64["kt"][k][0])
+    dom_ms, dom_launches = r64["kt"][dom]
+    model = kernel_model(8)[dom]
+    units = N * r64["load_iters"]                       # voxel-loads processed by the timed launches
+    avg_ms = dom_ms / max(dom_launches, 1)
+    units_per_launch = units / max(dom_launches, 1)
+    achieved_ops = model["fp64_ops"] * units_per_launch / (avg_ms * 1e-3)
+    achieved_gbs = model["bytes"] * units_per_launch / (avg_ms * 1e-3) / 1e9
+    share = {k: r64["kt"][k][0] / max(sum(v[0] for v in r64["kt"].values()), 1e-30) for k in r64["kt"]}
     out = {
         "metric": METRIC,
         "value": value,
@@ -199,38 +214,35 @@ def run_ours(args):
         "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": "128^3 hex8 elasticity, 60 periodic spheres E100/nu0.2 in E1/nu0.3, 6 unit Mandel "
-                               "strains batched, C_ref = volume mean, FP64 PCG to 1e-6",
+                               "strains batched, C_ref = volume mean, FP64 PCG to 1e-6 (Algorithm 2 + solve + C_eff)",
                    "dof": c * N, "loads": len(loads), "tol": w["tol"],
-                   "l2": "inputs > L2 (50 MB per field, 1.5 GB working set); no flush"},
+                   "l2": "inputs > L2 (50 MB per field, ~2 GB working set); no flush"},
         "time_to_tol_s": r64["ms"] * 1e-3,
-        "pcg_iterations": r64["iters"],
+        "pcg_iterations_per_load": [i["iterations"] for i in r64["out"]["info"]],
         "C_eff_diag": [float(v) for v in np.diag(r64["out"]["C_eff"])],
         "e2e": {"value": c * N * (e_iters[-1]) / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(N + w["moduli"].nbytes + loads.nbytes),
                 "d2h_bytes_per_step": int(len(loads) * c * N * 8 + 6 * 6 * 8 + len(loads) * 6 * 8),
                 "ms_per_step": e2e_ms},
         "mixed": {"value": c * N * rmx["iters"] / (rmx["ms"] * 1e-3), "ms_per_step": rmx["ms"],
-                  "time_to_tol_s": rmx["ms"] * 1e-3, "inner_iterations": rmx["iters"],
+                  "time_to_tol_s": rmx["ms"] * 1e-3, "inner_iterations_per_load": [i["iterations"] for i in rmx["out"]["info"]],
+                  "refinements_per_load": [i["refinements"] for i in rmx["out"]["info"]],
                   "speedup_vs_fp64": r64["ms"] / rmx["ms"],
                   "C_eff_rel_diff_vs_fp64": float(np.abs(rmx["out"]["C_eff"] - r64["out"]["C_eff"]).max()
                                                   / np.abs(r64["out"]["C_eff"]).max()),
-                  "clocks": rmx["clocks"]},
-        "roofline": {"bound": "alu", "kernel": "hex8_apply_kernel<double> (FP64 stiffness apply)",
-                     "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                     "hbm_frac": (2 * c * N * 8 + N) / (k_ms * 1e-3) / 1e9 / hbm, "hbm_peak_gbs": hbm,
-                     "hbm_peak_source": hbm_src, "kernel_ms": k_ms},
+                  "kernel_ms": {k: v[0] for k, v in rmx["kt"].items()},
+                  "gpu_launches": rmx["launches"], "clocks": rmx["clocks"]},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_ops / 1e12, "peak": FP64_INSTR_PEAK / 1e12,
+                     "unit": "T FP64-instr/s", "frac": achieved_ops / FP64_INSTR_PEAK, "traffic": None,
+                     "peak_source": "152 SMs x 2 FP64 lanes/clk x 2.07 GHz (unit count x max clock)",
+                     "avg_launch_ms": avg_ms, "launches": dom_launches,
+                     "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm, "hbm_frac": achieved_gbs / hbm,
+                     "hbm_peak_source": hbm_src, "fp64_kernel_share": share},
         "clocks": r64["clocks"],
-        "gpu_launches": None,
+        "gpu_launches": r64["launches"],
     }
     out["cpu_baseline"] = cpu_baseline(short=True)
     print(json.dumps(out))
-
-
-# FP64 operations per voxel of the isotropic hex8 elasticity apply (modal formulation): counted from
-# the element code, FMA = 2 flop
-ISO_HEX8_ELASTIC_FLOPS = 420
 
 
 def cpu_baseline(short=False):

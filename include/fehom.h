@@ -72,7 +72,19 @@ typedef struct {
   double inner_tol;  /* mixed only: relative K_ref^-1-norm reduction per inner FP32 solve (default 1e-3) */
   void* stream;      /* cudaStream_t for every launch and copy; NULL = a blocking stream the context creates */
   int use_graph;     /* 1 (default): replay PCG iterations from a captured CUDA graph; 0: plain launches */
+  int profile;       /* 1: record CUDA events around every kernel of the PCG iterations (see fehom_kernel_times) */
 } fehom_options;
+
+/* Kernel classes of one PCG iteration, for fehom_kernel_times. */
+enum {
+  FEHOM_K_STIFFNESS = 0, /* K p and <p, K p> (Sec. 5.1) */
+  FEHOM_K_FFT_X_FWD = 1, /* r -= alpha K p, forward FFT along x */
+  FEHOM_K_FFT_Y_FWD = 2, /* forward FFT along y (3-D only) */
+  FEHOM_K_FFT_LAST = 3,  /* last axis: forward FFT, block solve (Sec. 5.3), <r, z>, inverse FFT */
+  FEHOM_K_FFT_Y_INV = 4, /* inverse FFT along y (3-D only) */
+  FEHOM_K_FFT_X_INV = 5, /* inverse FFT along x, x += alpha p, p = z + beta p */
+  FEHOM_K_COUNT = 6
+};
 
 typedef struct {
   int iterations;          /* PCG iterations (mixed: inner FP32 iterations summed over refinements) */
@@ -146,6 +158,16 @@ void fehom_destroy(fehom_ctx* ctx);
 /* Text of the context's last error ("" if none); owned by the context, valid until the next call.  With
  * ctx == NULL: the message of the last failed fehom_setup on the calling thread. */
 const char* fehom_last_error(const fehom_ctx* ctx);
+
+/* Device time spent in each kernel class of the PCG iterations since setup, recorded with CUDA
+ * events on the context's stream when opt.profile == 1 (iterations after a load has finished are
+ * not counted).  precision selects the FP64 kernels or the FP32 kernels of the mixed path.
+ * ms[FEHOM_K_COUNT]: total milliseconds; count[FEHOM_K_COUNT]: launches timed. */
+fehom_status fehom_kernel_times(const fehom_ctx* ctx, int precision, double* ms, int64_t* count);
+
+/* Number of kernel launches the context has issued since setup (kernels replayed from a CUDA graph
+ * are counted once per replay). */
+fehom_status fehom_launch_count(const fehom_ctx* ctx, int64_t* count);
 
 /* Grid facts of a context: c (DOF per node), m (flux components), N (nodes), nxh (n_x / 2 + 1). */
 fehom_status fehom_query(const fehom_ctx* ctx, int* c, int* m, int64_t* N, int64_t* nxh);

@@ -60,6 +60,14 @@ struct fehom_ctx {
   // captured iteration graphs
   cudaGraphExec_t graph_exec = nullptr;
   long long graph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int graph_launches = 0;      // kernels per graph replay
+  // launch accounting and optional per-kernel event timing
+  long long launches = 0;
+  bool counting = true;        // false while a graph is being captured
+  bool events_made = false;
+  cudaEvent_t ev[8][FEHOM_K_COUNT][2];
+  double kms[2][FEHOM_K_COUNT] = {{0}};
+  long long kcnt[2][FEHOM_K_COUNT] = {{0}};
   std::string err;
 };
 
@@ -68,7 +76,7 @@ namespace {
 thread_local std::string g_setup_error;  // message of the last failed fehom_setup on this thread
 
 constexpr int kRedBlocks = 1 << 16;
-constexpr int kChunk = 8;  // PCG iterations per graph replay / convergence poll
+constexpr int kChunk = 8;  // PCG iterations per graph replay / convergence poll (<= 8: event slots)
 
 #define CK(call)                                                                  \
   do {                                                                            \
@@ -83,6 +91,12 @@ constexpr int kChunk = 8;  // PCG iterations per graph replay / convergence poll
   do {                       \
     ctx->err = (msg);        \
     return (code);           \
+  } while (0)
+
+#define TRY(x)                          \
+  do {                                  \
+    fehom_status s_ = (x);              \
+    if (s_ != FEHOM_OK) return s_;      \
   } while (0)
 
 bool size_ok(long long n) {
@@ -316,6 +330,19 @@ fehom_status ensure_partial(fehom_ctx* ctx, size_t n) {
   return FEHOM_OK;
 }
 
+inline void count_launch(fehom_ctx* ctx, int n = 1) {
+  if (ctx->counting) ctx->launches += n;
+}
+
+// event record that also works inside stream capture (becomes a timing node of the graph)
+inline cudaError_t record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t err = cudaStreamIsCapturing(s, &cs);
+  if (err != cudaSuccess) return err;
+  if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  return cudaEventRecord(e, s);
+}
+
 // ------------------------------------------------------------------------------------------------
 // preconditioner passes
 // ------------------------------------------------------------------------------------------------
@@ -327,45 +354,85 @@ cudaError_t fft_forward(fehom_ctx* ctx, FftArgs f, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// ev: optional [FEHOM_K_COUNT][2] events recorded around each pass (PCG profiling)
 template <typename T>
 cudaError_t precond_passes(fehom_ctx* ctx, FftArgs f, int fwd_mode, int inv_mode, void* fwd_field,
-                           const void* fwd_ap, void* inv_f0, void* inv_f2, cudaStream_t s) {
+                           const void* fwd_ap, void* inv_f0, void* inv_f2, cudaStream_t s,
+                           cudaEvent_t (*ev)[2] = nullptr) {
   cudaError_t e;
+  auto timed = [&](int k, auto&& launch) -> cudaError_t {
+    cudaError_t r;
+    if (ev && (r = record(ev[k][0], s)) != cudaSuccess) return r;
+    if ((r = launch()) != cudaSuccess) return r;
+    count_launch(ctx);
+    if (ev && (r = record(ev[k][1], s)) != cudaSuccess) return r;
+    return cudaSuccess;
+  };
   f.mode = fwd_mode;
   f.f0 = fwd_field;
   f.f1 = fwd_ap;
-  if ((e = launch_fft_x_fwd<T>(f, s)) != cudaSuccess) return e;
-  if (ctx->d.dim == 3 && (e = launch_fft_y<T>(f, 0, s)) != cudaSuccess) return e;
-  if ((e = launch_fft_last_solve<T>(f, s)) != cudaSuccess) return e;
-  if (ctx->d.dim == 3 && (e = launch_fft_y<T>(f, 1, s)) != cudaSuccess) return e;
+  if ((e = timed(FEHOM_K_FFT_X_FWD, [&] { return launch_fft_x_fwd<T>(f, s); })) != cudaSuccess) return e;
+  if (ctx->d.dim == 3 && (e = timed(FEHOM_K_FFT_Y_FWD, [&] { return launch_fft_y<T>(f, 0, s); })) != cudaSuccess) return e;
+  if ((e = timed(FEHOM_K_FFT_LAST, [&] { return launch_fft_last_solve<T>(f, s); })) != cudaSuccess) return e;
+  if (ctx->d.dim == 3 && (e = timed(FEHOM_K_FFT_Y_INV, [&] { return launch_fft_y<T>(f, 1, s); })) != cudaSuccess) return e;
   f.mode = inv_mode;
   f.f0 = inv_f0;
   f.f2 = inv_f2;
-  return launch_fft_x_inv<T>(f, s);
+  return timed(FEHOM_K_FFT_X_INV, [&] { return launch_fft_x_inv<T>(f, s); });
 }
 
 // one PCG iteration for every active load
 template <typename T>
-cudaError_t pcg_iteration(fehom_ctx* ctx, int n_loads, T* x, T* r, T* p, T* ap, cudaStream_t s) {
+cudaError_t pcg_iteration(fehom_ctx* ctx, int n_loads, T* x, T* r, T* p, T* ap, cudaStream_t s,
+                          cudaEvent_t (*ev)[2] = nullptr) {
   const bool fp32 = sizeof(T) == 4;
   StencilArgs a = stencil_args(ctx, fp32, n_loads);
   a.x = p;
   a.y = ap;
   a.st = ctx->st;
-  cudaError_t e = launch_stiffness<T>(a, s);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (ev && (e = record(ev[FEHOM_K_STIFFNESS][0], s)) != cudaSuccess) return e;
+  if ((e = launch_stiffness<T>(a, s)) != cudaSuccess) return e;
+  count_launch(ctx);
+  if (ev && (e = record(ev[FEHOM_K_STIFFNESS][1], s)) != cudaSuccess) return e;
   FftArgs f;
   fill_dims_args(ctx, f, fp32, n_loads);
   f.st = ctx->st;
-  return precond_passes<T>(ctx, f, FX_PCG, FX_PCG, r, ap, x, p, s);
+  return precond_passes<T>(ctx, f, FX_PCG, FX_PCG, r, ap, x, p, s, ev);
+}
+
+fehom_status make_events(fehom_ctx* ctx) {
+  if (ctx->events_made) return FEHOM_OK;
+  for (int i = 0; i < kChunk; ++i)
+    for (int k = 0; k < FEHOM_K_COUNT; ++k)
+      for (int j = 0; j < 2; ++j) CK(cudaEventCreate(&ctx->ev[i][k][j]));
+  ctx->events_made = true;
+  return FEHOM_OK;
+}
+
+// accumulate the event times of the first `n_iter` iterations of the last chunk
+fehom_status harvest_events(fehom_ctx* ctx, int prec, int n_iter) {
+  const int nk = FEHOM_K_COUNT;
+  for (int i = 0; i < std::min(n_iter, kChunk); ++i)
+    for (int k = 0; k < nk; ++k) {
+      if (ctx->d.dim == 2 && (k == FEHOM_K_FFT_Y_FWD || k == FEHOM_K_FFT_Y_INV)) continue;
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, ctx->ev[i][k][0], ctx->ev[i][k][1]));
+      ctx->kms[prec][k] += ms;
+      ctx->kcnt[prec][k] += 1;
+    }
+  return FEHOM_OK;
 }
 
 template <typename T>
 fehom_status run_iterations(fehom_ctx* ctx, int n_loads, T* x, T* r, T* p, T* ap, int max_iter,
                             std::vector<PcgState>& hs) {
   cudaStream_t s = ctx->stream;
-  const long long key[8] = {1, (long long)n_loads, (long long)(size_t)x, (long long)(size_t)r, (long long)(size_t)p,
+  const long long key[8] = {ctx->opt.profile ? 2 : 1, (long long)n_loads, (long long)(size_t)x, (long long)(size_t)r, (long long)(size_t)p,
                             (long long)(size_t)ap, (long long)sizeof(T), (long long)(size_t)ctx->st};
+  const bool prof = ctx->opt.profile != 0;
+  if (prof) TRY(make_events(ctx));
+  const int prec = sizeof(T) == 4 ? 1 : 0;
   bool use_graph = ctx->opt.use_graph != 0;
   if (use_graph && std::memcmp(key, ctx->graph_key, sizeof(key)) != 0) {
     if (ctx->graph_exec) {
@@ -375,7 +442,11 @@ fehom_status run_iterations(fehom_ctx* ctx, int n_loads, T* x, T* r, T* p, T* ap
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < kChunk && e == cudaSuccess; ++i) e = pcg_iteration<T>(ctx, n_loads, x, r, p, ap, s);
+    const long long before = ctx->launches;
+    for (int i = 0; i < kChunk && e == cudaSuccess; ++i)
+      e = pcg_iteration<T>(ctx, n_loads, x, r, p, ap, s, prof ? ctx->ev[i] : nullptr);
+    ctx->graph_launches = (int)(ctx->launches - before);
+    ctx->launches = before;  // captured kernels are counted when the graph is replayed
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
     CK(e);
     CK(e2);
@@ -384,15 +455,24 @@ fehom_status run_iterations(fehom_ctx* ctx, int n_loads, T* x, T* r, T* p, T* ap
     std::memcpy(ctx->graph_key, key, sizeof(key));
   }
   hs.resize(n_loads);
+  std::vector<PcgState> prev(n_loads);
+  CK(cudaMemcpyAsync(prev.data(), ctx->st, sizeof(PcgState) * n_loads, cudaMemcpyDeviceToHost, s));
   for (int done = 0; done < max_iter + kChunk;) {
     if (use_graph) {
       CK(cudaGraphLaunch(ctx->graph_exec, s));
+      ctx->launches += ctx->graph_launches;
     } else {
-      for (int i = 0; i < kChunk; ++i) CK(pcg_iteration<T>(ctx, n_loads, x, r, p, ap, s));
+      for (int i = 0; i < kChunk; ++i) CK(pcg_iteration<T>(ctx, n_loads, x, r, p, ap, s, prof ? ctx->ev[i] : nullptr));
     }
     done += kChunk;
     CK(cudaMemcpyAsync(hs.data(), ctx->st, sizeof(PcgState) * n_loads, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (prof) {
+      int worked = 0;
+      for (int l = 0; l < n_loads; ++l) worked = std::max(worked, hs[l].iter - prev[l].iter);
+      TRY(harvest_events(ctx, prec, worked));
+      prev = hs;
+    }
     bool all = true;
     for (int l = 0; l < n_loads; ++l)
       if (hs[l].state == ST_RUN || hs[l].state == ST_CONV || hs[l].state == ST_FIN_MAX) all = false;
@@ -442,6 +522,7 @@ fehom_status compute_rhs(fehom_ctx* ctx, int n_loads, const double* loads, doubl
   a.tau = ctx->tau;
   a.y_scale = -1.0;
   CK(launch_stiffness<double>(a, ctx->stream));
+  count_launch(ctx);
   return FEHOM_OK;
 }
 
@@ -465,6 +546,7 @@ fehom_status mean_flux(fehom_ctx* ctx, int n_loads, const double* loads_host, co
   a.partial = ctx->partial;
   int blocks = 0;
   CK(launch_mean_flux(a, &blocks, ctx->stream));
+  count_launch(ctx);
   std::vector<double> hp((size_t)n_loads * blocks * ctx->m);
   CK(cudaMemcpyAsync(hp.data(), ctx->partial, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -485,6 +567,7 @@ fehom_status norms2(fehom_ctx* ctx, int n_loads, const double* v, std::vector<do
   int blocks = 0;
   const long long n = (long long)ctx->d.c * ctx->d.N;
   CK(launch_norm2(v, n, n_loads, n, ctx->partial, &blocks, ctx->stream));
+  count_launch(ctx);
   std::vector<double> hp((size_t)n_loads * blocks);
   CK(cudaMemcpyAsync(hp.data(), ctx->partial, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -494,11 +577,6 @@ fehom_status norms2(fehom_ctx* ctx, int n_loads, const double* v, std::vector<do
   return FEHOM_OK;
 }
 
-#define TRY(x)                          \
-  do {                                  \
-    fehom_status s_ = (x);              \
-    if (s_ != FEHOM_OK) return s_;      \
-  } while (0)
 
 }  // namespace
 
@@ -514,9 +592,26 @@ void fehom_default_options(fehom_options* opt) {
   opt->inner_tol = 1e-3;
   opt->stream = nullptr;
   opt->use_graph = 1;
+  opt->profile = 0;
 }
 
 const char* fehom_last_error(const fehom_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
+
+fehom_status fehom_kernel_times(const fehom_ctx* ctx, int precision, double* ms, int64_t* count) {
+  if (!ctx || !ms || !count) return FEHOM_E_INVALID;
+  const int p = precision == FEHOM_MIXED ? 1 : 0;
+  for (int k = 0; k < FEHOM_K_COUNT; ++k) {
+    ms[k] = ctx->kms[p][k];
+    count[k] = ctx->kcnt[p][k];
+  }
+  return FEHOM_OK;
+}
+
+fehom_status fehom_launch_count(const fehom_ctx* ctx, int64_t* count) {
+  if (!ctx || !count) return FEHOM_E_INVALID;
+  *count = ctx->launches;
+  return FEHOM_OK;
+}
 
 fehom_status fehom_query(const fehom_ctx* ctx, int* c, int* m, int64_t* N, int64_t* nxh) {
   if (!ctx) return FEHOM_E_INVALID;
@@ -534,6 +629,10 @@ void fehom_destroy(fehom_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->events_made)
+    for (int i = 0; i < kChunk; ++i)
+      for (int k = 0; k < FEHOM_K_COUNT; ++k)
+        for (int j = 0; j < 2; ++j) cudaEventDestroy(ctx->ev[i][k][j]);
   dfree(ctx->ids); dfree(ctx->mats64); dfree(ctx->mats32); dfree(ctx->iso64); dfree(ctx->iso32);
   dfree(ctx->rmats64); dfree(ctx->riso64); dfree(ctx->moduli_d);
   for (int i = 0; i < 3; ++i) { dfree(ctx->tw64[i]); dfree(ctx->tw32[i]); }
@@ -604,6 +703,7 @@ static fehom_status setup_impl(fehom_ctx* ctx, int elem, int physics, const int6
   CK(cudaMalloc(&hist, 256 * sizeof(unsigned long long)));
   CK(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), s));
   CK(launch_phase_histogram(ctx->ids, N, hist, s));
+  count_launch(ctx);
   std::vector<unsigned long long> hh(256);
   CK(cudaMemcpyAsync(hh.data(), hist, 256 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -721,6 +821,7 @@ fehom_status fehom_precond_build(fehom_ctx* ctx) {
   a.y_scale = 1.0;
   a.red = ctx->red;
   CK(launch_stiffness<double>(a, s));
+  count_launch(ctx);
   // forward FFT of every component of every column -> spec64[beta][alpha][Nh]
   FftArgs f;
   fill_dims_args(ctx, f, false, c);
@@ -728,8 +829,13 @@ fehom_status fehom_precond_build(fehom_ctx* ctx) {
   f.mode = FX_PLAIN;
   f.f0 = ctx->ap64;
   CK(launch_fft_x_fwd<double>(f, s));
-  if (ctx->d.dim == 3) CK(launch_fft_y<double>(f, 0, s));
+  count_launch(ctx);
+  if (ctx->d.dim == 3) {
+    CK(launch_fft_y<double>(f, 0, s));
+    count_launch(ctx);
+  }
   CK(launch_fft_last_solve<double>(f, s));
+  count_launch(ctx);
   // per-wavevector inverse
   const long long Nh = ctx->d.Nh;
   const int ne = c * (c + 1) / 2;
@@ -747,6 +853,7 @@ fehom_status fehom_precond_build(fehom_ctx* ctx) {
   sa.zero_tol = 1e-12;
   int blocks = 0;
   CK(launch_symbol_build(sa, &blocks, s));
+  count_launch(ctx);
   std::vector<double> hp(4 * blocks);
   CK(cudaMemcpyAsync(hp.data(), ctx->partial, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   // the k = 0 block
@@ -807,6 +914,7 @@ fehom_status fehom_apply_stiffness(fehom_ctx* ctx, const void* x, void* y, int p
   a.y = y;
   if (precision == FEHOM_MIXED) CK(launch_stiffness<float>(a, ctx->stream));
   else CK(launch_stiffness<double>(a, ctx->stream));
+  count_launch(ctx);
   CK(cudaStreamSynchronize(ctx->stream));
   return FEHOM_OK;
 }
@@ -851,6 +959,7 @@ static fehom_status finish_outputs(fehom_ctx* ctx, int n_loads, const double* lo
   cudaStream_t s = ctx->stream;
   const long long cN = (long long)ctx->d.c * ctx->d.N;
   CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, s));
+  count_launch(ctx);
   // true FP64 residual b - K x
   TRY(compute_rhs(ctx, n_loads, loads, ctx->b64));
   std::vector<double> bn;
@@ -859,7 +968,9 @@ static fehom_status finish_outputs(fehom_ctx* ctx, int n_loads, const double* lo
   a.x = ctx->x64;
   a.y = ctx->ap64;
   CK(launch_stiffness<double>(a, s));
+  count_launch(ctx);
   CK(launch_axpby_d(ctx->ap64, ctx->b64, -1.0, 1.0, cN * n_loads, s));
+  count_launch(ctx);
   std::vector<double> rn;
   TRY(norms2(ctx, n_loads, ctx->b64, rn));
   rel2.resize(n_loads);
@@ -926,11 +1037,14 @@ static fehom_status solve_fp64(fehom_ctx* ctx, int n_loads, const double* loads,
     CK(cudaStreamSynchronize(s));
     CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
     CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, s));
+    count_launch(ctx);
     StencilArgs a = stencil_args(ctx, false, n_loads);
     a.x = ctx->x64;
     a.y = ctx->ap64;
     CK(launch_stiffness<double>(a, s));
+    count_launch(ctx);
     CK(launch_axpby_d(ctx->ap64, ctx->r64, -1.0, 1.0, cN * n_loads, s));
+    count_launch(ctx);
     std::vector<PcgState> hs0(n_loads);
     for (int l = 0; l < n_loads; ++l) {
       std::memset(&hs0[l], 0, sizeof(PcgState));
@@ -959,6 +1073,7 @@ static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads
   if (x0) {
     CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
     CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, s));
+    count_launch(ctx);
   } else {
     CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * n_loads, s));
   }
@@ -978,11 +1093,14 @@ static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads
       a.x = ctx->x64;
       a.y = ctx->ap64;
       CK(launch_stiffness<double>(a, s));
+      count_launch(ctx);
       CK(launch_axpby_d(ctx->ap64, ctx->r64, -1.0, 1.0, cN * n_loads, s));
+      count_launch(ctx);
     }
     if (outer == 0 && x0) {
       // normalisation <b, K_ref^+ b> from b itself
       CK(launch_cast_d2f(ctx->b64, ctx->r32, 1.0, cN * n_loads, s));
+      count_launch(ctx);
       TRY(set_states(ctx, n_loads, ctx->opt.inner_tol, 1, -1.0));
       TRY(pcg_init<float>(ctx, n_loads, ctx->r32, ctx->p32));
       std::vector<PcgState> h0(n_loads);
@@ -991,6 +1109,7 @@ static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads
       for (int l = 0; l < n_loads; ++l) bnorm2[l] = h0[l].rz_init;
     }
     CK(launch_cast_d2f(ctx->r64, ctx->r32, 1.0, cN * n_loads, s));
+    count_launch(ctx);
     CK(cudaMemsetAsync(ctx->x32, 0, sizeof(float) * cN * n_loads, s));
     const int remaining = std::max(1, ctx->opt.max_iter - total_inner);
     TRY(set_states(ctx, n_loads, ctx->opt.inner_tol, remaining, -1.0));
@@ -1025,6 +1144,7 @@ static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads
     }
     total_inner += mx;
     CK(launch_add_f2d(ctx->x32, ctx->x64, 1.0, cN * n_loads, s));
+    count_launch(ctx);
   }
   for (int l = 0; l < n_loads; ++l) {
     hs[l].iter = inner_it[l];

@@ -27,12 +27,14 @@ STATUS = {0: "FEHOM_OK", 1: "FEHOM_E_INVALID", 2: "FEHOM_E_UNSUPPORTED_SIZE", 3:
 # every entry point declared in include/fehom.h
 EXPORTS = ("fehom_default_options", "fehom_setup", "fehom_precond_build", "fehom_solve", "fehom_destroy",
            "fehom_last_error", "fehom_query", "fehom_apply_stiffness", "fehom_rhs", "fehom_apply_precond",
-           "fehom_get_symbol_inverse", "fehom_mean_flux")
+           "fehom_get_symbol_inverse", "fehom_mean_flux", "fehom_kernel_times", "fehom_launch_count")
+
+KERNEL_CLASSES = ("stiffness", "fft_x_fwd", "fft_y_fwd", "fft_last", "fft_y_inv", "fft_x_inv")
 
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_iter", C.c_int), ("inner_tol", C.c_double),
-                ("stream", C.c_void_p), ("use_graph", C.c_int)]
+                ("stream", C.c_void_p), ("use_graph", C.c_int), ("profile", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -84,6 +86,10 @@ def load_library(path: str = LIB_PATH):
     lib.fehom_get_symbol_inverse.restype = i
     lib.fehom_mean_flux.argtypes = [vp, dp, vp, dp]
     lib.fehom_mean_flux.restype = i
+    lib.fehom_kernel_times.argtypes = [vp, i, dp, i64p]
+    lib.fehom_kernel_times.restype = i
+    lib.fehom_launch_count.argtypes = [vp, i64p]
+    lib.fehom_launch_count.restype = i
     _lib = lib
     return lib
 
@@ -103,7 +109,7 @@ class Solver:
     """One periodic cell: fehom_setup on construction, fehom_destroy on close()."""
 
     def __init__(self, elem, physics, n, ids, moduli, ref_material=None, precision="fp64", max_iter=10000,
-                 inner_tol=1e-3, cell=None, use_graph=True, stream=None):
+                 inner_tol=1e-3, cell=None, use_graph=True, stream=None, profile=False):
         torch = _torch()
         self.lib = load_library()
         self.elem, self.physics = elem, physics
@@ -116,6 +122,7 @@ class Solver:
         opt.max_iter = int(max_iter)
         opt.inner_tol = float(inner_tol)
         opt.use_graph = 1 if use_graph else 0
+        opt.profile = 1 if profile else 0
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opt.stream = C.c_void_p(self.stream.cuda_stream)
         self._opt = opt
@@ -216,6 +223,18 @@ class Solver:
         out = np.zeros(ne * self.Nh)
         self._check(self.lib.fehom_get_symbol_inverse(self.ctx, _dptr(out)))
         return out.reshape(ne, self.n[2], self.n[1], self.nxh)
+
+    def kernel_times(self, precision="fp64"):
+        """{class: (total ms, launches timed)} of the PCG iteration kernels (needs profile=True)."""
+        ms = (C.c_double * 6)()
+        cnt = (C.c_int64 * 6)()
+        self._check(self.lib.fehom_kernel_times(self.ctx, PRECISION[precision], ms, cnt))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def launch_count(self):
+        n = C.c_int64()
+        self._check(self.lib.fehom_launch_count(self.ctx, C.byref(n)))
+        return n.value
 
     def mean_flux(self, e, u):
         e = np.ascontiguousarray(np.asarray(e, np.float64))
