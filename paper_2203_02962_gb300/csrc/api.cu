@@ -958,8 +958,9 @@ static fehom_status finish_outputs(fehom_ctx* ctx, int n_loads, const double* lo
                                    std::vector<double>& rel2) {
   cudaStream_t s = ctx->stream;
   const long long cN = (long long)ctx->d.c * ctx->d.N;
-  CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, s));
-  count_launch(ctx);
+  TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
+  CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
+  count_launch(ctx, 2);
   // true FP64 residual b - K x
   TRY(compute_rhs(ctx, n_loads, loads, ctx->b64));
   std::vector<double> bn;
@@ -1036,8 +1037,9 @@ static fehom_status solve_fp64(fehom_ctx* ctx, int n_loads, const double* loads,
     CK(cudaMemcpyAsync(h0.data(), ctx->st, sizeof(PcgState) * n_loads, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
-    CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, s));
-    count_launch(ctx);
+    TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
+    CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
+    count_launch(ctx, 2);
     StencilArgs a = stencil_args(ctx, false, n_loads);
     a.x = ctx->x64;
     a.y = ctx->ap64;
@@ -1072,8 +1074,9 @@ static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads
   TRY(compute_rhs(ctx, n_loads, loads, ctx->b64));
   if (x0) {
     CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
-    CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, s));
-    count_launch(ctx);
+    TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
+    CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
+    count_launch(ctx, 2);
   } else {
     CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * n_loads, s));
   }
@@ -1132,6 +1135,9 @@ static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads
         all = false;
         outer_it[l] += 1;
         if (h[l].state != ST_RUN) h[l].state = ST_RUN;  // inner criterion met at start: still do >= 1 step
+        // inner stopping point: the relative reduction inner_tol, or (if less work) half the distance
+        // to the outer target tol * sqrt(<b, K_ref^+ b>)
+        h[l].tol2 = std::max(h[l].tol2, 0.25 * tol * tol * bnorm2[l]);
       }
     }
     if (all || total_inner >= ctx->opt.max_iter) break;

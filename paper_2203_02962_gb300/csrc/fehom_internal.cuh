@@ -157,7 +157,9 @@ cudaError_t launch_fill(void* p, long long n, int bytes_per_elem, cudaStream_t s
 cudaError_t launch_axpby_d(const double* x, double* y, double a, double b, long long n, cudaStream_t s);
 cudaError_t launch_cast_d2f(const double* x, float* y, double scale, long long n, cudaStream_t s);
 cudaError_t launch_add_f2d(const float* x, double* y, double scale, long long n, cudaStream_t s);
-cudaError_t launch_sub_mean(double* x, int c, long long N, int n_loads, long long load_stride, cudaStream_t s);
+// removes the mean of every (component, load); partial: scratch of n_loads * c * 304 doubles (two launches)
+cudaError_t launch_sub_mean(double* x, int c, long long N, int n_loads, long long load_stride, double* partial,
+                            cudaStream_t s);
 // per-load sum of squares and sum (FP64 partials -> host)
 cudaError_t launch_norm2(const double* x, long long n, int n_loads, long long load_stride, double* partial,
                          int* blocks_out, cudaStream_t s);

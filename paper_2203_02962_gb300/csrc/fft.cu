@@ -113,26 +113,21 @@ template <typename C, bool INV> struct Dft<C, 3, INV> {
   }
 };
 
-// One Stockham stage over `ncols` independent lines.  COLS: element-major layout (addr e*ld + col),
-// otherwise line-major (addr col*ld + e).
-template <typename C, int R, bool INV, bool COLS>
-__device__ __forceinline__ void stage(const C* __restrict__ in, C* __restrict__ out, int L, int Ns, int ncols, int ld,
+// One Stockham stage over NCOLS independent columns held element-major in shared memory
+// (element e of column col at e * LD + col).  Ns (the span of the stages done so far) is a power of
+// two: the radix-3 stage, when there is one, runs last.
+template <typename C, int R, bool INV, int NCOLS, int LD>
+__device__ __forceinline__ void stage(const C* __restrict__ in, C* __restrict__ out, int L, int Ns,
                                       const C* __restrict__ tw) {
   const int nb = L / R;
   const int tstride = L / (Ns * R);
-  for (int w = threadIdx.x; w < ncols * nb; w += blockDim.x) {
-    int col, j;
-    if (COLS) {
-      col = w % ncols;
-      j = w / ncols;
-    } else {
-      j = w % nb;
-      col = w / nb;
-    }
+  const int nw = NCOLS * nb;
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+    const int col = w % NCOLS, j = w / NCOLS;
     C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = COLS ? in[(j + r * nb) * ld + col] : in[col * ld + j + r * nb];
-    const int kk = j % Ns;
+    for (int r = 0; r < R; ++r) v[r] = in[(j + r * nb) * LD + col];
+    const int kk = j & (Ns - 1);
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -143,40 +138,38 @@ __device__ __forceinline__ void stage(const C* __restrict__ in, C* __restrict__ 
     Dft<C, R, INV>::run(v);
     const int base = (j - kk) * R + kk;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int e = base + r * Ns;
-      if (COLS) out[e * ld + col] = v[r];
-      else out[col * ld + e] = v[r];
-    }
+    for (int r = 0; r < R; ++r) out[(base + r * Ns) * LD + col] = v[r];
   }
   __syncthreads();
 }
 
-// Full length-L transform of `ncols` lines held in b0; returns the buffer holding the result.
-template <typename C, bool INV, bool COLS>
-__device__ C* fft_smem(C* b0, C* b1, int L, int ncols, int ld, const C* tw) {
-  int Ns = 1, rem = L;
+// Full length-L transform (L = 2^k or 3 * 2^k) of NCOLS columns held in b0; returns the buffer
+// holding the result (b0 or b1).
+template <typename C, bool INV, int NCOLS, int LD>
+__device__ C* fft_smem(C* b0, C* b1, int L, const C* tw) {
+  int Ns = 1;
+  int rem = (L % 3 == 0) ? L / 3 : L;
   C* in = b0;
   C* out = b1;
-  if (rem % 3 == 0) {
-    stage<C, 3, INV, COLS>(in, out, L, Ns, ncols, ld, tw);
-    Ns *= 3; rem /= 3;
-    C* t = in; in = out; out = t;
-  }
+  auto swap = [&] { C* t = in; in = out; out = t; };
   while (rem % 8 == 0 && rem != 16) {  // 16 = 4 * 4 is cheaper than 8 * 2
-    stage<C, 8, INV, COLS>(in, out, L, Ns, ncols, ld, tw);
+    stage<C, 8, INV, NCOLS, LD>(in, out, L, Ns, tw);
     Ns *= 8; rem /= 8;
-    C* t = in; in = out; out = t;
+    swap();
   }
   while (rem % 4 == 0) {
-    stage<C, 4, INV, COLS>(in, out, L, Ns, ncols, ld, tw);
+    stage<C, 4, INV, NCOLS, LD>(in, out, L, Ns, tw);
     Ns *= 4; rem /= 4;
-    C* t = in; in = out; out = t;
+    swap();
   }
   if (rem % 2 == 0) {
-    stage<C, 2, INV, COLS>(in, out, L, Ns, ncols, ld, tw);
+    stage<C, 2, INV, NCOLS, LD>(in, out, L, Ns, tw);
     Ns *= 2; rem /= 2;
-    C* t = in; in = out; out = t;
+    swap();
+  }
+  if (L % 3 == 0) {
+    stage<C, 3, INV, NCOLS, LD>(in, out, L, Ns, tw);
+    swap();
   }
   return in;
 }
@@ -234,17 +227,38 @@ __device__ __forceinline__ bool second_half_active(const PcgState* st, int load)
 constexpr int XT = 256;  // threads of the x passes
 constexpr int ST = 256;  // threads of the strided passes
 
+// (line, position) of a flat index over lines of length n, x fastest; shift/mask when n = 2^k
+struct LineIdx {
+  int n, lg;
+  bool pow2;
+  __device__ explicit LineIdx(int n_) : n(n_), lg(0), pow2((n_ & (n_ - 1)) == 0) {
+    while ((2 << lg) <= n) ++lg;
+  }
+  __device__ __forceinline__ void split(int idx, int& q, int& x) const {
+    if (pow2) {
+      q = idx >> lg;
+      x = idx & (n - 1);
+    } else {
+      q = idx / n;
+      x = idx - q * n;
+    }
+  }
+};
+
 // ------------------------------------------------------------------------------------------------
-// x passes
+// x passes: P pairs of real lines per CTA, each pair packed into one complex line; shared memory
+// holds the P complex lines element-major with a padded stride P + 1 (conflict-free both when the
+// lines are read along x and when the butterflies run across the P columns).
 // ------------------------------------------------------------------------------------------------
-template <typename T, bool UPDATE>
-__global__ void __launch_bounds__(XT) fft_x_fwd_kernel(FftArgs a, int P) {
+template <typename T, bool UPDATE, int P>
+__global__ void __launch_bounds__(XT) fft_x_fwd_kernel(FftArgs a) {
   using C = typename V2<T>::t;
+  constexpr int LD = P + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims d = a.d;
   const int nx = d.nx, nxh = d.nxh;
   C* b0 = reinterpret_cast<C*>(smem_raw);
-  C* b1 = b0 + P * nx;
+  C* b1 = b0 + nx * LD;
   const int comp = blockIdx.y, load = blockIdx.z;
   if (UPDATE && !first_half_active(a.st, load)) return;
   const long long nlines = (long long)d.ny * d.nz;
@@ -254,8 +268,10 @@ __global__ void __launch_bounds__(XT) fft_x_fwd_kernel(FftArgs a, int P) {
   C* spec = reinterpret_cast<C*>(a.spec) + (long long)load * a.load_stride_s + (long long)comp * d.Nh;
   const T alpha = UPDATE ? T(a.st[load].alpha) : T(0);
   const long long line_base = 2LL * blockIdx.x * P;
+  const LineIdx li(nx);
   for (int idx = threadIdx.x; idx < P * nx; idx += XT) {
-    const int q = idx / nx, xx = idx - q * nx;
+    int q, xx;
+    li.split(idx, q, xx);
     const long long l0 = line_base + 2 * q;
     T v0 = T(0), v1 = T(0);
     if (l0 < nlines) {
@@ -272,76 +288,75 @@ __global__ void __launch_bounds__(XT) fft_x_fwd_kernel(FftArgs a, int P) {
         }
       }
     }
-    b0[q * nx + xx] = mk<C>(v0, v1);
+    b0[xx * LD + q] = mk<C>(v0, v1);
   }
   __syncthreads();
-  const C* res = fft_smem<C, false, false>(b0, b1, nx, P, nx, reinterpret_cast<const C*>(a.tw.x));
+  const C* res = fft_smem<C, false, P, LD>(b0, b1, nx, reinterpret_cast<const C*>(a.tw.x));
+  // split Z = FFT(a + i b) into the half spectra A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i)
   for (int idx = threadIdx.x; idx < P * nxh; idx += XT) {
-    const int q = idx / nxh, k = idx - q * nxh;
+    const int k = idx / P, q = idx % P;
     const long long l0 = line_base + 2 * q;
     if (l0 >= nlines) continue;
-    const C zk = res[q * nx + k];
-    const C zn = res[q * nx + (k == 0 ? 0 : nx - k)];
+    const C zk = res[k * LD + q];
+    const C zn = res[(k == 0 ? 0 : nx - k) * LD + q];
     const T h = T(0.5);
-    const C A = mk<C>(h * (zk.x + zn.x), h * (zk.y - zn.y));
-    const C B = mk<C>(h * (zk.y + zn.y), h * (zn.x - zk.x));
-    spec[l0 * nxh + k] = A;
-    if (l0 + 1 < nlines) spec[(l0 + 1) * nxh + k] = B;
+    spec[l0 * nxh + k] = mk<C>(h * (zk.x + zn.x), h * (zk.y - zn.y));
+    if (l0 + 1 < nlines) spec[(l0 + 1) * nxh + k] = mk<C>(h * (zk.y + zn.y), h * (zn.x - zk.x));
   }
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(XT) fft_x_inv_kernel(FftArgs a, int P) {
+template <typename T, int MODE, int P>
+__global__ void __launch_bounds__(XT) fft_x_inv_kernel(FftArgs a) {
   using C = typename V2<T>::t;
+  constexpr int LD = P + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_sh[32];
   const Dims d = a.d;
   const int nx = d.nx, nxh = d.nxh, half = nx / 2;
   C* b0 = reinterpret_cast<C*>(smem_raw);
-  C* b1 = b0 + P * nx;
+  C* b1 = b0 + nx * LD;
   const int comp = blockIdx.y, load = blockIdx.z;
   if (MODE != FX_PLAIN && !second_half_active(a.st, load)) return;
   const long long nlines = (long long)d.ny * d.nz;
   const long long foff = (long long)load * a.load_stride_f + (long long)comp * d.N;
   const C* spec = reinterpret_cast<const C*>(a.spec) + (long long)load * a.load_stride_s + (long long)comp * d.Nh;
   const long long line_base = 2LL * blockIdx.x * P;
+  const LineIdx li(nx);
   for (int idx = threadIdx.x; idx < P * nx; idx += XT) {
-    const int q = idx / nx, k = idx - q * nx;
+    int q, k;
+    li.split(idx, q, k);
     const long long l0 = line_base + 2 * q;
     C z = mk<C>(T(0), T(0));
     if (l0 < nlines) {
+      // Hermitian completion of the two half spectra, then Z = A + i B
       const bool has1 = l0 + 1 < nlines;
-      C A, B = mk<C>(T(0), T(0));
-      if (k <= half) {
-        A = spec[l0 * nxh + k];
-        if (has1) B = spec[(l0 + 1) * nxh + k];
-        if (k == 0 || k == half) {
-          A.y = T(0);
-          B.y = T(0);
-        }
-      } else {
-        const C a0 = spec[l0 * nxh + nx - k];
-        A = mk<C>(a0.x, -a0.y);
-        if (has1) {
-          const C b0_ = spec[(l0 + 1) * nxh + nx - k];
-          B = mk<C>(b0_.x, -b0_.y);
-        }
+      const bool lo = k <= half;
+      const int kk = lo ? k : nx - k;
+      C A = spec[l0 * nxh + kk];
+      C B = has1 ? spec[(l0 + 1) * nxh + kk] : mk<C>(T(0), T(0));
+      if (!lo) {
+        A.y = -A.y;
+        B.y = -B.y;
+      } else if (k == 0 || k == half) {
+        A.y = T(0);
+        B.y = T(0);
       }
-      z = mk<C>(A.x - B.y, A.y + B.x);  // A + i B
+      z = mk<C>(A.x - B.y, A.y + B.x);
     }
-    b0[q * nx + k] = z;
+    b0[k * LD + q] = z;
   }
   __syncthreads();
-  const C* res = fft_smem<C, true, false>(b0, b1, nx, P, nx, reinterpret_cast<const C*>(a.tw.x));
+  const C* res = fft_smem<C, true, P, LD>(b0, b1, nx, reinterpret_cast<const C*>(a.tw.x));
   T* f0 = reinterpret_cast<T*>(a.f0) + foff;
   T* f2 = (MODE != FX_PLAIN) ? reinterpret_cast<T*>(a.f2) + foff : nullptr;
   const T alpha = (MODE == FX_PCG) ? T(a.st[load].alpha) : T(0);
   const T beta = (MODE == FX_PCG) ? T(a.st[load].beta) : T(0);
   for (int idx = threadIdx.x; idx < P * nx; idx += XT) {
-    const int q = idx / nx, xx = idx - q * nx;
+    int q, xx;
+    li.split(idx, q, xx);
     const long long l0 = line_base + 2 * q;
     if (l0 >= nlines) continue;
-    const C zc = res[q * nx + xx];
+    const C zc = res[xx * LD + q];
     const bool has1 = l0 + 1 < nlines;
     const long long g0 = l0 * nx + xx, g1 = g0 + nx;
     if (MODE == FX_PLAIN) {
@@ -381,7 +396,8 @@ __global__ void __launch_bounds__(XT) fft_x_inv_kernel(FftArgs a, int P) {
 
 // ------------------------------------------------------------------------------------------------
 // strided passes: columns cf = 0..ncols-1 of the half spectrum; element e of column cf at
-//   (cf / nxh) * outer + e * estride + (cf % nxh)
+//   (cf / nxh) * outer + e * estride + (cf % nxh).  A CTA holds TC consecutive columns; their base
+//   offsets are computed once per CTA.
 // ------------------------------------------------------------------------------------------------
 struct ColMap {
   int L;             // transform length (axis size)
@@ -390,10 +406,27 @@ struct ColMap {
   long long estride; // stride along the axis
 };
 
-template <typename T, bool INV>
-__global__ void __launch_bounds__(ST) fft_strided_kernel(FftArgs a, ColMap m, int TC, const typename V2<T>::t* tw) {
+template <int TC>
+__device__ __forceinline__ void column_bases(const ColMap& m, int nxh, int cf0, long long* base, int* kx) {
+  if (threadIdx.x < TC) {
+    const int cf = cf0 + threadIdx.x;
+    if (cf < m.ncols) {
+      base[threadIdx.x] = (long long)(cf / nxh) * m.outer + (cf % nxh);
+      kx[threadIdx.x] = cf % nxh;
+    } else {
+      base[threadIdx.x] = -1;
+      kx[threadIdx.x] = 0;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, bool INV, int TC>
+__global__ void __launch_bounds__(ST) fft_strided_kernel(FftArgs a, ColMap m, const typename V2<T>::t* tw) {
   using C = typename V2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long base[TC];
+  __shared__ int kxs[TC];
   C* b0 = reinterpret_cast<C*>(smem_raw);
   C* b1 = b0 + m.L * TC;
   const int comp = blockIdx.y, load = blockIdx.z;
@@ -402,65 +435,63 @@ __global__ void __launch_bounds__(ST) fft_strided_kernel(FftArgs a, ColMap m, in
     if (INV && !second_half_active(a.st, load)) return;
   }
   C* spec = reinterpret_cast<C*>(a.spec) + (long long)load * a.load_stride_s + (long long)comp * a.d.Nh;
-  const int nxh = a.d.nxh;
-  const int cf0 = blockIdx.x * TC;
+  column_bases<TC>(m, a.d.nxh, blockIdx.x * TC, base, kxs);
   for (int idx = threadIdx.x; idx < m.L * TC; idx += ST) {
-    const int e = idx / TC, t = idx - e * TC;
-    const int cf = cf0 + t;
-    C v = mk<C>(T(0), T(0));
-    if (cf < m.ncols) v = spec[(long long)(cf / nxh) * m.outer + (long long)e * m.estride + (cf % nxh)];
-    b0[idx] = v;
+    const int e = idx / TC, t = idx % TC;
+    const long long cb = base[t];
+    b0[idx] = cb >= 0 ? spec[cb + (long long)e * m.estride] : mk<C>(T(0), T(0));
   }
   __syncthreads();
-  const C* res = fft_smem<C, INV, true>(b0, b1, m.L, TC, TC, tw);
+  const C* res = fft_smem<C, INV, TC, TC>(b0, b1, m.L, tw);
   for (int idx = threadIdx.x; idx < m.L * TC; idx += ST) {
-    const int e = idx / TC, t = idx - e * TC;
-    const int cf = cf0 + t;
-    if (cf < m.ncols) spec[(long long)(cf / nxh) * m.outer + (long long)e * m.estride + (cf % nxh)] = res[idx];
+    const int e = idx / TC, t = idx % TC;
+    const long long cb = base[t];
+    if (cb >= 0) spec[cb + (long long)e * m.estride] = res[idx];
   }
 }
 
 // Last axis with the block solve.  3-D: axis z, columns cf = ky * nxh + kx.  2-D: axis y, cf = kx.
-template <typename T, int NC, bool SOLVE>
-__global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, int TC, const typename V2<T>::t* tw) {
+// Shared memory: [e][component][TC] (all c components of the same columns).
+template <typename T, int NC, bool SOLVE, int TC>
+__global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, const typename V2<T>::t* tw) {
   using C = typename V2<T>::t;
+  constexpr int W = NC * TC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_sh[32];
-  const int W = NC * TC;  // columns held by the CTA (component-major)
+  __shared__ long long base[TC];
+  __shared__ int kxs[TC];
   C* b0 = reinterpret_cast<C*>(smem_raw);
   C* b1 = b0 + m.L * W;
   const int load = blockIdx.z;
   if (!first_half_active(a.st, load)) return;
   C* spec = reinterpret_cast<C*>(a.spec) + (long long)load * a.load_stride_s;
   const long long Nh = a.d.Nh;
-  const int nxh = a.d.nxh, half = a.d.nx / 2;
-  const int cf0 = blockIdx.x * TC;
+  const int half = a.d.nx / 2;
+  column_bases<TC>(m, a.d.nxh, blockIdx.x * TC, base, kxs);
   for (int idx = threadIdx.x; idx < m.L * W; idx += ST) {
-    const int e = idx / W, rem = idx - e * W, comp = rem / TC, t = rem - comp * TC;
-    const int cf = cf0 + t;
-    C v = mk<C>(T(0), T(0));
-    if (cf < m.ncols) v = spec[comp * Nh + (long long)(cf / nxh) * m.outer + (long long)e * m.estride + (cf % nxh)];
-    b0[idx] = v;
+    const int e = idx / W, rem = idx % W, comp = rem / TC, t = rem % TC;
+    const long long cb = base[t];
+    b0[idx] = cb >= 0 ? spec[comp * Nh + cb + (long long)e * m.estride] : mk<C>(T(0), T(0));
   }
   __syncthreads();
-  C* res = fft_smem<C, false, true>(b0, b1, m.L, W, W, tw);
+  C* res = fft_smem<C, false, W, W>(b0, b1, m.L, tw);
   C* other = (res == b0) ? b1 : b0;
   if (!SOLVE) {
     for (int idx = threadIdx.x; idx < m.L * W; idx += ST) {
-      const int e = idx / W, rem = idx - e * W, comp = rem / TC, t = rem - comp * TC;
-      const int cf = cf0 + t;
-      if (cf < m.ncols) spec[comp * Nh + (long long)(cf / nxh) * m.outer + (long long)e * m.estride + (cf % nxh)] = res[idx];
+      const int e = idx / W, rem = idx % W, comp = rem / TC, t = rem % TC;
+      const long long cb = base[t];
+      if (cb >= 0) spec[comp * Nh + cb + (long long)e * m.estride] = res[idx];
     }
     return;
   }
   const T* sym = reinterpret_cast<const T*>(a.sym);
   double dot = 0.0;
   for (int idx = threadIdx.x; idx < m.L * TC; idx += ST) {
-    const int e = idx / TC, t = idx - e * TC;
-    const int cf = cf0 + t;
-    if (cf >= m.ncols) continue;
-    const long long ti = (long long)(cf / nxh) * m.outer + (long long)e * m.estride + (cf % nxh);
-    const int kx = cf % nxh;
+    const int e = idx / TC, t = idx % TC;
+    const long long cb = base[t];
+    if (cb < 0) continue;
+    const long long ti = cb + (long long)e * m.estride;
+    const int kx = kxs[t];
     const double wgt = (kx == 0 || kx == half) ? 1.0 : 2.0;
     C r[NC], z[NC];
 #pragma unroll
@@ -489,11 +520,11 @@ __global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, int T
     dot = fma(wgt, acc, dot);
   }
   __syncthreads();
-  const C* out = fft_smem<C, true, true>(res, other, m.L, W, W, tw);
+  const C* out = fft_smem<C, true, W, W>(res, other, m.L, tw);
   for (int idx = threadIdx.x; idx < m.L * W; idx += ST) {
-    const int e = idx / W, rem = idx - e * W, comp = rem / TC, t = rem - comp * TC;
-    const int cf = cf0 + t;
-    if (cf < m.ncols) spec[comp * Nh + (long long)(cf / nxh) * m.outer + (long long)e * m.estride + (cf % nxh)] = out[idx];
+    const int e = idx / W, rem = idx % W, comp = rem / TC, t = rem % TC;
+    const long long cb = base[t];
+    if (cb >= 0) spec[comp * Nh + cb + (long long)e * m.estride] = out[idx];
   }
   if (a.st != nullptr) {
     const double part = block_sum(dot, red_sh);
@@ -606,22 +637,29 @@ cudaError_t set_smem(K kern, size_t bytes) {
   return cudaSuccess;
 }
 
-constexpr size_t kSmemBudget = 112 * 1024;  // two CTAs per SM
+constexpr size_t kSmemPair = 112 * 1024;  // two CTAs per SM
+constexpr size_t kSmemMax = 200 * 1024;
 
-// pairs of x lines per CTA: as many as fit (power of two), at most 8
+// pairs of x lines per CTA: 8, or 4 when 8 does not fit
 template <typename T> int x_pairs(const Dims& d) {
   using C = typename V2<T>::t;
-  const long long pairs = ((long long)d.ny * d.nz + 1) / 2;
-  int P = 8;
-  while (P > 1 && (2ull * P * d.nx * sizeof(C) > kSmemBudget || P > pairs)) P >>= 1;
-  return P;
+  return (2ull * d.nx * 9 * sizeof(C) <= 160 * 1024) ? 8 : 4;
 }
 
+// columns per CTA of a strided pass over nc components: 128-byte rows, halved until it fits
 template <typename T> int tile_cols(int L, int nc) {
   using C = typename V2<T>::t;
-  int TC = 16;
-  while (TC > 1 && 2ull * L * nc * TC * sizeof(C) > kSmemBudget) TC >>= 1;
-  return TC;
+  int TC = sizeof(T) == 4 ? 16 : 8;
+  while (TC > 2 && 2ull * L * nc * TC * sizeof(C) > kSmemPair) TC >>= 1;
+  return 2ull * L * nc * TC * sizeof(C) <= kSmemMax ? TC : 0;
+}
+
+template <typename K, typename... Args>
+cudaError_t launch_with_smem(K kern, dim3 grid, int threads, size_t smem, cudaStream_t s, Args... args) {
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, threads, smem, s>>>(args...);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -635,19 +673,12 @@ cudaError_t launch_fft_x_fwd(const FftArgs& a, cudaStream_t s) {
   const int P = x_pairs<T>(a.d);
   const long long pairs = ((long long)a.d.ny * a.d.nz + 1) / 2;
   dim3 grid((unsigned)((pairs + P - 1) / P), a.d.c, a.n_loads);
-  const size_t smem = 2ull * P * a.d.nx * sizeof(C);
-  if (a.mode == FX_PCG) {
-    auto k = fft_x_fwd_kernel<T, true>;
-    cudaError_t e = set_smem(k, smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, XT, smem, s>>>(a, P);
-  } else {
-    auto k = fft_x_fwd_kernel<T, false>;
-    cudaError_t e = set_smem(k, smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, XT, smem, s>>>(a, P);
-  }
-  return cudaGetLastError();
+  const size_t smem = 2ull * a.d.nx * (P + 1) * sizeof(C);
+  const bool up = a.mode == FX_PCG;
+  if (P == 8) return up ? launch_with_smem(fft_x_fwd_kernel<T, true, 8>, grid, XT, smem, s, a)
+                        : launch_with_smem(fft_x_fwd_kernel<T, false, 8>, grid, XT, smem, s, a);
+  return up ? launch_with_smem(fft_x_fwd_kernel<T, true, 4>, grid, XT, smem, s, a)
+            : launch_with_smem(fft_x_fwd_kernel<T, false, 4>, grid, XT, smem, s, a);
 }
 
 template <typename T>
@@ -657,22 +688,27 @@ cudaError_t launch_fft_x_inv(const FftArgs& a, cudaStream_t s) {
   const long long pairs = ((long long)a.d.ny * a.d.nz + 1) / 2;
   dim3 grid((unsigned)((pairs + P - 1) / P), a.d.c, a.n_loads);
   if (a.st != nullptr && (long long)grid.x * grid.y > a.red.max_blocks) return cudaErrorInvalidConfiguration;
-  const size_t smem = 2ull * P * a.d.nx * sizeof(C);
-  cudaError_t e;
-  if (a.mode == FX_PCG) {
-    auto k = fft_x_inv_kernel<T, FX_PCG>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    k<<<grid, XT, smem, s>>>(a, P);
-  } else if (a.mode == FX_PCG_INIT) {
-    auto k = fft_x_inv_kernel<T, FX_PCG_INIT>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    k<<<grid, XT, smem, s>>>(a, P);
-  } else {
-    auto k = fft_x_inv_kernel<T, FX_PLAIN>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    k<<<grid, XT, smem, s>>>(a, P);
+  const size_t smem = 2ull * a.d.nx * (P + 1) * sizeof(C);
+  if (P == 8) {
+    if (a.mode == FX_PCG) return launch_with_smem(fft_x_inv_kernel<T, FX_PCG, 8>, grid, XT, smem, s, a);
+    if (a.mode == FX_PCG_INIT) return launch_with_smem(fft_x_inv_kernel<T, FX_PCG_INIT, 8>, grid, XT, smem, s, a);
+    return launch_with_smem(fft_x_inv_kernel<T, FX_PLAIN, 8>, grid, XT, smem, s, a);
   }
-  return cudaGetLastError();
+  if (a.mode == FX_PCG) return launch_with_smem(fft_x_inv_kernel<T, FX_PCG, 4>, grid, XT, smem, s, a);
+  if (a.mode == FX_PCG_INIT) return launch_with_smem(fft_x_inv_kernel<T, FX_PCG_INIT, 4>, grid, XT, smem, s, a);
+  return launch_with_smem(fft_x_inv_kernel<T, FX_PLAIN, 4>, grid, XT, smem, s, a);
+}
+
+template <typename T, bool INV>
+static cudaError_t launch_strided_tc(const FftArgs& a, const ColMap& m, int TC, dim3 grid, size_t smem,
+                                     const typename V2<T>::t* tw, cudaStream_t s) {
+  switch (TC) {
+    case 16: return launch_with_smem(fft_strided_kernel<T, INV, 16>, grid, ST, smem, s, a, m, tw);
+    case 8: return launch_with_smem(fft_strided_kernel<T, INV, 8>, grid, ST, smem, s, a, m, tw);
+    case 4: return launch_with_smem(fft_strided_kernel<T, INV, 4>, grid, ST, smem, s, a, m, tw);
+    case 2: return launch_with_smem(fft_strided_kernel<T, INV, 2>, grid, ST, smem, s, a, m, tw);
+    default: return cudaErrorInvalidConfiguration;
+  }
 }
 
 template <typename T>
@@ -681,20 +717,24 @@ cudaError_t launch_fft_y(const FftArgs& a, int inverse, cudaStream_t s) {
   // 3-D middle axis: columns (z, kx), element e = ky
   ColMap m{a.d.ny, a.d.nz * a.d.nxh, (long long)a.d.ny * a.d.nxh, (long long)a.d.nxh};
   const int TC = tile_cols<T>(m.L, 1);
+  if (TC == 0) return cudaErrorInvalidConfiguration;
   dim3 grid((m.ncols + TC - 1) / TC, a.d.c, a.n_loads);
   const size_t smem = 2ull * m.L * TC * sizeof(C);
   const C* tw = reinterpret_cast<const C*>(a.tw.y);
-  cudaError_t e;
-  if (inverse) {
-    auto k = fft_strided_kernel<T, true>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    k<<<grid, ST, smem, s>>>(a, m, TC, tw);
-  } else {
-    auto k = fft_strided_kernel<T, false>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    k<<<grid, ST, smem, s>>>(a, m, TC, tw);
+  return inverse ? launch_strided_tc<T, true>(a, m, TC, grid, smem, tw, s)
+                 : launch_strided_tc<T, false>(a, m, TC, grid, smem, tw, s);
+}
+
+template <typename T, int NC, bool SOLVE>
+static cudaError_t launch_last_tc(const FftArgs& a, const ColMap& m, int TC, dim3 grid, size_t smem,
+                                  const typename V2<T>::t* tw, cudaStream_t s) {
+  switch (TC) {
+    case 16: return launch_with_smem(fft_last_kernel<T, NC, SOLVE, 16>, grid, ST, smem, s, a, m, tw);
+    case 8: return launch_with_smem(fft_last_kernel<T, NC, SOLVE, 8>, grid, ST, smem, s, a, m, tw);
+    case 4: return launch_with_smem(fft_last_kernel<T, NC, SOLVE, 4>, grid, ST, smem, s, a, m, tw);
+    case 2: return launch_with_smem(fft_last_kernel<T, NC, SOLVE, 2>, grid, ST, smem, s, a, m, tw);
+    default: return cudaErrorInvalidConfiguration;
   }
-  return cudaGetLastError();
 }
 
 template <typename T, int NC>
@@ -710,20 +750,12 @@ static cudaError_t launch_last_nc(const FftArgs& a, cudaStream_t s) {
     tw = reinterpret_cast<const C*>(a.tw.y);
   }
   const int TC = tile_cols<T>(m.L, NC);
+  if (TC == 0) return cudaErrorInvalidConfiguration;
   dim3 grid((m.ncols + TC - 1) / TC, 1, a.n_loads);
   if (a.st != nullptr && (long long)grid.x > a.red.max_blocks) return cudaErrorInvalidConfiguration;
   const size_t smem = 2ull * m.L * NC * TC * sizeof(C);
-  cudaError_t e;
-  if (a.sym) {
-    auto k = fft_last_kernel<T, NC, true>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    k<<<grid, ST, smem, s>>>(a, m, TC, tw);
-  } else {
-    auto k = fft_last_kernel<T, NC, false>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    k<<<grid, ST, smem, s>>>(a, m, TC, tw);
-  }
-  return cudaGetLastError();
+  return a.sym ? launch_last_tc<T, NC, true>(a, m, TC, grid, smem, tw, s)
+               : launch_last_tc<T, NC, false>(a, m, TC, grid, smem, tw, s);
 }
 
 template <typename T>

@@ -261,16 +261,22 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
   const double* tau = HAS_E ? a.tau + (long long)load * a.n_phases * (3 * C) : nullptr;
   const long long plane = (long long)d.nx * d.ny;
 
+  // Each thread stages the same (at most two) halo positions of every node plane: their in-plane
+  // offsets (periodic wrap included) are computed once, so the z march does no index division.
+  constexpr int NPOS = PY * PX;
+  static_assert(NPOS <= 2 * NT, "two halo positions per thread");
+  const int p1 = tid + NT;
+  const int off0 = wrap(j0 - 1 + tid / PX, d.ny) * d.nx + wrap(i0 - 1 + tid % PX, d.nx);
+  const int off1 = p1 < NPOS ? wrap(j0 - 1 + p1 / PX, d.ny) * d.nx + wrap(i0 - 1 + p1 % PX, d.nx) : 0;
   auto load_plane = [&](int slot, int k) {
     if (!HAS_X) return;
-    const int kk = wrap(k, d.nz);
-    for (int idx = tid; idx < C * PY * PX; idx += NT) {
-      const int px = idx % PX;
-      const int py = (idx / PX) % PY;
-      const int j = idx / (PX * PY);
-      const int gi = wrap(i0 - 1 + px, d.nx);
-      const int gj = wrap(j0 - 1 + py, d.ny);
-      pl[((slot * C + j) * PY + py) * PX + px] = x[(long long)j * d.N + kk * plane + (long long)gj * d.nx + gi];
+    const T* xk = x + (long long)wrap(k, d.nz) * plane;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const T* xj = xk + (long long)j * d.N;
+      T* dst = pl + (slot * C + j) * NPOS;
+      dst[tid] = __ldg(xj + off0);
+      if (p1 < NPOS) dst[p1] = __ldg(xj + off1);
     }
   };
 

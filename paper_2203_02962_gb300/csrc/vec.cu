@@ -45,13 +45,26 @@ __device__ double block_sum(double v) {
   return t;
 }
 
-// one CTA per (component, load): mean over the component, then subtract it
-__global__ void __launch_bounds__(1024) sub_mean_kernel(double* x, long long N, long long load_stride) {
-  double* p = x + (long long)blockIdx.y * load_stride + (long long)blockIdx.x * N;
+// mean removal per (component, load): CTA partial sums, then every CTA re-adds the partials of its
+// (component, load) in index order (the same sum in every CTA) and subtracts the mean from its slice
+constexpr int SM_BLOCKS = 2 * 152;
+
+__global__ void mean_partial_kernel(const double* __restrict__ x, long long N, long long load_stride, double* partial) {
+  const double* p = x + (long long)blockIdx.z * load_stride + (long long)blockIdx.y * N;
   double acc = 0.0;
-  for (long long i = threadIdx.x; i < N; i += blockDim.x) acc += p[i];
+  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < N; i += (long long)gridDim.x * VT) acc += p[i];
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0) partial[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void mean_subtract_kernel(double* __restrict__ x, long long N, long long load_stride,
+                                     const double* __restrict__ partial) {
+  const double* pp = partial + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += VT) acc += pp[b];
   const double mean = block_sum(acc) / (double)N;
-  for (long long i = threadIdx.x; i < N; i += blockDim.x) p[i] -= mean;
+  double* p = x + (long long)blockIdx.z * load_stride + (long long)blockIdx.y * N;
+  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < N; i += (long long)gridDim.x * VT) p[i] -= mean;
 }
 
 __global__ void norm2_kernel(const double* __restrict__ x, long long n, long long load_stride, double* partial) {
@@ -84,8 +97,13 @@ cudaError_t launch_add_f2d(const float* x, double* y, double scale, long long n,
   return cudaGetLastError();
 }
 
-cudaError_t launch_sub_mean(double* x, int c, long long N, int n_loads, long long load_stride, cudaStream_t s) {
-  sub_mean_kernel<<<dim3(c, n_loads), 1024, 0, s>>>(x, N, load_stride);
+cudaError_t launch_sub_mean(double* x, int c, long long N, int n_loads, long long load_stride, double* partial,
+                            cudaStream_t s) {
+  const dim3 grid(SM_BLOCKS, c, n_loads);
+  mean_partial_kernel<<<grid, VT, 0, s>>>(x, N, load_stride, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  mean_subtract_kernel<<<grid, VT, 0, s>>>(x, N, load_stride, partial);
   return cudaGetLastError();
 }
 
