@@ -40,7 +40,6 @@ struct fehom_ctx {
   double* mats64 = nullptr; float* mats32 = nullptr;   // [phase][D*D]
   double* iso64 = nullptr; float* iso32 = nullptr;     // [phase][2]
   double* rmats64 = nullptr; double* riso64 = nullptr;  // reference material (one phase)
-  double* moduli_d = nullptr;                           // [phase][m*m]
   double2* tw64[3] = {nullptr, nullptr, nullptr};
   float2* tw32[3] = {nullptr, nullptr, nullptr};
   double* sym64 = nullptr; float* sym32 = nullptr;
@@ -54,7 +53,6 @@ struct fehom_ctx {
   PcgState* st = nullptr;
   RedScratch red{};
   double* tau = nullptr;       // [load][phase][D]
-  double* loads_d = nullptr;   // [load][m]
   double* partial = nullptr;   // general reduction scratch
   size_t partial_cap = 0;
   // captured iteration graphs
@@ -505,8 +503,8 @@ fehom_status set_states(fehom_ctx* ctx, int n_loads, double tol_rel, int max_ite
   return FEHOM_OK;
 }
 
-// b = -D^T W C e for every load (FP64) into `b`
-fehom_status compute_rhs(fehom_ctx* ctx, int n_loads, const double* loads, double* b) {
+// per-phase prestress tau_l = w S P^T C_p e_l of every load, uploaded for the stiffness kernel
+fehom_status upload_tau(fehom_ctx* ctx, int n_loads, const double* loads) {
   const int P = ctx->n_phases, D = ctx->D;
   std::vector<double> tau((size_t)n_loads * P * D);
   for (int l = 0; l < n_loads; ++l)
@@ -516,67 +514,59 @@ fehom_status compute_rhs(fehom_ctx* ctx, int n_loads, const double* loads, doubl
   dfree(ctx->tau);
   CK(cudaMalloc(&ctx->tau, tau.size() * sizeof(double)));
   CK(cudaMemcpyAsync(ctx->tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  return FEHOM_OK;
+}
+
+// y = -D^T W C (e_l + D x_l) for every load (x == NULL: the right-hand side b = -D^T W C e), in FP64,
+// with the fused statistics: y2[l] = ||y_l||^2 and flux[l] = <sigma>_l (Sec. 2 average with the
+// quadrature of Eq. global_sum), recovered from the summed monomial-1 duals as P S^-1 sum T / |Y|.
+// Needs upload_tau for the same loads first.
+fehom_status residual_stats(fehom_ctx* ctx, int n_loads, const double* x, double* y, std::vector<double>* y2,
+                            std::vector<double>* flux) {
   StencilArgs a = stencil_args(ctx, false, n_loads);
-  a.x = nullptr;
-  a.y = b;
+  a.x = x;
+  a.y = y;
   a.tau = ctx->tau;
   a.y_scale = -1.0;
-  CK(launch_stiffness<double>(a, ctx->stream));
+  const int ctas = stiffness_ctas(ctx->d);
+  const int W = 1 + ctx->D;
+  TRY(ensure_partial(ctx, (size_t)n_loads * ctas * W));
+  a.stats = ctx->partial;
+  int got = 0;
+  CK(launch_stiffness<double>(a, ctx->stream, &got));
   count_launch(ctx);
-  return FEHOM_OK;
-}
-
-fehom_status mean_flux(fehom_ctx* ctx, int n_loads, const double* loads_host, const double* u, double* out) {
-  dfree(ctx->loads_d);
-  CK(cudaMalloc(&ctx->loads_d, sizeof(double) * n_loads * ctx->m));
-  CK(cudaMemcpyAsync(ctx->loads_d, loads_host, sizeof(double) * n_loads * ctx->m, cudaMemcpyHostToDevice, ctx->stream));
-  const int blocks_max = 4 * 152;
-  fehom_status st = ensure_partial(ctx, (size_t)n_loads * blocks_max * ctx->m);
-  if (st != FEHOM_OK) return st;
-  MeanFluxArgs a{};
-  a.d = ctx->d;
-  a.u = u;
-  a.ids = ctx->ids;
-  a.moduli = ctx->moduli_d;
-  a.loads = ctx->loads_d;
-  a.n_loads = n_loads;
-  a.m = ctx->m;
-  a.load_stride = (long long)ctx->d.c * ctx->d.N;
-  for (int i = 0; i < 3; ++i) a.h[i] = ctx->h[i];
-  a.partial = ctx->partial;
-  int blocks = 0;
-  CK(launch_mean_flux(a, &blocks, ctx->stream));
-  count_launch(ctx);
-  std::vector<double> hp((size_t)n_loads * blocks * ctx->m);
+  if (got != ctas) FAIL(FEHOM_E_CUDA, "stiffness statistics: CTA count mismatch");
+  std::vector<double> hp((size_t)n_loads * ctas * W);
   CK(cudaMemcpyAsync(hp.data(), ctx->partial, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  double cell_vol = 1.0;
-  for (int i = 0; i < ctx->d.dim; ++i) cell_vol *= ctx->h[i] * (i == 0 ? ctx->d.nx : i == 1 ? ctx->d.ny : ctx->d.nz);
-  for (int l = 0; l < n_loads; ++l)
-    for (int r = 0; r < ctx->m; ++r) {
-      double acc = 0.0;
-      for (int b = 0; b < blocks; ++b) acc += hp[((size_t)l * blocks + b) * ctx->m + r];
-      out[l * ctx->m + r] = acc / cell_vol;
+  const int dim = ctx->d.dim, m = ctx->m, D = ctx->D;
+  const std::vector<double> P = grad_to_flux(dim, ctx->physics);
+  double w, sc[3];
+  kernel_scales(ctx, &w, sc);
+  double cell = 1.0;
+  const int n3[3] = {ctx->d.nx, ctx->d.ny, ctx->d.nz};
+  for (int i = 0; i < dim; ++i) cell *= ctx->h[i] * n3[i];
+  if (y2) y2->assign(n_loads, 0.0);
+  if (flux) flux->assign((size_t)n_loads * m, 0.0);
+  std::vector<double> T(D);
+  for (int l = 0; l < n_loads; ++l) {
+    double yy = 0.0;
+    std::fill(T.begin(), T.end(), 0.0);
+    for (int b = 0; b < ctas; ++b) {
+      const double* pb = &hp[((size_t)l * ctas + b) * W];
+      yy += pb[0];
+      for (int i = 0; i < D; ++i) T[i] += pb[1 + i];
     }
+    if (y2) (*y2)[l] = yy;
+    if (flux)
+      for (int I = 0; I < m; ++I) {
+        double v = 0.0;
+        for (int q = 0; q < D; ++q) v += P[I * D + q] * T[q] / sc[q % dim];
+        (*flux)[(size_t)l * m + I] = v / cell;
+      }
+  }
   return FEHOM_OK;
 }
-
-fehom_status norms2(fehom_ctx* ctx, int n_loads, const double* v, std::vector<double>& out) {
-  fehom_status st = ensure_partial(ctx, (size_t)n_loads * 256);
-  if (st != FEHOM_OK) return st;
-  int blocks = 0;
-  const long long n = (long long)ctx->d.c * ctx->d.N;
-  CK(launch_norm2(v, n, n_loads, n, ctx->partial, &blocks, ctx->stream));
-  count_launch(ctx);
-  std::vector<double> hp((size_t)n_loads * blocks);
-  CK(cudaMemcpyAsync(hp.data(), ctx->partial, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  out.assign(n_loads, 0.0);
-  for (int l = 0; l < n_loads; ++l)
-    for (int b = 0; b < blocks; ++b) out[l] += hp[(size_t)l * blocks + b];
-  return FEHOM_OK;
-}
-
 
 }  // namespace
 
@@ -634,13 +624,13 @@ void fehom_destroy(fehom_ctx* ctx) {
       for (int k = 0; k < FEHOM_K_COUNT; ++k)
         for (int j = 0; j < 2; ++j) cudaEventDestroy(ctx->ev[i][k][j]);
   dfree(ctx->ids); dfree(ctx->mats64); dfree(ctx->mats32); dfree(ctx->iso64); dfree(ctx->iso32);
-  dfree(ctx->rmats64); dfree(ctx->riso64); dfree(ctx->moduli_d);
+  dfree(ctx->rmats64); dfree(ctx->riso64);
   for (int i = 0; i < 3; ++i) { dfree(ctx->tw64[i]); dfree(ctx->tw32[i]); }
   dfree(ctx->sym64); dfree(ctx->sym32);
   dfree(ctx->x64); dfree(ctx->r64); dfree(ctx->p64); dfree(ctx->ap64); dfree(ctx->b64); dfree(ctx->spec64);
   dfree(ctx->x32); dfree(ctx->r32); dfree(ctx->p32); dfree(ctx->ap32); dfree(ctx->spec32);
   dfree(ctx->st); dfree(ctx->red.partial); dfree(ctx->red.count);
-  dfree(ctx->tau); dfree(ctx->loads_d); dfree(ctx->partial);
+  dfree(ctx->tau); dfree(ctx->partial);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   cudaSetDevice(prev);
   delete ctx;
@@ -734,8 +724,6 @@ static fehom_status setup_impl(fehom_ctx* ctx, int elem, int physics, const int6
   grad_material(ctx, ctx->cref.data(), rm.data());
   CK(cudaMalloc(&ctx->rmats64, rm.size() * sizeof(double)));
   CK(cudaMemcpyAsync(ctx->rmats64, rm.data(), rm.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  CK(cudaMalloc(&ctx->moduli_d, ctx->moduli.size() * sizeof(double)));
-  CK(cudaMemcpyAsync(ctx->moduli_d, ctx->moduli.data(), ctx->moduli.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   // isotropic fast path (hex8 elasticity on a cubic grid)
   if (elem == FEHOM_HEX8_3D && physics == FEHOM_ELASTIC && ctx->h[0] == ctx->h[1] && ctx->h[1] == ctx->h[2]) {
     bool all = true;
@@ -921,9 +909,8 @@ fehom_status fehom_apply_stiffness(fehom_ctx* ctx, const void* x, void* y, int p
 
 fehom_status fehom_rhs(fehom_ctx* ctx, const double* e, double* b) {
   if (!ctx || !e || !b) return FEHOM_E_INVALID;
-  TRY(compute_rhs(ctx, 1, e, b));
-  CK(cudaStreamSynchronize(ctx->stream));
-  return FEHOM_OK;
+  TRY(upload_tau(ctx, 1, e));
+  return residual_stats(ctx, 1, nullptr, b, nullptr, nullptr);
 }
 
 fehom_status fehom_apply_precond(fehom_ctx* ctx, const void* r, void* z, int precision) {
@@ -950,34 +937,22 @@ fehom_status fehom_get_symbol_inverse(fehom_ctx* ctx, double* out) {
 
 fehom_status fehom_mean_flux(fehom_ctx* ctx, const double* e, const double* u, double* out) {
   if (!ctx || !e || !u || !out) return FEHOM_E_INVALID;
-  return mean_flux(ctx, 1, e, u, out);
+  TRY(upload_tau(ctx, 1, e));
+  std::vector<double> flux;
+  TRY(residual_stats(ctx, 1, u, ctx->ap64, nullptr, &flux));
+  std::memcpy(out, flux.data(), sizeof(double) * ctx->m);
+  return FEHOM_OK;
 }
 
+// fields (mean removed), <sigma> and C_eff of a finished solve; flux: the mean fluxes of the final x
 static fehom_status finish_outputs(fehom_ctx* ctx, int n_loads, const double* loads, double* fluct_out,
                                    int fluct_on_device, double* mean_flux_out, double* c_eff_out,
-                                   std::vector<double>& rel2) {
+                                   const std::vector<double>& flux) {
   cudaStream_t s = ctx->stream;
   const long long cN = (long long)ctx->d.c * ctx->d.N;
   TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
   CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
   count_launch(ctx, 2);
-  // true FP64 residual b - K x
-  TRY(compute_rhs(ctx, n_loads, loads, ctx->b64));
-  std::vector<double> bn;
-  TRY(norms2(ctx, n_loads, ctx->b64, bn));
-  StencilArgs a = stencil_args(ctx, false, n_loads);
-  a.x = ctx->x64;
-  a.y = ctx->ap64;
-  CK(launch_stiffness<double>(a, s));
-  count_launch(ctx);
-  CK(launch_axpby_d(ctx->ap64, ctx->b64, -1.0, 1.0, cN * n_loads, s));
-  count_launch(ctx);
-  std::vector<double> rn;
-  TRY(norms2(ctx, n_loads, ctx->b64, rn));
-  rel2.resize(n_loads);
-  for (int l = 0; l < n_loads; ++l) rel2[l] = bn[l] > 0 ? std::sqrt(rn[l] / bn[l]) : 0.0;
-  std::vector<double> flux((size_t)n_loads * ctx->m);
-  TRY(mean_flux(ctx, n_loads, loads, ctx->x64, flux.data()));
   if (mean_flux_out) std::memcpy(mean_flux_out, flux.data(), flux.size() * sizeof(double));
   if (c_eff_out && n_loads == ctx->m) {
     // C_eff = S E^-1 with S[:, l] = flux_l, E[:, l] = e_l  ->  solve E^T C_eff^T = S^T
@@ -1023,16 +998,17 @@ static fehom_status finish_outputs(fehom_ctx* ctx, int n_loads, const double* lo
 }
 
 static fehom_status solve_fp64(fehom_ctx* ctx, int n_loads, const double* loads, double tol, const double* x0,
-                               std::vector<PcgState>& hs) {
+                               std::vector<PcgState>& hs, std::vector<double>& flux, std::vector<double>& rel2) {
   cudaStream_t s = ctx->stream;
   const long long cN = (long long)ctx->d.c * ctx->d.N;
-  TRY(compute_rhs(ctx, n_loads, loads, ctx->r64));
-  double bn = -1.0;
+  TRY(upload_tau(ctx, n_loads, loads));
+  std::vector<double> bn2, rn2;
+  TRY(residual_stats(ctx, n_loads, nullptr, ctx->b64, &bn2, nullptr));  // b = -D^T W C e
   if (x0) {
     // <b, K_ref^+ b> first (normalisation of the stopping test), then r0 = b - K x0
     TRY(set_states(ctx, n_loads, tol, ctx->opt.max_iter, -1.0));
-    CK(cudaMemcpyAsync(ctx->b64, ctx->r64, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
-    TRY(pcg_init<double>(ctx, n_loads, ctx->b64, ctx->p64));
+    CK(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
+    TRY(pcg_init<double>(ctx, n_loads, ctx->r64, ctx->p64));
     std::vector<PcgState> h0(n_loads);
     CK(cudaMemcpyAsync(h0.data(), ctx->st, sizeof(PcgState) * n_loads, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1040,13 +1016,7 @@ static fehom_status solve_fp64(fehom_ctx* ctx, int n_loads, const double* loads,
     TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
     CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
     count_launch(ctx, 2);
-    StencilArgs a = stencil_args(ctx, false, n_loads);
-    a.x = ctx->x64;
-    a.y = ctx->ap64;
-    CK(launch_stiffness<double>(a, s));
-    count_launch(ctx);
-    CK(launch_axpby_d(ctx->ap64, ctx->r64, -1.0, 1.0, cN * n_loads, s));
-    count_launch(ctx);
+    TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->r64, nullptr, nullptr));
     std::vector<PcgState> hs0(n_loads);
     for (int l = 0; l < n_loads; ++l) {
       std::memset(&hs0[l], 0, sizeof(PcgState));
@@ -1057,21 +1027,29 @@ static fehom_status solve_fp64(fehom_ctx* ctx, int n_loads, const double* loads,
     }
     CK(cudaMemcpyAsync(ctx->st, hs0.data(), sizeof(PcgState) * n_loads, cudaMemcpyHostToDevice, s));
   } else {
+    CK(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * n_loads, s));
-    TRY(set_states(ctx, n_loads, tol, ctx->opt.max_iter, bn));
+    TRY(set_states(ctx, n_loads, tol, ctx->opt.max_iter, -1.0));
   }
   TRY(pcg_init<double>(ctx, n_loads, ctx->r64, ctx->p64));
-  return run_iterations<double>(ctx, n_loads, ctx->x64, ctx->r64, ctx->p64, ctx->ap64, ctx->opt.max_iter, hs);
+  TRY(run_iterations<double>(ctx, n_loads, ctx->x64, ctx->r64, ctx->p64, ctx->ap64, ctx->opt.max_iter, hs));
+  // true FP64 residual of the final iterate, fused with the volume averages
+  TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->ap64, &rn2, &flux));
+  rel2.resize(n_loads);
+  for (int l = 0; l < n_loads; ++l) rel2[l] = bn2[l] > 0 ? std::sqrt(rn2[l] / bn2[l]) : 0.0;
+  return FEHOM_OK;
 }
 
 // FP32 PCG inside FP64 iterative refinement: r = b - K x (FP64), K d = r in FP32 to inner_tol, x += d.
 static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads, double tol, const double* x0,
                                 std::vector<PcgState>& hs, std::vector<int>& outer_it, std::vector<int>& inner_it,
-                                std::vector<double>& relM) {
+                                std::vector<double>& relM, std::vector<double>& flux, std::vector<double>& rel2) {
   cudaStream_t s = ctx->stream;
   TRY(grow32(ctx, n_loads));
   const long long cN = (long long)ctx->d.c * ctx->d.N;
-  TRY(compute_rhs(ctx, n_loads, loads, ctx->b64));
+  TRY(upload_tau(ctx, n_loads, loads));
+  std::vector<double> bn2, rn2;
+  TRY(residual_stats(ctx, n_loads, nullptr, ctx->b64, &bn2, nullptr));  // b = -D^T W C e
   if (x0) {
     CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
     TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
@@ -1087,18 +1065,15 @@ static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads
   relM.assign(n_loads, 1.0);
   hs.assign(n_loads, PcgState{});
   int total_inner = 0;
+  bool stats_current = false;  // flux / rn2 belong to the current x
   const int max_outer = 60;
   for (int outer = 0; outer < max_outer; ++outer) {
-    // r = b - K x in FP64
-    CK(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
+    const double* r64 = ctx->b64;
     if (outer > 0 || x0) {
-      StencilArgs a = stencil_args(ctx, false, n_loads);
-      a.x = ctx->x64;
-      a.y = ctx->ap64;
-      CK(launch_stiffness<double>(a, s));
-      count_launch(ctx);
-      CK(launch_axpby_d(ctx->ap64, ctx->r64, -1.0, 1.0, cN * n_loads, s));
-      count_launch(ctx);
+      // true residual r = b - K x = -D^T W C (e + D x) in FP64, with ||r||^2 and <sigma>
+      TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->r64, &rn2, &flux));
+      r64 = ctx->r64;
+      stats_current = true;
     }
     if (outer == 0 && x0) {
       // normalisation <b, K_ref^+ b> from b itself
@@ -1111,7 +1086,7 @@ static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads
       CK(cudaStreamSynchronize(s));
       for (int l = 0; l < n_loads; ++l) bnorm2[l] = h0[l].rz_init;
     }
-    CK(launch_cast_d2f(ctx->r64, ctx->r32, 1.0, cN * n_loads, s));
+    CK(launch_cast_d2f(r64, ctx->r32, 1.0, cN * n_loads, s));
     count_launch(ctx);
     CK(cudaMemsetAsync(ctx->x32, 0, sizeof(float) * cN * n_loads, s));
     const int remaining = std::max(1, ctx->opt.max_iter - total_inner);
@@ -1151,10 +1126,14 @@ static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads
     total_inner += mx;
     CK(launch_add_f2d(ctx->x32, ctx->x64, 1.0, cN * n_loads, s));
     count_launch(ctx);
+    stats_current = false;
   }
+  if (!stats_current) TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->ap64, &rn2, &flux));
+  rel2.resize(n_loads);
   for (int l = 0; l < n_loads; ++l) {
     hs[l].iter = inner_it[l];
     hs[l].state = done[l] ? ST_DONE : ST_MAXIT;
+    rel2[l] = bn2[l] > 0 ? std::sqrt(rn2[l] / bn2[l]) : 0.0;
   }
   return FEHOM_OK;
 }
@@ -1179,8 +1158,9 @@ fehom_status fehom_solve(fehom_ctx* ctx, int n_loads, const double* loads, doubl
   std::vector<double> relM(n_loads, 0.0);
   fehom_status st;
   const bool mixed = ctx->opt.precision == FEHOM_MIXED;
-  if (mixed) st = solve_mixed(ctx, n_loads, loads, tol, x0, hs, outer_it, inner_it, relM);
-  else st = solve_fp64(ctx, n_loads, loads, tol, x0, hs);
+  std::vector<double> flux, rel2;
+  if (mixed) st = solve_mixed(ctx, n_loads, loads, tol, x0, hs, outer_it, inner_it, relM, flux, rel2);
+  else st = solve_fp64(ctx, n_loads, loads, tol, x0, hs, flux, rel2);
   if (st != FEHOM_OK) return st;
   CK(cudaEventRecord(e1, s));
   CK(cudaEventSynchronize(e1));
@@ -1188,8 +1168,7 @@ fehom_status fehom_solve(fehom_ctx* ctx, int n_loads, const double* loads, doubl
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  std::vector<double> rel2;
-  TRY(finish_outputs(ctx, n_loads, loads, fluct_out, fluct_on_device, mean_flux_out, c_eff_out, rel2));
+  TRY(finish_outputs(ctx, n_loads, loads, fluct_out, fluct_on_device, mean_flux_out, c_eff_out, flux));
   bool brk = false, notconv = false;
   for (int l = 0; l < n_loads; ++l) {
     if (hs[l].state == ST_BREAK) brk = true;

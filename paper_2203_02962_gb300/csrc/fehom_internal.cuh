@@ -72,24 +72,18 @@ struct StencilArgs {
   // fused PCG reduction <x, y> -> pAp, alpha = rz / pAp (nullptr = off)
   PcgState* st;
   RedScratch red;
+  // fused statistics (nullptr = off): per load and CTA, sum y^2 and the sum of the monomial-1 duals
+  // of the CTA's elements, [load][cta][1 + c * dim] doubles
+  double* stats;
 };
 
-// Launches y = D^T W C (D x + e) for every load (blockIdx.z).  T = double or float.
+// Launches y = D^T W C (D x + e) for every load (blockIdx.z).  T = double or float.  ctas (optional)
+// receives the number of CTAs per load (the stride of the statistics partials).
 template <typename T>
-cudaError_t launch_stiffness(const StencilArgs& a, cudaStream_t s);
+cudaError_t launch_stiffness(const StencilArgs& a, cudaStream_t s, int* ctas = nullptr);
 
-struct MeanFluxArgs {
-  Dims d;
-  const double* u;      // [load][c][N] or nullptr
-  const uint8_t* ids;
-  const double* moduli; // [phase][m*m] Mandel / conductivity matrices (FP64)
-  const double* loads;  // [load][m] (device)
-  int n_loads, m;
-  long long load_stride;
-  double h[3];
-  double* partial;      // [load][blocks][m]
-};
-cudaError_t launch_mean_flux(const MeanFluxArgs& a, int* blocks_out, cudaStream_t s);
+// CTAs per load of a stiffness launch (the stride of the statistics partials)
+int stiffness_ctas(const Dims& d);
 
 cudaError_t launch_phase_histogram(const uint8_t* ids, long long N, unsigned long long* hist,
                                    cudaStream_t s);
@@ -153,15 +147,10 @@ cudaError_t make_twiddles(int L, double2** d64, float2** d32);
 // ------------------------------------------------------------------------------------------------
 // vec.cu: small vector kernels used by the solve driver
 // ------------------------------------------------------------------------------------------------
-cudaError_t launch_fill(void* p, long long n, int bytes_per_elem, cudaStream_t s);  // zero
-cudaError_t launch_axpby_d(const double* x, double* y, double a, double b, long long n, cudaStream_t s);
 cudaError_t launch_cast_d2f(const double* x, float* y, double scale, long long n, cudaStream_t s);
 cudaError_t launch_add_f2d(const float* x, double* y, double scale, long long n, cudaStream_t s);
 // removes the mean of every (component, load); partial: scratch of n_loads * c * 304 doubles (two launches)
 cudaError_t launch_sub_mean(double* x, int c, long long N, int n_loads, long long load_stride, double* partial,
                             cudaStream_t s);
-// per-load sum of squares and sum (FP64 partials -> host)
-cudaError_t launch_norm2(const double* x, long long n, int n_loads, long long load_stride, double* partial,
-                         int* blocks_out, cudaStream_t s);
 
 }  // namespace fehom

@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 namespace fehom {
 namespace {
@@ -142,10 +143,29 @@ __device__ __forceinline__ void contract_iso(const T (&g)[3][3], T lam, T mu, T 
 }
 
 // Hex8 element: nodal values u[j][corner] (corner = a + 2b + 4c) -> forces f[j][corner].
-template <typename T, int C, bool ISO, bool HAS_E>
+// Without a nodal field (HAS_X false: the right-hand side -D^T W C e) only the monomial-1 dual
+// T1 = tau is nonzero and the forces reduce to f_abc = xi_a tau_x + eta_b tau_y + zeta_c tau_z.
+// t1o receives the monomial-1 dual (Chat g_1 + tau), whose sum over elements is |Y| S P^T <sigma>.
+template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E>
 __device__ __forceinline__ void hex8_element(const T (&u)[C][8], const T* __restrict__ Ch,
                                              const T* __restrict__ iso, const double* __restrict__ tau,
-                                             T (&f)[C][8]) {
+                                             T (&f)[C][8], T (&t1o)[C][3]) {
+  if constexpr (!HAS_X) {
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const T Q1 = HAS_E ? T(tau[j * 3 + 0]) : T(0);
+      const T Q2 = HAS_E ? T(tau[j * 3 + 1]) : T(0);
+      const T Q3 = HAS_E ? T(tau[j * 3 + 2]) : T(0);
+      t1o[j][0] = Q1;
+      t1o[j][1] = Q2;
+      t1o[j][2] = Q3;
+      const T a0 = -Q2 - Q3, a1 = Q2 - Q3, a2 = Q3 - Q2, a3 = Q2 + Q3;  // eta_b Q2 + zeta_c Q3, bc = b + 2c
+      f[j][0] = a0 - Q1; f[j][1] = a0 + Q1;
+      f[j][2] = a1 - Q1; f[j][3] = a1 + Q1;
+      f[j][4] = a2 - Q1; f[j][5] = a2 + Q1;
+      f[j][6] = a3 - Q1; f[j][7] = a3 + Q1;
+    }
+  } else {
   // forward butterflies: q[j][n], n = 1..7 (xi, eta, zeta, xi eta, eta zeta, xi zeta, xi eta zeta)
   T q1[C], q2[C], q3[C], q4[C], q5[C], q6[C], q7[C];
 #pragma unroll
@@ -207,6 +227,10 @@ __device__ __forceinline__ void hex8_element(const T (&u)[C][8], const T* __rest
 #pragma unroll
       for (int i = 0; i < 3; ++i) t1[j][i] += T(tau[j * 3 + i]);
   }
+#pragma unroll
+  for (int j = 0; j < C; ++j)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t1o[j][i] = t1[j][i];
   // dual modal forces and transposed butterflies
 #pragma unroll
   for (int j = 0; j < C; ++j) {
@@ -231,21 +255,42 @@ __device__ __forceinline__ void hex8_element(const T (&u)[C][8], const T* __rest
       f[j][2 * bc + 1] = s[bc] + d[bc];
     }
   }
+  }  // HAS_X
+}
+
+// ------------------------------------------------------------------------------------------------
+// reductions fused into the stiffness apply
+//   RED_NONE  y only
+//   RED_PCG   <x, y> -> pAp and alpha = rz / pAp in the load's PCG state (last CTA, fixed order)
+//   RED_STATS per CTA: sum y^2 over its nodes and the sum of the monomial-1 duals over its elements
+//             (partials [load][cta][1 + D], reduced on the host in index order)
+// ------------------------------------------------------------------------------------------------
+enum { RED_NONE = 0, RED_PCG = 1, RED_STATS = 2 };
+
+__device__ void pcg_alpha_update(PcgState& s, double total) {
+  s.pAp = total;
+  if (!(total > 0.0) || !isfinite(total)) {
+    s.state = ST_BREAK;
+    s.alpha = 0.0;
+  } else {
+    s.alpha = s.rz / total;
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
 // 3-D hex8 kernel
 // ------------------------------------------------------------------------------------------------
-template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, bool DOT>
+template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED>
 __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NPOS = PY * PX;
   T* pl = reinterpret_cast<T*>(smem_raw);                 // [2][C][PY][PX]
-  T* F = pl + 2 * C * PY * PX;                             // [4 bottom + 4 top][C][EY][EX]
+  T* F = pl + 2 * C * NPOS;                                // [4 bottom + 4 top][C][EY][EX]
   __shared__ double red_sh[32];
 
   const Dims d = a.d;
   const int load = blockIdx.z;
-  if (DOT && a.st != nullptr && a.st[load].state != ST_RUN) return;
+  if (RED == RED_PCG && a.st != nullptr && a.st[load].state != ST_RUN) return;
 
   const int tiles_x = (d.nx + BX - 1) / BX;
   const int i0 = (blockIdx.x % tiles_x) * BX;
@@ -263,41 +308,49 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
 
   // Each thread stages the same (at most two) halo positions of every node plane: their in-plane
   // offsets (periodic wrap included) are computed once, so the z march does no index division.
-  constexpr int NPOS = PY * PX;
   static_assert(NPOS <= 2 * NT, "two halo positions per thread");
   const int p1 = tid + NT;
   const int off0 = wrap(j0 - 1 + tid / PX, d.ny) * d.nx + wrap(i0 - 1 + tid % PX, d.nx);
   const int off1 = p1 < NPOS ? wrap(j0 - 1 + p1 / PX, d.ny) * d.nx + wrap(i0 - 1 + p1 % PX, d.nx) : 0;
-  auto load_plane = [&](int slot, int k) {
-    if (!HAS_X) return;
-    const T* xk = x + (long long)wrap(k, d.nz) * plane;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      const T* xj = xk + (long long)j * d.N;
-      T* dst = pl + (slot * C + j) * NPOS;
-      dst[tid] = __ldg(xj + off0);
-      if (p1 < NPOS) dst[p1] = __ldg(xj + off1);
-    }
-  };
 
   // node-thread state: top-corner contributions carried to the next plane
   const int ni = tid % BX, nj = tid / BX;  // valid node thread when tid < BX * BY
   const bool node_thread = tid < BX * BY && (i0 + ni) < d.nx && (j0 + nj) < d.ny;
+  const long long node_off = (long long)(j0 + nj) * d.nx + i0 + ni;
   T carry[C];
 #pragma unroll
   for (int j = 0; j < C; ++j) carry[j] = T(0);
-  double dot = 0.0;
+  double acc_y = 0.0;                  // RED_PCG: <x, y>;  RED_STATS: sum y^2
+  double acc_t[3 * C];                 // RED_STATS: sum of the monomial-1 duals of owned elements
+#pragma unroll
+  for (int i = 0; i < 3 * C; ++i) acc_t[i] = 0.0;
 
   const int ei = tid % EX, ej = tid / EX;  // element thread
   const bool elem_thread = tid < NE;
-  const int gie = wrap(i0 - 1 + ei, d.nx);
-  const int gje = wrap(j0 - 1 + ej, d.ny);
+  const int elem_off = wrap(j0 - 1 + ej, d.ny) * d.nx + wrap(i0 - 1 + ei, d.nx);
+  const bool owner = elem_thread && ei >= 1 && ej >= 1 && i0 + ei - 1 < d.nx && j0 + ej - 1 < d.ny;
 
-  int cur = 0;
-  load_plane(cur, k0 - 1);
-  for (int k = k0 - 1; k < k1; ++k) {
-    // element layer k spans node planes k (slot cur) and k + 1 (slot cur ^ 1)
-    load_plane(cur ^ 1, k + 1);
+  // plane index kz (wrapped) of node plane k, kept incrementally
+  int kz = wrap(k0 - 1, d.nz);
+  auto load_plane = [&](auto slot_c, int kzp) {
+    if constexpr (HAS_X) {
+      constexpr int slot = decltype(slot_c)::value;
+      const T* xk = x + (long long)kzp * plane;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const T* xj = xk + (long long)j * d.N;
+        T* dst = pl + (slot * C + j) * NPOS;
+        dst[tid] = __ldg(xj + off0);
+        if (p1 < NPOS) dst[p1] = __ldg(xj + off1);
+      }
+    }
+  };
+  auto next = [&](int z) { return z + 1 == d.nz ? 0 : z + 1; };
+
+  // element layer k spans node planes k (slot CUR) and k + 1 (slot CUR ^ 1); kzc = wrap(k)
+  auto layer = [&](auto cur_c, int k, int kzc) {
+    constexpr int CUR = decltype(cur_c)::value;
+    load_plane(std::integral_constant<int, CUR ^ 1>{}, next(kzc));
     __syncthreads();
     if (elem_thread) {
       T u[C][8];
@@ -306,62 +359,81 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
 #pragma unroll
         for (int cn = 0; cn < 8; ++cn) {
           const int aa = cn & 1, bb = (cn >> 1) & 1, cc = cn >> 2;
-          u[j][cn] = HAS_X ? pl[(((cur ^ cc) * C + j) * PY + ej + bb) * PX + ei + aa] : T(0);
+          u[j][cn] = HAS_X ? pl[((CUR ^ cc) * C + j) * NPOS + (ej + bb) * PX + ei + aa] : T(0);
         }
-      const int kk = wrap(k, d.nz);
-      const int ph = a.ids ? a.ids[(long long)kk * plane + (long long)gje * d.nx + gie] : 0;
-      T f[C][8];
-      hex8_element<T, C, ISO, HAS_E>(u, mats + (long long)ph * (9 * C * C), isot + 2 * ph,
-                                     HAS_E ? tau + ph * (3 * C) : nullptr, f);
+      const int ph = a.ids ? a.ids[(long long)kzc * plane + elem_off] : 0;
+      T f[C][8], t1[C][3];
+      hex8_element<T, C, ISO, HAS_X, HAS_E>(u, mats + (long long)ph * (9 * C * C), isot + 2 * ph,
+                                            HAS_E ? tau + ph * (3 * C) : nullptr, f, t1);
 #pragma unroll
       for (int j = 0; j < C; ++j)
 #pragma unroll
-        for (int cn = 0; cn < 8; ++cn) F[((cn * C + j) * EY + ej) * EX + ei] = f[j][cn];
+        for (int cn = 0; cn < 8; ++cn) F[(cn * C + j) * NE + ej * EX + ei] = f[j][cn];
+      if (RED == RED_STATS && owner && k >= k0) {
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) acc_t[j * 3 + i] += (double)t1[j][i];
+      }
     }
     __syncthreads();
     if (node_thread) {
       // node (i, j) of plane k: bottom corners (c = 0) of layer k from elements (i-1..i, j-1..j)
       // plus the carried top corners of layer k-1; then carry the top corners of layer k.
+      const int e00 = nj * EX + ni;
 #pragma unroll
       for (int j = 0; j < C; ++j) {
-        T bot = F[((3 * C + j) * EY + nj) * EX + ni]          // corner (1,1,0) of element (i-1, j-1)
-              + F[((2 * C + j) * EY + nj) * EX + ni + 1]      // corner (0,1,0) of element (i, j-1)
-              + F[((1 * C + j) * EY + nj + 1) * EX + ni]      // corner (1,0,0) of element (i-1, j)
-              + F[((0 * C + j) * EY + nj + 1) * EX + ni + 1]; // corner (0,0,0) of element (i, j)
-        T top = F[((7 * C + j) * EY + nj) * EX + ni]
-              + F[((6 * C + j) * EY + nj) * EX + ni + 1]
-              + F[((5 * C + j) * EY + nj + 1) * EX + ni]
-              + F[((4 * C + j) * EY + nj + 1) * EX + ni + 1];
+        const T bot = F[(3 * C + j) * NE + e00]            // corner (1,1,0) of element (i-1, j-1)
+                    + F[(2 * C + j) * NE + e00 + 1]        // corner (0,1,0) of element (i, j-1)
+                    + F[(1 * C + j) * NE + e00 + EX]       // corner (1,0,0) of element (i-1, j)
+                    + F[(0 * C + j) * NE + e00 + EX + 1];  // corner (0,0,0) of element (i, j)
+        const T top = F[(7 * C + j) * NE + e00] + F[(6 * C + j) * NE + e00 + 1] +
+                      F[(5 * C + j) * NE + e00 + EX] + F[(4 * C + j) * NE + e00 + EX + 1];
         if (k >= k0) {
           const T val = T(a.y_scale) * (carry[j] + bot);
-          const long long gidx = (long long)j * d.N + (long long)k * plane + (long long)(j0 + nj) * d.nx + i0 + ni;
-          y[gidx] = val;
-          if (DOT) dot += (double)val * (double)pl[((cur * C + j) * PY + nj + 1) * PX + ni + 1];
+          y[(long long)j * d.N + (long long)k * plane + node_off] = val;
+          if (RED == RED_PCG) acc_y += (double)val * (double)pl[(CUR * C + j) * NPOS + (nj + 1) * PX + ni + 1];
+          if (RED == RED_STATS) acc_y += (double)val * (double)val;
         }
         carry[j] = top;
       }
     }
-    cur ^= 1;
-    // the next iteration overwrites slot cur^1 (old plane k) only after its __syncthreads
+    // the next layer overwrites this layer's bottom plane only after its first barrier
     __syncthreads();
+  };
+
+  load_plane(std::integral_constant<int, 0>{}, kz);
+  int k = k0 - 1;
+  while (k < k1) {
+    layer(std::integral_constant<int, 0>{}, k, kz);
+    kz = next(kz);
+    ++k;
+    if (k >= k1) break;
+    layer(std::integral_constant<int, 1>{}, k, kz);
+    kz = next(kz);
+    ++k;
   }
-  if (DOT) {
-    const double part = block_sum(dot, red_sh);
+
+  if (RED == RED_PCG) {
+    const double part = block_sum(acc_y, red_sh);
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     double total;
     if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load, nblk,
                          bid, red_sh, &total)) {
-      if (threadIdx.x == 0) {
-        PcgState& s = a.st[load];
-        s.pAp = total;
-        if (!(total > 0.0) || !isfinite(total)) {
-          s.state = ST_BREAK;
-          s.alpha = 0.0;
-        } else {
-          s.alpha = s.rz / total;
-        }
-      }
+      if (threadIdx.x == 0) pcg_alpha_update(a.st[load], total);
+    }
+  }
+  if (RED == RED_STATS) {
+    const int nblk = gridDim.x * gridDim.y;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    double* out = a.stats + ((long long)load * nblk + bid) * (1 + 3 * C);
+    const double ty = block_sum(acc_y, red_sh);
+    if (threadIdx.x == 0) out[0] = ty;
+#pragma unroll
+    for (int i = 0; i < 3 * C; ++i) {
+      const double t = block_sum(acc_t[i], red_sh);
+      if (threadIdx.x == 0) out[1 + i] = t;
     }
   }
 }
@@ -369,9 +441,11 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
 // ------------------------------------------------------------------------------------------------
 // 2-D pixel kernels (P1 triangles, Q1)
 // ------------------------------------------------------------------------------------------------
+// t1o receives the sum of the quadrature-point duals that carry the constant strain (both triangles
+// for P1, the monomial-1 dual for Q1): their sum over elements is |Y| S P^T <sigma>.
 template <typename T, int C, int ELEM, bool HAS_E>
 __device__ __forceinline__ void pixel_element(const T (&u)[C][4], const T* __restrict__ Ch,
-                                              const double* __restrict__ tau, T (&f)[C][4]) {
+                                              const double* __restrict__ tau, T (&f)[C][4], T (&t1o)[C][2]) {
   constexpr int D = 2 * C;
   // corners: 0 = (0,0), 1 = (1,0), 2 = (0,1), 3 = (1,1); g[j][dir] = raw difference / modal coefficient
   auto contract = [&](const T (&g)[C][2], T w, T (&out)[C][2], int mask) {
@@ -410,6 +484,10 @@ __device__ __forceinline__ void pixel_element(const T (&u)[C][4], const T* __res
         }
     }
 #pragma unroll
+    for (int j = 0; j < C; ++j)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) t1o[j][i] = tA[j][i] + tB[j][i];
+#pragma unroll
     for (int j = 0; j < C; ++j) {
       f[j][0] = -tA[j][0] - tB[j][1];
       f[j][1] = tA[j][0] - tA[j][1];
@@ -439,6 +517,10 @@ __device__ __forceinline__ void pixel_element(const T (&u)[C][4], const T* __res
         for (int i = 0; i < 2; ++i) t1[j][i] += T(tau[j * 2 + i]);
     }
 #pragma unroll
+    for (int j = 0; j < C; ++j)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) t1o[j][i] = t1[j][i];
+#pragma unroll
     for (int j = 0; j < C; ++j) {
       const T Q1 = t1[j][0], Q2 = t1[j][1], Q3 = tx[j][1] + ty[j][0];
       // transposed: d0 = Q1 - Q3, d1 = Q1 + Q3, s0 = -Q2, s1 = Q2
@@ -454,7 +536,7 @@ __device__ __forceinline__ void pixel_element(const T (&u)[C][4], const T* __res
 constexpr int BY2 = 8;  // 2-D tile: BX x BY2 nodes
 constexpr int PY2 = BY2 + 2, EY2 = BY2 + 1, NE2 = EX * EY2, NT2 = ((NE2 + 31) / 32) * 32;
 
-template <typename T, int C, int ELEM, bool HAS_X, bool HAS_E, bool DOT>
+template <typename T, int C, int ELEM, bool HAS_X, bool HAS_E, int RED>
 __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* pl = reinterpret_cast<T*>(smem_raw);  // [C][PY2][PX]
@@ -462,7 +544,7 @@ __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
   __shared__ double red_sh[32];
   const Dims d = a.d;
   const int load = blockIdx.z;
-  if (DOT && a.st != nullptr && a.st[load].state != ST_RUN) return;
+  if (RED == RED_PCG && a.st != nullptr && a.st[load].state != ST_RUN) return;
   const int tiles_x = (d.nx + BX - 1) / BX;
   const int i0 = (blockIdx.x % tiles_x) * BX;
   const int j0 = (blockIdx.x / tiles_x) * BY2;
@@ -479,6 +561,9 @@ __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
   }
   __syncthreads();
   const int ei = tid % EX, ej = tid / EX;
+  double acc_t[2 * C];
+#pragma unroll
+  for (int i = 0; i < 2 * C; ++i) acc_t[i] = 0.0;
   if (tid < NE2) {
     T u[C][4];
 #pragma unroll
@@ -487,15 +572,21 @@ __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
       for (int cn = 0; cn < 4; ++cn)
         u[j][cn] = HAS_X ? pl[(j * PY2 + ej + (cn >> 1)) * PX + ei + (cn & 1)] : T(0);
     const int ph = a.ids ? a.ids[(long long)wrap(j0 - 1 + ej, d.ny) * d.nx + wrap(i0 - 1 + ei, d.nx)] : 0;
-    T f[C][4];
-    pixel_element<T, C, ELEM, HAS_E>(u, mats + (long long)ph * (4 * C * C), HAS_E ? tau + ph * (2 * C) : nullptr, f);
+    T f[C][4], t1[C][2];
+    pixel_element<T, C, ELEM, HAS_E>(u, mats + (long long)ph * (4 * C * C), HAS_E ? tau + ph * (2 * C) : nullptr, f, t1);
 #pragma unroll
     for (int j = 0; j < C; ++j)
 #pragma unroll
       for (int cn = 0; cn < 4; ++cn) F[((cn * C + j) * EY2 + ej) * EX + ei] = f[j][cn];
+    if (RED == RED_STATS && ei >= 1 && ej >= 1 && i0 + ei - 1 < d.nx && j0 + ej - 1 < d.ny) {
+#pragma unroll
+      for (int j = 0; j < C; ++j)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) acc_t[j * 2 + i] += (double)t1[j][i];
+    }
   }
   __syncthreads();
-  double dot = 0.0;
+  double acc_y = 0.0;
   const int ni = tid % BX, nj = tid / BX;
   if (tid < BX * BY2 && i0 + ni < d.nx && j0 + nj < d.ny) {
 #pragma unroll
@@ -504,24 +595,26 @@ __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
                   F[((1 * C + j) * EY2 + nj + 1) * EX + ni] + F[((0 * C + j) * EY2 + nj + 1) * EX + ni + 1];
       const T val = T(a.y_scale) * v;
       y[(long long)j * d.N + (long long)(j0 + nj) * d.nx + i0 + ni] = val;
-      if (DOT) dot += (double)val * (double)pl[(j * PY2 + nj + 1) * PX + ni + 1];
+      if (RED == RED_PCG) acc_y += (double)val * (double)pl[(j * PY2 + nj + 1) * PX + ni + 1];
+      if (RED == RED_STATS) acc_y += (double)val * (double)val;
     }
   }
-  if (DOT) {
-    const double part = block_sum(dot, red_sh);
+  if (RED == RED_PCG) {
+    const double part = block_sum(acc_y, red_sh);
     double total;
     if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load,
                          gridDim.x, blockIdx.x, red_sh, &total)) {
-      if (threadIdx.x == 0) {
-        PcgState& s = a.st[load];
-        s.pAp = total;
-        if (!(total > 0.0) || !isfinite(total)) {
-          s.state = ST_BREAK;
-          s.alpha = 0.0;
-        } else {
-          s.alpha = s.rz / total;
-        }
-      }
+      if (threadIdx.x == 0) pcg_alpha_update(a.st[load], total);
+    }
+  }
+  if (RED == RED_STATS) {
+    double* out = a.stats + ((long long)load * gridDim.x + blockIdx.x) * (1 + 2 * C);
+    const double ty = block_sum(acc_y, red_sh);
+    if (threadIdx.x == 0) out[0] = ty;
+#pragma unroll
+    for (int i = 0; i < 2 * C; ++i) {
+      const double t = block_sum(acc_t[i], red_sh);
+      if (threadIdx.x == 0) out[1 + i] = t;
     }
   }
 }
@@ -532,18 +625,24 @@ cudaError_t set_smem(K kern, size_t bytes) {
   return cudaSuccess;
 }
 
-template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, bool DOT>
-cudaError_t launch_hex8_t(const StencilArgs& a, cudaStream_t s) {
+// hex8 grid: x-y tiles times z slabs (enough CTAs for 2 waves of 152 SMs, at least 8 planes a slab)
+void hex8_grid(const Dims& d, int* tiles, int* slabs, int* kz) {
+  *tiles = ((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
+  int sl = (2 * 152 + *tiles - 1) / *tiles;
+  sl = max(1, min(sl, d.nz / 8 > 0 ? d.nz / 8 : 1));
+  *kz = (d.nz + sl - 1) / sl;
+  *slabs = (d.nz + *kz - 1) / *kz;
+}
+
+template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED>
+cudaError_t launch_hex8_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
   const Dims& d = a.d;
-  const int tiles = ((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
-  // z slabs: enough CTAs to fill 2 waves of 152 SMs, at least 8 planes per slab
-  int slabs = (2 * 152 + tiles - 1) / tiles;
-  slabs = max(1, min(slabs, d.nz / 8 > 0 ? d.nz / 8 : 1));
-  const int kz = (d.nz + slabs - 1) / slabs;
-  slabs = (d.nz + kz - 1) / kz;
-  if (DOT && tiles * slabs > a.red.max_blocks) return cudaErrorInvalidConfiguration;
+  int tiles, slabs, kz;
+  hex8_grid(d, &tiles, &slabs, &kz);
+  if (ctas) *ctas = tiles * slabs;
+  if (RED == RED_PCG && tiles * slabs > a.red.max_blocks) return cudaErrorInvalidConfiguration;
   const size_t smem = sizeof(T) * (2 * C * PY * PX + 8 * C * EY * EX);
-  auto kern = hex8_apply_kernel<T, C, ISO, HAS_X, HAS_E, DOT>;
+  auto kern = hex8_apply_kernel<T, C, ISO, HAS_X, HAS_E, RED>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(tiles, slabs, a.n_loads);
@@ -551,13 +650,14 @@ cudaError_t launch_hex8_t(const StencilArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename T, int C, int ELEM, bool HAS_X, bool HAS_E, bool DOT>
-cudaError_t launch_pixel_t(const StencilArgs& a, cudaStream_t s) {
+template <typename T, int C, int ELEM, bool HAS_X, bool HAS_E, int RED>
+cudaError_t launch_pixel_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
   const Dims& d = a.d;
   const int tiles = ((d.nx + BX - 1) / BX) * ((d.ny + BY2 - 1) / BY2);
-  if (DOT && tiles > a.red.max_blocks) return cudaErrorInvalidConfiguration;
+  if (ctas) *ctas = tiles;
+  if (RED == RED_PCG && tiles > a.red.max_blocks) return cudaErrorInvalidConfiguration;
   const size_t smem = sizeof(T) * (C * PY2 * PX + 4 * C * EY2 * EX);
-  auto kern = pixel_apply_kernel<T, C, ELEM, HAS_X, HAS_E, DOT>;
+  auto kern = pixel_apply_kernel<T, C, ELEM, HAS_X, HAS_E, RED>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(tiles, 1, a.n_loads);
@@ -565,131 +665,72 @@ cudaError_t launch_pixel_t(const StencilArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// modes: PCG (x, <x, y>), STATS (residual / right-hand side with sums), plain (x and/or e)
 template <typename T, int C, bool ISO>
-cudaError_t dispatch_hex8(const StencilArgs& a, cudaStream_t s) {
-  const bool hx = a.x != nullptr, he = a.tau != nullptr, dot = a.st != nullptr;
-  if (dot) {
+cudaError_t dispatch_hex8(const StencilArgs& a, int* ctas, cudaStream_t s) {
+  const bool hx = a.x != nullptr, he = a.tau != nullptr;
+  if (a.st != nullptr) {
     if (!hx || he) return cudaErrorInvalidValue;
-    return launch_hex8_t<T, C, ISO, true, false, true>(a, s);
+    return launch_hex8_t<T, C, ISO, true, false, RED_PCG>(a, ctas, s);
   }
-  if (hx && he) return launch_hex8_t<T, C, ISO, true, true, false>(a, s);
-  if (hx) return launch_hex8_t<T, C, ISO, true, false, false>(a, s);
-  if (he) return launch_hex8_t<T, C, ISO, false, true, false>(a, s);
+  if (a.stats != nullptr) {
+    if (hx && he) return launch_hex8_t<T, C, ISO, true, true, RED_STATS>(a, ctas, s);
+    if (he) return launch_hex8_t<T, C, ISO, false, true, RED_STATS>(a, ctas, s);
+    return cudaErrorInvalidValue;
+  }
+  if (hx && he) return launch_hex8_t<T, C, ISO, true, true, RED_NONE>(a, ctas, s);
+  if (hx) return launch_hex8_t<T, C, ISO, true, false, RED_NONE>(a, ctas, s);
+  if (he) return launch_hex8_t<T, C, ISO, false, true, RED_NONE>(a, ctas, s);
   return cudaErrorInvalidValue;
 }
 
 template <typename T, int C, int ELEM>
-cudaError_t dispatch_pixel(const StencilArgs& a, cudaStream_t s) {
-  const bool hx = a.x != nullptr, he = a.tau != nullptr, dot = a.st != nullptr;
-  if (dot) {
+cudaError_t dispatch_pixel(const StencilArgs& a, int* ctas, cudaStream_t s) {
+  const bool hx = a.x != nullptr, he = a.tau != nullptr;
+  if (a.st != nullptr) {
     if (!hx || he) return cudaErrorInvalidValue;
-    return launch_pixel_t<T, C, ELEM, true, false, true>(a, s);
+    return launch_pixel_t<T, C, ELEM, true, false, RED_PCG>(a, ctas, s);
   }
-  if (hx && he) return launch_pixel_t<T, C, ELEM, true, true, false>(a, s);
-  if (hx) return launch_pixel_t<T, C, ELEM, true, false, false>(a, s);
-  if (he) return launch_pixel_t<T, C, ELEM, false, true, false>(a, s);
+  if (a.stats != nullptr) {
+    if (hx && he) return launch_pixel_t<T, C, ELEM, true, true, RED_STATS>(a, ctas, s);
+    if (he) return launch_pixel_t<T, C, ELEM, false, true, RED_STATS>(a, ctas, s);
+    return cudaErrorInvalidValue;
+  }
+  if (hx && he) return launch_pixel_t<T, C, ELEM, true, true, RED_NONE>(a, ctas, s);
+  if (hx) return launch_pixel_t<T, C, ELEM, true, false, RED_NONE>(a, ctas, s);
+  if (he) return launch_pixel_t<T, C, ELEM, false, true, RED_NONE>(a, ctas, s);
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_stiffness(const StencilArgs& a, cudaStream_t s) {
+cudaError_t launch_stiffness(const StencilArgs& a, cudaStream_t s, int* ctas) {
   const Dims& d = a.d;
   if (d.elem == HEX8_3D) {
-    if (d.c == 1) return dispatch_hex8<T, 1, false>(a, s);
-    if (a.iso) return dispatch_hex8<T, 3, true>(a, s);
-    return dispatch_hex8<T, 3, false>(a, s);
+    if (d.c == 1) return dispatch_hex8<T, 1, false>(a, ctas, s);
+    if (a.iso) return dispatch_hex8<T, 3, true>(a, ctas, s);
+    return dispatch_hex8<T, 3, false>(a, ctas, s);
   }
-  if (d.elem == P1TRI2_2D) return d.c == 1 ? dispatch_pixel<T, 1, P1TRI2_2D>(a, s) : dispatch_pixel<T, 2, P1TRI2_2D>(a, s);
-  if (d.elem == Q1_2D) return d.c == 1 ? dispatch_pixel<T, 1, Q1_2D>(a, s) : dispatch_pixel<T, 2, Q1_2D>(a, s);
+  if (d.elem == P1TRI2_2D)
+    return d.c == 1 ? dispatch_pixel<T, 1, P1TRI2_2D>(a, ctas, s) : dispatch_pixel<T, 2, P1TRI2_2D>(a, ctas, s);
+  if (d.elem == Q1_2D) return d.c == 1 ? dispatch_pixel<T, 1, Q1_2D>(a, ctas, s) : dispatch_pixel<T, 2, Q1_2D>(a, ctas, s);
   return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_stiffness<double>(const StencilArgs&, cudaStream_t);
-template cudaError_t launch_stiffness<float>(const StencilArgs&, cudaStream_t);
+int stiffness_ctas(const Dims& d) {
+  if (d.elem == HEX8_3D) {
+    int tiles, slabs, kz;
+    hex8_grid(d, &tiles, &slabs, &kz);
+    return tiles * slabs;
+  }
+  return ((d.nx + BX - 1) / BX) * ((d.ny + BY2 - 1) / BY2);
+}
 
-// ------------------------------------------------------------------------------------------------
-// volume average of flux / stress: <sigma> = (1/|Y|) sum_e V_e C_e (e + mean strain of element e)
-// ------------------------------------------------------------------------------------------------
+template cudaError_t launch_stiffness<double>(const StencilArgs&, cudaStream_t, int*);
+template cudaError_t launch_stiffness<float>(const StencilArgs&, cudaStream_t, int*);
+
 namespace {
-constexpr int MF_T = 256;
-
-__device__ __forceinline__ void grad_to_flux_vec(int dim, int c, const double (&G)[3][3], double (&eps)[6]) {
-  // G[i][j]: derivative i of component j.  Scalar: eps = grad; elastic: Mandel strain
-  if (c == 1) {
-    for (int i = 0; i < dim; ++i) eps[i] = G[i][0];
-    return;
-  }
-  const double r2 = 0.70710678118654752440;  // 1 / sqrt(2)
-  if (dim == 2) {
-    eps[0] = G[0][0];
-    eps[1] = G[1][1];
-    eps[2] = r2 * (G[0][1] + G[1][0]);
-  } else {
-    eps[0] = G[0][0];
-    eps[1] = G[1][1];
-    eps[2] = G[2][2];
-    eps[3] = r2 * (G[1][2] + G[2][1]);
-    eps[4] = r2 * (G[0][2] + G[2][0]);
-    eps[5] = r2 * (G[0][1] + G[1][0]);
-  }
-}
-
-__global__ void __launch_bounds__(MF_T) mean_flux_kernel(MeanFluxArgs a) {
-  const Dims d = a.d;
-  const int load = blockIdx.y;
-  const double* u = a.u ? a.u + (long long)load * a.load_stride : nullptr;
-  const double* e = a.loads + load * a.m;
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  const double vol = a.h[0] * a.h[1] * (d.dim == 3 ? a.h[2] : 1.0);
-  for (long long v = blockIdx.x * (long long)MF_T + threadIdx.x; v < d.N; v += (long long)gridDim.x * MF_T) {
-    const int i = (int)(v % d.nx);
-    const int j = (int)((v / d.nx) % d.ny);
-    const int k = (int)(v / ((long long)d.nx * d.ny));
-    // element-mean gradient G[i][j] (derivative i of component j) from the corner values
-    double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    if (u) {
-      const int ncorner = d.dim == 3 ? 8 : 4;
-      for (int comp = 0; comp < d.c; ++comp) {
-        double uc[8];
-        for (int cn = 0; cn < ncorner; ++cn) {
-          const int ii = (i + (cn & 1)) % d.nx, jj = (j + ((cn >> 1) & 1)) % d.ny;
-          const int kk = d.dim == 3 ? (k + (cn >> 2)) % d.nz : 0;
-          uc[cn] = u[(long long)comp * d.N + ((long long)kk * d.ny + jj) * d.nx + ii];
-        }
-        if (d.dim == 3) {
-          // mean of d/dxi over the voxel: (1/4) sum over the 4 x-edges, divided by h
-          G[0][comp] = ((uc[1] - uc[0]) + (uc[3] - uc[2]) + (uc[5] - uc[4]) + (uc[7] - uc[6])) / (4.0 * a.h[0]);
-          G[1][comp] = ((uc[2] - uc[0]) + (uc[3] - uc[1]) + (uc[6] - uc[4]) + (uc[7] - uc[5])) / (4.0 * a.h[1]);
-          G[2][comp] = ((uc[4] - uc[0]) + (uc[5] - uc[1]) + (uc[6] - uc[2]) + (uc[7] - uc[3])) / (4.0 * a.h[2]);
-        } else if (d.elem == Q1_2D) {
-          G[0][comp] = ((uc[1] - uc[0]) + (uc[3] - uc[2])) / (2.0 * a.h[0]);
-          G[1][comp] = ((uc[2] - uc[0]) + (uc[3] - uc[1])) / (2.0 * a.h[1]);
-        } else {
-          // mean of the two triangles: A: (u1 - u0, u3 - u1), B: (u3 - u2, u2 - u0)
-          G[0][comp] = 0.5 * ((uc[1] - uc[0]) + (uc[3] - uc[2])) / a.h[0];
-          G[1][comp] = 0.5 * ((uc[3] - uc[1]) + (uc[2] - uc[0])) / a.h[1];
-        }
-      }
-    }
-    double eps[6] = {0, 0, 0, 0, 0, 0};
-    grad_to_flux_vec(d.dim, d.c, G, eps);
-    const int ph = a.ids ? a.ids[v] : 0;
-    const double* C = a.moduli + (long long)ph * a.m * a.m;
-    for (int r = 0; r < a.m; ++r) {
-      double s = 0.0;
-      for (int q = 0; q < a.m; ++q) s += C[r * a.m + q] * (e[q] + eps[q]);
-      acc[r] += vol * s;
-    }
-  }
-  __shared__ double sh[32];
-  for (int r = 0; r < a.m; ++r) {
-    const double t = block_sum(acc[r], sh);
-    if (threadIdx.x == 0) a.partial[((long long)load * gridDim.x + blockIdx.x) * a.m + r] = t;
-  }
-}
-
 __global__ void phase_hist_kernel(const uint8_t* ids, long long N, unsigned long long* hist) {
   __shared__ unsigned int h[256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
@@ -701,14 +742,6 @@ __global__ void phase_hist_kernel(const uint8_t* ids, long long N, unsigned long
     if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
 }
 }  // namespace
-
-cudaError_t launch_mean_flux(const MeanFluxArgs& a, int* blocks_out, cudaStream_t s) {
-  const int blocks = (int)std::min<long long>(4 * 152, (a.d.N + MF_T - 1) / MF_T);
-  *blocks_out = blocks;
-  dim3 grid(blocks, a.n_loads);
-  mean_flux_kernel<<<grid, MF_T, 0, s>>>(a);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_phase_histogram(const uint8_t* ids, long long N, unsigned long long* hist, cudaStream_t s) {
   const int blocks = (int)std::min<long long>(2 * 152, (N + 255) / 256);

@@ -1,5 +1,5 @@
-// Small vector kernels of the solve driver: the FP64 residual of the iterative-refinement loop,
-// precision casts, mean removal and norms.  All reductions are FP64 with a fixed order.
+// Small vector kernels of the solve driver: precision casts of the iterative-refinement loop and
+// mean removal.  All reductions are FP64 with a fixed order.
 #include "fehom_internal.cuh"
 
 #include <algorithm>
@@ -10,11 +10,6 @@ namespace {
 constexpr int VT = 256;
 
 int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>(8 * 152, (n + VT - 1) / VT)); }
-
-__global__ void axpby_d_kernel(const double* __restrict__ x, double* __restrict__ y, double a, double b, long long n) {
-  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
-    y[i] = fma(a, x[i], b * y[i]);
-}
 
 __global__ void cast_d2f_kernel(const double* __restrict__ x, float* __restrict__ y, double s, long long n) {
   for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
@@ -67,25 +62,7 @@ __global__ void mean_subtract_kernel(double* __restrict__ x, long long N, long l
   for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < N; i += (long long)gridDim.x * VT) p[i] -= mean;
 }
 
-__global__ void norm2_kernel(const double* __restrict__ x, long long n, long long load_stride, double* partial) {
-  const double* p = x + (long long)blockIdx.y * load_stride;
-  double acc = 0.0;
-  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
-    acc = fma(p[i], p[i], acc);
-  const double t = block_sum(acc);
-  if (threadIdx.x == 0) partial[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
-}
-
 }  // namespace
-
-cudaError_t launch_fill(void* p, long long n, int bytes_per_elem, cudaStream_t s) {
-  return cudaMemsetAsync(p, 0, (size_t)n * bytes_per_elem, s);
-}
-
-cudaError_t launch_axpby_d(const double* x, double* y, double a, double b, long long n, cudaStream_t s) {
-  axpby_d_kernel<<<grid_for(n), VT, 0, s>>>(x, y, a, b, n);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_cast_d2f(const double* x, float* y, double scale, long long n, cudaStream_t s) {
   cast_d2f_kernel<<<grid_for(n), VT, 0, s>>>(x, y, scale, n);
@@ -104,14 +81,6 @@ cudaError_t launch_sub_mean(double* x, int c, long long N, int n_loads, long lon
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   mean_subtract_kernel<<<grid, VT, 0, s>>>(x, N, load_stride, partial);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_norm2(const double* x, long long n, int n_loads, long long load_stride, double* partial,
-                         int* blocks_out, cudaStream_t s) {
-  const int blocks = std::min(grid_for(n), 256);
-  *blocks_out = blocks;
-  norm2_kernel<<<dim3(blocks, n_loads), VT, 0, s>>>(x, n, load_stride, partial);
   return cudaGetLastError();
 }
 
