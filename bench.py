@@ -159,7 +159,8 @@ def run_ours(args):
         kt = {k: (t_after[k][0] - t_before[k][0], t_after[k][1] - t_before[k][1]) for k in t_after}
         load_iters = sum(sum(i["iterations"] for i in o["info"]) for o in outs)
         results[prec] = dict(ms=ms, iters=load_iters / args.steps, out=outs[-1], clocks=clk.summary(), kt=kt,
-                             load_iters=load_iters, launches=s.launch_count() - l_before)
+                             load_iters=load_iters, launches=s.launch_count() - l_before,
+                             plan=s.fft_plan(prec))
         s.close()
 
     # e2e: host phase ids -> setup -> build -> solve -> fields back to pinned host memory
@@ -239,7 +240,8 @@ def run_ours(args):
                                                   / np.abs(r64["out"]["C_eff"]).max()),
                   "C_eff_rel_err_vs_fp64_tol1e-10": err(rmx["out"]["C_eff"]),
                   "kernel_ms": {k: v[0] for k, v in rmx["kt"].items()},
-                  "gpu_launches": rmx["launches"], "clocks": rmx["clocks"]},
+                  "gpu_launches": rmx["launches"], "fft_plan": rmx["plan"], "clocks": rmx["clocks"]},
+        "fft_plan_fp64": r64["plan"],
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_ops / 1e12, "peak": FP64_INSTR_PEAK / 1e12,
                      "unit": "T FP64-instr/s", "frac": achieved_ops / FP64_INSTR_PEAK, "traffic": None,
                      "peak_source": "152 SMs x 2 FP64 lanes/clk x 2.07 GHz (unit count x max clock)",

@@ -73,6 +73,8 @@ typedef struct {
   void* stream;      /* cudaStream_t for every launch and copy; NULL = a blocking stream the context creates */
   int use_graph;     /* 1 (default): replay PCG iterations from a captured CUDA graph; 0: plain launches */
   int profile;       /* 1: record CUDA events around every kernel of the PCG iterations (see fehom_kernel_times) */
+  int autotune;      /* 1 (default): on the first solve of a batch size, time the FFT passes' launch plans
+                        (x-line pairs per CTA, columns per CTA) on the context's buffers and keep the fastest */
 } fehom_options;
 
 /* Kernel classes of one PCG iteration, for fehom_kernel_times. */
@@ -164,6 +166,11 @@ const char* fehom_last_error(const fehom_ctx* ctx);
  * not counted).  precision selects the FP64 kernels or the FP32 kernels of the mixed path.
  * ms[FEHOM_K_COUNT]: total milliseconds; count[FEHOM_K_COUNT]: launches timed. */
 fehom_status fehom_kernel_times(const fehom_ctx* ctx, int precision, double* ms, int64_t* count);
+
+/* Launch plan of the FFT passes in use for a precision (FEHOM_FP64 / FEHOM_MIXED): x-line pairs per
+ * CTA, columns per CTA of the y pass and of the last-axis pass (0 = built-in choice, not tuned yet),
+ * and the device milliseconds of the chosen plans measured by the tuner (ms[3], may be NULL). */
+fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int* tc_y, int* tc_last, double* ms);
 
 /* Number of kernel launches the context has issued since setup (kernels replayed from a CUDA graph
  * are counted once per replay). */

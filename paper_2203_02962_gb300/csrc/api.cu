@@ -64,6 +64,11 @@ struct fehom_ctx {
   bool counting = true;        // false while a graph is being captured
   bool events_made = false;
   cudaEvent_t ev[8][FEHOM_K_COUNT][2];
+  struct FftPlan {
+    int pairs = 0, tc_y = 0, tc_last = 0;
+    int tuned_loads = 0;
+    double ms[3] = {0, 0, 0};
+  } plan[2];                   // [0] FP64 kernels, [1] FP32 kernels
   double kms[2][FEHOM_K_COUNT] = {{0}};
   long long kcnt[2][FEHOM_K_COUNT] = {{0}};
   std::string err;
@@ -273,6 +278,10 @@ void fill_dims_args(fehom_ctx* ctx, FftArgs& f, bool fp32, int n_loads) {
   f.f1 = nullptr;
   f.f2 = nullptr;
   f.spec = fp32 ? (void*)ctx->spec32 : (void*)ctx->spec64;
+  const auto& pl = ctx->plan[fp32 ? 1 : 0];
+  f.pairs = pl.pairs;
+  f.tc_y = pl.tc_y;
+  f.tc_last = pl.tc_last;
 }
 
 StencilArgs stencil_args(fehom_ctx* ctx, bool fp32, int n_loads) {
@@ -419,6 +428,92 @@ fehom_status harvest_events(fehom_ctx* ctx, int prec, int n_iter) {
       ctx->kms[prec][k] += ms;
       ctx->kcnt[prec][k] += 1;
     }
+  return FEHOM_OK;
+}
+
+// Launch-plan tuner of the FFT passes: each candidate is timed with CUDA events on the context's
+// stream over the solve's own buffers (zeroed first), for the batch size of the solve.
+template <typename T>
+fehom_status autotune_fft(fehom_ctx* ctx, int n_loads) {
+  const int prec = sizeof(T) == 4 ? 1 : 0;
+  auto& pl = ctx->plan[prec];
+  if (!ctx->opt.autotune || pl.tuned_loads == n_loads) return FEHOM_OK;
+  cudaStream_t s = ctx->stream;
+  T* fin = prec ? (T*)ctx->r32 : (T*)ctx->r64;
+  T* fout = prec ? (T*)ctx->ap32 : (T*)ctx->ap64;
+  void* spec = prec ? (void*)ctx->spec32 : (void*)ctx->spec64;
+  const size_t fb = sizeof(T) * (size_t)n_loads * ctx->d.c * ctx->d.N;
+  const size_t sb = 2 * sizeof(T) * (size_t)n_loads * ctx->d.c * ctx->d.Nh;
+  CK(cudaMemsetAsync(fin, 0, fb, s));
+  CK(cudaMemsetAsync(spec, 0, sb, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  FftArgs base;
+  fill_dims_args(ctx, base, prec == 1, n_loads);
+  base.st = nullptr;
+  base.mode = FX_PLAIN;
+  auto timeit = [&](auto&& body) -> double {
+    if (body() != cudaSuccess) {
+      cudaGetLastError();
+      return -1.0;
+    }
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3; ++r) body();
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / 3.0;
+  };
+  auto pick = [&](const int* cand, int nc, auto&& body, int* best, double* best_ms) {
+    *best = 0;
+    *best_ms = 1e30;
+    for (int i = 0; i < nc; ++i) {
+      const double ms = timeit([&] { return body(cand[i]); });
+      if (ms > 0 && ms < *best_ms) {
+        *best_ms = ms;
+        *best = cand[i];
+      }
+    }
+  };
+  const int pairs[2] = {8, 4};
+  const int tcs[4] = {16, 8, 4, 2};
+  int bp, by = 0, bl;
+  double mp, my = 0, ml;
+  pick(pairs, 2, [&](int P) {
+    FftArgs f = base;
+    f.pairs = P;
+    f.f0 = fin;
+    cudaError_t e = launch_fft_x_fwd<T>(f, s);
+    if (e != cudaSuccess) return e;
+    f.f0 = fout;
+    return launch_fft_x_inv<T>(f, s);
+  }, &bp, &mp);
+  if (ctx->d.dim == 3)
+    pick(tcs, 4, [&](int TC) {
+      FftArgs f = base;
+      f.tc_y = TC;
+      cudaError_t e = launch_fft_y<T>(f, 0, s);
+      if (e != cudaSuccess) return e;
+      return launch_fft_y<T>(f, 1, s);
+    }, &by, &my);
+  pick(tcs, 4, [&](int TC) {
+    FftArgs f = base;
+    f.tc_last = TC;
+    return launch_fft_last_solve<T>(f, s);
+  }, &bl, &ml);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  pl.pairs = bp;
+  pl.tc_y = by;
+  pl.tc_last = bl;
+  pl.ms[0] = mp;
+  pl.ms[1] = my;
+  pl.ms[2] = ml;
+  pl.tuned_loads = n_loads;
+  ctx->graph_key[0] = 0;  // captured iterations used the previous plan
   return FEHOM_OK;
 }
 
@@ -583,6 +678,7 @@ void fehom_default_options(fehom_options* opt) {
   opt->stream = nullptr;
   opt->use_graph = 1;
   opt->profile = 0;
+  opt->autotune = 1;
 }
 
 const char* fehom_last_error(const fehom_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
@@ -594,6 +690,17 @@ fehom_status fehom_kernel_times(const fehom_ctx* ctx, int precision, double* ms,
     ms[k] = ctx->kms[p][k];
     count[k] = ctx->kcnt[p][k];
   }
+  return FEHOM_OK;
+}
+
+fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int* tc_y, int* tc_last, double* ms) {
+  if (!ctx) return FEHOM_E_INVALID;
+  const auto& pl = ctx->plan[precision == FEHOM_MIXED ? 1 : 0];
+  if (pairs) *pairs = pl.pairs;
+  if (tc_y) *tc_y = pl.tc_y;
+  if (tc_last) *tc_last = pl.tc_last;
+  if (ms)
+    for (int i = 0; i < 3; ++i) ms[i] = pl.ms[i];
   return FEHOM_OK;
 }
 
@@ -1001,6 +1108,7 @@ static fehom_status solve_fp64(fehom_ctx* ctx, int n_loads, const double* loads,
                                std::vector<PcgState>& hs, std::vector<double>& flux, std::vector<double>& rel2) {
   cudaStream_t s = ctx->stream;
   const long long cN = (long long)ctx->d.c * ctx->d.N;
+  TRY(autotune_fft<double>(ctx, n_loads));
   TRY(upload_tau(ctx, n_loads, loads));
   std::vector<double> bn2, rn2;
   TRY(residual_stats(ctx, n_loads, nullptr, ctx->b64, &bn2, nullptr));  // b = -D^T W C e
@@ -1047,6 +1155,7 @@ static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads
   cudaStream_t s = ctx->stream;
   TRY(grow32(ctx, n_loads));
   const long long cN = (long long)ctx->d.c * ctx->d.N;
+  TRY(autotune_fft<float>(ctx, n_loads));
   TRY(upload_tau(ctx, n_loads, loads));
   std::vector<double> bn2, rn2;
   TRY(residual_stats(ctx, n_loads, nullptr, ctx->b64, &bn2, nullptr));  // b = -D^T W C e

@@ -120,6 +120,9 @@ struct FftArgs {
   PcgState* st;      // nullptr = no PCG bookkeeping
   RedScratch red;
   int init;          // solve pass: 1 = first apply (sets rz, bnorm2)
+  // launch plan (0 = built-in choice): x-line pairs per CTA (4 or 8), columns per CTA of the y pass
+  // and of the last-axis pass (2, 4, 8 or 16)
+  int pairs, tc_y, tc_last;
 };
 
 template <typename T> cudaError_t launch_fft_x_fwd(const FftArgs& a, cudaStream_t s);

@@ -640,18 +640,23 @@ cudaError_t set_smem(K kern, size_t bytes) {
 constexpr size_t kSmemPair = 112 * 1024;  // two CTAs per SM
 constexpr size_t kSmemMax = 200 * 1024;
 
-// pairs of x lines per CTA: 8, or 4 when 8 does not fit
-template <typename T> int x_pairs(const Dims& d) {
+// pairs of x lines per CTA: the planned value when it fits, else 8, or 4 when 8 does not fit
+template <typename T> int x_pairs(const Dims& d, int planned) {
   using C = typename V2<T>::t;
-  return (2ull * d.nx * 9 * sizeof(C) <= 160 * 1024) ? 8 : 4;
+  auto fits = [&](int P) { return 2ull * d.nx * (P + 1) * sizeof(C) <= 160 * 1024; };
+  if ((planned == 4 || planned == 8) && fits(planned)) return planned;
+  return fits(8) ? 8 : 4;
 }
 
-// columns per CTA of a strided pass over nc components: 128-byte rows, halved until it fits
-template <typename T> int tile_cols(int L, int nc) {
+// columns per CTA of a strided pass over nc components: the planned value when it fits, else
+// 128-byte rows halved until two CTAs fit on an SM; 0 = no tile fits
+template <typename T> int tile_cols(int L, int nc, int planned) {
   using C = typename V2<T>::t;
+  auto bytes = [&](int TC) { return 2ull * L * nc * TC * sizeof(C); };
+  if ((planned == 2 || planned == 4 || planned == 8 || planned == 16) && bytes(planned) <= kSmemMax) return planned;
   int TC = sizeof(T) == 4 ? 16 : 8;
-  while (TC > 2 && 2ull * L * nc * TC * sizeof(C) > kSmemPair) TC >>= 1;
-  return 2ull * L * nc * TC * sizeof(C) <= kSmemMax ? TC : 0;
+  while (TC > 2 && bytes(TC) > kSmemPair) TC >>= 1;
+  return bytes(TC) <= kSmemMax ? TC : 0;
 }
 
 template <typename K, typename... Args>
@@ -670,7 +675,7 @@ cudaError_t launch_with_smem(K kern, dim3 grid, int threads, size_t smem, cudaSt
 template <typename T>
 cudaError_t launch_fft_x_fwd(const FftArgs& a, cudaStream_t s) {
   using C = typename V2<T>::t;
-  const int P = x_pairs<T>(a.d);
+  const int P = x_pairs<T>(a.d, a.pairs);
   const long long pairs = ((long long)a.d.ny * a.d.nz + 1) / 2;
   dim3 grid((unsigned)((pairs + P - 1) / P), a.d.c, a.n_loads);
   const size_t smem = 2ull * a.d.nx * (P + 1) * sizeof(C);
@@ -684,7 +689,7 @@ cudaError_t launch_fft_x_fwd(const FftArgs& a, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_fft_x_inv(const FftArgs& a, cudaStream_t s) {
   using C = typename V2<T>::t;
-  const int P = x_pairs<T>(a.d);
+  const int P = x_pairs<T>(a.d, a.pairs);
   const long long pairs = ((long long)a.d.ny * a.d.nz + 1) / 2;
   dim3 grid((unsigned)((pairs + P - 1) / P), a.d.c, a.n_loads);
   if (a.st != nullptr && (long long)grid.x * grid.y > a.red.max_blocks) return cudaErrorInvalidConfiguration;
@@ -716,7 +721,7 @@ cudaError_t launch_fft_y(const FftArgs& a, int inverse, cudaStream_t s) {
   using C = typename V2<T>::t;
   // 3-D middle axis: columns (z, kx), element e = ky
   ColMap m{a.d.ny, a.d.nz * a.d.nxh, (long long)a.d.ny * a.d.nxh, (long long)a.d.nxh};
-  const int TC = tile_cols<T>(m.L, 1);
+  const int TC = tile_cols<T>(m.L, 1, a.tc_y);
   if (TC == 0) return cudaErrorInvalidConfiguration;
   dim3 grid((m.ncols + TC - 1) / TC, a.d.c, a.n_loads);
   const size_t smem = 2ull * m.L * TC * sizeof(C);
@@ -749,7 +754,7 @@ static cudaError_t launch_last_nc(const FftArgs& a, cudaStream_t s) {
     m = ColMap{a.d.ny, a.d.nxh, 0LL, (long long)a.d.nxh};
     tw = reinterpret_cast<const C*>(a.tw.y);
   }
-  const int TC = tile_cols<T>(m.L, NC);
+  const int TC = tile_cols<T>(m.L, NC, a.tc_last);
   if (TC == 0) return cudaErrorInvalidConfiguration;
   dim3 grid((m.ncols + TC - 1) / TC, 1, a.n_loads);
   if (a.st != nullptr && (long long)grid.x > a.red.max_blocks) return cudaErrorInvalidConfiguration;

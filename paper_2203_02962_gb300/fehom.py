@@ -27,14 +27,16 @@ STATUS = {0: "FEHOM_OK", 1: "FEHOM_E_INVALID", 2: "FEHOM_E_UNSUPPORTED_SIZE", 3:
 # every entry point declared in include/fehom.h
 EXPORTS = ("fehom_default_options", "fehom_setup", "fehom_precond_build", "fehom_solve", "fehom_destroy",
            "fehom_last_error", "fehom_query", "fehom_apply_stiffness", "fehom_rhs", "fehom_apply_precond",
-           "fehom_get_symbol_inverse", "fehom_mean_flux", "fehom_kernel_times", "fehom_launch_count")
+           "fehom_get_symbol_inverse", "fehom_mean_flux", "fehom_kernel_times", "fehom_launch_count",
+           "fehom_fft_plan")
 
 KERNEL_CLASSES = ("stiffness", "fft_x_fwd", "fft_y_fwd", "fft_last", "fft_y_inv", "fft_x_inv")
 
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_iter", C.c_int), ("inner_tol", C.c_double),
-                ("stream", C.c_void_p), ("use_graph", C.c_int), ("profile", C.c_int)]
+                ("stream", C.c_void_p), ("use_graph", C.c_int), ("profile", C.c_int),
+                ("autotune", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -90,6 +92,9 @@ def load_library(path: str = LIB_PATH):
     lib.fehom_kernel_times.restype = i
     lib.fehom_launch_count.argtypes = [vp, i64p]
     lib.fehom_launch_count.restype = i
+    ip = C.POINTER(C.c_int)
+    lib.fehom_fft_plan.argtypes = [vp, i, ip, ip, ip, dp]
+    lib.fehom_fft_plan.restype = i
     _lib = lib
     return lib
 
@@ -109,7 +114,7 @@ class Solver:
     """One periodic cell: fehom_setup on construction, fehom_destroy on close()."""
 
     def __init__(self, elem, physics, n, ids, moduli, ref_material=None, precision="fp64", max_iter=10000,
-                 inner_tol=1e-3, cell=None, use_graph=True, stream=None, profile=False):
+                 inner_tol=1e-3, cell=None, use_graph=True, stream=None, profile=False, autotune=True):
         torch = _torch()
         self.lib = load_library()
         self.elem, self.physics = elem, physics
@@ -123,6 +128,7 @@ class Solver:
         opt.inner_tol = float(inner_tol)
         opt.use_graph = 1 if use_graph else 0
         opt.profile = 1 if profile else 0
+        opt.autotune = 1 if autotune else 0
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opt.stream = C.c_void_p(self.stream.cuda_stream)
         self._opt = opt
@@ -230,6 +236,13 @@ class Solver:
         cnt = (C.c_int64 * 6)()
         self._check(self.lib.fehom_kernel_times(self.ctx, PRECISION[precision], ms, cnt))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def fft_plan(self, precision="fp64"):
+        """Launch plan of the FFT passes: pairs, tc_y, tc_last and the tuner's times (ms)."""
+        p, y, l = C.c_int(), C.c_int(), C.c_int()
+        ms = (C.c_double * 3)()
+        self._check(self.lib.fehom_fft_plan(self.ctx, PRECISION[precision], C.byref(p), C.byref(y), C.byref(l), ms))
+        return {"pairs": p.value, "tc_y": y.value, "tc_last": l.value, "ms": list(ms)}
 
     def launch_count(self):
         n = C.c_int64()

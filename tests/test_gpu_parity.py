@@ -337,3 +337,22 @@ def test_full_size_bench_config_sampled():
     r_rows = b_rows[rows] - fem.stiffness_rows(g, w["ids"].ravel(), w["moduli"], u0, rows)
     assert np.abs(r_rows).max() < 1e-3 * np.abs(b_rows).max()
     s.close()
+
+
+def test_autotuned_plans_are_valid_and_agree():
+    """The FFT launch-plan tuner only changes tiling: results agree with the built-in plan."""
+    n = 32
+    ids, mod = _small_elastic(n, seed=12)
+    outs, plans = [], []
+    for tune in (True, False):
+        for prec in ("fp64", "mixed"):
+            s = _solver("hex8_3d", "elastic", (n, n, n), ids, mod, precision=prec, autotune=tune)
+            s.precond_build()
+            outs.append(s.solve(np.eye(6), tol=1e-9)["C_eff"])
+            plans.append(s.fft_plan(prec))
+            s.close()
+    for p in plans[:2]:
+        assert p["pairs"] in (4, 8) and p["tc_y"] in (2, 4, 8, 16) and p["tc_last"] in (2, 4, 8, 16)
+    for p in plans[2:]:
+        assert p["pairs"] == 0 and p["tc_last"] == 0
+    assert _rel(outs[0], outs[2]) < 1e-9 and _rel(outs[1], outs[3]) < 1e-8
