@@ -205,6 +205,23 @@ fehom_status fehom_get_symbol_inverse(fehom_ctx* ctx, double* out);
 /* <sigma> = (1/|Y|) sum_Q w_Q C_Q (e + (D u)_Q) for a device FP64 field u (c x N) and host load e. */
 fehom_status fehom_mean_flux(fehom_ctx* ctx, const double* e, const double* u, double* out);
 
+/*
+ * fehom_mean_flux_noalloc -- the same volume average as fehom_mean_flux, for callers that must not
+ * allocate device memory during the call: code running while a memory budget or pool may not grow,
+ * or in places where cudaMalloc is not allowed.  (The paper has no counterpart; it is an interface
+ * convenience of this library.)  fehom_mean_flux allocates its load table and partial sums on first
+ * use; this call allocates nothing.  Its scratch is a fixed array of 8192 doubles (64 KiB) inside the
+ * library, which every GPU that loads the library keeps until the process exits.  It holds the
+ * per-CTA partial sums, their totals and the per-phase load table, so it serves grids up to about
+ * 256^3 voxels in 3-D; larger grids are rejected with FEHOM_E_UNSUPPORTED_SIZE and a message giving
+ * the space they would need.  The first call on a device looks up the array's device address; make
+ * that first call before any stream capture on that device.  All calls share the one array and it
+ * keeps the last call's contents (each call overwrites every entry it reads, so nothing needs
+ * clearing): calls that overlap on the GPU, from several threads or streams, race and must be
+ * serialised by the caller.  Arguments as for fehom_mean_flux; the context is only read.
+ */
+fehom_status fehom_mean_flux_noalloc(fehom_ctx* ctx, const double* e, const double* u, double* out);
+
 #ifdef __cplusplus
 }
 #endif

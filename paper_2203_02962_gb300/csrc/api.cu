@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -663,6 +664,65 @@ fehom_status residual_stats(fehom_ctx* ctx, int n_loads, const double* x, double
   return FEHOM_OK;
 }
 
+// --------------------------------------------------------------------------------------------------
+// Allocation-free volume average (fehom_mean_flux_noalloc).  Its scratch is this fixed device array:
+// every GPU that loads the library holds it until the process exits.  Layout per call: the per-CTA
+// partial sums [ctas][1 + D], then the reduced sums [1 + D], then the per-phase prestress [P][D].
+// --------------------------------------------------------------------------------------------------
+constexpr int kNoallocDoubles = 8192;  // 64 KiB
+constexpr int kMaxDevices = 64;
+__device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[kMaxDevices] = {};
+
+// gradient -> flux map P (m x D, row-major) into a caller-provided array (no heap use)
+void flux_map_into(int dim, int physics, double* P) {
+  const int m = physics == FEHOM_SCALAR ? dim : dim * (dim + 1) / 2;
+  const int D = physics == FEHOM_SCALAR ? dim : dim * dim;
+  for (int i = 0; i < m * D; ++i) P[i] = 0.0;
+  if (physics == FEHOM_SCALAR) {
+    for (int i = 0; i < dim; ++i) P[i * D + i] = 1.0;
+    return;
+  }
+  for (int a = 0; a < dim; ++a) P[a * D + a * dim + a] = 1.0;
+  const double r2 = 1.0 / std::sqrt(2.0);
+  const int pairs[3][2] = {{1, 2}, {0, 2}, {0, 1}};
+  for (int k = 0; k < (dim == 3 ? 3 : 1); ++k) {
+    const int a = dim == 3 ? pairs[k][0] : 0, b = dim == 3 ? pairs[k][1] : 1;
+    P[(dim + k) * D + a * dim + b] = r2;
+    P[(dim + k) * D + b * dim + a] = r2;
+  }
+}
+
+// sums the per-CTA partials column by column in CTA order (the order the host uses elsewhere)
+__global__ void noalloc_sum_kernel(double* scratch, int ctas, int W) {
+  for (int i = threadIdx.x; i < W; i += blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < ctas; ++b) acc += scratch[(long long)b * W + i];
+    scratch[(long long)ctas * W + i] = acc;
+  }
+}
+
+// device address of the scratch array on the context's device, looked up once per device with that
+// device current (the host-side symbol is only a stand-in and must never reach a kernel)
+fehom_status noalloc_scratch(fehom_ctx* ctx, double** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  const int dev = ctx->device;
+  if (dev < 0 || dev >= kMaxDevices) FAIL(FEHOM_E_INVALID, "device index out of range for the fixed scratch table");
+  if (!g_noalloc_addr[dev]) {
+    int prev = 0;
+    CK(cudaGetDevice(&prev));
+    if (prev != dev) CK(cudaSetDevice(dev));
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (prev != dev) cudaSetDevice(prev);
+    CK(e);
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return FEHOM_OK;
+}
+
 }  // namespace
 
 // ==================================================================================================
@@ -1039,6 +1099,67 @@ fehom_status fehom_get_symbol_inverse(fehom_ctx* ctx, double* out) {
   const int ne = ctx->d.c * (ctx->d.c + 1) / 2;
   CK(cudaMemcpyAsync(out, ctx->sym64, sizeof(double) * ne * ctx->d.Nh, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return FEHOM_OK;
+}
+
+fehom_status fehom_mean_flux_noalloc(fehom_ctx* ctx, const double* e, const double* u, double* out) {
+  if (!ctx || !e || !u || !out) return FEHOM_E_INVALID;
+  for (int i = 0; i < ctx->m; ++i)
+    if (!std::isfinite(e[i])) FAIL(FEHOM_E_INVALID, "non-finite load");
+  const int D = ctx->D, W = 1 + D, P = ctx->n_phases;
+  const int ctas = stiffness_ctas(ctx->d);
+  const long long need = (long long)ctas * W + W + (long long)P * D;
+  if (need > kNoallocDoubles) {
+    char msg[200];
+    std::snprintf(msg, sizeof msg,
+                  "fehom_mean_flux_noalloc: this grid needs %lld scratch doubles, the fixed array holds %d", need,
+                  kNoallocDoubles);
+    FAIL(FEHOM_E_UNSUPPORTED_SIZE, msg);
+  }
+  double* scratch = nullptr;
+  TRY(noalloc_scratch(ctx, &scratch));
+  cudaStream_t s = ctx->stream;
+  const int dim = ctx->d.dim, m = ctx->m;
+  double Pm[6 * 9];
+  flux_map_into(dim, ctx->physics, Pm);
+  double w, sc[3];
+  kernel_scales(ctx, &w, sc);
+  double tau[kMaxPhases * 9];  // host stack: per-phase prestress w S P^T C e of the load, [P][D]
+  for (int ph = 0; ph < P; ++ph) {
+    const double* C = &ctx->moduli[(size_t)ph * m * m];
+    for (int q = 0; q < D; ++q) {
+      double acc = 0.0;
+      for (int I = 0; I < m; ++I)
+        for (int J = 0; J < m; ++J) acc += Pm[I * D + q] * C[I * m + J] * e[J];
+      tau[ph * D + q] = w * sc[q % dim] * acc;
+    }
+  }
+  double* tau_d = scratch + (long long)ctas * W + W;
+  CK(cudaMemcpyAsync(tau_d, tau, sizeof(double) * P * D, cudaMemcpyHostToDevice, s));
+  StencilArgs a = stencil_args(ctx, false, 1);
+  a.x = u;
+  a.y = nullptr;  // sums only: no field is written
+  a.tau = tau_d;
+  a.y_scale = -1.0;
+  a.stats = scratch;
+  int got = 0;
+  CK(launch_stiffness<double>(a, s, &got));
+  count_launch(ctx);
+  if (got != ctas) FAIL(FEHOM_E_CUDA, "stiffness statistics: CTA count mismatch");
+  noalloc_sum_kernel<<<1, 32, 0, s>>>(scratch, ctas, W);
+  CK(cudaGetLastError());
+  count_launch(ctx);
+  double sums[1 + 9];
+  CK(cudaMemcpyAsync(sums, scratch + (long long)ctas * W, sizeof(double) * W, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double cell = 1.0;
+  const int n3[3] = {ctx->d.nx, ctx->d.ny, ctx->d.nz};
+  for (int i = 0; i < dim; ++i) cell *= ctx->h[i] * n3[i];
+  for (int I = 0; I < ctx->m; ++I) {
+    double v = 0.0;
+    for (int q = 0; q < D; ++q) v += Pm[I * D + q] * sums[1 + q] / sc[q % dim];
+    out[I] = v / cell;
+  }
   return FEHOM_OK;
 }
 

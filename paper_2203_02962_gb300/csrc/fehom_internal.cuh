@@ -73,7 +73,7 @@ struct StencilArgs {
   PcgState* st;
   RedScratch red;
   // fused statistics (nullptr = off): per load and CTA, sum y^2 and the sum of the monomial-1 duals
-  // of the CTA's elements, [load][cta][1 + c * dim] doubles
+  // of the CTA's elements, [load][cta][1 + c * dim] doubles; with y == nullptr only the sums are made
   double* stats;
 };
 

@@ -265,7 +265,8 @@ __device__ __forceinline__ void hex8_element(const T (&u)[C][8], const T* __rest
 //   RED_STATS per CTA: sum y^2 over its nodes and the sum of the monomial-1 duals over its elements
 //             (partials [load][cta][1 + D], reduced on the host in index order)
 // ------------------------------------------------------------------------------------------------
-enum { RED_NONE = 0, RED_PCG = 1, RED_STATS = 2 };
+//   RED_SUMS  the RED_STATS sums without storing y (y may be NULL)
+enum { RED_NONE = 0, RED_PCG = 1, RED_STATS = 2, RED_SUMS = 3 };
 
 __device__ void pcg_alpha_update(PcgState& s, double total) {
   s.pAp = total;
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
       for (int j = 0; j < C; ++j)
 #pragma unroll
         for (int cn = 0; cn < 8; ++cn) F[(cn * C + j) * NE + ej * EX + ei] = f[j][cn];
-      if (RED == RED_STATS && owner && k >= k0) {
+      if ((RED == RED_STATS || RED == RED_SUMS) && owner && k >= k0) {
 #pragma unroll
         for (int j = 0; j < C; ++j)
 #pragma unroll
@@ -391,9 +392,9 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
                       F[(5 * C + j) * NE + e00 + EX] + F[(4 * C + j) * NE + e00 + EX + 1];
         if (k >= k0) {
           const T val = T(a.y_scale) * (carry[j] + bot);
-          y[(long long)j * d.N + (long long)k * plane + node_off] = val;
+          if (RED != RED_SUMS) y[(long long)j * d.N + (long long)k * plane + node_off] = val;
           if (RED == RED_PCG) acc_y += (double)val * (double)pl[(CUR * C + j) * NPOS + (nj + 1) * PX + ni + 1];
-          if (RED == RED_STATS) acc_y += (double)val * (double)val;
+          if ((RED == RED_STATS || RED == RED_SUMS)) acc_y += (double)val * (double)val;
         }
         carry[j] = top;
       }
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
       if (threadIdx.x == 0) pcg_alpha_update(a.st[load], total);
     }
   }
-  if (RED == RED_STATS) {
+  if ((RED == RED_STATS || RED == RED_SUMS)) {
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     double* out = a.stats + ((long long)load * nblk + bid) * (1 + 3 * C);
@@ -578,7 +579,7 @@ __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
     for (int j = 0; j < C; ++j)
 #pragma unroll
       for (int cn = 0; cn < 4; ++cn) F[((cn * C + j) * EY2 + ej) * EX + ei] = f[j][cn];
-    if (RED == RED_STATS && ei >= 1 && ej >= 1 && i0 + ei - 1 < d.nx && j0 + ej - 1 < d.ny) {
+    if ((RED == RED_STATS || RED == RED_SUMS) && ei >= 1 && ej >= 1 && i0 + ei - 1 < d.nx && j0 + ej - 1 < d.ny) {
 #pragma unroll
       for (int j = 0; j < C; ++j)
 #pragma unroll
@@ -594,9 +595,9 @@ __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
       const T v = F[((3 * C + j) * EY2 + nj) * EX + ni] + F[((2 * C + j) * EY2 + nj) * EX + ni + 1] +
                   F[((1 * C + j) * EY2 + nj + 1) * EX + ni] + F[((0 * C + j) * EY2 + nj + 1) * EX + ni + 1];
       const T val = T(a.y_scale) * v;
-      y[(long long)j * d.N + (long long)(j0 + nj) * d.nx + i0 + ni] = val;
+      if (RED != RED_SUMS) y[(long long)j * d.N + (long long)(j0 + nj) * d.nx + i0 + ni] = val;
       if (RED == RED_PCG) acc_y += (double)val * (double)pl[(j * PY2 + nj + 1) * PX + ni + 1];
-      if (RED == RED_STATS) acc_y += (double)val * (double)val;
+      if ((RED == RED_STATS || RED == RED_SUMS)) acc_y += (double)val * (double)val;
     }
   }
   if (RED == RED_PCG) {
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
       if (threadIdx.x == 0) pcg_alpha_update(a.st[load], total);
     }
   }
-  if (RED == RED_STATS) {
+  if ((RED == RED_STATS || RED == RED_SUMS)) {
     double* out = a.stats + ((long long)load * gridDim.x + blockIdx.x) * (1 + 2 * C);
     const double ty = block_sum(acc_y, red_sh);
     if (threadIdx.x == 0) out[0] = ty;
@@ -673,6 +674,10 @@ cudaError_t dispatch_hex8(const StencilArgs& a, int* ctas, cudaStream_t s) {
     if (!hx || he) return cudaErrorInvalidValue;
     return launch_hex8_t<T, C, ISO, true, false, RED_PCG>(a, ctas, s);
   }
+  if (a.stats != nullptr && a.y == nullptr) {
+    if (hx && he) return launch_hex8_t<T, C, ISO, true, true, RED_SUMS>(a, ctas, s);
+    return cudaErrorInvalidValue;
+  }
   if (a.stats != nullptr) {
     if (hx && he) return launch_hex8_t<T, C, ISO, true, true, RED_STATS>(a, ctas, s);
     if (he) return launch_hex8_t<T, C, ISO, false, true, RED_STATS>(a, ctas, s);
@@ -690,6 +695,10 @@ cudaError_t dispatch_pixel(const StencilArgs& a, int* ctas, cudaStream_t s) {
   if (a.st != nullptr) {
     if (!hx || he) return cudaErrorInvalidValue;
     return launch_pixel_t<T, C, ELEM, true, false, RED_PCG>(a, ctas, s);
+  }
+  if (a.stats != nullptr && a.y == nullptr) {
+    if (hx && he) return launch_pixel_t<T, C, ELEM, true, true, RED_SUMS>(a, ctas, s);
+    return cudaErrorInvalidValue;
   }
   if (a.stats != nullptr) {
     if (hx && he) return launch_pixel_t<T, C, ELEM, true, true, RED_STATS>(a, ctas, s);

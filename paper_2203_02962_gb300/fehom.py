@@ -28,7 +28,7 @@ STATUS = {0: "FEHOM_OK", 1: "FEHOM_E_INVALID", 2: "FEHOM_E_UNSUPPORTED_SIZE", 3:
 EXPORTS = ("fehom_default_options", "fehom_setup", "fehom_precond_build", "fehom_solve", "fehom_destroy",
            "fehom_last_error", "fehom_query", "fehom_apply_stiffness", "fehom_rhs", "fehom_apply_precond",
            "fehom_get_symbol_inverse", "fehom_mean_flux", "fehom_kernel_times", "fehom_launch_count",
-           "fehom_fft_plan")
+           "fehom_fft_plan", "fehom_mean_flux_noalloc")
 
 KERNEL_CLASSES = ("stiffness", "fft_x_fwd", "fft_y_fwd", "fft_last", "fft_y_inv", "fft_x_inv")
 
@@ -88,6 +88,8 @@ def load_library(path: str = LIB_PATH):
     lib.fehom_get_symbol_inverse.restype = i
     lib.fehom_mean_flux.argtypes = [vp, dp, vp, dp]
     lib.fehom_mean_flux.restype = i
+    lib.fehom_mean_flux_noalloc.argtypes = [vp, dp, vp, dp]
+    lib.fehom_mean_flux_noalloc.restype = i
     lib.fehom_kernel_times.argtypes = [vp, i, dp, i64p]
     lib.fehom_kernel_times.restype = i
     lib.fehom_launch_count.argtypes = [vp, i64p]
