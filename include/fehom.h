@@ -167,6 +167,21 @@ const char* fehom_last_error(const fehom_ctx* ctx);
  * ms[FEHOM_K_COUNT]: total milliseconds; count[FEHOM_K_COUNT]: launches timed. */
 fehom_status fehom_kernel_times(const fehom_ctx* ctx, int precision, double* ms, int64_t* count);
 
+/* PCG coefficients alpha_j, beta_j (j = 0 .. count-1) of the last PCG run of a load (FP64 solve; the
+ * last inner FP32 run of a mixed solve), up to `capacity` and at most 2048; with them the CG-Lanczos
+ * tridiagonal matrix T (T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_j,j+1 = sqrt(beta_j)/alpha_j)
+ * gives Ritz values of K_ref^+ K (Sec. 4.3).  Host arrays. */
+fehom_status fehom_pcg_coefficients(fehom_ctx* ctx, int load, int capacity, double* alpha, double* beta, int* count);
+
+/* Element-by-element eigenvalue bounds of K_ref^+ K (Sec. 4.3).  For each node I the lower (upper)
+ * bound is the smallest (largest) extreme generalized eigenvalue of (C_e, C_ref) over the voxels e that
+ * contain the node; counted once per DOF of the node and sorted, they bound the eigenvalues of the
+ * preconditioned operator one by one.  Returned as ascending (value, count) lists: lo_values /
+ * lo_counts (n_lo entries) and hi_values / hi_counts (n_hi entries), host arrays of at least
+ * n_phases entries; the counts add up to c N.  Needs fehom_setup. */
+fehom_status fehom_eig_bounds(fehom_ctx* ctx, double* lo_values, int64_t* lo_counts, int* n_lo, double* hi_values,
+                              int64_t* hi_counts, int* n_hi);
+
 /* Launch plan of the FFT passes in use for a precision (FEHOM_FP64 / FEHOM_MIXED): x-line pairs per
  * CTA, columns per CTA of the y pass and of the last-axis pass (0 = built-in choice, not tuned yet),
  * and the device milliseconds of the chosen plans measured by the tuner (ms[3], may be NULL). */

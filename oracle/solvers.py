@@ -233,3 +233,27 @@ def homogenise(grid: fem.Grid, phases, moduli, loads, method="cg", tol=1e-14, C_
     S = np.array(fluxes).T
     C_eff = S @ np.linalg.inv(loads.T) if loads.shape[0] == loads.shape[1] else None
     return dict(fields=np.array(fields), mean_flux=np.array(fluxes), C_eff=C_eff, iters=iters)
+
+
+# ----------------------------------------------------------------------------------------------
+# Sec. 4.3: element-by-element eigenvalue bounds of K_ref^-1 K
+# ----------------------------------------------------------------------------------------------
+def eig_bounds(grid: fem.Grid, phases, moduli, C_ref):
+    """Sorted lower and upper bound sequences (length c N) of the eigenvalues of K_ref^-1 K.
+
+    For each node I: lambda_I^L / lambda_I^U = min / max over the voxels in supp(phi_I) of the
+    extreme generalized eigenvalues of (C_e, C_ref) (constant material per voxel, so one pair per
+    voxel); each value counted once per DOF of the node (d times for elasticity) and sorted.
+    """
+    import scipy.linalg as sl
+    phases = np.asarray(phases).ravel()
+    lam = [sl.eigh(np.asarray(C, float), np.asarray(C_ref, float), eigvals_only=True) for C in moduli]
+    lo_p = np.array([l.min() for l in lam])
+    hi_p = np.array([l.max() for l in lam])
+    en = grid.element_nodes()
+    node_lo = np.full(grid.N, np.inf)
+    node_hi = np.full(grid.N, -np.inf)
+    for a in range(grid.ne):
+        np.minimum.at(node_lo, en[:, a], lo_p[phases])
+        np.maximum.at(node_hi, en[:, a], hi_p[phases])
+    return np.sort(np.repeat(node_lo, grid.c)), np.sort(np.repeat(node_hi, grid.c))

@@ -71,6 +71,7 @@ struct fehom_ctx {
     double ms[3] = {0, 0, 0};
   } plan[2];                   // [0] FP64 kernels, [1] FP32 kernels
   double kms[2][FEHOM_K_COUNT] = {{0}};
+  int hist_count[kMaxLoads] = {0};  // PCG coefficients recorded per load by the last PCG run
   long long kcnt[2][FEHOM_K_COUNT] = {{0}};
   std::string err;
 };
@@ -572,6 +573,7 @@ fehom_status run_iterations(fehom_ctx* ctx, int n_loads, T* x, T* r, T* p, T* ap
       if (hs[l].state == ST_RUN || hs[l].state == ST_CONV || hs[l].state == ST_FIN_MAX) all = false;
     if (all) break;
   }
+  for (int l = 0; l < n_loads; ++l) ctx->hist_count[l] = std::min(hs[l].iter, kHist);
   return FEHOM_OK;
 }
 
@@ -753,6 +755,95 @@ fehom_status fehom_kernel_times(const fehom_ctx* ctx, int precision, double* ms,
   return FEHOM_OK;
 }
 
+fehom_status fehom_pcg_coefficients(fehom_ctx* ctx, int load, int capacity, double* alpha, double* beta, int* count) {
+  if (!ctx || !alpha || !beta || !count || load < 0 || load >= kMaxLoads || capacity < 0) return FEHOM_E_INVALID;
+  const int n = std::min(capacity, ctx->hist_count[load]);
+  *count = n;
+  if (n == 0) return FEHOM_OK;
+  CK(cudaMemcpyAsync(alpha, ctx->red.hist + (size_t)load * 2 * kHist, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(beta, ctx->red.hist + ((size_t)load * 2 + 1) * kHist, sizeof(double) * n,
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FEHOM_OK;
+}
+
+fehom_status fehom_eig_bounds(fehom_ctx* ctx, double* lo_values, int64_t* lo_counts, int* n_lo, double* hi_values,
+                              int64_t* hi_counts, int* n_hi) {
+  if (!ctx || !lo_values || !lo_counts || !n_lo || !hi_values || !hi_counts || !n_hi) return FEHOM_E_INVALID;
+  const int m = ctx->m, P = ctx->n_phases;
+  // extreme generalized eigenvalues of (C_p, C_ref): eigenvalues of L^-1 C_p L^-T with C_ref = L L^T
+  std::vector<double> L((size_t)m * m, 0.0);
+  const double* R = ctx->cref.data();
+  for (int j = 0; j < m; ++j) {
+    double sj = R[j * m + j];
+    for (int k = 0; k < j; ++k) sj -= L[j * m + k] * L[j * m + k];
+    L[j * m + j] = std::sqrt(sj);
+    for (int i = j + 1; i < m; ++i) {
+      double t = R[i * m + j];
+      for (int k = 0; k < j; ++k) t -= L[i * m + k] * L[j * m + k];
+      L[i * m + j] = t / L[j * m + j];
+    }
+  }
+  auto lsolve = [&](std::vector<double>& B) {  // B <- L^-1 B (column by column)
+    for (int col = 0; col < m; ++col)
+      for (int i = 0; i < m; ++i) {
+        double t = B[i * m + col];
+        for (int k = 0; k < i; ++k) t -= L[i * m + k] * B[k * m + col];
+        B[i * m + col] = t / L[i * m + i];
+      }
+  };
+  std::vector<double> lo(P), hi(P);
+  for (int p = 0; p < P; ++p) {
+    std::vector<double> A(ctx->moduli.begin() + (size_t)p * m * m, ctx->moduli.begin() + (size_t)(p + 1) * m * m);
+    lsolve(A);                                    // L^-1 C
+    std::vector<double> At((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) At[i * m + j] = A[j * m + i];
+    lsolve(At);                                   // L^-1 (L^-1 C)^T = L^-1 C L^-T (symmetric)
+    std::vector<double> V, ev;
+    jacobi_eig(m, At, V, ev);
+    lo[p] = *std::min_element(ev.begin(), ev.end());
+    hi[p] = *std::max_element(ev.begin(), ev.end());
+  }
+  double* dv = nullptr;
+  unsigned long long* dh = nullptr;
+  CK(cudaMalloc(&dv, sizeof(double) * 2 * P));
+  CK(cudaMalloc(&dh, sizeof(unsigned long long) * 512));
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(dv, lo.data(), sizeof(double) * P, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dv + P, hi.data(), sizeof(double) * P, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(dh, 0, sizeof(unsigned long long) * 512, s));
+  CK(launch_eig_bounds(ctx->d, ctx->ids, dv, dv + P, dh, dh + 256, s));
+  count_launch(ctx);
+  std::vector<unsigned long long> hh(512);
+  CK(cudaMemcpyAsync(hh.data(), dh, sizeof(unsigned long long) * 512, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  cudaFree(dv);
+  cudaFree(dh);
+  // (value, count) lists, ascending, equal values merged; each node counts once per DOF
+  auto emit = [&](const std::vector<double>& val, const unsigned long long* h, double* ov, int64_t* oc, int* n) {
+    std::vector<std::pair<double, long long>> e;
+    for (int p = 0; p < P; ++p)
+      if (h[p]) e.push_back({val[p], (long long)h[p] * ctx->d.c});
+    std::sort(e.begin(), e.end());
+    int k = 0;
+    for (size_t i = 0; i < e.size(); ++i) {
+      if (k > 0 && ov[k - 1] == e[i].first) {
+        oc[k - 1] += e[i].second;
+      } else {
+        ov[k] = e[i].first;
+        oc[k] = e[i].second;
+        ++k;
+      }
+    }
+    *n = k;
+  };
+  emit(lo, hh.data(), lo_values, lo_counts, n_lo);
+  emit(hi, hh.data() + 256, hi_values, hi_counts, n_hi);
+  return FEHOM_OK;
+}
+
 fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int* tc_y, int* tc_last, double* ms) {
   if (!ctx) return FEHOM_E_INVALID;
   const auto& pl = ctx->plan[precision == FEHOM_MIXED ? 1 : 0];
@@ -796,7 +887,7 @@ void fehom_destroy(fehom_ctx* ctx) {
   dfree(ctx->sym64); dfree(ctx->sym32);
   dfree(ctx->x64); dfree(ctx->r64); dfree(ctx->p64); dfree(ctx->ap64); dfree(ctx->b64); dfree(ctx->spec64);
   dfree(ctx->x32); dfree(ctx->r32); dfree(ctx->p32); dfree(ctx->ap32); dfree(ctx->spec32);
-  dfree(ctx->st); dfree(ctx->red.partial); dfree(ctx->red.count);
+  dfree(ctx->st); dfree(ctx->red.partial); dfree(ctx->red.count); dfree(ctx->red.hist);
   dfree(ctx->tau); dfree(ctx->partial);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   cudaSetDevice(prev);
@@ -927,6 +1018,7 @@ static fehom_status setup_impl(fehom_ctx* ctx, int elem, int physics, const int6
   ctx->red.max_blocks = kRedBlocks;
   CK(cudaMalloc(&ctx->red.partial, sizeof(double) * (size_t)kMaxLoads * kRedBlocks));
   CK(cudaMalloc(&ctx->red.count, sizeof(unsigned) * kMaxLoads));
+  CK(cudaMalloc(&ctx->red.hist, sizeof(double) * (size_t)kMaxLoads * 2 * kHist));
   CK(cudaMemsetAsync(ctx->red.count, 0, sizeof(unsigned) * kMaxLoads, s));
   TRY(grow64(ctx, 1));
   CK(cudaStreamSynchronize(s));

@@ -52,7 +52,10 @@ struct RedScratch {
   double* partial;   // [kMaxLoads][max_blocks]
   unsigned* count;   // [kMaxLoads] arrival counters (self-resetting)
   int max_blocks;
+  double* hist;      // PCG coefficients [load][2][kHist] (alpha_j, beta_j) or nullptr
 };
+
+constexpr int kHist = 2048;  // PCG coefficients kept per load (for the Lanczos / Ritz check)
 
 // ------------------------------------------------------------------------------------------------
 // stencil.cu
@@ -87,6 +90,11 @@ int stiffness_ctas(const Dims& d);
 
 cudaError_t launch_phase_histogram(const uint8_t* ids, long long N, unsigned long long* hist,
                                    cudaStream_t s);
+
+// Sec. 4.3 bounds: per node, the phase whose lo (hi) value is smallest (largest) over the voxels that
+// contain the node; histograms of those phases, [256] each (zeroed by the caller)
+cudaError_t launch_eig_bounds(const Dims& d, const uint8_t* ids, const double* lo, const double* hi,
+                              unsigned long long* hist_lo, unsigned long long* hist_hi, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------------
 // fft.cu

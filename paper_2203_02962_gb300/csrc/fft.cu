@@ -544,6 +544,7 @@ __global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, const
           else if (total <= s.tol2) s.state = ST_CONV;
         } else {
           s.beta = (s.rz > 0.0) ? total / s.rz : 0.0;
+          if (a.red.hist != nullptr && s.iter < kHist) a.red.hist[((long long)load * 2 + 1) * kHist + s.iter] = s.beta;
           s.rz = total;
           if (!isfinite(total)) s.state = ST_BREAK;
           else if (total <= s.tol2) s.state = ST_CONV;

@@ -268,7 +268,7 @@ __device__ __forceinline__ void hex8_element(const T (&u)[C][8], const T* __rest
 //   RED_SUMS  the RED_STATS sums without storing y (y may be NULL)
 enum { RED_NONE = 0, RED_PCG = 1, RED_STATS = 2, RED_SUMS = 3 };
 
-__device__ void pcg_alpha_update(PcgState& s, double total) {
+__device__ void pcg_alpha_update(PcgState& s, double total, double* hist) {
   s.pAp = total;
   if (!(total > 0.0) || !isfinite(total)) {
     s.state = ST_BREAK;
@@ -276,6 +276,7 @@ __device__ void pcg_alpha_update(PcgState& s, double total) {
   } else {
     s.alpha = s.rz / total;
   }
+  if (hist != nullptr && s.iter < kHist) hist[s.iter] = s.alpha;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -422,7 +423,8 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
     double total;
     if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load, nblk,
                          bid, red_sh, &total)) {
-      if (threadIdx.x == 0) pcg_alpha_update(a.st[load], total);
+      if (threadIdx.x == 0)
+        pcg_alpha_update(a.st[load], total, a.red.hist ? a.red.hist + (long long)load * 2 * kHist : nullptr);
     }
   }
   if ((RED == RED_STATS || RED == RED_SUMS)) {
@@ -605,7 +607,8 @@ __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
     double total;
     if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load,
                          gridDim.x, blockIdx.x, red_sh, &total)) {
-      if (threadIdx.x == 0) pcg_alpha_update(a.st[load], total);
+      if (threadIdx.x == 0)
+        pcg_alpha_update(a.st[load], total, a.red.hist ? a.red.hist + (long long)load * 2 * kHist : nullptr);
     }
   }
   if ((RED == RED_STATS || RED == RED_SUMS)) {
@@ -740,6 +743,35 @@ template cudaError_t launch_stiffness<double>(const StencilArgs&, cudaStream_t, 
 template cudaError_t launch_stiffness<float>(const StencilArgs&, cudaStream_t, int*);
 
 namespace {
+__global__ void eig_bounds_kernel(Dims d, const uint8_t* __restrict__ ids, const double* __restrict__ lo,
+                                  const double* __restrict__ hi, unsigned long long* hist_lo,
+                                  unsigned long long* hist_hi) {
+  __shared__ unsigned int hl[256], hh[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) hl[i] = hh[i] = 0u;
+  __syncthreads();
+  const long long plane = (long long)d.nx * d.ny;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < d.N; v += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(v % d.nx), j = (int)((v / d.nx) % d.ny), k = (int)(v / plane);
+    int pmin = -1, pmax = -1;
+    const int ncorner = d.dim == 3 ? 8 : 4;
+    for (int cn = 0; cn < ncorner; ++cn) {
+      // the voxel that has this node as its corner (a, b, c)
+      const int ii = wrap(i - (cn & 1), d.nx), jj = wrap(j - ((cn >> 1) & 1), d.ny);
+      const int kk = d.dim == 3 ? wrap(k - (cn >> 2), d.nz) : 0;
+      const int p = ids ? ids[(long long)kk * plane + (long long)jj * d.nx + ii] : 0;
+      if (pmin < 0 || lo[p] < lo[pmin]) pmin = p;
+      if (pmax < 0 || hi[p] > hi[pmax]) pmax = p;
+    }
+    atomicAdd(&hl[pmin], 1u);
+    atomicAdd(&hh[pmax], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    if (hl[i]) atomicAdd(&hist_lo[i], (unsigned long long)hl[i]);
+    if (hh[i]) atomicAdd(&hist_hi[i], (unsigned long long)hh[i]);
+  }
+}
+
 __global__ void phase_hist_kernel(const uint8_t* ids, long long N, unsigned long long* hist) {
   __shared__ unsigned int h[256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
@@ -751,6 +783,13 @@ __global__ void phase_hist_kernel(const uint8_t* ids, long long N, unsigned long
     if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
 }
 }  // namespace
+
+cudaError_t launch_eig_bounds(const Dims& d, const uint8_t* ids, const double* lo, const double* hi,
+                              unsigned long long* hist_lo, unsigned long long* hist_hi, cudaStream_t s) {
+  const int blocks = (int)std::min<long long>(2 * 152, (d.N + 255) / 256);
+  eig_bounds_kernel<<<blocks, 256, 0, s>>>(d, ids, lo, hi, hist_lo, hist_hi);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_phase_histogram(const uint8_t* ids, long long N, unsigned long long* hist, cudaStream_t s) {
   const int blocks = (int)std::min<long long>(2 * 152, (N + 255) / 256);

@@ -28,7 +28,7 @@ STATUS = {0: "FEHOM_OK", 1: "FEHOM_E_INVALID", 2: "FEHOM_E_UNSUPPORTED_SIZE", 3:
 EXPORTS = ("fehom_default_options", "fehom_setup", "fehom_precond_build", "fehom_solve", "fehom_destroy",
            "fehom_last_error", "fehom_query", "fehom_apply_stiffness", "fehom_rhs", "fehom_apply_precond",
            "fehom_get_symbol_inverse", "fehom_mean_flux", "fehom_kernel_times", "fehom_launch_count",
-           "fehom_fft_plan", "fehom_mean_flux_noalloc")
+           "fehom_fft_plan", "fehom_mean_flux_noalloc", "fehom_pcg_coefficients", "fehom_eig_bounds")
 
 KERNEL_CLASSES = ("stiffness", "fft_x_fwd", "fft_y_fwd", "fft_last", "fft_y_inv", "fft_x_inv")
 
@@ -90,6 +90,10 @@ def load_library(path: str = LIB_PATH):
     lib.fehom_mean_flux.restype = i
     lib.fehom_mean_flux_noalloc.argtypes = [vp, dp, vp, dp]
     lib.fehom_mean_flux_noalloc.restype = i
+    lib.fehom_pcg_coefficients.argtypes = [vp, i, i, dp, dp, C.POINTER(C.c_int)]
+    lib.fehom_pcg_coefficients.restype = i
+    lib.fehom_eig_bounds.argtypes = [vp, dp, i64p, C.POINTER(C.c_int), dp, i64p, C.POINTER(C.c_int)]
+    lib.fehom_eig_bounds.restype = i
     lib.fehom_kernel_times.argtypes = [vp, i, dp, i64p]
     lib.fehom_kernel_times.restype = i
     lib.fehom_launch_count.argtypes = [vp, i64p]
@@ -250,6 +254,25 @@ class Solver:
         n = C.c_int64()
         self._check(self.lib.fehom_launch_count(self.ctx, C.byref(n)))
         return n.value
+
+    def pcg_coefficients(self, load=0, capacity=2048):
+        """alpha_j, beta_j of the last PCG run of a load (numpy arrays)."""
+        a = np.zeros(capacity)
+        b = np.zeros(capacity)
+        n = C.c_int()
+        self._check(self.lib.fehom_pcg_coefficients(self.ctx, int(load), int(capacity), _dptr(a), _dptr(b), C.byref(n)))
+        return a[: n.value], b[: n.value]
+
+    def eig_bounds(self):
+        """Sorted lower and upper bound sequences of the eigenvalues of K_ref^+ K (length c N each)."""
+        P = 256
+        lv, hv = np.zeros(P), np.zeros(P)
+        lc, hc = np.zeros(P, np.int64), np.zeros(P, np.int64)
+        nl, nh = C.c_int(), C.c_int()
+        i64 = C.POINTER(C.c_int64)
+        self._check(self.lib.fehom_eig_bounds(self.ctx, _dptr(lv), lc.ctypes.data_as(i64), C.byref(nl), _dptr(hv),
+                                              hc.ctypes.data_as(i64), C.byref(nh)))
+        return (np.repeat(lv[: nl.value], lc[: nl.value]), np.repeat(hv[: nh.value], hc[: nh.value]))
 
     def mean_flux(self, e, u):
         e = np.ascontiguousarray(np.asarray(e, np.float64))

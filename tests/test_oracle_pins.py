@@ -393,3 +393,40 @@ def test_coated_sphere_bulk_modulus_golden():
     mod_bad = [mod[0], mod[0], mod[2]]
     sig_bad = solvers.homogenise(g, ids, mod_bad, e[None, :], method="pcg", tol=1e-8)["mean_flux"][0]
     assert abs(sig_bad[:3].mean() - gd["K_eff"]) > 0.3
+
+
+@pytest.mark.parametrize("elem,shape,physics", [("hex8_3d", (4, 4, 4), "elastic"), ("p1tri2_2d", (6, 6), "scalar"),
+                                                 ("q1_2d", (6, 4), "elastic"), ("hex8_3d", (4, 2, 6), "scalar")])
+def test_element_eigenvalue_bounds_bracket_the_spectrum(elem, shape, physics):
+    """Sec. 4.3: sorted per-node bounds bracket every eigenvalue of K_ref^-1 K on the mean-zero
+    space: lower[j + c] <= lambda_j <= upper[j] (dense generalized eigenproblem on tiny grids)."""
+    import scipy.linalg as sl
+    g = fem.Grid(shape, elem, physics)
+    rng = np.random.default_rng(17)
+    ids = rng.integers(0, 3, g.N)
+    if physics == "elastic":
+        mod = [I.isotropic_elastic_mandel(E, nu, g.dim) for E, nu in ((1, 0.3), (30, 0.2), (5, 0.4))]
+    else:
+        mod = [k * np.eye(g.dim) for k in (1.0, 30.0, 5.0)]
+    C_ref = fem.mean_material(g, ids, mod)
+    K = fem.assemble_K(g, ids, mod).toarray()
+    Kr = fem.assemble_K(g, np.zeros(g.N, int), [C_ref]).toarray()
+    Q, _ = np.linalg.qr(solvers.constant_modes(g), mode="complete")
+    B = Q[:, g.c:]
+    lam = np.sort(sl.eigh(B.T @ K @ B, B.T @ Kr @ B, eigvals_only=True))
+    lower, upper = solvers.eig_bounds(g, ids, mod, C_ref)
+    n = lam.size
+    assert np.all(lower[g.c:] <= lam + 1e-9) and np.all(lam <= upper[:n] + 1e-9)
+    # the global bounds are the phase extremes
+    assert lower[0] == min(sl.eigh(C, C_ref, eigvals_only=True).min() for C in mod)
+
+
+def test_coated_sphere_balance_reproduces_printed_moduli():
+    """Sec. 6.2 golden values: the neutral-inclusion balance at rho = 1e3 gives the printed K1, K2."""
+    from paper_2203_02962_gb300 import coated_sphere
+    with open(os.path.join(HERE, "golden", "hashin_coated_sphere.json")) as fh:
+        gd = json.load(fh)
+    (K1, G1), (K2, G2), (Ke, Ge) = coated_sphere.balanced_moduli(1e3)
+    assert abs(K1 - gd["K1"]) < 5e-9 and abs(K2 - gd["K2"]) < 5e-7
+    assert abs(G1 - gd["G1"]) < 5e-9 and abs(G2 - gd["G2"]) < 5e-7
+    assert Ke == gd["K_eff"] and abs(Ge - gd["G_eff"]) < 1e-15
