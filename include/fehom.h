@@ -154,6 +154,31 @@ fehom_status fehom_solve(fehom_ctx* ctx, int n_loads, const double* loads, doubl
                          double* fluct_out, int fluct_on_device, double* mean_flux_out, double* c_eff_out,
                          fehom_solve_info* info);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batches: many cells (contexts, possibly of different grid sizes and materials) solved together
+ * for the same loads.  The PCG iterations of all contexts are captured into one CUDA graph with one
+ * branch per context and replayed until every load of every context is finished (the stopping test
+ * and iteration bookkeeping stay per context and load, in device memory); the set-up and refinement
+ * steps of each context run on that context's own stream.  Contexts must share one device and one
+ * precision, have passed fehom_precond_build, and should have their own streams (NULL stream option)
+ * so that their branches can run concurrently.  A context must not be used elsewhere while a batch
+ * that holds it is solving.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct fehom_batch fehom_batch; /* opaque, owned by the library; the contexts stay the caller's */
+
+/* Create a batch over n_ctx contexts (the array is copied; the contexts are not). */
+fehom_status fehom_batch_create(fehom_batch** out, int n_ctx, fehom_ctx* const* ctxs);
+
+/* Solve every context of the batch for the n_loads loads (host, n_loads x m, the same for all).
+ * Outputs per context c, host arrays or NULL: mean_flux_out[c][n_loads][m], c_eff_out[c][m][m] (when
+ * n_loads == m), info[c][n_loads] (solve_ms = the whole batch).  Fields stay in each context
+ * (fluctuation fields are not returned by this call).  Returns the worst status over the contexts. */
+fehom_status fehom_solve_batch(fehom_batch* b, int n_loads, const double* loads, double tol, double* mean_flux_out,
+                               double* c_eff_out, fehom_solve_info* info);
+
+void fehom_batch_destroy(fehom_batch* b);
+const char* fehom_batch_last_error(const fehom_batch* b);
+
 /* Release every device and host resource of the context (NULL is ignored). */
 void fehom_destroy(fehom_ctx* ctx);
 

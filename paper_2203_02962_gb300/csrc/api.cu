@@ -1317,87 +1317,102 @@ static fehom_status finish_outputs(fehom_ctx* ctx, int n_loads, const double* lo
   return FEHOM_OK;
 }
 
-static fehom_status solve_fp64(fehom_ctx* ctx, int n_loads, const double* loads, double tol, const double* x0,
-                               std::vector<PcgState>& hs, std::vector<double>& flux, std::vector<double>& rel2) {
-  cudaStream_t s = ctx->stream;
-  const long long cN = (long long)ctx->d.c * ctx->d.N;
-  TRY(autotune_fft<double>(ctx, n_loads));
-  TRY(upload_tau(ctx, n_loads, loads));
-  std::vector<double> bn2, rn2;
-  TRY(residual_stats(ctx, n_loads, nullptr, ctx->b64, &bn2, nullptr));  // b = -D^T W C e
-  if (x0) {
-    // <b, K_ref^+ b> first (normalisation of the stopping test), then r0 = b - K x0
-    TRY(set_states(ctx, n_loads, tol, ctx->opt.max_iter, -1.0));
-    CK(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
-    TRY(pcg_init<double>(ctx, n_loads, ctx->r64, ctx->p64));
-    std::vector<PcgState> h0(n_loads);
-    CK(cudaMemcpyAsync(h0.data(), ctx->st, sizeof(PcgState) * n_loads, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
-    TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
-    CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
-    count_launch(ctx, 2);
-    TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->r64, nullptr, nullptr));
-    std::vector<PcgState> hs0(n_loads);
-    for (int l = 0; l < n_loads; ++l) {
-      std::memset(&hs0[l], 0, sizeof(PcgState));
-      hs0[l].bnorm2 = h0[l].bnorm2;
-      hs0[l].tol2_rel = tol * tol;
-      hs0[l].state = ST_RUN;
-      hs0[l].max_iter = ctx->opt.max_iter;
-    }
-    CK(cudaMemcpyAsync(ctx->st, hs0.data(), sizeof(PcgState) * n_loads, cudaMemcpyHostToDevice, s));
-  } else {
-    CK(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * n_loads, s));
-    TRY(set_states(ctx, n_loads, tol, ctx->opt.max_iter, -1.0));
-  }
-  TRY(pcg_init<double>(ctx, n_loads, ctx->r64, ctx->p64));
-  TRY(run_iterations<double>(ctx, n_loads, ctx->x64, ctx->r64, ctx->p64, ctx->ap64, ctx->opt.max_iter, hs));
-  // true FP64 residual of the final iterate, fused with the volume averages
-  TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->ap64, &rn2, &flux));
-  rel2.resize(n_loads);
-  for (int l = 0; l < n_loads; ++l) rel2[l] = bn2[l] > 0 ? std::sqrt(rn2[l] / bn2[l]) : 0.0;
-  return FEHOM_OK;
-}
-
-// FP32 PCG inside FP64 iterative refinement: r = b - K x (FP64), K d = r in FP32 to inner_tol, x += d.
-static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads, double tol, const double* x0,
-                                std::vector<PcgState>& hs, std::vector<int>& outer_it, std::vector<int>& inner_it,
-                                std::vector<double>& relM, std::vector<double>& flux, std::vector<double>& rel2) {
-  cudaStream_t s = ctx->stream;
-  TRY(grow32(ctx, n_loads));
-  const long long cN = (long long)ctx->d.c * ctx->d.N;
-  TRY(autotune_fft<float>(ctx, n_loads));
-  TRY(upload_tau(ctx, n_loads, loads));
-  std::vector<double> bn2, rn2;
-  TRY(residual_stats(ctx, n_loads, nullptr, ctx->b64, &bn2, nullptr));  // b = -D^T W C e
-  if (x0) {
-    CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
-    TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
-    CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
-    count_launch(ctx, 2);
-  } else {
-    CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * n_loads, s));
-  }
-  std::vector<double> bnorm2(n_loads, -1.0);
-  std::vector<bool> done(n_loads, false);
-  outer_it.assign(n_loads, 0);
-  inner_it.assign(n_loads, 0);
-  relM.assign(n_loads, 1.0);
-  hs.assign(n_loads, PcgState{});
+// One solve of one context, split into phases so that the PCG iterations of several contexts can
+// run from one captured graph (fehom_solve_batch) as well as alone (fehom_solve).
+//   FP64:  begin (tuner, b, initial preconditioner apply) -> iterations -> end_step (true residual)
+//   mixed: begin (tuner, b) -> { begin_step (FP64 residual, FP32 initial apply, per-load decision)
+//                                -> iterations -> end_step (x += d) } until every load is done
+struct SolveRun {
+  fehom_ctx* ctx = nullptr;
+  int n_loads = 0;
+  const double* loads = nullptr;
+  double tol = 0;
+  const double* x0 = nullptr;
+  bool mixed = false;
+  std::vector<PcgState> hs;
+  std::vector<int> outer_it, inner_it;
+  std::vector<double> relM, flux, rel2, bn2, rn2, bnorm2;
+  std::vector<bool> done;
   int total_inner = 0;
-  bool stats_current = false;  // flux / rn2 belong to the current x
-  const int max_outer = 60;
-  for (int outer = 0; outer < max_outer; ++outer) {
+  int steps = 0;
+  bool stats_current = false;
+  bool finished = false;
+
+  fehom_status begin() {
+    cudaStream_t s = ctx->stream;
+    const long long cN = (long long)ctx->d.c * ctx->d.N;
+    TRY(grow64(ctx, n_loads));
+    if (mixed) TRY(grow32(ctx, n_loads));
+    if (mixed) TRY(autotune_fft<float>(ctx, n_loads));
+    else TRY(autotune_fft<double>(ctx, n_loads));
+    TRY(upload_tau(ctx, n_loads, loads));
+    TRY(residual_stats(ctx, n_loads, nullptr, ctx->b64, &bn2, nullptr));  // b = -D^T W C e
+    outer_it.assign(n_loads, 0);
+    inner_it.assign(n_loads, 0);
+    relM.assign(n_loads, 1.0);
+    hs.assign(n_loads, PcgState{});
+    if (mixed) {
+      if (x0) {
+        CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
+        TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
+        CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
+        count_launch(ctx, 2);
+      } else {
+        CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * n_loads, s));
+      }
+      bnorm2.assign(n_loads, -1.0);
+      done.assign(n_loads, false);
+      return FEHOM_OK;
+    }
+    if (x0) {
+      // <b, K_ref^+ b> first (normalisation of the stopping test), then r0 = b - K x0
+      TRY(set_states(ctx, n_loads, tol, ctx->opt.max_iter, -1.0));
+      CK(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
+      TRY(pcg_init<double>(ctx, n_loads, ctx->r64, ctx->p64));
+      std::vector<PcgState> h0(n_loads);
+      CK(cudaMemcpyAsync(h0.data(), ctx->st, sizeof(PcgState) * n_loads, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
+      TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
+      CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
+      count_launch(ctx, 2);
+      TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->r64, nullptr, nullptr));
+      std::vector<PcgState> hs0(n_loads);
+      for (int l = 0; l < n_loads; ++l) {
+        std::memset(&hs0[l], 0, sizeof(PcgState));
+        hs0[l].bnorm2 = h0[l].bnorm2;
+        hs0[l].tol2_rel = tol * tol;
+        hs0[l].state = ST_RUN;
+        hs0[l].max_iter = ctx->opt.max_iter;
+      }
+      CK(cudaMemcpyAsync(ctx->st, hs0.data(), sizeof(PcgState) * n_loads, cudaMemcpyHostToDevice, s));
+    } else {
+      CK(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * n_loads, s));
+      TRY(set_states(ctx, n_loads, tol, ctx->opt.max_iter, -1.0));
+    }
+    TRY(pcg_init<double>(ctx, n_loads, ctx->r64, ctx->p64));
+    return FEHOM_OK;
+  }
+
+  // Prepares the next PCG run; *need = false when the solve is complete (nothing to iterate).
+  fehom_status begin_step(bool* need) {
+    *need = false;
+    if (finished) return FEHOM_OK;
+    if (!mixed) {
+      *need = steps == 0;
+      return FEHOM_OK;
+    }
+    cudaStream_t s = ctx->stream;
+    const long long cN = (long long)ctx->d.c * ctx->d.N;
     const double* r64 = ctx->b64;
-    if (outer > 0 || x0) {
+    if (steps > 0 || x0) {
       // true residual r = b - K x = -D^T W C (e + D x) in FP64, with ||r||^2 and <sigma>
       TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->r64, &rn2, &flux));
       r64 = ctx->r64;
       stats_current = true;
     }
-    if (outer == 0 && x0) {
+    if (steps == 0 && x0) {
       // normalisation <b, K_ref^+ b> from b itself
       CK(launch_cast_d2f(ctx->b64, ctx->r32, 1.0, cN * n_loads, s));
       count_launch(ctx);
@@ -1437,77 +1452,374 @@ static fehom_status solve_mixed(fehom_ctx* ctx, int n_loads, const double* loads
         h[l].tol2 = std::max(h[l].tol2, 0.25 * tol * tol * bnorm2[l]);
       }
     }
-    if (all || total_inner >= ctx->opt.max_iter) break;
+    if (all || total_inner >= ctx->opt.max_iter || steps >= 60) return finish_mixed();
     CK(cudaMemcpyAsync(ctx->st, h.data(), sizeof(PcgState) * n_loads, cudaMemcpyHostToDevice, s));
-    TRY(run_iterations<float>(ctx, n_loads, ctx->x32, ctx->r32, ctx->p32, ctx->ap32, remaining, hs));
+    *need = true;
+    return FEHOM_OK;
+  }
+
+  // After the PCG run: hs holds the device states at its end.
+  fehom_status end_step() {
+    ++steps;
+    if (!mixed) {
+      TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->ap64, &rn2, &flux));  // true residual + averages
+      rel2.resize(n_loads);
+      for (int l = 0; l < n_loads; ++l) rel2[l] = bn2[l] > 0 ? std::sqrt(rn2[l] / bn2[l]) : 0.0;
+      finished = true;
+      return FEHOM_OK;
+    }
+    const long long cN = (long long)ctx->d.c * ctx->d.N;
     int mx = 0;
     for (int l = 0; l < n_loads; ++l) {
       if (!done[l]) inner_it[l] += hs[l].iter;
       mx = std::max(mx, hs[l].iter);
     }
     total_inner += mx;
-    CK(launch_add_f2d(ctx->x32, ctx->x64, 1.0, cN * n_loads, s));
+    CK(launch_add_f2d(ctx->x32, ctx->x64, 1.0, cN * n_loads, ctx->stream));
     count_launch(ctx);
     stats_current = false;
+    return FEHOM_OK;
   }
-  if (!stats_current) TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->ap64, &rn2, &flux));
-  rel2.resize(n_loads);
-  for (int l = 0; l < n_loads; ++l) {
-    hs[l].iter = inner_it[l];
-    hs[l].state = done[l] ? ST_DONE : ST_MAXIT;
-    rel2[l] = bn2[l] > 0 ? std::sqrt(rn2[l] / bn2[l]) : 0.0;
+
+  fehom_status finish_mixed() {
+    if (!stats_current) TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->ap64, &rn2, &flux));
+    rel2.resize(n_loads);
+    for (int l = 0; l < n_loads; ++l) {
+      hs[l].iter = inner_it[l];
+      hs[l].state = done[l] ? ST_DONE : ST_MAXIT;
+      rel2[l] = bn2[l] > 0 ? std::sqrt(rn2[l] / bn2[l]) : 0.0;
+    }
+    finished = true;
+    return FEHOM_OK;
+  }
+
+  // outputs, info and status of the finished solve
+  fehom_status report(double* fluct_out, int fluct_on_device, double* mean_flux_out, double* c_eff_out,
+                      fehom_solve_info* info, float ms) {
+    TRY(finish_outputs(ctx, n_loads, loads, fluct_out, fluct_on_device, mean_flux_out, c_eff_out, flux));
+    bool brk = false, notconv = false;
+    for (int l = 0; l < n_loads; ++l) {
+      if (hs[l].state == ST_BREAK) brk = true;
+      if (hs[l].state != ST_DONE) notconv = true;
+      if (info) {
+        info[l].iterations = hs[l].iter;
+        info[l].refinements = mixed ? outer_it[l] : 0;
+        info[l].converged = hs[l].state == ST_DONE;
+        info[l].rel_residual_M =
+            mixed ? relM[l] : (hs[l].bnorm2 > 0 ? std::sqrt(std::max(hs[l].rz, 0.0) / hs[l].bnorm2) : 0.0);
+        info[l].rel_residual_2 = rel2[l];
+        info[l].solve_ms = ms;
+      }
+    }
+    if (brk) FAIL(FEHOM_E_BREAKDOWN, "PCG breakdown (non-positive or non-finite curvature)");
+    if (notconv) FAIL(FEHOM_E_NOT_CONVERGED, "PCG did not reach the tolerance within max_iter");
+    ctx->err.clear();
+    return FEHOM_OK;
+  }
+};
+
+static fehom_status check_solve_args(fehom_ctx* ctx, int n_loads, const double* loads, double tol) {
+  if (!ctx->built) FAIL(FEHOM_E_STATE, "fehom_solve before fehom_precond_build");
+  if (n_loads < 1 || n_loads > kMaxLoads || !loads) FAIL(FEHOM_E_INVALID, "n_loads must be in 1..64 with loads given");
+  if (!(tol > 0.0 && tol < 1.0)) FAIL(FEHOM_E_INVALID, "tol must be in (0, 1)");
+  for (int i = 0; i < n_loads * ctx->m; ++i)
+    if (!std::isfinite(loads[i])) FAIL(FEHOM_E_INVALID, "non-finite load");
+  return FEHOM_OK;
+}
+
+// ----------------------------------------------------------------------------------------------------
+// batches of contexts: their PCG iterations replayed from one CUDA graph, one branch per context
+// ----------------------------------------------------------------------------------------------------
+}  // extern "C"
+
+struct fehom_batch {
+  std::vector<fehom_ctx*> ctxs;
+  cudaStream_t main = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  PcgState* st = nullptr;                      // [n_ctx][kMaxLoads], the contexts' states during a batch
+  cudaGraphExec_t exec[2] = {nullptr, nullptr}; // per precision (FP64, FP32)
+  int exec_loads[2] = {0, 0};
+  int per_ctx_launches[2] = {0, 0};
+  std::string err;
+};
+
+namespace {
+
+#define BCK(call)                                                                 \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      b->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+      return e_ == cudaErrorMemoryAllocation ? FEHOM_E_OOM : FEHOM_E_CUDA;        \
+    }                                                                             \
+  } while (0)
+
+fehom_status mark_done(fehom_ctx* ctx, int n_loads) {
+  std::vector<PcgState> h(n_loads);
+  for (auto& x : h) {
+    std::memset(&x, 0, sizeof(x));
+    x.state = ST_DONE;
+  }
+  CK(cudaMemcpyAsync(ctx->st, h.data(), sizeof(PcgState) * n_loads, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FEHOM_OK;
+}
+
+template <typename T> T* buf_x(fehom_ctx* c) { if constexpr (sizeof(T) == 4) return c->x32; else return c->x64; }
+template <typename T> T* buf_r(fehom_ctx* c) { if constexpr (sizeof(T) == 4) return c->r32; else return c->r64; }
+template <typename T> T* buf_p(fehom_ctx* c) { if constexpr (sizeof(T) == 4) return c->p32; else return c->p64; }
+template <typename T> T* buf_ap(fehom_ctx* c) { if constexpr (sizeof(T) == 4) return c->ap32; else return c->ap64; }
+
+// PCG iterations of every context of the batch until all their loads are finished
+template <typename T>
+fehom_status run_iterations_batch(fehom_batch* b, std::vector<SolveRun>& runs, int n_loads, int max_iter) {
+  const int prec = sizeof(T) == 4 ? 1 : 0;
+  const int nc = (int)b->ctxs.size();
+  if (!b->exec[prec] || b->exec_loads[prec] != n_loads) {
+    if (b->exec[prec]) cudaGraphExecDestroy(b->exec[prec]);
+    b->exec[prec] = nullptr;
+    cudaGraph_t g;
+    BCK(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(b->fork, b->main);
+    int launches = 0;
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+      fehom_ctx* ctx = b->ctxs[c];
+      e = cudaStreamWaitEvent(ctx->stream, b->fork, 0);
+      const long long before = ctx->launches;
+      for (int i = 0; i < kChunk && e == cudaSuccess; ++i)
+        e = pcg_iteration<T>(ctx, n_loads, buf_x<T>(ctx), buf_r<T>(ctx), buf_p<T>(ctx), buf_ap<T>(ctx), ctx->stream);
+      launches = (int)(ctx->launches - before);
+      ctx->launches = before;  // counted per replay
+      if (e == cudaSuccess) e = cudaEventRecord(b->joins[c], ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->joins[c], 0);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(b->main, &g);
+    BCK(e);
+    BCK(e2);
+    BCK(cudaGraphInstantiate(&b->exec[prec], g, 0));
+    cudaGraphDestroy(g);
+    b->exec_loads[prec] = n_loads;
+    b->per_ctx_launches[prec] = launches;
+  }
+  // the contexts' set-up work (on their own streams) precedes the replays
+  for (int c = 0; c < nc; ++c) {
+    BCK(cudaEventRecord(b->joins[c], b->ctxs[c]->stream));
+    BCK(cudaStreamWaitEvent(b->main, b->joins[c], 0));
+  }
+  std::vector<PcgState> hs((size_t)nc * kMaxLoads);
+  for (int done = 0; done < max_iter + kChunk;) {
+    BCK(cudaGraphLaunch(b->exec[prec], b->main));
+    for (auto* ctx : b->ctxs) ctx->launches += b->per_ctx_launches[prec];
+    done += kChunk;
+    BCK(cudaMemcpyAsync(hs.data(), b->st, sizeof(PcgState) * hs.size(), cudaMemcpyDeviceToHost, b->main));
+    BCK(cudaStreamSynchronize(b->main));
+    bool all = true;
+    for (int c = 0; c < nc; ++c)
+      for (int l = 0; l < n_loads; ++l) {
+        const int st = hs[(size_t)c * kMaxLoads + l].state;
+        if (st == ST_RUN || st == ST_CONV || st == ST_FIN_MAX) all = false;
+      }
+    if (all) break;
+  }
+  for (int c = 0; c < nc; ++c) {
+    runs[c].hs.assign(hs.begin() + (size_t)c * kMaxLoads, hs.begin() + (size_t)c * kMaxLoads + n_loads);
+    for (int l = 0; l < n_loads; ++l) b->ctxs[c]->hist_count[l] = std::min(runs[c].hs[l].iter, kHist);
   }
   return FEHOM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fehom_status fehom_batch_create(fehom_batch** out, int n_ctx, fehom_ctx* const* ctxs) {
+  if (!out || n_ctx < 1 || !ctxs) return FEHOM_E_INVALID;
+  *out = nullptr;
+  for (int c = 0; c < n_ctx; ++c)
+    if (!ctxs[c]) return FEHOM_E_INVALID;
+  fehom_batch* b = new (std::nothrow) fehom_batch();
+  if (!b) return FEHOM_E_OOM;
+  b->ctxs.assign(ctxs, ctxs + n_ctx);
+  auto fail = [&](fehom_status st) {
+    g_setup_error = b->err;
+    fehom_batch_destroy(b);
+    return st;
+  };
+  const int dev = ctxs[0]->device;
+  const int prec = ctxs[0]->opt.precision;
+  for (int c = 0; c < n_ctx; ++c) {
+    if (ctxs[c]->device != dev) {
+      b->err = "all contexts of a batch must live on one device";
+      return fail(FEHOM_E_INVALID);
+    }
+    if (ctxs[c]->opt.precision != prec) {
+      b->err = "all contexts of a batch must use the same precision";
+      return fail(FEHOM_E_INVALID);
+    }
+    for (int k = 0; k < c; ++k)
+      if (ctxs[k] == ctxs[c]) {
+        b->err = "a context appears twice in the batch";
+        return fail(FEHOM_E_INVALID);
+      }
+  }
+  cudaError_t e = cudaStreamCreate(&b->main);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  b->joins.resize(n_ctx, nullptr);
+  for (int c = 0; c < n_ctx && e == cudaSuccess; ++c) e = cudaEventCreateWithFlags(&b->joins[c], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc(&b->st, sizeof(PcgState) * (size_t)n_ctx * kMaxLoads);
+  if (e != cudaSuccess) {
+    b->err = std::string("fehom_batch_create: ") + cudaGetErrorString(e);
+    return fail(e == cudaErrorMemoryAllocation ? FEHOM_E_OOM : FEHOM_E_CUDA);
+  }
+  *out = b;
+  return FEHOM_OK;
+}
+
+void fehom_batch_destroy(fehom_batch* b) {
+  if (!b) return;
+  if (b->main) cudaStreamSynchronize(b->main);
+  for (int p = 0; p < 2; ++p)
+    if (b->exec[p]) cudaGraphExecDestroy(b->exec[p]);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (auto ev : b->joins)
+    if (ev) cudaEventDestroy(ev);
+  if (b->st) cudaFree(b->st);
+  if (b->main) cudaStreamDestroy(b->main);
+  delete b;
+}
+
+const char* fehom_batch_last_error(const fehom_batch* b) { return b ? b->err.c_str() : g_setup_error.c_str(); }
+
+fehom_status fehom_solve_batch(fehom_batch* b, int n_loads, const double* loads, double tol, double* mean_flux_out,
+                               double* c_eff_out, fehom_solve_info* info) {
+  if (!b) return FEHOM_E_INVALID;
+  const int nc = (int)b->ctxs.size();
+  for (int c = 0; c < nc; ++c) {
+    const fehom_status st = check_solve_args(b->ctxs[c], n_loads, loads, tol);
+    if (st != FEHOM_OK) {
+      b->err = "context " + std::to_string(c) + ": " + b->ctxs[c]->err;
+      return st;
+    }
+  }
+  const bool mixed = b->ctxs[0]->opt.precision == FEHOM_MIXED;
+  // every context keeps its PCG states in the batch's array while the batch runs
+  std::vector<PcgState*> saved(nc);
+  for (int c = 0; c < nc; ++c) {
+    saved[c] = b->ctxs[c]->st;
+    b->ctxs[c]->st = b->st + (size_t)c * kMaxLoads;
+  }
+  auto body = [&]() -> fehom_status {
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    BCK(cudaEventRecord(e0, b->main));
+    std::vector<SolveRun> runs(nc);
+    for (int c = 0; c < nc; ++c) {
+      SolveRun& r = runs[c];
+      r.ctx = b->ctxs[c];
+      r.n_loads = n_loads;
+      r.loads = loads;
+      r.tol = tol;
+      r.mixed = mixed;
+      const fehom_status st = r.begin();
+      if (st != FEHOM_OK) {
+        b->err = "context " + std::to_string(c) + ": " + r.ctx->err;
+        return st;
+      }
+    }
+    int max_iter = 0;
+    for (auto* ctx : b->ctxs) max_iter = std::max(max_iter, ctx->opt.max_iter);
+    for (;;) {
+      bool any = false;
+      for (int c = 0; c < nc; ++c) {
+        bool need = false;
+        fehom_status st = runs[c].begin_step(&need);
+        if (st == FEHOM_OK && !need) st = mark_done(runs[c].ctx, n_loads);
+        if (st != FEHOM_OK) {
+          b->err = "context " + std::to_string(c) + ": " + runs[c].ctx->err;
+          return st;
+        }
+        any = any || need;
+      }
+      if (!any) break;
+      const fehom_status st = mixed ? run_iterations_batch<float>(b, runs, n_loads, max_iter)
+                                    : run_iterations_batch<double>(b, runs, n_loads, max_iter);
+      if (st != FEHOM_OK) return st;
+      for (int c = 0; c < nc; ++c) {
+        if (runs[c].finished) continue;
+        const fehom_status st2 = runs[c].end_step();
+        if (st2 != FEHOM_OK) {
+          b->err = "context " + std::to_string(c) + ": " + runs[c].ctx->err;
+          return st2;
+        }
+      }
+    }
+    for (auto* ctx : b->ctxs) {
+      BCK(cudaEventRecord(b->joins[0], ctx->stream));
+      BCK(cudaStreamWaitEvent(b->main, b->joins[0], 0));
+    }
+    BCK(cudaEventRecord(e1, b->main));
+    BCK(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    fehom_status worst = FEHOM_OK;
+    const int m = b->ctxs[0]->m;
+    for (int c = 0; c < nc; ++c) {
+      const int mc = b->ctxs[c]->m;
+      const fehom_status st = runs[c].report(nullptr, 0, mean_flux_out ? mean_flux_out + (size_t)c * n_loads * mc : nullptr,
+                                             c_eff_out ? c_eff_out + (size_t)c * mc * mc : nullptr,
+                                             info ? info + (size_t)c * n_loads : nullptr, ms);
+      if (st != FEHOM_OK && (worst == FEHOM_OK || st == FEHOM_E_CUDA)) {
+        worst = st;
+        b->err = "context " + std::to_string(c) + ": " + runs[c].ctx->err;
+      }
+    }
+    (void)m;
+    if (worst == FEHOM_OK) b->err.clear();
+    return worst;
+  };
+  const fehom_status st = body();
+  for (int c = 0; c < nc; ++c) b->ctxs[c]->st = saved[c];
+  return st;
 }
 
 fehom_status fehom_solve(fehom_ctx* ctx, int n_loads, const double* loads, double tol, const double* x0,
                          double* fluct_out, int fluct_on_device, double* mean_flux_out, double* c_eff_out,
                          fehom_solve_info* info) {
   if (!ctx) return FEHOM_E_INVALID;
-  if (!ctx->built) FAIL(FEHOM_E_STATE, "fehom_solve before fehom_precond_build");
-  if (n_loads < 1 || n_loads > kMaxLoads || !loads) FAIL(FEHOM_E_INVALID, "n_loads must be in 1..64 with loads given");
-  if (!(tol > 0.0 && tol < 1.0)) FAIL(FEHOM_E_INVALID, "tol must be in (0, 1)");
-  for (int i = 0; i < n_loads * ctx->m; ++i)
-    if (!std::isfinite(loads[i])) FAIL(FEHOM_E_INVALID, "non-finite load");
-  TRY(grow64(ctx, n_loads));
+  TRY(check_solve_args(ctx, n_loads, loads, tol));
   cudaStream_t s = ctx->stream;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, s));
-  std::vector<PcgState> hs;
-  std::vector<int> outer_it(n_loads, 0), inner_it;
-  std::vector<double> relM(n_loads, 0.0);
-  fehom_status st;
-  const bool mixed = ctx->opt.precision == FEHOM_MIXED;
-  std::vector<double> flux, rel2;
-  if (mixed) st = solve_mixed(ctx, n_loads, loads, tol, x0, hs, outer_it, inner_it, relM, flux, rel2);
-  else st = solve_fp64(ctx, n_loads, loads, tol, x0, hs, flux, rel2);
-  if (st != FEHOM_OK) return st;
+  SolveRun run;
+  run.ctx = ctx;
+  run.n_loads = n_loads;
+  run.loads = loads;
+  run.tol = tol;
+  run.x0 = x0;
+  run.mixed = ctx->opt.precision == FEHOM_MIXED;
+  TRY(run.begin());
+  for (;;) {
+    bool need = false;
+    TRY(run.begin_step(&need));
+    if (!need) break;
+    if (run.mixed) TRY(run_iterations<float>(ctx, n_loads, ctx->x32, ctx->r32, ctx->p32, ctx->ap32,
+                                             std::max(1, ctx->opt.max_iter - run.total_inner), run.hs));
+    else TRY(run_iterations<double>(ctx, n_loads, ctx->x64, ctx->r64, ctx->p64, ctx->ap64, ctx->opt.max_iter, run.hs));
+    TRY(run.end_step());
+  }
   CK(cudaEventRecord(e1, s));
   CK(cudaEventSynchronize(e1));
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  TRY(finish_outputs(ctx, n_loads, loads, fluct_out, fluct_on_device, mean_flux_out, c_eff_out, flux));
-  bool brk = false, notconv = false;
-  for (int l = 0; l < n_loads; ++l) {
-    if (hs[l].state == ST_BREAK) brk = true;
-    if (hs[l].state != ST_DONE) notconv = true;
-    if (info) {
-      info[l].iterations = hs[l].iter;
-      info[l].refinements = mixed ? outer_it[l] : 0;
-      info[l].converged = hs[l].state == ST_DONE;
-      info[l].rel_residual_M = mixed ? relM[l] : (hs[l].bnorm2 > 0 ? std::sqrt(std::max(hs[l].rz, 0.0) / hs[l].bnorm2) : 0.0);
-      info[l].rel_residual_2 = rel2[l];
-      info[l].solve_ms = ms;
-    }
-  }
-  if (brk) FAIL(FEHOM_E_BREAKDOWN, "PCG breakdown (non-positive or non-finite curvature)");
-  if (notconv) FAIL(FEHOM_E_NOT_CONVERGED, "PCG did not reach the tolerance within max_iter");
-  ctx->err.clear();
-  return FEHOM_OK;
+  return run.report(fluct_out, fluct_on_device, mean_flux_out, c_eff_out, info, ms);
 }
 
 }  // extern "C"

@@ -28,7 +28,8 @@ STATUS = {0: "FEHOM_OK", 1: "FEHOM_E_INVALID", 2: "FEHOM_E_UNSUPPORTED_SIZE", 3:
 EXPORTS = ("fehom_default_options", "fehom_setup", "fehom_precond_build", "fehom_solve", "fehom_destroy",
            "fehom_last_error", "fehom_query", "fehom_apply_stiffness", "fehom_rhs", "fehom_apply_precond",
            "fehom_get_symbol_inverse", "fehom_mean_flux", "fehom_kernel_times", "fehom_launch_count",
-           "fehom_fft_plan", "fehom_mean_flux_noalloc", "fehom_pcg_coefficients", "fehom_eig_bounds")
+           "fehom_fft_plan", "fehom_mean_flux_noalloc", "fehom_pcg_coefficients", "fehom_eig_bounds",
+           "fehom_batch_create", "fehom_solve_batch", "fehom_batch_destroy", "fehom_batch_last_error")
 
 KERNEL_CLASSES = ("stiffness", "fft_x_fwd", "fft_y_fwd", "fft_last", "fft_y_inv", "fft_x_inv")
 
@@ -94,6 +95,14 @@ def load_library(path: str = LIB_PATH):
     lib.fehom_pcg_coefficients.restype = i
     lib.fehom_eig_bounds.argtypes = [vp, dp, i64p, C.POINTER(C.c_int), dp, i64p, C.POINTER(C.c_int)]
     lib.fehom_eig_bounds.restype = i
+    lib.fehom_batch_create.argtypes = [C.POINTER(vp), i, C.POINTER(vp)]
+    lib.fehom_batch_create.restype = i
+    lib.fehom_solve_batch.argtypes = [vp, i, dp, d, dp, dp, C.POINTER(SolveInfo)]
+    lib.fehom_solve_batch.restype = i
+    lib.fehom_batch_destroy.argtypes = [vp]
+    lib.fehom_batch_destroy.restype = None
+    lib.fehom_batch_last_error.argtypes = [vp]
+    lib.fehom_batch_last_error.restype = C.c_char_p
     lib.fehom_kernel_times.argtypes = [vp, i, dp, i64p]
     lib.fehom_kernel_times.restype = i
     lib.fehom_launch_count.argtypes = [vp, i64p]
@@ -279,3 +288,41 @@ class Solver:
         out = np.zeros(self.m)
         self._check(self.lib.fehom_mean_flux(self.ctx, _dptr(e), C.c_void_p(u.data_ptr()), _dptr(out)))
         return out
+
+
+class Batch:
+    """Several Solver cells solved together (fehom_solve_batch): one CUDA graph, one branch per cell."""
+
+    def __init__(self, solvers):
+        self.lib = load_library()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[sv.ctx.value for sv in self.solvers])
+        b = C.c_void_p()
+        st = self.lib.fehom_batch_create(C.byref(b), len(self.solvers), arr)
+        if st != 0:
+            raise FehomError(st, self.lib.fehom_batch_last_error(None).decode())
+        self.b = b
+
+    def solve(self, loads, tol, raise_on_failure=True):
+        loads = np.ascontiguousarray(np.atleast_2d(np.asarray(loads, np.float64)))
+        L, nc = loads.shape[0], len(self.solvers)
+        m = self.solvers[0].m
+        flux = np.zeros((nc, L, m))
+        ceff = np.full((nc, m, m), np.nan)
+        info = (SolveInfo * (nc * L))()
+        st = self.lib.fehom_solve_batch(self.b, L, _dptr(loads), float(tol), _dptr(flux), _dptr(ceff), info)
+        if st != 0 and raise_on_failure:
+            raise FehomError(st, self.lib.fehom_batch_last_error(self.b).decode())
+        infos = [[{k: getattr(info[c * L + l], k) for k, _ in SolveInfo._fields_} for l in range(L)] for c in range(nc)]
+        return dict(status=st, mean_flux=flux, C_eff=ceff if L == m else None, info=infos)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.fehom_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -206,3 +206,20 @@ def hashin_coated_sphere_moduli():
     G1, G2, Geff = 0.00079236, 0.7923620, 0.6
     return np.stack([bulk_shear_mandel(K1, G1), bulk_shear_mandel(K2, G2), bulk_shear_mandel(Keff, Geff)])
 
+
+
+def workload_batched_spheres(count: int = 48, sizes=(32, 64, 96), seed0: int = 0):
+    """Cells of uneven size for batched solves: ``count`` instances split evenly over ``sizes``;
+    60 periodic spheres with radii U[n/16, n/8] (the 128^3 workload's statistics scaled to n), matrix
+    E = 1, nu = 0.3, inclusions nu = 0.2 with a per-instance stiffness contrast 10^U[1, 3]."""
+    out = []
+    per = count // len(sizes)
+    for i in range(count):
+        n = sizes[min(i // per, len(sizes) - 1)]
+        seed = seed0 + i
+        rng = np.random.default_rng(10_000 + seed)
+        contrast = 10.0 ** rng.uniform(1.0, 3.0)
+        ids = spheres3d(n, 60, n / 16.0, n / 8.0, seed)
+        moduli = np.stack([isotropic_elastic_mandel(1.0, 0.3), isotropic_elastic_mandel(contrast, 0.2)])
+        out.append(dict(n=(n, n, n), ids=ids, moduli=moduli, contrast=contrast, seed=seed))
+    return out

@@ -357,3 +357,34 @@ def test_autotuned_plans_are_valid_and_agree():
     for p in plans[2:]:
         assert p["pairs"] == 0 and p["tc_last"] == 0
     assert _rel(outs[0], outs[2]) < 1e-9 and _rel(outs[1], outs[3]) < 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_equals_individual_solves(precision):
+    """fehom_solve_batch (one graph, one branch per cell; cells of different sizes and contrasts)
+    gives the per-cell results of separate fehom_solve calls."""
+    fehom = _fehom()
+    cells = I.workload_batched_spheres(count=4, sizes=(16, 24), seed0=30)
+    def make():
+        return [fehom.Solver("hex8_3d", "elastic", c["n"], c["ids"], c["moduli"], precision=precision, autotune=False)
+                for c in cells]
+    single = make()
+    ref = []
+    for sv in single:
+        sv.precond_build()
+        ref.append(sv.solve(np.eye(6), tol=1e-8, fields=None))
+    solvers_b = make()
+    for sv in solvers_b:
+        sv.precond_build()
+    batch = fehom.Batch(solvers_b)
+    out = batch.solve(np.eye(6), tol=1e-8)
+    tol = 1e-10 if precision == "fp64" else 1e-8
+    for c in range(len(cells)):
+        assert _rel(out["C_eff"][c], ref[c]["C_eff"]) < tol
+        assert [i["iterations"] for i in out["info"][c]] == [i["iterations"] for i in ref[c]["info"]]
+    # a second batch solve reuses the captured graph and gives the same answer
+    out2 = batch.solve(np.eye(6), tol=1e-8)
+    assert _rel(out2["C_eff"], out["C_eff"]) < tol
+    batch.close()
+    for sv in single + solvers_b:
+        sv.close()
