@@ -109,7 +109,7 @@ def kernel_model(s):
     spec = c * hs * 2 * s              # one half-spectrum pass over the c components
     sym = 6 * s * hs                   # packed 3x3 symmetric K_hat^+ per half-spectrum k
     return {
-        "stiffness": {"bytes": 2 * c * s + 1, "fp64_ops": 250},
+        "stiffness": {"bytes": 2 * c * s + 1, "fp64_ops": 204},
         "fft_x_fwd": {"bytes": 3 * c * s + spec, "fp64_ops": 3 * 4.0 * 7 * 3.5 / 2 * 2},
         "fft_y_fwd": {"bytes": 2 * spec, "fp64_ops": 3 * hs * 7 * 3.5},
         "fft_last": {"bytes": 2 * spec + sym, "fp64_ops": 3 * hs * 2 * 7 * 3.5 + hs * 18},

@@ -479,11 +479,11 @@ fehom_status autotune_fft(fehom_ctx* ctx, int n_loads) {
       }
     }
   };
-  const int pairs[2] = {8, 4};
+  const int pairs[3] = {16, 8, 4};
   const int tcs[4] = {16, 8, 4, 2};
   int bp, by = 0, bl;
   double mp, my = 0, ml;
-  pick(pairs, 2, [&](int P) {
+  pick(pairs, 3, [&](int P) {
     FftArgs f = base;
     f.pairs = P;
     f.f0 = fin;
@@ -1050,25 +1050,54 @@ fehom_status fehom_precond_build(fehom_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   TRY(grow64(ctx, c));
   const long long cN = (long long)c * ctx->d.N;
-  // Algorithm 2: impulses i^beta at node 0 of component beta (one "load" per beta)
-  CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * c, s));
-  const double one = 1.0;
-  for (int be = 0; be < c; ++be)
-    CK(cudaMemcpyAsync(ctx->x64 + be * cN + (long long)be * ctx->d.N, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+  // Algorithm 2: the columns K_ref i^beta for the unit impulses i^beta at node 0 of component beta
+  // (one "load" per beta).  K_ref i^beta is nonzero only on the 3^d nodes around node 0, so when
+  // every axis has at least 4 nodes it is computed on a periodic 4^d proxy grid of the same spacing
+  // (same element tables) and placed into the full grid; otherwise on the full grid itself.
+  const bool proxy = ctx->d.nx >= 4 && ctx->d.ny >= 4 && (ctx->d.dim == 2 || ctx->d.nz >= 4);
   StencilArgs a{};
-  a.d = ctx->d;
-  a.x = ctx->x64;
-  a.y = ctx->ap64;
   a.ids = nullptr;  // uniform reference material
   a.mats = ctx->rmats64;
   a.iso = (ctx->iso_ref && ctx->iso) ? ctx->riso64 : nullptr;
   a.n_phases = 1;
   a.n_loads = c;
-  a.load_stride = cN;
   a.y_scale = 1.0;
   a.red = ctx->red;
-  CK(launch_stiffness<double>(a, s));
-  count_launch(ctx);
+  const double one = 1.0;
+  if (proxy) {
+    Dims pd = ctx->d;
+    pd.nx = pd.ny = 4;
+    pd.nz = ctx->d.dim == 3 ? 4 : 1;
+    pd.nxh = 3;
+    pd.N = (long long)pd.nx * pd.ny * pd.nz;
+    pd.Nh = (long long)pd.nxh * pd.ny * pd.nz;
+    const long long pcN = (long long)c * pd.N;
+    TRY(ensure_partial(ctx, (size_t)std::max<long long>(2 * c * pcN, 4 * 2 * 152)));
+    double* px = ctx->partial;
+    double* py = ctx->partial + c * pcN;
+    CK(cudaMemsetAsync(px, 0, sizeof(double) * c * pcN, s));
+    for (int be = 0; be < c; ++be)
+      CK(cudaMemcpyAsync(px + be * pcN + (long long)be * pd.N, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    a.d = pd;
+    a.x = px;
+    a.y = py;
+    a.load_stride = pcN;
+    CK(launch_stiffness<double>(a, s));
+    count_launch(ctx);
+    CK(cudaMemsetAsync(ctx->ap64, 0, sizeof(double) * cN * c, s));
+    CK(launch_impulse_scatter(py, pd, ctx->d, c, ctx->ap64, s));
+    count_launch(ctx);
+  } else {
+    CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * c, s));
+    for (int be = 0; be < c; ++be)
+      CK(cudaMemcpyAsync(ctx->x64 + be * cN + (long long)be * ctx->d.N, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    a.d = ctx->d;
+    a.x = ctx->x64;
+    a.y = ctx->ap64;
+    a.load_stride = cN;
+    CK(launch_stiffness<double>(a, s));
+    count_launch(ctx);
+  }
   // forward FFT of every component of every column -> spec64[beta][alpha][Nh]
   FftArgs f;
   fill_dims_args(ctx, f, false, c);

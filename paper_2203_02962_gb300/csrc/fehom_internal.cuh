@@ -57,6 +57,34 @@ struct RedScratch {
 
 constexpr int kHist = 2048;  // PCG coefficients kept per load (for the Lanczos / Ritz check)
 
+// Dot-product accumulator of the FP32 kernels.  On GB300 an FP64 instruction costs 64 FP32 lanes, so
+// the FP32 kernels do not accumulate in FP64 directly: each product is split exactly into float
+// head + tail (fma), both parts are added with Neumaier's compensated summation, and the per-thread
+// (sum, compensation) pair is converted to FP64 once.  The per-thread result carries FP64-level
+// accuracy; the CTA and grid reductions that follow are FP64.  The FP64 kernels accumulate in FP64.
+template <typename T> struct DotAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T a, T b) { s = fma((double)a, (double)b, s); }
+  __device__ __forceinline__ void add_scaled(T a, T b, double w) { s = fma(w * (double)a, (double)b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct DotAcc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add1(float v) {
+    const float t = s + v;
+    c += (fabsf(s) >= fabsf(v)) ? (s - t) + v : (v - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = a * b;
+    add1(p);
+    add1(fmaf(a, b, -p));
+  }
+  // w = 1 or 2 (Parseval weights): exact in float
+  __device__ __forceinline__ void add_scaled(float a, float b, double w) { add((float)w * a, b); }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // ------------------------------------------------------------------------------------------------
 // stencil.cu
 // ------------------------------------------------------------------------------------------------
@@ -128,7 +156,7 @@ struct FftArgs {
   PcgState* st;      // nullptr = no PCG bookkeeping
   RedScratch red;
   int init;          // solve pass: 1 = first apply (sets rz, bnorm2)
-  // launch plan (0 = built-in choice): x-line pairs per CTA (4 or 8), columns per CTA of the y pass
+  // launch plan (0 = built-in choice): x-line pairs per CTA (4, 8 or 16), columns per CTA of the y pass
   // and of the last-axis pass (2, 4, 8 or 16)
   int pairs, tc_y, tc_last;
 };
@@ -160,6 +188,12 @@ cudaError_t make_twiddles(int L, double2** d64, float2** d32);
 // ------------------------------------------------------------------------------------------------
 cudaError_t launch_cast_d2f(const double* x, float* y, double scale, long long n, cudaStream_t s);
 cudaError_t launch_add_f2d(const float* x, double* y, double scale, long long n, cudaStream_t s);
+// Algorithm 2 on a proxy grid: copies the 3^d-node neighbourhood of node 0 of the impulse responses
+// computed on the 4^d proxy `pd` (py: [beta][alpha][pd.N]) into zeroed full-grid columns
+// (out: [beta][alpha][full.N])
+cudaError_t launch_impulse_scatter(const double* py, const Dims& pd, const Dims& full, int c, double* out,
+                                   cudaStream_t s);
+
 // removes the mean of every (component, load); partial: scratch of n_loads * c * 304 doubles (two launches)
 cudaError_t launch_sub_mean(double* x, int c, long long N, int n_loads, long long load_stride, double* partial,
                             cudaStream_t s);

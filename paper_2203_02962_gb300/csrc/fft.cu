@@ -485,14 +485,14 @@ __global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, const
     return;
   }
   const T* sym = reinterpret_cast<const T*>(a.sym);
-  double dot = 0.0;
+  DotAcc<T> dot;
   for (int idx = threadIdx.x; idx < m.L * TC; idx += ST) {
     const int e = idx / TC, t = idx % TC;
     const long long cb = base[t];
     if (cb < 0) continue;
     const long long ti = cb + (long long)e * m.estride;
     const int kx = kxs[t];
-    const double wgt = (kx == 0 || kx == half) ? 1.0 : 2.0;
+    const T wgt = (kx == 0 || kx == half) ? T(1) : T(2);
     C r[NC], z[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) r[c] = res[e * W + c * TC + t];
@@ -510,14 +510,12 @@ __global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, const
       z[1] = mk<C>(fma(k01, r[0].x, fma(k11, r[1].x, k12 * r[2].x)), fma(k01, r[0].y, fma(k11, r[1].y, k12 * r[2].y)));
       z[2] = mk<C>(fma(k02, r[0].x, fma(k12, r[1].x, k22 * r[2].x)), fma(k02, r[0].y, fma(k12, r[1].y, k22 * r[2].y)));
     }
-    double acc = 0.0;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      acc = fma((double)r[c].x, (double)z[c].x, acc);
-      acc = fma((double)r[c].y, (double)z[c].y, acc);
+      dot.add(wgt * r[c].x, z[c].x);  // wgt in {1, 2}: exact
+      dot.add(wgt * r[c].y, z[c].y);
       res[e * W + c * TC + t] = z[c];
     }
-    dot = fma(wgt, acc, dot);
   }
   __syncthreads();
   const C* out = fft_smem<C, true, W, W>(res, other, m.L, tw);
@@ -527,7 +525,7 @@ __global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, const
     if (cb >= 0) spec[comp * Nh + cb + (long long)e * m.estride] = out[idx];
   }
   if (a.st != nullptr) {
-    const double part = block_sum(dot, red_sh);
+    const double part = block_sum(dot.value(), red_sh);
     double total;
     if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load, gridDim.x,
                          blockIdx.x, red_sh, &total)) {
@@ -645,7 +643,7 @@ constexpr size_t kSmemMax = 200 * 1024;
 template <typename T> int x_pairs(const Dims& d, int planned) {
   using C = typename V2<T>::t;
   auto fits = [&](int P) { return 2ull * d.nx * (P + 1) * sizeof(C) <= 160 * 1024; };
-  if ((planned == 4 || planned == 8) && fits(planned)) return planned;
+  if ((planned == 4 || planned == 8 || planned == 16) && fits(planned)) return planned;
   return fits(8) ? 8 : 4;
 }
 
@@ -681,6 +679,8 @@ cudaError_t launch_fft_x_fwd(const FftArgs& a, cudaStream_t s) {
   dim3 grid((unsigned)((pairs + P - 1) / P), a.d.c, a.n_loads);
   const size_t smem = 2ull * a.d.nx * (P + 1) * sizeof(C);
   const bool up = a.mode == FX_PCG;
+  if (P == 16) return up ? launch_with_smem(fft_x_fwd_kernel<T, true, 16>, grid, XT, smem, s, a)
+                         : launch_with_smem(fft_x_fwd_kernel<T, false, 16>, grid, XT, smem, s, a);
   if (P == 8) return up ? launch_with_smem(fft_x_fwd_kernel<T, true, 8>, grid, XT, smem, s, a)
                         : launch_with_smem(fft_x_fwd_kernel<T, false, 8>, grid, XT, smem, s, a);
   return up ? launch_with_smem(fft_x_fwd_kernel<T, true, 4>, grid, XT, smem, s, a)
@@ -695,6 +695,11 @@ cudaError_t launch_fft_x_inv(const FftArgs& a, cudaStream_t s) {
   dim3 grid((unsigned)((pairs + P - 1) / P), a.d.c, a.n_loads);
   if (a.st != nullptr && (long long)grid.x * grid.y > a.red.max_blocks) return cudaErrorInvalidConfiguration;
   const size_t smem = 2ull * a.d.nx * (P + 1) * sizeof(C);
+  if (P == 16) {
+    if (a.mode == FX_PCG) return launch_with_smem(fft_x_inv_kernel<T, FX_PCG, 16>, grid, XT, smem, s, a);
+    if (a.mode == FX_PCG_INIT) return launch_with_smem(fft_x_inv_kernel<T, FX_PCG_INIT, 16>, grid, XT, smem, s, a);
+    return launch_with_smem(fft_x_inv_kernel<T, FX_PLAIN, 16>, grid, XT, smem, s, a);
+  }
   if (P == 8) {
     if (a.mode == FX_PCG) return launch_with_smem(fft_x_inv_kernel<T, FX_PCG, 8>, grid, XT, smem, s, a);
     if (a.mode == FX_PCG_INIT) return launch_with_smem(fft_x_inv_kernel<T, FX_PCG_INIT, 8>, grid, XT, smem, s, a);

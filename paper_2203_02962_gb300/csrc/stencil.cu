@@ -35,8 +35,7 @@ namespace {
 
 constexpr int BX = 32;
 constexpr int BY = 8;
-constexpr int PX = BX + 2;
-constexpr int PY = BY + 2;
+constexpr int PX = BX + 2;  // halo row of the 2-D pixel kernel
 constexpr int EX = BX + 1;
 constexpr int EY = BY + 1;
 constexpr int NE = EX * EY;              // elements per layer per CTA (297)
@@ -142,120 +141,97 @@ __device__ __forceinline__ void contract_iso(const T (&g)[3][3], T lam, T mu, T 
     }
 }
 
-// Hex8 element: nodal values u[j][corner] (corner = a + 2b + 4c) -> forces f[j][corner].
-// Without a nodal field (HAS_X false: the right-hand side -D^T W C e) only the monomial-1 dual
-// T1 = tau is nonzero and the forces reduce to f_abc = xi_a tau_x + eta_b tau_y + zeta_c tau_z.
-// t1o receives the monomial-1 dual (Chat g_1 + tau), whose sum over elements is |Y| S P^T <sigma>.
+// Hex8 element in face form.  The Hadamard (modal) transform of the 8 nodal values factors into an
+// in-plane part per x-y face -- (ss, sd, ds, dd) = the sums / differences along x, then along y, of
+// the face's 4 nodes -- and a z part that combines the element's bottom (c = 0) and top (c = 1)
+// faces.  Each face is shared by the two element layers next to it, so the kernel forms it once per
+// node plane.  In reverse, the element's dual modal forces give per-face partials (the transposed
+// z part); a face's two partials are summed before the transposed in-plane part spreads them to
+// its 4 corner nodes.
+//   bot/top[j][0..3] = (ss, sd, ds, dd) of the bottom / top face of component j
+//   pb/pt[j][0..3]   = the element's partials for its bottom / top face
+//   t1o              = the monomial-1 dual (Chat g_1 + tau), whose sum over elements is |Y| S P^T <sigma>
+// Without a nodal field (HAS_X false: the right-hand side -D^T W C e) only T1 = tau is nonzero.
 template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E>
-__device__ __forceinline__ void hex8_element(const T (&u)[C][8], const T* __restrict__ Ch,
-                                             const T* __restrict__ iso, const double* __restrict__ tau,
-                                             T (&f)[C][8], T (&t1o)[C][3]) {
-  if constexpr (!HAS_X) {
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      const T Q1 = HAS_E ? T(tau[j * 3 + 0]) : T(0);
-      const T Q2 = HAS_E ? T(tau[j * 3 + 1]) : T(0);
-      const T Q3 = HAS_E ? T(tau[j * 3 + 2]) : T(0);
-      t1o[j][0] = Q1;
-      t1o[j][1] = Q2;
-      t1o[j][2] = Q3;
-      const T a0 = -Q2 - Q3, a1 = Q2 - Q3, a2 = Q3 - Q2, a3 = Q2 + Q3;  // eta_b Q2 + zeta_c Q3, bc = b + 2c
-      f[j][0] = a0 - Q1; f[j][1] = a0 + Q1;
-      f[j][2] = a1 - Q1; f[j][3] = a1 + Q1;
-      f[j][4] = a2 - Q1; f[j][5] = a2 + Q1;
-      f[j][6] = a3 - Q1; f[j][7] = a3 + Q1;
-    }
-  } else {
-  // forward butterflies: q[j][n], n = 1..7 (xi, eta, zeta, xi eta, eta zeta, xi zeta, xi eta zeta)
-  T q1[C], q2[C], q3[C], q4[C], q5[C], q6[C], q7[C];
-#pragma unroll
-  for (int j = 0; j < C; ++j) {
-    T s[4], d[4];
-#pragma unroll
-    for (int bc = 0; bc < 4; ++bc) {  // bc = b + 2c
-      s[bc] = u[j][2 * bc + 1] + u[j][2 * bc];
-      d[bc] = u[j][2 * bc + 1] - u[j][2 * bc];
-    }
-    // along y (b): index bc = b + 2c
-    const T ss0 = s[1] + s[0], sd0 = s[1] - s[0], ss1 = s[3] + s[2], sd1 = s[3] - s[2];
-    const T ds0 = d[1] + d[0], dd0 = d[1] - d[0], ds1 = d[3] + d[2], dd1 = d[3] - d[2];
-    // along z (c)
-    q3[j] = ss1 - ss0;
-    q2[j] = sd1 + sd0;
-    q5[j] = sd1 - sd0;
-    q1[j] = ds1 + ds0;
-    q6[j] = ds1 - ds0;
-    q4[j] = dd1 + dd0;
-    q7[j] = dd1 - dd0;
-  }
-  // gradient coefficients per monomial, g[j][dir]
-  T g1[C][3], gx[C][3], gy[C][3], gz[C][3], gyz[C][3], gxz[C][3], gxy[C][3];
-#pragma unroll
-  for (int j = 0; j < C; ++j) {
-    g1[j][0] = q1[j]; g1[j][1] = q2[j]; g1[j][2] = q3[j];
-    gx[j][0] = T(0);  gx[j][1] = q4[j]; gx[j][2] = q6[j];   // monomial xi
-    gy[j][0] = q4[j]; gy[j][1] = T(0);  gy[j][2] = q5[j];   // eta
-    gz[j][0] = q6[j]; gz[j][1] = q5[j]; gz[j][2] = T(0);    // zeta
-    gyz[j][0] = q7[j]; gyz[j][1] = T(0); gyz[j][2] = T(0);  // eta zeta
-    gxz[j][0] = T(0); gxz[j][1] = q7[j]; gxz[j][2] = T(0);  // xi zeta
-    gxy[j][0] = T(0); gxy[j][1] = T(0); gxy[j][2] = q7[j];  // xi eta
-  }
+__device__ __forceinline__ void hex8_element_faces(const T (&bot)[C][4], const T (&top)[C][4], const T* __restrict__ Ch,
+                                                   const T* __restrict__ iso, const double* __restrict__ tau,
+                                                   T (&pb)[C][4], T (&pt)[C][4], T (&t1o)[C][3]) {
   T t1[C][3], tx[C][3], ty[C][3], tz[C][3], tyz[C][3], txz[C][3], txy[C][3];
-  constexpr double third = 1.0 / 3.0, ninth = 1.0 / 9.0;
-  if constexpr (ISO && C == 3) {
-    const T lam = iso[0], mu = iso[1];
-    contract_iso<7>(g1, lam, mu, t1);
-    const T l3 = lam * T(third), m3 = mu * T(third), l9 = lam * T(ninth), m9 = mu * T(ninth);
-    contract_iso<6>(gx, l3, m3, tx);
-    contract_iso<5>(gy, l3, m3, ty);
-    contract_iso<3>(gz, l3, m3, tz);
-    contract_iso<1>(gyz, l9, m9, tyz);
-    contract_iso<2>(gxz, l9, m9, txz);
-    contract_iso<4>(gxy, l9, m9, txy);
-  } else {
-    contract_gen<7>(Ch, g1, T(1), t1);
-    contract_gen<6>(Ch, gx, T(third), tx);
-    contract_gen<5>(Ch, gy, T(third), ty);
-    contract_gen<3>(Ch, gz, T(third), tz);
-    contract_gen<1>(Ch, gyz, T(ninth), tyz);
-    contract_gen<2>(Ch, gxz, T(ninth), txz);
-    contract_gen<4>(Ch, gxy, T(ninth), txy);
-  }
-  if constexpr (HAS_E) {
+  if constexpr (!HAS_X) {
 #pragma unroll
     for (int j = 0; j < C; ++j)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) t1[j][i] += T(tau[j * 3 + i]);
+      for (int i = 0; i < 3; ++i) {
+        t1[j][i] = HAS_E ? T(tau[j * 3 + i]) : T(0);
+        tx[j][i] = ty[j][i] = tz[j][i] = tyz[j][i] = txz[j][i] = txy[j][i] = T(0);
+      }
+  } else {
+    // z part of the modal transform: q[j][n], n = 1..7 (xi, eta, zeta, xi eta, eta zeta, xi zeta, xi eta zeta)
+    T q1[C], q2[C], q3[C], q4[C], q5[C], q6[C], q7[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      q3[j] = top[j][0] - bot[j][0];
+      q2[j] = top[j][1] + bot[j][1];
+      q5[j] = top[j][1] - bot[j][1];
+      q1[j] = top[j][2] + bot[j][2];
+      q6[j] = top[j][2] - bot[j][2];
+      q4[j] = top[j][3] + bot[j][3];
+      q7[j] = top[j][3] - bot[j][3];
+    }
+    // gradient coefficients per monomial, g[j][dir]
+    T g1[C][3], gx[C][3], gy[C][3], gz[C][3], gyz[C][3], gxz[C][3], gxy[C][3];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      g1[j][0] = q1[j]; g1[j][1] = q2[j]; g1[j][2] = q3[j];
+      gx[j][0] = T(0);  gx[j][1] = q4[j]; gx[j][2] = q6[j];   // monomial xi
+      gy[j][0] = q4[j]; gy[j][1] = T(0);  gy[j][2] = q5[j];   // eta
+      gz[j][0] = q6[j]; gz[j][1] = q5[j]; gz[j][2] = T(0);    // zeta
+      gyz[j][0] = q7[j]; gyz[j][1] = T(0); gyz[j][2] = T(0);  // eta zeta
+      gxz[j][0] = T(0); gxz[j][1] = q7[j]; gxz[j][2] = T(0);  // xi zeta
+      gxy[j][0] = T(0); gxy[j][1] = T(0); gxy[j][2] = q7[j];  // xi eta
+    }
+    constexpr double third = 1.0 / 3.0, ninth = 1.0 / 9.0;
+    if constexpr (ISO && C == 3) {
+      const T lam = iso[0], mu = iso[1];
+      contract_iso<7>(g1, lam, mu, t1);
+      const T l3 = lam * T(third), m3 = mu * T(third), l9 = lam * T(ninth), m9 = mu * T(ninth);
+      contract_iso<6>(gx, l3, m3, tx);
+      contract_iso<5>(gy, l3, m3, ty);
+      contract_iso<3>(gz, l3, m3, tz);
+      contract_iso<1>(gyz, l9, m9, tyz);
+      contract_iso<2>(gxz, l9, m9, txz);
+      contract_iso<4>(gxy, l9, m9, txy);
+    } else {
+      contract_gen<7>(Ch, g1, T(1), t1);
+      contract_gen<6>(Ch, gx, T(third), tx);
+      contract_gen<5>(Ch, gy, T(third), ty);
+      contract_gen<3>(Ch, gz, T(third), tz);
+      contract_gen<1>(Ch, gyz, T(ninth), tyz);
+      contract_gen<2>(Ch, gxz, T(ninth), txz);
+      contract_gen<4>(Ch, gxy, T(ninth), txy);
+    }
+    if constexpr (HAS_E) {
+#pragma unroll
+      for (int j = 0; j < C; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) t1[j][i] += T(tau[j * 3 + i]);
+    }
   }
 #pragma unroll
-  for (int j = 0; j < C; ++j)
+  for (int j = 0; j < C; ++j) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) t1o[j][i] = t1[j][i];
-  // dual modal forces and transposed butterflies
-#pragma unroll
-  for (int j = 0; j < C; ++j) {
+    // dual modal forces, then the transposed z part
     const T Q1 = t1[j][0], Q2 = t1[j][1], Q3 = t1[j][2];
     const T Q4 = tx[j][1] + ty[j][0];
     const T Q5 = ty[j][2] + tz[j][1];
     const T Q6 = tx[j][2] + tz[j][0];
     const T Q7 = tyz[j][0] + txz[j][1] + txy[j][2];
-    // z stage (transposed)
-    const T ds0 = Q1 - Q6, ds1 = Q1 + Q6;
-    const T dd0 = Q4 - Q7, dd1 = Q4 + Q7;
-    const T sd0 = Q2 - Q5, sd1 = Q2 + Q5;
-    const T ss0 = -Q3, ss1 = Q3;
-    // y stage (transposed): s[b + 2c], d[b + 2c]
-    T s[4], d[4];
-    s[0] = ss0 - sd0; s[1] = ss0 + sd0; s[2] = ss1 - sd1; s[3] = ss1 + sd1;
-    d[0] = ds0 - dd0; d[1] = ds0 + dd0; d[2] = ds1 - dd1; d[3] = ds1 + dd1;
-    // x stage (transposed)
-#pragma unroll
-    for (int bc = 0; bc < 4; ++bc) {
-      f[j][2 * bc] = s[bc] - d[bc];
-      f[j][2 * bc + 1] = s[bc] + d[bc];
-    }
+    pb[j][0] = -Q3;      pt[j][0] = Q3;
+    pb[j][1] = Q2 - Q5;  pt[j][1] = Q2 + Q5;
+    pb[j][2] = Q1 - Q6;  pt[j][2] = Q1 + Q6;
+    pb[j][3] = Q4 - Q7;  pt[j][3] = Q4 + Q7;
   }
-  }  // HAS_X
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -281,13 +257,20 @@ __device__ void pcg_alpha_update(PcgState& s, double total, double* hist) {
 
 // ------------------------------------------------------------------------------------------------
 // 3-D hex8 kernel
+//
+// Per element layer k (between node planes k and k + 1), two barriers:
+//   A. face threads read the 4 nodes of their x-y face of plane k + 1 (periodic offsets computed
+//      once; neighbouring faces share nodes through L1) and store its in-plane butterflies;
+//   B. element threads combine the faces of planes k and k + 1, contract with the material, add
+//      the bottom partials to the top partials carried from layer k - 1 (registers) and spread the
+//      face total to its 4 corners of plane k;
+//   C. node threads gather the 4 faces around their node of plane k and write y.
 // ------------------------------------------------------------------------------------------------
 template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED>
 __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int NPOS = PY * PX;
-  T* pl = reinterpret_cast<T*>(smem_raw);                 // [2][C][PY][PX]
-  T* F = pl + 2 * C * NPOS;                                // [4 bottom + 4 top][C][EY][EX]
+  T* FB = reinterpret_cast<T*>(smem_raw);  // [2 planes][4][C][NE] face butterflies
+  T* FC = FB + 2 * 4 * C * NE;              // [4 corners][C][NE] face contributions to plane k
   __shared__ double red_sh[32];
 
   const Dims d = a.d;
@@ -308,69 +291,84 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
   const double* tau = HAS_E ? a.tau + (long long)load * a.n_phases * (3 * C) : nullptr;
   const long long plane = (long long)d.nx * d.ny;
 
-  // Each thread stages the same (at most two) halo positions of every node plane: their in-plane
-  // offsets (periodic wrap included) are computed once, so the z march does no index division.
-  static_assert(NPOS <= 2 * NT, "two halo positions per thread");
-  const int p1 = tid + NT;
-  const int off0 = wrap(j0 - 1 + tid / PX, d.ny) * d.nx + wrap(i0 - 1 + tid % PX, d.nx);
-  const int off1 = p1 < NPOS ? wrap(j0 - 1 + p1 / PX, d.ny) * d.nx + wrap(i0 - 1 + p1 % PX, d.nx) : 0;
+  // face / element thread (ei, ej): face (ei, ej) of a plane = the x-y square whose corners are the
+  // nodes (i0 - 1 + ei + a, j0 - 1 + ej + b); element (ei, ej) of a layer sits on that face
+  const int ei = tid % EX, ej = tid / EX;
+  const bool face_thread = tid < NE;
+  const int fi0 = wrap(i0 - 1 + ei, d.nx), fi1 = wrap(i0 + ei, d.nx);
+  const int fj0 = wrap(j0 - 1 + ej, d.ny), fj1 = wrap(j0 + ej, d.ny);
+  const int off00 = fj0 * d.nx + fi0, off10 = fj0 * d.nx + fi1, off01 = fj1 * d.nx + fi0, off11 = fj1 * d.nx + fi1;
+  const bool owner = face_thread && ei >= 1 && ej >= 1 && i0 + ei - 1 < d.nx && j0 + ej - 1 < d.ny;
 
-  // node-thread state: top-corner contributions carried to the next plane
-  const int ni = tid % BX, nj = tid / BX;  // valid node thread when tid < BX * BY
+  // node thread (ni, nj): node (i0 + ni, j0 + nj)
+  const int ni = tid % BX, nj = tid / BX;
   const bool node_thread = tid < BX * BY && (i0 + ni) < d.nx && (j0 + nj) < d.ny;
   const long long node_off = (long long)(j0 + nj) * d.nx + i0 + ni;
-  T carry[C];
+
+  T carry[C][4];  // top partials of the previous layer for this thread's face
 #pragma unroll
-  for (int j = 0; j < C; ++j) carry[j] = T(0);
-  double acc_y = 0.0;                  // RED_PCG: <x, y>;  RED_STATS: sum y^2
-  double acc_t[3 * C];                 // RED_STATS: sum of the monomial-1 duals of owned elements
+  for (int j = 0; j < C; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) carry[j][q] = T(0);
+  DotAcc<T> acc_p;                     // RED_PCG: <x, y>
+  double acc_y = 0.0;                  // RED_STATS / RED_SUMS: sum y^2 (FP64 kernels only)
+  double acc_t[3 * C];                 // RED_STATS / RED_SUMS: sum of the monomial-1 duals of owned elements
 #pragma unroll
   for (int i = 0; i < 3 * C; ++i) acc_t[i] = 0.0;
 
-  const int ei = tid % EX, ej = tid / EX;  // element thread
-  const bool elem_thread = tid < NE;
-  const int elem_off = wrap(j0 - 1 + ej, d.ny) * d.nx + wrap(i0 - 1 + ei, d.nx);
-  const bool owner = elem_thread && ei >= 1 && ej >= 1 && i0 + ei - 1 < d.nx && j0 + ej - 1 < d.ny;
-
-  // plane index kz (wrapped) of node plane k, kept incrementally
-  int kz = wrap(k0 - 1, d.nz);
-  auto load_plane = [&](auto slot_c, int kzp) {
+  auto next = [&](int z) { return z + 1 == d.nz ? 0 : z + 1; };
+  // A: in-plane butterflies of the faces of node plane kz into slot SLOT
+  auto faces = [&](auto slot_c, int kz) {
     if constexpr (HAS_X) {
-      constexpr int slot = decltype(slot_c)::value;
-      const T* xk = x + (long long)kzp * plane;
+      constexpr int SLOT = decltype(slot_c)::value;
+      if (face_thread) {
+        const T* xk = x + (long long)kz * plane;
 #pragma unroll
-      for (int j = 0; j < C; ++j) {
-        const T* xj = xk + (long long)j * d.N;
-        T* dst = pl + (slot * C + j) * NPOS;
-        dst[tid] = __ldg(xj + off0);
-        if (p1 < NPOS) dst[p1] = __ldg(xj + off1);
+        for (int j = 0; j < C; ++j) {
+          const T* xj = xk + (long long)j * d.N;
+          const T v00 = __ldg(xj + off00), v10 = __ldg(xj + off10), v01 = __ldg(xj + off01), v11 = __ldg(xj + off11);
+          const T s0 = v10 + v00, d0 = v10 - v00, s1 = v11 + v01, d1 = v11 - v01;
+          T* fb = FB + ((SLOT * 4) * C + j) * NE + tid;
+          fb[0 * C * NE] = s1 + s0;  // ss
+          fb[1 * C * NE] = s1 - s0;  // sd
+          fb[2 * C * NE] = d1 + d0;  // ds
+          fb[3 * C * NE] = d1 - d0;  // dd
+        }
       }
     }
   };
-  auto next = [&](int z) { return z + 1 == d.nz ? 0 : z + 1; };
 
-  // element layer k spans node planes k (slot CUR) and k + 1 (slot CUR ^ 1); kzc = wrap(k)
+  // B + C for element layer k (planes k: slot CUR, k + 1: slot CUR ^ 1); kzc = wrap(k)
   auto layer = [&](auto cur_c, int k, int kzc) {
     constexpr int CUR = decltype(cur_c)::value;
-    load_plane(std::integral_constant<int, CUR ^ 1>{}, next(kzc));
+    faces(std::integral_constant<int, CUR ^ 1>{}, next(kzc));
     __syncthreads();
-    if (elem_thread) {
-      T u[C][8];
+    if (face_thread) {
+      T bot[C][4], top[C][4];
 #pragma unroll
       for (int j = 0; j < C; ++j)
 #pragma unroll
-        for (int cn = 0; cn < 8; ++cn) {
-          const int aa = cn & 1, bb = (cn >> 1) & 1, cc = cn >> 2;
-          u[j][cn] = HAS_X ? pl[((CUR ^ cc) * C + j) * NPOS + (ej + bb) * PX + ei + aa] : T(0);
+        for (int q = 0; q < 4; ++q) {
+          bot[j][q] = HAS_X ? FB[((CUR * 4 + q) * C + j) * NE + tid] : T(0);
+          top[j][q] = HAS_X ? FB[(((CUR ^ 1) * 4 + q) * C + j) * NE + tid] : T(0);
         }
-      const int ph = a.ids ? a.ids[(long long)kzc * plane + elem_off] : 0;
-      T f[C][8], t1[C][3];
-      hex8_element<T, C, ISO, HAS_X, HAS_E>(u, mats + (long long)ph * (9 * C * C), isot + 2 * ph,
-                                            HAS_E ? tau + ph * (3 * C) : nullptr, f, t1);
+      const int ph = a.ids ? a.ids[(long long)kzc * plane + off00] : 0;
+      T pb[C][4], pt[C][4], t1[C][3];
+      hex8_element_faces<T, C, ISO, HAS_X, HAS_E>(bot, top, mats + (long long)ph * (9 * C * C), isot + 2 * ph,
+                                                  HAS_E ? tau + ph * (3 * C) : nullptr, pb, pt, t1);
 #pragma unroll
-      for (int j = 0; j < C; ++j)
+      for (int j = 0; j < C; ++j) {
+        // face total of plane k, then the transposed in-plane part: corners (a, b) of the face
+        const T ss = pb[j][0] + carry[j][0], sd = pb[j][1] + carry[j][1];
+        const T ds = pb[j][2] + carry[j][2], dd = pb[j][3] + carry[j][3];
+        const T s0 = ss - sd, s1 = ss + sd, d0 = ds - dd, d1 = ds + dd;
+        FC[(0 * C + j) * NE + tid] = s0 - d0;  // corner (0, 0)
+        FC[(1 * C + j) * NE + tid] = s0 + d0;  // corner (1, 0)
+        FC[(2 * C + j) * NE + tid] = s1 - d1;  // corner (0, 1)
+        FC[(3 * C + j) * NE + tid] = s1 + d1;  // corner (1, 1)
 #pragma unroll
-        for (int cn = 0; cn < 8; ++cn) F[(cn * C + j) * NE + ej * EX + ei] = f[j][cn];
+        for (int q = 0; q < 4; ++q) carry[j][q] = pt[j][q];
+      }
       if ((RED == RED_STATS || RED == RED_SUMS) && owner && k >= k0) {
 #pragma unroll
         for (int j = 0; j < C; ++j)
@@ -379,32 +377,26 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
       }
     }
     __syncthreads();
-    if (node_thread) {
-      // node (i, j) of plane k: bottom corners (c = 0) of layer k from elements (i-1..i, j-1..j)
-      // plus the carried top corners of layer k-1; then carry the top corners of layer k.
+    if (node_thread && k >= k0) {
+      // node (i, j) of plane k is corner (1,1) of face (i-1, j-1), (0,1) of (i, j-1),
+      // (1,0) of (i-1, j) and (0,0) of (i, j)
       const int e00 = nj * EX + ni;
 #pragma unroll
       for (int j = 0; j < C; ++j) {
-        const T bot = F[(3 * C + j) * NE + e00]            // corner (1,1,0) of element (i-1, j-1)
-                    + F[(2 * C + j) * NE + e00 + 1]        // corner (0,1,0) of element (i, j-1)
-                    + F[(1 * C + j) * NE + e00 + EX]       // corner (1,0,0) of element (i-1, j)
-                    + F[(0 * C + j) * NE + e00 + EX + 1];  // corner (0,0,0) of element (i, j)
-        const T top = F[(7 * C + j) * NE + e00] + F[(6 * C + j) * NE + e00 + 1] +
-                      F[(5 * C + j) * NE + e00 + EX] + F[(4 * C + j) * NE + e00 + EX + 1];
-        if (k >= k0) {
-          const T val = T(a.y_scale) * (carry[j] + bot);
-          if (RED != RED_SUMS) y[(long long)j * d.N + (long long)k * plane + node_off] = val;
-          if (RED == RED_PCG) acc_y += (double)val * (double)pl[(CUR * C + j) * NPOS + (nj + 1) * PX + ni + 1];
-          if ((RED == RED_STATS || RED == RED_SUMS)) acc_y += (double)val * (double)val;
-        }
-        carry[j] = top;
+        const T v = FC[(3 * C + j) * NE + e00] + FC[(2 * C + j) * NE + e00 + 1] +
+                    FC[(1 * C + j) * NE + e00 + EX] + FC[(0 * C + j) * NE + e00 + EX + 1];
+        const T val = T(a.y_scale) * v;
+        const long long gidx = (long long)j * d.N + (long long)kzc * plane + node_off;
+        if (RED != RED_SUMS) y[gidx] = val;
+        if (RED == RED_PCG) acc_p.add(val, __ldg(x + gidx));
+        if (RED == RED_STATS || RED == RED_SUMS) acc_y += (double)val * (double)val;
       }
     }
-    // the next layer overwrites this layer's bottom plane only after its first barrier
-    __syncthreads();
+    // the next layer's barrier A orders these reads of FC and FB before their next writes
   };
 
-  load_plane(std::integral_constant<int, 0>{}, kz);
+  int kz = wrap(k0 - 1, d.nz);
+  faces(std::integral_constant<int, 0>{}, kz);
   int k = k0 - 1;
   while (k < k1) {
     layer(std::integral_constant<int, 0>{}, k, kz);
@@ -417,7 +409,7 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
   }
 
   if (RED == RED_PCG) {
-    const double part = block_sum(acc_y, red_sh);
+    const double part = block_sum(acc_p.value(), red_sh);
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     double total;
@@ -427,7 +419,7 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
         pcg_alpha_update(a.st[load], total, a.red.hist ? a.red.hist + (long long)load * 2 * kHist : nullptr);
     }
   }
-  if ((RED == RED_STATS || RED == RED_SUMS)) {
+  if (RED == RED_STATS || RED == RED_SUMS) {
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     double* out = a.stats + ((long long)load * nblk + bid) * (1 + 3 * C);
@@ -589,6 +581,7 @@ __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
     }
   }
   __syncthreads();
+  DotAcc<T> acc_p;
   double acc_y = 0.0;
   const int ni = tid % BX, nj = tid / BX;
   if (tid < BX * BY2 && i0 + ni < d.nx && j0 + nj < d.ny) {
@@ -598,12 +591,12 @@ __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
                   F[((1 * C + j) * EY2 + nj + 1) * EX + ni] + F[((0 * C + j) * EY2 + nj + 1) * EX + ni + 1];
       const T val = T(a.y_scale) * v;
       if (RED != RED_SUMS) y[(long long)j * d.N + (long long)(j0 + nj) * d.nx + i0 + ni] = val;
-      if (RED == RED_PCG) acc_y += (double)val * (double)pl[(j * PY2 + nj + 1) * PX + ni + 1];
+      if (RED == RED_PCG) acc_p.add(val, pl[(j * PY2 + nj + 1) * PX + ni + 1]);
       if ((RED == RED_STATS || RED == RED_SUMS)) acc_y += (double)val * (double)val;
     }
   }
   if (RED == RED_PCG) {
-    const double part = block_sum(acc_y, red_sh);
+    const double part = block_sum(acc_p.value(), red_sh);
     double total;
     if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load,
                          gridDim.x, blockIdx.x, red_sh, &total)) {
@@ -645,7 +638,7 @@ cudaError_t launch_hex8_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
   hex8_grid(d, &tiles, &slabs, &kz);
   if (ctas) *ctas = tiles * slabs;
   if (RED == RED_PCG && tiles * slabs > a.red.max_blocks) return cudaErrorInvalidConfiguration;
-  const size_t smem = sizeof(T) * (2 * C * PY * PX + 8 * C * EY * EX);
+  const size_t smem = sizeof(T) * (2 * 4 * C * NE + 4 * C * NE);
   auto kern = hex8_apply_kernel<T, C, ISO, HAS_X, HAS_E, RED>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;

@@ -62,7 +62,25 @@ __global__ void mean_subtract_kernel(double* __restrict__ x, long long N, long l
   for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < N; i += (long long)gridDim.x * VT) p[i] -= mean;
 }
 
+__global__ void impulse_scatter_kernel(const double* __restrict__ py, Dims pd, Dims full, int c, double* out) {
+  const int nb = full.dim == 3 ? 27 : 9;
+  const int t = threadIdx.x;
+  if (t >= c * c * nb) return;
+  const int o = t % nb, pair = t / nb, al = pair % c, be = pair / c;
+  const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = full.dim == 3 ? o / 9 - 1 : 0;
+  auto wrapi = [](int i, int n) { return ((i % n) + n) % n; };
+  const long long ps = ((long long)wrapi(dz, pd.nz) * pd.ny + wrapi(dy, pd.ny)) * pd.nx + wrapi(dx, pd.nx);
+  const long long fs = ((long long)wrapi(dz, full.nz) * full.ny + wrapi(dy, full.ny)) * full.nx + wrapi(dx, full.nx);
+  out[((long long)be * c + al) * full.N + fs] = py[((long long)be * c + al) * pd.N + ps];
+}
+
 }  // namespace
+
+cudaError_t launch_impulse_scatter(const double* py, const Dims& pd, const Dims& full, int c, double* out,
+                                   cudaStream_t s) {
+  impulse_scatter_kernel<<<1, 256, 0, s>>>(py, pd, full, c, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cast_d2f(const double* x, float* y, double scale, long long n, cudaStream_t s) {
   cast_d2f_kernel<<<grid_for(n), VT, 0, s>>>(x, y, scale, n);

@@ -353,7 +353,7 @@ def test_autotuned_plans_are_valid_and_agree():
             plans.append(s.fft_plan(prec))
             s.close()
     for p in plans[:2]:
-        assert p["pairs"] in (4, 8) and p["tc_y"] in (2, 4, 8, 16) and p["tc_last"] in (2, 4, 8, 16)
+        assert p["pairs"] in (4, 8, 16) and p["tc_y"] in (2, 4, 8, 16) and p["tc_last"] in (2, 4, 8, 16)
     for p in plans[2:]:
         assert p["pairs"] == 0 and p["tc_last"] == 0
     assert _rel(outs[0], outs[2]) < 1e-9 and _rel(outs[1], outs[3]) < 1e-8
