@@ -251,9 +251,38 @@ def run_ours(args):
         "clocks": r64["clocks"],
         "gpu_launches": r64["launches"],
     }
+    out["cufft_reference"] = cufft_comparison(N, c, len(loads), rmx["kt"], r64["kt"], rmx["load_iters"],
+                                              r64["load_iters"], args.steps)
     out["batched"] = run_batched(args)
     out["cpu_baseline"] = cpu_baseline(short=True)
     print(json.dumps(out))
+
+
+def cufft_comparison(N, c, n_loads, kt32, kt64, iters32, iters64, steps):
+    """cuFFT (through torch.fft) on the same half-spectrum transforms as one preconditioner apply:
+    forward r2c + inverse c2r of n_loads x c fields of 128^3, timed with CUDA events; beside it the
+    device time of our five FFT passes per apply (which also do the block solve, the Parseval dot
+    and the CG updates).  A comparison only: cuFFT is not used by the solver."""
+    import torch
+    out = {}
+    for name, dt, kt, its in (("fp32", torch.float32, kt32, iters32), ("fp64", torch.float64, kt64, iters64)):
+        x = torch.randn((n_loads, c, 128, 128, 128), dtype=dt, device="cuda")
+        for _ in range(3):
+            y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(2, 3, 4)), s=(128, 128, 128), dim=(2, 3, 4))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(2, 3, 4)), s=(128, 128, 128), dim=(2, 3, 4))
+        e1.record()
+        torch.cuda.synchronize()
+        cu_ms = e0.elapsed_time(e1) / 5
+        ours = sum(kt[k][0] for k in ("fft_x_fwd", "fft_y_fwd", "fft_last", "fft_y_inv", "fft_x_inv"))
+        iters_per_step = its / steps
+        ours_ms = ours / steps / max(1.0, iters_per_step / n_loads)
+        out[name] = {"cufft_ms_per_apply": cu_ms, "ours_ms_per_apply": ours_ms, "ratio_ours_over_cufft": ours_ms / cu_ms}
+        del x, y
+    return out
 
 
 def run_batched(args):
