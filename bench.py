@@ -373,14 +373,15 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_ncu_case(precision):
-    """One untimed solve of the benchmark workload, for kernel captures under ncu."""
+def run_ncu_case(precision, n_loads=6):
+    """One untimed solve of the benchmark workload (its first n_loads loads), for kernel captures
+    under ncu; fewer loads keep the device memory that ncu saves between replay passes small."""
     import torch
     from paper_2203_02962_gb300 import fehom
     w = workload()
     s = fehom.Solver("hex8_3d", "elastic", w["n"], w["ids"], w["moduli"], precision=precision)
     s.precond_build()
-    out = s.solve(w["loads"], tol=w["tol"], fields=None)
+    out = s.solve(w["loads"][:n_loads], tol=w["tol"], fields=None)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": precision, "iterations": [i["iterations"] for i in out["info"]],
                       "launches": s.launch_count()}))
@@ -395,12 +396,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ncu-case", default=None, choices=["fp64", "mixed"],
                     help="run one untimed solve of the workload (for ncu kernel captures) and exit")
+    ap.add_argument("--ncu-loads", type=int, default=6, help="loads of the --ncu-case solve (1-6)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.ncu_case:
-        run_ncu_case(args.ncu_case)
+        run_ncu_case(args.ncu_case, args.ncu_loads)
         return
     run_ours(args)
 

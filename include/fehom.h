@@ -75,6 +75,9 @@ typedef struct {
   int profile;       /* 1: record CUDA events around every kernel of the PCG iterations (see fehom_kernel_times) */
   int autotune;      /* 1 (default): on the first solve of a batch size, time the FFT passes' launch plans
                         (x-line pairs per CTA, columns per CTA) on the context's buffers and keep the fastest */
+  int x0_scaling;    /* 1 (default): a warm start x0 (mean removed) is replaced, per load, by gamma x0 with
+                        gamma = <b, x0> / <x0, K x0> (0 when <x0, K x0> = 0): the multiple of x0 closest to
+                        the solution in the energy norm, never farther from it than the zero guess */
 } fehom_options;
 
 /* Kernel classes of one PCG iteration, for fehom_kernel_times. */

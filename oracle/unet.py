@@ -14,7 +14,8 @@ loosen it).  This module is the plain definition of that network and of its grad
   ``off(t) = (dz, dy, dx)`` in {-1, 0, 1}^3 with ``t = 9 (dz + 1) + 3 (dy + 1) + (dx + 1)``;
 * ReLU after every 3x3x3 convolution; 2x2x2 mean pooling down; nearest-neighbour upsampling and
   channel concatenation (skip first) up; a 1x1x1 linear head to one channel per load;
-* loss = mean over samples, loads and voxels of the squared difference to the target;
+* loss = mean over samples, loads and voxels of the squared difference to the target, or a
+  discrete H^1 seminorm of that difference (``field_loss``);
 * gradients by the chain rule, one adjoint per operation (``*_T`` functions);
 * Adam (Kingma and Ba, 2015) with bias correction.
 
@@ -166,8 +167,24 @@ def forward(theta, specs, x, act_round=None):
     return out, cache
 
 
-def loss_and_grad(theta, specs, xs, targets, act_round=None):
-    """Mean squared error over a batch and its gradient with respect to theta.
+def field_loss(r, count, kind="mse", l2_weight=0.0):
+    """Loss of one sample's residual r = output - target (n_loads, D, H, W) and its gradient.
+
+    mse: sum r^2 / count.  h1: (sum over the three axes of the squared forward differences of r,
+    periodic, + l2_weight sum r^2) / count -- a discrete H^1 seminorm, the energy of the Laplacian.
+    count = number of target values of the whole batch."""
+    if kind == "mse":
+        return float((r * r).sum()) / count, 2.0 * r / count
+    loss, g = l2_weight * float((r * r).sum()), 2.0 * l2_weight * r
+    for ax in (1, 2, 3):
+        d = np.roll(r, -1, axis=ax) - r
+        loss += float((d * d).sum())
+        g = g + 2.0 * (2.0 * r - np.roll(r, -1, axis=ax) - np.roll(r, 1, axis=ax))
+    return loss / count, g / count
+
+
+def loss_and_grad(theta, specs, xs, targets, act_round=None, loss_kind="mse", l2_weight=0.0):
+    """Loss (field_loss, summed over the batch) and its gradient with respect to theta.
 
     xs: (B, Cin, D, H, W); targets: (B, n_loads, D, H, W).  Returns (loss, grad, outputs).
     """
@@ -181,9 +198,8 @@ def loss_and_grad(theta, specs, xs, targets, act_round=None):
     for x, t in zip(xs, targets):
         out, c = forward(theta, specs, x, act_round)
         outs.append(out)
-        r = out - t
-        loss += float((r * r).sum()) / count
-        g_out = 2.0 * r / count
+        li, g_out = field_loss(out - t, count, loss_kind, l2_weight)
+        loss += li
         Wo, bo = P["head"]
         top = c["d0"] if L > 1 else c["e0"]
         G["head"][0][...] += np.einsum("lzyx,czyx->lc", g_out, top)

@@ -15,7 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfehom.so")
-SOURCES = ["stencil.cu", "fft.cu", "vec.cu", "api.cu"]
+SOURCES = ["stencil.cu", "fft.cu", "vec.cu", "api.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -39,7 +39,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(OUT, exist_ok=True)
     headers = [os.path.join(SRC, "fehom_internal.cuh"),
-               os.path.join(os.path.dirname(PKG), "include", "fehom.h")]
+               os.path.join(os.path.dirname(PKG), "include", "fehom.h"),
+               os.path.join(os.path.dirname(PKG), "include", "fehom_unet.h")]
     jobs = []
     for src in SOURCES:
         s = os.path.join(SRC, src)

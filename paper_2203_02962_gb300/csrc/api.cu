@@ -741,6 +741,7 @@ void fehom_default_options(fehom_options* opt) {
   opt->use_graph = 1;
   opt->profile = 0;
   opt->autotune = 1;
+  opt->x0_scaling = 1;
 }
 
 const char* fehom_last_error(const fehom_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
@@ -1346,6 +1347,21 @@ static fehom_status finish_outputs(fehom_ctx* ctx, int n_loads, const double* lo
   return FEHOM_OK;
 }
 
+// Warm start x0 (already in x64, mean removed): x64[l] *= <b, x0> / <x0, K x0> per load, in FP64.
+fehom_status scale_warm_start(fehom_ctx* ctx, int n_loads) {
+  if (!ctx->opt.x0_scaling) return FEHOM_OK;
+  cudaStream_t s = ctx->stream;
+  const long long cN = (long long)ctx->d.c * ctx->d.N;
+  StencilArgs a = stencil_args(ctx, false, n_loads);
+  a.x = ctx->x64;
+  a.y = ctx->ap64;
+  CK(launch_stiffness<double>(a, s));
+  TRY(ensure_partial(ctx, (size_t)n_loads * 2 * 304));
+  CK(launch_galerkin_scale(ctx->x64, ctx->ap64, ctx->b64, n_loads, cN, ctx->partial, s));
+  count_launch(ctx, 3);
+  return FEHOM_OK;
+}
+
 // One solve of one context, split into phases so that the PCG iterations of several contexts can
 // run from one captured graph (fehom_solve_batch) as well as alone (fehom_solve).
 //   FP64:  begin (tuner, b, initial preconditioner apply) -> iterations -> end_step (true residual)
@@ -1386,6 +1402,7 @@ struct SolveRun {
         TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
         CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
         count_launch(ctx, 2);
+        TRY(scale_warm_start(ctx, n_loads));
       } else {
         CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double) * cN * n_loads, s));
       }
@@ -1405,6 +1422,7 @@ struct SolveRun {
       TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
       CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
       count_launch(ctx, 2);
+      TRY(scale_warm_start(ctx, n_loads));
       TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->r64, nullptr, nullptr));
       std::vector<PcgState> hs0(n_loads);
       for (int l = 0; l < n_loads; ++l) {

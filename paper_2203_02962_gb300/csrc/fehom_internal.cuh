@@ -197,5 +197,9 @@ cudaError_t launch_impulse_scatter(const double* py, const Dims& pd, const Dims&
 // removes the mean of every (component, load); partial: scratch of n_loads * c * 304 doubles (two launches)
 cudaError_t launch_sub_mean(double* x, int c, long long N, int n_loads, long long load_stride, double* partial,
                             cudaStream_t s);
+// x[l] *= gamma_l = <x[l], b[l]> / <x[l], kx[l]> (0 when <x[l], kx[l]> <= 0), l < n_loads, slices of n doubles;
+// partial: scratch of n_loads * 2 * 304 doubles (two launches, fixed summation order)
+cudaError_t launch_galerkin_scale(double* x, const double* kx, const double* b, int n_loads, long long n,
+                                  double* partial, cudaStream_t s);
 
 }  // namespace fehom

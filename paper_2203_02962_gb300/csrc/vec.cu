@@ -62,6 +62,37 @@ __global__ void mean_subtract_kernel(double* __restrict__ x, long long N, long l
   for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < N; i += (long long)gridDim.x * VT) p[i] -= mean;
 }
 
+// Galerkin scaling of a warm start: CTA partial sums of x.kx and x.b per load, then every CTA re-adds
+// the partials of its load in index order, forms gamma and scales its slice
+__global__ void dot2_partial_kernel(const double* __restrict__ x, const double* __restrict__ kx,
+                                    const double* __restrict__ b, long long n, double* partial) {
+  const long long off = (long long)blockIdx.y * n;
+  double s1 = 0.0, s2 = 0.0;
+  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) {
+    s1 = fma(x[off + i], kx[off + i], s1);
+    s2 = fma(x[off + i], b[off + i], s2);
+  }
+  const double t1 = block_sum(s1);
+  const double t2 = block_sum(s2);
+  if (threadIdx.x == 0) {
+    partial[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 2] = t1;
+    partial[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 2 + 1] = t2;
+  }
+}
+
+__global__ void galerkin_scale_kernel(double* __restrict__ x, long long n, const double* __restrict__ partial) {
+  const double* pp = partial + (long long)blockIdx.y * gridDim.x * 2;
+  double a1 = 0.0, a2 = 0.0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += VT) {
+    a1 += pp[2 * k];
+    a2 += pp[2 * k + 1];
+  }
+  const double xkx = block_sum(a1), xb = block_sum(a2);
+  const double gamma = (xkx > 0.0 && isfinite(xb / xkx)) ? xb / xkx : 0.0;
+  double* p = x + (long long)blockIdx.y * n;
+  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) p[i] *= gamma;
+}
+
 __global__ void impulse_scatter_kernel(const double* __restrict__ py, Dims pd, Dims full, int c, double* out) {
   const int nb = full.dim == 3 ? 27 : 9;
   const int t = threadIdx.x;
@@ -89,6 +120,16 @@ cudaError_t launch_cast_d2f(const double* x, float* y, double scale, long long n
 
 cudaError_t launch_add_f2d(const float* x, double* y, double scale, long long n, cudaStream_t s) {
   add_f2d_kernel<<<grid_for(n), VT, 0, s>>>(x, y, scale, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin_scale(double* x, const double* kx, const double* b, int n_loads, long long n,
+                                  double* partial, cudaStream_t s) {
+  const dim3 grid(SM_BLOCKS, n_loads);
+  dot2_partial_kernel<<<grid, VT, 0, s>>>(x, kx, b, n, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  galerkin_scale_kernel<<<grid, VT, 0, s>>>(x, n, partial);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,11 @@ EXPORTS = ("fehom_default_options", "fehom_setup", "fehom_precond_build", "fehom
            "fehom_last_error", "fehom_query", "fehom_apply_stiffness", "fehom_rhs", "fehom_apply_precond",
            "fehom_get_symbol_inverse", "fehom_mean_flux", "fehom_kernel_times", "fehom_launch_count",
            "fehom_fft_plan", "fehom_mean_flux_noalloc", "fehom_pcg_coefficients", "fehom_eig_bounds",
-           "fehom_batch_create", "fehom_solve_batch", "fehom_batch_destroy", "fehom_batch_last_error")
+           "fehom_batch_create", "fehom_solve_batch", "fehom_batch_destroy", "fehom_batch_last_error",
+           # include/fehom_unet.h
+           "fehom_unet_create", "fehom_unet_destroy", "fehom_unet_last_error", "fehom_unet_param_count",
+           "fehom_unet_set_params", "fehom_unet_get_params", "fehom_unet_predict", "fehom_unet_loss_grad",
+           "fehom_unet_train_step", "fehom_conv3_bf16", "fehom_conv3_wgrad_bf16", "fehom_unet_set_loss")
 
 KERNEL_CLASSES = ("stiffness", "fft_x_fwd", "fft_y_fwd", "fft_last", "fft_y_inv", "fft_x_inv")
 
@@ -37,7 +41,7 @@ KERNEL_CLASSES = ("stiffness", "fft_x_fwd", "fft_y_fwd", "fft_last", "fft_y_inv"
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_iter", C.c_int), ("inner_tol", C.c_double),
                 ("stream", C.c_void_p), ("use_graph", C.c_int), ("profile", C.c_int),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int), ("x0_scaling", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -110,6 +114,31 @@ def load_library(path: str = LIB_PATH):
     ip = C.POINTER(C.c_int)
     lib.fehom_fft_plan.argtypes = [vp, i, ip, ip, ip, dp]
     lib.fehom_fft_plan.restype = i
+    fp = C.POINTER(C.c_float)
+    lib.fehom_unet_create.argtypes = [C.POINTER(vp), C.c_int64, i, ip, i, i, i, vp]
+    lib.fehom_unet_create.restype = i
+    lib.fehom_unet_destroy.argtypes = [vp]
+    lib.fehom_unet_destroy.restype = None
+    lib.fehom_unet_last_error.argtypes = [vp]
+    lib.fehom_unet_last_error.restype = C.c_char_p
+    lib.fehom_unet_set_loss.argtypes = [vp, i, d]
+    lib.fehom_unet_set_loss.restype = i
+    lib.fehom_unet_param_count.argtypes = [vp, i64p]
+    lib.fehom_unet_param_count.restype = i
+    lib.fehom_unet_set_params.argtypes = [vp, fp]
+    lib.fehom_unet_set_params.restype = i
+    lib.fehom_unet_get_params.argtypes = [vp, fp]
+    lib.fehom_unet_get_params.restype = i
+    lib.fehom_unet_predict.argtypes = [vp, i, vp, vp, d, vp]
+    lib.fehom_unet_predict.restype = i
+    lib.fehom_unet_loss_grad.argtypes = [vp, i, vp, vp, vp, d, dp, fp]
+    lib.fehom_unet_loss_grad.restype = i
+    lib.fehom_unet_train_step.argtypes = [vp, i, vp, vp, vp, d, d, dp]
+    lib.fehom_unet_train_step.restype = i
+    lib.fehom_conv3_bf16.argtypes = [i, i, i, i, i, i, vp, vp, vp, i, vp, vp]
+    lib.fehom_conv3_bf16.restype = i
+    lib.fehom_conv3_wgrad_bf16.argtypes = [i, i, i, i, i, i, vp, vp, vp, vp]
+    lib.fehom_conv3_wgrad_bf16.restype = i
     _lib = lib
     return lib
 
@@ -129,7 +158,8 @@ class Solver:
     """One periodic cell: fehom_setup on construction, fehom_destroy on close()."""
 
     def __init__(self, elem, physics, n, ids, moduli, ref_material=None, precision="fp64", max_iter=10000,
-                 inner_tol=1e-3, cell=None, use_graph=True, stream=None, profile=False, autotune=True):
+                 inner_tol=1e-3, cell=None, use_graph=True, stream=None, profile=False, autotune=True,
+                 x0_scaling=True):
         torch = _torch()
         self.lib = load_library()
         self.elem, self.physics = elem, physics
@@ -144,6 +174,7 @@ class Solver:
         opt.use_graph = 1 if use_graph else 0
         opt.profile = 1 if profile else 0
         opt.autotune = 1 if autotune else 0
+        opt.x0_scaling = 1 if x0_scaling else 0
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opt.stream = C.c_void_p(self.stream.cuda_stream)
         self._opt = opt
@@ -326,3 +357,106 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class UNet:
+    """The warm-start network of include/fehom_unet.h (fehom_unet_create on construction)."""
+
+    def __init__(self, n, widths=(16, 32, 64, 128), n_phases=2, n_out=3, max_batch=8, stream=None):
+        torch = _torch()
+        self.lib = load_library()
+        self.n, self.widths, self.n_out, self.n_phases = int(n), tuple(int(w) for w in widths), int(n_out), int(n_phases)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        w = (C.c_int * len(self.widths))(*self.widths)
+        net = C.c_void_p()
+        st = self.lib.fehom_unet_create(C.byref(net), self.n, len(self.widths), w, self.n_phases, self.n_out,
+                                        int(max_batch), C.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise FehomError(st, self.lib.fehom_unet_last_error(None).decode())
+        self.net = net
+        cnt = C.c_int64()
+        self.lib.fehom_unet_param_count(net, C.byref(cnt))
+        self.n_params = cnt.value
+
+    def _check(self, st):
+        if st != 0:
+            raise FehomError(st, self.lib.fehom_unet_last_error(self.net).decode())
+
+    def close(self):
+        if getattr(self, "net", None):
+            self.lib.fehom_unet_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_loss(self, kind="mse", l2_weight=0.0):
+        self._check(self.lib.fehom_unet_set_loss(self.net, {"mse": 0, "h1": 1}[kind], float(l2_weight)))
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(np.asarray(theta, np.float32))
+        assert t.size == self.n_params
+        self._check(self.lib.fehom_unet_set_params(self.net, t.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def get_params(self):
+        t = np.zeros(self.n_params, np.float32)
+        self._check(self.lib.fehom_unet_get_params(self.net, t.ctypes.data_as(C.POINTER(C.c_float))))
+        return t
+
+    def predict(self, ids, features, out_scale, out=None):
+        """ids: uint8 [B, N] (device), features: float32 [B, n_phases] (device) -> x0 float64 [B, n_out, N]."""
+        torch = _torch()
+        B = ids.shape[0]
+        if out is None:
+            out = torch.empty((B, self.n_out, self.n ** 3), dtype=torch.float64, device=ids.device)
+        self._check(self.lib.fehom_unet_predict(self.net, B, _ptr(ids), _ptr(features), float(out_scale), _ptr(out)))
+        return out
+
+    def loss_grad(self, ids, features, target, out_scale):
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_double()
+        self._check(self.lib.fehom_unet_loss_grad(self.net, ids.shape[0], _ptr(ids), _ptr(features), _ptr(target),
+                                                  float(out_scale), C.byref(loss), g.ctypes.data_as(C.POINTER(C.c_float))))
+        return loss.value, g
+
+    def train_step(self, ids, features, target, out_scale, lr, want_loss=False):
+        loss = C.c_double()
+        self._check(self.lib.fehom_unet_train_step(self.net, ids.shape[0], _ptr(ids), _ptr(features), _ptr(target),
+                                                   float(out_scale), float(lr), C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+
+def conv3_bf16(x, w, bias=None, relu=False):
+    """Tensor-core periodic 3x3x3 convolution (fehom_conv3_bf16): x bf16 [B, D, H, W, Cin],
+    w bf16 [27, Cout, Cin] -> float32 [B, D, H, W, Cout]."""
+    torch = _torch()
+    lib = load_library()
+    B, D, H, W, Cin = x.shape
+    Cout = w.shape[1]
+    y = torch.empty((B, D, H, W, Cout), dtype=torch.float32, device=x.device)
+    st = lib.fehom_conv3_bf16(B, D, H, W, Cin, Cout, _ptr(x), _ptr(w), _ptr(bias), 1 if relu else 0, _ptr(y),
+                              C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != 0:
+        raise FehomError(st, "fehom_conv3_bf16")
+    return y
+
+
+def conv3_wgrad_bf16(x, dy):
+    """Weight gradient of the periodic 3x3x3 convolution (fehom_conv3_wgrad_bf16) -> float32 [27, Cout, Cin]."""
+    torch = _torch()
+    lib = load_library()
+    B, D, H, W, Cin = x.shape
+    Cout = dy.shape[-1]
+    dw = torch.empty((27, Cout, Cin), dtype=torch.float32, device=x.device)
+    st = lib.fehom_conv3_wgrad_bf16(B, D, H, W, Cin, Cout, _ptr(x), _ptr(dy), _ptr(dw),
+                                    C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != 0:
+        raise FehomError(st, "fehom_conv3_wgrad_bf16")
+    return dw

@@ -223,3 +223,23 @@ def workload_batched_spheres(count: int = 48, sizes=(32, 64, 96), seed0: int = 0
         moduli = np.stack([isotropic_elastic_mandel(1.0, 0.3), isotropic_elastic_mandel(contrast, 0.2)])
         out.append(dict(n=(n, n, n), ids=ids, moduli=moduli, contrast=contrast, seed=seed))
     return out
+
+
+def workload_warmstart(n: int = 64, count: int = 4000, seed0: int = 0):
+    """Scalar-conductivity cells for the learned warm start: even seeds draw 60 periodic spheres with
+    radii U[n/16, n/8], odd seeds a Gaussian random field with correlation length n/16 voxels
+    thresholded at 50 % volume; phase 1 has conductivity 10^U[1, 3] in a matrix of conductivity 1."""
+    out = []
+    for i in range(count):
+        seed = seed0 + i
+        rng = np.random.default_rng(20_000 + seed)
+        contrast = 10.0 ** rng.uniform(1.0, 3.0)
+        if seed % 2 == 0:
+            ids = spheres3d(n, 60, n / 16.0, n / 8.0, seed)
+            kind = "spheres"
+        else:
+            ids = grf_threshold((n, n, n), ell=n / 16.0, seed=seed)
+            kind = "grf"
+        moduli = np.stack([isotropic_conductivity(1.0, 3), isotropic_conductivity(contrast, 3)])
+        out.append(dict(n=(n, n, n), ids=ids, moduli=moduli, contrast=contrast, seed=seed, kind=kind))
+    return out

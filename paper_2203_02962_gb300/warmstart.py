@@ -1,0 +1,220 @@
+"""Learned warm start of the PCG solve: training data from the solver itself, training of the
+periodic U-Net (include/fehom_unet.h) on the GPU, and the comparison of PCG iterations and
+time-to-tolerance from the network's guess against the zero initial guess.
+
+The paper's method has no learned part; this module adds one around it without changing the solve:
+PCG still runs to the same tolerance, whose normalisation by the right-hand side (stopping rule of
+Sec. 6) does not depend on the initial guess.
+
+Workload (inputs.workload_warmstart): n^3 scalar-conductivity cells, half periodic spheres and half
+thresholded Gaussian random fields, inclusion conductivity 10^U[1, 3] in a matrix of 1, three unit
+macroscopic gradients each.  The network input is log10(conductivity) / 3 per voxel (a per-phase
+feature looked up by phase id); its three outputs, times a scale fixed from the training targets,
+are the initial fluctuation fields of the three loads.
+
+    python -m paper_2203_02962_gb300.warmstart --n 64 --train 4000 --test 500
+prints one JSON line with the training losses and the cold/warm PCG statistics.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import time
+
+import numpy as np
+
+from . import inputs
+
+LOADS = np.eye(3)
+
+
+def features(moduli) -> np.ndarray:
+    """Per-phase network input: log10 of the (isotropic) conductivity, divided by 3."""
+    return (np.log10(np.asarray(moduli)[:, 0, 0]) / 3.0).astype(np.float32)
+
+
+def _cells(args):
+    n, start, count = args
+    return inputs.workload_warmstart(n, count, start)
+
+
+def draw_cells(n: int, count: int, seed0: int, workers: int = 0):
+    """The seeded cells seed0 .. seed0 + count - 1, drawn in a spawn-started process pool."""
+    if workers <= 1 or count < 16:
+        return inputs.workload_warmstart(n, count, seed0)
+    chunk = max(1, count // (4 * workers))
+    jobs = [(n, seed0 + s, min(chunk, count - s)) for s in range(0, count, chunk)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        parts = pool.map(_cells, jobs)
+    return [c for p in parts for c in p]
+
+
+def solve_cells(cells, tol=1e-6, precision="mixed"):
+    """Solve every cell for the three unit gradients; device tensors of ids, features and fields."""
+    from . import fehom
+    torch = fehom._torch()
+    count = len(cells)
+    n = cells[0]["n"][0]
+    N = n ** 3
+    ids = torch.empty((count, N), dtype=torch.uint8, device="cuda")
+    feat = torch.empty((count, 2), dtype=torch.float32, device="cuda")
+    fields = torch.empty((count, 3, N), dtype=torch.float64, device="cuda")
+    iters = np.zeros((count, 3), np.int64)
+    for i, c in enumerate(cells):
+        ids[i].copy_(torch.from_numpy(np.ascontiguousarray(c["ids"].reshape(-1))))
+        feat[i].copy_(torch.from_numpy(features(c["moduli"])))
+        s = fehom.Solver("hex8_3d", "scalar", c["n"], ids[i], c["moduli"], precision=precision)
+        s.precond_build()
+        out = s.solve(LOADS, tol=tol)
+        fields[i].copy_(out["fields"][:, 0, :])
+        iters[i] = [inf["iterations"] for inf in out["info"]]
+        s.close()
+    return dict(ids=ids, feat=feat, fields=fields, iters=iters)
+
+
+def train(net, data, steps: int, batch: int, lr: float, out_scale: float, log_every: int = 50):
+    """Adam on contiguous mini-batches of the (randomly ordered) training set, cosine learning rate."""
+    count = data["ids"].shape[0]
+    per_epoch = max(1, count // batch)
+    losses = []
+    for k in range(steps):
+        j = (k % per_epoch) * batch
+        b = min(batch, count - j)
+        lr_k = lr * 0.5 * (1.0 + math.cos(math.pi * k / steps))
+        want = (k % log_every == 0) or (k == steps - 1)
+        loss = net.train_step(data["ids"][j:j + b], data["feat"][j:j + b], data["fields"][j:j + b], out_scale, lr_k,
+                              want_loss=want)
+        if want:
+            losses.append((k, loss))
+    return losses
+
+
+def evaluate(net, cells, data, out_scale: float, tol=1e-6, precision="mixed", max_batch=8):
+    """PCG from zero and from the network's guess on every test cell: iterations and device times."""
+    from . import fehom
+    torch = fehom._torch()
+    count = len(cells)
+    N = data["ids"].shape[1]
+    x0 = torch.empty((count, 3, N), dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for j in range(0, count, max_batch):
+        b = min(max_batch, count - j)
+        net.predict(data["ids"][j:j + b], data["feat"][j:j + b], out_scale, out=x0[j:j + b])
+    e1.record()
+    torch.cuda.synchronize()
+    predict_ms = e0.elapsed_time(e1) / count
+    cold, warm, raw = [], [], []
+    for i, c in enumerate(cells):
+        for scaled, runs in ((True, ((cold, None), (warm, x0[i]))), (False, ((raw, x0[i]),))):
+            s = fehom.Solver("hex8_3d", "scalar", c["n"], data["ids"][i], c["moduli"], precision=precision,
+                             x0_scaling=scaled)
+            s.precond_build()
+            s.solve(LOADS, tol=tol, fields=None)  # first solve of a batch size tunes the FFT plans
+            for dst, guess in runs:
+                out = s.solve(LOADS, tol=tol, x0=guess, fields=None, raise_on_failure=False)
+                dst.append(dict(iterations=sum(inf["iterations"] for inf in out["info"]),
+                                ms=out["info"][0]["solve_ms"],  # the three loads are solved as one batch
+                                converged=all(inf["converged"] for inf in out["info"])))
+            s.close()
+
+    def stats(rows):
+        return {"iterations_mean": float(np.mean([r["iterations"] for r in rows])),
+                "solve_ms_mean": float(np.mean([r["ms"] for r in rows])),
+                "all_converged": bool(all(r["converged"] for r in rows))}
+
+    return stats(cold), stats(warm), stats(raw), predict_ms
+
+
+def experiment(n=64, n_train=4000, n_test=500, steps=None, batch=8, lr=1e-3, seed=0, widths=(16, 32, 64, 128),
+               tol=1e-6, precision="mixed", workers=0):
+    """Generate, train, evaluate; returns a dict of the results (see the module docstring)."""
+    from . import fehom
+    torch = fehom._torch()
+    t0 = time.perf_counter()
+    cells_train = draw_cells(n, n_train, seed * 1_000_000, workers)
+    cells_test = draw_cells(n, n_test, seed * 1_000_000 + 10_000_000, workers)
+    t_draw = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    data = solve_cells(cells_train, tol, precision)
+    test = solve_cells(cells_test, tol, precision)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    out_scale = float(data["fields"].std())
+    net = fehom.UNet(n, widths, n_phases=2, n_out=3, max_batch=batch)
+    net.set_params(init_params(widths, 3, seed))
+    if steps is None:
+        steps = 8 * max(1, n_train // batch)  # 8 epochs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = train(net, data, steps, batch, lr, out_scale)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    cold, warm, raw, predict_ms = evaluate(net, cells_test, test, out_scale, tol, precision, batch)
+    net.close()
+    return {"n": n, "n_train": n_train, "n_test": n_test, "steps": steps, "batch": batch, "lr": lr,
+            "widths": list(widths), "n_params": int(sum(_layer_sizes(widths, 3))), "out_scale": out_scale,
+            "train_loss_first": losses[0][1], "train_loss_last": losses[-1][1], "losses": losses,
+            "cold": cold, "warm": warm, "warm_unscaled": raw, "predict_ms_per_cell": predict_ms,
+            "iteration_saving": 1.0 - warm["iterations_mean"] / cold["iterations_mean"],
+            "time_saving_incl_predict": 1.0 - (warm["solve_ms_mean"] + predict_ms) / cold["solve_ms_mean"],
+            "data_iterations_mean": float(data["iters"].sum(axis=1).mean()),
+            "seconds": {"draw": t_draw, "solve": t_solve, "train": t_train}}
+
+
+def _layer_sizes(widths, n_out):
+    """(Cin, Cout) of the 3x3x3 layers in parameter order -> sizes of each weight and bias block."""
+    w = list(widths)
+    L = len(w)
+    shapes = [(1, w[0]), (w[0], w[0])]
+    for l in range(1, L):
+        shapes += [(w[l - 1], w[l]), (w[l], w[l])]
+    for l in range(L - 2, -1, -1):
+        shapes += [(w[l] + w[l + 1], w[l]), (w[l], w[l])]
+    sizes = []
+    for ci, co in shapes:
+        sizes += [27 * ci * co, co]
+    sizes += [n_out * w[0], n_out]
+    return sizes
+
+
+def init_params(widths, n_out: int, seed: int) -> np.ndarray:
+    """He-normal initial weights (std sqrt(2 / fan_in); head sqrt(1 / fan_in)), zero biases, in the
+    flat parameter order of include/fehom_unet.h, from numpy default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    sizes = _layer_sizes(widths, n_out)
+    w = list(widths)
+    fan = [1 * 27, w[0] * 27]
+    for l in range(1, len(w)):
+        fan += [w[l - 1] * 27, w[l] * 27]
+    for l in range(len(w) - 2, -1, -1):
+        fan += [(w[l] + w[l + 1]) * 27, w[l] * 27]
+    parts = []
+    for k, f in enumerate(fan):
+        parts.append(rng.standard_normal(sizes[2 * k]) * math.sqrt(2.0 / f))
+        parts.append(np.zeros(sizes[2 * k + 1]))
+    parts.append(rng.standard_normal(sizes[-2]) * math.sqrt(1.0 / w[0]))
+    parts.append(np.zeros(sizes[-1]))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--train", type=int, default=4000)
+    ap.add_argument("--test", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--workers", type=int, default=max(1, (mp.cpu_count() or 2) - 1))
+    args = ap.parse_args()
+    res = experiment(args.n, args.train, args.test, args.steps, args.batch, args.lr, args.seed, workers=args.workers)
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,4 +1,4 @@
-"""The C-ABI library loads and exports every entry point that include/fehom.h declares (no GPU)."""
+"""The C-ABI library loads and exports every entry point that include/*.h declares (no GPU)."""
 import ctypes
 import os
 import re
@@ -9,7 +9,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    txt = open(os.path.join(ROOT, "include", "fehom.h")).read()
+    inc = os.path.join(ROOT, "include")
+    txt = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(fehom_[a-z0-9_]+)\s*\(", txt)))
 

@@ -262,6 +262,34 @@ def test_warm_start_with_solution_converges_immediately():
     s.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_warm_start_galerkin_scaling(precision):
+    """x0 = 2.5 u*: the energy-optimal factor <b, x0> / <x0, K x0> is 1 / 2.5, so the scaled start is
+    the solution; without the scaling PCG has to remove the excess.  A constant x0 (mean-free part 0)
+    gets gamma = 0 and behaves like the zero guess."""
+    n = 16
+    ids, mod = _small_elastic(n, seed=11)
+    ref = _solver("hex8_3d", "elastic", (n, n, n), ids, mod)
+    ref.precond_build()
+    o = ref.solve(np.eye(6), tol=1e-11)
+    ref.close()
+    u = o["fields"].contiguous()
+    for scaled in (True, False):
+        s = _solver("hex8_3d", "elastic", (n, n, n), ids, mod, precision=precision, x0_scaling=scaled)
+        s.precond_build()
+        w = s.solve(np.eye(6), tol=1e-6, x0=(2.5 * u).contiguous())
+        its = [i["iterations"] for i in w["info"]]
+        if scaled:
+            assert max(its) <= 1, its
+        else:
+            assert min(its) > 1, its
+        assert _rel(w["C_eff"], o["C_eff"]) < 1e-5
+        cold = s.solve(np.eye(6), tol=1e-6)
+        c = s.solve(np.eye(6), tol=1e-6, x0=(u * 0 + 3.0).contiguous())
+        assert [i["iterations"] for i in c["info"]] == [i["iterations"] for i in cold["info"]]
+        s.close()
+
+
 def test_homogeneous_and_zero_load():
     C = _rand_spd(6, 12)
     ids = np.zeros((8, 8, 8), np.uint8)

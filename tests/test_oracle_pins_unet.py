@@ -58,21 +58,22 @@ def test_adjoints():
     assert abs(float((U.up(x) * q).sum()) - float((x * U.up_T(q)).sum())) < 1e-11
 
 
-@pytest.mark.parametrize("widths,n", [((2, 3), 4), ((2, 2, 3), 8)])
-def test_gradient_matches_central_differences(widths, n):
+@pytest.mark.parametrize("widths,n,kind", [((2, 3), 4, "mse"), ((2, 2, 3), 8, "mse"), ((2, 3), 4, "h1")])
+def test_gradient_matches_central_differences(widths, n, kind):
     rng = _rng(3)
     specs = U.layer_specs(widths, in_ch=1, n_loads=2)
     theta = U.init_params(specs, seed=5) + 0.05 * rng.standard_normal(U.n_params(specs))
     xs = rng.standard_normal((2, 1, n, n, n))
     ts = rng.standard_normal((2, 2, n, n, n))
-    loss, grad, _ = U.loss_and_grad(theta, specs, xs, ts)
+    f = lambda th: U.loss_and_grad(th, specs, xs, ts, loss_kind=kind, l2_weight=0.1)
+    loss, grad, _ = f(theta)
     h = 1e-6
     idx = rng.choice(theta.size, size=40, replace=False)
     for i in idx:
         tp, tm = theta.copy(), theta.copy()
         tp[i] += h
         tm[i] -= h
-        fd = (U.loss_and_grad(tp, specs, xs, ts)[0] - U.loss_and_grad(tm, specs, xs, ts)[0]) / (2 * h)
+        fd = (f(tp)[0] - f(tm)[0]) / (2 * h)
         assert abs(fd - grad[i]) <= 1e-6 * max(1e-3, abs(fd)), (i, fd, grad[i])
 
 
@@ -109,3 +110,14 @@ def test_first_adam_step_closed_form():
     new = U.adam_step(th.copy(), g, m, v, step=1, lr=1e-2)
     # m_hat = g, v_hat = g^2 after bias correction
     assert np.allclose(new, th - 1e-2 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+
+
+def test_h1_loss_of_a_single_mode():
+    # r = cos(2 pi x / n) on one load: each forward difference squared sums to n^3 (2 - 2 cos(2 pi / n)) / 2
+    n = 8
+    x = np.arange(n)
+    r = np.broadcast_to(np.cos(2 * np.pi * x / n), (1, n, n, n)).copy()
+    loss, g = U.field_loss(r, count=1, kind="h1", l2_weight=0.0)
+    assert abs(loss - n ** 3 * (2 - 2 * np.cos(2 * np.pi / n)) / 2) < 1e-10
+    # the gradient is 2 (-Laplacian) r = 2 (2 - 2 cos(2 pi / n)) r for this eigenmode
+    assert np.abs(g - 2 * (2 - 2 * np.cos(2 * np.pi / n)) * r).max() < 1e-12
