@@ -254,6 +254,7 @@ def run_ours(args):
     out["cufft_reference"] = cufft_comparison(N, c, len(loads), rmx["kt"], r64["kt"], rmx["load_iters"],
                                               r64["load_iters"], args.steps)
     out["batched"] = run_batched(args)
+    out["warm_start_unet"] = run_unet(args)
     out["cpu_baseline"] = cpu_baseline(short=True)
     print(json.dumps(out))
 
@@ -328,6 +329,72 @@ def run_batched(args):
             "wall_ms_per_step": wall_ms, "sequential_wall_ms_per_step": seq_ms,
             "speedup_vs_sequential": seq_ms / wall_ms, "all_converged": conv, "gpu_launches": launches,
             "clocks": clk.summary()}
+
+
+def unet_flops(n, widths, batch):
+    """Algorithmic FLOPs (2 per multiply-add) of one training step of the warm-start U-Net: every
+    3x3x3 convolution forward and weight gradient, and the input gradient of all but the first."""
+    w = list(widths)
+    L = len(w)
+    layers = [(1, w[0], 0), (w[0], w[0], 0)]
+    for l in range(1, L):
+        layers += [(w[l - 1], w[l], l), (w[l], w[l], l)]
+    for l in range(L - 2, -1, -1):
+        layers += [(w[l] + w[l + 1], w[l], l), (w[l], w[l], l)]
+    total = 0.0
+    for i, (ci, co, l) in enumerate(layers):
+        f = 2.0 * 27 * ci * co * batch * (n >> l) ** 3
+        total += f * (2 if i == 0 else 3)
+    return total
+
+
+def run_unet(args):
+    """One training step of the warm-start U-Net (64^3, widths 16-128, batch 8) on synthetic phase
+    fields and targets: device time per step and achieved BF16 tensor FLOP/s."""
+    import torch
+    from paper_2203_02962_gb300 import fehom, warmstart
+    n, widths, B = 64, (16, 32, 64, 128), 8
+    g = torch.Generator(device="cpu").manual_seed(0)
+    ids = (torch.rand((B, n ** 3), generator=g) < 0.3).to(torch.uint8).cuda()
+    feat = torch.tensor([[0.0, 0.3 + 0.08 * b] for b in range(B)], dtype=torch.float32).cuda()
+    tgt = (0.05 * torch.randn((B, 3, n ** 3), generator=g, dtype=torch.float64)).cuda()
+    net = fehom.UNet(n, widths, n_phases=2, n_out=3, max_batch=B)
+    net.set_params(warmstart.init_params(widths, 3, 0))
+    net.set_loss("h1", 0.1)
+    for _ in range(max(3, args.warmup)):
+        net.train_step(ids, feat, tgt, 0.05, 1e-4)
+    torch.cuda.synchronize()
+    steps = max(10, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(net.stream)
+    for _ in range(steps):
+        net.train_step(ids, feat, tgt, 0.05, 1e-4)
+    e1.record(net.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    x0 = torch.empty((B, 3, n ** 3), dtype=torch.float64, device="cuda")
+    e0.record(net.stream)
+    for _ in range(steps):
+        net.predict(ids, feat, 0.05, out=x0)
+    e1.record(net.stream)
+    torch.cuda.synchronize()
+    pms = e0.elapsed_time(e1) / steps
+    net.close()
+    flops = unet_flops(n, widths, B)
+    peak = peaks_tensor()
+    return {"workload": f"U-Net training step, {n}^3, widths {list(widths)}, batch {B}, H1 loss, Adam",
+            "ms_per_step": ms, "predict_ms_per_batch": pms, "algorithmic_tflop_per_step": flops / 1e12,
+            "achieved_tflops": flops / (ms * 1e-3) / 1e12, "peak_tflops_bf16_sustained": peak,
+            "frac": flops / (ms * 1e-3) / 1e12 / peak if peak else None}
+
+
+def peaks_tensor():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d.get("bf16_tflops_sustained") or d.get("bf16_tflops"))
+    except Exception:
+        return 1700.0
 
 
 def cpu_baseline(short=False):

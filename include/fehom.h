@@ -78,6 +78,9 @@ typedef struct {
   int x0_scaling;    /* 1 (default): a warm start x0 (mean removed) is replaced, per load, by gamma x0 with
                         gamma = <b, x0> / <x0, K x0> (0 when <x0, K x0> = 0): the multiple of x0 closest to
                         the solution in the energy norm, never farther from it than the zero guess */
+  int fft_xy;        /* FP32 register-split FFT passes: the fused x-y passes (3-D fields with 128 x 128 planes)
+                        and the last-axis pass for nz = 128 (c = 1 or 3): -1 (default) the tuner decides for
+                        each (the generic passes when autotune = 0), 0 never, 1 always when supported */
 } fehom_options;
 
 /* Kernel classes of one PCG iteration, for fehom_kernel_times. */
@@ -212,8 +215,21 @@ fehom_status fehom_eig_bounds(fehom_ctx* ctx, double* lo_values, int64_t* lo_cou
 
 /* Launch plan of the FFT passes in use for a precision (FEHOM_FP64 / FEHOM_MIXED): x-line pairs per
  * CTA, columns per CTA of the y pass and of the last-axis pass (0 = built-in choice, not tuned yet),
- * and the device milliseconds of the chosen plans measured by the tuner (ms[3], may be NULL). */
-fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int* tc_y, int* tc_last, double* ms);
+ * the device milliseconds of the chosen plans measured by the tuner (ms[3]: x passes, y passes,
+ * last-axis pass; may be NULL), and whether the fused x-y passes replace the separate x and y passes
+ * (*xy_fused = 1; FP32 3-D fields with 128 x 128 planes; then ms[0] times them and ms[1] = 0; may be NULL). */
+fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int* tc_y, int* tc_last, double* ms,
+                            int* xy_fused);
+
+/* Energy form of the effective tensor of the last fehom_solve whose n_loads == m loads were linearly
+ * independent and which asked for C_eff: with fields x_l, right-hand sides b_l and true residuals
+ * r_l = b_l - K x_l, the energies sum_Q w_Q (e_i + D x_i)^T C (e_j + D x_j) = e_i^T C_eff e_j |Y|
+ * (the Hill-Mandel form of the homogenised energy, Sec. 2 with the quadrature of Sec. 3) are
+ * |Y| e_i^T <C> e_j - x_j . b_i - x_i . r_j, symmetrised; the result is stationary at the solution,
+ * so its error is second order in the solve error (the volume-averaged stress of fehom_solve is
+ * first order).  FP64, reduced on the device in a fixed order.  c_eff: host, m x m row-major.
+ * FEHOM_E_STATE when no such solve has run. */
+fehom_status fehom_effective_energy(const fehom_ctx* ctx, double* c_eff);
 
 /* Number of kernel launches the context has issued since setup (kernels replayed from a CUDA graph
  * are counted once per replay). */

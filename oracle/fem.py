@@ -224,6 +224,24 @@ def mean_flux(grid: Grid, phases, moduli, e, u):
     return acc
 
 
+def energy(grid: Grid, phases, moduli, e_i, u_i, e_j, u_j):
+    """sum_Q w_Q (e_i + (D u_i)_Q)^T C_Q (e_j + (D u_j)_Q): the bilinear form of the cell energy of
+    Sec. 2 (strain e + grad u, stress C times it) with the quadrature of Eq. global_sum.  At the
+    solutions of the loads e_i, e_j it equals |Y| e_i^T C_eff e_j (Hill-Mandel)."""
+    phases = np.asarray(phases).ravel()
+    dofs = grid.element_dofs()
+    ui, uj = u_i[dofs], u_j[dofs]
+    acc = 0.0
+    for B, w in element_B(grid):
+        si = np.asarray(e_i, float)[None, :] + ui @ B.T
+        sj = np.asarray(e_j, float)[None, :] + uj @ B.T
+        for p, C in enumerate(moduli):
+            sel = phases == p
+            if np.any(sel):
+                acc += w * float(np.einsum("qa,ab,qb->", si[sel], C, sj[sel]))
+    return acc
+
+
 def mean_material(grid: Grid, phases, moduli):
     """C_mean = (1/|Y|) sum_Q C(x_Q) w_Q (Sec. 6.2 reference-material choice)."""
     phases = np.asarray(phases).ravel()

@@ -34,6 +34,7 @@ struct fehom_ctx {
   std::vector<double> moduli;     // [phase][m*m]
   std::vector<double> cref;       // [m*m]
   std::vector<double> frac;       // volume fractions
+  std::vector<double> c_eff_energy;  // energy-form C_eff of the last solve with m loads (empty: none)
   bool iso = false;               // isotropic phases on a cubic grid (fast stiffness path)
   bool iso_ref = false;
   // device
@@ -67,6 +68,8 @@ struct fehom_ctx {
   cudaEvent_t ev[8][FEHOM_K_COUNT][2];
   struct FftPlan {
     int pairs = 0, tc_y = 0, tc_last = 0;
+    int xy = 0;        // 1: fused x-y passes
+    int last_reg = 0;  // 1: register-split last-axis pass
     int tuned_loads = 0;
     double ms[3] = {0, 0, 0};
   } plan[2];                   // [0] FP64 kernels, [1] FP32 kernels
@@ -284,6 +287,9 @@ void fill_dims_args(fehom_ctx* ctx, FftArgs& f, bool fp32, int n_loads) {
   f.pairs = pl.pairs;
   f.tc_y = pl.tc_y;
   f.tc_last = pl.tc_last;
+  f.xy = (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.xy)) && fft_xy_supported(ctx->d, fp32) ? 1 : 0;
+  f.last_reg =
+      (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.last_reg)) && fft_last128_supported(ctx->d, fp32) ? 1 : 0;
 }
 
 StencilArgs stencil_args(fehom_ctx* ctx, bool fp32, int n_loads) {
@@ -380,6 +386,14 @@ cudaError_t precond_passes(fehom_ctx* ctx, FftArgs f, int fwd_mode, int inv_mode
   f.mode = fwd_mode;
   f.f0 = fwd_field;
   f.f1 = fwd_ap;
+  if (f.xy) {  // fused x-y passes: their times are reported under the x classes
+    if ((e = timed(FEHOM_K_FFT_X_FWD, [&] { return launch_fft_xy<T>(f, 0, s); })) != cudaSuccess) return e;
+    if ((e = timed(FEHOM_K_FFT_LAST, [&] { return launch_fft_last_solve<T>(f, s); })) != cudaSuccess) return e;
+    f.mode = inv_mode;
+    f.f0 = inv_f0;
+    f.f2 = inv_f2;
+    return timed(FEHOM_K_FFT_X_INV, [&] { return launch_fft_xy<T>(f, 1, s); });
+  }
   if ((e = timed(FEHOM_K_FFT_X_FWD, [&] { return launch_fft_x_fwd<T>(f, s); })) != cudaSuccess) return e;
   if (ctx->d.dim == 3 && (e = timed(FEHOM_K_FFT_Y_FWD, [&] { return launch_fft_y<T>(f, 0, s); })) != cudaSuccess) return e;
   if ((e = timed(FEHOM_K_FFT_LAST, [&] { return launch_fft_last_solve<T>(f, s); })) != cudaSuccess) return e;
@@ -424,7 +438,9 @@ fehom_status harvest_events(fehom_ctx* ctx, int prec, int n_iter) {
   const int nk = FEHOM_K_COUNT;
   for (int i = 0; i < std::min(n_iter, kChunk); ++i)
     for (int k = 0; k < nk; ++k) {
-      if (ctx->d.dim == 2 && (k == FEHOM_K_FFT_Y_FWD || k == FEHOM_K_FFT_Y_INV)) continue;
+      const bool no_y = ctx->d.dim == 2 || (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && ctx->plan[prec].xy)) &&
+                                                fft_xy_supported(ctx->d, prec == 1);
+      if (no_y && (k == FEHOM_K_FFT_Y_FWD || k == FEHOM_K_FFT_Y_INV)) continue;
       float ms = 0.0f;
       CK(cudaEventElapsedTime(&ms, ctx->ev[i][k][0], ctx->ev[i][k][1]));
       ctx->kms[prec][k] += ms;
@@ -455,6 +471,8 @@ fehom_status autotune_fft(fehom_ctx* ctx, int n_loads) {
   fill_dims_args(ctx, base, prec == 1, n_loads);
   base.st = nullptr;
   base.mode = FX_PLAIN;
+  base.xy = 0;
+  base.last_reg = 0;
   auto timeit = [&](auto&& body) -> double {
     if (body() != cudaSuccess) {
       cudaGetLastError();
@@ -505,12 +523,43 @@ fehom_status autotune_fft(fehom_ctx* ctx, int n_loads) {
     f.tc_last = TC;
     return launch_fft_last_solve<T>(f, s);
   }, &bl, &ml);
+  // fused x-y passes against the best separate x and y passes
+  int xy = 0;
+  if (ctx->opt.fft_xy < 0 && fft_xy_supported(ctx->d, prec == 1)) {
+    const double mxy = timeit([&] {
+      FftArgs f = base;
+      f.f0 = fin;
+      cudaError_t e = launch_fft_xy<T>(f, 0, s);
+      if (e != cudaSuccess) return e;
+      f.f0 = fout;
+      return launch_fft_xy<T>(f, 1, s);
+    });
+    if (mxy > 0 && mxy < mp + my) {
+      xy = 1;
+      mp = mxy;
+      my = 0;
+    }
+  }
+  int last_reg = 0;
+  if (ctx->opt.fft_xy < 0 && fft_last128_supported(ctx->d, prec == 1)) {
+    const double mreg = timeit([&] {
+      FftArgs f = base;
+      f.last_reg = 1;
+      return launch_fft_last_solve<T>(f, s);
+    });
+    if (mreg > 0 && mreg < ml) {
+      last_reg = 1;
+      ml = mreg;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaGetLastError());
   pl.pairs = bp;
   pl.tc_y = by;
   pl.tc_last = bl;
+  pl.xy = ctx->opt.fft_xy == 1 ? (fft_xy_supported(ctx->d, prec == 1) ? 1 : 0) : xy;
+  pl.last_reg = ctx->opt.fft_xy == 1 ? (fft_last128_supported(ctx->d, prec == 1) ? 1 : 0) : last_reg;
   pl.ms[0] = mp;
   pl.ms[1] = my;
   pl.ms[2] = ml;
@@ -742,6 +791,7 @@ void fehom_default_options(fehom_options* opt) {
   opt->profile = 0;
   opt->autotune = 1;
   opt->x0_scaling = 1;
+  opt->fft_xy = -1;
 }
 
 const char* fehom_last_error(const fehom_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
@@ -845,14 +895,25 @@ fehom_status fehom_eig_bounds(fehom_ctx* ctx, double* lo_values, int64_t* lo_cou
   return FEHOM_OK;
 }
 
-fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int* tc_y, int* tc_last, double* ms) {
+fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int* tc_y, int* tc_last, double* ms,
+                            int* xy_fused) {
   if (!ctx) return FEHOM_E_INVALID;
   const auto& pl = ctx->plan[precision == FEHOM_MIXED ? 1 : 0];
+  if (xy_fused)
+    *xy_fused = (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.xy)) &&
+                fft_xy_supported(ctx->d, precision == FEHOM_MIXED);
   if (pairs) *pairs = pl.pairs;
   if (tc_y) *tc_y = pl.tc_y;
   if (tc_last) *tc_last = pl.tc_last;
   if (ms)
     for (int i = 0; i < 3; ++i) ms[i] = pl.ms[i];
+  return FEHOM_OK;
+}
+
+fehom_status fehom_effective_energy(const fehom_ctx* ctx, double* c_eff) {
+  if (!ctx || !c_eff) return FEHOM_E_INVALID;
+  if (ctx->c_eff_energy.empty()) return FEHOM_E_STATE;
+  std::memcpy(c_eff, ctx->c_eff_energy.data(), ctx->c_eff_energy.size() * sizeof(double));
   return FEHOM_OK;
 }
 
@@ -1295,11 +1356,79 @@ fehom_status fehom_mean_flux(fehom_ctx* ctx, const double* e, const double* u, d
 }
 
 // fields (mean removed), <sigma> and C_eff of a finished solve; flux: the mean fluxes of the final x
-static fehom_status finish_outputs(fehom_ctx* ctx, int n_loads, const double* loads, double* fluct_out,
-                                   int fluct_on_device, double* mean_flux_out, double* c_eff_out,
-                                   const std::vector<double>& flux) {
+// C = E^-1 B for the m x m row-major E (rows = loads) by Gaussian elimination with partial pivoting;
+// false when E is singular.
+static bool solve_loads(int m, std::vector<double> E, std::vector<double>& B) {
+  for (int col = 0; col < m; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < m; ++r)
+      if (std::fabs(E[r * m + col]) > std::fabs(E[piv * m + col])) piv = r;
+    if (std::fabs(E[piv * m + col]) < 1e-300) return false;
+    for (int k = 0; k < m; ++k) {
+      std::swap(E[col * m + k], E[piv * m + k]);
+      std::swap(B[col * m + k], B[piv * m + k]);
+    }
+    for (int r = 0; r < m; ++r) {
+      if (r == col) continue;
+      const double f = E[r * m + col] / E[col * m + col];
+      for (int k = 0; k < m; ++k) {
+        E[r * m + k] -= f * E[col * m + k];
+        B[r * m + k] -= f * B[col * m + k];
+      }
+    }
+  }
+  for (int r = 0; r < m; ++r)
+    for (int k = 0; k < m; ++k) B[r * m + k] /= E[r * m + r];
+  return true;
+}
+
+// Energy form of C_eff (m loads e_l, fields x_l, right-hand sides b_l, true residuals r_l): for any x,
+//   sum_q w_q (e_i + D x_i)^T C (e_j + D x_j) = |Y| e_i^T <C> e_j - x_j . b_i - x_i . r_j,
+// (b = -D^T W C e, r = b - K x), stationary at the solution, so its error is second order in the
+// solve error.  A = E C_eff E^T  ->  C_eff = E^-1 A E^-T.
+static fehom_status energy_c_eff(fehom_ctx* ctx, int m, const double* loads, const double* res) {
+  ctx->c_eff_energy.clear();
+  if (!res || m > 6) return FEHOM_OK;
   cudaStream_t s = ctx->stream;
   const long long cN = (long long)ctx->d.c * ctx->d.N;
+  TRY(ensure_partial(ctx, (size_t)m * 2 * m * 304 + 2 * m * m));
+  double* out = ctx->partial + (size_t)m * 2 * m * 304;
+  CK(launch_pair_dots(ctx->x64, ctx->b64, res, m, cN, ctx->partial, out, s));
+  count_launch(ctx, 2);
+  std::vector<double> dots(2 * m * m);
+  CK(cudaMemcpyAsync(dots.data(), out, sizeof(double) * dots.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> Cm(m * m, 0.0);
+  for (int p = 0; p < ctx->n_phases; ++p)
+    for (int k = 0; k < m * m; ++k) Cm[k] += ctx->frac[p] * ctx->moduli[(size_t)p * m * m + k];
+  std::vector<double> A(m * m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      double ece = 0.0;
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) ece += loads[i * m + a] * Cm[a * m + b] * loads[j * m + b];
+      // dots[(i m + j) 2 + 0] = x_i . b_j, [.. + 1] = x_i . r_j
+      A[i * m + j] = ece - (dots[(j * m + i) * 2] + dots[(i * m + j) * 2 + 1]) / ctx->vol;
+    }
+  for (int i = 0; i < m; ++i)
+    for (int j = i + 1; j < m; ++j) A[i * m + j] = A[j * m + i] = 0.5 * (A[i * m + j] + A[j * m + i]);
+  std::vector<double> E(loads, loads + m * m);
+  if (!solve_loads(m, E, A)) return FEHOM_OK;  // A <- E^-1 A
+  std::vector<double> T(m * m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) T[i * m + j] = A[j * m + i];
+  if (!solve_loads(m, E, T)) return FEHOM_OK;  // E^-1 (E^-1 A)^T = E^-1 A E^-T (A symmetric)
+  ctx->c_eff_energy = T;
+  return FEHOM_OK;
+}
+
+static fehom_status finish_outputs(fehom_ctx* ctx, int n_loads, const double* loads, double* fluct_out,
+                                   int fluct_on_device, double* mean_flux_out, double* c_eff_out,
+                                   const std::vector<double>& flux, const double* res) {
+  cudaStream_t s = ctx->stream;
+  const long long cN = (long long)ctx->d.c * ctx->d.N;
+  ctx->c_eff_energy.clear();
+  if (c_eff_out && n_loads == ctx->m) TRY(energy_c_eff(ctx, n_loads, loads, res));
   TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
   CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
   count_launch(ctx, 2);
@@ -1382,6 +1511,7 @@ struct SolveRun {
   int steps = 0;
   bool stats_current = false;
   bool finished = false;
+  const double* last_res = nullptr;  // buffer holding b - K x of the current x (FP64)
 
   fehom_status begin() {
     cudaStream_t s = ctx->stream;
@@ -1458,6 +1588,7 @@ struct SolveRun {
       TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->r64, &rn2, &flux));
       r64 = ctx->r64;
       stats_current = true;
+      last_res = ctx->r64;
     }
     if (steps == 0 && x0) {
       // normalisation <b, K_ref^+ b> from b itself
@@ -1510,6 +1641,7 @@ struct SolveRun {
     ++steps;
     if (!mixed) {
       TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->ap64, &rn2, &flux));  // true residual + averages
+      last_res = ctx->ap64;
       rel2.resize(n_loads);
       for (int l = 0; l < n_loads; ++l) rel2[l] = bn2[l] > 0 ? std::sqrt(rn2[l] / bn2[l]) : 0.0;
       finished = true;
@@ -1529,7 +1661,10 @@ struct SolveRun {
   }
 
   fehom_status finish_mixed() {
-    if (!stats_current) TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->ap64, &rn2, &flux));
+    if (!stats_current) {
+      TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->ap64, &rn2, &flux));
+      last_res = ctx->ap64;
+    }
     rel2.resize(n_loads);
     for (int l = 0; l < n_loads; ++l) {
       hs[l].iter = inner_it[l];
@@ -1543,7 +1678,7 @@ struct SolveRun {
   // outputs, info and status of the finished solve
   fehom_status report(double* fluct_out, int fluct_on_device, double* mean_flux_out, double* c_eff_out,
                       fehom_solve_info* info, float ms) {
-    TRY(finish_outputs(ctx, n_loads, loads, fluct_out, fluct_on_device, mean_flux_out, c_eff_out, flux));
+    TRY(finish_outputs(ctx, n_loads, loads, fluct_out, fluct_on_device, mean_flux_out, c_eff_out, flux, last_res));
     bool brk = false, notconv = false;
     for (int l = 0; l < n_loads; ++l) {
       if (hs[l].state == ST_BREAK) brk = true;

@@ -159,6 +159,8 @@ struct FftArgs {
   // launch plan (0 = built-in choice): x-line pairs per CTA (4, 8 or 16), columns per CTA of the y pass
   // and of the last-axis pass (2, 4, 8 or 16)
   int pairs, tc_y, tc_last;
+  int xy;        // 1: fused x-y passes (launch_fft_xy) in place of the separate x and y passes
+  int last_reg;  // 1: register-split last-axis pass (FP32 3-D, nz = 128, c = 1 or 3) with the block solve
 };
 
 template <typename T> cudaError_t launch_fft_x_fwd(const FftArgs& a, cudaStream_t s);
@@ -167,6 +169,12 @@ template <typename T> cudaError_t launch_fft_y(const FftArgs& a, int inverse, cu
 // last axis (z in 3-D, y in 2-D): forward FFT, z^ = K_hat^+ r^ / N, <r, z>, inverse FFT.
 // sym == nullptr: forward only (used by Algorithm 2).
 template <typename T> cudaError_t launch_fft_last_solve(const FftArgs& a, cudaStream_t s);
+// Fused x-y passes (one CTA per z-plane and component; FP32 3-D fields with 128 x 128 planes):
+// forward = x forward (with the FX_PCG update) + y forward; inverse = y inverse + x inverse (with the
+// FX_PCG / FX_PCG_INIT updates and the iteration bookkeeping).  cudaErrorInvalidValue when unsupported.
+template <typename T> cudaError_t launch_fft_xy(const FftArgs& a, int inverse, cudaStream_t s);
+bool fft_xy_supported(const Dims& d, bool fp32);
+bool fft_last128_supported(const Dims& d, bool fp32);
 
 // Algorithm 2 tail: spectra of the c impulse responses -> packed FP64 K_hat blocks, with the
 // largest |Im| and largest asymmetry recorded; then per-wavevector inverse.
@@ -197,6 +205,10 @@ cudaError_t launch_impulse_scatter(const double* py, const Dims& pd, const Dims&
 // removes the mean of every (component, load); partial: scratch of n_loads * c * 304 doubles (two launches)
 cudaError_t launch_sub_mean(double* x, int c, long long N, int n_loads, long long load_stride, double* partial,
                             cudaStream_t s);
+// out[(i L + j) 2 + k] = x_i . b_j (k = 0), x_i . r_j (k = 1) for i, j < L <= 6, slices of n doubles;
+// partial: scratch of L * 2 L * 304 doubles; out: 2 L^2 doubles (device).  Fixed summation order.
+cudaError_t launch_pair_dots(const double* x, const double* b, const double* r, int L, long long n, double* partial,
+                             double* out, cudaStream_t s);
 // x[l] *= gamma_l = <x[l], b[l]> / <x[l], kx[l]> (0 when <x[l], kx[l]> <= 0), l < n_loads, slices of n doubles;
 // partial: scratch of n_loads * 2 * 304 doubles (two launches, fixed summation order)
 cudaError_t launch_galerkin_scale(double* x, const double* kx, const double* b, int n_loads, long long n,

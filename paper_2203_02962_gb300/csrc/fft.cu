@@ -553,6 +553,424 @@ __global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, const
   }
 }
 
+
+// ------------------------------------------------------------------------------------------------
+// Fused x-y passes for FP32 fields with 128 x 128 planes (3-D): one CTA transforms one z-plane of one
+// component, so the half spectrum crosses HBM once per direction instead of twice.  Each 128-point
+// transform is split 128 = 16 x 8: a 16-point DFT in registers over the stride-8 subsequence, the
+// twiddles W_128^(j k1), one shared-memory exchange, then 8-point DFTs (output index k1 + 16 k2).
+//   forward: rows 2q, 2q+1 -> one complex line (fused r -= alpha Ap); the y pass splits the two half
+//            spectra on the fly; the real columns kx = 0 and kx = 64 share one complex column and are
+//            separated after the transform.
+//   inverse: columns kx = 0 and kx = 64 (whose inverse transforms are real) share one complex column;
+//            the x pass completes the Hermitian lines and applies the PCG updates of FX_PCG.
+// ------------------------------------------------------------------------------------------------
+constexpr int XY_N = 128, XY_H = 65, XY_THREADS = 512;
+constexpr int XY_LDQ = 148;  // line stride (complex) of the x-pass buffer: [k1][9] per line, padded
+constexpr int XY_LDT = 145;  // column stride of the y-pass buffer: [k1][9] per column, padded
+constexpr int XY_LDP = 66;   // row stride of the y-inverse result plane (64 columns used)
+constexpr int XY_BUF = 64 * XY_LDQ;
+constexpr size_t XY_SMEM = (XY_BUF + XY_N) * sizeof(float2);
+
+// 16-point DFT in registers, natural order in and out: n = n1 + 4 n2, k = 4 k1 + k2
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+  const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, r2 = 0.70710678118654752440f;
+  float2 y[4][4];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    y[n1][0] = v[n1];
+    y[n1][1] = v[n1 + 4];
+    y[n1][2] = v[n1 + 8];
+    y[n1][3] = v[n1 + 12];
+    dft4<float2, INV>(y[n1][0], y[n1][1], y[n1][2], y[n1][3]);
+  }
+  // y[n1][k2] *= W_16^(n1 k2) (forward); conjugate for the inverse
+  const float sg = INV ? 1.0f : -1.0f;
+  y[1][1] = cmul(y[1][1], mk<float2>(c1, sg * s1));
+  y[1][2] = cmul(y[1][2], mk<float2>(r2, sg * r2));
+  y[1][3] = cmul(y[1][3], mk<float2>(s1, sg * c1));
+  y[2][1] = cmul(y[2][1], mk<float2>(r2, sg * r2));
+  y[2][2] = rot<float2, INV>(y[2][2]);
+  y[2][3] = cmul(y[2][3], mk<float2>(-r2, sg * r2));
+  y[3][1] = cmul(y[3][1], mk<float2>(s1, sg * c1));
+  y[3][2] = cmul(y[3][2], mk<float2>(-r2, sg * r2));
+  y[3][3] = cmul(y[3][3], mk<float2>(-c1, -sg * s1));
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) {
+    float2 a0 = y[0][k2], a1 = y[1][k2], a2 = y[2][k2], a3 = y[3][k2];
+    dft4<float2, INV>(a0, a1, a2, a3);
+    v[k2] = a0;
+    v[4 + k2] = a1;
+    v[8 + k2] = a2;
+    v[12 + k2] = a3;
+  }
+}
+
+template <bool UPDATE>
+__global__ void __launch_bounds__(XY_THREADS, 2) fft_xy_fwd128_kernel(FftArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* S = reinterpret_cast<float2*>(smem_raw);
+  float2* Cz = S + XY_BUF;
+  const int z = blockIdx.x, comp = blockIdx.y, load = blockIdx.z;
+  if (UPDATE && !first_half_active(a.st, load)) return;
+  const long long foff = (long long)load * a.load_stride_f + (long long)comp * a.d.N + (long long)z * XY_N * XY_N;
+  float* r = reinterpret_cast<float*>(a.f0) + foff;
+  const float* ap = UPDATE ? reinterpret_cast<const float*>(a.f1) + foff : nullptr;
+  float2* spec = reinterpret_cast<float2*>(a.spec) + (long long)load * a.load_stride_s + (long long)comp * a.d.Nh +
+                 (long long)z * XY_N * XY_H;
+  const float alpha = UPDATE ? float(a.st[load].alpha) : 0.0f;
+  const float2* twx = reinterpret_cast<const float2*>(a.tw.x);
+  const float2* twy = reinterpret_cast<const float2*>(a.tw.y);
+  const int t = threadIdx.x;
+  {  // x, stage 1: line q = rows (2q, 2q+1), subsequence j
+    const int q = t >> 3, j = t & 7;
+    float* r0 = r + 2 * q * XY_N;
+    float* r1 = r0 + XY_N;
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int x = j + 8 * m;
+      float v0 = r0[x], v1 = r1[x];
+      if (UPDATE) {
+        v0 = fmaf(-alpha, ap[2 * q * XY_N + x], v0);
+        v1 = fmaf(-alpha, ap[(2 * q + 1) * XY_N + x], v1);
+        r0[x] = v0;
+        r1[x] = v1;
+      }
+      v[m] = make_float2(v0, v1);
+    }
+    dft16<false>(v);
+    float2* Sq = S + q * XY_LDQ;
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) Sq[k1 * 9 + j] = k1 == 0 ? v[0] : cmul(v[k1], __ldg(twx + j * k1));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int round = 0; round < 2; ++round) {  // x, stage 2: a warp holds both lines it rewrites
+    const int task = t + XY_THREADS * round;
+    const int q = task >> 4, k1 = task & 15;
+    float2* Sq = S + q * XY_LDQ;
+    float2 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = Sq[k1 * 9 + j];
+    __syncwarp();
+    Dft<float2, 8, false>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) Sq[k1 + 16 * k2] = v[k2];
+    __syncwarp();
+  }
+  __syncthreads();
+  {  // y, stage 1: column kx (kx = 0 carries kx = 0 and kx = 64), subsequence j of the rows
+    const int kx = t & 63, j = t >> 6;
+    const int sodd = j & 1, q0 = j >> 1;
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const float2* Sq = S + (q0 + 4 * m) * XY_LDQ;
+      if (kx == 0) {
+        const float2 z0 = Sq[0], z64 = Sq[64];
+        v[m] = sodd ? make_float2(z0.y, z64.y) : make_float2(z0.x, z64.x);
+      } else {
+        const float2 zk = Sq[kx], zn = Sq[XY_N - kx];
+        v[m] = sodd ? make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x))
+                    : make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+      }
+    }
+    __syncthreads();  // every line has been read before the column buffer overwrites it
+    dft16<false>(v);
+    float2* Tc = S + kx * XY_LDT;
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) Tc[k1 * 9 + j] = k1 == 0 ? v[0] : cmul(v[k1], __ldg(twy + j * k1));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int round = 0; round < 2; ++round) {  // y, stage 2 -> half spectrum (packed column to Cz)
+    const int task = t + XY_THREADS * round;
+    const int kx = task & 63, k1 = task >> 6;
+    const float2* Tc = S + kx * XY_LDT;
+    float2 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = Tc[k1 * 9 + j];
+    Dft<float2, 8, false>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+      const int ky = k1 + 16 * k2;
+      if (kx == 0) Cz[ky] = v[k2];
+      else spec[ky * XY_H + kx] = v[k2];
+    }
+  }
+  __syncthreads();
+  if (t < XY_N) {  // separate the spectra of the real columns kx = 0 and kx = 64
+    const float2 c = Cz[t], cn = Cz[(XY_N - t) & (XY_N - 1)];
+    spec[t * XY_H] = make_float2(0.5f * (c.x + cn.x), 0.5f * (c.y - cn.y));
+    spec[t * XY_H + 64] = make_float2(0.5f * (c.y + cn.y), 0.5f * (cn.x - c.x));
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(XY_THREADS, 2) fft_xy_inv128_kernel(FftArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_sh[32];
+  float2* S = reinterpret_cast<float2*>(smem_raw);
+  const int z = blockIdx.x, comp = blockIdx.y, load = blockIdx.z;
+  if (MODE != FX_PLAIN && !second_half_active(a.st, load)) return;
+  const long long foff = (long long)load * a.load_stride_f + (long long)comp * a.d.N + (long long)z * XY_N * XY_N;
+  const float2* spec = reinterpret_cast<const float2*>(a.spec) + (long long)load * a.load_stride_s +
+                       (long long)comp * a.d.Nh + (long long)z * XY_N * XY_H;
+  const float2* twx = reinterpret_cast<const float2*>(a.tw.x);
+  const float2* twy = reinterpret_cast<const float2*>(a.tw.y);
+  const int t = threadIdx.x;
+  {  // y inverse, stage 1: column kx (kx = 0 carries kx = 0 and kx = 64 as real and imaginary parts)
+    const int kx = t & 63, j = t >> 6;
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int ky = j + 8 * m;
+      if (kx == 0) {
+        const float2 s0 = spec[ky * XY_H], s64 = spec[ky * XY_H + 64];
+        v[m] = make_float2(s0.x - s64.y, s0.y + s64.x);
+      } else {
+        v[m] = spec[ky * XY_H + kx];
+      }
+    }
+    dft16<true>(v);
+    float2* Tc = S + kx * XY_LDT;
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) Tc[k1 * 9 + j] = k1 == 0 ? v[0] : cmulc(v[k1], __ldg(twy + j * k1));
+  }
+  __syncthreads();
+  {  // y inverse, stage 2 -> plane P[y][kx]
+    float2 w[2][8];
+#pragma unroll
+    for (int round = 0; round < 2; ++round) {
+      const int task = t + XY_THREADS * round;
+      const int kx = task & 63, k1 = task >> 6;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[round][j] = S[kx * XY_LDT + k1 * 9 + j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int round = 0; round < 2; ++round) {
+      const int task = t + XY_THREADS * round;
+      const int kx = task & 63, k1 = task >> 6;
+      Dft<float2, 8, true>::run(w[round]);
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) S[(k1 + 16 * k2) * XY_LDP + kx] = w[round][k2];
+    }
+  }
+  __syncthreads();
+  {  // x inverse, stage 1: line q = rows (2q, 2q+1), Hermitian completion, Z = A + i B
+    const int q = t >> 3, j = t & 7;
+    const float2* PA = S + 2 * q * XY_LDP;
+    const float2* PB = PA + XY_LDP;
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int k = j + 8 * m;
+      float2 A, B;
+      if (k == 0) {
+        A = make_float2(PA[0].x, 0.0f);
+        B = make_float2(PB[0].x, 0.0f);
+      } else if (k == 64) {
+        A = make_float2(PA[0].y, 0.0f);
+        B = make_float2(PB[0].y, 0.0f);
+      } else if (k < 64) {
+        A = PA[k];
+        B = PB[k];
+      } else {
+        A = PA[XY_N - k];
+        B = PB[XY_N - k];
+        A.y = -A.y;
+        B.y = -B.y;
+      }
+      v[m] = make_float2(A.x - B.y, A.y + B.x);
+    }
+    __syncthreads();  // the plane has been read before the line buffer overwrites it
+    dft16<true>(v);
+    float2* Sq = S + q * XY_LDQ;
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) Sq[k1 * 9 + j] = k1 == 0 ? v[0] : cmulc(v[k1], __ldg(twx + j * k1));
+  }
+  __syncthreads();
+  float* f0 = reinterpret_cast<float*>(a.f0) + foff;
+  float* f2 = (MODE != FX_PLAIN) ? reinterpret_cast<float*>(a.f2) + foff : nullptr;
+  const float alpha = (MODE == FX_PCG) ? float(a.st[load].alpha) : 0.0f;
+  const float beta = (MODE == FX_PCG) ? float(a.st[load].beta) : 0.0f;
+#pragma unroll
+  for (int round = 0; round < 2; ++round) {  // x inverse, stage 2, and the fused field updates
+    const int task = t + XY_THREADS * round;
+    const int q = task >> 4, k1 = task & 15;
+    const float2* Sq = S + q * XY_LDQ;
+    float2 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = Sq[k1 * 9 + j];
+    Dft<float2, 8, true>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+      const int x = k1 + 16 * k2;
+      const long long g0 = 2LL * q * XY_N + x, g1 = g0 + XY_N;
+      if (MODE == FX_PLAIN) {
+        f0[g0] = v[k2].x;
+        f0[g1] = v[k2].y;
+      } else if (MODE == FX_PCG_INIT) {
+        f2[g0] = v[k2].x;
+        f2[g1] = v[k2].y;
+      } else {
+        const float p0 = f2[g0], p1 = f2[g1];
+        f0[g0] = fmaf(alpha, p0, f0[g0]);
+        f0[g1] = fmaf(alpha, p1, f0[g1]);
+        f2[g0] = fmaf(beta, p0, v[k2].x);
+        f2[g1] = fmaf(beta, p1, v[k2].y);
+      }
+    }
+  }
+  if (MODE != FX_PLAIN && a.st != nullptr) {
+    // the last CTA over all planes and components finalises the iteration bookkeeping
+    const int nblk = gridDim.x * gridDim.y;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    double total;
+    __syncthreads();
+    if (finish_reduction(0.0, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load, nblk, bid,
+                         red_sh, &total)) {
+      if (threadIdx.x == 0) {
+        PcgState& st = a.st[load];
+        if (MODE == FX_PCG) st.iter += 1;
+        if (st.state == ST_CONV) st.state = ST_DONE;
+        else if (st.state == ST_FIN_MAX) st.state = ST_MAXIT;
+      }
+    }
+  }
+}
+
+
+// Last axis (z) of FP32 3-D fields with nz = 128, 16 columns x NC components per CTA, with the block
+// solve: the same 16 x 8 split as the fused x-y passes.  Stage 1: 16-point DFTs of the stride-8 z
+// subsequences read straight from the spectrum; stage 2 (one thread per column and k1): 8-point DFTs
+// giving the NC components at kz = k1 + 16 k2, the block solve and the Parseval sum in registers, and
+// the first half of the inverse (8-point inverse DFTs, conjugate twiddles); stage 3: 16-point inverse
+// DFTs written straight back.  Shared memory is touched twice per direction instead of once per
+// radix stage.
+template <int NC>
+__global__ void __launch_bounds__(128 * NC, NC == 3 ? 2 : 4) fft_last128_kernel(FftArgs a) {
+  constexpr int TCL = 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_sh[32];
+  float2* S = reinterpret_cast<float2*>(smem_raw);  // NC * 16 * 8 * 16 complex
+  const int load = blockIdx.z;
+  if (!first_half_active(a.st, load)) return;
+  float2* spec = reinterpret_cast<float2*>(a.spec) + (long long)load * a.load_stride_s;
+  const long long Nh = a.d.Nh;
+  const long long es = (long long)a.d.ny * a.d.nxh;
+  const int ncols = a.d.ny * a.d.nxh;
+  const int nxh = a.d.nxh, half = a.d.nx / 2;
+  const int cf0 = blockIdx.x * TCL;
+  const float2* tw = reinterpret_cast<const float2*>(a.tw.z);
+  const float* sym = reinterpret_cast<const float*>(a.sym);
+  const int tid = threadIdx.x;
+  {  // stage 1: task (column t, subsequence j, component c)
+    const int t = tid & 15, j = (tid >> 4) & 7, c = tid >> 7;
+    const int cf = cf0 + t;
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = cf < ncols ? spec[c * Nh + cf + (j + 8 * m) * es] : make_float2(0.f, 0.f);
+    dft16<false>(v);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1)
+      S[((c * 16 + k1) * 8 + j) * TCL + t] = k1 == 0 ? v[0] : cmul(v[k1], __ldg(tw + j * k1));
+  }
+  __syncthreads();
+  DotAcc<float> dot;
+  const bool active = tid < 256;
+  const int t = tid & 15, k1 = (tid >> 4) & 15;
+  const int cf = cf0 + t;
+  float2 zr[NC][8];
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) zr[c][j] = S[((c * 16 + k1) * 8 + j) * TCL + t];
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) Dft<float2, 8, false>::run(zr[c]);
+    const int kx = cf % nxh;
+    const float wgt = (kx == 0 || kx == half) ? 1.0f : 2.0f;
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+      if (cf >= ncols) break;
+      const long long ti = cf + (long long)(k1 + 16 * k2) * es;
+      float2 r[NC], z[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) r[c] = zr[c][k2];
+      if constexpr (NC == 1) {
+        const float k00 = sym[ti];
+        z[0] = make_float2(k00 * r[0].x, k00 * r[0].y);
+      } else {
+        const float k00 = sym[ti], k11 = sym[Nh + ti], k22 = sym[2 * Nh + ti];
+        const float k12 = sym[3 * Nh + ti], k02 = sym[4 * Nh + ti], k01 = sym[5 * Nh + ti];
+        z[0] = make_float2(fmaf(k00, r[0].x, fmaf(k01, r[1].x, k02 * r[2].x)), fmaf(k00, r[0].y, fmaf(k01, r[1].y, k02 * r[2].y)));
+        z[1] = make_float2(fmaf(k01, r[0].x, fmaf(k11, r[1].x, k12 * r[2].x)), fmaf(k01, r[0].y, fmaf(k11, r[1].y, k12 * r[2].y)));
+        z[2] = make_float2(fmaf(k02, r[0].x, fmaf(k12, r[1].x, k22 * r[2].x)), fmaf(k02, r[0].y, fmaf(k12, r[1].y, k22 * r[2].y)));
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        dot.add(wgt * r[c].x, z[c].x);  // wgt in {1, 2}: exact
+        dot.add(wgt * r[c].y, z[c].y);
+        zr[c][k2] = z[c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      Dft<float2, 8, true>::run(zr[c]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        S[((c * 8 + j) * 16 + k1) * TCL + t] = j == 0 ? zr[c][0] : cmulc(zr[c][j], __ldg(tw + j * k1));
+    }
+  }
+  __syncthreads();
+  {  // stage 3: task (column t, subsequence j, component c): 16-point inverse DFT over k1
+    const int tt = tid & 15, j = (tid >> 4) & 7, c = tid >> 7;
+    const int cff = cf0 + tt;
+    float2 v[16];
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) v[kk] = S[((c * 8 + j) * 16 + kk) * TCL + tt];
+    dft16<true>(v);
+    if (cff < ncols) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) spec[c * Nh + cff + (j + 8 * m) * es] = v[m];
+    }
+  }
+  if (a.st != nullptr) {
+    const double part = block_sum(dot.value(), red_sh);
+    double total;
+    if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load, gridDim.x,
+                         blockIdx.x, red_sh, &total)) {
+      if (threadIdx.x == 0) {
+        PcgState& st = a.st[load];
+        if (a.init) {
+          st.rz = total;
+          st.rz_init = total;
+          if (st.bnorm2 < 0.0) st.bnorm2 = total;  // zero initial guess: <b, K_ref^+ b> = <r0, z0>
+          st.tol2 = st.tol2_rel * st.bnorm2;
+          st.alpha = 0.0;
+          st.beta = 0.0;
+          if (!isfinite(total)) st.state = ST_BREAK;
+          else if (total <= st.tol2) st.state = ST_CONV;
+        } else {
+          st.beta = (st.rz > 0.0) ? total / st.rz : 0.0;
+          if (a.red.hist != nullptr && st.iter < kHist) a.red.hist[((long long)load * 2 + 1) * kHist + st.iter] = st.beta;
+          st.rz = total;
+          if (!isfinite(total)) st.state = ST_BREAK;
+          else if (total <= st.tol2) st.state = ST_CONV;
+          else if (st.iter + 1 >= st.max_iter) st.state = ST_FIN_MAX;
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Algorithm 2 tail: packed symbol, checks and per-wavevector inverse
 // ------------------------------------------------------------------------------------------------
@@ -769,12 +1187,44 @@ static cudaError_t launch_last_nc(const FftArgs& a, cudaStream_t s) {
                : launch_last_tc<T, NC, false>(a, m, TC, grid, smem, tw, s);
 }
 
+bool fft_last128_supported(const Dims& d, bool fp32) {
+  return fp32 && d.dim == 3 && d.nz == 128 && (d.c == 1 || d.c == 3) && (d.ny * d.nxh) % 16 == 0;
+}
+
 template <typename T>
 cudaError_t launch_fft_last_solve(const FftArgs& a, cudaStream_t s) {
+  if (sizeof(T) == 4 && a.last_reg && a.sym && fft_last128_supported(a.d, true)) {
+    const dim3 grid((a.d.ny * a.d.nxh) / 16, 1, a.n_loads);
+    if (a.st != nullptr && (long long)grid.x > a.red.max_blocks) return cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)a.d.c * 16 * 8 * 16 * sizeof(float2);
+    if (a.d.c == 1) return launch_with_smem(fft_last128_kernel<1>, grid, 128, smem, s, a);
+    return launch_with_smem(fft_last128_kernel<3>, grid, 384, smem, s, a);
+  }
   if (a.d.c == 1) return launch_last_nc<T, 1>(a, s);
   if (a.d.c == 2) return launch_last_nc<T, 2>(a, s);
   if (a.d.c == 3) return launch_last_nc<T, 3>(a, s);
   return cudaErrorInvalidValue;
+}
+
+template <>
+cudaError_t launch_fft_xy<float>(const FftArgs& a, int inverse, cudaStream_t s) {
+  if (!fft_xy_supported(a.d, true)) return cudaErrorInvalidValue;
+  const dim3 grid(a.d.nz, a.d.c, a.n_loads);
+  if (!inverse && a.mode == FX_PCG) return launch_with_smem(fft_xy_fwd128_kernel<true>, grid, XY_THREADS, XY_SMEM, s, a);
+  if (!inverse) return launch_with_smem(fft_xy_fwd128_kernel<false>, grid, XY_THREADS, XY_SMEM, s, a);
+  if (a.st != nullptr && (long long)grid.x * grid.y > a.red.max_blocks) return cudaErrorInvalidConfiguration;
+  if (a.mode == FX_PCG) return launch_with_smem(fft_xy_inv128_kernel<FX_PCG>, grid, XY_THREADS, XY_SMEM, s, a);
+  if (a.mode == FX_PCG_INIT) return launch_with_smem(fft_xy_inv128_kernel<FX_PCG_INIT>, grid, XY_THREADS, XY_SMEM, s, a);
+  return launch_with_smem(fft_xy_inv128_kernel<FX_PLAIN>, grid, XY_THREADS, XY_SMEM, s, a);
+}
+
+template <>
+cudaError_t launch_fft_xy<double>(const FftArgs&, int, cudaStream_t) {
+  return cudaErrorInvalidValue;
+}
+
+bool fft_xy_supported(const Dims& d, bool fp32) {
+  return fp32 && d.dim == 3 && d.nx == 128 && d.ny == 128 && d.nxh == 65;
 }
 
 template cudaError_t launch_fft_x_fwd<double>(const FftArgs&, cudaStream_t);

@@ -3,10 +3,11 @@
 // The 3x3x3 convolutions are implicit GEMMs on the tcgen05 tensor cores (BF16 operands, FP32
 // accumulators in tensor memory):
 //   * conv3_tc_kernel (forward, and input gradient through flipped/transposed weights): one CTA
-//     computes a 1 x 16 x 8 (z, y, x) output tile = the M = 128 rows of the MMA, N = up to 64 output
-//     channels.  Per 16-channel slice of the input it stages the periodic halo tile (3 x 18 x 10
-//     voxels) once in shared memory in the no-swizzle K-major core-matrix layout; each of the 27
-//     taps is then the same tile read through a shifted matrix descriptor (the 8 x-voxels of a core
+//     computes ZT (1, 2 or 4) output planes of a 16 x 8 (y, x) tile; each plane is the M = 128 rows
+//     of its own MMAs and accumulator, N = up to 64 output channels.  Per 16-channel slice of the
+//     input it stages the periodic halo ((ZT + 2) x 18 x 10 voxels) and the slice's weights once in
+//     shared memory in the no-swizzle K-major core-matrix layout; each of the 27 taps of each plane
+//     is then the same halo read through a shifted matrix descriptor (the 8 x-voxels of a core
 //     matrix row are contiguous in the halo), so the taps cost no data movement.
 //   * wgrad_tc_kernel (weight gradient): M = 128 rows = output channels (zero-padded), N = 16 input
 //     channels, K = voxels of a tile; three x-shifted copies of the halo keep every tap a shifted
@@ -158,29 +159,34 @@ struct ConvArgs {
   int* err;
 };
 
-constexpr int kHaloVox = 3 * 18 * 10;            // z-1..z+1, y0-1..y0+16, x0-1..x0+8
-constexpr int kConvA = 2 * kHaloVox * 16;        // two 8-channel halves, 16 B per voxel and half
-template <int NT>
-__host__ __device__ constexpr int conv_stage_bytes() { return kConvA + 27 * NT * 32; }
-// The allocation is padded so that every address a descriptor of this kernel can form, under either
-// assignment of its two byte offsets to the M/N and K directions, lies inside the CTA's shared memory.
-constexpr int kConvSmemFloor = 212 * 1024;
-template <int NT>
-__host__ __device__ constexpr int conv_smem_bytes() {
-  return 2 * conv_stage_bytes<NT>() + 32 > kConvSmemFloor ? 2 * conv_stage_bytes<NT>() + 32 : kConvSmemFloor;
+constexpr int kHaloVox = 3 * 18 * 10;            // z-1..z+1, y0-1..y0+16, x0-1..x0+8 (one output plane)
+constexpr int kPlaneVox = 18 * 10;
+template <int ZT>
+__host__ __device__ constexpr int conv_halo_vox() { return (ZT + 2) * kPlaneVox; }
+template <int NT, int ZT>
+__host__ __device__ constexpr int conv_stage_bytes() { return 2 * conv_halo_vox<ZT>() * 16 + 27 * NT * 32; }
+template <int NT, int ZT>
+__host__ __device__ constexpr int conv_smem_bytes() { return 2 * conv_stage_bytes<NT, ZT>() + 32; }
+template <int NT, int ZT>
+__host__ __device__ constexpr uint32_t conv_tmem_cols() {
+  return NT * ZT <= 32 ? 32 : NT * ZT <= 64 ? 64 : NT * ZT <= 128 ? 128 : 256;
 }
 
-template <int NT>
+// One CTA: ZT consecutive output planes of a 16 x 8 (y, x) tile, NT output channels.  The weights of
+// a 16-channel input slice are staged once and serve all ZT planes (ZT accumulators in TMEM).
+template <int NT, int ZT>
 __global__ void __launch_bounds__(128, 1) conv3_tc_kernel(ConvArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  constexpr int STAGE = conv_stage_bytes<NT>();
-  constexpr uint32_t NCOLS = NT < 32 ? 32 : NT;
+  constexpr int HV = conv_halo_vox<ZT>();
+  constexpr int ABYTES = 2 * HV * 16;
+  constexpr int STAGE = conv_stage_bytes<NT, ZT>();
+  constexpr uint32_t NCOLS = conv_tmem_cols<NT, ZT>();
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + 2 * STAGE + 16);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int tiles_x = (a.W + 7) >> 3;
   const int x0 = (blockIdx.x % tiles_x) * 8, y0 = (blockIdx.x / tiles_x) * 16;
-  const int z = blockIdx.y;
+  const int z0 = blockIdx.y * ZT;
   const int ntn = a.Cout / NT;
   const int b = blockIdx.z / ntn, n0 = (blockIdx.z % ntn) * NT;
   const long long V = static_cast<long long>(a.D) * a.H * a.W;
@@ -202,14 +208,14 @@ __global__ void __launch_bounds__(128, 1) conv3_tc_kernel(ConvArgs a) {
   const bf16* xb = a.x + b * V * a.Cin;
   auto load_stage = [&](int kc, int s) {
     uint8_t* As = smem + s * STAGE;
-    uint8_t* Bs = As + kConvA;
-    for (int idx = tid; idx < 2 * kHaloVox; idx += 128) {
-      const int half = idx >= kHaloVox ? 1 : 0, h = idx - half * kHaloVox;
-      const int zz = h / 180, ry = (h % 180) / 10, rx = h % 10;
-      const int zi = wrapi(z + zz - 1, a.D), yi = wrapi(y0 + ry - 1, a.H), xi = wrapi(x0 + rx - 1, a.W);
+    uint8_t* Bs = As + ABYTES;
+    for (int idx = tid; idx < 2 * HV; idx += 128) {
+      const int half = idx >= HV ? 1 : 0, h = idx - half * HV;
+      const int zz = h / kPlaneVox, ry = (h % kPlaneVox) / 10, rx = h % 10;
+      const int zi = wrapi(z0 + zz - 1, a.D), yi = wrapi(y0 + ry - 1, a.H), xi = wrapi(x0 + rx - 1, a.W);
       const uint4 v = *reinterpret_cast<const uint4*>(
           xb + ((static_cast<long long>(zi) * a.H + yi) * a.W + xi) * a.Cin + kc * 16 + half * 8);
-      *reinterpret_cast<uint4*>(As + half * (kHaloVox * 16) + h * 16) = v;
+      *reinterpret_cast<uint4*>(As + half * (HV * 16) + h * 16) = v;
     }
     for (int idx = tid; idx < 27 * NT * 2; idx += 128) {
       const int half = idx & 1, co = (idx >> 1) % NT, tap = (idx >> 1) / NT;
@@ -220,15 +226,18 @@ __global__ void __launch_bounds__(128, 1) conv3_tc_kernel(ConvArgs a) {
   };
   const uint32_t idesc = idesc_bf16(128, NT);
   auto issue = [&](int kc, int s) {
-    const uint32_t As = smem_u32(smem + s * STAGE), Bs = As + kConvA;
+    const uint32_t As = smem_u32(smem + s * STAGE), Bs = As + ABYTES;
     tc_fence_after();
     for (int t = 0; t < 27; ++t) {
       const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;  // offsets + 1
-      // A: rows = 16 output lines (SBO = one halo row, 10 voxels), K halves 8 channels apart (LBO)
-      const uint64_t ad = smem_desc(As + (dz * 180 + dy * 10 + dx) * 16, kHaloVox * 16, 160);
       // B: rows = output channels (SBO 128 B per 8 rows), K halves NT * 16 bytes apart
       const uint64_t bd = smem_desc(Bs + t * (NT * 32), NT * 16, 128);
-      mma_bf16(tmem, ad, bd, idesc, (kc > 0 || t > 0) ? 1u : 0u);
+#pragma unroll
+      for (int zz = 0; zz < ZT; ++zz) {
+        // A: rows = 16 output lines of plane zz (SBO = one halo row, 10 voxels), K halves HV voxels apart
+        const uint64_t ad = smem_desc(As + ((zz + dz) * kPlaneVox + dy * 10 + dx) * 16, HV * 16, 160);
+        mma_bf16(tmem + zz * NT, ad, bd, idesc, (kc > 0 || t > 0) ? 1u : 0u);
+      }
     }
     mma_commit(&bar[s]);
   };
@@ -257,40 +266,43 @@ __global__ void __launch_bounds__(128, 1) conv3_tc_kernel(ConvArgs a) {
     const int ty = tid >> 3, tx = tid & 7;
     const int yy = y0 + ty, xx = x0 + tx;
     const bool valid = yy < a.H && xx < a.W;
-    const long long vox = b * V + (static_cast<long long>(z) * a.H + (valid ? yy : 0)) * a.W + (valid ? xx : 0);
-    for (int c0 = 0; c0 < NT; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
-      if (!valid) continue;
-      const int n = n0 + c0;
-      if (a.bias) {
+    for (int zz = 0; zz < ZT; ++zz) {
+      const long long vox =
+          b * V + (static_cast<long long>(z0 + zz) * a.H + (valid ? yy : 0)) * a.W + (valid ? xx : 0);
+      for (int c0 = 0; c0 < NT; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + zz * NT + c0, v);
+        if (!valid) continue;
+        const int n = n0 + c0;
+        if (a.bias) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] += a.bias[n + j];
-      }
-      if (a.relu) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.0f);
-      }
-      if (a.mask) {
-        const uint4* mp = reinterpret_cast<const uint4*>(a.mask + vox * a.Cout + n);
-        for (int h = 0; h < 2; ++h) {
-          float mk[8];
-          unpack8(mp[h], mk);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) v[8 * h + j] = mk[j] > 0.0f ? v[8 * h + j] : 0.0f;
+          for (int j = 0; j < 16; ++j) v[j] += a.bias[n + j];
         }
-      }
-      if (a.y32) {
-        float4* yp = reinterpret_cast<float4*>(a.y32 + vox * a.Cout + n);
+        if (a.relu) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) yp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      } else {
-        uint4* yp = reinterpret_cast<uint4*>(a.y + vox * a.Cout + n);
-        for (int h = 0; h < 2; ++h) {
-          float f[8];
+          for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.0f);
+        }
+        if (a.mask) {
+          const uint4* mp = reinterpret_cast<const uint4*>(a.mask + vox * a.Cout + n);
+          for (int h = 0; h < 2; ++h) {
+            float mk[8];
+            unpack8(mp[h], mk);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) f[j] = v[8 * h + j];
-          yp[h] = pack8(f);
+            for (int j = 0; j < 8; ++j) v[8 * h + j] = mk[j] > 0.0f ? v[8 * h + j] : 0.0f;
+          }
+        }
+        if (a.y32) {
+          float4* yp = reinterpret_cast<float4*>(a.y32 + vox * a.Cout + n);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) yp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+          uint4* yp = reinterpret_cast<uint4*>(a.y + vox * a.Cout + n);
+          for (int h = 0; h < 2; ++h) {
+            float f[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) f[j] = v[8 * h + j];
+            yp[h] = pack8(f);
+          }
         }
       }
     }
@@ -818,23 +830,31 @@ __global__ void prep_weights_kernel(const float* __restrict__ w, bf16* __restric
 // ------------------------------------------------------------------------------------------------
 int blocks_for(long long n, int bs) { return static_cast<int>(std::max<long long>(1, (n + bs - 1) / bs)); }
 
-template <int NT>
+template <int NT, int ZT>
 cudaError_t launch_conv_nt(const ConvArgs& a, int B, cudaStream_t s) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(conv3_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem_bytes<NT>());
+    attr = cudaFuncSetAttribute(conv3_tc_kernel<NT, ZT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                conv_smem_bytes<NT, ZT>());
   });
   if (attr != cudaSuccess) return attr;
-  const dim3 grid(((a.W + 7) / 8) * ((a.H + 15) / 16), a.D, B * (a.Cout / NT));
-  conv3_tc_kernel<NT><<<grid, 128, conv_smem_bytes<NT>(), s>>>(a);
+  const dim3 grid(((a.W + 7) / 8) * ((a.H + 15) / 16), a.D / ZT, B * (a.Cout / NT));
+  conv3_tc_kernel<NT, ZT><<<grid, 128, conv_smem_bytes<NT, ZT>(), s>>>(a);
   return cudaGetLastError();
 }
 
+template <int NT>
+cudaError_t launch_conv_z(const ConvArgs& a, int B, cudaStream_t s) {
+  if (a.D % 4 == 0) return launch_conv_nt<NT, 4>(a, B, s);
+  if (a.D % 2 == 0) return launch_conv_nt<NT, 2>(a, B, s);
+  return launch_conv_nt<NT, 1>(a, B, s);
+}
+
 cudaError_t launch_conv(const ConvArgs& a, int B, cudaStream_t s) {
-  if (a.Cout % 64 == 0) return launch_conv_nt<64>(a, B, s);
-  if (a.Cout % 32 == 0) return launch_conv_nt<32>(a, B, s);
-  return launch_conv_nt<16>(a, B, s);
+  if (a.Cout % 64 == 0) return launch_conv_z<64>(a, B, s);
+  if (a.Cout % 32 == 0) return launch_conv_z<32>(a, B, s);
+  return launch_conv_z<16>(a, B, s);
 }
 
 struct WgradPlan {

@@ -93,6 +93,41 @@ __global__ void galerkin_scale_kernel(double* __restrict__ x, long long n, const
   for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) p[i] *= gamma;
 }
 
+// Energy-form effective tensor: for loads i, j < L <= 6, dots x_i . b_j and x_i . r_j over n entries.
+// partial[((i * G + blk) * L + j) * 2 + k]; then out[(i * L + j) * 2 + k] sums the G partials in order.
+constexpr int kPairMax = 6;
+__global__ void pair_dots_kernel(const double* __restrict__ x, const double* __restrict__ b,
+                                 const double* __restrict__ r, int L, long long n, double* partial) {
+  const int i = blockIdx.y;
+  const double* xi = x + (long long)i * n;
+  double acc[2 * kPairMax];
+#pragma unroll
+  for (int q = 0; q < 2 * kPairMax; ++q) acc[q] = 0.0;
+  for (long long k = blockIdx.x * (long long)VT + threadIdx.x; k < n; k += (long long)gridDim.x * VT) {
+    const double xv = xi[k];
+#pragma unroll
+    for (int j = 0; j < kPairMax; ++j) {
+      if (j < L) {
+        acc[2 * j] = fma(xv, b[(long long)j * n + k], acc[2 * j]);
+        acc[2 * j + 1] = fma(xv, r[(long long)j * n + k], acc[2 * j + 1]);
+      }
+    }
+  }
+  for (int q = 0; q < 2 * L; ++q) {
+    const double t = block_sum(acc[q]);
+    if (threadIdx.x == 0) partial[((long long)i * gridDim.x + blockIdx.x) * 2 * L + q] = t;
+  }
+}
+
+__global__ void pair_dots_final_kernel(const double* __restrict__ partial, int L, int G, double* out) {
+  const int q = threadIdx.x;  // (i, j, k) flattened, 2 L L entries
+  if (q >= 2 * L * L) return;
+  const int i = q / (2 * L), jk = q % (2 * L);
+  double s = 0.0;
+  for (int g = 0; g < G; ++g) s += partial[((long long)i * G + g) * 2 * L + jk];
+  out[q] = s;
+}
+
 __global__ void impulse_scatter_kernel(const double* __restrict__ py, Dims pd, Dims full, int c, double* out) {
   const int nb = full.dim == 3 ? 27 : 9;
   const int t = threadIdx.x;
@@ -120,6 +155,16 @@ cudaError_t launch_cast_d2f(const double* x, float* y, double scale, long long n
 
 cudaError_t launch_add_f2d(const float* x, double* y, double scale, long long n, cudaStream_t s) {
   add_f2d_kernel<<<grid_for(n), VT, 0, s>>>(x, y, scale, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_dots(const double* x, const double* b, const double* r, int L, long long n, double* partial,
+                             double* out, cudaStream_t s) {
+  if (L < 1 || L > kPairMax) return cudaErrorInvalidValue;
+  pair_dots_kernel<<<dim3(SM_BLOCKS, L), VT, 0, s>>>(x, b, r, L, n, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  pair_dots_final_kernel<<<1, 128, 0, s>>>(partial, L, SM_BLOCKS, out);
   return cudaGetLastError();
 }
 

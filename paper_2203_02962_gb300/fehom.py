@@ -30,6 +30,7 @@ EXPORTS = ("fehom_default_options", "fehom_setup", "fehom_precond_build", "fehom
            "fehom_get_symbol_inverse", "fehom_mean_flux", "fehom_kernel_times", "fehom_launch_count",
            "fehom_fft_plan", "fehom_mean_flux_noalloc", "fehom_pcg_coefficients", "fehom_eig_bounds",
            "fehom_batch_create", "fehom_solve_batch", "fehom_batch_destroy", "fehom_batch_last_error",
+           "fehom_effective_energy",
            # include/fehom_unet.h
            "fehom_unet_create", "fehom_unet_destroy", "fehom_unet_last_error", "fehom_unet_param_count",
            "fehom_unet_set_params", "fehom_unet_get_params", "fehom_unet_predict", "fehom_unet_loss_grad",
@@ -41,7 +42,7 @@ KERNEL_CLASSES = ("stiffness", "fft_x_fwd", "fft_y_fwd", "fft_last", "fft_y_inv"
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_iter", C.c_int), ("inner_tol", C.c_double),
                 ("stream", C.c_void_p), ("use_graph", C.c_int), ("profile", C.c_int),
-                ("autotune", C.c_int), ("x0_scaling", C.c_int)]
+                ("autotune", C.c_int), ("x0_scaling", C.c_int), ("fft_xy", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -109,10 +110,12 @@ def load_library(path: str = LIB_PATH):
     lib.fehom_batch_last_error.restype = C.c_char_p
     lib.fehom_kernel_times.argtypes = [vp, i, dp, i64p]
     lib.fehom_kernel_times.restype = i
+    lib.fehom_effective_energy.argtypes = [vp, dp]
+    lib.fehom_effective_energy.restype = i
     lib.fehom_launch_count.argtypes = [vp, i64p]
     lib.fehom_launch_count.restype = i
     ip = C.POINTER(C.c_int)
-    lib.fehom_fft_plan.argtypes = [vp, i, ip, ip, ip, dp]
+    lib.fehom_fft_plan.argtypes = [vp, i, ip, ip, ip, dp, ip]
     lib.fehom_fft_plan.restype = i
     fp = C.POINTER(C.c_float)
     lib.fehom_unet_create.argtypes = [C.POINTER(vp), C.c_int64, i, ip, i, i, i, vp]
@@ -159,7 +162,7 @@ class Solver:
 
     def __init__(self, elem, physics, n, ids, moduli, ref_material=None, precision="fp64", max_iter=10000,
                  inner_tol=1e-3, cell=None, use_graph=True, stream=None, profile=False, autotune=True,
-                 x0_scaling=True):
+                 x0_scaling=True, fft_xy=-1):
         torch = _torch()
         self.lib = load_library()
         self.elem, self.physics = elem, physics
@@ -175,6 +178,7 @@ class Solver:
         opt.profile = 1 if profile else 0
         opt.autotune = 1 if autotune else 0
         opt.x0_scaling = 1 if x0_scaling else 0
+        opt.fft_xy = int(fft_xy)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opt.stream = C.c_void_p(self.stream.cuda_stream)
         self._opt = opt
@@ -284,11 +288,18 @@ class Solver:
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
 
     def fft_plan(self, precision="fp64"):
-        """Launch plan of the FFT passes: pairs, tc_y, tc_last and the tuner's times (ms)."""
-        p, y, l = C.c_int(), C.c_int(), C.c_int()
+        """Launch plan of the FFT passes: pairs, tc_y, tc_last, the tuner's times (ms), fused x-y passes."""
+        p, y, l, xy = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         ms = (C.c_double * 3)()
-        self._check(self.lib.fehom_fft_plan(self.ctx, PRECISION[precision], C.byref(p), C.byref(y), C.byref(l), ms))
-        return {"pairs": p.value, "tc_y": y.value, "tc_last": l.value, "ms": list(ms)}
+        self._check(self.lib.fehom_fft_plan(self.ctx, PRECISION[precision], C.byref(p), C.byref(y), C.byref(l), ms,
+                                            C.byref(xy)))
+        return {"pairs": p.value, "tc_y": y.value, "tc_last": l.value, "ms": list(ms), "xy_fused": xy.value}
+
+    def effective_energy(self):
+        """Energy (Hill-Mandel) form of C_eff from the last solve with m independent loads."""
+        out = np.zeros((self.m, self.m))
+        self._check(self.lib.fehom_effective_energy(self.ctx, _dptr(out)))
+        return out
 
     def launch_count(self):
         n = C.c_int64()

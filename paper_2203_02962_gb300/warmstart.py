@@ -107,8 +107,19 @@ def evaluate(net, cells, data, out_scale: float, tol=1e-6, precision="mixed", ma
     e1.record()
     torch.cuda.synchronize()
     predict_ms = e0.elapsed_time(e1) / count
-    cold, warm, raw = [], [], []
+    cold, warm, raw, energy = [], [], [], []
     for i, c in enumerate(cells):
+        # energy-norm error of the Galerkin-scaled guess relative to the zero guess, per load:
+        # |u - g x|_K / |u|_K with g = <x, K u> / <x, K x> (the scaling fehom_solve applies)
+        s = fehom.Solver("hex8_3d", "scalar", c["n"], data["ids"][i], c["moduli"])
+        for l in range(3):
+            u, xg = data["fields"][i, l].contiguous(), x0[i, l] - x0[i, l].mean()
+            ku, kx = s.apply_stiffness(u), s.apply_stiffness(xg.contiguous())
+            uh, xh, kuh, kxh = (t.cpu().numpy() for t in (u, xg, ku, kx))
+            uku, xku, xkx = float(uh @ kuh), float(xh @ kuh), float(xh @ kxh)
+            g = xku / xkx if xkx > 0 else 0.0
+            energy.append(math.sqrt(max(uku - 2 * g * xku + g * g * xkx, 0.0) / uku))
+        s.close()
         for scaled, runs in ((True, ((cold, None), (warm, x0[i]))), (False, ((raw, x0[i]),))):
             s = fehom.Solver("hex8_3d", "scalar", c["n"], data["ids"][i], c["moduli"], precision=precision,
                              x0_scaling=scaled)
@@ -126,11 +137,13 @@ def evaluate(net, cells, data, out_scale: float, tol=1e-6, precision="mixed", ma
                 "solve_ms_mean": float(np.mean([r["ms"] for r in rows])),
                 "all_converged": bool(all(r["converged"] for r in rows))}
 
-    return stats(cold), stats(warm), stats(raw), predict_ms
+    w = stats(warm)
+    w["energy_error_rel_mean"] = float(np.mean(energy))
+    return stats(cold), w, stats(raw), predict_ms
 
 
 def experiment(n=64, n_train=4000, n_test=500, steps=None, batch=8, lr=1e-3, seed=0, widths=(16, 32, 64, 128),
-               tol=1e-6, precision="mixed", workers=0):
+               tol=1e-6, precision="mixed", workers=0, loss="h1", l2_weight=0.1):
     """Generate, train, evaluate; returns a dict of the results (see the module docstring)."""
     from . import fehom
     torch = fehom._torch()
@@ -146,6 +159,7 @@ def experiment(n=64, n_train=4000, n_test=500, steps=None, batch=8, lr=1e-3, see
     out_scale = float(data["fields"].std())
     net = fehom.UNet(n, widths, n_phases=2, n_out=3, max_batch=batch)
     net.set_params(init_params(widths, 3, seed))
+    net.set_loss(loss, l2_weight)
     if steps is None:
         steps = 8 * max(1, n_train // batch)  # 8 epochs
     torch.cuda.synchronize()
@@ -156,6 +170,7 @@ def experiment(n=64, n_train=4000, n_test=500, steps=None, batch=8, lr=1e-3, see
     cold, warm, raw, predict_ms = evaluate(net, cells_test, test, out_scale, tol, precision, batch)
     net.close()
     return {"n": n, "n_train": n_train, "n_test": n_test, "steps": steps, "batch": batch, "lr": lr,
+            "loss": loss, "l2_weight": l2_weight,
             "widths": list(widths), "n_params": int(sum(_layer_sizes(widths, 3))), "out_scale": out_scale,
             "train_loss_first": losses[0][1], "train_loss_last": losses[-1][1], "losses": losses,
             "cold": cold, "warm": warm, "warm_unscaled": raw, "predict_ms_per_cell": predict_ms,
@@ -211,8 +226,11 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--workers", type=int, default=max(1, (mp.cpu_count() or 2) - 1))
+    ap.add_argument("--loss", default="h1", choices=["mse", "h1"])
+    ap.add_argument("--l2-weight", type=float, default=0.1)
     args = ap.parse_args()
-    res = experiment(args.n, args.train, args.test, args.steps, args.batch, args.lr, args.seed, workers=args.workers)
+    res = experiment(args.n, args.train, args.test, args.steps, args.batch, args.lr, args.seed, workers=args.workers,
+                     loss=args.loss, l2_weight=args.l2_weight)
     print(json.dumps(res))
 
 

@@ -148,6 +148,63 @@ def test_symbol_and_preconditioner(elem, physics, shape):
     s.close()
 
 
+@pytest.mark.parametrize("physics", ["elastic", "scalar"])
+def test_fused_xy_passes_match_oracle(physics):
+    """The fused x-y FFT passes (FP32, 128 x 128 planes): preconditioner apply against the oracle, and
+    mixed-precision solves with and without them agree."""
+    torch = _torch()
+    shape = (6, 128, 128)
+    g = fem.Grid(shape, "hex8_3d", physics)
+    rng = np.random.default_rng(21)
+    ids = (rng.random(shape) < 0.3).astype(np.uint8)
+    mod = _materials(physics, 3, "iso")[:2]
+    C_ref = fem.mean_material(g, ids.ravel(), mod)
+    Kinv = solvers.kref_pinv_symbol(solvers.kref_symbol(g, C_ref))
+    r = rng.standard_normal(g.c * g.N)
+    z_ref = solvers.apply_precond(g, Kinv, r)
+    outs = {}
+    for fused in (1, 0):
+        s = _solver("hex8_3d", physics, shape, ids, mod, precision="mixed", fft_xy=fused, autotune=False)
+        s.precond_build()
+        z32 = s.apply_precond(torch.tensor(r, dtype=torch.float32, device="cuda"), "mixed").double().cpu().numpy()
+        assert _rel(z32, z_ref) < 2e-5, fused
+        loads = np.eye(6 if physics == "elastic" else 3)
+        outs[fused] = s.solve(loads, tol=1e-9, fields=None)
+        assert s.fft_plan("mixed")["xy_fused"] == fused
+        s.close()
+    assert _rel(outs[1]["C_eff"], outs[0]["C_eff"]) < 1e-7
+
+
+@pytest.mark.parametrize("physics", ["elastic", "scalar"])
+def test_register_split_last_axis_pass_matches_oracle(physics):
+    """The register-split last-axis pass (FP32, nz = 128) with the fused x-y passes (128 x 128 planes):
+    preconditioner apply on a 128^3 cell against the oracle, and mixed solves with and without them agree."""
+    torch = _torch()
+    shape = (128, 128, 128)
+    g = fem.Grid(shape, "hex8_3d", physics)
+    rng = np.random.default_rng(23)
+    ids = (rng.random(shape) < 0.3).astype(np.uint8)
+    mod = _materials(physics, 3, "iso")[:2]
+    C_ref = fem.mean_material(g, ids.ravel(), mod)
+    Kinv = solvers.kref_pinv_symbol(solvers.kref_symbol(g, C_ref))
+    r = rng.standard_normal(g.c * g.N)
+    z_ref = solvers.apply_precond(g, Kinv, r)
+    outs = {}
+    for fused in (1, 0):
+        s = _solver("hex8_3d", physics, shape, ids, mod, precision="mixed", fft_xy=fused, autotune=False)
+        s.precond_build()
+        z32 = s.apply_precond(torch.tensor(r, dtype=torch.float32, device="cuda"), "mixed").double().cpu().numpy()
+        assert _rel(z32, z_ref) < 2e-5, fused
+        loads = np.eye(6 if physics == "elastic" else 3)[:2]
+        outs[fused] = s.solve(loads, tol=1e-8, fields=None)
+        s.close()
+    assert _rel(outs[1]["mean_flux"], outs[0]["mean_flux"]) < 1e-6
+    for a, b in zip(outs[1]["info"], outs[0]["info"]):
+        assert a["converged"] and abs(a["iterations"] - b["iterations"]) <= 3
+    for a, b in zip(outs[1]["info"], outs[0]["info"]):
+        assert a["converged"] and abs(a["iterations"] - b["iterations"]) <= 3
+
+
 def _small_elastic(n=16, seed=3):
     ids = I.spheres3d(n, count=8, rmin=2.0, rmax=3.5, seed=seed)
     mod = np.stack([I.isotropic_elastic_mandel(1.0, 0.3), I.isotropic_elastic_mandel(100.0, 0.2)])
@@ -366,6 +423,41 @@ def test_full_size_bench_config_sampled():
     r_rows = b_rows[rows] - fem.stiffness_rows(g, w["ids"].ravel(), w["moduli"], u0, rows)
     assert np.abs(r_rows).max() < 1e-3 * np.abs(b_rows).max()
     s.close()
+
+
+def test_full_size_grf_scalar_512_mixed_and_fp64():
+    """512^3 scalar conductivity, thresholded GRF, contrast 1000, three unit gradients (134M DOF):
+    sampled stiffness rows against the oracle; FP64 and mixed solves to 1e-6 converge, give a symmetric
+    C_eff inside the Voigt-Reuss bounds, and agree with each other."""
+    torch = _torch()
+    w = I.workload_grf_scalar(512)
+    shape = (512, 512, 512)
+    g = fem.Grid(shape, "hex8_3d", "scalar")
+    ids = w["ids"].ravel()
+    f = np.bincount(ids, minlength=2) / g.N
+    voigt = sum(fp * Cp for fp, Cp in zip(f, w["moduli"]))
+    reuss = np.linalg.inv(sum(fp * np.linalg.inv(Cp) for fp, Cp in zip(f, w["moduli"])))
+    C = {}
+    for prec in ("fp64", "mixed"):
+        s = _solver("hex8_3d", "scalar", shape, w["ids"], w["moduli"], precision=prec)
+        if prec == "fp64":
+            rng = np.random.default_rng(5)
+            x = rng.standard_normal(g.N)
+            y = s.apply_stiffness(torch.tensor(x, device="cuda")).cpu().numpy()
+            rows = rng.integers(0, g.N, 2000)
+            y_ref = fem.stiffness_rows(g, ids, w["moduli"], x, rows)
+            assert np.abs(y[rows] - y_ref).max() <= 1e-12 * np.abs(y_ref).max()
+            del x, y
+        s.precond_build()
+        out = s.solve(w["loads"], tol=w["tol"], fields=None)
+        assert all(i["converged"] for i in out["info"]), out["info"]
+        assert all(i["rel_residual_2"] < 1e-4 for i in out["info"]), out["info"]
+        C[prec] = out["C_eff"]
+        sym = 0.5 * (C[prec] + C[prec].T)
+        assert np.abs(C[prec] - C[prec].T).max() <= 1e-4 * np.abs(C[prec]).max()
+        assert np.linalg.eigvalsh(voigt - sym).min() > 0 and np.linalg.eigvalsh(sym - reuss).min() > 0
+        s.close()
+    assert _rel(C["mixed"], C["fp64"]) < 1e-5
 
 
 def test_autotuned_plans_are_valid_and_agree():

@@ -430,3 +430,32 @@ def test_coated_sphere_balance_reproduces_printed_moduli():
     assert abs(K1 - gd["K1"]) < 5e-9 and abs(K2 - gd["K2"]) < 5e-7
     assert abs(G1 - gd["G1"]) < 5e-9 and abs(G2 - gd["G2"]) < 5e-7
     assert Ke == gd["K_eff"] and abs(Ge - gd["G_eff"]) < 1e-15
+
+
+def test_energy_bilinear_form_pins():
+    """fem.energy: at the exact solutions it is |Y| e_i^T C_eff e_j for every pair of loads (Hill-Mandel,
+    bilinear); with zero fluctuations it is |Y| e^T <C> e; it is symmetric; and it is stationary at the
+    solution: E(u + eps v) - E(u) = eps^2 v^T K v exactly."""
+    g = fem.Grid((4, 3, 4), "hex8_3d", "elastic")
+    rng = np.random.default_rng(17)
+    ids = rng.integers(0, 2, g.N)
+    mod = [_rand_spd(6, 40, 1.0), _rand_spd(6, 41, 20.0)]
+    loads = np.eye(6)
+    r = solvers.homogenise(g, ids, mod, loads, method="sparse")
+    vol = g.vp * g.N
+    u = r["fields"]
+    for i in range(6):
+        for j in range(6):
+            Eij = fem.energy(g, ids, mod, loads[i], u[i], loads[j], u[j])
+            assert abs(Eij - vol * r["C_eff"][i, j]) < 1e-10 * vol * np.abs(r["C_eff"]).max()
+            assert abs(Eij - fem.energy(g, ids, mod, loads[j], u[j], loads[i], u[i])) < 1e-12
+    e = rng.standard_normal(6)
+    z = np.zeros(g.c * g.N)
+    em = e @ fem.mean_material(g, ids, mod) @ e
+    assert abs(fem.energy(g, ids, mod, e, z, e, z) - vol * em) < 1e-12 * abs(em)
+    K = fem.assemble_K(g, ids, mod)
+    v = rng.standard_normal(g.c * g.N)
+    for eps in (1e-3, 1e-1):
+        d = fem.energy(g, ids, mod, loads[2], u[2] + eps * v, loads[2], u[2] + eps * v) \
+            - fem.energy(g, ids, mod, loads[2], u[2], loads[2], u[2])
+        assert abs(d - eps * eps * v @ (K @ v)) < 1e-9 * max(1.0, eps * eps * abs(v @ (K @ v)))
