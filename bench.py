@@ -119,6 +119,8 @@ def kernel_model(s):
 
 
 FP64_INSTR_PEAK = 152 * 2 * 2.07e9     # FP64 instructions/s: 152 SMs x 2 FP64 lanes-per-clock x max clock
+# DRAM bytes (read + write) of one 6-load FP64 stiffness launch on the 128^3 workload, from ncu
+FP64_STIFFNESS_DRAM_BYTES = 324.392960e6 + 263.367680e6
 
 
 def run_ours(args):
@@ -160,7 +162,7 @@ def run_ours(args):
         load_iters = sum(sum(i["iterations"] for i in o["info"]) for o in outs)
         results[prec] = dict(ms=ms, iters=load_iters / args.steps, out=outs[-1], clocks=clk.summary(), kt=kt,
                              load_iters=load_iters, launches=s.launch_count() - l_before,
-                             plan=s.fft_plan(prec))
+                             plan=s.fft_plan(prec), C_energy=s.effective_energy())
         s.close()
 
     # e2e: host phase ids -> setup -> build -> solve -> fields back to pinned host memory
@@ -192,6 +194,7 @@ def run_ours(args):
     sref = fehom.Solver("hex8_3d", "elastic", n, ids_dev, w["moduli"], stream=stream)
     sref.precond_build()
     C_ref = sref.solve(loads, tol=1e-10, fields=None)["C_eff"]
+    C_ref_energy = sref.effective_energy()
     sref.close()
     r64, rmx = results["fp64"], results["mixed"]
     err = lambda C: float(np.abs(C - C_ref).max() / np.abs(C_ref).max())
@@ -228,6 +231,8 @@ def run_ours(args):
         "pcg_iterations_per_load": [i["iterations"] for i in r64["out"]["info"]],
         "C_eff_diag": [float(v) for v in np.diag(r64["out"]["C_eff"])],
         "C_eff_rel_err_vs_fp64_tol1e-10": err(r64["out"]["C_eff"]),
+        "C_eff_energy_rel_err_vs_fp64_tol1e-10": float(np.abs(r64["C_energy"] - C_ref_energy).max()
+                                                       / np.abs(C_ref_energy).max()),
         "e2e": {"value": c * N * (e_iters[-1]) / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(N + w["moduli"].nbytes + loads.nbytes),
                 "d2h_bytes_per_step": int(len(loads) * c * N * 8 + 6 * 6 * 8 + len(loads) * 6 * 8),
@@ -239,11 +244,19 @@ def run_ours(args):
                   "C_eff_rel_diff_vs_fp64": float(np.abs(rmx["out"]["C_eff"] - r64["out"]["C_eff"]).max()
                                                   / np.abs(r64["out"]["C_eff"]).max()),
                   "C_eff_rel_err_vs_fp64_tol1e-10": err(rmx["out"]["C_eff"]),
+                  "C_eff_energy_rel_diff_vs_fp64": float(np.abs(rmx["C_energy"] - r64["C_energy"]).max()
+                                                         / np.abs(r64["C_energy"]).max()),
+                  "C_eff_energy_rel_err_vs_fp64_tol1e-10": float(np.abs(rmx["C_energy"] - C_ref_energy).max()
+                                                                 / np.abs(C_ref_energy).max()),
                   "kernel_ms": {k: v[0] for k, v in rmx["kt"].items()},
                   "gpu_launches": rmx["launches"], "fft_plan": rmx["plan"], "clocks": rmx["clocks"]},
         "fft_plan_fp64": r64["plan"],
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_ops / 1e12, "peak": FP64_INSTR_PEAK / 1e12,
-                     "unit": "T FP64-instr/s", "frac": achieved_ops / FP64_INSTR_PEAK, "traffic": None,
+                     "unit": "T FP64-instr/s", "frac": achieved_ops / FP64_INSTR_PEAK,
+                     "traffic": FP64_STIFFNESS_DRAM_BYTES if dom == "stiffness" else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 6-load launch, "
+                                       "profiles/hex8_apply_fp64_128cube_elastic.md",
+                     "algorithmic_bytes_per_launch": model["bytes"] * units_per_launch,
                      "peak_source": "152 SMs x 2 FP64 lanes/clk x 2.07 GHz (unit count x max clock)",
                      "avg_launch_ms": avg_ms, "launches": dom_launches,
                      "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm, "hbm_frac": achieved_gbs / hbm,

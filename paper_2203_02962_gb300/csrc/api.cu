@@ -1408,7 +1408,7 @@ static fehom_status energy_c_eff(fehom_ctx* ctx, int m, const double* loads, con
       for (int a = 0; a < m; ++a)
         for (int b = 0; b < m; ++b) ece += loads[i * m + a] * Cm[a * m + b] * loads[j * m + b];
       // dots[(i m + j) 2 + 0] = x_i . b_j, [.. + 1] = x_i . r_j
-      A[i * m + j] = ece - (dots[(j * m + i) * 2] + dots[(i * m + j) * 2 + 1]) / ctx->vol;
+      A[i * m + j] = ece - (dots[(j * m + i) * 2] + dots[(i * m + j) * 2 + 1]) / (ctx->vol * (double)ctx->d.N);
     }
   for (int i = 0; i < m; ++i)
     for (int j = i + 1; j < m; ++j) A[i * m + j] = A[j * m + i] = 0.5 * (A[i * m + j] + A[j * m + i]);

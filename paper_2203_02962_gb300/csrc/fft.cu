@@ -851,8 +851,12 @@ __global__ void __launch_bounds__(XY_THREADS, 2) fft_xy_inv128_kernel(FftArgs a)
 // the first half of the inverse (8-point inverse DFTs, conjugate twiddles); stage 3: 16-point inverse
 // DFTs written straight back.  Shared memory is touched twice per direction instead of once per
 // radix stage.
+// Threads: 128 per component for stages 1 and 3, at least 256 (16 columns x 16 k1) for stage 2.
 template <int NC>
-__global__ void __launch_bounds__(128 * NC, NC == 3 ? 2 : 4) fft_last128_kernel(FftArgs a) {
+__host__ __device__ constexpr int last128_threads() { return NC == 1 ? 256 : 128 * NC; }
+
+template <int NC>
+__global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_last128_kernel(FftArgs a) {
   constexpr int TCL = 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_sh[32];
@@ -868,7 +872,7 @@ __global__ void __launch_bounds__(128 * NC, NC == 3 ? 2 : 4) fft_last128_kernel(
   const float2* tw = reinterpret_cast<const float2*>(a.tw.z);
   const float* sym = reinterpret_cast<const float*>(a.sym);
   const int tid = threadIdx.x;
-  {  // stage 1: task (column t, subsequence j, component c)
+  if (tid < 128 * NC) {  // stage 1: task (column t, subsequence j, component c)
     const int t = tid & 15, j = (tid >> 4) & 7, c = tid >> 7;
     const int cf = cf0 + t;
     float2 v[16];
@@ -930,7 +934,7 @@ __global__ void __launch_bounds__(128 * NC, NC == 3 ? 2 : 4) fft_last128_kernel(
     }
   }
   __syncthreads();
-  {  // stage 3: task (column t, subsequence j, component c): 16-point inverse DFT over k1
+  if (tid < 128 * NC) {  // stage 3: task (column t, subsequence j, component c): 16-point inverse DFT over k1
     const int tt = tid & 15, j = (tid >> 4) & 7, c = tid >> 7;
     const int cff = cf0 + tt;
     float2 v[16];
@@ -1197,8 +1201,8 @@ cudaError_t launch_fft_last_solve(const FftArgs& a, cudaStream_t s) {
     const dim3 grid((a.d.ny * a.d.nxh) / 16, 1, a.n_loads);
     if (a.st != nullptr && (long long)grid.x > a.red.max_blocks) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)a.d.c * 16 * 8 * 16 * sizeof(float2);
-    if (a.d.c == 1) return launch_with_smem(fft_last128_kernel<1>, grid, 128, smem, s, a);
-    return launch_with_smem(fft_last128_kernel<3>, grid, 384, smem, s, a);
+    if (a.d.c == 1) return launch_with_smem(fft_last128_kernel<1>, grid, last128_threads<1>(), smem, s, a);
+    return launch_with_smem(fft_last128_kernel<3>, grid, last128_threads<3>(), smem, s, a);
   }
   if (a.d.c == 1) return launch_last_nc<T, 1>(a, s);
   if (a.d.c == 2) return launch_last_nc<T, 2>(a, s);

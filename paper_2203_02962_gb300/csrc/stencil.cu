@@ -46,6 +46,18 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+// 4-byte asynchronous global -> shared copies (FP32 stiffness: node planes fetched one layer ahead)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+constexpr int RP = BX + 2;           // row pitch of a staged node plane (nodes i0 - 1 .. i0 + BX)
+constexpr int RPLANE = RP * (BY + 2);  // nodes of a staged plane per component (340)
+
 // Block-wide FP64 sum; every thread gets the result. `sh` holds >= 32 doubles.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -266,11 +278,25 @@ __device__ void pcg_alpha_update(PcgState& s, double total, double* hist) {
 //      face total to its 4 corners of plane k;
 //   C. node threads gather the 4 faces around their node of plane k and write y.
 // ------------------------------------------------------------------------------------------------
+// RAW (FP32 kernels with a field): instead of barrier A, the raw node planes (tile + halo) are
+// fetched with cp.async one layer ahead into a ring of three plane buffers, and each element forms
+// the butterflies of its two faces itself (FP32 adds are cheap; the FP64 kernels keep the shared
+// face butterflies, which save FP64 operations).  The x values of the <x, y> dot come from the same
+// staged plane.
+template <typename T, int C, bool HAS_X>
+__host__ __device__ constexpr bool hex8_raw() { return HAS_X && sizeof(T) == 4; }
+template <typename T, int C, bool HAS_X>
+__host__ __device__ constexpr size_t hex8_smem_elems() {
+  return hex8_raw<T, C, HAS_X>() ? (size_t)3 * C * RPLANE + 4 * C * NE : (size_t)2 * 4 * C * NE + 4 * C * NE;
+}
+
 template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED>
-__global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_per_cta) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) hex8_apply_kernel(StencilArgs a, int kz_per_cta) {
+  constexpr bool RAW = hex8_raw<T, C, HAS_X>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* FB = reinterpret_cast<T*>(smem_raw);  // [2 planes][4][C][NE] face butterflies
-  T* FC = FB + 2 * 4 * C * NE;              // [4 corners][C][NE] face contributions to plane k
+  T* FB = reinterpret_cast<T*>(smem_raw);  // [2 planes][4][C][NE] face butterflies (not RAW)
+  T* RW = reinterpret_cast<T*>(smem_raw);  // [3 slots][C][BY + 2][RP] staged node planes (RAW)
+  T* FC = RAW ? RW + 3 * C * RPLANE : FB + 2 * 4 * C * NE;  // [4 corners][C][NE] face contributions to plane k
   __shared__ double red_sh[32];
 
   const Dims d = a.d;
@@ -338,20 +364,70 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
     }
   };
 
+  // RAW: stage node plane kz (tile nodes i0 - 1 .. i0 + BX, j0 - 1 .. j0 + BY) into ring slot `slot`;
+  // this thread copies the entries tid + q NT, whose in-plane source offsets are fixed per CTA
+  constexpr int NSTAGE = (C * RPLANE + NT - 1) / NT;
+  int soff[NSTAGE];
+#pragma unroll
+  for (int q = 0; q < NSTAGE; ++q) {
+    const int idx = tid + q * NT;
+    soff[q] = -1;
+    if (RAW && idx < C * RPLANE) {
+      const int j = idx / RPLANE, rem = idx - j * RPLANE, r = rem / RP, c = rem - r * RP;
+      soff[q] = j * (int)d.N + wrap(j0 - 1 + r, d.ny) * d.nx + wrap(i0 - 1 + c, d.nx);
+    }
+  }
+  auto stage_plane = [&](int slot, int kz) {
+    if constexpr (RAW) {
+      const T* xk = x + (long long)kz * plane;
+      T* dst = RW + slot * C * RPLANE;
+#pragma unroll
+      for (int q = 0; q < NSTAGE; ++q)
+        if (soff[q] >= 0) cp_async4(dst + tid + q * NT, xk + soff[q]);
+    }
+    cp_async_commit();
+  };
+  // RAW: butterflies (ss, sd, ds, dd) of this thread's face in staged slot `slot`
+  auto raw_face = [&](int slot, T (&f)[C][4]) {
+    const T* src = RW + slot * C * RPLANE + ej * RP + ei;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const T* sj = src + j * RPLANE;
+      const T v00 = sj[0], v10 = sj[1], v01 = sj[RP], v11 = sj[RP + 1];
+      const T s0 = v10 + v00, d0 = v10 - v00, s1 = v11 + v01, d1 = v11 - v01;
+      f[j][0] = s1 + s0;
+      f[j][1] = s1 - s0;
+      f[j][2] = d1 + d0;
+      f[j][3] = d1 - d0;
+    }
+  };
+  auto ring = [&](int k) { return (k - k0 + 1) % 3; };
+
   // B + C for element layer k (planes k: slot CUR, k + 1: slot CUR ^ 1); kzc = wrap(k)
   auto layer = [&](auto cur_c, int k, int kzc) {
     constexpr int CUR = decltype(cur_c)::value;
-    faces(std::integral_constant<int, CUR ^ 1>{}, next(kzc));
-    __syncthreads();
+    if constexpr (RAW) {
+      cp_async_wait_all();  // plane k + 1 (issued one layer earlier) has landed
+      __syncthreads();      // ... for every thread; the ring slot of plane k - 1 is free again
+      if (k + 2 <= k1) stage_plane(ring(k + 2), wrap(k + 2, d.nz));
+    } else {
+      faces(std::integral_constant<int, CUR ^ 1>{}, next(kzc));
+      __syncthreads();
+    }
     if (face_thread) {
       T bot[C][4], top[C][4];
+      if constexpr (RAW) {
+        raw_face(ring(k), bot);
+        raw_face(ring(k + 1), top);
+      } else {
 #pragma unroll
-      for (int j = 0; j < C; ++j)
+        for (int j = 0; j < C; ++j)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          bot[j][q] = HAS_X ? FB[((CUR * 4 + q) * C + j) * NE + tid] : T(0);
-          top[j][q] = HAS_X ? FB[(((CUR ^ 1) * 4 + q) * C + j) * NE + tid] : T(0);
-        }
+          for (int q = 0; q < 4; ++q) {
+            bot[j][q] = HAS_X ? FB[((CUR * 4 + q) * C + j) * NE + tid] : T(0);
+            top[j][q] = HAS_X ? FB[(((CUR ^ 1) * 4 + q) * C + j) * NE + tid] : T(0);
+          }
+      }
       const int ph = a.ids ? a.ids[(long long)kzc * plane + off00] : 0;
       T pb[C][4], pt[C][4], t1[C][3];
       hex8_element_faces<T, C, ISO, HAS_X, HAS_E>(bot, top, mats + (long long)ph * (9 * C * C), isot + 2 * ph,
@@ -388,7 +464,10 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
         const T val = T(a.y_scale) * v;
         const long long gidx = (long long)j * d.N + (long long)kzc * plane + node_off;
         if (RED != RED_SUMS) y[gidx] = val;
-        if (RED == RED_PCG) acc_p.add(val, __ldg(x + gidx));
+        if constexpr (RED == RED_PCG) {
+          if constexpr (RAW) acc_p.add(val, RW[(ring(k) * C + j) * RPLANE + (nj + 1) * RP + ni + 1]);
+          else acc_p.add(val, __ldg(x + gidx));
+        }
         if (RED == RED_STATS || RED == RED_SUMS) acc_y += (double)val * (double)val;
       }
     }
@@ -396,7 +475,12 @@ __global__ void __launch_bounds__(NT) hex8_apply_kernel(StencilArgs a, int kz_pe
   };
 
   int kz = wrap(k0 - 1, d.nz);
-  faces(std::integral_constant<int, 0>{}, kz);
+  if constexpr (RAW) {
+    stage_plane(ring(k0 - 1), kz);
+    stage_plane(ring(k0), next(kz));
+  } else {
+    faces(std::integral_constant<int, 0>{}, kz);
+  }
   int k = k0 - 1;
   while (k < k1) {
     layer(std::integral_constant<int, 0>{}, k, kz);
@@ -638,7 +722,7 @@ cudaError_t launch_hex8_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
   hex8_grid(d, &tiles, &slabs, &kz);
   if (ctas) *ctas = tiles * slabs;
   if (RED == RED_PCG && tiles * slabs > a.red.max_blocks) return cudaErrorInvalidConfiguration;
-  const size_t smem = sizeof(T) * (2 * 4 * C * NE + 4 * C * NE);
+  const size_t smem = sizeof(T) * hex8_smem_elems<T, C, HAS_X>();
   auto kern = hex8_apply_kernel<T, C, ISO, HAS_X, HAS_E, RED>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;

@@ -347,6 +347,37 @@ def test_warm_start_galerkin_scaling(precision):
         s.close()
 
 
+def test_energy_form_c_eff():
+    """Energy (Hill-Mandel) form of C_eff: equals the oracle's bilinear energy of the GPU's own fields at
+    any accuracy, matches the exact C_eff when converged, is far closer to it than the stress average
+    when loosely converged, and makes mixed and FP64 agree to 1e-7 at tol 1e-6."""
+    n = 16
+    ids, mod = _small_elastic(n, seed=14)
+    g = fem.Grid((n, n, n), "hex8_3d", "elastic")
+    exact = solvers.homogenise(g, ids.ravel(), mod, np.eye(6), method="cg", tol=1e-14)["C_eff"]
+    s = _solver("hex8_3d", "elastic", (n, n, n), ids, mod)
+    s.precond_build()
+    loose = s.solve(np.eye(6), tol=1e-3)
+    CE = s.effective_energy()
+    u = loose["fields"].cpu().numpy()
+    vol = g.vp * g.N
+    ref = np.array([[fem.energy(g, ids.ravel(), mod, np.eye(6)[i], u[i].ravel(), np.eye(6)[j], u[j].ravel())
+                     for j in range(6)] for i in range(6)]) / vol
+    assert _rel(CE, 0.5 * (ref + ref.T)) < 1e-11
+    assert np.abs(CE - exact).max() < 0.05 * np.abs(loose["C_eff"] - exact).max()
+    s.solve(np.eye(6), tol=1e-12, fields=None)
+    assert _rel(s.effective_energy(), exact) < 1e-10
+    s.close()
+    ce = {}
+    for prec in ("fp64", "mixed"):
+        t = _solver("hex8_3d", "elastic", (n, n, n), ids, mod, precision=prec)
+        t.precond_build()
+        t.solve(np.eye(6), tol=1e-6, fields=None)
+        ce[prec] = t.effective_energy()
+        t.close()
+    assert _rel(ce["mixed"], ce["fp64"]) < 1e-7
+
+
 def test_homogeneous_and_zero_load():
     C = _rand_spd(6, 12)
     ids = np.zeros((8, 8, 8), np.uint8)
