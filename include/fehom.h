@@ -216,8 +216,9 @@ fehom_status fehom_eig_bounds(fehom_ctx* ctx, double* lo_values, int64_t* lo_cou
 /* Launch plan of the FFT passes in use for a precision (FEHOM_FP64 / FEHOM_MIXED): x-line pairs per
  * CTA, columns per CTA of the y pass and of the last-axis pass (0 = built-in choice, not tuned yet),
  * the device milliseconds of the chosen plans measured by the tuner (ms[3]: x passes, y passes,
- * last-axis pass; may be NULL), and whether the fused x-y passes replace the separate x and y passes
- * (*xy_fused = 1; FP32 3-D fields with 128 x 128 planes; then ms[0] times them and ms[1] = 0; may be NULL). */
+ * last-axis pass; may be NULL), and the register-split FP32 passes in use as a bit mask (*xy_fused,
+ * may be NULL): bit 0 = fused x-y passes (128 x 128 planes; then ms[0] times them and ms[1] = 0),
+ * bit 1 = register-split last-axis pass (nz = 128). */
 fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int* tc_y, int* tc_last, double* ms,
                             int* xy_fused);
 

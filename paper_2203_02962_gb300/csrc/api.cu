@@ -899,9 +899,12 @@ fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int
                             int* xy_fused) {
   if (!ctx) return FEHOM_E_INVALID;
   const auto& pl = ctx->plan[precision == FEHOM_MIXED ? 1 : 0];
-  if (xy_fused)
-    *xy_fused = (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.xy)) &&
-                fft_xy_supported(ctx->d, precision == FEHOM_MIXED);
+  if (xy_fused) {
+    const bool fp32 = precision == FEHOM_MIXED;
+    const int a = (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.xy)) && fft_xy_supported(ctx->d, fp32);
+    const int b = (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.last_reg)) && fft_last128_supported(ctx->d, fp32);
+    *xy_fused = a | (b << 1);
+  }
   if (pairs) *pairs = pl.pairs;
   if (tc_y) *tc_y = pl.tc_y;
   if (tc_last) *tc_last = pl.tc_last;

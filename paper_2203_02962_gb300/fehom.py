@@ -293,7 +293,8 @@ class Solver:
         ms = (C.c_double * 3)()
         self._check(self.lib.fehom_fft_plan(self.ctx, PRECISION[precision], C.byref(p), C.byref(y), C.byref(l), ms,
                                             C.byref(xy)))
-        return {"pairs": p.value, "tc_y": y.value, "tc_last": l.value, "ms": list(ms), "xy_fused": xy.value}
+        return {"pairs": p.value, "tc_y": y.value, "tc_last": l.value, "ms": list(ms), "xy_fused": xy.value & 1,
+                "last_reg": (xy.value >> 1) & 1}
 
     def effective_energy(self):
         """Energy (Hill-Mandel) form of C_eff from the last solve with m independent loads."""
