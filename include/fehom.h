@@ -222,6 +222,36 @@ fehom_status fehom_eig_bounds(fehom_ctx* ctx, double* lo_values, int64_t* lo_cou
 fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int* tc_y, int* tc_last, double* ms,
                             int* xy_fused);
 
+/* Replaces the reference material (Sec. 4.1, Eq. Kref; m x m, host, symmetric positive definite) of
+ * the context, e.g. when the tangent of a nonlinear problem changes (the reassembly of Sec. 5 before
+ * Algorithm 2).  Call fehom_precond_build before the next solve (FEHOM_E_STATE otherwise). */
+fehom_status fehom_set_reference(fehom_ctx* ctx, const double* C_ref);
+
+/* Newton's method of Algorithm 1 for a nonlinear conductivity (FEHOM_SCALAR on FEHOM_HEX8_3D):
+ * the nonlinear system D^T W q(e + D u) = 0 (Sec. 3) with the per-phase law
+ *     q(g) = k_p s^((n_p - 1) / 2) g,  s = 1 + |g|^2 / g0^2,
+ * k_p from the context's (isotropic) phase conductivities, n_p = power_n[p] > 0 (n_p = 1: linear).
+ * Each Newton step evaluates flux and tangent at the 2 x 2 x 2 Gauss points (FP64), sets the reference
+ * material to the volume mean of the tangent and rebuilds the preconditioner (Algorithm 2), solves
+ * K_t delta = -R with PCG to the relative K_ref^-1-norm tolerance tol_cg, updates u and stops when
+ * ||D delta|| <= eta_nw ||D u|| (Sec. 6, termination criteria), after at most max_newton (<= 32) steps.
+ * e: host, 3 entries.  fluct_out: NULL, or N doubles (device when fluct_on_device, else host) that
+ * receive the mean-zero fluctuation.  mean_flux_out: host, 3 entries, or NULL.  info: host, filled.
+ * Leaves the context's reference material at the last tangent mean.  FEHOM_E_NOT_CONVERGED when the
+ * Newton test did not pass within max_newton steps (outputs are still written). */
+typedef struct {
+  int newton_iterations;  /* Newton steps taken */
+  int pcg_iterations;     /* PCG iterations over all steps */
+  int converged;          /* 1 when the Newton test passed */
+  int n_hist;             /* entries of the histories below */
+  double residual[32];    /* ||R(u_k)||_2 at the start of step k */
+  double increment[32];   /* ||D delta_k|| / ||D u_{k+1}|| of step k */
+  int pcg_per_step[32];   /* PCG iterations of step k */
+} fehom_newton_info;
+fehom_status fehom_newton_solve(fehom_ctx* ctx, const double* e, const double* power_n, double g0, double tol_cg,
+                                double eta_nw, int max_newton, double* fluct_out, int fluct_on_device,
+                                double* mean_flux_out, fehom_newton_info* info);
+
 /* Energy form of the effective tensor of the last fehom_solve whose n_loads == m loads were linearly
  * independent and which asked for C_eff: with fields x_l, right-hand sides b_l and true residuals
  * r_l = b_l - K x_l, the energies sum_Q w_Q (e_i + D x_i)^T C (e_j + D x_j) = e_i^T C_eff e_j |Y|

@@ -15,7 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfehom.so")
-SOURCES = ["stencil.cu", "fft.cu", "vec.cu", "api.cu", "unet.cu"]
+SOURCES = ["stencil.cu", "fft.cu", "vec.cu", "api.cu", "unet.cu", "newton.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -913,6 +913,205 @@ fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int
   return FEHOM_OK;
 }
 
+fehom_status fehom_set_reference(fehom_ctx* ctx, const double* C_ref) {
+  if (!ctx || !C_ref) return FEHOM_E_INVALID;
+  const int m = ctx->m;
+  if (!spd(C_ref, m)) FAIL(FEHOM_E_INVALID, "C_ref must be symmetric positive definite");
+  cudaStream_t s = ctx->stream;
+  ctx->cref.assign(C_ref, C_ref + (size_t)m * m);
+  std::vector<double> rm((size_t)ctx->D * ctx->D);
+  grad_material(ctx, C_ref, rm.data());
+  CK(cudaMemcpyAsync(ctx->rmats64, rm.data(), rm.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  ctx->iso_ref = false;
+  double lam, mu;
+  if (ctx->iso && iso_elastic(C_ref, 3, &lam, &mu)) {
+    double w, sc[3];
+    kernel_scales(ctx, &w, sc);
+    const double ri[2] = {w * sc[0] * sc[0] * lam, w * sc[0] * sc[0] * mu};
+    if (!ctx->riso64) CK(cudaMalloc(&ctx->riso64, 2 * sizeof(double)));
+    CK(cudaMemcpyAsync(ctx->riso64, ri, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    ctx->iso_ref = true;
+  }
+  CK(cudaStreamSynchronize(s));
+  ctx->built = false;
+  return FEHOM_OK;
+}
+
+// Algorithm 1 (Newton) for the power-law conductivity of nl_element_kernel; linear solves by PCG with
+// the FFT preconditioner of the volume-mean tangent, rebuilt every Newton step (Algorithm 2).
+fehom_status fehom_newton_solve(fehom_ctx* ctx, const double* e, const double* power_n, double g0, double tol_cg,
+                                double eta_nw, int max_newton, double* fluct_out, int fluct_on_device,
+                                double* mean_flux_out, fehom_newton_info* info) {
+  if (!ctx || !e || !power_n || !info) return FEHOM_E_INVALID;
+  if (ctx->physics != FEHOM_SCALAR || ctx->d.elem != HEX8_3D)
+    FAIL(FEHOM_E_INVALID, "fehom_newton_solve: scalar conductivity on FEHOM_HEX8_3D only");
+  if (!(g0 > 0.0) || !(tol_cg > 0.0 && tol_cg < 1.0) || !(eta_nw > 0.0) || max_newton < 1 || max_newton > 32)
+    FAIL(FEHOM_E_INVALID, "need g0 > 0, 0 < tol_cg < 1, eta_nw > 0, 1 <= max_newton <= 32");
+  const int P = ctx->n_phases;
+  std::vector<double> kp(P), np(power_n, power_n + P);
+  for (int p = 0; p < P; ++p) {
+    const double* C = &ctx->moduli[(size_t)p * 9];
+    const bool iso = C[1] == 0 && C[2] == 0 && C[3] == 0 && C[5] == 0 && C[6] == 0 && C[7] == 0 && C[0] == C[4] &&
+                     C[4] == C[8];
+    if (!iso) FAIL(FEHOM_E_INVALID, "fehom_newton_solve: phase conductivities must be isotropic (k I)");
+    if (!(np[p] > 0.0) || !std::isfinite(np[p])) FAIL(FEHOM_E_INVALID, "power_n must be positive");
+    kp[p] = C[0];
+  }
+  std::memset(info, 0, sizeof(*info));
+  cudaStream_t s = ctx->stream;
+  TRY(grow64(ctx, 1));
+  const long long N = ctx->d.N;
+  const int nb = nl_blocks(N), vb = nl_vec_blocks();
+  double *u = nullptr, *T = nullptr, *E = nullptr, *z = nullptr, *dk = nullptr, *dpart = nullptr;
+  struct Free {
+    std::vector<void*> p;
+    ~Free() { for (void* q : p) cudaFree(q); }
+  } guard;
+  auto dalloc = [&](double** q, size_t n) -> cudaError_t {
+    cudaError_t r = cudaMalloc(q, n * sizeof(double));
+    if (r == cudaSuccess) guard.p.push_back(*q);
+    return r;
+  };
+  CK(dalloc(&u, N));
+  CK(dalloc(&T, (size_t)N * 48));
+  CK(dalloc(&E, (size_t)N * 8));
+  CK(dalloc(&z, N));
+  CK(dalloc(&dk, 2 * P));
+  CK(dalloc(&dpart, (size_t)std::max(nb * 9, vb)));
+  CK(cudaMemcpyAsync(dk, kp.data(), P * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dk + P, np.data(), P * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(u, 0, N * sizeof(double), s));
+  NlArgs base{};
+  base.d = ctx->d;
+  for (int i = 0; i < 3; ++i) base.h[i] = ctx->h[i];
+  base.vvox = ctx->vol;
+  base.ids = ctx->ids;
+  base.kp = dk;
+  base.np = dk + P;
+  base.g0 = g0;
+  base.T = T;
+  base.E = E;
+  base.partial = dpart;
+  for (int i = 0; i < 3; ++i) base.e[i] = e[i];
+  const double volY = ctx->vol * (double)N;
+  std::vector<double> hp((size_t)std::max(nb * 9, vb));
+  auto sum_partials = [&](int blocks, int stride, int r, double* out) -> fehom_status {
+    CK(cudaMemcpyAsync(hp.data(), dpart, sizeof(double) * blocks * stride, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double acc = 0.0;
+    for (int b = 0; b < blocks; ++b) acc += hp[(size_t)b * stride + r];
+    *out = acc;
+    return FEHOM_OK;
+  };
+  auto dot = [&](const double* x, const double* y, double* out) -> fehom_status {
+    CK(launch_nl_dot(N, x, y, dpart, s));
+    return sum_partials(vb, 1, 0, out);
+  };
+  auto flux_and_tangent = [&](double* qbar, double* Abar) -> fehom_status {
+    NlArgs a = base;
+    a.x = u;
+    CK(launch_nl_element(a, 0, s));
+    count_launch(ctx);
+    for (int r = 0; r < 3; ++r) TRY(sum_partials(nb, 9, r, &qbar[r]));
+    for (int r = 0; r < 6; ++r) TRY(sum_partials(nb, 9, 3 + r, &Abar[r]));
+    for (int r = 0; r < 3; ++r) qbar[r] /= volY;
+    for (int r = 0; r < 6; ++r) Abar[r] /= volY;
+    return FEHOM_OK;
+  };
+  auto grad_norm2 = [&](const double* x, double* out) -> fehom_status {
+    NlArgs a = base;
+    a.x = x;
+    CK(launch_nl_element(a, 2, s));
+    count_launch(ctx);
+    return sum_partials(nb, 1, 0, out);
+  };
+  auto precond = [&](const double* r, double* zz) -> fehom_status {
+    FftArgs f;
+    fill_dims_args(ctx, f, false, 1);
+    CK(precond_passes<double>(ctx, f, FX_PLAIN, FX_PLAIN, const_cast<double*>(r), nullptr, zz, nullptr, s));
+    return FEHOM_OK;
+  };
+  double qbar[3], Abar[6];
+  for (int it = 0; it < max_newton; ++it) {
+    // residual R(u) = D^T W q(e + D u) (b = -R) and the tangent at u
+    TRY(flux_and_tangent(qbar, Abar));
+    {
+      NlArgs a = base;
+      a.y = ctx->b64;
+      CK(launch_nl_gather(a, -1.0, 0, s));
+      count_launch(ctx);
+    }
+    double bb;
+    TRY(dot(ctx->b64, ctx->b64, &bb));
+    info->residual[it] = std::sqrt(bb);
+    // reference material = volume mean of the tangent; Algorithm 2 again
+    const double Cref[9] = {Abar[0], Abar[5], Abar[4], Abar[5], Abar[1], Abar[3], Abar[4], Abar[3], Abar[2]};
+    TRY(fehom_set_reference(ctx, Cref));
+    TRY(fehom_precond_build(ctx));
+    // PCG on K_t delta = b, delta in x64 (stopping test of Sec. 6, normalised by b)
+    CK(cudaMemsetAsync(ctx->x64, 0, N * sizeof(double), s));
+    CK(cudaMemcpyAsync(ctx->r64, ctx->b64, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TRY(precond(ctx->r64, z));
+    double rz;
+    TRY(dot(ctx->r64, z, &rz));
+    const double bz = rz;
+    int k = 0;
+    if (bz > 0.0) {
+      CK(cudaMemcpyAsync(ctx->p64, z, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      for (k = 1; k <= ctx->opt.max_iter; ++k) {
+        NlArgs a = base;
+        a.x = ctx->p64;
+        CK(launch_nl_element(a, 1, s));
+        a.y = ctx->ap64;
+        CK(launch_nl_gather(a, 1.0, 1, s));
+        count_launch(ctx, 2);
+        double pAp;
+        TRY(sum_partials(nb, 1, 0, &pAp));
+        if (!(pAp > 0.0) || !std::isfinite(pAp)) FAIL(FEHOM_E_BREAKDOWN, "Newton: non-positive curvature in PCG");
+        const double alpha = rz / pAp;
+        CK(launch_nl_axpby(N, alpha, ctx->p64, 1.0, ctx->x64, nullptr, nullptr, s));
+        CK(launch_nl_axpby(N, -alpha, ctx->ap64, 1.0, ctx->r64, nullptr, nullptr, s));
+        TRY(precond(ctx->r64, z));
+        double rz_new;
+        TRY(dot(ctx->r64, z, &rz_new));
+        count_launch(ctx, 3);
+        if (std::sqrt(std::max(rz_new, 0.0)) <= tol_cg * std::sqrt(bz)) break;
+        CK(launch_nl_axpby(N, 1.0, z, rz_new / rz, ctx->p64, nullptr, nullptr, s));
+        count_launch(ctx);
+        rz = rz_new;
+      }
+      if (k > ctx->opt.max_iter) k = ctx->opt.max_iter;
+    }
+    info->pcg_per_step[it] = k;
+    info->pcg_iterations += k;
+    CK(launch_nl_axpby(N, 1.0, ctx->x64, 1.0, u, nullptr, nullptr, s));
+    count_launch(ctx);
+    double dd, uu;
+    TRY(grad_norm2(ctx->x64, &dd));
+    TRY(grad_norm2(u, &uu));
+    const double ratio = uu > 0.0 ? std::sqrt(dd / uu) : 0.0;
+    info->increment[it] = ratio;
+    info->newton_iterations = it + 1;
+    info->n_hist = it + 1;
+    if (ratio <= eta_nw) {
+      info->converged = 1;
+      break;
+    }
+  }
+  // outputs at the final u
+  TRY(flux_and_tangent(qbar, Abar));
+  if (mean_flux_out)
+    for (int r = 0; r < 3; ++r) mean_flux_out[r] = qbar[r];
+  TRY(ensure_partial(ctx, (size_t)ctx->d.c * 2 * 152));
+  CK(launch_sub_mean(u, 1, N, 1, N, ctx->partial, s));
+  count_launch(ctx, 2);
+  if (fluct_out)
+    CK(cudaMemcpyAsync(fluct_out, u, N * sizeof(double), fluct_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       s));
+  CK(cudaStreamSynchronize(s));
+  return info->converged ? FEHOM_OK : FEHOM_E_NOT_CONVERGED;
+}
+
 fehom_status fehom_effective_energy(const fehom_ctx* ctx, double* c_eff) {
   if (!ctx || !c_eff) return FEHOM_E_INVALID;
   if (ctx->c_eff_energy.empty()) return FEHOM_E_STATE;

@@ -214,4 +214,32 @@ cudaError_t launch_pair_dots(const double* x, const double* b, const double* r, 
 cudaError_t launch_galerkin_scale(double* x, const double* kx, const double* b, int n_loads, long long n,
                                   double* partial, cudaStream_t s);
 
+// ------------------------------------------------------------------------------------------------
+// Newton's method for a nonlinear scalar conductivity (hex8, per-Gauss-point tangents, FP64)
+// ------------------------------------------------------------------------------------------------
+struct NlArgs {
+  Dims d;
+  double h[3];          // voxel edges
+  double vvox;          // voxel volume
+  const double* x;      // element kernels: the nodal field; gather: the dot partner
+  double e[3];          // macroscopic gradient (flux mode)
+  const uint8_t* ids;   // phase per voxel (nullptr: phase 0)
+  const double* kp;     // per phase: k
+  const double* np;     // per phase: n
+  double g0;
+  double* T;            // [N][8][6] tangents per Gauss point (xx, yy, zz, yz, xz, xy)
+  double* E;            // [N][8] element contributions per corner
+  double* y;            // gather output [N]
+  double* partial;      // block partials
+};
+int nl_blocks(long long n);
+int nl_vec_blocks();
+// mode 0: flux + tangent at x (partials: sum w q (3), sum w A (6) per block); 1: tangent apply to x;
+// 2: partials of sum w |D x|^2
+cudaError_t launch_nl_element(const NlArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_nl_gather(const NlArgs& a, double scale, int dot, cudaStream_t s);
+cudaError_t launch_nl_axpby(long long n, double alpha, const double* x, double beta, double* y, const double* z,
+                            double* partial, cudaStream_t s);
+cudaError_t launch_nl_dot(long long n, const double* x, const double* y, double* partial, cudaStream_t s);
+
 }  // namespace fehom

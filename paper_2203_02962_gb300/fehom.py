@@ -30,7 +30,7 @@ EXPORTS = ("fehom_default_options", "fehom_setup", "fehom_precond_build", "fehom
            "fehom_get_symbol_inverse", "fehom_mean_flux", "fehom_kernel_times", "fehom_launch_count",
            "fehom_fft_plan", "fehom_mean_flux_noalloc", "fehom_pcg_coefficients", "fehom_eig_bounds",
            "fehom_batch_create", "fehom_solve_batch", "fehom_batch_destroy", "fehom_batch_last_error",
-           "fehom_effective_energy",
+           "fehom_effective_energy", "fehom_set_reference", "fehom_newton_solve",
            # include/fehom_unet.h
            "fehom_unet_create", "fehom_unet_destroy", "fehom_unet_last_error", "fehom_unet_param_count",
            "fehom_unet_set_params", "fehom_unet_get_params", "fehom_unet_predict", "fehom_unet_loss_grad",
@@ -48,6 +48,12 @@ class Options(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("converged", C.c_int),
                 ("rel_residual_M", C.c_double), ("rel_residual_2", C.c_double), ("solve_ms", C.c_double)]
+
+
+class NewtonInfo(C.Structure):
+    _fields_ = [("newton_iterations", C.c_int), ("pcg_iterations", C.c_int), ("converged", C.c_int),
+                ("n_hist", C.c_int), ("residual", C.c_double * 32), ("increment", C.c_double * 32),
+                ("pcg_per_step", C.c_int * 32)]
 
 
 class FehomError(RuntimeError):
@@ -110,6 +116,10 @@ def load_library(path: str = LIB_PATH):
     lib.fehom_batch_last_error.restype = C.c_char_p
     lib.fehom_kernel_times.argtypes = [vp, i, dp, i64p]
     lib.fehom_kernel_times.restype = i
+    lib.fehom_set_reference.argtypes = [vp, dp]
+    lib.fehom_set_reference.restype = i
+    lib.fehom_newton_solve.argtypes = [vp, dp, dp, d, d, d, i, vp, i, dp, C.POINTER(NewtonInfo)]
+    lib.fehom_newton_solve.restype = i
     lib.fehom_effective_energy.argtypes = [vp, dp]
     lib.fehom_effective_energy.restype = i
     lib.fehom_launch_count.argtypes = [vp, i64p]
@@ -295,6 +305,30 @@ class Solver:
                                             C.byref(xy)))
         return {"pairs": p.value, "tc_y": y.value, "tc_last": l.value, "ms": list(ms), "xy_fused": xy.value & 1,
                 "last_reg": (xy.value >> 1) & 1}
+
+    def set_reference(self, C_ref):
+        """Replace the reference material (then call precond_build)."""
+        Cr = np.ascontiguousarray(np.asarray(C_ref, np.float64))
+        self._check(self.lib.fehom_set_reference(self.ctx, _dptr(Cr)))
+
+    def newton_solve(self, e, power_n, g0, tol_cg=1e-10, eta=1e-10, max_newton=32, raise_on_failure=True):
+        """Algorithm 1 for the power-law conductivity (fehom_newton_solve); returns the mean-zero
+        fluctuation (device tensor), the mean flux and the Newton history."""
+        torch = _torch()
+        e = np.ascontiguousarray(np.asarray(e, np.float64))
+        pn = np.ascontiguousarray(np.asarray(power_n, np.float64))
+        out = torch.empty((self.N,), dtype=torch.float64, device="cuda")
+        flux = np.zeros(3)
+        info = NewtonInfo()
+        st = self.lib.fehom_newton_solve(self.ctx, _dptr(e), _dptr(pn), float(g0), float(tol_cg), float(eta),
+                                         int(max_newton), C.c_void_p(out.data_ptr()), 1, _dptr(flux), C.byref(info))
+        if st != 0 and raise_on_failure:
+            self._check(st)
+        n = info.n_hist
+        return dict(status=st, fields=out, mean_flux=flux, newton_iterations=info.newton_iterations,
+                    pcg_iterations=info.pcg_iterations, converged=bool(info.converged),
+                    residual=list(info.residual[:n]), increment=list(info.increment[:n]),
+                    pcg_per_step=list(info.pcg_per_step[:n]))
 
     def effective_energy(self):
         """Energy (Hill-Mandel) form of C_eff from the last solve with m independent loads."""
