@@ -31,7 +31,7 @@ import math
 import numpy as np
 import scipy.sparse as sp
 
-ELEMS = ("p1tri2_2d", "q1_2d", "hex8_3d")
+ELEMS = ("p1tri2_2d", "q1_2d", "hex8_3d", "p1tri4_2d")
 
 
 # ----------------------------------------------------------------------------------------------
@@ -56,6 +56,14 @@ class Grid:
         # local corner ordering: a + 2 b (+ 4 c)
         self.corners = sorted(self.corners, key=lambda t: sum(v << i for i, v in enumerate(t)))
         self.ne = len(self.corners)
+        # two-node stencil (Fig. 3 c): a corner node and a centre node per pixel, four P1 triangles;
+        # the DOF vector is [corner values; centre values] (node type as the outer block, like a
+        # component), scalar physics only
+        self.nn = 2 if elem == "p1tri4_2d" else 1
+        if self.nn == 2:
+            assert physics == "scalar"
+            self.c = 2              # DOF blocks of N values (node types)
+            self.ne = 5             # element DOFs: 4 corners + centre
 
     def node_index(self, ijk):
         """Flat node index of integer coordinates (tuple of arrays, x first), wrapped periodically."""
@@ -70,14 +78,17 @@ class Grid:
         """(N_elem, n_e) array: global node of each local corner of each voxel."""
         coords = np.meshgrid(*[np.arange(n) for n in self.n_xyz], indexing="ij")
         base = [c.transpose(*range(self.dim)[::-1]).ravel() for c in coords]  # x-fastest flattening
-        out = np.empty((self.N, self.ne), dtype=np.int64)
+        out = np.empty((self.N, len(self.corners)), dtype=np.int64)
         for a, off in enumerate(self.corners):
             out[:, a] = self.node_index([base[ax] + off[ax] for ax in range(self.dim)])
         return out
 
     def element_dofs(self):
-        """(N_elem, c * n_e) DOF map, element DOF order (component j, corner a) -> j * n_e + a."""
+        """(N_elem, c * n_e) DOF map, element DOF order (component j, corner a) -> j * n_e + a.
+        Two-node stencil: the 4 corner DOFs then the pixel's centre DOF (N + pixel)."""
         nodes = self.element_nodes()
+        if self.nn == 2:
+            return np.concatenate([nodes, self.N + np.arange(self.N)[:, None]], axis=1)
         return np.concatenate([j * self.N + nodes for j in range(self.c)], axis=1)
 
 
@@ -95,7 +106,18 @@ def quadrature(grid: Grid):
     """List of (dN, w) per quadrature point of one voxel: dN is (d, n_e) = dphi_a/dx_beta."""
     h, d = grid.h, grid.dim
     pts = []
-    if grid.elem == "p1tri2_2d":
+    if grid.elem == "p1tri4_2d":
+        # Fig. 3 c: triangles (edge, centre) for the bottom, right, top and left edges, w = V_p / 4
+        corner_xy = {off: np.array(off, dtype=float) * h for off in grid.corners}
+        centre = 0.5 * h
+        for e0, e1 in (((0, 0), (1, 0)), ((1, 0), (1, 1)), ((1, 1), (0, 1)), ((0, 1), (0, 0))):
+            g = _p1_gradients(np.array([corner_xy[e0], corner_xy[e1], centre]))
+            dN = np.zeros((2, 5))
+            dN[:, grid.corners.index(e0)] = g[:, 0]
+            dN[:, grid.corners.index(e1)] = g[:, 1]
+            dN[:, 4] = g[:, 2]
+            pts.append((dN, grid.vp / 4.0))
+    elif grid.elem == "p1tri2_2d":
         corner_xy = {off: np.array(off, dtype=float) * h for off in grid.corners}
         for tri in (((0, 0), (1, 0), (1, 1)), ((0, 0), (1, 1), (0, 1))):
             g = _p1_gradients(np.array([corner_xy[t] for t in tri]))

@@ -81,7 +81,10 @@ def apply_precond(grid: fem.Grid, K_inv_hat, r):
 # linear solvers
 # ----------------------------------------------------------------------------------------------
 def constant_modes(grid: fem.Grid):
-    """Z: (c N, c) indicator columns of the constants per component (kernel of K)."""
+    """Z: indicator columns of the constants per physical component (kernel of K): (c N, c), or for
+    the two-node stencil the single column of ones (every node of the field at the same value)."""
+    if getattr(grid, "nn", 1) == 2:
+        return np.ones((grid.c * grid.N, 1))
     Z = np.zeros((grid.c * grid.N, grid.c))
     for j in range(grid.c):
         Z[j * grid.N:(j + 1) * grid.N, j] = 1.0
@@ -90,6 +93,8 @@ def constant_modes(grid: fem.Grid):
 
 def project_mean_zero(grid: fem.Grid, u):
     u = np.array(u, dtype=float, copy=True)
+    if getattr(grid, "nn", 1) == 2:
+        return u - u.mean()
     for j in range(grid.c):
         u[j * grid.N:(j + 1) * grid.N] -= u[j * grid.N:(j + 1) * grid.N].mean()
     return u
@@ -99,7 +104,7 @@ def solve_dense(grid: fem.Grid, K, b):
     """Mean-zero solution of K u = b from the dense bordered system (tiny grids only)."""
     Kd = K.toarray() if sp.issparse(K) else np.asarray(K)
     Z = constant_modes(grid)
-    n, c = Kd.shape[0], grid.c
+    n, c = Kd.shape[0], Z.shape[1]
     A = np.zeros((n + c, n + c))
     A[:n, :n], A[:n, n:], A[n:, :n] = Kd, Z, Z.T
     rhs = np.concatenate([b, np.zeros(c)])
@@ -111,7 +116,7 @@ def solve_sparse(grid: fem.Grid, K, b):
     import scipy.sparse.linalg as spla
     Z = sp.csr_matrix(constant_modes(grid))
     A = sp.bmat([[K, Z], [Z.T, None]], format="csc")
-    rhs = np.concatenate([b, np.zeros(grid.c)])
+    rhs = np.concatenate([b, np.zeros(Z.shape[1])])
     return spla.spsolve(A, rhs)[: K.shape[0]]
 
 

@@ -459,3 +459,74 @@ def test_energy_bilinear_form_pins():
         d = fem.energy(g, ids, mod, loads[2], u[2] + eps * v, loads[2], u[2] + eps * v) \
             - fem.energy(g, ids, mod, loads[2], u[2], loads[2], u[2])
         assert abs(d - eps * eps * v @ (K @ v)) < 1e-9 * max(1.0, eps * eps * abs(v @ (K @ v)))
+
+
+# ------------------------------------------------------------------------------------------------
+# two-node stencil (Fig. 3 c): corner + centre node per pixel, four P1 triangles
+# ------------------------------------------------------------------------------------------------
+def test_two_node_stencil_element_patch_test():
+    """Every triangle reproduces the gradient of a linear field sampled at its corner and centre
+    nodes exactly; the four weights sum to the pixel area."""
+    g = fem.Grid((3, 4), "p1tri4_2d", "scalar")
+    a = np.array([0.7, -1.3])
+    hx, hy = g.h
+    pos = {0: (0, 0), 1: (hx, 0), 2: (0, hy), 3: (hx, hy), 4: (hx / 2, hy / 2)}
+    ve = np.array([a @ np.array(pos[i]) for i in range(5)])
+    qp = fem.quadrature(g)
+    assert len(qp) == 4 and abs(sum(w for _, w in qp) - g.vp) < 1e-15
+    for dN, w in qp:
+        assert np.allclose(dN @ ve, a, atol=1e-12)
+
+
+def test_two_node_stencil_operator_and_rhs():
+    g = fem.Grid((4, 6), "p1tri4_2d", "scalar")
+    rng = np.random.default_rng(31)
+    ids = rng.integers(0, 2, g.N)
+    mod = [_rand_spd(2, 60, 1.0), _rand_spd(2, 61, 8.0)]
+    K = fem.assemble_K(g, ids, mod)
+    assert K.shape == (2 * g.N, 2 * g.N)
+    assert abs(K - K.T).max() < 1e-13
+    assert np.abs(K @ np.ones(2 * g.N)).max() < 1e-12          # one null vector: the constants
+    ev = np.linalg.eigvalsh(K.toarray())
+    assert (ev < 1e-10 * ev.max()).sum() == 1
+    # homogeneous material: the constant flux has zero divergence, b = 0
+    Kh = fem.assemble_rhs(g, np.zeros(g.N, int), [mod[1]], np.array([1.0, -0.5]))
+    assert np.abs(Kh).max() < 1e-13
+
+
+def test_two_node_stencil_laminate_exact():
+    g = fem.Grid((4, 8), "p1tri4_2d", "scalar")
+    layer = (np.arange(8) >= 3).astype(int)
+    ids = np.broadcast_to(layer, (4, 8)).ravel()
+    k = [1.0, 9.0]
+    mod = [kk * np.eye(2) for kk in k]
+    r = solvers.homogenise(g, ids, mod, np.eye(2), method="sparse")
+    f = np.array([3 / 8, 5 / 8])
+    harm = 1.0 / (f[0] / k[0] + f[1] / k[1])
+    arith = f[0] * k[0] + f[1] * k[1]
+    assert abs(r["C_eff"][0, 0] - harm) < 1e-12 and abs(r["C_eff"][1, 1] - arith) < 1e-12
+    assert abs(r["C_eff"][0, 1]) < 1e-12 and abs(r["C_eff"][1, 0]) < 1e-12
+
+
+def test_two_node_stencil_symbol_and_pseudo_inverse():
+    """Algorithm 2 on the two-node stencil: Hermitian 2 x 2 blocks; the k = 0 block has exactly one
+    null eigenvalue (d N_n = 2 blocks, d = 1 rigid mode) and needs a true pseudo-inverse; every
+    other block is invertible; with C_ref = C PCG converges in one iteration."""
+    g = fem.Grid((6, 8), "p1tri4_2d", "scalar")
+    C = _rand_spd(2, 62, 3.0)
+    Kh = solvers.kref_symbol(g, C)
+    blocks = np.moveaxis(Kh.reshape(2, 2, -1), 2, 0)
+    assert np.abs(blocks - np.conj(np.swapaxes(blocks, 1, 2))).max() < 1e-12 * np.abs(blocks).max()
+    assert np.abs(blocks[:, 0, 1].imag).max() > 1e-3 * np.abs(blocks).max()   # the centre coupling is complex
+    ev0 = np.linalg.eigvalsh(blocks[0])
+    assert abs(ev0[0]) < 1e-12 * np.abs(blocks).max() and ev0[1] > 1e-3 * np.abs(blocks).max()
+    evs = np.linalg.eigvalsh(blocks[1:])
+    assert evs.min() > 1e-6 * np.abs(blocks).max()
+    Kinv = solvers.kref_pinv_symbol(Kh)
+    P0 = Kinv[:, :, 0, 0] @ Kh[:, :, 0, 0]
+    assert np.allclose(P0, np.array([[0.5, -0.5], [-0.5, 0.5]]), atol=1e-12)   # projector off the constants
+    K = fem.assemble_K(g, np.zeros(g.N, int), [C])
+    rng = np.random.default_rng(5)
+    b = solvers.project_mean_zero(g, rng.standard_normal(2 * g.N))
+    res = solvers.pcg(lambda v: K @ v, lambda v: solvers.apply_precond(g, Kinv, v), b, 1e-12)
+    assert res["iters"] == 1
