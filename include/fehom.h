@@ -55,7 +55,13 @@ typedef enum {
 typedef enum {
   FEHOM_P1TRI2_2D = 1, /* two linear triangles per pixel, split along (0,0)-(1,1), 1 QP each (Fig. 3 b) */
   FEHOM_HEX8_3D = 2,   /* trilinear hexahedron, 2x2x2 Gauss points (3-D analogue of Fig. 3 a) */
-  FEHOM_Q1_2D = 3      /* bilinear quadrilateral, 2x2 Gauss points (Fig. 3 a) */
+  FEHOM_Q1_2D = 3,     /* bilinear quadrilateral, 2x2 Gauss points (Fig. 3 a) */
+  FEHOM_P1TRI4_2D = 4  /* two-node stencil (Fig. 3 c, N_n = 2): a corner node and a pixel-centre node per
+                          pixel, four linear triangles (edge, centre) with one point each, w = V_p/4;
+                          FEHOM_SCALAR only.  Fields have c = 2 blocks of N values: corner nodes
+                          (node i + n_x j), then pixel centres (pixel i + n_x j).  The Fourier blocks are
+                          Hermitian 2 x 2 (fehom_get_symbol_inverse: entries 00, 11, Re 01, Im 01); the
+                          constant over both node types is the single null mode, removed from fields */
 } fehom_elem;
 
 typedef enum { FEHOM_SCALAR = 1, FEHOM_ELASTIC = 2 } fehom_physics;

@@ -174,7 +174,7 @@ void kernel_scales(const fehom_ctx* ctx, double* w, double s[3]) {
     else if (ctx->d.elem == Q1_2D) s[i] = 1.0 / (2.0 * ctx->h[i]);     // (2/h) / 4
     else s[i] = 1.0 / ctx->h[i];                                       // raw differences of P1
   }
-  *w = (ctx->d.elem == P1TRI2_2D) ? 0.5 * ctx->vol : ctx->vol;
+  *w = (ctx->d.elem == P1TRI2_2D) ? 0.5 * ctx->vol : (ctx->d.elem == P1TRI4_2D ? 0.25 * ctx->vol : ctx->vol);
 }
 
 // Chat = w S P^T C P S  (D x D) for one material C (m x m)
@@ -287,9 +287,18 @@ void fill_dims_args(fehom_ctx* ctx, FftArgs& f, bool fp32, int n_loads) {
   f.pairs = pl.pairs;
   f.tc_y = pl.tc_y;
   f.tc_last = pl.tc_last;
+  f.herm = ctx->d.elem == P1TRI4_2D ? 1 : 0;
   f.xy = (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.xy)) && fft_xy_supported(ctx->d, fp32) ? 1 : 0;
   f.last_reg =
       (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.last_reg)) && fft_last128_supported(ctx->d, fp32) ? 1 : 0;
+}
+
+// Removes the constant null mode from every load's field: the mean of each component, or for the
+// two-node stencil the common mean of all nodes of both types (its only null mode).
+cudaError_t sub_mean_fields(fehom_ctx* ctx, double* x, int n_loads, cudaStream_t s) {
+  const long long cN = (long long)ctx->d.c * ctx->d.N;
+  if (ctx->d.elem == P1TRI4_2D) return launch_sub_mean(x, 1, cN, n_loads, cN, ctx->partial, s);
+  return launch_sub_mean(x, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s);
 }
 
 StencilArgs stencil_args(fehom_ctx* ctx, bool fp32, int n_loads) {
@@ -822,6 +831,7 @@ fehom_status fehom_pcg_coefficients(fehom_ctx* ctx, int load, int capacity, doub
 fehom_status fehom_eig_bounds(fehom_ctx* ctx, double* lo_values, int64_t* lo_counts, int* n_lo, double* hi_values,
                               int64_t* hi_counts, int* n_hi) {
   if (!ctx || !lo_values || !lo_counts || !n_lo || !hi_values || !hi_counts || !n_hi) return FEHOM_E_INVALID;
+  if (ctx->d.elem == P1TRI4_2D) FAIL(FEHOM_E_INVALID, "fehom_eig_bounds: not available for the two-node stencil");
   const int m = ctx->m, P = ctx->n_phases;
   // extreme generalized eigenvalues of (C_p, C_ref): eigenvalues of L^-1 C_p L^-T with C_ref = L L^T
   std::vector<double> L((size_t)m * m, 0.0);
@@ -1165,7 +1175,10 @@ static fehom_status setup_impl(fehom_ctx* ctx, int elem, int physics, const int6
   else fehom_default_options(&ctx->opt);
   if (ctx->opt.max_iter <= 0) ctx->opt.max_iter = 10000;
   if (!(ctx->opt.inner_tol > 0.0 && ctx->opt.inner_tol < 1.0)) ctx->opt.inner_tol = 1e-3;
-  if (elem != FEHOM_P1TRI2_2D && elem != FEHOM_HEX8_3D && elem != FEHOM_Q1_2D) FAIL(FEHOM_E_INVALID, "unknown element type");
+  if (elem != FEHOM_P1TRI2_2D && elem != FEHOM_HEX8_3D && elem != FEHOM_Q1_2D && elem != FEHOM_P1TRI4_2D)
+    FAIL(FEHOM_E_INVALID, "unknown element type");
+  if (elem == FEHOM_P1TRI4_2D && physics != FEHOM_SCALAR)
+    FAIL(FEHOM_E_INVALID, "the two-node stencil FEHOM_P1TRI4_2D is built for FEHOM_SCALAR only");
   if (physics != FEHOM_SCALAR && physics != FEHOM_ELASTIC) FAIL(FEHOM_E_INVALID, "unknown physics");
   if (!n || !phase_ids || !phase_moduli) FAIL(FEHOM_E_INVALID, "NULL argument");
   if (n_phases < 1 || n_phases > kMaxPhases) FAIL(FEHOM_E_INVALID, "n_phases must be in 1..256");
@@ -1182,10 +1195,11 @@ static fehom_status setup_impl(fehom_ctx* ctx, int elem, int physics, const int6
   ctx->d.N = (long long)ctx->d.nx * ctx->d.ny * ctx->d.nz;
   ctx->d.Nh = (long long)ctx->d.nxh * ctx->d.ny * ctx->d.nz;
   ctx->d.c = physics == FEHOM_SCALAR ? 1 : dim;
+  if (elem == FEHOM_P1TRI4_2D) ctx->d.c = 2;  // field blocks = node types (corner, centre)
   ctx->d.elem = elem;
   ctx->physics = physics;
   ctx->m = physics == FEHOM_SCALAR ? dim : dim * (dim + 1) / 2;
-  ctx->D = ctx->d.c * dim;
+  ctx->D = (physics == FEHOM_SCALAR ? 1 : dim) * dim;
   ctx->vol = 1.0;
   for (int i = 0; i < 3; ++i) {
     const double l = (cell && i < dim) ? cell[i] : 1.0;
@@ -1378,7 +1392,8 @@ fehom_status fehom_precond_build(fehom_ctx* ctx) {
   count_launch(ctx);
   // per-wavevector inverse
   const long long Nh = ctx->d.Nh;
-  const int ne = c * (c + 1) / 2;
+  const bool herm = ctx->d.elem == P1TRI4_2D;
+  const int ne = herm ? 4 : c * (c + 1) / 2;
   if (!ctx->sym64) {
     CK(cudaMalloc(&ctx->sym64, sizeof(double) * ne * Nh));
     CK(cudaMalloc(&ctx->sym32, sizeof(float) * ne * Nh));
@@ -1391,6 +1406,7 @@ fehom_status fehom_precond_build(fehom_ctx* ctx) {
   sa.sym32 = ctx->sym32;
   sa.partial = ctx->partial;
   sa.zero_tol = 1e-12;
+  sa.herm = herm ? 1 : 0;
   int blocks = 0;
   CK(launch_symbol_build(sa, &blocks, s));
   count_launch(ctx);
@@ -1412,7 +1428,8 @@ fehom_status fehom_precond_build(fehom_ctx* ctx) {
   }
   char msg[256];
   if (!(mx_abs > 0) || mx_im > 1e-9 * mx_abs || mx_asym > 1e-9 * mx_abs) {
-    std::snprintf(msg, sizeof msg, "reference symbol not real symmetric: max|Im| %.3e, asym %.3e, max %.3e", mx_im,
+    std::snprintf(msg, sizeof msg, "reference symbol not real symmetric (Hermitian for the two-node stencil): "
+                  "max|Im| %.3e, asym %.3e, max %.3e", mx_im,
                   mx_asym, mx_abs);
     FAIL(FEHOM_E_INVALID, msg);
   }
@@ -1435,9 +1452,9 @@ fehom_status fehom_precond_build(fehom_ctx* ctx) {
   const int pi2[3][2] = {{0, 0}, {1, 1}, {0, 1}};
   const double invN = 1.0 / (double)ctx->d.N;
   for (int e = 0; e < ne; ++e) {
-    const int i = c == 3 ? pi3[e][0] : (c == 2 ? pi2[e][0] : 0);
-    const int j = c == 3 ? pi3[e][1] : (c == 2 ? pi2[e][1] : 0);
-    const double v = pinv[i * c + j] * invN;
+    const int i = c == 3 ? pi3[e][0] : (c == 2 ? pi2[std::min(e, 2)][0] : 0);
+    const int j = c == 3 ? pi3[e][1] : (c == 2 ? pi2[std::min(e, 2)][1] : 0);
+    const double v = (herm && e == 3) ? 0.0 : pinv[i * c + j] * invN;  // Im of the k = 0 block: 0
     const float vf = (float)v;
     CK(cudaMemcpyAsync(ctx->sym64 + (long long)e * Nh, &v, sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->sym32 + (long long)e * Nh, &vf, sizeof(float), cudaMemcpyHostToDevice, s));
@@ -1481,7 +1498,7 @@ fehom_status fehom_apply_precond(fehom_ctx* ctx, const void* r, void* z, int pre
 fehom_status fehom_get_symbol_inverse(fehom_ctx* ctx, double* out) {
   if (!ctx || !out) return FEHOM_E_INVALID;
   if (!ctx->built) FAIL(FEHOM_E_STATE, "fehom_get_symbol_inverse before fehom_precond_build");
-  const int ne = ctx->d.c * (ctx->d.c + 1) / 2;
+  const int ne = ctx->d.elem == P1TRI4_2D ? 4 : ctx->d.c * (ctx->d.c + 1) / 2;
   CK(cudaMemcpyAsync(out, ctx->sym64, sizeof(double) * ne * ctx->d.Nh, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return FEHOM_OK;
@@ -1632,7 +1649,7 @@ static fehom_status finish_outputs(fehom_ctx* ctx, int n_loads, const double* lo
   ctx->c_eff_energy.clear();
   if (c_eff_out && n_loads == ctx->m) TRY(energy_c_eff(ctx, n_loads, loads, res));
   TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
-  CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
+  CK(sub_mean_fields(ctx, ctx->x64, n_loads, s));
   count_launch(ctx, 2);
   if (mean_flux_out) std::memcpy(mean_flux_out, flux.data(), flux.size() * sizeof(double));
   if (c_eff_out && n_loads == ctx->m) {
@@ -1732,7 +1749,7 @@ struct SolveRun {
       if (x0) {
         CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
         TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
-        CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
+        CK(sub_mean_fields(ctx, ctx->x64, n_loads, s));
         count_launch(ctx, 2);
         TRY(scale_warm_start(ctx, n_loads));
       } else {
@@ -1752,7 +1769,7 @@ struct SolveRun {
       CK(cudaStreamSynchronize(s));
       CK(cudaMemcpyAsync(ctx->x64, x0, sizeof(double) * cN * n_loads, cudaMemcpyDeviceToDevice, s));
       TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
-      CK(launch_sub_mean(ctx->x64, ctx->d.c, ctx->d.N, n_loads, cN, ctx->partial, s));
+      CK(sub_mean_fields(ctx, ctx->x64, n_loads, s));
       count_launch(ctx, 2);
       TRY(scale_warm_start(ctx, n_loads));
       TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->r64, nullptr, nullptr));

@@ -16,7 +16,7 @@ namespace fehom {
 constexpr int kMaxLoads = 64;      // loads solved as one batch
 constexpr int kMaxPhases = 256;
 
-enum Elem { P1TRI2_2D = 1, HEX8_3D = 2, Q1_2D = 3 };
+enum Elem { P1TRI2_2D = 1, HEX8_3D = 2, Q1_2D = 3, P1TRI4_2D = 4 };  // P1TRI4_2D: two node types per pixel (c = 2 blocks)
 
 struct Dims {
   int dim;        // 2 or 3
@@ -159,6 +159,7 @@ struct FftArgs {
   // launch plan (0 = built-in choice): x-line pairs per CTA (4, 8 or 16), columns per CTA of the y pass
   // and of the last-axis pass (2, 4, 8 or 16)
   int pairs, tc_y, tc_last;
+  int herm;      // 1: Hermitian 2 x 2 symbol blocks (two-node stencil), packed (00, 11, Re 01, Im 01)
   int xy;        // 1: fused x-y passes (launch_fft_xy) in place of the separate x and y passes
   int last_reg;  // 1: register-split last-axis pass (FP32 3-D, nz = 128, c = 1 or 3) with the block solve
 };
@@ -186,6 +187,7 @@ struct SymbolArgs {
   double* diag;      // [4]: max |Im|, max asymmetry, max |K_hat|, min eigenvalue ratio (atomic max/min via partials)
   double* partial;   // [blocks][4]
   double zero_tol;   // relative cut for the k = 0 pseudo-inverse
+  int herm;          // 1: two-node stencil, Hermitian 2 x 2 blocks packed (00, 11, Re 01, Im 01)
 };
 cudaError_t launch_symbol_build(const SymbolArgs& a, int* blocks_out, cudaStream_t s);
 

@@ -501,8 +501,14 @@ __global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, const
       z[0] = mk<C>(k00 * r[0].x, k00 * r[0].y);
     } else if constexpr (NC == 2) {
       const T k00 = sym[ti], k11 = sym[Nh + ti], k01 = sym[2 * Nh + ti];
-      z[0] = mk<C>(fma(k00, r[0].x, k01 * r[1].x), fma(k00, r[0].y, k01 * r[1].y));
-      z[1] = mk<C>(fma(k01, r[0].x, k11 * r[1].x), fma(k01, r[0].y, k11 * r[1].y));
+      if (a.herm) {  // z0 = k00 r0 + k01 r1, z1 = conj(k01) r0 + k11 r1 with complex k01
+        const T k01i = sym[3 * Nh + ti];
+        z[0] = mk<C>(fma(k00, r[0].x, fma(k01, r[1].x, -k01i * r[1].y)), fma(k00, r[0].y, fma(k01, r[1].y, k01i * r[1].x)));
+        z[1] = mk<C>(fma(k11, r[1].x, fma(k01, r[0].x, k01i * r[0].y)), fma(k11, r[1].y, fma(k01, r[0].y, -k01i * r[0].x)));
+      } else {
+        z[0] = mk<C>(fma(k00, r[0].x, k01 * r[1].x), fma(k00, r[0].y, k01 * r[1].y));
+        z[1] = mk<C>(fma(k01, r[0].x, k11 * r[1].x), fma(k01, r[0].y, k11 * r[1].y));
+      }
     } else {
       const T k00 = sym[ti], k11 = sym[Nh + ti], k22 = sym[2 * Nh + ti];
       const T k12 = sym[3 * Nh + ti], k02 = sym[4 * Nh + ti], k01 = sym[5 * Nh + ti];
@@ -1052,6 +1058,58 @@ __global__ void symbol_kernel(SymbolArgs a) {
     for (int i = 0; i < 4; ++i) a.partial[blockIdx.x * 4 + i] = sh[i][0];
 }
 
+// Two-node stencil: the 2 x 2 blocks are Hermitian (the centre node sits half a pixel off the corner
+// grid, so the corner-centre coupling carries a phase).  Per k != 0 the regular inverse
+// [[c, -b], [-conj b, a]] / (a c - |b|^2) of [[a, b], [conj b, c]]; k = 0 is set by the host.
+// Packed (00, 11, Re 01, Im 01) / N.  Diagnostics: |Im| of the diagonal, |K01 - conj K10|.
+__global__ void symbol_herm2_kernel(SymbolArgs a) {
+  const long long Nh = a.d.Nh;
+  const double2* sp = reinterpret_cast<const double2*>(a.spec);
+  const double invN = 1.0 / (double)a.d.N;
+  double mx_im = 0.0, mx_asym = 0.0, mx_abs = 0.0, mn_piv = 1e300;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Nh; k += (long long)gridDim.x * blockDim.x) {
+    const double2 k00 = sp[0 * Nh + k], k11 = sp[3 * Nh + k];
+    const double2 k01 = sp[2 * Nh + k];  // component 0 of the response to the centre impulse
+    const double2 k10 = sp[1 * Nh + k];  // component 1 of the response to the corner impulse
+    mx_im = fmax(mx_im, fmax(fabs(k00.y), fabs(k11.y)));
+    mx_asym = fmax(mx_asym, fmax(fabs(k01.x - k10.x), fabs(k01.y + k10.y)));
+    mx_abs = fmax(mx_abs, fmax(fmax(fabs(k00.x), fabs(k11.x)), fmax(hypot(k01.x, k01.y), hypot(k10.x, k10.y))));
+    const double A = k00.x, Cc = k11.x;
+    const double bx = 0.5 * (k01.x + k10.x), by = 0.5 * (k01.y - k10.y);
+    double inv[4] = {0, 0, 0, 0};
+    if (k != 0) {
+      const double det = A * Cc - (bx * bx + by * by);
+      mn_piv = fmin(mn_piv, fmin(A, det / A));
+      inv[0] = Cc / det;
+      inv[1] = A / det;
+      inv[2] = -bx / det;
+      inv[3] = -by / det;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      a.sym64[e * Nh + k] = inv[e] * invN;
+      if (a.sym32) a.sym32[e * Nh + k] = (float)(inv[e] * invN);
+    }
+  }
+  __shared__ double sh[4][256];
+  sh[0][threadIdx.x] = mx_im;
+  sh[1][threadIdx.x] = mx_asym;
+  sh[2][threadIdx.x] = mx_abs;
+  sh[3][threadIdx.x] = mn_piv;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sh[0][threadIdx.x] = fmax(sh[0][threadIdx.x], sh[0][threadIdx.x + s]);
+      sh[1][threadIdx.x] = fmax(sh[1][threadIdx.x], sh[1][threadIdx.x + s]);
+      sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + s]);
+      sh[3][threadIdx.x] = fmin(sh[3][threadIdx.x], sh[3][threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 4; ++i) a.partial[blockIdx.x * 4 + i] = sh[i][0];
+}
+
 template <typename K>
 cudaError_t set_smem(K kern, size_t bytes) {
   if (bytes > 32 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -1243,7 +1301,8 @@ template cudaError_t launch_fft_last_solve<float>(const FftArgs&, cudaStream_t);
 cudaError_t launch_symbol_build(const SymbolArgs& a, int* blocks_out, cudaStream_t s) {
   const int blocks = (int)std::min<long long>(2 * 152, (a.d.Nh + 255) / 256);
   *blocks_out = blocks;
-  if (a.d.c == 1) symbol_kernel<1><<<blocks, 256, 0, s>>>(a);
+  if (a.herm) symbol_herm2_kernel<<<blocks, 256, 0, s>>>(a);
+  else if (a.d.c == 1) symbol_kernel<1><<<blocks, 256, 0, s>>>(a);
   else if (a.d.c == 2) symbol_kernel<2><<<blocks, 256, 0, s>>>(a);
   else symbol_kernel<3><<<blocks, 256, 0, s>>>(a);
   return cudaGetLastError();

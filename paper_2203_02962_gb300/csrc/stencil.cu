@@ -700,6 +700,126 @@ __global__ void __launch_bounds__(NT2) pixel_apply_kernel(StencilArgs a) {
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Two-node stencil (Fig. 3 c, P1TRI4_2D, scalar): per pixel a corner node (type 0, field block 0)
+// and a centre node (type 1, block 1), four P1 triangles (edge, centre) with w = V_p / 4 each.
+// Scaled gradients G = (h_x g_x, h_y g_y) of the bottom, right, top and left triangles:
+//   b: (u10 - u00, 2 uO - u00 - u10)   r: (u10 + u11 - 2 uO, u11 - u10)
+//   t: (u11 - u01, u01 + u11 - 2 uO)   l: (2 uO - u00 - u01, u01 - u00)
+// dual t_T = Chat G_T + tau (Chat = w S C S, S = diag(1 / h)), forces f_a = sum_T (dG_T / du_a) . t_T.
+// ------------------------------------------------------------------------------------------------
+template <typename T, bool HAS_E>
+__device__ __forceinline__ void pixel4_element(const T (&u)[4], T uO, const T* __restrict__ Ch,
+                                               const double* __restrict__ tau, T (&f)[4], T& fO, T (&t1o)[2]) {
+  const T G[4][2] = {{u[1] - u[0], T(2) * uO - u[0] - u[1]},
+                     {u[1] + u[3] - T(2) * uO, u[3] - u[1]},
+                     {u[3] - u[2], u[2] + u[3] - T(2) * uO},
+                     {T(2) * uO - u[0] - u[2], u[2] - u[0]}};
+  const T c00 = __ldg(Ch + 0), c01 = __ldg(Ch + 1), c10 = __ldg(Ch + 2), c11 = __ldg(Ch + 3);
+  T t[4][2];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    t[q][0] = fma(c00, G[q][0], c01 * G[q][1]);
+    t[q][1] = fma(c10, G[q][0], c11 * G[q][1]);
+    if constexpr (HAS_E) {
+      t[q][0] += T(tau[0]);
+      t[q][1] += T(tau[1]);
+    }
+  }
+  t1o[0] = t[0][0] + t[1][0] + t[2][0] + t[3][0];
+  t1o[1] = t[0][1] + t[1][1] + t[2][1] + t[3][1];
+  // corners 0 = (0,0), 1 = (1,0), 2 = (0,1), 3 = (1,1)
+  f[0] = -t[0][0] - t[0][1] - t[3][0] - t[3][1];
+  f[1] = t[0][0] - t[0][1] + t[1][0] - t[1][1];
+  f[3] = t[1][0] + t[1][1] + t[2][0] + t[2][1];
+  f[2] = -t[2][0] + t[2][1] - t[3][0] + t[3][1];
+  fO = T(2) * (t[0][1] - t[1][0] - t[2][1] + t[3][0]);
+}
+
+template <typename T, bool HAS_X, bool HAS_E, int RED>
+__global__ void __launch_bounds__(NT2) pixel4_apply_kernel(StencilArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* pl = reinterpret_cast<T*>(smem_raw);  // [2 types][PY2][PX]: corner nodes, pixel centres
+  T* F = pl + 2 * PY2 * PX;                // [5][EY2][EX]: forces on the 4 corners and the centre
+  __shared__ double red_sh[32];
+  const Dims d = a.d;
+  const int load = blockIdx.z;
+  if (RED == RED_PCG && a.st != nullptr && a.st[load].state != ST_RUN) return;
+  const int tiles_x = (d.nx + BX - 1) / BX;
+  const int i0 = (blockIdx.x % tiles_x) * BX;
+  const int j0 = (blockIdx.x / tiles_x) * BY2;
+  const int tid = threadIdx.x;
+  const T* x = HAS_X ? reinterpret_cast<const T*>(a.x) + (long long)load * a.load_stride : nullptr;
+  T* y = reinterpret_cast<T*>(a.y) + (long long)load * a.load_stride;
+  const T* mats = reinterpret_cast<const T*>(a.mats);
+  const double* tau = HAS_E ? a.tau + (long long)load * a.n_phases * 2 : nullptr;
+  if (HAS_X) {
+    for (int idx = tid; idx < 2 * PY2 * PX; idx += NT2) {
+      const int px = idx % PX, py = (idx / PX) % PY2, j = idx / (PX * PY2);
+      pl[idx] = x[(long long)j * d.N + (long long)wrap(j0 - 1 + py, d.ny) * d.nx + wrap(i0 - 1 + px, d.nx)];
+    }
+  }
+  __syncthreads();
+  const int ei = tid % EX, ej = tid / EX;
+  double acc_t[2] = {0.0, 0.0};
+  if (tid < NE2) {
+    // element (ei, ej) = pixel (i0 - 1 + ei, j0 - 1 + ej): corners (ei + a, ej + b), centre (ei, ej) of the tile
+    T u[4], uO = T(0);
+#pragma unroll
+    for (int cn = 0; cn < 4; ++cn) u[cn] = HAS_X ? pl[(ej + (cn >> 1)) * PX + ei + (cn & 1)] : T(0);
+    if (HAS_X) uO = pl[(PY2 + ej) * PX + ei];
+    const int ph = a.ids ? a.ids[(long long)wrap(j0 - 1 + ej, d.ny) * d.nx + wrap(i0 - 1 + ei, d.nx)] : 0;
+    T f[4], fO, t1[2];
+    pixel4_element<T, HAS_E>(u, uO, mats + (long long)ph * 4, HAS_E ? tau + ph * 2 : nullptr, f, fO, t1);
+#pragma unroll
+    for (int cn = 0; cn < 4; ++cn) F[(cn * EY2 + ej) * EX + ei] = f[cn];
+    F[(4 * EY2 + ej) * EX + ei] = fO;
+    if ((RED == RED_STATS || RED == RED_SUMS) && ei >= 1 && ej >= 1 && i0 + ei - 1 < d.nx && j0 + ej - 1 < d.ny) {
+      acc_t[0] += (double)t1[0];
+      acc_t[1] += (double)t1[1];
+    }
+  }
+  __syncthreads();
+  DotAcc<T> acc_p;
+  double acc_y = 0.0;
+  const int ni = tid % BX, nj = tid / BX;
+  if (tid < BX * BY2 && i0 + ni < d.nx && j0 + nj < d.ny) {
+    // corner node (i0 + ni, j0 + nj): the four pixels around it; centre of pixel (i0 + ni, j0 + nj): element (ni + 1, nj + 1)
+    const T v0 = F[(3 * EY2 + nj) * EX + ni] + F[(2 * EY2 + nj) * EX + ni + 1] + F[(1 * EY2 + nj + 1) * EX + ni] +
+                 F[(0 * EY2 + nj + 1) * EX + ni + 1];
+    const T v1 = F[(4 * EY2 + nj + 1) * EX + ni + 1];
+    const T val0 = T(a.y_scale) * v0, val1 = T(a.y_scale) * v1;
+    const long long g = (long long)(j0 + nj) * d.nx + i0 + ni;
+    if (RED != RED_SUMS) {
+      y[g] = val0;
+      y[d.N + g] = val1;
+    }
+    if (RED == RED_PCG) {
+      acc_p.add(val0, pl[(nj + 1) * PX + ni + 1]);
+      acc_p.add(val1, pl[(PY2 + nj + 1) * PX + ni + 1]);
+    }
+    if ((RED == RED_STATS || RED == RED_SUMS)) acc_y += (double)val0 * (double)val0 + (double)val1 * (double)val1;
+  }
+  if (RED == RED_PCG) {
+    const double part = block_sum(acc_p.value(), red_sh);
+    double total;
+    if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load,
+                         gridDim.x, blockIdx.x, red_sh, &total)) {
+      if (threadIdx.x == 0)
+        pcg_alpha_update(a.st[load], total, a.red.hist ? a.red.hist + (long long)load * 2 * kHist : nullptr);
+    }
+  }
+  if ((RED == RED_STATS || RED == RED_SUMS)) {
+    double* out = a.stats + ((long long)load * gridDim.x + blockIdx.x) * 3;
+    const double ty = block_sum(acc_y, red_sh);
+    if (threadIdx.x == 0) out[0] = ty;
+    for (int i = 0; i < 2; ++i) {
+      const double t = block_sum(acc_t[i], red_sh);
+      if (threadIdx.x == 0) out[1 + i] = t;
+    }
+  }
+}
+
 template <typename K>
 cudaError_t set_smem(K kern, size_t bytes) {
   if (bytes > 32 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -728,6 +848,21 @@ cudaError_t launch_hex8_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   dim3 grid(tiles, slabs, a.n_loads);
   kern<<<grid, NT, smem, s>>>(a, kz);
+  return cudaGetLastError();
+}
+
+template <typename T, bool HAS_X, bool HAS_E, int RED>
+cudaError_t launch_pixel4_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
+  const Dims& d = a.d;
+  const int tiles = ((d.nx + BX - 1) / BX) * ((d.ny + BY2 - 1) / BY2);
+  if (ctas) *ctas = tiles;
+  if (RED == RED_PCG && tiles > a.red.max_blocks) return cudaErrorInvalidConfiguration;
+  const size_t smem = sizeof(T) * (2 * PY2 * PX + 5 * EY2 * EX);
+  auto kern = pixel4_apply_kernel<T, HAS_X, HAS_E, RED>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(tiles, 1, a.n_loads);
+  kern<<<grid, NT2, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -791,6 +926,28 @@ cudaError_t dispatch_pixel(const StencilArgs& a, int* ctas, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+template <typename T>
+cudaError_t dispatch_pixel4(const StencilArgs& a, int* ctas, cudaStream_t s) {
+  const bool hx = a.x != nullptr, he = a.tau != nullptr;
+  if (a.st != nullptr) {
+    if (!hx || he) return cudaErrorInvalidValue;
+    return launch_pixel4_t<T, true, false, RED_PCG>(a, ctas, s);
+  }
+  if (a.stats != nullptr && a.y == nullptr) {
+    if (hx && he) return launch_pixel4_t<T, true, true, RED_SUMS>(a, ctas, s);
+    return cudaErrorInvalidValue;
+  }
+  if (a.stats != nullptr) {
+    if (hx && he) return launch_pixel4_t<T, true, true, RED_STATS>(a, ctas, s);
+    if (he) return launch_pixel4_t<T, false, true, RED_STATS>(a, ctas, s);
+    return cudaErrorInvalidValue;
+  }
+  if (hx && he) return launch_pixel4_t<T, true, true, RED_NONE>(a, ctas, s);
+  if (hx) return launch_pixel4_t<T, true, false, RED_NONE>(a, ctas, s);
+  if (he) return launch_pixel4_t<T, false, true, RED_NONE>(a, ctas, s);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 template <typename T>
@@ -804,6 +961,7 @@ cudaError_t launch_stiffness(const StencilArgs& a, cudaStream_t s, int* ctas) {
   if (d.elem == P1TRI2_2D)
     return d.c == 1 ? dispatch_pixel<T, 1, P1TRI2_2D>(a, ctas, s) : dispatch_pixel<T, 2, P1TRI2_2D>(a, ctas, s);
   if (d.elem == Q1_2D) return d.c == 1 ? dispatch_pixel<T, 1, Q1_2D>(a, ctas, s) : dispatch_pixel<T, 2, Q1_2D>(a, ctas, s);
+  if (d.elem == P1TRI4_2D) return dispatch_pixel4<T>(a, ctas, s);
   return cudaErrorInvalidValue;
 }
 

@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfehom.so")
 
-ELEM = {"p1tri2_2d": 1, "hex8_3d": 2, "q1_2d": 3}
+ELEM = {"p1tri2_2d": 1, "hex8_3d": 2, "q1_2d": 3, "p1tri4_2d": 4}
 PHYSICS = {"scalar": 1, "elastic": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
 STATUS = {0: "FEHOM_OK", 1: "FEHOM_E_INVALID", 2: "FEHOM_E_UNSUPPORTED_SIZE", 3: "FEHOM_E_OOM",
@@ -285,7 +285,7 @@ class Solver:
         return z
 
     def symbol_inverse(self):
-        ne = self.c * (self.c + 1) // 2
+        ne = 4 if self.elem == "p1tri4_2d" else self.c * (self.c + 1) // 2
         out = np.zeros(ne * self.Nh)
         self._check(self.lib.fehom_get_symbol_inverse(self.ctx, _dptr(out)))
         return out.reshape(ne, self.n[2], self.n[1], self.nxh)

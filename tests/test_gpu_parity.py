@@ -539,3 +539,62 @@ def test_batch_equals_individual_solves(precision):
     batch.close()
     for sv in single + solvers_b:
         sv.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# two-node stencil (Fig. 3 c): corner + centre node per pixel, four P1 triangles, Hermitian blocks
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(8, 16), (12, 48), (6, 96)])
+def test_two_node_stencil_operators_match_oracle(shape):
+    torch = _torch()
+    g = fem.Grid(shape, "p1tri4_2d", "scalar")
+    rng = np.random.default_rng(sum(shape))
+    ids = rng.integers(0, 3, size=shape).astype(np.uint8)
+    mod = _materials("scalar", 2, "aniso")
+    s = _solver("p1tri4_2d", "scalar", shape, ids, mod)
+    assert s.c == 2
+    K = fem.assemble_K(g, ids.ravel(), mod)
+    x = rng.standard_normal(2 * g.N)
+    for prec, tol in (("fp64", 1e-12), ("mixed", 2e-5)):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        y = s.apply_stiffness(torch.tensor(x, dtype=dt, device="cuda"), prec).double().cpu().numpy()
+        ref = K @ x
+        assert _rel(y, ref) < tol, prec
+    e = np.array([0.8, -0.3])
+    b = s.rhs(e).cpu().numpy()
+    assert _rel(b, fem.assemble_rhs(g, ids.ravel(), mod, e)) < 1e-12
+    s.precond_build()
+    C_ref = fem.mean_material(g, ids.ravel(), mod)
+    Kinv = solvers.kref_pinv_symbol(solvers.kref_symbol(g, C_ref))
+    tab = s.symbol_inverse()[:, 0]                                    # (4, ny, nxh)
+    nxh = g.n_xyz[0] // 2 + 1
+    ref01 = Kinv[0, 1][..., :nxh] / g.N
+    assert _rel(tab[0], Kinv[0, 0].real[..., :nxh] / g.N) < 1e-12
+    assert _rel(tab[1], Kinv[1, 1].real[..., :nxh] / g.N) < 1e-12
+    assert _rel(tab[2] + 1j * tab[3], ref01) < 1e-12
+    r = solvers.project_mean_zero(g, rng.standard_normal(2 * g.N))
+    z_ref = solvers.apply_precond(g, Kinv, r)
+    z = s.apply_precond(torch.tensor(r, device="cuda")).cpu().numpy()
+    assert _rel(z, z_ref) < 1e-12
+    z32 = s.apply_precond(torch.tensor(r, dtype=torch.float32, device="cuda"), "mixed").double().cpu().numpy()
+    assert _rel(z32, z_ref) < 2e-5
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_two_node_stencil_solve_matches_oracle(precision):
+    shape = (32, 32)
+    g = fem.Grid(shape, "p1tri4_2d", "scalar")
+    ids = I.circle2d(32, 0.3)
+    mod = np.stack([I.isotropic_conductivity(1.0, 2), I.isotropic_conductivity(10.0, 2)])
+    ref = solvers.homogenise(g, ids.ravel(), mod, np.eye(2), method="sparse")
+    s = _solver("p1tri4_2d", "scalar", shape, ids, mod, precision=precision)
+    s.precond_build()
+    out = s.solve(np.eye(2), tol=1e-12)
+    tol = 1e-10 if precision == "fp64" else 1e-8
+    assert _rel(out["C_eff"], ref["C_eff"]) < tol
+    u = out["fields"].cpu().numpy().reshape(2, -1)
+    assert np.abs(u - ref["fields"]).max() < (1e-9 if precision == "fp64" else 1e-7) * np.abs(ref["fields"]).max()
+    assert abs(u[0].sum()) < 1e-9  # the common mean of both node types is removed
+    assert all(i["converged"] for i in out["info"])
+    s.close()
