@@ -16,7 +16,7 @@ What is computed (definitions, no blocking or fusion):
 * Sec. 2 (average strain definition) with the quadrature of Eq. global_sum: the volume average of
   flux / stress, <sigma> = (1/|Y|) sum_Q w_Q C_Q (e + (D u)_Q).
 
-Conventions (readings of the paper, listed in the design doc): unit cell [0, 1]^d, grid of n_x x n_y
+Conventions (readings of the paper where it is silent): unit cell [0, 1]^d, grid of n_x x n_y
 (x n_z) nodes, node (i, j, k) at h * (i, j, k), voxel (i, j, k) with corner nodes (i + a, j + b,
 k + c) mod n; node flat index i + n_x (j + n_y k); DOF index comp * N + node (component-blocked,
 the paper's u = [u_1; u_2] ordering of Eq. Du_mat).  Mandel order (11, 22, 12) in 2-D and

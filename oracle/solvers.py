@@ -8,7 +8,7 @@ TEST INFRASTRUCTURE ONLY.  Nothing on the product path imports, links or calls t
   first node of that type, giving the first columns of the blocks K_ref[alpha, beta]; their
   d-dimensional DFTs are the diagonals of the Fourier blocks.  Sec. 5.3, Eq. block_inversion: the
   c x c blocks are inverted one wavevector at a time, with the Moore-Penrose pseudo-inverse at the
-  zero frequency.  DFT convention (a reading): unnormalised forward transform
+  zero frequency.  DFT convention (a reading of the paper): unnormalised forward transform
   exp(-2 pi i k.x / n), inverse with 1/N, so that the block eigenvalues are the DFT of the first
   column (numpy.fft conventions).
 * Sec. 4.2, Eq. M_inverse: K_ref^+ r = F^-1 [K_hat^+ (F r)] per component block.

@@ -361,6 +361,18 @@ __global__ void __launch_bounds__(128, 1) wgrad_tc_kernel(WgradArgs a) {
   tc_fence_after();
   const uint32_t tmem = *slot;
 
+  // 8 x 8 transpose of bf16: in[x] holds channels 0..7 of voxel x; out[c] holds voxels 0..7 of channel c
+  auto transpose8 = [](const uint4 (&in)[8], uint4 (&out)[8]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t w[8] = {(&in[0].x)[k], (&in[1].x)[k], (&in[2].x)[k], (&in[3].x)[k],
+                             (&in[4].x)[k], (&in[5].x)[k], (&in[6].x)[k], (&in[7].x)[k]};
+      out[2 * k] = make_uint4(__byte_perm(w[0], w[1], 0x5410), __byte_perm(w[2], w[3], 0x5410),
+                              __byte_perm(w[4], w[5], 0x5410), __byte_perm(w[6], w[7], 0x5410));
+      out[2 * k + 1] = make_uint4(__byte_perm(w[0], w[1], 0x7632), __byte_perm(w[2], w[3], 0x7632),
+                                  __byte_perm(w[4], w[5], 0x7632), __byte_perm(w[6], w[7], 0x7632));
+    }
+  };
   auto load_tile = [&](int tile, int s) {
     uint8_t* As = smem + s * kWgStage;
     uint8_t* Bs = As + kWgA;
@@ -372,33 +384,44 @@ __global__ void __launch_bounds__(128, 1) wgrad_tc_kernel(WgradArgs a) {
     const int z = r % a.D, b = r / a.D;
     const int x0 = txi * 8, y0 = tyi * 16;
     const int cg8 = a.Cout >> 3;
-    for (int idx = tid; idx < 128 * cg8; idx += 128) {
-      const int vox = idx & 127, cg = idx >> 7;
-      const int ty = vox >> 3, tx = vox & 7;
-      const int yy = y0 + ty, xx = x0 + tx;
-      uint4 v = make_uint4(0, 0, 0, 0);  // duplicate (wrapped) positions contribute nothing
-      if (yy < a.H && xx < a.W)
-        v = *reinterpret_cast<const uint4*>(a.dy + (b * V + (static_cast<long long>(z) * a.H + yy) * a.W + xx) * a.Cout +
-                                            cg * 8);
-      const bf16* e = reinterpret_cast<const bf16*>(&v);
+    // A: per (line ty, 8 output channels) the 8 voxels of the line, transposed to [channel][8 x]
+    for (int task = tid; task < 16 * cg8; task += 128) {
+      const int ty = task / cg8, cg = task - ty * cg8;
+      const int yy = y0 + ty;
+      uint4 in[8], out[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) *reinterpret_cast<bf16*>(As + ty * 2048 + (cg * 8 + j) * 16 + tx * 2) = e[j];
+      for (int tx = 0; tx < 8; ++tx) {
+        const int xx = x0 + tx;
+        in[tx] = make_uint4(0, 0, 0, 0);  // duplicate (wrapped) positions contribute nothing
+        if (yy < a.H && xx < a.W)
+          in[tx] = *reinterpret_cast<const uint4*>(a.dy + (b * V + (static_cast<long long>(z) * a.H + yy) * a.W + xx) *
+                                                   a.Cout + cg * 8);
+      }
+      transpose8(in, out);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4*>(As + ty * 2048 + (cg * 8 + c) * 16) = out[c];
     }
+    // B: per (halo line (zz, ry), 8 input channels) the 10 voxels rx = 0..9 of the line; copy c (shift
+    // dx = c - 1) holds rx = c .. c + 7, transposed to [channel][8 x]
     const bf16* xb = a.x + b * V * a.Cin + kc * 16;
-    for (int idx = tid; idx < 2 * kHaloVox; idx += 128) {
-      const int half = idx >= kHaloVox ? 1 : 0, h = idx - half * kHaloVox;
-      const int zz = h / 180, ry = (h % 180) / 10, rx = h % 10;
-      const int zi = wrapi(z + zz - 1, a.D), yi = wrapi(y0 + ry - 1, a.H), xi = wrapi(x0 + rx - 1, a.W);
-      const uint4 v =
-          *reinterpret_cast<const uint4*>(xb + ((static_cast<long long>(zi) * a.H + yi) * a.W + xi) * a.Cin + half * 8);
-      const bf16* e = reinterpret_cast<const bf16*>(&v);
-      const int line = zz * 18 + ry;
-      for (int c = 0; c < 3; ++c) {  // copy c holds x shifted by dx = c - 1: position rx - c
-        const int xp = rx - c;
-        if (xp < 0 || xp > 7) continue;
+    for (int task = tid; task < 54 * 2; task += 128) {
+      const int line = task >> 1, half = task & 1;
+      const int zz = line / 18, ry = line - zz * 18;
+      const int zi = wrapi(z + zz - 1, a.D), yi = wrapi(y0 + ry - 1, a.H);
+      const bf16* row = xb + (static_cast<long long>(zi) * a.H + yi) * a.W * a.Cin + half * 8;
+      uint4 v[10];
+#pragma unroll
+      for (int rx = 0; rx < 10; ++rx)
+        v[rx] = *reinterpret_cast<const uint4*>(row + static_cast<long long>(wrapi(x0 + rx - 1, a.W)) * a.Cin);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        uint4 in[8], out[8];
+#pragma unroll
+        for (int xp = 0; xp < 8; ++xp) in[xp] = v[xp + c];
+        transpose8(in, out);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-          *reinterpret_cast<bf16*>(Bs + c * kWgCopy + line * 256 + (half * 8 + j) * 16 + xp * 2) = e[j];
+          *reinterpret_cast<uint4*>(Bs + c * kWgCopy + line * 256 + (half * 8 + j) * 16) = out[j];
       }
     }
   };

@@ -598,3 +598,18 @@ def test_two_node_stencil_solve_matches_oracle(precision):
     assert abs(u[0].sum()) < 1e-9  # the common mean of both node types is removed
     assert all(i["converged"] for i in out["info"])
     s.close()
+
+
+def test_full_size_mixed_meets_fp64_energy_c_eff():
+    """The benchmark workload (128^3 elasticity, 6 loads, tol 1e-6): the mixed-precision solve reaches
+    the tolerance with an energy-form C_eff within 1e-7 of the FP64 solve's."""
+    w = I.workload_spheres_elastic(128, seed=0)
+    ce = {}
+    for prec in ("fp64", "mixed"):
+        s = _fehom().Solver("hex8_3d", "elastic", w["n"], w["ids"], w["moduli"], precision=prec)
+        s.precond_build()
+        out = s.solve(w["loads"], tol=w["tol"], fields=None)
+        assert all(i["converged"] for i in out["info"])
+        ce[prec] = s.effective_energy()
+        s.close()
+    assert _rel(ce["mixed"], ce["fp64"]) < 1e-7
