@@ -139,13 +139,16 @@ def workload():
 # Algorithmic work per voxel and load of each PCG kernel class on the 128^3 elastic workload
 # (c = 3 DOF per voxel).  Bytes: fields read + written once (s bytes per scalar), half spectra
 # nxh / nx = 65/128 complex per real voxel per component, phase ids 1 byte.  FP64 operations: counted
-# from the kernels' arithmetic (one FP64 instruction = add, mul or fma).
+# from the kernels' arithmetic (one FP64 instruction = add, mul or fma).  Stiffness, per voxel (one
+# element, one node plane) for isotropic phases: in-plane butterflies of the node plane 24, z part
+# 21, closed-form duals 35, transposed z part 18, face totals 12, transposed in-plane part 24, node
+# gather and scale 12, fused <p, Ap> 3 = 149.
 def kernel_model(s):
     c, hs = 3, 65.0 / 128.0
     spec = c * hs * 2 * s              # one half-spectrum pass over the c components
     sym = 6 * s * hs                   # packed 3x3 symmetric K_hat^+ per half-spectrum k
     return {
-        "stiffness": {"bytes": 2 * c * s + 1, "fp64_ops": 204},
+        "stiffness": {"bytes": 2 * c * s + 1, "fp64_ops": 149},
         "fft_x_fwd": {"bytes": 3 * c * s + spec, "fp64_ops": 3 * 4.0 * 7 * 3.5 / 2 * 2},
         "fft_y_fwd": {"bytes": 2 * spec, "fp64_ops": 3 * hs * 7 * 3.5},
         "fft_last": {"bytes": 2 * spec + sym, "fp64_ops": 3 * hs * 2 * 7 * 3.5 + hs * 18},

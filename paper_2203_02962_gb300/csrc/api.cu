@@ -40,7 +40,7 @@ struct fehom_ctx {
   // device
   uint8_t* ids = nullptr;
   double* mats64 = nullptr; float* mats32 = nullptr;   // [phase][D*D]
-  double* iso64 = nullptr; float* iso32 = nullptr;     // [phase][2]
+  double* iso64 = nullptr; float* iso32 = nullptr;     // [phase][kIsoStride]
   double* rmats64 = nullptr; double* riso64 = nullptr;  // reference material (one phase)
   double2* tw64[3] = {nullptr, nullptr, nullptr};
   float2* tw32[3] = {nullptr, nullptr, nullptr};
@@ -684,7 +684,7 @@ fehom_status residual_stats(fehom_ctx* ctx, int n_loads, const double* x, double
   a.y = y;
   a.tau = ctx->tau;
   a.y_scale = -1.0;
-  const int ctas = stiffness_ctas(ctx->d);
+  const int ctas = stiffness_ctas(ctx->d, n_loads);
   const int W = 1 + ctx->D;
   TRY(ensure_partial(ctx, (size_t)n_loads * ctas * W));
   a.stats = ctx->partial;
@@ -937,9 +937,10 @@ fehom_status fehom_set_reference(fehom_ctx* ctx, const double* C_ref) {
   if (ctx->iso && iso_elastic(C_ref, 3, &lam, &mu)) {
     double w, sc[3];
     kernel_scales(ctx, &w, sc);
-    const double ri[2] = {w * sc[0] * sc[0] * lam, w * sc[0] * sc[0] * mu};
-    if (!ctx->riso64) CK(cudaMalloc(&ctx->riso64, 2 * sizeof(double)));
-    CK(cudaMemcpyAsync(ctx->riso64, ri, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    double ri[kIsoStride];
+    iso_entry(w * sc[0] * sc[0] * lam, w * sc[0] * sc[0] * mu, ri);
+    if (!ctx->riso64) CK(cudaMalloc(&ctx->riso64, kIsoStride * sizeof(double)));
+    CK(cudaMemcpyAsync(ctx->riso64, ri, kIsoStride * sizeof(double), cudaMemcpyHostToDevice, s));
     ctx->iso_ref = true;
   }
   CK(cudaStreamSynchronize(s));
@@ -1263,14 +1264,13 @@ static fehom_status setup_impl(fehom_ctx* ctx, int elem, int physics, const int6
   // isotropic fast path (hex8 elasticity on a cubic grid)
   if (elem == FEHOM_HEX8_3D && physics == FEHOM_ELASTIC && ctx->h[0] == ctx->h[1] && ctx->h[1] == ctx->h[2]) {
     bool all = true;
-    std::vector<double> iso(2 * n_phases);
+    std::vector<double> iso((size_t)kIsoStride * n_phases);
     double w, sc[3];
     kernel_scales(ctx, &w, sc);
     for (int p = 0; p < n_phases && all; ++p) {
       double lam, mu;
       all = iso_elastic(&ctx->moduli[(size_t)p * m * m], 3, &lam, &mu);
-      iso[2 * p] = w * sc[0] * sc[0] * lam;
-      iso[2 * p + 1] = w * sc[0] * sc[0] * mu;
+      iso_entry(w * sc[0] * sc[0] * lam, w * sc[0] * sc[0] * mu, &iso[(size_t)kIsoStride * p]);
     }
     if (all) {
       ctx->iso = true;
@@ -1283,9 +1283,10 @@ static fehom_status setup_impl(fehom_ctx* ctx, int elem, int physics, const int6
     double lam, mu;
     if (iso_elastic(ctx->cref.data(), 3, &lam, &mu)) {
       ctx->iso_ref = true;
-      const double ri[2] = {w * sc[0] * sc[0] * lam, w * sc[0] * sc[0] * mu};
-      CK(cudaMalloc(&ctx->riso64, 2 * sizeof(double)));
-      CK(cudaMemcpyAsync(ctx->riso64, ri, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+      double ri[kIsoStride];
+      iso_entry(w * sc[0] * sc[0] * lam, w * sc[0] * sc[0] * mu, ri);
+      CK(cudaMalloc(&ctx->riso64, kIsoStride * sizeof(double)));
+      CK(cudaMemcpyAsync(ctx->riso64, ri, kIsoStride * sizeof(double), cudaMemcpyHostToDevice, s));
     }
   }
   // twiddles
@@ -1509,7 +1510,7 @@ fehom_status fehom_mean_flux_noalloc(fehom_ctx* ctx, const double* e, const doub
   for (int i = 0; i < ctx->m; ++i)
     if (!std::isfinite(e[i])) FAIL(FEHOM_E_INVALID, "non-finite load");
   const int D = ctx->D, W = 1 + D, P = ctx->n_phases;
-  const int ctas = stiffness_ctas(ctx->d);
+  const int ctas = stiffness_ctas(ctx->d, 1);
   const long long need = (long long)ctas * W + W + (long long)P * D;
   if (need > kNoallocDoubles) {
     char msg[200];

@@ -88,13 +88,21 @@ template <> struct DotAcc<float> {
 // ------------------------------------------------------------------------------------------------
 // stencil.cu
 // ------------------------------------------------------------------------------------------------
+// Isotropic cubic fast path: per phase lambda', mu' (the material in gradient coordinates) and the
+// constants of the closed-form hex8 duals: [lambda', mu', 2 mu', lambda'/3, mu'/3, (lambda' + 4 mu')/9, 0, 0].
+constexpr int kIsoStride = 8;
+inline void iso_entry(double lam, double mu, double* out) {
+  out[0] = lam; out[1] = mu; out[2] = 2.0 * mu; out[3] = lam / 3.0; out[4] = mu / 3.0;
+  out[5] = (lam + 4.0 * mu) / 9.0; out[6] = 0.0; out[7] = 0.0;
+}
+
 struct StencilArgs {
   Dims d;
   const void* x;        // [load][c][N] or nullptr (treated as zero)
   void* y;              // [load][c][N]
   const uint8_t* ids;   // [N]; nullptr = every voxel is phase 0 (uniform material)
   const void* mats;     // [phase][D*D] gradient-space material, T
-  const void* iso;      // [phase][2] (lambda', mu') for the isotropic cubic fast path, or nullptr
+  const void* iso;      // [phase][kIsoStride] (iso_entry) for the isotropic cubic fast path, or nullptr
   const double* tau;    // [load][phase][D] prestress of the macroscopic load (FP64), or nullptr
   int n_phases;
   int n_loads;
@@ -114,7 +122,7 @@ template <typename T>
 cudaError_t launch_stiffness(const StencilArgs& a, cudaStream_t s, int* ctas = nullptr);
 
 // CTAs per load of a stiffness launch (the stride of the statistics partials)
-int stiffness_ctas(const Dims& d);
+int stiffness_ctas(const Dims& d, int n_loads);  // CTAs per load of an FP64 launch over n_loads loads
 
 cudaError_t launch_phase_histogram(const uint8_t* ids, long long N, unsigned long long* hist,
                                    cudaStream_t s);

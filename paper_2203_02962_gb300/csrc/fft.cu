@@ -577,6 +577,13 @@ constexpr int XY_LDT = 145;  // column stride of the y-pass buffer: [k1][9] per 
 constexpr int XY_LDP = 66;   // row stride of the y-inverse result plane (64 columns used)
 constexpr int XY_BUF = 64 * XY_LDQ;
 constexpr size_t XY_SMEM = (XY_BUF + XY_N) * sizeof(float2);
+// Row staging of the x passes: the 64 line pairs of a plane as two float arrays (rows 2q and 2q+1),
+// aliasing the line buffer.  Global rows move with coalesced 16-byte accesses (one warp per line
+// pair) and the stride-8 subsequences are gathered in shared memory.  Row strides: 136 floats put
+// the 4 line pairs read by a warp in the forward gather on disjoint banks; 144 does the same for the
+// 2 line pairs a warp writes in the inverse.
+constexpr int XY_LDF_F = 136, XY_LDF_I = 144;
+static_assert(2 * 64 * XY_LDF_I <= 2 * XY_BUF, "row staging must fit in the line buffer");
 
 // 16-point DFT in registers, natural order in and out: n = n1 + 4 n2, k = 4 k1 + k2
 template <bool INV>
@@ -629,23 +636,39 @@ __global__ void __launch_bounds__(XY_THREADS, 2) fft_xy_fwd128_kernel(FftArgs a)
   const float2* twx = reinterpret_cast<const float2*>(a.tw.x);
   const float2* twy = reinterpret_cast<const float2*>(a.tw.y);
   const int t = threadIdx.x;
+  {  // x, stage 0: rows to shared memory (one warp per line pair, 16-byte accesses), r -= alpha Ap
+    float* Rre = reinterpret_cast<float*>(S);
+    float* Rim = Rre + 64 * XY_LDF_F;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int task = t + XY_THREADS * it;
+      const int q = task >> 5, x = 4 * (task & 31);
+      float4* g0 = reinterpret_cast<float4*>(r + 2 * q * XY_N + x);
+      float4* g1 = reinterpret_cast<float4*>(r + (2 * q + 1) * XY_N + x);
+      float4 v0 = *g0, v1 = *g1;
+      if (UPDATE) {
+        const float4 a0 = __ldg(reinterpret_cast<const float4*>(ap + 2 * q * XY_N + x));
+        const float4 a1 = __ldg(reinterpret_cast<const float4*>(ap + (2 * q + 1) * XY_N + x));
+        v0 = make_float4(fmaf(-alpha, a0.x, v0.x), fmaf(-alpha, a0.y, v0.y), fmaf(-alpha, a0.z, v0.z),
+                         fmaf(-alpha, a0.w, v0.w));
+        v1 = make_float4(fmaf(-alpha, a1.x, v1.x), fmaf(-alpha, a1.y, v1.y), fmaf(-alpha, a1.z, v1.z),
+                         fmaf(-alpha, a1.w, v1.w));
+        *g0 = v0;
+        *g1 = v1;
+      }
+      *reinterpret_cast<float4*>(Rre + q * XY_LDF_F + x) = v0;
+      *reinterpret_cast<float4*>(Rim + q * XY_LDF_F + x) = v1;
+    }
+  }
+  __syncthreads();
   {  // x, stage 1: line q = rows (2q, 2q+1), subsequence j
     const int q = t >> 3, j = t & 7;
-    float* r0 = r + 2 * q * XY_N;
-    float* r1 = r0 + XY_N;
+    const float* Rre = reinterpret_cast<const float*>(S) + q * XY_LDF_F + j;
+    const float* Rim = Rre + 64 * XY_LDF_F;
     float2 v[16];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int x = j + 8 * m;
-      float v0 = r0[x], v1 = r1[x];
-      if (UPDATE) {
-        v0 = fmaf(-alpha, ap[2 * q * XY_N + x], v0);
-        v1 = fmaf(-alpha, ap[(2 * q + 1) * XY_N + x], v1);
-        r0[x] = v0;
-        r1[x] = v1;
-      }
-      v[m] = make_float2(v0, v1);
-    }
+    for (int m = 0; m < 16; ++m) v[m] = make_float2(Rre[8 * m], Rim[8 * m]);
+    __syncthreads();  // every row has been gathered before the line buffer overwrites it
     dft16<false>(v);
     float2* Sq = S + q * XY_LDQ;
 #pragma unroll
@@ -799,36 +822,54 @@ __global__ void __launch_bounds__(XY_THREADS, 2) fft_xy_inv128_kernel(FftArgs a)
     for (int k1 = 0; k1 < 16; ++k1) Sq[k1 * 9 + j] = k1 == 0 ? v[0] : cmulc(v[k1], __ldg(twx + j * k1));
   }
   __syncthreads();
+  {  // x inverse, stage 2: 8-point DFTs, rows (2q, 2q+1) of z to the row buffers (aliasing the lines)
+    float2 w[2][8];
+#pragma unroll
+    for (int round = 0; round < 2; ++round) {
+      const int task = t + XY_THREADS * round;
+      const int q = task >> 4, k1 = task & 15;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[round][j] = S[q * XY_LDQ + k1 * 9 + j];
+    }
+    __syncthreads();  // every line has been read before the row buffers overwrite it
+    float* Rre = reinterpret_cast<float*>(S);
+    float* Rim = Rre + 64 * XY_LDF_I;
+#pragma unroll
+    for (int round = 0; round < 2; ++round) {
+      const int task = t + XY_THREADS * round;
+      const int q = task >> 4, k1 = task & 15;
+      Dft<float2, 8, true>::run(w[round]);
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) {
+        Rre[q * XY_LDF_I + k1 + 16 * k2] = w[round][k2].x;
+        Rim[q * XY_LDF_I + k1 + 16 * k2] = w[round][k2].y;
+      }
+    }
+  }
+  __syncthreads();
   float* f0 = reinterpret_cast<float*>(a.f0) + foff;
   float* f2 = (MODE != FX_PLAIN) ? reinterpret_cast<float*>(a.f2) + foff : nullptr;
   const float alpha = (MODE == FX_PCG) ? float(a.st[load].alpha) : 0.0f;
   const float beta = (MODE == FX_PCG) ? float(a.st[load].beta) : 0.0f;
 #pragma unroll
-  for (int round = 0; round < 2; ++round) {  // x inverse, stage 2, and the fused field updates
-    const int task = t + XY_THREADS * round;
-    const int q = task >> 4, k1 = task & 15;
-    const float2* Sq = S + q * XY_LDQ;
-    float2 v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = Sq[k1 * 9 + j];
-    Dft<float2, 8, true>::run(v);
-#pragma unroll
-    for (int k2 = 0; k2 < 8; ++k2) {
-      const int x = k1 + 16 * k2;
-      const long long g0 = 2LL * q * XY_N + x, g1 = g0 + XY_N;
-      if (MODE == FX_PLAIN) {
-        f0[g0] = v[k2].x;
-        f0[g1] = v[k2].y;
-      } else if (MODE == FX_PCG_INIT) {
-        f2[g0] = v[k2].x;
-        f2[g1] = v[k2].y;
-      } else {
-        const float p0 = f2[g0], p1 = f2[g1];
-        f0[g0] = fmaf(alpha, p0, f0[g0]);
-        f0[g1] = fmaf(alpha, p1, f0[g1]);
-        f2[g0] = fmaf(beta, p0, v[k2].x);
-        f2[g1] = fmaf(beta, p1, v[k2].y);
-      }
+  for (int it = 0; it < 8; ++it) {  // rows to global memory (one warp per row, 16-byte accesses), PCG updates
+    const int task = t + XY_THREADS * it;
+    const int row = task >> 5, x = 4 * (task & 31);
+    const float* R = reinterpret_cast<const float*>(S) + (row & 1) * 64 * XY_LDF_I + (row >> 1) * XY_LDF_I + x;
+    const float4 zv = *reinterpret_cast<const float4*>(R);
+    const long long g = (long long)row * XY_N + x;
+    if (MODE == FX_PLAIN) {
+      *reinterpret_cast<float4*>(f0 + g) = zv;
+    } else if (MODE == FX_PCG_INIT) {
+      *reinterpret_cast<float4*>(f2 + g) = zv;
+    } else {
+      float4* xp = reinterpret_cast<float4*>(f0 + g);
+      float4* pp = reinterpret_cast<float4*>(f2 + g);
+      const float4 pv = *pp, xv = *xp;
+      *xp = make_float4(fmaf(alpha, pv.x, xv.x), fmaf(alpha, pv.y, xv.y), fmaf(alpha, pv.z, xv.z),
+                        fmaf(alpha, pv.w, xv.w));
+      *pp = make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y), fmaf(beta, pv.z, zv.z),
+                        fmaf(beta, pv.w, zv.w));
     }
   }
   if (MODE != FX_PLAIN && a.st != nullptr) {

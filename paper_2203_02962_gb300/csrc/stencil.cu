@@ -34,12 +34,8 @@ namespace fehom {
 namespace {
 
 constexpr int BX = 32;
-constexpr int BY = 8;
 constexpr int PX = BX + 2;  // halo row of the 2-D pixel kernel
 constexpr int EX = BX + 1;
-constexpr int EY = BY + 1;
-constexpr int NE = EX * EY;              // elements per layer per CTA (297)
-constexpr int NT = ((NE + 31) / 32) * 32; // threads (320)
 
 __device__ __forceinline__ int wrap(int i, int n) {
   i %= n;
@@ -55,8 +51,22 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-constexpr int RP = BX + 2;           // row pitch of a staged node plane (nodes i0 - 1 .. i0 + BX)
-constexpr int RPLANE = RP * (BY + 2);  // nodes of a staged plane per component (340)
+constexpr int RP = BX + 2;  // row pitch of a staged node plane (nodes i0 - 1 .. i0 + BX)
+
+// hex8 tiles: BX x BY output nodes per CTA, (BX + 1) x (BY + 1) elements per layer, one element per
+// thread.  FP64 kernels take BY = 16 at one CTA per SM: the FP64 pipe is their bound, and the taller
+// tile spends fewer lanes on halo elements (576 threads for 512 nodes instead of 320 for 256).  FP32
+// kernels take BY = 8 at three CTAs per SM, which keeps the issue slots busy across the per-layer
+// barriers.
+template <typename T>
+struct Hex8Tile {
+  static constexpr int BY = sizeof(T) == 8 ? 16 : 8;
+  static constexpr int EY = BY + 1;
+  static constexpr int NE = EX * EY;                 // elements per layer per CTA (561 / 297)
+  static constexpr int NT = ((NE + 31) / 32) * 32;   // threads (576 / 320)
+  static constexpr int RPLANE = RP * (BY + 2);       // nodes of a staged plane per component
+  static constexpr int PER_SM = sizeof(T) == 8 ? 1 : 3;  // resident CTAs per SM (launch bounds)
+};
 
 // Block-wide FP64 sum; every thread gets the result. `sh` holds >= 32 doubles.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -129,30 +139,6 @@ __device__ __forceinline__ void contract_gen(const T* __restrict__ Ch, const T (
     }
 }
 
-// Isotropic material on a cubic grid: T_ij = lam tr(g) delta_ij + mu (g_ij + g_ji) (entries in MASK).
-template <int MASK, typename T>
-__device__ __forceinline__ void contract_iso(const T (&g)[3][3], T lam, T mu, T (&out)[3][3]) {
-  // g[j][i]: derivative i of component j; entries outside MASK are zero
-  T tr = T(0);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-    if ((MASK >> i) & 1) tr += g[i][i];
-  const T lt = lam * tr;
-  const T mu2 = mu + mu;
-#pragma unroll
-  for (int j = 0; j < 3; ++j)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      if (!((MASK >> i) & 1)) continue;
-      if (i == j) {
-        out[j][i] = fma(mu2, g[j][j], lt);
-      } else {
-        // g[i][j] (derivative j of component i) is nonzero only when direction j is active
-        out[j][i] = ((MASK >> j) & 1) ? mu * (g[j][i] + g[i][j]) : mu * g[j][i];
-      }
-    }
-}
-
 // Hex8 element in face form.  The Hadamard (modal) transform of the 8 nodal values factors into an
 // in-plane part per x-y face -- (ss, sd, ds, dd) = the sums / differences along x, then along y, of
 // the face's 4 nodes -- and a z part that combines the element's bottom (c = 0) and top (c = 1)
@@ -164,21 +150,37 @@ __device__ __forceinline__ void contract_iso(const T (&g)[3][3], T lam, T mu, T 
 //   pb/pt[j][0..3]   = the element's partials for its bottom / top face
 //   t1o              = the monomial-1 dual (Chat g_1 + tau), whose sum over elements is |Y| S P^T <sigma>
 // Without a nodal field (HAS_X false: the right-hand side -D^T W C e) only T1 = tau is nonzero.
+//
+// Modal coefficients q_n[j] of component j (z part below) and the gradient they give per monomial
+// (g_m[j][i]: derivative i of component j multiplying monomial m):
+//   1: (q1, q2, q3)   xi: (0, q4, q6)   eta: (q4, 0, q5)   zeta: (q6, q5, 0)
+//   eta zeta: (q7, 0, 0)   xi zeta: (0, q7, 0)   xi eta: (0, 0, q7)
+// The dual Q_n[j] = dE/dq_n[j] sums t_m = Chat g_m over the monomials that q_n enters.
+//
+// Isotropic material on cubic voxels, t_m = lam' tr(g_m) I + mu' (g_m + g_m^T) weighted 1, 1/3, 1/9:
+// the duals reduce to closed forms (35 operations instead of seven contractions):
+//   Q1..Q3 = the columns of t_1 (symmetric: Q1[1] = Q2[0], Q1[2] = Q3[0], Q2[2] = Q3[1])
+//   Q4 = (L tr_y + mu' q4[0], L tr_x + mu' q4[1], M (q4[2] + s))
+//   Q5 = (M (q5[0] + s), L tr_z + mu' q5[1], L tr_y + mu' q5[2])
+//   Q6 = (L tr_z + mu' q6[0], M (q6[1] + s), L tr_x + mu' q6[2])
+//   Q7 = K7 q7
+// with L = lam'/3, M = mu'/3, K7 = (lam' + 4 mu')/9, tr_x = q4[1] + q6[2], tr_y = q4[0] + q5[2],
+// tr_z = q6[0] + q5[1] (the traces of the linear monomials' gradients), s = q4[2] + q5[0] + q6[1].
 template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E>
 __device__ __forceinline__ void hex8_element_faces(const T (&bot)[C][4], const T (&top)[C][4], const T* __restrict__ Ch,
                                                    const T* __restrict__ iso, const double* __restrict__ tau,
                                                    T (&pb)[C][4], T (&pt)[C][4], T (&t1o)[C][3]) {
-  T t1[C][3], tx[C][3], ty[C][3], tz[C][3], tyz[C][3], txz[C][3], txy[C][3];
+  T Q1[C], Q2[C], Q3[C], Q4[C], Q5[C], Q6[C], Q7[C];
   if constexpr (!HAS_X) {
 #pragma unroll
-    for (int j = 0; j < C; ++j)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        t1[j][i] = HAS_E ? T(tau[j * 3 + i]) : T(0);
-        tx[j][i] = ty[j][i] = tz[j][i] = tyz[j][i] = txz[j][i] = txy[j][i] = T(0);
-      }
+    for (int j = 0; j < C; ++j) {
+      Q1[j] = HAS_E ? T(tau[j * 3 + 0]) : T(0);
+      Q2[j] = HAS_E ? T(tau[j * 3 + 1]) : T(0);
+      Q3[j] = HAS_E ? T(tau[j * 3 + 2]) : T(0);
+      Q4[j] = Q5[j] = Q6[j] = Q7[j] = T(0);
+    }
   } else {
-    // z part of the modal transform: q[j][n], n = 1..7 (xi, eta, zeta, xi eta, eta zeta, xi zeta, xi eta zeta)
+    // z part of the modal transform
     T q1[C], q2[C], q3[C], q4[C], q5[C], q6[C], q7[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) {
@@ -190,30 +192,53 @@ __device__ __forceinline__ void hex8_element_faces(const T (&bot)[C][4], const T
       q4[j] = top[j][3] + bot[j][3];
       q7[j] = top[j][3] - bot[j][3];
     }
-    // gradient coefficients per monomial, g[j][dir]
-    T g1[C][3], gx[C][3], gy[C][3], gz[C][3], gyz[C][3], gxz[C][3], gxy[C][3];
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      g1[j][0] = q1[j]; g1[j][1] = q2[j]; g1[j][2] = q3[j];
-      gx[j][0] = T(0);  gx[j][1] = q4[j]; gx[j][2] = q6[j];   // monomial xi
-      gy[j][0] = q4[j]; gy[j][1] = T(0);  gy[j][2] = q5[j];   // eta
-      gz[j][0] = q6[j]; gz[j][1] = q5[j]; gz[j][2] = T(0);    // zeta
-      gyz[j][0] = q7[j]; gyz[j][1] = T(0); gyz[j][2] = T(0);  // eta zeta
-      gxz[j][0] = T(0); gxz[j][1] = q7[j]; gxz[j][2] = T(0);  // xi zeta
-      gxy[j][0] = T(0); gxy[j][1] = T(0); gxy[j][2] = q7[j];  // xi eta
-    }
-    constexpr double third = 1.0 / 3.0, ninth = 1.0 / 9.0;
     if constexpr (ISO && C == 3) {
-      const T lam = iso[0], mu = iso[1];
-      contract_iso<7>(g1, lam, mu, t1);
-      const T l3 = lam * T(third), m3 = mu * T(third), l9 = lam * T(ninth), m9 = mu * T(ninth);
-      contract_iso<6>(gx, l3, m3, tx);
-      contract_iso<5>(gy, l3, m3, ty);
-      contract_iso<3>(gz, l3, m3, tz);
-      contract_iso<1>(gyz, l9, m9, tyz);
-      contract_iso<2>(gxz, l9, m9, txz);
-      contract_iso<4>(gxy, l9, m9, txy);
+      T lam, mu, mu2, L, M, K7;
+      if constexpr (sizeof(T) == 4) {  // one entry = 8 floats, 32-byte aligned: two 16-byte loads
+        const float4 c0 = __ldg(reinterpret_cast<const float4*>(iso));
+        const float4 c1 = __ldg(reinterpret_cast<const float4*>(iso) + 1);
+        lam = c0.x; mu = c0.y; mu2 = c0.z; L = c0.w; M = c1.x; K7 = c1.y;
+      } else {  // one entry = 8 doubles, 64-byte aligned: three 16-byte loads
+        const double2 c0 = __ldg(reinterpret_cast<const double2*>(iso));
+        const double2 c1 = __ldg(reinterpret_cast<const double2*>(iso) + 1);
+        const double2 c2 = __ldg(reinterpret_cast<const double2*>(iso) + 2);
+        lam = c0.x; mu = c0.y; mu2 = c1.x; L = c1.y; M = c2.x; K7 = c2.y;
+      }
+      const T lt = lam * (q1[0] + q2[1] + q3[2]);
+      Q1[0] = fma(mu2, q1[0], lt);
+      Q2[1] = fma(mu2, q2[1], lt);
+      Q3[2] = fma(mu2, q3[2], lt);
+      Q1[1] = Q2[0] = mu * (q1[1] + q2[0]);
+      Q1[2] = Q3[0] = mu * (q1[2] + q3[0]);
+      Q2[2] = Q3[1] = mu * (q2[2] + q3[1]);
+      const T Ltx = L * (q4[1] + q6[2]), Lty = L * (q4[0] + q5[2]), Ltz = L * (q6[0] + q5[1]);
+      const T sm = q4[2] + q5[0] + q6[1];
+      Q4[0] = fma(mu, q4[0], Lty);
+      Q4[1] = fma(mu, q4[1], Ltx);
+      Q4[2] = M * (q4[2] + sm);
+      Q5[0] = M * (q5[0] + sm);
+      Q5[1] = fma(mu, q5[1], Ltz);
+      Q5[2] = fma(mu, q5[2], Lty);
+      Q6[0] = fma(mu, q6[0], Ltz);
+      Q6[1] = M * (q6[1] + sm);
+      Q6[2] = fma(mu, q6[2], Ltx);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Q7[j] = K7 * q7[j];
     } else {
+      // general material: contract each monomial's gradient, then sum the contributions per mode
+      T g1[C][3], gx[C][3], gy[C][3], gz[C][3], gyz[C][3], gxz[C][3], gxy[C][3];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        g1[j][0] = q1[j]; g1[j][1] = q2[j]; g1[j][2] = q3[j];
+        gx[j][0] = T(0);  gx[j][1] = q4[j]; gx[j][2] = q6[j];
+        gy[j][0] = q4[j]; gy[j][1] = T(0);  gy[j][2] = q5[j];
+        gz[j][0] = q6[j]; gz[j][1] = q5[j]; gz[j][2] = T(0);
+        gyz[j][0] = q7[j]; gyz[j][1] = T(0); gyz[j][2] = T(0);
+        gxz[j][0] = T(0); gxz[j][1] = q7[j]; gxz[j][2] = T(0);
+        gxy[j][0] = T(0); gxy[j][1] = T(0); gxy[j][2] = q7[j];
+      }
+      constexpr double third = 1.0 / 3.0, ninth = 1.0 / 9.0;
+      T t1[C][3], tx[C][3], ty[C][3], tz[C][3], tyz[C][3], txz[C][3], txy[C][3];
       contract_gen<7>(Ch, g1, T(1), t1);
       contract_gen<6>(Ch, gx, T(third), tx);
       contract_gen<5>(Ch, gy, T(third), ty);
@@ -221,28 +246,32 @@ __device__ __forceinline__ void hex8_element_faces(const T (&bot)[C][4], const T
       contract_gen<1>(Ch, gyz, T(ninth), tyz);
       contract_gen<2>(Ch, gxz, T(ninth), txz);
       contract_gen<4>(Ch, gxy, T(ninth), txy);
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        Q1[j] = t1[j][0]; Q2[j] = t1[j][1]; Q3[j] = t1[j][2];
+        Q4[j] = tx[j][1] + ty[j][0];
+        Q5[j] = ty[j][2] + tz[j][1];
+        Q6[j] = tx[j][2] + tz[j][0];
+        Q7[j] = tyz[j][0] + txz[j][1] + txy[j][2];
+      }
     }
     if constexpr (HAS_E) {
 #pragma unroll
-      for (int j = 0; j < C; ++j)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) t1[j][i] += T(tau[j * 3 + i]);
+      for (int j = 0; j < C; ++j) {
+        Q1[j] += T(tau[j * 3 + 0]);
+        Q2[j] += T(tau[j * 3 + 1]);
+        Q3[j] += T(tau[j * 3 + 2]);
+      }
     }
   }
 #pragma unroll
   for (int j = 0; j < C; ++j) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) t1o[j][i] = t1[j][i];
-    // dual modal forces, then the transposed z part
-    const T Q1 = t1[j][0], Q2 = t1[j][1], Q3 = t1[j][2];
-    const T Q4 = tx[j][1] + ty[j][0];
-    const T Q5 = ty[j][2] + tz[j][1];
-    const T Q6 = tx[j][2] + tz[j][0];
-    const T Q7 = tyz[j][0] + txz[j][1] + txy[j][2];
-    pb[j][0] = -Q3;      pt[j][0] = Q3;
-    pb[j][1] = Q2 - Q5;  pt[j][1] = Q2 + Q5;
-    pb[j][2] = Q1 - Q6;  pt[j][2] = Q1 + Q6;
-    pb[j][3] = Q4 - Q7;  pt[j][3] = Q4 + Q7;
+    t1o[j][0] = Q1[j]; t1o[j][1] = Q2[j]; t1o[j][2] = Q3[j];
+    // the transposed z part
+    pb[j][0] = -Q3[j];         pt[j][0] = Q3[j];
+    pb[j][1] = Q2[j] - Q5[j];  pt[j][1] = Q2[j] + Q5[j];
+    pb[j][2] = Q1[j] - Q6[j];  pt[j][2] = Q1[j] + Q6[j];
+    pb[j][3] = Q4[j] - Q7[j];  pt[j][3] = Q4[j] + Q7[j];
   }
 }
 
@@ -270,33 +299,44 @@ __device__ void pcg_alpha_update(PcgState& s, double total, double* hist) {
 // ------------------------------------------------------------------------------------------------
 // 3-D hex8 kernel
 //
-// Per element layer k (between node planes k and k + 1), two barriers:
+// Per element layer k (between node planes k and k + 1):
 //   A. face threads read the 4 nodes of their x-y face of plane k + 1 (periodic offsets computed
-//      once; neighbouring faces share nodes through L1) and store its in-plane butterflies;
+//      once; neighbouring faces share nodes through L1) and store its in-plane butterflies (one
+//      thread per face: the butterflies are private to it);
 //   B. element threads combine the faces of planes k and k + 1, contract with the material, add
 //      the bottom partials to the top partials carried from layer k - 1 (registers) and spread the
-//      face total to its 4 corners of plane k;
+//      face total to its 4 corners of plane k (corner buffer k mod 2);
+//   (barrier)
 //   C. node threads gather the 4 faces around their node of plane k and write y.
+// One barrier per layer: the corner buffers alternate, so the gather of layer k - 1 and the writes
+// of layer k + 1 to the same buffer are ordered by the barrier of layer k.
 // ------------------------------------------------------------------------------------------------
-// RAW (FP32 kernels with a field): instead of barrier A, the raw node planes (tile + halo) are
-// fetched with cp.async one layer ahead into a ring of three plane buffers, and each element forms
-// the butterflies of its two faces itself (FP32 adds are cheap; the FP64 kernels keep the shared
-// face butterflies, which save FP64 operations).  The x values of the <x, y> dot come from the same
-// staged plane.
+// RAW (FP32 kernels with a field): instead of step A, the raw node planes (tile + halo) are fetched
+// with cp.async one layer ahead into a ring of three plane buffers, made visible by a second
+// barrier per layer (which also orders the single corner buffer), and each element forms the
+// butterflies of its top face itself, the bottom face being the previous layer's top (FP32 adds are
+// cheap; the FP64 kernels keep the per-plane butterflies, which save FP64 operations).  The x
+// values of the <x, y> dot come from the same staged plane.
 template <typename T, int C, bool HAS_X>
 __host__ __device__ constexpr bool hex8_raw() { return HAS_X && sizeof(T) == 4; }
 template <typename T, int C, bool HAS_X>
 __host__ __device__ constexpr size_t hex8_smem_elems() {
-  return hex8_raw<T, C, HAS_X>() ? (size_t)3 * C * RPLANE + 4 * C * NE : (size_t)2 * 4 * C * NE + 4 * C * NE;
+  using TL = Hex8Tile<T>;
+  return hex8_raw<T, C, HAS_X>() ? (size_t)3 * C * TL::RPLANE + 4 * C * TL::NE
+                                 : (size_t)2 * 4 * C * TL::NE + 2 * 4 * C * TL::NE;
 }
 
 template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) hex8_apply_kernel(StencilArgs a, int kz_per_cta) {
+__global__ void __launch_bounds__(Hex8Tile<T>::NT, Hex8Tile<T>::PER_SM)
+    hex8_apply_kernel(StencilArgs a, int kz_per_cta) {
   constexpr bool RAW = hex8_raw<T, C, HAS_X>();
+  constexpr int BY = Hex8Tile<T>::BY, NE = Hex8Tile<T>::NE, NT = Hex8Tile<T>::NT;
+  constexpr int RPLANE = Hex8Tile<T>::RPLANE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* FB = reinterpret_cast<T*>(smem_raw);  // [2 planes][4][C][NE] face butterflies (not RAW)
   T* RW = reinterpret_cast<T*>(smem_raw);  // [3 slots][C][BY + 2][RP] staged node planes (RAW)
-  T* FC = RAW ? RW + 3 * C * RPLANE : FB + 2 * 4 * C * NE;  // [4 corners][C][NE] face contributions to plane k
+  // [4 corners][C][NE] face contributions to plane k; without RAW two of them, by the parity of k
+  T* FC0 = RAW ? RW + 3 * C * RPLANE : FB + 2 * 4 * C * NE;
   __shared__ double red_sh[32];
 
   const Dims d = a.d;
@@ -316,6 +356,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) hex8_apply_kernel(
   const T* isot = reinterpret_cast<const T*>(a.iso);
   const double* tau = HAS_E ? a.tau + (long long)load * a.n_phases * (3 * C) : nullptr;
   const long long plane = (long long)d.nx * d.ny;
+  const T ysc = T(a.y_scale);
 
   // face / element thread (ei, ej): face (ei, ej) of a plane = the x-y square whose corners are the
   // nodes (i0 - 1 + ei + a, j0 - 1 + ej + b); element (ei, ej) of a layer sits on that face
@@ -402,23 +443,39 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) hex8_apply_kernel(
     }
   };
   auto ring = [&](int k) { return (k - k0 + 1) % 3; };
+  T fprev[C][4];  // RAW: butterflies of the top face of the previous layer (this layer's bottom face)
 
   // B + C for element layer k (planes k: slot CUR, k + 1: slot CUR ^ 1); kzc = wrap(k)
   auto layer = [&](auto cur_c, int k, int kzc) {
-    constexpr int CUR = decltype(cur_c)::value;
+    [[maybe_unused]] constexpr int CUR = decltype(cur_c)::value;
+    [[maybe_unused]] const int s0 = RAW ? ring(k) : 0, s1 = s0 == 2 ? 0 : s0 + 1, s2 = s1 == 2 ? 0 : s1 + 1;
     if constexpr (RAW) {
       cp_async_wait_all();  // plane k + 1 (issued one layer earlier) has landed
       __syncthreads();      // ... for every thread; the ring slot of plane k - 1 is free again
-      if (k + 2 <= k1) stage_plane(ring(k + 2), wrap(k + 2, d.nz));
+      if (k + 2 <= k1) stage_plane(s2, wrap(k + 2, d.nz));
     } else {
+      // the face butterflies are private to their thread, and the corner buffer FC alternates with
+      // the parity of the layer (the barrier of layer k - 1 orders the gather of layer k - 2 before
+      // the writes below), so no barrier is needed here
       faces(std::integral_constant<int, CUR ^ 1>{}, next(kzc));
-      __syncthreads();
     }
+    T* FC = RAW ? FC0 : FC0 + CUR * 4 * C * NE;
     if (face_thread) {
       T bot[C][4], top[C][4];
       if constexpr (RAW) {
-        raw_face(ring(k), bot);
-        raw_face(ring(k + 1), top);
+        if (k == k0 - 1) {
+          raw_face(s0, bot);
+        } else {
+#pragma unroll
+          for (int j = 0; j < C; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bot[j][q] = fprev[j][q];
+        }
+        raw_face(s1, top);
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) fprev[j][q] = top[j][q];
       } else {
 #pragma unroll
         for (int j = 0; j < C; ++j)
@@ -430,7 +487,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) hex8_apply_kernel(
       }
       const int ph = a.ids ? a.ids[(long long)kzc * plane + off00] : 0;
       T pb[C][4], pt[C][4], t1[C][3];
-      hex8_element_faces<T, C, ISO, HAS_X, HAS_E>(bot, top, mats + (long long)ph * (9 * C * C), isot + 2 * ph,
+      hex8_element_faces<T, C, ISO, HAS_X, HAS_E>(bot, top, mats + (long long)ph * (9 * C * C), isot + kIsoStride * ph,
                                                   HAS_E ? tau + ph * (3 * C) : nullptr, pb, pt, t1);
 #pragma unroll
       for (int j = 0; j < C; ++j) {
@@ -461,17 +518,18 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) hex8_apply_kernel(
       for (int j = 0; j < C; ++j) {
         const T v = FC[(3 * C + j) * NE + e00] + FC[(2 * C + j) * NE + e00 + 1] +
                     FC[(1 * C + j) * NE + e00 + EX] + FC[(0 * C + j) * NE + e00 + EX + 1];
-        const T val = T(a.y_scale) * v;
+        const T val = ysc * v;
         const long long gidx = (long long)j * d.N + (long long)kzc * plane + node_off;
         if (RED != RED_SUMS) y[gidx] = val;
         if constexpr (RED == RED_PCG) {
-          if constexpr (RAW) acc_p.add(val, RW[(ring(k) * C + j) * RPLANE + (nj + 1) * RP + ni + 1]);
+          if constexpr (RAW) acc_p.add(val, RW[(s0 * C + j) * RPLANE + (nj + 1) * RP + ni + 1]);
           else acc_p.add(val, __ldg(x + gidx));
         }
         if (RED == RED_STATS || RED == RED_SUMS) acc_y += (double)val * (double)val;
       }
     }
-    // the next layer's barrier A orders these reads of FC and FB before their next writes
+    // RAW: the next layer's first barrier orders these reads of FC and of the staged plane before
+    // their next writes; otherwise the next layer writes the other corner buffer
   };
 
   int kz = wrap(k0 - 1, d.nz);
@@ -826,20 +884,33 @@ cudaError_t set_smem(K kern, size_t bytes) {
   return cudaSuccess;
 }
 
-// hex8 grid: x-y tiles times z slabs (enough CTAs for 2 waves of 152 SMs, at least 8 planes a slab)
-void hex8_grid(const Dims& d, int* tiles, int* slabs, int* kz) {
-  *tiles = ((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
-  int sl = (2 * 152 + *tiles - 1) / *tiles;
-  sl = max(1, min(sl, d.nz / 8 > 0 ? d.nz / 8 : 1));
-  *kz = (d.nz + sl - 1) / sl;
-  *slabs = (d.nz + *kz - 1) / *kz;
+// hex8 grid: x-y tiles times z slabs times loads.  Each slab recomputes one element layer below it,
+// and the CTAs run in waves over the 152 SMs, a CTA's layer time growing with the CTAs sharing its
+// SM; the slab depth kz (at least 4 planes) minimises waves x (kz + 1), waves = ceil(CTAs / 152).
+template <typename T>
+void hex8_grid(const Dims& d, int n_loads, int* tiles, int* slabs, int* kz) {
+  *tiles = ((d.nx + BX - 1) / BX) * ((d.ny + Hex8Tile<T>::BY - 1) / Hex8Tile<T>::BY);
+  const long long cols = (long long)*tiles * max(n_loads, 1);
+  long long best = -1;
+  int bkz = d.nz;
+  for (int sl = 1; sl <= max(1, d.nz / 4); ++sl) {
+    const int k = (d.nz + sl - 1) / sl;
+    const long long ctas = cols * ((d.nz + k - 1) / k);
+    const long long cost = ((ctas + 151) / 152) * (k + 1);
+    if (best < 0 || cost < best) {
+      best = cost;
+      bkz = k;
+    }
+  }
+  *kz = bkz;
+  *slabs = (d.nz + bkz - 1) / bkz;
 }
 
 template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED>
 cudaError_t launch_hex8_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
   const Dims& d = a.d;
   int tiles, slabs, kz;
-  hex8_grid(d, &tiles, &slabs, &kz);
+  hex8_grid<T>(d, a.n_loads, &tiles, &slabs, &kz);
   if (ctas) *ctas = tiles * slabs;
   if (RED == RED_PCG && tiles * slabs > a.red.max_blocks) return cudaErrorInvalidConfiguration;
   const size_t smem = sizeof(T) * hex8_smem_elems<T, C, HAS_X>();
@@ -847,7 +918,7 @@ cudaError_t launch_hex8_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(tiles, slabs, a.n_loads);
-  kern<<<grid, NT, smem, s>>>(a, kz);
+  kern<<<grid, Hex8Tile<T>::NT, smem, s>>>(a, kz);
   return cudaGetLastError();
 }
 
@@ -965,10 +1036,10 @@ cudaError_t launch_stiffness(const StencilArgs& a, cudaStream_t s, int* ctas) {
   return cudaErrorInvalidValue;
 }
 
-int stiffness_ctas(const Dims& d) {
+int stiffness_ctas(const Dims& d, int n_loads) {
   if (d.elem == HEX8_3D) {
     int tiles, slabs, kz;
-    hex8_grid(d, &tiles, &slabs, &kz);
+    hex8_grid<double>(d, n_loads, &tiles, &slabs, &kz);
     return tiles * slabs;
   }
   return ((d.nx + BX - 1) / BX) * ((d.ny + BY2 - 1) / BY2);
