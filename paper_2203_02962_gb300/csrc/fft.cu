@@ -899,37 +899,58 @@ __global__ void __launch_bounds__(XY_THREADS, 2) fft_xy_inv128_kernel(FftArgs a)
 // DFTs written straight back.  Shared memory is touched twice per direction instead of once per
 // radix stage.
 // Threads: 128 per component for stages 1 and 3, at least 256 (16 columns x 16 k1) for stage 2.
+// The CTA's slice of the packed symbol (16 columns x 128 kz x 1 or 6 entries) is fetched into shared
+// memory by cp.async while stage 1 runs; the grid runs the loads of one column group next to each
+// other (load = blockIdx.x), so the slice is read from HBM once and from L2 by the other loads.
+// Requires ny * nxh to be a multiple of 16 (no partial column groups).
 template <int NC>
 __host__ __device__ constexpr int last128_threads() { return NC == 1 ? 256 : 128 * NC; }
+template <int NC>
+__host__ __device__ constexpr size_t last128_smem() {
+  return (size_t)NC * 16 * 8 * 16 * sizeof(float2) + (size_t)(NC == 1 ? 1 : 6) * 128 * 16 * sizeof(float);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
 
 template <int NC>
 __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_last128_kernel(FftArgs a) {
   constexpr int TCL = 16;
+  constexpr int NS = NC == 1 ? 1 : 6;  // packed symbol entries
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_sh[32];
-  float2* S = reinterpret_cast<float2*>(smem_raw);  // NC * 16 * 8 * 16 complex
-  const int load = blockIdx.z;
+  float2* S = reinterpret_cast<float2*>(smem_raw);                // NC * 16 * 8 * 16 complex
+  float* Ssym = reinterpret_cast<float*>(S + NC * 16 * 8 * TCL);  // [NS][128 kz][16 columns]
+  const int load = blockIdx.x;
   if (!first_half_active(a.st, load)) return;
   float2* spec = reinterpret_cast<float2*>(a.spec) + (long long)load * a.load_stride_s;
   const long long Nh = a.d.Nh;
   const long long es = (long long)a.d.ny * a.d.nxh;
-  const int ncols = a.d.ny * a.d.nxh;
   const int nxh = a.d.nxh, half = a.d.nx / 2;
-  const int cf0 = blockIdx.x * TCL;
+  const int cf0 = blockIdx.y * TCL;
   const float2* tw = reinterpret_cast<const float2*>(a.tw.z);
   const float* sym = reinterpret_cast<const float*>(a.sym);
   const int tid = threadIdx.x;
+  for (int ch = tid; ch < NS * 128 * 4; ch += last128_threads<NC>()) {  // 16-byte chunks of the slice
+    const int e = ch >> 9, kz = (ch >> 2) & 127, q4 = ch & 3;
+    cp_async16(Ssym + (e * 128 + kz) * TCL + 4 * q4, sym + e * Nh + cf0 + kz * es + 4 * q4);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
   if (tid < 128 * NC) {  // stage 1: task (column t, subsequence j, component c)
     const int t = tid & 15, j = (tid >> 4) & 7, c = tid >> 7;
     const int cf = cf0 + t;
     float2 v[16];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = cf < ncols ? spec[c * Nh + cf + (j + 8 * m) * es] : make_float2(0.f, 0.f);
+    for (int m = 0; m < 16; ++m) v[m] = spec[c * Nh + cf + (j + 8 * m) * es];
     dft16<false>(v);
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1)
       S[((c * 16 + k1) * 8 + j) * TCL + t] = k1 == 0 ? v[0] : cmul(v[k1], __ldg(tw + j * k1));
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   DotAcc<float> dot;
   const bool active = tid < 256;
@@ -950,17 +971,17 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_la
     const float wgt = (kx == 0 || kx == half) ? 1.0f : 2.0f;
 #pragma unroll
     for (int k2 = 0; k2 < 8; ++k2) {
-      if (cf >= ncols) break;
-      const long long ti = cf + (long long)(k1 + 16 * k2) * es;
+      const float* ks = Ssym + (k1 + 16 * k2) * TCL + t;  // entry e at ks[e * 128 * TCL]
       float2 r[NC], z[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) r[c] = zr[c][k2];
       if constexpr (NC == 1) {
-        const float k00 = sym[ti];
+        const float k00 = ks[0];
         z[0] = make_float2(k00 * r[0].x, k00 * r[0].y);
       } else {
-        const float k00 = sym[ti], k11 = sym[Nh + ti], k22 = sym[2 * Nh + ti];
-        const float k12 = sym[3 * Nh + ti], k02 = sym[4 * Nh + ti], k01 = sym[5 * Nh + ti];
+        constexpr int E = 128 * TCL;
+        const float k00 = ks[0], k11 = ks[E], k22 = ks[2 * E];
+        const float k12 = ks[3 * E], k02 = ks[4 * E], k01 = ks[5 * E];
         z[0] = make_float2(fmaf(k00, r[0].x, fmaf(k01, r[1].x, k02 * r[2].x)), fmaf(k00, r[0].y, fmaf(k01, r[1].y, k02 * r[2].y)));
         z[1] = make_float2(fmaf(k01, r[0].x, fmaf(k11, r[1].x, k12 * r[2].x)), fmaf(k01, r[0].y, fmaf(k11, r[1].y, k12 * r[2].y)));
         z[2] = make_float2(fmaf(k02, r[0].x, fmaf(k12, r[1].x, k22 * r[2].x)), fmaf(k02, r[0].y, fmaf(k12, r[1].y, k22 * r[2].y)));
@@ -988,16 +1009,14 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_la
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) v[kk] = S[((c * 8 + j) * 16 + kk) * TCL + tt];
     dft16<true>(v);
-    if (cff < ncols) {
 #pragma unroll
-      for (int m = 0; m < 16; ++m) spec[c * Nh + cff + (j + 8 * m) * es] = v[m];
-    }
+    for (int m = 0; m < 16; ++m) spec[c * Nh + cff + (j + 8 * m) * es] = v[m];
   }
   if (a.st != nullptr) {
     const double part = block_sum(dot.value(), red_sh);
     double total;
-    if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load, gridDim.x,
-                         blockIdx.x, red_sh, &total)) {
+    if (finish_reduction(part, a.red.partial + (long long)load * a.red.max_blocks, a.red.count + load, gridDim.y,
+                         blockIdx.y, red_sh, &total)) {
       if (threadIdx.x == 0) {
         PcgState& st = a.st[load];
         if (a.init) {
@@ -1297,11 +1316,12 @@ bool fft_last128_supported(const Dims& d, bool fp32) {
 template <typename T>
 cudaError_t launch_fft_last_solve(const FftArgs& a, cudaStream_t s) {
   if (sizeof(T) == 4 && a.last_reg && a.sym && fft_last128_supported(a.d, true)) {
-    const dim3 grid((a.d.ny * a.d.nxh) / 16, 1, a.n_loads);
-    if (a.st != nullptr && (long long)grid.x > a.red.max_blocks) return cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)a.d.c * 16 * 8 * 16 * sizeof(float2);
-    if (a.d.c == 1) return launch_with_smem(fft_last128_kernel<1>, grid, last128_threads<1>(), smem, s, a);
-    return launch_with_smem(fft_last128_kernel<3>, grid, last128_threads<3>(), smem, s, a);
+    const int groups = (a.d.ny * a.d.nxh) / 16;
+    if (groups > 65535) return cudaErrorInvalidConfiguration;
+    const dim3 grid(a.n_loads, groups, 1);
+    if (a.st != nullptr && (long long)groups > a.red.max_blocks) return cudaErrorInvalidConfiguration;
+    if (a.d.c == 1) return launch_with_smem(fft_last128_kernel<1>, grid, last128_threads<1>(), last128_smem<1>(), s, a);
+    return launch_with_smem(fft_last128_kernel<3>, grid, last128_threads<3>(), last128_smem<3>(), s, a);
   }
   if (a.d.c == 1) return launch_last_nc<T, 1>(a, s);
   if (a.d.c == 2) return launch_last_nc<T, 2>(a, s);

@@ -49,7 +49,8 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 constexpr int RP = BX + 2;  // row pitch of a staged node plane (nodes i0 - 1 .. i0 + BX)
 
@@ -319,10 +320,11 @@ __device__ void pcg_alpha_update(PcgState& s, double total, double* hist) {
 // values of the <x, y> dot come from the same staged plane.
 template <typename T, int C, bool HAS_X>
 __host__ __device__ constexpr bool hex8_raw() { return HAS_X && sizeof(T) == 4; }
+constexpr int kRing = 5;  // RAW: staged node planes k .. k + 4
 template <typename T, int C, bool HAS_X>
 __host__ __device__ constexpr size_t hex8_smem_elems() {
   using TL = Hex8Tile<T>;
-  return hex8_raw<T, C, HAS_X>() ? (size_t)3 * C * TL::RPLANE + 4 * C * TL::NE
+  return hex8_raw<T, C, HAS_X>() ? (size_t)kRing * C * TL::RPLANE + 2 * 4 * C * TL::NE
                                  : (size_t)2 * 4 * C * TL::NE + 2 * 4 * C * TL::NE;
 }
 
@@ -334,9 +336,9 @@ __global__ void __launch_bounds__(Hex8Tile<T>::NT, Hex8Tile<T>::PER_SM)
   constexpr int RPLANE = Hex8Tile<T>::RPLANE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* FB = reinterpret_cast<T*>(smem_raw);  // [2 planes][4][C][NE] face butterflies (not RAW)
-  T* RW = reinterpret_cast<T*>(smem_raw);  // [3 slots][C][BY + 2][RP] staged node planes (RAW)
+  T* RW = reinterpret_cast<T*>(smem_raw);  // [kRing slots][C][BY + 2][RP] staged node planes (RAW)
   // [4 corners][C][NE] face contributions to plane k; without RAW two of them, by the parity of k
-  T* FC0 = RAW ? RW + 3 * C * RPLANE : FB + 2 * 4 * C * NE;
+  T* FC0 = RAW ? RW + kRing * C * RPLANE : FB + 2 * 4 * C * NE;
   __shared__ double red_sh[32];
 
   const Dims d = a.d;
@@ -442,24 +444,18 @@ __global__ void __launch_bounds__(Hex8Tile<T>::NT, Hex8Tile<T>::PER_SM)
       f[j][3] = d1 - d0;
     }
   };
-  auto ring = [&](int k) { return (k - k0 + 1) % 3; };
+  auto ring = [&](int k) { return (k - k0 + 1) % kRing; };
   T fprev[C][4];  // RAW: butterflies of the top face of the previous layer (this layer's bottom face)
 
   // B + C for element layer k (planes k: slot CUR, k + 1: slot CUR ^ 1); kzc = wrap(k)
   auto layer = [&](auto cur_c, int k, int kzc) {
     [[maybe_unused]] constexpr int CUR = decltype(cur_c)::value;
-    [[maybe_unused]] const int s0 = RAW ? ring(k) : 0, s1 = s0 == 2 ? 0 : s0 + 1, s2 = s1 == 2 ? 0 : s1 + 1;
-    if constexpr (RAW) {
-      cp_async_wait_all();  // plane k + 1 (issued one layer earlier) has landed
-      __syncthreads();      // ... for every thread; the ring slot of plane k - 1 is free again
-      if (k + 2 <= k1) stage_plane(s2, wrap(k + 2, d.nz));
-    } else {
-      // the face butterflies are private to their thread, and the corner buffer FC alternates with
-      // the parity of the layer (the barrier of layer k - 1 orders the gather of layer k - 2 before
-      // the writes below), so no barrier is needed here
-      faces(std::integral_constant<int, CUR ^ 1>{}, next(kzc));
-    }
-    T* FC = RAW ? FC0 : FC0 + CUR * 4 * C * NE;
+    [[maybe_unused]] const int s0 = RAW ? ring(k) : 0, s1 = s0 == kRing - 1 ? 0 : s0 + 1;
+    // the face butterflies are private to their thread, and the corner buffer FC alternates with
+    // the parity of the layer (the barrier of layer k - 1 orders the gather of layer k - 2 before
+    // the writes below), so no barrier is needed before the element step
+    if constexpr (!RAW) faces(std::integral_constant<int, CUR ^ 1>{}, next(kzc));
+    T* FC = FC0 + CUR * 4 * C * NE;
     if (face_thread) {
       T bot[C][4], top[C][4];
       if constexpr (RAW) {
@@ -509,7 +505,14 @@ __global__ void __launch_bounds__(Hex8Tile<T>::NT, Hex8Tile<T>::PER_SM)
           for (int i = 0; i < 3; ++i) acc_t[j * 3 + i] += (double)t1[j][i];
       }
     }
+    // RAW: this thread's copies of plane k + 2 (issued three layers ago) have landed; the barrier
+    // makes them visible for element layer k + 1 and frees the slot of plane k - 1
+    if constexpr (RAW) cp_async_wait_group<1>();
     __syncthreads();
+    if constexpr (RAW) {
+      if (k + 4 <= k1) stage_plane(ring(k + 4), wrap(k + 4, d.nz));
+      else cp_async_commit();  // an empty group keeps one group per layer
+    }
     if (node_thread && k >= k0) {
       // node (i, j) of plane k is corner (1,1) of face (i-1, j-1), (0,1) of (i, j-1),
       // (1,0) of (i-1, j) and (0,0) of (i, j)
@@ -528,14 +531,19 @@ __global__ void __launch_bounds__(Hex8Tile<T>::NT, Hex8Tile<T>::PER_SM)
         if (RED == RED_STATS || RED == RED_SUMS) acc_y += (double)val * (double)val;
       }
     }
-    // RAW: the next layer's first barrier orders these reads of FC and of the staged plane before
-    // their next writes; otherwise the next layer writes the other corner buffer
+    // the next layer writes the other corner buffer; plane k's slot is refilled after the barrier
+    // of layer k + 1
   };
 
   int kz = wrap(k0 - 1, d.nz);
-  if constexpr (RAW) {
-    stage_plane(ring(k0 - 1), kz);
-    stage_plane(ring(k0), next(kz));
+  if constexpr (RAW) {  // planes k0 - 1 .. k0 + 2, one group each; the first two visible to all
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      if (k0 - 1 + p <= k1) stage_plane(ring(k0 - 1 + p), wrap(k0 - 1 + p, d.nz));
+      else cp_async_commit();
+    }
+    cp_async_wait_group<2>();
+    __syncthreads();
   } else {
     faces(std::integral_constant<int, 0>{}, kz);
   }
