@@ -59,9 +59,11 @@ constexpr int kHist = 2048;  // PCG coefficients kept per load (for the Lanczos 
 
 // Dot-product accumulator of the FP32 kernels.  On GB300 an FP64 instruction costs 64 FP32 lanes, so
 // the FP32 kernels do not accumulate in FP64 directly: each product is split exactly into float
-// head + tail (fma), both parts are added with Neumaier's compensated summation, and the per-thread
-// (sum, compensation) pair is converted to FP64 once.  The per-thread result carries FP64-level
-// accuracy; the CTA and grid reductions that follow are FP64.  The FP64 kernels accumulate in FP64.
+// head + tail (fma), the heads are added with Knuth's TwoSum, their rounding errors and the product
+// tails -- both of order 2^-24 of the heads -- are summed plainly into a compensation term, and the
+// per-thread (sum, compensation) pair is converted to FP64 once.  The per-thread result carries
+// FP64-level accuracy (relative error of order 2^-48 of the sum of magnitudes); the CTA and grid
+// reductions that follow are FP64.  The FP64 kernels accumulate in FP64.
 template <typename T> struct DotAcc {
   double s = 0.0;
   __device__ __forceinline__ void add(T a, T b) { s = fma((double)a, (double)b, s); }
@@ -69,19 +71,17 @@ template <typename T> struct DotAcc {
   __device__ __forceinline__ double value() const { return s; }
 };
 template <> struct DotAcc<float> {
-  float s = 0.0f, c = 0.0f;
-  __device__ __forceinline__ void add1(float v) {
-    const float t = s + v;
-    c += (fabsf(s) >= fabsf(v)) ? (s - t) + v : (v - t) + s;
-    s = t;
-  }
+  float s = 0.0f, c = 0.0f;  // head sum; TwoSum errors and product tails
   __device__ __forceinline__ void add(float a, float b) {
-    const float p = a * b;
-    add1(p);
-    add1(fmaf(a, b, -p));
+    const float p = a * b;  // a b = p + fma(a, b, -p) exactly
+    const float t = s + p;  // s + p = t + ((s - (t - z)) + (p - z)) exactly (TwoSum)
+    const float z = t - s;
+    c += ((s - (t - z)) + (p - z)) + fmaf(a, b, -p);
+    s = t;
   }
   // w = 1 or 2 (Parseval weights): exact in float
   __device__ __forceinline__ void add_scaled(float a, float b, double w) { add((float)w * a, b); }
+  __device__ __forceinline__ void scale2() { s += s; c += c; }  // exact
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 

@@ -988,11 +988,12 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_la
       }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        dot.add(wgt * r[c].x, z[c].x);  // wgt in {1, 2}: exact
-        dot.add(wgt * r[c].y, z[c].y);
+        dot.add(r[c].x, z[c].x);  // the column's Parseval weight is applied to the thread's sum below
+        dot.add(r[c].y, z[c].y);
         zr[c][k2] = z[c];
       }
     }
+    if (wgt != 1.0f) dot.scale2();
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       Dft<float2, 8, true>::run(zr[c]);
