@@ -465,6 +465,11 @@ fehom_status autotune_fft(fehom_ctx* ctx, int n_loads) {
   const int prec = sizeof(T) == 4 ? 1 : 0;
   auto& pl = ctx->plan[prec];
   if (!ctx->opt.autotune || pl.tuned_loads == n_loads) return FEHOM_OK;
+  // register-split passes forced on every axis: the generic passes are not used, nothing to time
+  if (prec == 1 && ctx->opt.fft_xy == 1 && fft_xy_supported(ctx->d, true) && fft_last128_supported(ctx->d, true)) {
+    pl.tuned_loads = n_loads;
+    return FEHOM_OK;
+  }
   cudaStream_t s = ctx->stream;
   T* fin = prec ? (T*)ctx->r32 : (T*)ctx->r64;
   T* fout = prec ? (T*)ctx->ap32 : (T*)ctx->ap64;
