@@ -87,6 +87,11 @@ typedef struct {
   int fft_xy;        /* FP32 register-split FFT passes: the fused x-y passes (3-D fields with 128 x 128 planes)
                         and the last-axis pass for nz = 128 (c = 1 or 3): -1 (default) the tuner decides for
                         each (the generic passes when autotune = 0), 0 never, 1 always when supported */
+  int residual_df;   /* mixed only: 1 (default) the refinement residual is updated as r -= K d for each FP32
+                        correction d, with K d evaluated in double-float arithmetic (pairs of floats, about
+                        48 significant bits, on the FP32 pipe) where supported (FEHOM_HEX8_3D elasticity with
+                        isotropic phases on cubic voxels; see fehom_residual_update); 0 always recomputes
+                        b - K x with the FP64 stiffness */
 } fehom_options;
 
 /* Kernel classes of one PCG iteration, for fehom_kernel_times. */
@@ -288,6 +293,19 @@ fehom_status fehom_apply_stiffness(fehom_ctx* ctx, const void* x, void* y, int p
 
 /* b = -D^T W C e for one macroscopic gradient / strain e (host, m doubles); b: c x N FP64. */
 fehom_status fehom_rhs(fehom_ctx* ctx, const double* e, double* b);
+
+/* Refinement residual in double-float arithmetic (the step of the mixed solve, option residual_df):
+   r_out = r_in - K d for one load, d an FP32 field (device, c x N, the layout of fehom_apply_stiffness),
+   r_in / r_out FP64 fields (device; r_out may equal r_in).  K d is evaluated with the FP64 kernel's
+   element (face form, closed-form isotropic duals, Sec. 5.1 operator K = D^T W C D) on pairs of floats
+   hi + lo: the first butterfly stage of d is exact, later sums and products round once in double-float
+   (relative error of order 2^-44 of the operands' magnitudes); r_out = r_in - (hi + lo) is formed in
+   FP64.  sums_out (host, 1 + m doubles, or NULL): ||r_out||^2, then the volume-averaged stress of the
+   field d alone (Mandel, no macroscopic strain; the change of <sigma> that adding d to the fluctuation
+   makes).  FEHOM_E_UNSUPPORTED_SIZE unless the context is FEHOM_HEX8_3D elasticity with isotropic phases
+   on cubic voxels. */
+fehom_status fehom_residual_update(fehom_ctx* ctx, const float* d, const double* r_in, double* r_out,
+                                   double* sums_out);
 
 /* z = K_ref^+ r = F^-1 K_hat^+ F r (Eq. M_inverse); r, z: c x N.  Needs fehom_precond_build. */
 fehom_status fehom_apply_precond(fehom_ctx* ctx, const void* r, void* z, int precision);

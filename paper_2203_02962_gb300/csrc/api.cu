@@ -41,6 +41,7 @@ struct fehom_ctx {
   uint8_t* ids = nullptr;
   double* mats64 = nullptr; float* mats32 = nullptr;   // [phase][D*D]
   double* iso64 = nullptr; float* iso32 = nullptr;     // [phase][kIsoStride]
+  float* isodf = nullptr;                               // [phase][16]: the iso constants as (hi, lo) float pairs
   double* rmats64 = nullptr; double* riso64 = nullptr;  // reference material (one phase)
   double2* tw64[3] = {nullptr, nullptr, nullptr};
   float2* tw32[3] = {nullptr, nullptr, nullptr};
@@ -682,8 +683,45 @@ fehom_status upload_tau(fehom_ctx* ctx, int n_loads, const double* loads) {
 // with the fused statistics: y2[l] = ||y_l||^2 and flux[l] = <sigma>_l (Sec. 2 average with the
 // quadrature of Eq. global_sum), recovered from the summed monomial-1 duals as P S^-1 sum T / |Y|.
 // Needs upload_tau for the same loads first.
+// Volume-averaged flux / stress of every load from the sums T (n_loads x D) of the monomial-1 duals
+// over all elements (sum T = |Y| S P^T <sigma>).
+void sums_to_flux(const fehom_ctx* ctx, int n_loads, const std::vector<double>& T, std::vector<double>* flux) {
+  const int dim = ctx->d.dim, m = ctx->m, D = ctx->D;
+  const std::vector<double> P = grad_to_flux(dim, ctx->physics);
+  double w, sc[3];
+  kernel_scales(ctx, &w, sc);
+  double cell = 1.0;
+  const int n3[3] = {ctx->d.nx, ctx->d.ny, ctx->d.nz};
+  for (int i = 0; i < dim; ++i) cell *= ctx->h[i] * n3[i];
+  flux->assign((size_t)n_loads * m, 0.0);
+  for (int l = 0; l < n_loads; ++l)
+    for (int I = 0; I < m; ++I) {
+      double v = 0.0;
+      for (int q = 0; q < D; ++q) v += P[I * D + q] * T[(size_t)l * D + q] / sc[q % dim];
+      (*flux)[(size_t)l * m + I] = v / cell;
+    }
+}
+
+// Per-load sums of the stiffness statistics partials [load][cta][1 + D]: y2 = sum y^2, T = dual sums.
+fehom_status reduce_stats(fehom_ctx* ctx, int n_loads, int ctas, std::vector<double>* y2, std::vector<double>* T) {
+  const int D = ctx->D, W = 1 + D;
+  std::vector<double> hp((size_t)n_loads * ctas * W);
+  CK(cudaMemcpyAsync(hp.data(), ctx->partial, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (y2) y2->assign(n_loads, 0.0);
+  if (T) T->assign((size_t)n_loads * D, 0.0);
+  for (int l = 0; l < n_loads; ++l)
+    for (int b = 0; b < ctas; ++b) {  // fixed order
+      const double* pb = &hp[((size_t)l * ctas + b) * W];
+      if (y2) (*y2)[l] += pb[0];
+      if (T)
+        for (int i = 0; i < D; ++i) (*T)[(size_t)l * D + i] += pb[1 + i];
+    }
+  return FEHOM_OK;
+}
+
 fehom_status residual_stats(fehom_ctx* ctx, int n_loads, const double* x, double* y, std::vector<double>* y2,
-                            std::vector<double>* flux) {
+                            std::vector<double>* flux, std::vector<double>* tsum = nullptr) {
   StencilArgs a = stencil_args(ctx, false, n_loads);
   a.x = x;
   a.y = y;
@@ -697,36 +735,33 @@ fehom_status residual_stats(fehom_ctx* ctx, int n_loads, const double* x, double
   CK(launch_stiffness<double>(a, ctx->stream, &got));
   count_launch(ctx);
   if (got != ctas) FAIL(FEHOM_E_CUDA, "stiffness statistics: CTA count mismatch");
-  std::vector<double> hp((size_t)n_loads * ctas * W);
-  CK(cudaMemcpyAsync(hp.data(), ctx->partial, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  const int dim = ctx->d.dim, m = ctx->m, D = ctx->D;
-  const std::vector<double> P = grad_to_flux(dim, ctx->physics);
-  double w, sc[3];
-  kernel_scales(ctx, &w, sc);
-  double cell = 1.0;
-  const int n3[3] = {ctx->d.nx, ctx->d.ny, ctx->d.nz};
-  for (int i = 0; i < dim; ++i) cell *= ctx->h[i] * n3[i];
-  if (y2) y2->assign(n_loads, 0.0);
-  if (flux) flux->assign((size_t)n_loads * m, 0.0);
-  std::vector<double> T(D);
-  for (int l = 0; l < n_loads; ++l) {
-    double yy = 0.0;
-    std::fill(T.begin(), T.end(), 0.0);
-    for (int b = 0; b < ctas; ++b) {
-      const double* pb = &hp[((size_t)l * ctas + b) * W];
-      yy += pb[0];
-      for (int i = 0; i < D; ++i) T[i] += pb[1 + i];
-    }
-    if (y2) (*y2)[l] = yy;
-    if (flux)
-      for (int I = 0; I < m; ++I) {
-        double v = 0.0;
-        for (int q = 0; q < D; ++q) v += P[I * D + q] * T[q] / sc[q % dim];
-        (*flux)[(size_t)l * m + I] = v / cell;
-      }
-  }
+  std::vector<double> T;
+  TRY(reduce_stats(ctx, n_loads, ctas, y2, &T));
+  if (flux) sums_to_flux(ctx, n_loads, T, flux);
+  if (tsum) *tsum = T;
   return FEHOM_OK;
+}
+
+// Refinement residual in double-float arithmetic: r_out = r_in - K d for FP32 corrections d
+// (hex8 elasticity, isotropic phases, cubic voxels), with ||r_out||^2 and the dual sums of d.
+bool residual_df_supported(const fehom_ctx* ctx) {
+  return ctx->isodf != nullptr && ctx->d.elem == HEX8_3D && ctx->d.c == 3;
+}
+
+fehom_status residual_update_df(fehom_ctx* ctx, int n_loads, const float* d, const double* r_in, double* r_out,
+                                std::vector<double>* y2, std::vector<double>* dT) {
+  StencilArgs a = stencil_args(ctx, true, n_loads);
+  a.x = d;
+  a.y = r_out;
+  a.iso = ctx->isodf;
+  const int ctas = residual_df_ctas(ctx->d, n_loads);
+  TRY(ensure_partial(ctx, (size_t)n_loads * ctas * (1 + ctx->D)));
+  a.stats = ctx->partial;
+  int got = 0;
+  CK(launch_residual_df(a, r_in, ctx->stream, &got));
+  count_launch(ctx);
+  if (got != ctas) FAIL(FEHOM_E_CUDA, "double-float residual: CTA count mismatch");
+  return reduce_stats(ctx, n_loads, ctas, y2, dT);
 }
 
 // --------------------------------------------------------------------------------------------------
@@ -806,6 +841,7 @@ void fehom_default_options(fehom_options* opt) {
   opt->autotune = 1;
   opt->x0_scaling = 1;
   opt->fft_xy = -1;
+  opt->residual_df = 1;
 }
 
 const char* fehom_last_error(const fehom_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
@@ -1161,7 +1197,7 @@ void fehom_destroy(fehom_ctx* ctx) {
     for (int i = 0; i < kChunk; ++i)
       for (int k = 0; k < FEHOM_K_COUNT; ++k)
         for (int j = 0; j < 2; ++j) cudaEventDestroy(ctx->ev[i][k][j]);
-  dfree(ctx->ids); dfree(ctx->mats64); dfree(ctx->mats32); dfree(ctx->iso64); dfree(ctx->iso32);
+  dfree(ctx->ids); dfree(ctx->mats64); dfree(ctx->mats32); dfree(ctx->iso64); dfree(ctx->iso32); dfree(ctx->isodf);
   dfree(ctx->rmats64); dfree(ctx->riso64);
   for (int i = 0; i < 3; ++i) { dfree(ctx->tw64[i]); dfree(ctx->tw32[i]); }
   dfree(ctx->sym64); dfree(ctx->sym32);
@@ -1280,10 +1316,22 @@ static fehom_status setup_impl(fehom_ctx* ctx, int elem, int physics, const int6
     if (all) {
       ctx->iso = true;
       std::vector<float> iso32(iso.begin(), iso.end());
+      // double-float copy of the six constants, hi = fl(v), lo = fl(v - hi) (refinement residuals)
+      std::vector<float> isodf((size_t)16 * n_phases, 0.0f);
+      for (int p = 0; p < n_phases; ++p)
+        for (int i = 0; i < 6; ++i) {
+          const double v = iso[(size_t)kIsoStride * p + i];
+          const float hi = (float)v;
+          isodf[(size_t)16 * p + 2 * i] = hi;
+          isodf[(size_t)16 * p + 2 * i + 1] = (float)(v - (double)hi);
+        }
       CK(cudaMalloc(&ctx->iso64, iso.size() * sizeof(double)));
       CK(cudaMalloc(&ctx->iso32, iso.size() * sizeof(float)));
+      CK(cudaMalloc(&ctx->isodf, isodf.size() * sizeof(float)));
       CK(cudaMemcpyAsync(ctx->iso64, iso.data(), iso.size() * sizeof(double), cudaMemcpyHostToDevice, s));
       CK(cudaMemcpyAsync(ctx->iso32, iso32.data(), iso32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(ctx->isodf, isodf.data(), isodf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+      CK(cudaStreamSynchronize(s));  // the host copies above are locals
     }
     double lam, mu;
     if (iso_elastic(ctx->cref.data(), 3, &lam, &mu)) {
@@ -1486,6 +1534,21 @@ fehom_status fehom_rhs(fehom_ctx* ctx, const double* e, double* b) {
   if (!ctx || !e || !b) return FEHOM_E_INVALID;
   TRY(upload_tau(ctx, 1, e));
   return residual_stats(ctx, 1, nullptr, b, nullptr, nullptr);
+}
+
+fehom_status fehom_residual_update(fehom_ctx* ctx, const float* d, const double* r_in, double* r_out,
+                                   double* sums_out) {
+  if (!ctx || !d || !r_in || !r_out) return FEHOM_E_INVALID;
+  if (!residual_df_supported(ctx))
+    FAIL(FEHOM_E_UNSUPPORTED_SIZE, "fehom_residual_update: hex8 elasticity with isotropic phases on cubic voxels only");
+  std::vector<double> y2, dT, fl;
+  TRY(residual_update_df(ctx, 1, d, r_in, r_out, &y2, &dT));
+  if (sums_out) {
+    sums_to_flux(ctx, 1, dT, &fl);
+    sums_out[0] = y2[0];
+    for (int i = 0; i < ctx->m; ++i) sums_out[1 + i] = fl[i];
+  }
+  return FEHOM_OK;
 }
 
 fehom_status fehom_apply_precond(fehom_ctx* ctx, const void* r, void* z, int precision) {
@@ -1731,6 +1794,8 @@ struct SolveRun {
   std::vector<PcgState> hs;
   std::vector<int> outer_it, inner_it;
   std::vector<double> relM, flux, rel2, bn2, rn2, bnorm2;
+  std::vector<double> tsum;  // mixed: dual sums of the current x (+ e), updated with each correction
+  bool df = false;           // mixed: refinement residuals r -= K d in double-float arithmetic
   std::vector<bool> done;
   int total_inner = 0;
   int steps = 0;
@@ -1746,7 +1811,8 @@ struct SolveRun {
     if (mixed) TRY(autotune_fft<float>(ctx, n_loads));
     else TRY(autotune_fft<double>(ctx, n_loads));
     TRY(upload_tau(ctx, n_loads, loads));
-    TRY(residual_stats(ctx, n_loads, nullptr, ctx->b64, &bn2, nullptr));  // b = -D^T W C e
+    TRY(residual_stats(ctx, n_loads, nullptr, ctx->b64, &bn2, nullptr, &tsum));  // b = -D^T W C e
+    df = mixed && ctx->opt.residual_df != 0 && residual_df_supported(ctx);
     outer_it.assign(n_loads, 0);
     inner_it.assign(n_loads, 0);
     relM.assign(n_loads, 1.0);
@@ -1808,9 +1874,20 @@ struct SolveRun {
     cudaStream_t s = ctx->stream;
     const long long cN = (long long)ctx->d.c * ctx->d.N;
     const double* r64 = ctx->b64;
-    if (steps > 0 || x0) {
+    if (steps > 0 && df) {
+      // r = b - K x updated by the last correction d (x += d in FP64): r -= K d with K d in
+      // double-float arithmetic (FP32 pairs), ||r||^2 and <sigma> from the dual sums of x + e
+      std::vector<double> dT;
+      TRY(residual_update_df(ctx, n_loads, ctx->x32, (steps == 1 && !x0) ? ctx->b64 : ctx->r64, ctx->r64, &rn2,
+                             &dT));
+      for (size_t i = 0; i < tsum.size(); ++i) tsum[i] += dT[i];
+      sums_to_flux(ctx, n_loads, tsum, &flux);
+      r64 = ctx->r64;
+      stats_current = true;
+      last_res = ctx->r64;
+    } else if (steps > 0 || x0) {
       // true residual r = b - K x = -D^T W C (e + D x) in FP64, with ||r||^2 and <sigma>
-      TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->r64, &rn2, &flux));
+      TRY(residual_stats(ctx, n_loads, ctx->x64, ctx->r64, &rn2, &flux, &tsum));
       r64 = ctx->r64;
       stats_current = true;
       last_res = ctx->r64;

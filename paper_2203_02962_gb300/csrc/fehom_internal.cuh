@@ -123,6 +123,12 @@ cudaError_t launch_stiffness(const StencilArgs& a, cudaStream_t s, int* ctas = n
 
 // CTAs per load of a stiffness launch (the stride of the statistics partials)
 int stiffness_ctas(const Dims& d, int n_loads);  // CTAs per load of an FP64 launch over n_loads loads
+// Refinement residual r_out = r_in - K d in double-float arithmetic (stencil.cu): a.x = d (float),
+// a.y = r_out (double, may alias r_in), a.iso = the double-float isotropic table ([phase][16] floats:
+// lambda', mu', 2 mu', lambda'/3, mu'/3, (lambda' + 4 mu')/9 as hi, lo pairs), a.stats = partial sums
+// [load][cta][1 + 9] (sum r_out^2, sums of the monomial-1 duals of d); hex8 elasticity only.
+cudaError_t launch_residual_df(const StencilArgs& a, const double* r_in, cudaStream_t s, int* ctas);
+int residual_df_ctas(const Dims& d, int n_loads);
 
 cudaError_t launch_phase_histogram(const uint8_t* ids, long long N, unsigned long long* hist,
                                    cudaStream_t s);

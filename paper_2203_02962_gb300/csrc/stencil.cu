@@ -1027,6 +1027,217 @@ cudaError_t dispatch_pixel4(const StencilArgs& a, int* ctas, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+
+// ------------------------------------------------------------------------------------------------
+// Refinement residual in double-float arithmetic (hex8 elasticity, isotropic phases, cubic voxels):
+//   r_out = r_in - K d,   K d = D^T W C D d  for an FP32 correction field d,
+// the element evaluated as in hex8_element_faces (face form, closed-form isotropic duals) on
+// double-float values: a value is hi + lo in two floats (about 48 significant bits), so the FP64-
+// accurate residual runs on the FP32 pipe, which on GB300 issues 64 times the FP64 rate.  The first
+// butterfly stage of the FP32 inputs is exact (TwoSum); later sums and products round once in
+// double-float, with an error of order 2^-44 of the operands' magnitudes.  r_in and r_out are FP64
+// (r_out may alias r_in); r_out = r_in - (hi + lo) is formed in FP64.  Fused statistics per load and
+// CTA: sum r_out^2 and the sums of the monomial-1 duals of d over the CTA's elements (the change of
+// |Y| S P^T <sigma>), [load][cta][1 + 9] doubles.  Tiles as the FP32 kernel (32 x 8), one CTA per SM.
+// ------------------------------------------------------------------------------------------------
+struct __align__(8) DF {
+  float h, l;
+};
+// Knuth's TwoSum: a + b = s + e exactly
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+// Dekker's FastTwoSum (|s| >= |e|): renormalises (s, e)
+__device__ __forceinline__ DF df_norm(float s, float e) {
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+__device__ __forceinline__ DF operator+(DF a, DF b) {
+  const DF s = df_two_sum(a.h, b.h);
+  return df_norm(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ DF operator-(DF a, DF b) {
+  const DF s = df_two_sum(a.h, -b.h);
+  return df_norm(s.h, s.l + (a.l - b.l));
+}
+__device__ __forceinline__ DF operator*(DF a, DF c) {  // the lo x lo term (2^-48) is dropped
+  const float p = a.h * c.h;
+  float e = fmaf(a.h, c.h, -p);
+  e = fmaf(a.h, c.l, e);
+  e = fmaf(a.l, c.h, e);
+  return df_norm(p, e);
+}
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (double)a.l; }
+
+__global__ void __launch_bounds__(Hex8Tile<float>::NT, 1)
+    hex8_residual_df_kernel(StencilArgs a, const double* __restrict__ r_in, int kz_per_cta) {
+  constexpr int C = 3, BY = Hex8Tile<float>::BY, NE = Hex8Tile<float>::NE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DF* FB = reinterpret_cast<DF*>(smem_raw);  // [2 planes][4][C][NE] face butterflies (thread-private)
+  DF* FC0 = FB + 2 * 4 * C * NE;             // [2 layers][4 corners][C][NE] face contributions
+  __shared__ double red_sh[32];
+
+  const Dims d = a.d;
+  const int load = blockIdx.z;
+  const int tiles_x = (d.nx + BX - 1) / BX;
+  const int i0 = (blockIdx.x % tiles_x) * BX;
+  const int j0 = (blockIdx.x / tiles_x) * BY;
+  const int k0 = blockIdx.y * kz_per_cta;
+  const int k1 = min(k0 + kz_per_cta, d.nz);
+  const int tid = threadIdx.x;
+  const float* dx = reinterpret_cast<const float*>(a.x) + (long long)load * a.load_stride;
+  const double* rin = r_in + (long long)load * a.load_stride;
+  double* rout = reinterpret_cast<double*>(a.y) + (long long)load * a.load_stride;
+  const float* isodf = reinterpret_cast<const float*>(a.iso);  // [phase][16]: 6 constants as (hi, lo)
+  const long long plane = (long long)d.nx * d.ny;
+
+  const int ei = tid % EX, ej = tid / EX;
+  const bool face_thread = tid < NE;
+  const int fi0 = wrap(i0 - 1 + ei, d.nx), fi1 = wrap(i0 + ei, d.nx);
+  const int fj0 = wrap(j0 - 1 + ej, d.ny), fj1 = wrap(j0 + ej, d.ny);
+  const int off00 = fj0 * d.nx + fi0, off10 = fj0 * d.nx + fi1, off01 = fj1 * d.nx + fi0, off11 = fj1 * d.nx + fi1;
+  const bool owner = face_thread && ei >= 1 && ej >= 1 && i0 + ei - 1 < d.nx && j0 + ej - 1 < d.ny;
+  const int ni = tid % BX, nj = tid / BX;
+  const bool node_thread = tid < BX * BY && (i0 + ni) < d.nx && (j0 + nj) < d.ny;
+  const long long node_off = (long long)(j0 + nj) * d.nx + i0 + ni;
+
+  DF carry[C][4];
+#pragma unroll
+  for (int j = 0; j < C; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) carry[j][q] = {0.0f, 0.0f};
+  DF acc_t[3 * C];
+#pragma unroll
+  for (int i = 0; i < 3 * C; ++i) acc_t[i] = {0.0f, 0.0f};
+  double acc_y = 0.0;
+
+  auto next = [&](int z) { return z + 1 == d.nz ? 0 : z + 1; };
+  auto faces = [&](int slot, int kz) {  // in-plane butterflies of plane kz (exact first stage)
+    if (face_thread) {
+      const float* xk = dx + (long long)kz * plane;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const float* xj = xk + (long long)j * d.N;
+        const float v00 = __ldg(xj + off00), v10 = __ldg(xj + off10), v01 = __ldg(xj + off01), v11 = __ldg(xj + off11);
+        const DF s0 = df_two_sum(v10, v00), d0 = df_two_sum(v10, -v00);
+        const DF s1 = df_two_sum(v11, v01), d1 = df_two_sum(v11, -v01);
+        DF* fb = FB + ((slot * 4) * C + j) * NE + tid;
+        fb[0 * C * NE] = s1 + s0;
+        fb[1 * C * NE] = s1 - s0;
+        fb[2 * C * NE] = d1 + d0;
+        fb[3 * C * NE] = d1 - d0;
+      }
+    }
+  };
+
+  // element layer k (planes k: slot cur, k + 1: slot cur ^ 1), then the gather of plane k
+  auto layer = [&](int cur, int k, int kzc) {
+    faces(cur ^ 1, next(kzc));
+    DF* FC = FC0 + cur * 4 * C * NE;
+    if (face_thread) {
+      DF q1[C], q2[C], q3[C], q4[C], q5[C], q6[C], q7[C];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const DF b0 = FB[((cur * 4 + 0) * C + j) * NE + tid], t0 = FB[(((cur ^ 1) * 4 + 0) * C + j) * NE + tid];
+        const DF b1 = FB[((cur * 4 + 1) * C + j) * NE + tid], t1 = FB[(((cur ^ 1) * 4 + 1) * C + j) * NE + tid];
+        const DF b2 = FB[((cur * 4 + 2) * C + j) * NE + tid], t2 = FB[(((cur ^ 1) * 4 + 2) * C + j) * NE + tid];
+        const DF b3 = FB[((cur * 4 + 3) * C + j) * NE + tid], t3 = FB[(((cur ^ 1) * 4 + 3) * C + j) * NE + tid];
+        q3[j] = t0 - b0;
+        q2[j] = t1 + b1;
+        q5[j] = t1 - b1;
+        q1[j] = t2 + b2;
+        q6[j] = t2 - b2;
+        q4[j] = t3 + b3;
+        q7[j] = t3 - b3;
+      }
+      const int ph = a.ids ? a.ids[(long long)kzc * plane + off00] : 0;
+      const float4 c0 = __ldg(reinterpret_cast<const float4*>(isodf + 16 * ph));
+      const float4 c1 = __ldg(reinterpret_cast<const float4*>(isodf + 16 * ph) + 1);
+      const float4 c2 = __ldg(reinterpret_cast<const float4*>(isodf + 16 * ph) + 2);
+      const DF lam = {c0.x, c0.y}, mu = {c0.z, c0.w}, mu2 = {c1.x, c1.y}, L = {c1.z, c1.w}, M = {c2.x, c2.y},
+               K7 = {c2.z, c2.w};
+      DF Q1[C], Q2[C], Q3[C], Q4[C], Q5[C], Q6[C], Q7[C];
+      const DF lt = lam * ((q1[0] + q2[1]) + q3[2]);
+      Q1[0] = mu2 * q1[0] + lt;
+      Q2[1] = mu2 * q2[1] + lt;
+      Q3[2] = mu2 * q3[2] + lt;
+      Q1[1] = Q2[0] = mu * (q1[1] + q2[0]);
+      Q1[2] = Q3[0] = mu * (q1[2] + q3[0]);
+      Q2[2] = Q3[1] = mu * (q2[2] + q3[1]);
+      const DF Ltx = L * (q4[1] + q6[2]), Lty = L * (q4[0] + q5[2]), Ltz = L * (q6[0] + q5[1]);
+      const DF sm = (q4[2] + q5[0]) + q6[1];
+      Q4[0] = mu * q4[0] + Lty;
+      Q4[1] = mu * q4[1] + Ltx;
+      Q4[2] = M * (q4[2] + sm);
+      Q5[0] = M * (q5[0] + sm);
+      Q5[1] = mu * q5[1] + Ltz;
+      Q5[2] = mu * q5[2] + Lty;
+      Q6[0] = mu * q6[0] + Ltz;
+      Q6[1] = M * (q6[1] + sm);
+      Q6[2] = mu * q6[2] + Ltx;
+#pragma unroll
+      for (int j = 0; j < C; ++j) Q7[j] = K7 * q7[j];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        // transposed z part, face total of plane k, transposed in-plane part
+        const DF ss = carry[j][0] - Q3[j], sd = (Q2[j] - Q5[j]) + carry[j][1];
+        const DF ds = (Q1[j] - Q6[j]) + carry[j][2], dd = (Q4[j] - Q7[j]) + carry[j][3];
+        carry[j][0] = Q3[j];
+        carry[j][1] = Q2[j] + Q5[j];
+        carry[j][2] = Q1[j] + Q6[j];
+        carry[j][3] = Q4[j] + Q7[j];
+        const DF s0 = ss - sd, s1 = ss + sd, d0 = ds - dd, d1 = ds + dd;
+        FC[(0 * C + j) * NE + tid] = s0 - d0;
+        FC[(1 * C + j) * NE + tid] = s0 + d0;
+        FC[(2 * C + j) * NE + tid] = s1 - d1;
+        FC[(3 * C + j) * NE + tid] = s1 + d1;
+      }
+      if (owner && k >= k0) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          acc_t[j * 3 + 0] = acc_t[j * 3 + 0] + Q1[j];
+          acc_t[j * 3 + 1] = acc_t[j * 3 + 1] + Q2[j];
+          acc_t[j * 3 + 2] = acc_t[j * 3 + 2] + Q3[j];
+        }
+      }
+    }
+    __syncthreads();
+    if (node_thread && k >= k0) {
+      const int e00 = nj * EX + ni;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const DF v = ((FC[(3 * C + j) * NE + e00] + FC[(2 * C + j) * NE + e00 + 1]) + FC[(1 * C + j) * NE + e00 + EX]) +
+                     FC[(0 * C + j) * NE + e00 + EX + 1];
+        const long long gidx = (long long)j * d.N + (long long)kzc * plane + node_off;
+        const double rv = rin[gidx] - df_to_double(v);
+        rout[gidx] = rv;
+        acc_y = fma(rv, rv, acc_y);
+      }
+    }
+  };
+
+  int kz = wrap(k0 - 1, d.nz);
+  faces(0, kz);
+  int cur = 0;
+  for (int k = k0 - 1; k < k1; ++k) {
+    layer(cur, k, kz);
+    kz = next(kz);
+    cur ^= 1;
+  }
+
+  const int nblk = gridDim.x * gridDim.y;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  double* out = a.stats + ((long long)load * nblk + bid) * (1 + 3 * C);
+  const double ty = block_sum(acc_y, red_sh);
+  if (threadIdx.x == 0) out[0] = ty;
+#pragma unroll
+  for (int i = 0; i < 3 * C; ++i) {
+    const double t = block_sum(df_to_double(acc_t[i]), red_sh);
+    if (threadIdx.x == 0) out[1 + i] = t;
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -1051,6 +1262,25 @@ int stiffness_ctas(const Dims& d, int n_loads) {
     return tiles * slabs;
   }
   return ((d.nx + BX - 1) / BX) * ((d.ny + BY2 - 1) / BY2);
+}
+
+cudaError_t launch_residual_df(const StencilArgs& a, const double* r_in, cudaStream_t s, int* ctas) {
+  const Dims& d = a.d;
+  if (d.elem != HEX8_3D || d.c != 3 || a.iso == nullptr || a.stats == nullptr) return cudaErrorInvalidValue;
+  int tiles, slabs, kz;
+  hex8_grid<float>(d, a.n_loads, &tiles, &slabs, &kz);
+  if (ctas) *ctas = tiles * slabs;
+  const size_t smem = sizeof(DF) * (size_t)(2 + 2) * 4 * 3 * Hex8Tile<float>::NE;
+  cudaError_t e = set_smem(hex8_residual_df_kernel, smem);
+  if (e != cudaSuccess) return e;
+  hex8_residual_df_kernel<<<dim3(tiles, slabs, a.n_loads), Hex8Tile<float>::NT, smem, s>>>(a, r_in, kz);
+  return cudaGetLastError();
+}
+
+int residual_df_ctas(const Dims& d, int n_loads) {
+  int tiles, slabs, kz;
+  hex8_grid<float>(d, n_loads, &tiles, &slabs, &kz);
+  return tiles * slabs;
 }
 
 template cudaError_t launch_stiffness<double>(const StencilArgs&, cudaStream_t, int*);

@@ -7,6 +7,8 @@ against the oracle's PCG, batched vs one-by-one loads, mixed vs FP64.  Error pat
 codes.  Tolerances: FP64 operators 1e-12 relative to the largest entry; FP32 operators 2e-5;
 solves at tol 1e-12: C_eff 1e-10 relative, fields 1e-9 relative max-norm.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -613,3 +615,95 @@ def test_full_size_mixed_meets_fp64_energy_c_eff():
         ce[prec] = s.effective_energy()
         s.close()
     assert _rel(ce["mixed"], ce["fp64"]) < 1e-7
+
+
+@pytest.mark.parametrize("shape", [(12, 12, 48), (24, 24, 24), (6, 6, 96)])
+def test_double_float_residual_update_matches_oracle(shape):
+    """r_out = r_in - K d with K d in double-float arithmetic (isotropic phases, cubic voxels): against
+    the oracle's assembled K at FP64-level accuracy, ||r_out||^2 in FP64, and <sigma> of d alone
+    against the oracle's volume average.  The shapes span several 32 x 8 tiles with ragged edges."""
+    torch = _torch()
+    g = fem.Grid(shape, "hex8_3d", "elastic")
+    cell = tuple(float(n) / 16.0 for n in shape[::-1])  # cubic voxels, h = 1/16 (x, y, z)
+    g.h = np.array(cell) / np.array(g.n_xyz, float)
+    g.vp = float(np.prod(g.h))
+    rng = np.random.default_rng(21)
+    ids = rng.integers(0, 3, size=shape).astype(np.uint8)
+    mod = np.stack([I.isotropic_elastic_mandel(1.0, 0.3), I.isotropic_elastic_mandel(100.0, 0.2),
+                    I.isotropic_elastic_mandel(7.0, 0.45)])
+    K = fem.assemble_K(g, ids.ravel(), mod)
+    d = rng.standard_normal(g.c * g.N).astype(np.float32)
+    r_in = rng.standard_normal(g.c * g.N)
+    ref = r_in - K @ d.astype(np.float64)
+    s = _solver("hex8_3d", "elastic", shape, ids, mod, cell=cell)
+    r_out, rn2, sig = s.residual_update(torch.tensor(d, device="cuda"), torch.tensor(r_in, device="cuda"))
+    r_out = r_out.cpu().numpy()
+    scale = np.abs(K).max() * np.abs(d).max()
+    assert np.abs(r_out - ref).max() <= 1e-11 * scale
+    assert abs(rn2 - float(ref @ ref)) <= 1e-10 * float(ref @ ref)
+    sig_ref = fem.mean_flux(g, ids.ravel(), mod, np.zeros(6), d.astype(np.float64)) / (g.vp * g.N)
+    assert np.abs(sig - sig_ref).max() <= 1e-11 * np.abs(sig_ref).max()
+    # in place (r_out = r_in)
+    r = torch.tensor(r_in, device="cuda")
+    s.residual_update(torch.tensor(d, device="cuda"), r, r)
+    assert np.abs(r.cpu().numpy() - ref).max() <= 1e-11 * scale
+    s.close()
+
+
+def test_double_float_residual_update_full_size_sampled():
+    """The 128^3 benchmark cell: the double-float update against the FP64 stiffness kernel everywhere
+    (both are checked against the oracle's rows elsewhere) and against the oracle's rows on a sample."""
+    torch = _torch()
+    w = I.workload_spheres_elastic(128, seed=0)
+    shape = (128, 128, 128)
+    g = fem.Grid(shape, "hex8_3d", "elastic")
+    s = _solver("hex8_3d", "elastic", shape, w["ids"], w["moduli"])
+    rng = np.random.default_rng(22)
+    d = torch.tensor(rng.standard_normal(g.c * g.N).astype(np.float32), device="cuda")
+    r_in = torch.tensor(rng.standard_normal(g.c * g.N), device="cuda")
+    r_out, _, _ = s.residual_update(d, r_in)
+    kd = s.apply_stiffness(d.double())
+    ref = (r_in - kd).cpu().numpy()
+    out = r_out.cpu().numpy()
+    scale = float(kd.abs().max())
+    assert np.abs(out - ref).max() <= 1e-11 * scale
+    rows = rng.integers(0, g.c * g.N, 2000)
+    kd_rows = fem.stiffness_rows(g, w["ids"].ravel(), w["moduli"], d.double().cpu().numpy(), rows)
+    assert np.abs(out[rows] - (r_in.cpu().numpy()[rows] - kd_rows)).max() <= 1e-11 * scale
+    s.close()
+
+
+def test_mixed_solve_double_float_residual_agrees_with_fp64_residual():
+    """The mixed solve with refinement residuals updated in double-float arithmetic agrees with the one
+    that recomputes b - K x by the FP64 stiffness: same iteration counts (within one), fields and C_eff."""
+    n = 32
+    ids, mod = _small_elastic(n, seed=23)
+    out = {}
+    for df in (True, False):
+        s = _solver("hex8_3d", "elastic", (n, n, n), ids, mod, precision="mixed", residual_df=df)
+        s.precond_build()
+        o = s.solve(np.eye(6), tol=1e-6)
+        out[df] = (o, s.effective_energy(), o["fields"].cpu().numpy())
+        s.close()
+    (a, ea, fa), (b, eb, fb) = out[True], out[False]
+    assert all(i["converged"] for i in a["info"]) and all(i["converged"] for i in b["info"])
+    for ia, ib in zip(a["info"], b["info"]):
+        assert abs(ia["iterations"] - ib["iterations"]) <= 1 and ia["refinements"] == ib["refinements"]
+    assert _rel(a["C_eff"], b["C_eff"]) < 1e-9
+    assert _rel(ea, eb) < 1e-11
+    assert np.abs(fa - fb).max() < 1e-8 * np.abs(fb).max()
+
+
+def test_double_float_residual_rejects_unsupported_contexts():
+    """Anisotropic phases (no isotropic table): FEHOM_E_UNSUPPORTED_SIZE, nothing written."""
+    torch = _torch()
+    shape = (8, 8, 8)
+    ids = np.zeros(shape, np.uint8)
+    s = _solver("hex8_3d", "elastic", shape, ids, _materials("elastic", 3, "aniso")[:1])
+    d = torch.zeros(3 * 512, dtype=torch.float32, device="cuda")
+    r = torch.ones(3 * 512, dtype=torch.float64, device="cuda")
+    st = s.lib.fehom_residual_update(s.ctx, C.c_void_p(d.data_ptr()), C.c_void_p(r.data_ptr()),
+                                     C.c_void_p(r.data_ptr()), None)
+    assert st == 2  # FEHOM_E_UNSUPPORTED_SIZE
+    assert float(r.min()) == 1.0 and float(r.max()) == 1.0
+    s.close()
