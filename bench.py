@@ -205,7 +205,7 @@ def run_ours(args):
         load_iters = sum(sum(i["iterations"] for i in o["info"]) for o in outs)
         results[prec] = dict(ms=ms, iters=load_iters / args.steps, out=outs[-1], clocks=clk.summary(), kt=kt,
                              load_iters=load_iters, launches=s.launch_count() - l_before,
-                             plan=s.fft_plan(prec), C_energy=s.effective_energy())
+                             plan=s.fft_plan(prec), stencil=s.stencil_plan(prec), C_energy=s.effective_energy())
         s.close()
 
     # e2e: host phase ids -> setup -> build -> solve -> fields back to pinned host memory
@@ -298,8 +298,11 @@ def run_ours(args):
                   "C_eff_energy_rel_err_vs_fp64_tol1e-10": float(np.abs(rmx["C_energy"] - C_ref_energy).max()
                                                                  / np.abs(C_ref_energy).max()),
                   "kernel_ms": {k: v[0] for k, v in rmx["kt"].items()},
-                  "gpu_launches": rmx["launches"], "fft_plan": rmx["plan"], "clocks": rmx["clocks"]},
+                  "gpu_launches": rmx["launches"], "fft_plan": rmx["plan"],
+                  "stencil_plan": {"rows": rmx["stencil"][0], "ms_rows_8_16": rmx["stencil"][1]},
+                  "clocks": rmx["clocks"]},
         "fft_plan_fp64": r64["plan"],
+        "stencil_plan_fp64": {"rows": r64["stencil"][0], "ms_rows_8_16": r64["stencil"][1]},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_ops / 1e12, "peak": FP64_INSTR_PEAK / 1e12,
                      "unit": "T FP64-instr/s", "frac": achieved_ops / FP64_INSTR_PEAK,
                      "traffic": FP64_STIFFNESS_DRAM_BYTES if dom == "stiffness" else None,

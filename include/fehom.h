@@ -92,6 +92,9 @@ typedef struct {
                         48 significant bits, on the FP32 pipe) where supported (FEHOM_HEX8_3D elasticity with
                         isotropic phases on cubic voxels; see fehom_residual_update); 0 always recomputes
                         b - K x with the FP64 stiffness */
+  int stencil_rows;  /* FEHOM_HEX8_3D PCG stiffness apply: node rows per tile (tiles are 32 x rows nodes), 8 or
+                        16; 0 (default) the stencil tuner times both on the first solve of a batch size and
+                        keeps the faster (with autotune = 0: 16 for FP64, 8 for FP32); see fehom_stencil_plan */
 } fehom_options;
 
 /* Kernel classes of one PCG iteration, for fehom_kernel_times. */
@@ -232,6 +235,11 @@ fehom_status fehom_eig_bounds(fehom_ctx* ctx, double* lo_values, int64_t* lo_cou
  * bit 1 = register-split last-axis pass (nz = 128). */
 fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int* tc_y, int* tc_last, double* ms,
                             int* xy_fused);
+
+/* Stencil plan of the PCG stiffness apply of one precision (FEHOM_HEX8_3D): *rows = the node rows per
+   tile in use (8 or 16); ms[2] = the tuner's timings of one apply with 8 and 16 rows (0 if not timed,
+   -1 if the candidate failed to launch).  Either output may be NULL. */
+fehom_status fehom_stencil_plan(const fehom_ctx* ctx, int precision, int* rows, double* ms);
 
 /* Replaces the reference material (Sec. 4.1, Eq. Kref; m x m, host, symmetric positive definite) of
  * the context, e.g. when the tangent of a nonlinear problem changes (the reassembly of Sec. 5 before

@@ -74,6 +74,12 @@ struct fehom_ctx {
     int tuned_loads = 0;
     double ms[3] = {0, 0, 0};
   } plan[2];                   // [0] FP64 kernels, [1] FP32 kernels
+  struct StencilPlan {
+    int rows = 0;         // hex8 PCG apply: node rows per tile (0 = the precision's default)
+    int tuned_loads = 0;
+    double ms[2] = {0, 0};  // timed candidates: 8 and 16 rows
+  } stencil[2];               // [0] FP64 kernels, [1] FP32 kernels
+  PcgState* tune_st = nullptr;  // running states for the stencil tuner's PCG-apply launches
   double kms[2][FEHOM_K_COUNT] = {{0}};
   int hist_count[kMaxLoads] = {0};  // PCG coefficients recorded per load by the last PCG run
   long long kcnt[2][FEHOM_K_COUNT] = {{0}};
@@ -315,6 +321,7 @@ StencilArgs stencil_args(fehom_ctx* ctx, bool fp32, int n_loads) {
   a.y_scale = 1.0;
   a.st = nullptr;
   a.red = ctx->red;
+  a.tile_rows = ctx->stencil[fp32 ? 1 : 0].rows;
   return a;
 }
 
@@ -583,11 +590,82 @@ fehom_status autotune_fft(fehom_ctx* ctx, int n_loads) {
   return FEHOM_OK;
 }
 
+// Stencil tuner: times the hex8 PCG stiffness apply with 8- and 16-row tiles (both precisions) on the
+// solve's buffers, for the batch size of the solve, and keeps the faster; option stencil_rows (8 or 16)
+// fixes the choice.  The launches use running scratch states, not the solve's.
+template <typename T>
+fehom_status autotune_stencil(fehom_ctx* ctx, int n_loads) {
+  const int prec = sizeof(T) == 4 ? 1 : 0;
+  auto& sp = ctx->stencil[prec];
+  if (ctx->d.elem != HEX8_3D) return FEHOM_OK;
+  if (ctx->opt.stencil_rows == 8 || ctx->opt.stencil_rows == 16) {
+    if (sp.rows != ctx->opt.stencil_rows) ctx->graph_key[0] = 0;
+    sp.rows = ctx->opt.stencil_rows;
+    sp.tuned_loads = n_loads;
+    return FEHOM_OK;
+  }
+  if (!ctx->opt.autotune || sp.tuned_loads == n_loads) return FEHOM_OK;
+  cudaStream_t s = ctx->stream;
+  if (!ctx->tune_st) CK(cudaMalloc(&ctx->tune_st, sizeof(PcgState) * kMaxLoads));
+  std::vector<PcgState> hs(n_loads);
+  for (auto& st : hs) {
+    std::memset(&st, 0, sizeof(st));
+    st.state = ST_RUN;
+    st.rz = 1.0;
+  }
+  T* pin = prec ? (T*)ctx->p32 : (T*)ctx->p64;
+  T* pout = prec ? (T*)ctx->ap32 : (T*)ctx->ap64;
+  // every component field of every load takes two values (a step halfway through its planes), so
+  // <p, K p> > 0 and the running states stay running (a zero or constant p would end them by
+  // breakdown and the timed launches would be empty)
+  const size_t row = sizeof(T) * (size_t)ctx->d.N, half = sizeof(T) * (size_t)(ctx->d.N / 2);
+  const size_t rows = (size_t)n_loads * ctx->d.c;
+  CK(cudaMemset2DAsync(pin, row, 0x3F, half, rows, s));
+  CK(cudaMemset2DAsync(reinterpret_cast<char*>(pin) + half, row, 0x40, row - half, rows, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e30;
+  int rows_best = 0;
+  for (int ci = 0; ci < 2; ++ci) {
+    const int rows = ci == 0 ? 8 : 16;
+    StencilArgs a = stencil_args(ctx, prec == 1, n_loads);
+    a.x = pin;
+    a.y = pout;
+    a.st = ctx->tune_st;
+    a.red.hist = nullptr;
+    a.tile_rows = rows;
+    CK(cudaMemcpyAsync(ctx->tune_st, hs.data(), sizeof(PcgState) * n_loads, cudaMemcpyHostToDevice, s));
+    double ms = -1.0;
+    if (launch_stiffness<T>(a, s) == cudaSuccess) {
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3; ++r) launch_stiffness<T>(a, s);
+      cudaEventRecord(e1, s);
+      float t = 0.f;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = t / 3.0;
+    }
+    cudaGetLastError();
+    count_launch(ctx, 4);
+    sp.ms[ci] = ms;
+    if (ms > 0 && ms < best) {
+      best = ms;
+      rows_best = rows;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rows_best == 0) FAIL(FEHOM_E_CUDA, "stencil tuner: no candidate ran");
+  sp.rows = rows_best;
+  sp.tuned_loads = n_loads;
+  ctx->graph_key[0] = 0;  // captured iterations used the previous tile
+  return FEHOM_OK;
+}
+
 template <typename T>
 fehom_status run_iterations(fehom_ctx* ctx, int n_loads, T* x, T* r, T* p, T* ap, int max_iter,
                             std::vector<PcgState>& hs) {
   cudaStream_t s = ctx->stream;
-  const long long key[8] = {ctx->opt.profile ? 2 : 1, (long long)n_loads, (long long)(size_t)x, (long long)(size_t)r, (long long)(size_t)p,
+  const long long key[8] = {(ctx->opt.profile ? 2 : 1) + 4 * ctx->stencil[sizeof(T) == 4 ? 1 : 0].rows, (long long)n_loads, (long long)(size_t)x, (long long)(size_t)r, (long long)(size_t)p,
                             (long long)(size_t)ap, (long long)sizeof(T), (long long)(size_t)ctx->st};
   const bool prof = ctx->opt.profile != 0;
   if (prof) TRY(make_events(ctx));
@@ -842,6 +920,7 @@ void fehom_default_options(fehom_options* opt) {
   opt->x0_scaling = 1;
   opt->fft_xy = -1;
   opt->residual_df = 1;
+  opt->stencil_rows = 0;
 }
 
 const char* fehom_last_error(const fehom_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
@@ -961,6 +1040,15 @@ fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int
   if (tc_last) *tc_last = pl.tc_last;
   if (ms)
     for (int i = 0; i < 3; ++i) ms[i] = pl.ms[i];
+  return FEHOM_OK;
+}
+
+fehom_status fehom_stencil_plan(const fehom_ctx* ctx, int precision, int* rows, double* ms) {
+  if (!ctx) return FEHOM_E_INVALID;
+  const auto& sp = ctx->stencil[precision == FEHOM_MIXED ? 1 : 0];
+  if (rows) *rows = sp.rows != 0 ? sp.rows : (precision == FEHOM_MIXED ? 8 : 16);
+  if (ms)
+    for (int i = 0; i < 2; ++i) ms[i] = sp.ms[i];
   return FEHOM_OK;
 }
 
@@ -1198,7 +1286,7 @@ void fehom_destroy(fehom_ctx* ctx) {
       for (int k = 0; k < FEHOM_K_COUNT; ++k)
         for (int j = 0; j < 2; ++j) cudaEventDestroy(ctx->ev[i][k][j]);
   dfree(ctx->ids); dfree(ctx->mats64); dfree(ctx->mats32); dfree(ctx->iso64); dfree(ctx->iso32); dfree(ctx->isodf);
-  dfree(ctx->rmats64); dfree(ctx->riso64);
+  dfree(ctx->rmats64); dfree(ctx->riso64); dfree(ctx->tune_st);
   for (int i = 0; i < 3; ++i) { dfree(ctx->tw64[i]); dfree(ctx->tw32[i]); }
   dfree(ctx->sym64); dfree(ctx->sym32);
   dfree(ctx->x64); dfree(ctx->r64); dfree(ctx->p64); dfree(ctx->ap64); dfree(ctx->b64); dfree(ctx->spec64);
@@ -1810,6 +1898,8 @@ struct SolveRun {
     if (mixed) TRY(grow32(ctx, n_loads));
     if (mixed) TRY(autotune_fft<float>(ctx, n_loads));
     else TRY(autotune_fft<double>(ctx, n_loads));
+    if (mixed) TRY(autotune_stencil<float>(ctx, n_loads));
+    else TRY(autotune_stencil<double>(ctx, n_loads));
     TRY(upload_tau(ctx, n_loads, loads));
     TRY(residual_stats(ctx, n_loads, nullptr, ctx->b64, &bn2, nullptr, &tsum));  // b = -D^T W C e
     df = mixed && ctx->opt.residual_df != 0 && residual_df_supported(ctx);

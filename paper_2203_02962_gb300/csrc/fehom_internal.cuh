@@ -108,6 +108,7 @@ struct StencilArgs {
   int n_loads;
   long long load_stride;  // elements between loads in x / y
   double y_scale;         // y = y_scale * D^T W C (D x + e)
+  int tile_rows;          // hex8 PCG apply: node rows per tile, 8 or 16 (0 = the precision's default)
   // fused PCG reduction <x, y> -> pAp, alpha = rz / pAp (nullptr = off)
   PcgState* st;
   RedScratch red;

@@ -55,19 +55,22 @@ __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.w
 constexpr int RP = BX + 2;  // row pitch of a staged node plane (nodes i0 - 1 .. i0 + BX)
 
 // hex8 tiles: BX x BY output nodes per CTA, (BX + 1) x (BY + 1) elements per layer, one element per
-// thread.  FP64 kernels take BY = 16 at one CTA per SM: the FP64 pipe is their bound, and the taller
-// tile spends fewer lanes on halo elements (576 threads for 512 nodes instead of 320 for 256).  FP32
-// kernels take BY = 8 at three CTAs per SM, which keeps the issue slots busy across the per-layer
-// barriers.
-template <typename T>
+// thread; BY = 8 (297 elements, 320 threads) or 16 (561 elements, 576 threads: fewer lanes on halo
+// elements, one CTA per SM).  Defaults: FP64 kernels BY = 16 (the FP64 pipe is their bound), FP32
+// kernels BY = 8 at three CTAs per SM (more warps to keep the issue slots busy across the per-layer
+// barriers).  The PCG apply of either precision takes either height; the stencil tuner of the context
+// (api.cu) times both on the solve's buffers and keeps the faster.
+template <typename T, int BYT>
 struct Hex8Tile {
-  static constexpr int BY = sizeof(T) == 8 ? 16 : 8;
+  static constexpr int BY = BYT;
   static constexpr int EY = BY + 1;
-  static constexpr int NE = EX * EY;                 // elements per layer per CTA (561 / 297)
-  static constexpr int NT = ((NE + 31) / 32) * 32;   // threads (576 / 320)
+  static constexpr int NE = EX * EY;                 // elements per layer per CTA (297 / 561)
+  static constexpr int NT = ((NE + 31) / 32) * 32;   // threads (320 / 576)
   static constexpr int RPLANE = RP * (BY + 2);       // nodes of a staged plane per component
-  static constexpr int PER_SM = sizeof(T) == 8 ? 1 : 3;  // resident CTAs per SM (launch bounds)
+  static constexpr int PER_SM = BY == 16 ? 1 : (sizeof(T) == 8 ? 2 : 3);  // resident CTAs per SM (launch bounds)
 };
+template <typename T>
+constexpr int hex8_default_rows() { return sizeof(T) == 8 ? 16 : 8; }
 
 // Block-wide FP64 sum; every thread gets the result. `sh` holds >= 32 doubles.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -321,19 +324,19 @@ __device__ void pcg_alpha_update(PcgState& s, double total, double* hist) {
 template <typename T, int C, bool HAS_X>
 __host__ __device__ constexpr bool hex8_raw() { return HAS_X && sizeof(T) == 4; }
 constexpr int kRing = 5;  // RAW: staged node planes k .. k + 4
-template <typename T, int C, bool HAS_X>
+template <typename T, int C, bool HAS_X, int BYT>
 __host__ __device__ constexpr size_t hex8_smem_elems() {
-  using TL = Hex8Tile<T>;
+  using TL = Hex8Tile<T, BYT>;
   return hex8_raw<T, C, HAS_X>() ? (size_t)kRing * C * TL::RPLANE + 2 * 4 * C * TL::NE
                                  : (size_t)2 * 4 * C * TL::NE + 2 * 4 * C * TL::NE;
 }
 
-template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED>
-__global__ void __launch_bounds__(Hex8Tile<T>::NT, Hex8Tile<T>::PER_SM)
+template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED, int BYT>
+__global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM)
     hex8_apply_kernel(StencilArgs a, int kz_per_cta) {
   constexpr bool RAW = hex8_raw<T, C, HAS_X>();
-  constexpr int BY = Hex8Tile<T>::BY, NE = Hex8Tile<T>::NE, NT = Hex8Tile<T>::NT;
-  constexpr int RPLANE = Hex8Tile<T>::RPLANE;
+  constexpr int BY = BYT, NE = Hex8Tile<T, BYT>::NE, NT = Hex8Tile<T, BYT>::NT;
+  constexpr int RPLANE = Hex8Tile<T, BYT>::RPLANE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* FB = reinterpret_cast<T*>(smem_raw);  // [2 planes][4][C][NE] face butterflies (not RAW)
   T* RW = reinterpret_cast<T*>(smem_raw);  // [kRing slots][C][BY + 2][RP] staged node planes (RAW)
@@ -895,9 +898,9 @@ cudaError_t set_smem(K kern, size_t bytes) {
 // hex8 grid: x-y tiles times z slabs times loads.  Each slab recomputes one element layer below it,
 // and the CTAs run in waves over the 152 SMs, a CTA's layer time growing with the CTAs sharing its
 // SM; the slab depth kz (at least 4 planes) minimises waves x (kz + 1), waves = ceil(CTAs / 152).
-template <typename T>
+template <int BYT>
 void hex8_grid(const Dims& d, int n_loads, int* tiles, int* slabs, int* kz) {
-  *tiles = ((d.nx + BX - 1) / BX) * ((d.ny + Hex8Tile<T>::BY - 1) / Hex8Tile<T>::BY);
+  *tiles = ((d.nx + BX - 1) / BX) * ((d.ny + BYT - 1) / BYT);
   const long long cols = (long long)*tiles * max(n_loads, 1);
   long long best = -1;
   int bkz = d.nz;
@@ -914,19 +917,19 @@ void hex8_grid(const Dims& d, int n_loads, int* tiles, int* slabs, int* kz) {
   *slabs = (d.nz + bkz - 1) / bkz;
 }
 
-template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED>
+template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED, int BYT = hex8_default_rows<T>()>
 cudaError_t launch_hex8_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
   const Dims& d = a.d;
   int tiles, slabs, kz;
-  hex8_grid<T>(d, a.n_loads, &tiles, &slabs, &kz);
+  hex8_grid<BYT>(d, a.n_loads, &tiles, &slabs, &kz);
   if (ctas) *ctas = tiles * slabs;
   if (RED == RED_PCG && tiles * slabs > a.red.max_blocks) return cudaErrorInvalidConfiguration;
-  const size_t smem = sizeof(T) * hex8_smem_elems<T, C, HAS_X>();
-  auto kern = hex8_apply_kernel<T, C, ISO, HAS_X, HAS_E, RED>;
+  const size_t smem = sizeof(T) * hex8_smem_elems<T, C, HAS_X, BYT>();
+  auto kern = hex8_apply_kernel<T, C, ISO, HAS_X, HAS_E, RED, BYT>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(tiles, slabs, a.n_loads);
-  kern<<<grid, Hex8Tile<T>::NT, smem, s>>>(a, kz);
+  kern<<<grid, Hex8Tile<T, BYT>::NT, smem, s>>>(a, kz);
   return cudaGetLastError();
 }
 
@@ -966,6 +969,8 @@ cudaError_t dispatch_hex8(const StencilArgs& a, int* ctas, cudaStream_t s) {
   const bool hx = a.x != nullptr, he = a.tau != nullptr;
   if (a.st != nullptr) {
     if (!hx || he) return cudaErrorInvalidValue;
+    if (a.tile_rows != 0 && a.tile_rows != hex8_default_rows<T>())
+      return launch_hex8_t<T, C, ISO, true, false, RED_PCG, 24 - hex8_default_rows<T>()>(a, ctas, s);
     return launch_hex8_t<T, C, ISO, true, false, RED_PCG>(a, ctas, s);
   }
   if (a.stats != nullptr && a.y == nullptr) {
@@ -1070,9 +1075,9 @@ __device__ __forceinline__ DF operator*(DF a, DF c) {  // the lo x lo term (2^-4
 }
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (double)a.l; }
 
-__global__ void __launch_bounds__(Hex8Tile<float>::NT, 1)
+__global__ void __launch_bounds__(Hex8Tile<float, 8>::NT, 1)
     hex8_residual_df_kernel(StencilArgs a, const double* __restrict__ r_in, int kz_per_cta) {
-  constexpr int C = 3, BY = Hex8Tile<float>::BY, NE = Hex8Tile<float>::NE;
+  constexpr int C = 3, BY = 8, NE = Hex8Tile<float, 8>::NE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DF* FB = reinterpret_cast<DF*>(smem_raw);  // [2 planes][4][C][NE] face butterflies (thread-private)
   DF* FC0 = FB + 2 * 4 * C * NE;             // [2 layers][4 corners][C][NE] face contributions
@@ -1258,7 +1263,7 @@ cudaError_t launch_stiffness(const StencilArgs& a, cudaStream_t s, int* ctas) {
 int stiffness_ctas(const Dims& d, int n_loads) {
   if (d.elem == HEX8_3D) {
     int tiles, slabs, kz;
-    hex8_grid<double>(d, n_loads, &tiles, &slabs, &kz);
+    hex8_grid<hex8_default_rows<double>()>(d, n_loads, &tiles, &slabs, &kz);
     return tiles * slabs;
   }
   return ((d.nx + BX - 1) / BX) * ((d.ny + BY2 - 1) / BY2);
@@ -1268,18 +1273,18 @@ cudaError_t launch_residual_df(const StencilArgs& a, const double* r_in, cudaStr
   const Dims& d = a.d;
   if (d.elem != HEX8_3D || d.c != 3 || a.iso == nullptr || a.stats == nullptr) return cudaErrorInvalidValue;
   int tiles, slabs, kz;
-  hex8_grid<float>(d, a.n_loads, &tiles, &slabs, &kz);
+  hex8_grid<8>(d, a.n_loads, &tiles, &slabs, &kz);
   if (ctas) *ctas = tiles * slabs;
-  const size_t smem = sizeof(DF) * (size_t)(2 + 2) * 4 * 3 * Hex8Tile<float>::NE;
+  const size_t smem = sizeof(DF) * (size_t)(2 + 2) * 4 * 3 * Hex8Tile<float, 8>::NE;
   cudaError_t e = set_smem(hex8_residual_df_kernel, smem);
   if (e != cudaSuccess) return e;
-  hex8_residual_df_kernel<<<dim3(tiles, slabs, a.n_loads), Hex8Tile<float>::NT, smem, s>>>(a, r_in, kz);
+  hex8_residual_df_kernel<<<dim3(tiles, slabs, a.n_loads), Hex8Tile<float, 8>::NT, smem, s>>>(a, r_in, kz);
   return cudaGetLastError();
 }
 
 int residual_df_ctas(const Dims& d, int n_loads) {
   int tiles, slabs, kz;
-  hex8_grid<float>(d, n_loads, &tiles, &slabs, &kz);
+  hex8_grid<8>(d, n_loads, &tiles, &slabs, &kz);
   return tiles * slabs;
 }
 

@@ -31,6 +31,7 @@ EXPORTS = ("fehom_default_options", "fehom_setup", "fehom_precond_build", "fehom
            "fehom_fft_plan", "fehom_mean_flux_noalloc", "fehom_pcg_coefficients", "fehom_eig_bounds",
            "fehom_batch_create", "fehom_solve_batch", "fehom_batch_destroy", "fehom_batch_last_error",
            "fehom_effective_energy", "fehom_set_reference", "fehom_newton_solve", "fehom_residual_update",
+           "fehom_stencil_plan",
            # include/fehom_unet.h
            "fehom_unet_create", "fehom_unet_destroy", "fehom_unet_last_error", "fehom_unet_param_count",
            "fehom_unet_set_params", "fehom_unet_get_params", "fehom_unet_predict", "fehom_unet_loss_grad",
@@ -42,7 +43,8 @@ KERNEL_CLASSES = ("stiffness", "fft_x_fwd", "fft_y_fwd", "fft_last", "fft_y_inv"
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_iter", C.c_int), ("inner_tol", C.c_double),
                 ("stream", C.c_void_p), ("use_graph", C.c_int), ("profile", C.c_int),
-                ("autotune", C.c_int), ("x0_scaling", C.c_int), ("fft_xy", C.c_int), ("residual_df", C.c_int)]
+                ("autotune", C.c_int), ("x0_scaling", C.c_int), ("fft_xy", C.c_int), ("residual_df", C.c_int),
+                ("stencil_rows", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -96,6 +98,8 @@ def load_library(path: str = LIB_PATH):
     lib.fehom_rhs.restype = i
     lib.fehom_residual_update.argtypes = [vp, vp, vp, vp, dp]
     lib.fehom_residual_update.restype = i
+    lib.fehom_stencil_plan.argtypes = [vp, i, C.POINTER(C.c_int), dp]
+    lib.fehom_stencil_plan.restype = i
     lib.fehom_apply_precond.argtypes = [vp, vp, vp, i]
     lib.fehom_apply_precond.restype = i
     lib.fehom_get_symbol_inverse.argtypes = [vp, dp]
@@ -174,7 +178,7 @@ class Solver:
 
     def __init__(self, elem, physics, n, ids, moduli, ref_material=None, precision="fp64", max_iter=10000,
                  inner_tol=1e-3, cell=None, use_graph=True, stream=None, profile=False, autotune=True,
-                 x0_scaling=True, fft_xy=-1, residual_df=True):
+                 x0_scaling=True, fft_xy=-1, residual_df=True, stencil_rows=0):
         torch = _torch()
         self.lib = load_library()
         self.elem, self.physics = elem, physics
@@ -192,6 +196,7 @@ class Solver:
         opt.x0_scaling = 1 if x0_scaling else 0
         opt.fft_xy = int(fft_xy)
         opt.residual_df = 1 if residual_df else 0
+        opt.stencil_rows = int(stencil_rows)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opt.stream = C.c_void_p(self.stream.cuda_stream)
         self._opt = opt
@@ -279,6 +284,13 @@ class Solver:
         b = torch.empty((self.c * self.N,), dtype=torch.float64, device="cuda")
         self._check(self.lib.fehom_rhs(self.ctx, _dptr(e), C.c_void_p(b.data_ptr())))
         return b
+
+    def stencil_plan(self, precision="fp64"):
+        """(rows, [ms with 8 rows, ms with 16 rows]) of the hex8 PCG stiffness apply."""
+        rows = C.c_int(0)
+        ms = np.zeros(2)
+        self._check(self.lib.fehom_stencil_plan(self.ctx, PRECISION[precision], C.byref(rows), _dptr(ms)))
+        return rows.value, ms.tolist()
 
     def residual_update(self, d, r_in, r_out=None):
         """r_out = r_in - K d with K d in double-float arithmetic (d: FP32 field, r_in / r_out: FP64 fields,

@@ -707,3 +707,32 @@ def test_double_float_residual_rejects_unsupported_contexts():
     assert st == 2  # FEHOM_E_UNSUPPORTED_SIZE
     assert float(r.min()) == 1.0 and float(r.max()) == 1.0
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_stencil_tile_heights_agree_with_oracle(precision):
+    """The PCG stiffness apply with 8- and 16-row tiles (forced, and as picked by the stencil tuner) gives
+    the oracle's C_eff on a grid whose y extent is ragged for the 16-row tiles (24 = 16 + 8) and whose x
+    extent is ragged for the 32-node tile width (48 = 32 + 16)."""
+    shape = (8, 24, 48)
+    rng = np.random.default_rng(31)
+    ids = rng.integers(0, 2, size=shape).astype(np.uint8)
+    mod = np.stack([I.isotropic_elastic_mandel(1.0, 0.3), I.isotropic_elastic_mandel(20.0, 0.2)])
+    cell = (48 / 16, 24 / 16, 8 / 16)  # cubic voxels: the isotropic fast path
+    g = fem.Grid(shape, "hex8_3d", "elastic")
+    g.h = np.array(cell) / np.array(g.n_xyz, float)
+    g.vp = float(np.prod(g.h))
+    # the oracle's averages are over the unit cell (|Y| = 1): divide by this cell's volume
+    ref = solvers.homogenise(g, ids.ravel(), mod, np.eye(6), method="cg", tol=1e-13)["C_eff"] / (g.vp * g.N)
+    tol, bound = (1e-10, 1e-9) if precision == "fp64" else (1e-8, 1e-7)
+    for rows in (8, 16, 0):
+        s = _solver("hex8_3d", "elastic", shape, ids, mod, precision=precision, cell=cell, stencil_rows=rows)
+        s.precond_build()
+        out = s.solve(np.eye(6), tol=tol)
+        assert all(i["converged"] for i in out["info"])
+        assert _rel(s.effective_energy(), ref) < bound
+        used, ms = s.stencil_plan(precision)
+        assert used == (rows if rows else used) and used in (8, 16)
+        if rows == 0:
+            assert ms[0] > 0 and ms[1] > 0 and used == (8 if ms[0] <= ms[1] else 16)
+        s.close()
