@@ -516,10 +516,11 @@ def run_ncu_case(precision, n_loads=6):
     import torch
     from paper_2203_02962_gb300 import fehom
     w = workload()
-    # mixed: the FFT plan the launch-plan tuner picks in the timed runs (register-split passes); under
-    # ncu the tuner's own timings are serialised replays and would pick differently
+    # the FFT plan and the stencil tile height the tuners pick in the timed runs (register-split FFT
+    # passes; 8-row FP32 and 16-row FP64 tiles); under ncu the tuners' own timings are serialised
+    # replays and would pick differently
     s = fehom.Solver("hex8_3d", "elastic", w["n"], w["ids"], w["moduli"], precision=precision,
-                     fft_xy=1 if precision == "mixed" else -1)
+                     fft_xy=1 if precision == "mixed" else -1, stencil_rows=8 if precision == "mixed" else 16)
     s.precond_build()
     out = s.solve(w["loads"][:n_loads], tol=w["tol"], fields=None)
     torch.cuda.synchronize()
