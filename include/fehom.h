@@ -315,6 +315,12 @@ fehom_status fehom_rhs(fehom_ctx* ctx, const double* e, double* b);
 fehom_status fehom_residual_update(fehom_ctx* ctx, const float* d, const double* r_in, double* r_out,
                                    double* sums_out);
 
+/* The right-hand side of fehom_rhs (b = -D^T W C e, Sec. 3.1 Eq. lin_system) in double-float arithmetic,
+   as the mixed solve forms it when residual_df is on: the per-phase prestress w S P^T C e is split into
+   float pairs on the host and the element's transposed operations run on pairs of floats; b (device,
+   c x N doubles) = hi + lo.  Same support and errors as fehom_residual_update. */
+fehom_status fehom_rhs_df(fehom_ctx* ctx, const double* e, double* b);
+
 /* z = K_ref^+ r = F^-1 K_hat^+ F r (Eq. M_inverse); r, z: c x N.  Needs fehom_precond_build. */
 fehom_status fehom_apply_precond(fehom_ctx* ctx, const void* r, void* z, int precision);
 

@@ -56,6 +56,7 @@ struct fehom_ctx {
   PcgState* st = nullptr;
   RedScratch red{};
   double* tau = nullptr;       // [load][phase][D]
+  float* taudf = nullptr;      // [load][phase][D][2]: tau as (hi, lo) float pairs (double-float right-hand side)
   double* partial = nullptr;   // general reduction scratch
   size_t partial_cap = 0;
   // captured iteration graphs
@@ -754,6 +755,14 @@ fehom_status upload_tau(fehom_ctx* ctx, int n_loads, const double* loads) {
   dfree(ctx->tau);
   CK(cudaMalloc(&ctx->tau, tau.size() * sizeof(double)));
   CK(cudaMemcpyAsync(ctx->tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<float> tdf(2 * tau.size());
+  for (size_t i = 0; i < tau.size(); ++i) {
+    tdf[2 * i] = (float)tau[i];
+    tdf[2 * i + 1] = (float)(tau[i] - (double)tdf[2 * i]);
+  }
+  dfree(ctx->taudf);
+  CK(cudaMalloc(&ctx->taudf, tdf.size() * sizeof(float)));
+  CK(cudaMemcpyAsync(ctx->taudf, tdf.data(), tdf.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
   return FEHOM_OK;
 }
 
@@ -836,10 +845,26 @@ fehom_status residual_update_df(fehom_ctx* ctx, int n_loads, const float* d, con
   TRY(ensure_partial(ctx, (size_t)n_loads * ctas * (1 + ctx->D)));
   a.stats = ctx->partial;
   int got = 0;
-  CK(launch_residual_df(a, r_in, ctx->stream, &got));
+  CK(launch_residual_df(a, r_in, nullptr, ctx->stream, &got));
   count_launch(ctx);
   if (got != ctas) FAIL(FEHOM_E_CUDA, "double-float residual: CTA count mismatch");
   return reduce_stats(ctx, n_loads, ctas, y2, dT);
+}
+
+// Right-hand side b = -D^T W C e of every load in double-float arithmetic (after upload_tau), with
+// ||b||^2 and the prestress sums (the dual sums at zero fluctuation).
+fehom_status rhs_df(fehom_ctx* ctx, int n_loads, double* b, std::vector<double>* y2, std::vector<double>* T) {
+  StencilArgs a = stencil_args(ctx, true, n_loads);
+  a.x = nullptr;
+  a.y = b;
+  const int ctas = residual_df_ctas(ctx->d, n_loads);
+  TRY(ensure_partial(ctx, (size_t)n_loads * ctas * (1 + ctx->D)));
+  a.stats = ctx->partial;
+  int got = 0;
+  CK(launch_residual_df(a, nullptr, ctx->taudf, ctx->stream, &got));
+  count_launch(ctx);
+  if (got != ctas) FAIL(FEHOM_E_CUDA, "double-float right-hand side: CTA count mismatch");
+  return reduce_stats(ctx, n_loads, ctas, y2, T);
 }
 
 // --------------------------------------------------------------------------------------------------
@@ -1292,7 +1317,7 @@ void fehom_destroy(fehom_ctx* ctx) {
   dfree(ctx->x64); dfree(ctx->r64); dfree(ctx->p64); dfree(ctx->ap64); dfree(ctx->b64); dfree(ctx->spec64);
   dfree(ctx->x32); dfree(ctx->r32); dfree(ctx->p32); dfree(ctx->ap32); dfree(ctx->spec32);
   dfree(ctx->st); dfree(ctx->red.partial); dfree(ctx->red.count); dfree(ctx->red.hist);
-  dfree(ctx->tau); dfree(ctx->partial);
+  dfree(ctx->tau); dfree(ctx->taudf); dfree(ctx->partial);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   cudaSetDevice(prev);
   delete ctx;
@@ -1639,6 +1664,17 @@ fehom_status fehom_residual_update(fehom_ctx* ctx, const float* d, const double*
   return FEHOM_OK;
 }
 
+fehom_status fehom_rhs_df(fehom_ctx* ctx, const double* e, double* b) {
+  if (!ctx || !e || !b) return FEHOM_E_INVALID;
+  if (!residual_df_supported(ctx))
+    FAIL(FEHOM_E_UNSUPPORTED_SIZE, "fehom_rhs_df: hex8 elasticity with isotropic phases on cubic voxels only");
+  for (int i = 0; i < ctx->m; ++i)
+    if (!std::isfinite(e[i])) FAIL(FEHOM_E_INVALID, "non-finite load");
+  TRY(upload_tau(ctx, 1, e));
+  std::vector<double> y2, T;
+  return rhs_df(ctx, 1, b, &y2, &T);
+}
+
 fehom_status fehom_apply_precond(fehom_ctx* ctx, const void* r, void* z, int precision) {
   if (!ctx || !r || !z) return FEHOM_E_INVALID;
   if (!ctx->built) FAIL(FEHOM_E_STATE, "fehom_apply_precond before fehom_precond_build");
@@ -1901,8 +1937,9 @@ struct SolveRun {
     if (mixed) TRY(autotune_stencil<float>(ctx, n_loads));
     else TRY(autotune_stencil<double>(ctx, n_loads));
     TRY(upload_tau(ctx, n_loads, loads));
-    TRY(residual_stats(ctx, n_loads, nullptr, ctx->b64, &bn2, nullptr, &tsum));  // b = -D^T W C e
     df = mixed && ctx->opt.residual_df != 0 && residual_df_supported(ctx);
+    if (df) TRY(rhs_df(ctx, n_loads, ctx->b64, &bn2, &tsum));  // b = -D^T W C e, double-float
+    else TRY(residual_stats(ctx, n_loads, nullptr, ctx->b64, &bn2, nullptr, &tsum));  // FP64
     outer_it.assign(n_loads, 0);
     inner_it.assign(n_loads, 0);
     relM.assign(n_loads, 1.0);

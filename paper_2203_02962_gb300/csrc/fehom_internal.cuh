@@ -128,7 +128,10 @@ int stiffness_ctas(const Dims& d, int n_loads);  // CTAs per load of an FP64 lau
 // a.y = r_out (double, may alias r_in), a.iso = the double-float isotropic table ([phase][16] floats:
 // lambda', mu', 2 mu', lambda'/3, mu'/3, (lambda' + 4 mu')/9 as hi, lo pairs), a.stats = partial sums
 // [load][cta][1 + 9] (sum r_out^2, sums of the monomial-1 duals of d); hex8 elasticity only.
-cudaError_t launch_residual_df(const StencilArgs& a, const double* r_in, cudaStream_t s, int* ctas);
+// With taudf (per-load, per-phase prestress as float pairs, [load][phase][9][2]) instead: r_out = the
+// right-hand side b = -D^T W C e (a.x, r_in unused), with sum b^2 and the prestress sums.
+cudaError_t launch_residual_df(const StencilArgs& a, const double* r_in, const float* taudf, cudaStream_t s,
+                               int* ctas);
 int residual_df_ctas(const Dims& d, int n_loads);
 
 cudaError_t launch_phase_histogram(const uint8_t* ids, long long N, unsigned long long* hist,

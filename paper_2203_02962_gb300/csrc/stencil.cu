@@ -1044,6 +1044,9 @@ cudaError_t dispatch_pixel4(const StencilArgs& a, int* ctas, cudaStream_t s) {
 // (r_out may alias r_in); r_out = r_in - (hi + lo) is formed in FP64.  Fused statistics per load and
 // CTA: sum r_out^2 and the sums of the monomial-1 duals of d over the CTA's elements (the change of
 // |Y| S P^T <sigma>), [load][cta][1 + 9] doubles.  Tiles as the FP32 kernel (32 x 8), one CTA per SM.
+// RHS = true: the right-hand side b = -D^T W C e instead (no field; the monomial-1 duals are the
+// per-phase prestress tau of the load, given as float pairs [load][phase][9][2]; r_in is not read):
+// r_out = b, with sum b^2 and the dual sums (|Y| S P^T <sigma> at zero fluctuation).
 // ------------------------------------------------------------------------------------------------
 struct __align__(8) DF {
   float h, l;
@@ -1075,8 +1078,10 @@ __device__ __forceinline__ DF operator*(DF a, DF c) {  // the lo x lo term (2^-4
 }
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (double)a.l; }
 
+template <bool RHS>
 __global__ void __launch_bounds__(Hex8Tile<float, 8>::NT, 1)
-    hex8_residual_df_kernel(StencilArgs a, const double* __restrict__ r_in, int kz_per_cta) {
+    hex8_residual_df_kernel(StencilArgs a, const double* __restrict__ r_in, const float* __restrict__ taudf,
+                            int kz_per_cta) {
   constexpr int C = 3, BY = 8, NE = Hex8Tile<float, 8>::NE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DF* FB = reinterpret_cast<DF*>(smem_raw);  // [2 planes][4][C][NE] face butterflies (thread-private)
@@ -1091,8 +1096,9 @@ __global__ void __launch_bounds__(Hex8Tile<float, 8>::NT, 1)
   const int k0 = blockIdx.y * kz_per_cta;
   const int k1 = min(k0 + kz_per_cta, d.nz);
   const int tid = threadIdx.x;
-  const float* dx = reinterpret_cast<const float*>(a.x) + (long long)load * a.load_stride;
-  const double* rin = r_in + (long long)load * a.load_stride;
+  const float* dx = RHS ? nullptr : reinterpret_cast<const float*>(a.x) + (long long)load * a.load_stride;
+  const double* rin = RHS ? nullptr : r_in + (long long)load * a.load_stride;
+  const float* tload = RHS ? taudf + (long long)load * a.n_phases * 18 : nullptr;
   double* rout = reinterpret_cast<double*>(a.y) + (long long)load * a.load_stride;
   const float* isodf = reinterpret_cast<const float*>(a.iso);  // [phase][16]: 6 constants as (hi, lo)
   const long long plane = (long long)d.nx * d.ny;
@@ -1119,7 +1125,7 @@ __global__ void __launch_bounds__(Hex8Tile<float, 8>::NT, 1)
 
   auto next = [&](int z) { return z + 1 == d.nz ? 0 : z + 1; };
   auto faces = [&](int slot, int kz) {  // in-plane butterflies of plane kz (exact first stage)
-    if (face_thread) {
+    if (!RHS && face_thread) {
       const float* xk = dx + (long long)kz * plane;
 #pragma unroll
       for (int j = 0; j < C; ++j) {
@@ -1140,7 +1146,30 @@ __global__ void __launch_bounds__(Hex8Tile<float, 8>::NT, 1)
   auto layer = [&](int cur, int k, int kzc) {
     faces(cur ^ 1, next(kzc));
     DF* FC = FC0 + cur * 4 * C * NE;
-    if (face_thread) {
+    if (face_thread && RHS) {  // only the prestress: Q1..Q3 = tau of the element's phase, Q4..Q7 = 0
+      const int ph = a.ids ? a.ids[(long long)kzc * plane + off00] : 0;
+      const float* tp = tload + ph * 18;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const DF Q1 = {tp[6 * j + 0], tp[6 * j + 1]}, Q2 = {tp[6 * j + 2], tp[6 * j + 3]},
+                 Q3 = {tp[6 * j + 4], tp[6 * j + 5]};
+        const DF ss = carry[j][0] - Q3, sd = Q2 + carry[j][1], ds = Q1 + carry[j][2], dd = carry[j][3];
+        carry[j][0] = Q3;
+        carry[j][1] = Q2;
+        carry[j][2] = Q1;
+        carry[j][3] = {0.0f, 0.0f};
+        const DF s0 = ss - sd, s1 = ss + sd, d0 = ds - dd, d1 = ds + dd;
+        FC[(0 * C + j) * NE + tid] = s0 - d0;
+        FC[(1 * C + j) * NE + tid] = s0 + d0;
+        FC[(2 * C + j) * NE + tid] = s1 - d1;
+        FC[(3 * C + j) * NE + tid] = s1 + d1;
+        if (owner && k >= k0) {
+          acc_t[j * 3 + 0] = acc_t[j * 3 + 0] + Q1;
+          acc_t[j * 3 + 1] = acc_t[j * 3 + 1] + Q2;
+          acc_t[j * 3 + 2] = acc_t[j * 3 + 2] + Q3;
+        }
+      }
+    } else if (face_thread) {
       DF q1[C], q2[C], q3[C], q4[C], q5[C], q6[C], q7[C];
 #pragma unroll
       for (int j = 0; j < C; ++j) {
@@ -1215,7 +1244,7 @@ __global__ void __launch_bounds__(Hex8Tile<float, 8>::NT, 1)
         const DF v = ((FC[(3 * C + j) * NE + e00] + FC[(2 * C + j) * NE + e00 + 1]) + FC[(1 * C + j) * NE + e00 + EX]) +
                      FC[(0 * C + j) * NE + e00 + EX + 1];
         const long long gidx = (long long)j * d.N + (long long)kzc * plane + node_off;
-        const double rv = rin[gidx] - df_to_double(v);
+        const double rv = (RHS ? 0.0 : rin[gidx]) - df_to_double(v);
         rout[gidx] = rv;
         acc_y = fma(rv, rv, acc_y);
       }
@@ -1225,6 +1254,7 @@ __global__ void __launch_bounds__(Hex8Tile<float, 8>::NT, 1)
   int kz = wrap(k0 - 1, d.nz);
   faces(0, kz);
   int cur = 0;
+  (void)tload;
   for (int k = k0 - 1; k < k1; ++k) {
     layer(cur, k, kz);
     kz = next(kz);
@@ -1269,16 +1299,20 @@ int stiffness_ctas(const Dims& d, int n_loads) {
   return ((d.nx + BX - 1) / BX) * ((d.ny + BY2 - 1) / BY2);
 }
 
-cudaError_t launch_residual_df(const StencilArgs& a, const double* r_in, cudaStream_t s, int* ctas) {
+cudaError_t launch_residual_df(const StencilArgs& a, const double* r_in, const float* taudf, cudaStream_t s,
+                               int* ctas) {
   const Dims& d = a.d;
-  if (d.elem != HEX8_3D || d.c != 3 || a.iso == nullptr || a.stats == nullptr) return cudaErrorInvalidValue;
+  if (d.elem != HEX8_3D || d.c != 3 || a.stats == nullptr) return cudaErrorInvalidValue;
+  const bool rhs = taudf != nullptr;
+  if (rhs ? false : (a.iso == nullptr || r_in == nullptr || a.x == nullptr)) return cudaErrorInvalidValue;
   int tiles, slabs, kz;
   hex8_grid<8>(d, a.n_loads, &tiles, &slabs, &kz);
   if (ctas) *ctas = tiles * slabs;
   const size_t smem = sizeof(DF) * (size_t)(2 + 2) * 4 * 3 * Hex8Tile<float, 8>::NE;
-  cudaError_t e = set_smem(hex8_residual_df_kernel, smem);
+  auto kern = rhs ? hex8_residual_df_kernel<true> : hex8_residual_df_kernel<false>;
+  cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  hex8_residual_df_kernel<<<dim3(tiles, slabs, a.n_loads), Hex8Tile<float, 8>::NT, smem, s>>>(a, r_in, kz);
+  kern<<<dim3(tiles, slabs, a.n_loads), Hex8Tile<float, 8>::NT, smem, s>>>(a, r_in, taudf, kz);
   return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ EXPORTS = ("fehom_default_options", "fehom_setup", "fehom_precond_build", "fehom
            "fehom_fft_plan", "fehom_mean_flux_noalloc", "fehom_pcg_coefficients", "fehom_eig_bounds",
            "fehom_batch_create", "fehom_solve_batch", "fehom_batch_destroy", "fehom_batch_last_error",
            "fehom_effective_energy", "fehom_set_reference", "fehom_newton_solve", "fehom_residual_update",
-           "fehom_stencil_plan",
+           "fehom_stencil_plan", "fehom_rhs_df",
            # include/fehom_unet.h
            "fehom_unet_create", "fehom_unet_destroy", "fehom_unet_last_error", "fehom_unet_param_count",
            "fehom_unet_set_params", "fehom_unet_get_params", "fehom_unet_predict", "fehom_unet_loss_grad",
@@ -100,6 +100,8 @@ def load_library(path: str = LIB_PATH):
     lib.fehom_residual_update.restype = i
     lib.fehom_stencil_plan.argtypes = [vp, i, C.POINTER(C.c_int), dp]
     lib.fehom_stencil_plan.restype = i
+    lib.fehom_rhs_df.argtypes = [vp, dp, vp]
+    lib.fehom_rhs_df.restype = i
     lib.fehom_apply_precond.argtypes = [vp, vp, vp, i]
     lib.fehom_apply_precond.restype = i
     lib.fehom_get_symbol_inverse.argtypes = [vp, dp]
@@ -302,6 +304,14 @@ class Solver:
         self._check(self.lib.fehom_residual_update(self.ctx, C.c_void_p(d.data_ptr()), C.c_void_p(r_in.data_ptr()),
                                                    C.c_void_p(r_out.data_ptr()), _dptr(sums)))
         return r_out, sums[0], sums[1:]
+
+    def rhs_df(self, e):
+        """b = -D^T W C e in double-float arithmetic (the mixed solve's right-hand side)."""
+        torch = _torch()
+        e = np.ascontiguousarray(np.asarray(e, np.float64))
+        b = torch.empty((self.c * self.N,), dtype=torch.float64, device="cuda")
+        self._check(self.lib.fehom_rhs_df(self.ctx, _dptr(e), C.c_void_p(b.data_ptr())))
+        return b
 
     def apply_precond(self, r, precision="fp64"):
         torch = _torch()
