@@ -1797,30 +1797,30 @@ static bool solve_loads(int m, std::vector<double> E, std::vector<double>& B) {
 // Energy form of C_eff (m loads e_l, fields x_l, right-hand sides b_l, true residuals r_l): for any x,
 //   sum_q w_q (e_i + D x_i)^T C (e_j + D x_j) = |Y| e_i^T <C> e_j - x_j . b_i - x_i . r_j,
 // (b = -D^T W C e, r = b - K x), stationary at the solution, so its error is second order in the
-// solve error.  A = E C_eff E^T  ->  C_eff = E^-1 A E^-T.
-static fehom_status energy_c_eff(fehom_ctx* ctx, int m, const double* loads, const double* res) {
+// solve error.  Since x_j . b_i = -sum_q w_q (D x_j)^T C e_i = -|Y| e_i^T (<sigma>_j - <C> e_j), with
+// <sigma>_j the volume average of the same quadrature, the form equals |Y| e_i^T <sigma>_j - x_i . r_j:
+// the stress average plus a correction from the residual, so only the dots x_i . r_j are formed.
+// A = E C_eff E^T  ->  C_eff = E^-1 A E^-T.
+static fehom_status energy_c_eff(fehom_ctx* ctx, int m, const double* loads, const double* res,
+                                 const std::vector<double>& flux) {
   ctx->c_eff_energy.clear();
-  if (!res || m > 6) return FEHOM_OK;
+  if (!res || m > 6 || flux.size() < (size_t)m * ctx->m) return FEHOM_OK;
   cudaStream_t s = ctx->stream;
   const long long cN = (long long)ctx->d.c * ctx->d.N;
-  TRY(ensure_partial(ctx, (size_t)m * 2 * m * 304 + 2 * m * m));
-  double* out = ctx->partial + (size_t)m * 2 * m * 304;
-  CK(launch_pair_dots(ctx->x64, ctx->b64, res, m, cN, ctx->partial, out, s));
+  TRY(ensure_partial(ctx, (size_t)m * m * 304 + m * m));
+  double* out = ctx->partial + (size_t)m * m * 304;
+  CK(launch_pair_dots(ctx->x64, res, m, cN, ctx->partial, out, s));
   count_launch(ctx, 2);
-  std::vector<double> dots(2 * m * m);
+  std::vector<double> dots(m * m);
   CK(cudaMemcpyAsync(dots.data(), out, sizeof(double) * dots.size(), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  std::vector<double> Cm(m * m, 0.0);
-  for (int p = 0; p < ctx->n_phases; ++p)
-    for (int k = 0; k < m * m; ++k) Cm[k] += ctx->frac[p] * ctx->moduli[(size_t)p * m * m + k];
   std::vector<double> A(m * m);
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < m; ++j) {
-      double ece = 0.0;
-      for (int a = 0; a < m; ++a)
-        for (int b = 0; b < m; ++b) ece += loads[i * m + a] * Cm[a * m + b] * loads[j * m + b];
-      // dots[(i m + j) 2 + 0] = x_i . b_j, [.. + 1] = x_i . r_j
-      A[i * m + j] = ece - (dots[(j * m + i) * 2] + dots[(i * m + j) * 2 + 1]) / (ctx->vol * (double)ctx->d.N);
+      double es = 0.0;  // e_i^T <sigma>_j
+      for (int a = 0; a < m; ++a) es += loads[i * m + a] * flux[(size_t)j * m + a];
+      // dots[i m + j] = x_i . r_j
+      A[i * m + j] = es - dots[i * m + j] / (ctx->vol * (double)ctx->d.N);
     }
   for (int i = 0; i < m; ++i)
     for (int j = i + 1; j < m; ++j) A[i * m + j] = A[j * m + i] = 0.5 * (A[i * m + j] + A[j * m + i]);
@@ -1840,7 +1840,7 @@ static fehom_status finish_outputs(fehom_ctx* ctx, int n_loads, const double* lo
   cudaStream_t s = ctx->stream;
   const long long cN = (long long)ctx->d.c * ctx->d.N;
   ctx->c_eff_energy.clear();
-  if (c_eff_out && n_loads == ctx->m) TRY(energy_c_eff(ctx, n_loads, loads, res));
+  if (c_eff_out && n_loads == ctx->m) TRY(energy_c_eff(ctx, n_loads, loads, res, flux));
   TRY(ensure_partial(ctx, (size_t)n_loads * ctx->d.c * 2 * 152));
   CK(sub_mean_fields(ctx, ctx->x64, n_loads, s));
   count_launch(ctx, 2);

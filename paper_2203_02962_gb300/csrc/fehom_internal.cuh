@@ -227,8 +227,8 @@ cudaError_t launch_sub_mean(double* x, int c, long long N, int n_loads, long lon
                             cudaStream_t s);
 // out[(i L + j) 2 + k] = x_i . b_j (k = 0), x_i . r_j (k = 1) for i, j < L <= 6, slices of n doubles;
 // partial: scratch of L * 2 L * 304 doubles; out: 2 L^2 doubles (device).  Fixed summation order.
-cudaError_t launch_pair_dots(const double* x, const double* b, const double* r, int L, long long n, double* partial,
-                             double* out, cudaStream_t s);
+cudaError_t launch_pair_dots(const double* x, const double* r, int L, long long n, double* partial, double* out,
+                             cudaStream_t s);
 // x[l] *= gamma_l = <x[l], b[l]> / <x[l], kx[l]> (0 when <x[l], kx[l]> <= 0), l < n_loads, slices of n doubles;
 // partial: scratch of n_loads * 2 * 304 doubles (two launches, fixed summation order)
 cudaError_t launch_galerkin_scale(double* x, const double* kx, const double* b, int n_loads, long long n,

@@ -93,38 +93,43 @@ __global__ void galerkin_scale_kernel(double* __restrict__ x, long long n, const
   for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) p[i] *= gamma;
 }
 
-// Energy-form effective tensor: for loads i, j < L <= 6, dots x_i . b_j and x_i . r_j over n entries.
-// partial[((i * G + blk) * L + j) * 2 + k]; then out[(i * L + j) * 2 + k] sums the G partials in order.
+// Energy-form effective tensor: for loads i, j < L <= 6, the dots x_i . r_j over n entries, in one
+// pass that reads each x_i and r_j once.  partial[blk * L * L + i * L + j]; then out[i * L + j] sums
+// the G partials in block order.
 constexpr int kPairMax = 6;
-__global__ void pair_dots_kernel(const double* __restrict__ x, const double* __restrict__ b,
-                                 const double* __restrict__ r, int L, long long n, double* partial) {
-  const int i = blockIdx.y;
-  const double* xi = x + (long long)i * n;
-  double acc[2 * kPairMax];
+__global__ void pair_dots_kernel(const double* __restrict__ x, const double* __restrict__ r, int L, long long n,
+                                 double* partial) {
+  double acc[kPairMax * kPairMax];
 #pragma unroll
-  for (int q = 0; q < 2 * kPairMax; ++q) acc[q] = 0.0;
+  for (int q = 0; q < kPairMax * kPairMax; ++q) acc[q] = 0.0;
   for (long long k = blockIdx.x * (long long)VT + threadIdx.x; k < n; k += (long long)gridDim.x * VT) {
-    const double xv = xi[k];
+    double xv[kPairMax], rv[kPairMax];
 #pragma unroll
-    for (int j = 0; j < kPairMax; ++j) {
-      if (j < L) {
-        acc[2 * j] = fma(xv, b[(long long)j * n + k], acc[2 * j]);
-        acc[2 * j + 1] = fma(xv, r[(long long)j * n + k], acc[2 * j + 1]);
-      }
+    for (int i = 0; i < kPairMax; ++i) {
+      xv[i] = i < L ? x[(long long)i * n + k] : 0.0;
+      rv[i] = i < L ? r[(long long)i * n + k] : 0.0;
     }
+#pragma unroll
+    for (int i = 0; i < kPairMax; ++i)
+#pragma unroll
+      for (int j = 0; j < kPairMax; ++j)
+        if (i < L && j < L) acc[i * kPairMax + j] = fma(xv[i], rv[j], acc[i * kPairMax + j]);
   }
-  for (int q = 0; q < 2 * L; ++q) {
-    const double t = block_sum(acc[q]);
-    if (threadIdx.x == 0) partial[((long long)i * gridDim.x + blockIdx.x) * 2 * L + q] = t;
-  }
+#pragma unroll
+  for (int i = 0; i < kPairMax; ++i)
+#pragma unroll
+    for (int j = 0; j < kPairMax; ++j)
+      if (i < L && j < L) {  // uniform: every thread reaches the block sum's barriers
+        const double t = block_sum(acc[i * kPairMax + j]);
+        if (threadIdx.x == 0) partial[(long long)blockIdx.x * L * L + i * L + j] = t;
+      }
 }
 
 __global__ void pair_dots_final_kernel(const double* __restrict__ partial, int L, int G, double* out) {
-  const int q = threadIdx.x;  // (i, j, k) flattened, 2 L L entries
-  if (q >= 2 * L * L) return;
-  const int i = q / (2 * L), jk = q % (2 * L);
+  const int q = threadIdx.x;  // (i, j) flattened, L L entries
+  if (q >= L * L) return;
   double s = 0.0;
-  for (int g = 0; g < G; ++g) s += partial[((long long)i * G + g) * 2 * L + jk];
+  for (int g = 0; g < G; ++g) s += partial[(long long)g * L * L + q];
   out[q] = s;
 }
 
@@ -158,10 +163,10 @@ cudaError_t launch_add_f2d(const float* x, double* y, double scale, long long n,
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair_dots(const double* x, const double* b, const double* r, int L, long long n, double* partial,
-                             double* out, cudaStream_t s) {
+cudaError_t launch_pair_dots(const double* x, const double* r, int L, long long n, double* partial, double* out,
+                             cudaStream_t s) {
   if (L < 1 || L > kPairMax) return cudaErrorInvalidValue;
-  pair_dots_kernel<<<dim3(SM_BLOCKS, L), VT, 0, s>>>(x, b, r, L, n, partial);
+  pair_dots_kernel<<<SM_BLOCKS, VT, 0, s>>>(x, r, L, n, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   pair_dots_final_kernel<<<1, 128, 0, s>>>(partial, L, SM_BLOCKS, out);
