@@ -51,8 +51,16 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
 
-constexpr int RP = BX + 2;  // row pitch of a staged node plane (nodes i0 - 1 .. i0 + BX)
+// staged node plane (FP32 kernels): a row holds the nodes i0 - 1 .. i0 + BX at columns RX0 .. RX0 + BX + 1,
+// so the tile interior i0 .. i0 + BX - 1 starts on a 16-byte boundary (column 4); row pitch 40 floats
+constexpr int RP = BX + 8;
+constexpr int RX0 = 3;
 
 // hex8 tiles: BX x BY output nodes per CTA, (BX + 1) x (BY + 1) elements per layer, one element per
 // thread; BY = 8 (297 elements, 320 threads) or 16 (561 elements, 576 threads: fewer lanes on halo
@@ -324,17 +332,22 @@ __device__ void pcg_alpha_update(PcgState& s, double total, double* hist) {
 template <typename T, int C, bool HAS_X>
 __host__ __device__ constexpr bool hex8_raw() { return HAS_X && sizeof(T) == 4; }
 constexpr int kRing = 5;  // RAW: staged node planes k .. k + 4
+// RAW elasticity packs the corner forces of an element as one float4 per corner (3 components + pad)
+template <typename T, int C, bool HAS_X>
+__host__ __device__ constexpr bool hex8_pack() { return hex8_raw<T, C, HAS_X>() && C == 3; }
 template <typename T, int C, bool HAS_X, int BYT>
 __host__ __device__ constexpr size_t hex8_smem_elems() {
   using TL = Hex8Tile<T, BYT>;
-  return hex8_raw<T, C, HAS_X>() ? (size_t)kRing * C * TL::RPLANE + 2 * 4 * C * TL::NE
-                                 : (size_t)2 * 4 * C * TL::NE + 2 * 4 * C * TL::NE;
+  return hex8_raw<T, C, HAS_X>()
+             ? (size_t)kRing * C * TL::RPLANE + 2 * 4 * (hex8_pack<T, C, HAS_X>() ? 4 : C) * TL::NE
+             : (size_t)2 * 4 * C * TL::NE + 2 * 4 * C * TL::NE;
 }
 
-template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED, int BYT>
+template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED, int BYT, bool WIDE = false>
 __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM)
     hex8_apply_kernel(StencilArgs a, int kz_per_cta) {
   constexpr bool RAW = hex8_raw<T, C, HAS_X>();
+  constexpr bool PACK = hex8_pack<T, C, HAS_X>();
   constexpr int BY = BYT, NE = Hex8Tile<T, BYT>::NE, NT = Hex8Tile<T, BYT>::NT;
   constexpr int RPLANE = Hex8Tile<T, BYT>::RPLANE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -410,32 +423,56 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
     }
   };
 
-  // RAW: stage node plane kz (tile nodes i0 - 1 .. i0 + BX, j0 - 1 .. j0 + BY) into ring slot `slot`;
-  // this thread copies the entries tid + q NT, whose in-plane source offsets are fixed per CTA
-  constexpr int NSTAGE = (C * RPLANE + NT - 1) / NT;
-  int soff[NSTAGE];
+  // RAW: stage node plane kz (tile nodes i0 - 1 .. i0 + BX, j0 - 1 .. j0 + BY) into ring slot `slot`.
+  // WIDE (every tile lies inside the grid along x; nx, the load stride and the field base 16-byte
+  // aligned; chosen by the host): each (component, row) is one 4-byte copy per halo node and eight
+  // 16-byte copies of the interior, one task per thread.  Otherwise every staged entry is a 4-byte copy
+  // with periodic wrap (this thread: entries tid + q NT of the padded plane; pad columns skipped).
+  // Source offsets are fixed per CTA.
+  constexpr int NROW = C * (BY + 2);  // staged rows per plane
+  constexpr int NSTAGE = WIDE ? 1 : (C * RPLANE + NT - 1) / NT;
+  int soff[NSTAGE], doff = 0;
+  bool w16 = false;
 #pragma unroll
-  for (int q = 0; q < NSTAGE; ++q) {
-    const int idx = tid + q * NT;
-    soff[q] = -1;
-    if (RAW && idx < C * RPLANE) {
-      const int j = idx / RPLANE, rem = idx - j * RPLANE, r = rem / RP, c = rem - r * RP;
-      soff[q] = j * (int)d.N + wrap(j0 - 1 + r, d.ny) * d.nx + wrap(i0 - 1 + c, d.nx);
+  for (int q = 0; q < NSTAGE; ++q) soff[q] = -1;
+  if constexpr (RAW && WIDE) {
+    if (tid < NROW * 10) {
+      const int row = tid / 10, q = tid - row * 10, j = row / (BY + 2), r = row - j * (BY + 2);
+      const int col = q == 0 ? 0 : (q == 9 ? BX + 1 : 1 + 4 * (q - 1));  // column relative to RX0
+      doff = j * RPLANE + r * RP + RX0 + col;
+      soff[0] = j * (int)d.N + wrap(j0 - 1 + r, d.ny) * d.nx + wrap(i0 - 1 + col, d.nx);
+      w16 = q != 0 && q != 9;
+    }
+  } else if constexpr (RAW) {
+#pragma unroll
+    for (int q = 0; q < NSTAGE; ++q) {
+      const int idx = tid + q * NT;
+      if (idx < C * RPLANE) {
+        const int j = idx / RPLANE, rem = idx - j * RPLANE, r = rem / RP, c = rem - r * RP - RX0;
+        if (c >= 0 && c < BX + 2) soff[q] = j * (int)d.N + wrap(j0 - 1 + r, d.ny) * d.nx + wrap(i0 - 1 + c, d.nx);
+      }
     }
   }
   auto stage_plane = [&](int slot, int kz) {
     if constexpr (RAW) {
       const T* xk = x + (long long)kz * plane;
       T* dst = RW + slot * C * RPLANE;
+      if constexpr (WIDE) {
+        if (soff[0] >= 0) {
+          if (w16) cp_async16(dst + doff, xk + soff[0]);
+          else cp_async4(dst + doff, xk + soff[0]);
+        }
+      } else {
 #pragma unroll
-      for (int q = 0; q < NSTAGE; ++q)
-        if (soff[q] >= 0) cp_async4(dst + tid + q * NT, xk + soff[q]);
+        for (int q = 0; q < NSTAGE; ++q)
+          if (soff[q] >= 0) cp_async4(dst + tid + q * NT, xk + soff[q]);
+      }
     }
     cp_async_commit();
   };
   // RAW: butterflies (ss, sd, ds, dd) of this thread's face in staged slot `slot`
   auto raw_face = [&](int slot, T (&f)[C][4]) {
-    const T* src = RW + slot * C * RPLANE + ej * RP + ei;
+    const T* src = RW + slot * C * RPLANE + ej * RP + RX0 + ei;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
       const T* sj = src + j * RPLANE;
@@ -458,7 +495,7 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
     // the parity of the layer (the barrier of layer k - 1 orders the gather of layer k - 2 before
     // the writes below), so no barrier is needed before the element step
     if constexpr (!RAW) faces(std::integral_constant<int, CUR ^ 1>{}, next(kzc));
-    T* FC = FC0 + CUR * 4 * C * NE;
+    T* FC = FC0 + CUR * 4 * (PACK ? 4 : C) * NE;
     if (face_thread) {
       T bot[C][4], top[C][4];
       if constexpr (RAW) {
@@ -488,18 +525,29 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
       T pb[C][4], pt[C][4], t1[C][3];
       hex8_element_faces<T, C, ISO, HAS_X, HAS_E>(bot, top, mats + (long long)ph * (9 * C * C), isot + kIsoStride * ph,
                                                   HAS_E ? tau + ph * (3 * C) : nullptr, pb, pt, t1);
+      T cv[4][C];  // corner forces: (0, 0), (1, 0), (0, 1), (1, 1)
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         // face total of plane k, then the transposed in-plane part: corners (a, b) of the face
         const T ss = pb[j][0] + carry[j][0], sd = pb[j][1] + carry[j][1];
         const T ds = pb[j][2] + carry[j][2], dd = pb[j][3] + carry[j][3];
         const T s0 = ss - sd, s1 = ss + sd, d0 = ds - dd, d1 = ds + dd;
-        FC[(0 * C + j) * NE + tid] = s0 - d0;  // corner (0, 0)
-        FC[(1 * C + j) * NE + tid] = s0 + d0;  // corner (1, 0)
-        FC[(2 * C + j) * NE + tid] = s1 - d1;  // corner (0, 1)
-        FC[(3 * C + j) * NE + tid] = s1 + d1;  // corner (1, 1)
+        cv[0][j] = s0 - d0;
+        cv[1][j] = s0 + d0;
+        cv[2][j] = s1 - d1;
+        cv[3][j] = s1 + d1;
 #pragma unroll
         for (int q = 0; q < 4; ++q) carry[j][q] = pt[j][q];
+      }
+      if constexpr (PACK) {
+        float4* F4 = reinterpret_cast<float4*>(FC);
+#pragma unroll
+        for (int cn = 0; cn < 4; ++cn) F4[cn * NE + tid] = make_float4(cv[cn][0], cv[cn][1], cv[cn][2], 0.0f);
+      } else {
+#pragma unroll
+        for (int cn = 0; cn < 4; ++cn)
+#pragma unroll
+          for (int j = 0; j < C; ++j) FC[(cn * C + j) * NE + tid] = cv[cn][j];
       }
       if ((RED == RED_STATS || RED == RED_SUMS) && owner && k >= k0) {
 #pragma unroll
@@ -520,15 +568,28 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
       // node (i, j) of plane k is corner (1,1) of face (i-1, j-1), (0,1) of (i, j-1),
       // (1,0) of (i-1, j) and (0,0) of (i, j)
       const int e00 = nj * EX + ni;
+      T gv[C];
+      if constexpr (PACK) {
+        const float4* F4 = reinterpret_cast<const float4*>(FC);
+        const float4 a3 = F4[3 * NE + e00], a2 = F4[2 * NE + e00 + 1], a1 = F4[1 * NE + e00 + EX],
+                     a0 = F4[0 * NE + e00 + EX + 1];
+        gv[0] = a3.x + a2.x + a1.x + a0.x;
+        gv[1] = a3.y + a2.y + a1.y + a0.y;
+        gv[2] = a3.z + a2.z + a1.z + a0.z;
+      } else {
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+          gv[j] = FC[(3 * C + j) * NE + e00] + FC[(2 * C + j) * NE + e00 + 1] + FC[(1 * C + j) * NE + e00 + EX] +
+                  FC[(0 * C + j) * NE + e00 + EX + 1];
+      }
 #pragma unroll
       for (int j = 0; j < C; ++j) {
-        const T v = FC[(3 * C + j) * NE + e00] + FC[(2 * C + j) * NE + e00 + 1] +
-                    FC[(1 * C + j) * NE + e00 + EX] + FC[(0 * C + j) * NE + e00 + EX + 1];
+        const T v = gv[j];
         const T val = ysc * v;
         const long long gidx = (long long)j * d.N + (long long)kzc * plane + node_off;
         if (RED != RED_SUMS) y[gidx] = val;
         if constexpr (RED == RED_PCG) {
-          if constexpr (RAW) acc_p.add(val, RW[(s0 * C + j) * RPLANE + (nj + 1) * RP + ni + 1]);
+          if constexpr (RAW) acc_p.add(val, RW[(s0 * C + j) * RPLANE + (nj + 1) * RP + RX0 + ni + 1]);
           else acc_p.add(val, __ldg(x + gidx));
         }
         if (RED == RED_STATS || RED == RED_SUMS) acc_y += (double)val * (double)val;
@@ -917,7 +978,8 @@ void hex8_grid(const Dims& d, int n_loads, int* tiles, int* slabs, int* kz) {
   *slabs = (d.nz + bkz - 1) / bkz;
 }
 
-template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED, int BYT = hex8_default_rows<T>()>
+template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED, int BYT = hex8_default_rows<T>(),
+          bool WIDE = false>
 cudaError_t launch_hex8_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
   const Dims& d = a.d;
   int tiles, slabs, kz;
@@ -925,7 +987,7 @@ cudaError_t launch_hex8_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
   if (ctas) *ctas = tiles * slabs;
   if (RED == RED_PCG && tiles * slabs > a.red.max_blocks) return cudaErrorInvalidConfiguration;
   const size_t smem = sizeof(T) * hex8_smem_elems<T, C, HAS_X, BYT>();
-  auto kern = hex8_apply_kernel<T, C, ISO, HAS_X, HAS_E, RED, BYT>;
+  auto kern = hex8_apply_kernel<T, C, ISO, HAS_X, HAS_E, RED, BYT, WIDE>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(tiles, slabs, a.n_loads);
@@ -964,14 +1026,25 @@ cudaError_t launch_pixel_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
 }
 
 // modes: PCG (x, <x, y>), STATS (residual / right-hand side with sums), plain (x and/or e)
+// every x tile full and 16-byte aligned rows: the FP32 PCG apply stages node planes with 16-byte copies
+bool hex8_wide(const StencilArgs& a) {
+  return a.d.nx % BX == 0 && a.d.nx % 4 == 0 && a.load_stride % 4 == 0 &&
+         (reinterpret_cast<unsigned long long>(a.x) & 15) == 0;
+}
+
 template <typename T, int C, bool ISO>
 cudaError_t dispatch_hex8(const StencilArgs& a, int* ctas, cudaStream_t s) {
   const bool hx = a.x != nullptr, he = a.tau != nullptr;
   if (a.st != nullptr) {
     if (!hx || he) return cudaErrorInvalidValue;
-    if (a.tile_rows != 0 && a.tile_rows != hex8_default_rows<T>())
-      return launch_hex8_t<T, C, ISO, true, false, RED_PCG, 24 - hex8_default_rows<T>()>(a, ctas, s);
-    return launch_hex8_t<T, C, ISO, true, false, RED_PCG>(a, ctas, s);
+    constexpr int R0 = hex8_default_rows<T>(), R1 = 24 - hex8_default_rows<T>();
+    const bool alt = a.tile_rows != 0 && a.tile_rows != R0;
+    if (hex8_raw<T, C, true>() && hex8_wide(a)) {  // FP32: 16-byte plane staging
+      return alt ? launch_hex8_t<T, C, ISO, true, false, RED_PCG, R1, true>(a, ctas, s)
+                 : launch_hex8_t<T, C, ISO, true, false, RED_PCG, R0, true>(a, ctas, s);
+    }
+    return alt ? launch_hex8_t<T, C, ISO, true, false, RED_PCG, R1>(a, ctas, s)
+               : launch_hex8_t<T, C, ISO, true, false, RED_PCG, R0>(a, ctas, s);
   }
   if (a.stats != nullptr && a.y == nullptr) {
     if (hx && he) return launch_hex8_t<T, C, ISO, true, true, RED_SUMS>(a, ctas, s);
