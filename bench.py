@@ -159,7 +159,7 @@ def kernel_model(s):
 
 FP64_INSTR_PEAK = 152 * 2 * 2.07e9     # FP64 instructions/s: 152 SMs x 2 FP64 lanes-per-clock x max clock
 # DRAM bytes (read + write) of one 6-load FP64 stiffness launch on the 128^3 workload, from ncu
-FP64_STIFFNESS_DRAM_BYTES = 324.437248e6 + 263.683840e6
+FP64_STIFFNESS_DRAM_BYTES = 324.696064e6 + 262.707200e6
 
 
 def run_ours(args):
