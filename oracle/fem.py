@@ -9,7 +9,8 @@ What is computed (definitions, no blocking or fusion):
   quadrature points, in Mandel form for elasticity (Eq. mandel_grad) and plain d-vector form for the
   scalar problem (App. A, Eq. Dt_mat).
 * Sec. 3, Eq. W_mat and Eq. global_sum: quadrature weights w^Q (Fig. 3: two P1 triangles per pixel
-  with w = V_p / 2; bilinear/trilinear elements with 2^d Gauss points, w = V_p / 2^d).
+  with w = V_p / 2; bilinear/trilinear elements with 2^d Gauss points, w = V_p / 2^d; the 3-D
+  counterpart of Fig. 3 b, six P1 tetrahedra per voxel with one point each, w = V_p / 6).
 * Sec. 3.1, Eq. lin_system: K = D^T W C D and, for the linear problem at u_(0) = 0,
   b = -D^T W C e.  Assembled as a scipy CSR matrix over element matrices
   K_e = sum_q w_q B_q^T C_e B_q with periodic node wrap.
@@ -21,7 +22,8 @@ Conventions (readings of the paper where it is silent): unit cell [0, 1]^d, grid
 k + c) mod n; node flat index i + n_x (j + n_y k); DOF index comp * N + node (component-blocked,
 the paper's u = [u_1; u_2] ordering of Eq. Du_mat).  Mandel order (11, 22, 12) in 2-D and
 (11, 22, 33, 23, 13, 12) in 3-D with sqrt(2) on shear strains.  P1 pixels are split along the
-(0, 0)-(1, 1) diagonal.
+(0, 0)-(1, 1) diagonal; P1 voxels into the six tetrahedra that share the (0, 0, 0)-(1, 1, 1)
+diagonal, one per order in which a path from (0, 0, 0) to (1, 1, 1) steps along x, y and z.
 """
 from __future__ import annotations
 
@@ -31,7 +33,7 @@ import math
 import numpy as np
 import scipy.sparse as sp
 
-ELEMS = ("p1tri2_2d", "q1_2d", "hex8_3d", "p1tri4_2d")
+ELEMS = ("p1tri2_2d", "q1_2d", "hex8_3d", "p1tri4_2d", "p1tet6_3d")
 
 
 # ----------------------------------------------------------------------------------------------
@@ -44,7 +46,7 @@ class Grid:
         assert elem in ELEMS and physics in ("scalar", "elastic")
         self.shape = tuple(int(s) for s in shape)
         self.dim = len(self.shape)
-        assert (self.dim == 3) == (elem == "hex8_3d")
+        assert (self.dim == 3) == (elem in ("hex8_3d", "p1tet6_3d"))
         self.elem, self.physics = elem, physics
         self.n_xyz = self.shape[::-1]                       # (n_x, n_y[, n_z])
         self.h = np.array([1.0 / n for n in self.n_xyz])     # unit cell
@@ -96,10 +98,11 @@ class Grid:
 # element gradients at the quadrature points (Sec. 3, Fig. 3)
 # ----------------------------------------------------------------------------------------------
 def _p1_gradients(verts):
-    """Gradients of the three P1 basis functions of a triangle with vertices ``verts`` (3 x 2)."""
-    A = np.column_stack([np.ones(3), verts])          # rows [1, x, y]; phi_i = coefficients
+    """Gradients of the d + 1 P1 basis functions of a simplex with vertices ``verts`` ((d+1) x d)."""
+    k = verts.shape[0]
+    A = np.column_stack([np.ones(k), verts])          # rows [1, x, y(, z)]; phi_i = coefficients
     coef = np.linalg.inv(A)                           # column i: coefficients of phi_i
-    return coef[1:, :]                                # (2, 3): d phi_i / d x_beta
+    return coef[1:, :]                                # (d, d + 1): d phi_i / d x_beta
 
 
 def quadrature(grid: Grid):
@@ -117,6 +120,20 @@ def quadrature(grid: Grid):
             dN[:, grid.corners.index(e1)] = g[:, 1]
             dN[:, 4] = g[:, 2]
             pts.append((dN, grid.vp / 4.0))
+    elif grid.elem == "p1tet6_3d":
+        # six tetrahedra (0,0,0) -> +e_p -> +e_q -> (1,1,1), one per order (p, q, r) of the axes
+        corner_xyz = {off: np.array(off, dtype=float) * h for off in grid.corners}
+        for order in itertools.permutations(range(3)):
+            path = [(0, 0, 0)]
+            for ax in order:
+                nxt = list(path[-1])
+                nxt[ax] = 1
+                path.append(tuple(nxt))
+            g = _p1_gradients(np.array([corner_xyz[t] for t in path]))
+            dN = np.zeros((3, grid.ne))
+            for col, t in enumerate(path):
+                dN[:, grid.corners.index(t)] = g[:, col]
+            pts.append((dN, grid.vp / 6.0))
     elif grid.elem == "p1tri2_2d":
         corner_xy = {off: np.array(off, dtype=float) * h for off in grid.corners}
         for tri in (((0, 0), (1, 0), (1, 1)), ((0, 0), (1, 1), (0, 1))):

@@ -66,6 +66,27 @@ def test_p1_scalar_is_five_point_laplacian():
         np.testing.assert_allclose(K[node], expect, atol=1e-13)
 
 
+def test_p1tet6_scalar_is_seven_point_laplacian():
+    """Six tetrahedra per voxel along the (0,0,0)-(1,1,1) diagonal, identity conductivity, cubic voxels:
+    K is the 7-point Laplacian times h (textbook stencil; the face- and body-diagonal couplings of the
+    six tetrahedra cancel), and the reference symbol of an elastic material is real (the split is
+    symmetric under the point reflection through the voxel centre)."""
+    n = 4
+    g = fem.Grid((n, n, n), "p1tet6_3d", "scalar")
+    K = fem.assemble_K(g, np.zeros(g.N, int), [np.eye(3)]).toarray()
+    h = g.h[0]
+    L = np.zeros_like(K)
+    for node in range(g.N):
+        x, y, z = node % n, (node // n) % n, node // (n * n)
+        L[node, node] = 6.0 * h
+        for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+            L[node, ((x + dx) % n) + n * (((y + dy) % n) + n * ((z + dz) % n))] -= h
+    np.testing.assert_allclose(K, L, atol=1e-14)
+    ge = fem.Grid((4, 6, 4), "p1tet6_3d", "elastic")
+    Sh = solvers.kref_symbol(ge, _rand_spd(6, 7))
+    assert np.abs(np.imag(Sh)).max() <= 1e-14 * np.abs(Sh).max()
+
+
 def test_hex8_scalar_element_closed_form():
     """Q1 3-D Laplacian element matrix: h*k*(1/3 diag, 0 edge, -1/12 face/body diagonal)."""
     n, k = 4, 3.0
@@ -89,7 +110,8 @@ def test_q1_2d_scalar_element_closed_form():
             assert abs(Ke[a, b] - {0: 4 / 6, 1: -1 / 6, 2: -2 / 6}[dist]) < 1e-14
 
 
-@pytest.mark.parametrize("elem,shape", [("hex8_3d", (3, 4, 5)), ("q1_2d", (4, 5)), ("p1tri2_2d", (4, 5))])
+@pytest.mark.parametrize("elem,shape", [("hex8_3d", (3, 4, 5)), ("q1_2d", (4, 5)), ("p1tri2_2d", (4, 5)),
+                                        ("p1tet6_3d", (3, 4, 5))])
 @pytest.mark.parametrize("physics", ["scalar", "elastic"])
 def test_patch_linear_field(elem, shape, physics):
     """A linear nodal field has the exact constant gradient / Mandel strain at every quadrature point,
@@ -199,7 +221,9 @@ def test_symbol_p1_isotropic_closed_form():
 @pytest.mark.parametrize("elem,shape,physics", [("hex8_3d", (4, 6, 4), "elastic"),
                                                  ("hex8_3d", (6, 4, 8), "scalar"),
                                                  ("p1tri2_2d", (6, 8), "elastic"),
-                                                 ("q1_2d", (6, 4), "scalar")])
+                                                 ("q1_2d", (6, 4), "scalar"),
+                                                 ("p1tet6_3d", (4, 6, 4), "elastic"),
+                                                 ("p1tet6_3d", (6, 4, 8), "scalar")])
 def test_precond_is_pseudo_inverse(elem, shape, physics):
     """K_ref (K_ref^+ r) = r minus its mean per component, for a random r (Eq. M_inverse)."""
     g = fem.Grid(shape, elem, physics)
@@ -218,7 +242,8 @@ def test_precond_is_pseudo_inverse(elem, shape, physics):
 # ------------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("elem,shape,physics", [("hex8_3d", (4, 4, 4), "elastic"),
                                                  ("p1tri2_2d", (8, 8), "scalar"),
-                                                 ("q1_2d", (6, 6), "elastic")])
+                                                 ("q1_2d", (6, 6), "elastic"),
+                                                 ("p1tet6_3d", (4, 4, 4), "elastic")])
 def test_homogeneous_material(elem, shape, physics):
     g = fem.Grid(shape, elem, physics)
     C = _rand_spd(g.m, 4)
@@ -234,7 +259,7 @@ def test_laminate_scalar_exact():
     """Layers normal to x: C_eff = diag(harmonic, arithmetic[, arithmetic]) exactly (FE space holds the solution)."""
     layers = [0, 0, 1, 1, 1, 0, 2, 2]
     ks = [1.0, 10.0, 3.0]
-    for elem, shape in (("hex8_3d", (2, 3, 8)), ("p1tri2_2d", (4, 8)), ("q1_2d", (4, 8))):
+    for elem, shape in (("hex8_3d", (2, 3, 8)), ("p1tri2_2d", (4, 8)), ("q1_2d", (4, 8)), ("p1tet6_3d", (2, 3, 8))):
         g = fem.Grid(shape, elem, "scalar")
         ids = I.laminate(shape, layers).ravel()
         mod = [k * np.eye(g.dim) for k in ks]
@@ -252,9 +277,9 @@ def test_laminate_elastic_exact():
     C_eff = <C> - <C_:n C_nn^-1 C_n:> + <C_:n C_nn^-1> <C_nn^-1>^-1 <C_nn^-1 C_n:>."""
     layers = [0, 1, 1, 0, 0, 2]
     Cs = [_rand_spd(6, 20), _rand_spd(6, 21, 5.0), I.isotropic_elastic_mandel(7.0, 0.25)]
-    g = fem.Grid((2, 2, 6), "hex8_3d", "elastic")
     ids = I.laminate((2, 2, 6), layers).ravel()
-    res = solvers.homogenise(g, ids, Cs, np.eye(6), method="dense")
+    res = solvers.homogenise(fem.Grid((2, 2, 6), "hex8_3d", "elastic"), ids, Cs, np.eye(6), method="dense")
+    res_tet = solvers.homogenise(fem.Grid((2, 2, 6), "p1tet6_3d", "elastic"), ids, Cs, np.eye(6), method="dense")
     nset = [0, 4, 5]
     f = np.bincount(layers, minlength=3) / len(layers)
     avg = lambda fn: sum(f[p] * fn(Cs[p]) for p in range(3))
@@ -266,6 +291,7 @@ def test_laminate_elastic_exact():
     R = avg(lambda C: inv_nn(C) @ C[nset, :])
     expect = A - Bm + L @ np.linalg.inv(M) @ R
     np.testing.assert_allclose(res["C_eff"], expect, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(res_tet["C_eff"], expect, rtol=1e-10, atol=1e-10)
 
 
 def _voigt_reuss_check(C_eff, moduli, ids):
@@ -307,7 +333,8 @@ def test_circle2d_invariants_and_solver_agreement():
 @pytest.mark.parametrize("elem,shape,physics", [("hex8_3d", (3, 2, 4), "elastic"),
                                                  ("hex8_3d", (2, 3, 4), "scalar"),
                                                  ("p1tri2_2d", (4, 6), "elastic"),
-                                                 ("q1_2d", (3, 4), "scalar")])
+                                                 ("q1_2d", (3, 4), "scalar"),
+                                                 ("p1tet6_3d", (3, 2, 4), "elastic")])
 def test_brute_force_tiny(elem, shape, physics):
     """Tiny random grids: dense bordered solve == CG == PCG; residual K u - b vanishes."""
     g = fem.Grid(shape, elem, physics)
