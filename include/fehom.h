@@ -80,7 +80,10 @@ typedef struct {
   int use_graph;     /* 1 (default): replay PCG iterations from a captured CUDA graph; 0: plain launches */
   int profile;       /* 1: record CUDA events around every kernel of the PCG iterations (see fehom_kernel_times) */
   int autotune;      /* 1 (default): on the first solve of a batch size, time the FFT passes' launch plans
-                        (x-line pairs per CTA, columns per CTA) on the context's buffers and keep the fastest */
+                        (x-line pairs per CTA, columns per CTA) on the context's buffers and keep the fastest.
+                        The chosen plans (and the stencil tuner's) are kept for the process: a later context
+                        with the same device, element, grid, field blocks, batch size, precision and
+                        restricting options takes them without timing again */
   int x0_scaling;    /* 1 (default): a warm start x0 (mean removed) is replaced, per load, by gamma x0 with
                         gamma = <b, x0> / <x0, K x0> (0 when <x0, K x0> = 0): the multiple of x0 closest to
                         the solution in the energy norm, never farther from it than the zero guess */

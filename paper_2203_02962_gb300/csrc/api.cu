@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -467,6 +468,23 @@ fehom_status harvest_events(fehom_ctx* ctx, int prec, int n_iter) {
   return FEHOM_OK;
 }
 
+// Tuned launch plans shared by every context of the process.  A plan depends only on the device, the
+// grid, the field blocks, the batch size, the precision and the options that restrict it, so a
+// context of the same shape (a new cell of a series, a solver rebuilt per request) takes the first
+// context's choice instead of timing the candidates again.
+struct PlanKey {
+  int v[12];
+  bool operator<(const PlanKey& o) const { return std::lexicographical_compare(v, v + 12, o.v, o.v + 12); }
+};
+std::mutex g_plan_mu;
+std::map<PlanKey, fehom_ctx::FftPlan> g_fft_plans;
+std::map<PlanKey, fehom_ctx::StencilPlan> g_stencil_plans;
+
+PlanKey plan_key(const fehom_ctx* ctx, int kind, int prec, int n_loads) {
+  return PlanKey{{kind, prec, ctx->device, ctx->d.elem, ctx->d.dim, ctx->d.nx, ctx->d.ny, ctx->d.nz, ctx->d.c,
+                  n_loads, kind == 0 ? ctx->opt.fft_xy : 0, kind == 1 ? (ctx->iso ? 1 : 0) : 0}};
+}
+
 // Launch-plan tuner of the FFT passes: each candidate is timed with CUDA events on the context's
 // stream over the solve's own buffers (zeroed first), for the batch size of the solve.
 template <typename T>
@@ -478,6 +496,16 @@ fehom_status autotune_fft(fehom_ctx* ctx, int n_loads) {
   if (prec == 1 && ctx->opt.fft_xy == 1 && fft_xy_supported(ctx->d, true) && fft_last128_supported(ctx->d, true)) {
     pl.tuned_loads = n_loads;
     return FEHOM_OK;
+  }
+  const PlanKey key = plan_key(ctx, 0, prec, n_loads);
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    const auto it = g_fft_plans.find(key);
+    if (it != g_fft_plans.end()) {
+      pl = it->second;
+      ctx->graph_key[0] = 0;  // captured iterations used the previous plan
+      return FEHOM_OK;
+    }
   }
   cudaStream_t s = ctx->stream;
   T* fin = prec ? (T*)ctx->r32 : (T*)ctx->r64;
@@ -588,6 +616,10 @@ fehom_status autotune_fft(fehom_ctx* ctx, int n_loads) {
   pl.ms[2] = ml;
   pl.tuned_loads = n_loads;
   ctx->graph_key[0] = 0;  // captured iterations used the previous plan
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_fft_plans[key] = pl;
+  }
   return FEHOM_OK;
 }
 
@@ -606,6 +638,16 @@ fehom_status autotune_stencil(fehom_ctx* ctx, int n_loads) {
     return FEHOM_OK;
   }
   if (!ctx->opt.autotune || sp.tuned_loads == n_loads) return FEHOM_OK;
+  const PlanKey key = plan_key(ctx, 1, prec, n_loads);
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    const auto it = g_stencil_plans.find(key);
+    if (it != g_stencil_plans.end()) {
+      if (sp.rows != it->second.rows) ctx->graph_key[0] = 0;
+      sp = it->second;
+      return FEHOM_OK;
+    }
+  }
   cudaStream_t s = ctx->stream;
   if (!ctx->tune_st) CK(cudaMalloc(&ctx->tune_st, sizeof(PcgState) * kMaxLoads));
   std::vector<PcgState> hs(n_loads);
@@ -659,6 +701,10 @@ fehom_status autotune_stencil(fehom_ctx* ctx, int n_loads) {
   sp.rows = rows_best;
   sp.tuned_loads = n_loads;
   ctx->graph_key[0] = 0;  // captured iterations used the previous tile
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_stencil_plans[key] = sp;
+  }
   return FEHOM_OK;
 }
 

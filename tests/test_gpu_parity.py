@@ -512,6 +512,26 @@ def test_autotuned_plans_are_valid_and_agree():
     assert _rel(outs[0], outs[2]) < 1e-9 and _rel(outs[1], outs[3]) < 1e-8
 
 
+def test_tuned_plans_are_shared_by_contexts_of_the_same_shape():
+    """The launch-plan tuners time their candidates once per shape in a process: a second context of
+    the same grid, field blocks, batch size and precision adopts the first one's plans (same choices
+    and the same recorded timings) and reproduces its result bit for bit."""
+    n = 48
+    ids, mod = _small_elastic(n, seed=21)
+    plans, fluxes = [], []
+    for _ in range(2):
+        s = _solver("hex8_3d", "elastic", (n, n, n), ids, mod, precision="mixed")
+        s.precond_build()
+        out = s.solve(np.eye(6)[:3], tol=1e-8)
+        plans.append((s.fft_plan("mixed"), s.stencil_plan("mixed")))
+        fluxes.append(np.asarray(out["mean_flux"]))
+        s.close()
+    (f0, s0), (f1, s1) = plans
+    assert f0["pairs"] in (4, 8, 16) and all(m >= 0 for m in f0["ms"])
+    assert f0 == f1 and s0 == s1
+    assert np.array_equal(fluxes[0], fluxes[1])
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_batch_equals_individual_solves(precision):
     """fehom_solve_batch (one graph, one branch per cell; cells of different sizes and contrasts)
