@@ -484,13 +484,14 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
       f[j][3] = d1 - d0;
     }
   };
-  auto ring = [&](int k) { return (k - k0 + 1) % kRing; };
   T fprev[C][4];  // RAW: butterflies of the top face of the previous layer (this layer's bottom face)
 
-  // B + C for element layer k (planes k: slot CUR, k + 1: slot CUR ^ 1); kzc = wrap(k)
-  auto layer = [&](auto cur_c, int k, int kzc) {
+  // B + C for element layer k (planes k: slot CUR, k + 1: slot CUR ^ 1); kzc = wrap(k).  RAW: plane k
+  // sits in ring slot s0 = (k - k0 + 1) mod kRing and plane k + 4 (kz4 = wrap(k + 4)) goes to the slot
+  // before it; both are carried from layer to layer instead of recomputed (no integer division)
+  auto layer = [&](auto cur_c, int k, int kzc, [[maybe_unused]] int s0, [[maybe_unused]] int kz4) {
     [[maybe_unused]] constexpr int CUR = decltype(cur_c)::value;
-    [[maybe_unused]] const int s0 = RAW ? ring(k) : 0, s1 = s0 == kRing - 1 ? 0 : s0 + 1;
+    [[maybe_unused]] const int s1 = s0 == kRing - 1 ? 0 : s0 + 1;
     // the face butterflies are private to their thread, and the corner buffer FC alternates with
     // the parity of the layer (the barrier of layer k - 1 orders the gather of layer k - 2 before
     // the writes below), so no barrier is needed before the element step
@@ -561,7 +562,7 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
     if constexpr (RAW) cp_async_wait_group<1>();
     __syncthreads();
     if constexpr (RAW) {
-      if (k + 4 <= k1) stage_plane(ring(k + 4), wrap(k + 4, d.nz));
+      if (k + 4 <= k1) stage_plane(s0 == 0 ? kRing - 1 : s0 - 1, kz4);
       else cp_async_commit();  // an empty group keeps one group per layer
     }
     if (node_thread && k >= k0) {
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
   if constexpr (RAW) {  // planes k0 - 1 .. k0 + 2, one group each; the first two visible to all
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      if (k0 - 1 + p <= k1) stage_plane(ring(k0 - 1 + p), wrap(k0 - 1 + p, d.nz));
+      if (k0 - 1 + p <= k1) stage_plane(p, wrap(k0 - 1 + p, d.nz));
       else cp_async_commit();
     }
     cp_async_wait_group<2>();
@@ -612,14 +613,21 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
     faces(std::integral_constant<int, 0>{}, kz);
   }
   int k = k0 - 1;
+  int s0 = 0, kz4 = RAW ? wrap(k0 + 3, d.nz) : 0;
+  auto advance = [&] {
+    kz = next(kz);
+    if constexpr (RAW) {
+      kz4 = next(kz4);
+      s0 = s0 == kRing - 1 ? 0 : s0 + 1;
+    }
+    ++k;
+  };
   while (k < k1) {
-    layer(std::integral_constant<int, 0>{}, k, kz);
-    kz = next(kz);
-    ++k;
+    layer(std::integral_constant<int, 0>{}, k, kz, s0, kz4);
+    advance();
     if (k >= k1) break;
-    layer(std::integral_constant<int, 1>{}, k, kz);
-    kz = next(kz);
-    ++k;
+    layer(std::integral_constant<int, 1>{}, k, kz, s0, kz4);
+    advance();
   }
 
   if (RED == RED_PCG) {
