@@ -327,6 +327,38 @@ fehom_status fehom_rhs_df(fehom_ctx* ctx, const double* e, double* b);
 /* z = K_ref^+ r = F^-1 K_hat^+ F r (Eq. M_inverse); r, z: c x N.  Needs fehom_precond_build. */
 fehom_status fehom_apply_precond(fehom_ctx* ctx, const void* r, void* z, int precision);
 
+/* The two halves of one PCG iteration as the solve runs them (Sec. 4.1, PCG of Saad's Alg. 9.1 in the
+ * symmetric form, with the operator K = D^T W C D of Sec. 5.1 and the preconditioner K_ref^+ of
+ * Eq. M_inverse / Sec. 5.3), for n_loads loads at once (1 <= n_loads <= 64), exposed so that the fused
+ * kernels of the iteration can be checked one by one.  Fields are device arrays of n_loads x c x N
+ * values of the precision's type (double for FEHOM_FP64, float for FEHOM_MIXED), load-major; the
+ * scalars are host arrays of n_loads doubles.  The calls use scratch PCG states of the context, not the
+ * solve's, and return after the work is complete.
+ *
+ * fehom_pcg_apply_stiffness -- the stiffness launch of an iteration: ap = K p, with <p, K p> reduced in
+ * the same launch (FP64 kernels in FP64; FP32 kernels with compensated FP32 products, then FP64) and
+ * alpha = rz / <p, K p> formed on the device.
+ *   rz       <r, z> of each load (the numerator of alpha).
+ *   rows     FEHOM_HEX8_3D: node rows per tile, 8 or 16 (0 = the context's plan); ignored otherwise.
+ *   staging  FEHOM_HEX8_3D FP32: 0 = the solve's choice (16-byte row copies of the node planes when every
+ *            x tile is full and the rows are 16-byte aligned), 1 = 4-byte copies of every plane entry.
+ *   pAp, alpha  NULL or host outputs.
+ * Errors: FEHOM_E_INVALID, FEHOM_E_BREAKDOWN (<p, K p> not positive and finite for some load; outputs
+ * still written), FEHOM_E_CUDA. */
+fehom_status fehom_pcg_apply_stiffness(fehom_ctx* ctx, int precision, int n_loads, const void* p, void* ap,
+                                       const double* rz, int rows, int staging, double* pAp, double* alpha);
+
+/* fehom_pcg_precond_step -- the preconditioner passes of an iteration with their fused vector updates:
+ *   alpha != NULL:  r -= alpha Ap;  z = K_ref^+ r;  rz_new = <r, z>;  beta = rz_new / rz;
+ *                   x += alpha p;  p = z + beta p            (r, x, p updated in place; ap read)
+ *   alpha == NULL:  the first apply of PCG:  z = K_ref^+ r;  rz_new = <r, z>;  p = z   (ap, x, rz unused)
+ * <r, z> is the Parseval sum over the half spectrum, formed in the last-axis pass.  The FFT launch plan is
+ * the context's (option fft_xy, or the tuner's choice after a solve).  rz_new, beta: NULL or host outputs.
+ * Errors: FEHOM_E_STATE (before fehom_precond_build), FEHOM_E_INVALID, FEHOM_E_BREAKDOWN (non-finite
+ * <r, z>), FEHOM_E_OOM, FEHOM_E_CUDA. */
+fehom_status fehom_pcg_precond_step(fehom_ctx* ctx, int precision, int n_loads, void* r, const void* ap, void* x,
+                                    void* p, const double* alpha, const double* rz, double* rz_new, double* beta);
+
 /* Copy the FP64 inverse symbol table to the host: out[e * Nh + (kz * n_y + ky) * nxh + kx] for the
  * packed symmetric entries e of K_hat^+(k) (c = 1: (00); c = 2: (00, 11, 01); c = 3: (00, 11, 22,
  * 12, 02, 01)), half spectrum kx = 0..n_x/2, Nh = nxh n_y n_z.  The stored values include the
@@ -345,8 +377,9 @@ fehom_status fehom_mean_flux(fehom_ctx* ctx, const double* e, const double* u, d
  * library, which every GPU that loads the library keeps until the process exits.  It holds the
  * per-CTA partial sums, their totals and the per-phase load table, so it serves grids up to about
  * 256^3 voxels in 3-D; larger grids are rejected with FEHOM_E_UNSUPPORTED_SIZE and a message giving
- * the space they would need.  The first call on a device looks up the array's device address; make
- * that first call before any stream capture on that device.  All calls share the one array and it
+ * the space they would need.  The first call on a device looks up the array's device address.  The call
+ * copies the load table from host memory and waits for the stream, so it never runs on a stream that is
+ * being captured into a CUDA graph: it returns FEHOM_E_STATE there.  All calls share the one array and it
  * keeps the last call's contents (each call overwrites every entry it reads, so nothing needs
  * clearing): calls that overlap on the GPU, from several threads or streams, race and must be
  * serialised by the caller.  Arguments as for fehom_mean_flux; the context is only read.

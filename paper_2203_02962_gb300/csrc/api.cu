@@ -1734,6 +1734,101 @@ fehom_status fehom_apply_precond(fehom_ctx* ctx, const void* r, void* z, int pre
   return FEHOM_OK;
 }
 
+// Running PCG states of the operator-level PCG entry points (the stencil tuner's array, never the
+// solve's): state RUN, the given <r, z> and alpha, no stopping test (tol^2 = 0), no iteration cap.
+static fehom_status op_states(fehom_ctx* ctx, int n_loads, const double* rz, const double* alpha) {
+  if (!ctx->tune_st) CK(cudaMalloc(&ctx->tune_st, sizeof(PcgState) * kMaxLoads));
+  std::vector<PcgState> hs(n_loads);
+  for (int l = 0; l < n_loads; ++l) {
+    std::memset(&hs[l], 0, sizeof(PcgState));
+    hs[l].state = ST_RUN;
+    hs[l].rz = rz ? rz[l] : 0.0;
+    hs[l].alpha = alpha ? alpha[l] : 0.0;
+    hs[l].bnorm2 = 1.0;
+    hs[l].max_iter = 1 << 30;
+  }
+  CK(cudaMemcpyAsync(ctx->tune_st, hs.data(), sizeof(PcgState) * n_loads, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FEHOM_OK;
+}
+
+static fehom_status op_read_states(fehom_ctx* ctx, int n_loads, std::vector<PcgState>* hs) {
+  hs->resize(n_loads);
+  CK(cudaMemcpyAsync(hs->data(), ctx->tune_st, sizeof(PcgState) * n_loads, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FEHOM_OK;
+}
+
+fehom_status fehom_pcg_apply_stiffness(fehom_ctx* ctx, int precision, int n_loads, const void* p, void* ap,
+                                       const double* rz, int rows, int staging, double* pAp, double* alpha) {
+  if (!ctx || !p || !ap || !rz) return FEHOM_E_INVALID;
+  if (n_loads < 1 || n_loads > kMaxLoads) FAIL(FEHOM_E_INVALID, "fehom_pcg_apply_stiffness: n_loads out of range");
+  if (rows != 0 && rows != 8 && rows != 16) FAIL(FEHOM_E_INVALID, "fehom_pcg_apply_stiffness: rows must be 0, 8 or 16");
+  if (staging != 0 && staging != 1) FAIL(FEHOM_E_INVALID, "fehom_pcg_apply_stiffness: staging must be 0 or 1");
+  if (precision != FEHOM_FP64 && precision != FEHOM_MIXED) FAIL(FEHOM_E_INVALID, "bad precision");
+  for (int l = 0; l < n_loads; ++l)
+    if (!std::isfinite(rz[l])) FAIL(FEHOM_E_INVALID, "fehom_pcg_apply_stiffness: non-finite <r, z>");
+  const bool fp32 = precision == FEHOM_MIXED;
+  TRY(op_states(ctx, n_loads, rz, nullptr));
+  StencilArgs a = stencil_args(ctx, fp32, n_loads);
+  a.x = p;
+  a.y = ap;
+  a.st = ctx->tune_st;
+  a.red.hist = nullptr;
+  if (rows) a.tile_rows = rows;
+  a.narrow = staging;
+  if (fp32) CK(launch_stiffness<float>(a, ctx->stream));
+  else CK(launch_stiffness<double>(a, ctx->stream));
+  count_launch(ctx);
+  std::vector<PcgState> hs;
+  TRY(op_read_states(ctx, n_loads, &hs));
+  bool broke = false;
+  for (int l = 0; l < n_loads; ++l) {
+    if (pAp) pAp[l] = hs[l].pAp;
+    if (alpha) alpha[l] = hs[l].alpha;
+    broke = broke || hs[l].state == ST_BREAK;
+  }
+  if (broke) FAIL(FEHOM_E_BREAKDOWN, "fehom_pcg_apply_stiffness: <p, K p> not positive and finite for a load");
+  return FEHOM_OK;
+}
+
+fehom_status fehom_pcg_precond_step(fehom_ctx* ctx, int precision, int n_loads, void* r, const void* ap, void* x,
+                                    void* p, const double* alpha, const double* rz, double* rz_new, double* beta) {
+  if (!ctx || !r || !p) return FEHOM_E_INVALID;
+  if (!ctx->built) FAIL(FEHOM_E_STATE, "fehom_pcg_precond_step before fehom_precond_build");
+  if (n_loads < 1 || n_loads > kMaxLoads) FAIL(FEHOM_E_INVALID, "fehom_pcg_precond_step: n_loads out of range");
+  if (precision != FEHOM_FP64 && precision != FEHOM_MIXED) FAIL(FEHOM_E_INVALID, "bad precision");
+  const bool init = alpha == nullptr;
+  if (!init && (!ap || !x || !rz)) FAIL(FEHOM_E_INVALID, "fehom_pcg_precond_step: ap, x and rz are needed with alpha");
+  if (!init)
+    for (int l = 0; l < n_loads; ++l)
+      if (!std::isfinite(alpha[l]) || !std::isfinite(rz[l]))
+        FAIL(FEHOM_E_INVALID, "fehom_pcg_precond_step: non-finite alpha or <r, z>");
+  const bool fp32 = precision == FEHOM_MIXED;
+  if (fp32) TRY(grow32(ctx, n_loads));
+  else TRY(grow64(ctx, n_loads));
+  TRY(op_states(ctx, n_loads, rz, alpha));
+  FftArgs f;
+  fill_dims_args(ctx, f, fp32, n_loads);
+  f.st = ctx->tune_st;
+  f.red.hist = nullptr;
+  f.init = init ? 1 : 0;
+  const int fm = init ? FX_PLAIN : FX_PCG, im = init ? FX_PCG_INIT : FX_PCG;
+  void* xi = init ? nullptr : x;
+  if (fp32) CK(precond_passes<float>(ctx, f, fm, im, r, ap, xi, p, ctx->stream));
+  else CK(precond_passes<double>(ctx, f, fm, im, r, ap, xi, p, ctx->stream));
+  std::vector<PcgState> hs;
+  TRY(op_read_states(ctx, n_loads, &hs));
+  bool bad = false;
+  for (int l = 0; l < n_loads; ++l) {
+    if (rz_new) rz_new[l] = hs[l].rz;
+    if (beta) beta[l] = init ? 0.0 : hs[l].beta;
+    bad = bad || hs[l].state == ST_BREAK;
+  }
+  if (bad) FAIL(FEHOM_E_BREAKDOWN, "fehom_pcg_precond_step: non-finite <r, z> for a load");
+  return FEHOM_OK;
+}
+
 fehom_status fehom_get_symbol_inverse(fehom_ctx* ctx, double* out) {
   if (!ctx || !out) return FEHOM_E_INVALID;
   if (!ctx->built) FAIL(FEHOM_E_STATE, "fehom_get_symbol_inverse before fehom_precond_build");
@@ -1757,9 +1852,14 @@ fehom_status fehom_mean_flux_noalloc(fehom_ctx* ctx, const double* e, const doub
                   kNoallocDoubles);
     FAIL(FEHOM_E_UNSUPPORTED_SIZE, msg);
   }
+  cudaStream_t s = ctx->stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone)
+    FAIL(FEHOM_E_STATE, "fehom_mean_flux_noalloc: the context's stream is being captured (the call copies "
+                        "between host and device and waits for the stream)");
   double* scratch = nullptr;
   TRY(noalloc_scratch(ctx, &scratch));
-  cudaStream_t s = ctx->stream;
   const int dim = ctx->d.dim, m = ctx->m;
   double Pm[6 * 9];
   flux_map_into(dim, ctx->physics, Pm);

@@ -109,6 +109,8 @@ struct StencilArgs {
   long long load_stride;  // elements between loads in x / y
   double y_scale;         // y = y_scale * D^T W C (D x + e)
   int tile_rows;          // hex8 PCG apply: node rows per tile, 8 or 16 (0 = the precision's default)
+  int narrow;             // 1: the FP32 hex8 PCG apply stages every plane entry with 4-byte copies even
+                          // where the 16-byte row copies apply (operator-level checks of both forms)
   // fused PCG reduction <x, y> -> pAp, alpha = rz / pAp (nullptr = off)
   PcgState* st;
   RedScratch red;

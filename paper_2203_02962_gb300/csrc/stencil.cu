@@ -1036,7 +1036,7 @@ cudaError_t launch_pixel_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
 // modes: PCG (x, <x, y>), STATS (residual / right-hand side with sums), plain (x and/or e)
 // every x tile full and 16-byte aligned rows: the FP32 PCG apply stages node planes with 16-byte copies
 bool hex8_wide(const StencilArgs& a) {
-  return a.d.nx % BX == 0 && a.d.nx % 4 == 0 && a.load_stride % 4 == 0 &&
+  return !a.narrow && a.d.nx % BX == 0 && a.d.nx % 4 == 0 && a.load_stride % 4 == 0 &&
          (reinterpret_cast<unsigned long long>(a.x) & 15) == 0;
 }
 

@@ -31,7 +31,7 @@ EXPORTS = ("fehom_default_options", "fehom_setup", "fehom_precond_build", "fehom
            "fehom_fft_plan", "fehom_mean_flux_noalloc", "fehom_pcg_coefficients", "fehom_eig_bounds",
            "fehom_batch_create", "fehom_solve_batch", "fehom_batch_destroy", "fehom_batch_last_error",
            "fehom_effective_energy", "fehom_set_reference", "fehom_newton_solve", "fehom_residual_update",
-           "fehom_stencil_plan", "fehom_rhs_df",
+           "fehom_stencil_plan", "fehom_rhs_df", "fehom_pcg_apply_stiffness", "fehom_pcg_precond_step",
            # include/fehom_unet.h
            "fehom_unet_create", "fehom_unet_destroy", "fehom_unet_last_error", "fehom_unet_param_count",
            "fehom_unet_set_params", "fehom_unet_get_params", "fehom_unet_predict", "fehom_unet_loss_grad",
@@ -102,6 +102,10 @@ def load_library(path: str = LIB_PATH):
     lib.fehom_stencil_plan.restype = i
     lib.fehom_rhs_df.argtypes = [vp, dp, vp]
     lib.fehom_rhs_df.restype = i
+    lib.fehom_pcg_apply_stiffness.argtypes = [vp, i, i, vp, vp, dp, i, i, dp, dp]
+    lib.fehom_pcg_apply_stiffness.restype = i
+    lib.fehom_pcg_precond_step.argtypes = [vp, i, i, vp, vp, vp, vp, dp, dp, dp, dp]
+    lib.fehom_pcg_precond_step.restype = i
     lib.fehom_apply_precond.argtypes = [vp, vp, vp, i]
     lib.fehom_apply_precond.restype = i
     lib.fehom_get_symbol_inverse.argtypes = [vp, dp]
@@ -319,6 +323,33 @@ class Solver:
         self._check(self.lib.fehom_apply_precond(self.ctx, C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr()),
                                                  PRECISION[precision]))
         return z
+
+    def pcg_apply_stiffness(self, p, rz, precision="fp64", rows=0, staging=0):
+        """Stiffness launch of a PCG iteration for a batch of loads: p [L, c, N] (device) -> (ap, <p, K p>,
+        alpha = rz / <p, K p>), with the solve's fused kernel (fehom_pcg_apply_stiffness)."""
+        torch = _torch()
+        L = p.shape[0]
+        ap = torch.empty_like(p)
+        rz = np.ascontiguousarray(np.broadcast_to(np.asarray(rz, np.float64), (L,)))
+        pap, alpha = np.zeros(L), np.zeros(L)
+        self._check(self.lib.fehom_pcg_apply_stiffness(self.ctx, PRECISION[precision], L, _ptr(p), _ptr(ap), _dptr(rz),
+                                                       int(rows), int(staging), _dptr(pap), _dptr(alpha)))
+        return ap, pap, alpha
+
+    def pcg_precond_step(self, r, p, precision="fp64", ap=None, x=None, alpha=None, rz=None):
+        """Preconditioner passes of a PCG iteration (fehom_pcg_precond_step), in place on r, x, p
+        ([L, c, N] device tensors).  Without alpha: the first apply (p = z).  Returns (rz_new, beta)."""
+        L = r.shape[0]
+        rz_new, beta = np.zeros(L), np.zeros(L)
+        al = rzp = None
+        if alpha is not None:
+            al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float64), (L,)))
+            rzp = np.ascontiguousarray(np.broadcast_to(np.asarray(rz, np.float64), (L,)))
+        self._check(self.lib.fehom_pcg_precond_step(self.ctx, PRECISION[precision], L, _ptr(r), _ptr(ap), _ptr(x),
+                                                    _ptr(p), _dptr(al) if al is not None else None,
+                                                    _dptr(rzp) if rzp is not None else None, _dptr(rz_new),
+                                                    _dptr(beta)))
+        return rz_new, beta
 
     def symbol_inverse(self):
         ne = 4 if self.elem == "p1tri4_2d" else self.c * (self.c + 1) // 2
