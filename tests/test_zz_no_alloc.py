@@ -59,3 +59,27 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     assert st == 2  # FEHOM_E_UNSUPPORTED_SIZE
     assert b"scratch" in lib.fehom_last_error(s.ctx)
     s.close()
+
+
+def test_noalloc_refuses_a_stream_under_capture():
+    """The call copies from host memory and waits for its stream, which a stream being captured into a
+    CUDA graph does not allow: it returns FEHOM_E_STATE there, and the capture still ends cleanly."""
+    import torch
+    from paper_2203_02962_gb300 import fehom, inputs
+    lib = fehom.load_library()
+    shape = (16, 24, 32)
+    ids = np.zeros(shape, np.uint8)
+    stream = torch.cuda.Stream()
+    s = fehom.Solver("hex8_3d", "scalar", shape[::-1], ids, inputs.isotropic_conductivity(1.0, 3)[None],
+                     stream=stream)
+    u = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    e = np.ones(3)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        st, _ = _call_noalloc(lib, s, e, u)
+    assert st == 7  # FEHOM_E_STATE
+    assert b"captured" in lib.fehom_last_error(s.ctx)
+    st, out = _call_noalloc(lib, s, e, u)  # outside the capture it works again
+    assert st == 0 and np.abs(out - s.mean_flux(e, u)).max() <= 1e-12 * np.abs(out).max()
+    s.close()
