@@ -557,3 +557,42 @@ def test_two_node_stencil_symbol_and_pseudo_inverse():
     b = solvers.project_mean_zero(g, rng.standard_normal(2 * g.N))
     res = solvers.pcg(lambda v: K @ v, lambda v: solvers.apply_precond(g, Kinv, v), b, 1e-12)
     assert res["iters"] == 1
+
+
+def test_lanczos_ritz_values_are_the_spectrum_after_n_steps():
+    """Sec. 4.3 (Ritz values from the CG coefficients): on a tiny SPD system A with SPD preconditioner M,
+    n = dim PCG steps span the whole space, so the eigenvalues of the CG-Lanczos tridiagonal matrix
+    equal the generalised eigenvalues of (A, M), i.e. the spectrum of M^-1 A.  A beta_j in place of
+    sqrt(beta_j) off the diagonal, or a dropped beta_{j-1} / alpha_{j-1} term, breaks the equality."""
+    import scipy.linalg as sl
+    n = 7
+    rng = np.random.default_rng(17)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(np.linspace(1.0, 9.0, n) ** 1.3) @ Q.T          # well-separated spectrum
+    M = _rand_spd(n, 18) / n
+    Minv = np.linalg.inv(M)
+    b = rng.standard_normal(n)
+    res = solvers.pcg(lambda v: A @ v, lambda v: Minv @ v, b, tol=0.0, maxiter=n)
+    assert res["iters"] == n
+    ritz = np.sort(solvers.lanczos_ritz(res["alphas"], res["betas"]))
+    exact = np.sort(sl.eigh(A, M, eigvals_only=True))
+    assert np.abs(ritz - exact).max() <= 1e-10 * exact.max()
+    # after fewer steps the Ritz values interlace inside the spectrum (Cauchy interlacing)
+    ritz3 = solvers.lanczos_ritz(res["alphas"][:3], res["betas"][:3])
+    assert exact.min() * (1 - 1e-12) <= ritz3.min() and ritz3.max() <= exact.max() * (1 + 1e-12)
+
+
+def test_mean_material_of_the_disc_cell_is_exact():
+    """Sec. 6.2 C_mean (volume mean) for the 32 x 32 disc cell: 284 of 1024 pixels have k = 10, the rest
+    k = 1, so C_mean = (1 + 9 * 284 / 1024) I = 3.49609375 I exactly in binary floating point."""
+    w = I.workload_circle2d_32()
+    g = fem.Grid((32, 32), "p1tri2_2d", "scalar")
+    assert int((w["ids"] == 1).sum()) == 284
+    Cm = fem.mean_material(g, w["ids"].ravel(), w["moduli"])
+    assert np.array_equal(Cm, 3.49609375 * np.eye(2))
+    # and for an anisotropic pair on a 3-D grid: the voxel-fraction weighted sum of the phase tensors
+    g3 = fem.Grid((4, 4, 4), "hex8_3d", "elastic")
+    ids = np.zeros(64, np.int64)
+    ids[:16] = 1
+    mod = [_rand_spd(6, 1), _rand_spd(6, 2)]
+    assert np.allclose(fem.mean_material(g3, ids, mod), 0.75 * mod[0] + 0.25 * mod[1], rtol=0, atol=1e-14)
