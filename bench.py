@@ -14,8 +14,9 @@ The mixed-precision form (FP32 stiffness/FFT in FP64 iterative refinement) is ti
 workload and reported under "mixed".  The inputs (fields of 50 MB per load and component set)
 are larger than L2, and every step rewrites them, so no L2 flush is added.
 
---impl reference runs the FP64 CPU oracle (assembled CSR + unpreconditioned CG) on a bounded
-sample of the same workload statistics on the host cores.
+--impl reference runs the FP64 CPU oracle (assembled CSR + unpreconditioned CG in C/OpenMP) to
+tolerance on a bounded sample of the same workload statistics on the host cores; --oracle-timing
+times it on the benchmark table's workloads beside the GPU solves.
 """
 from __future__ import annotations
 
@@ -479,45 +480,135 @@ def peaks_tensor():
         return 1700.0
 
 
+def _oracle_solve_loads(g, ids, mod, loads, tol, threads, which=None):
+    """The oracle's solve of K u = b for each load (assembled CSR + unpreconditioned CG in C/OpenMP,
+    stopping at ||r||_2 <= tol ||b||_2): per-load iterations and wall seconds (assembly not included),
+    and C_eff when every load was solved."""
+    from oracle import cg_native, fem, solvers
+    K = fem.assemble_K(g, ids, mod)
+    A = cg_native.CSR(K)
+    which = range(len(loads)) if which is None else which
+    its, secs, flux = [], [], []
+    for l in which:
+        b = fem.assemble_rhs(g, ids, mod, loads[l])
+        t0 = time.perf_counter()
+        x, it, _ = cg_native.cg(A, b, tol=tol, threads=threads)
+        secs.append(time.perf_counter() - t0)
+        its.append(it)
+        flux.append(fem.mean_flux(g, ids, mod, loads[l], solvers.project_mean_zero(g, x)) / (g.vp * g.N))
+    C = np.array(flux).T @ np.linalg.inv(np.asarray(loads).T) if len(flux) == len(loads) else None
+    return its, secs, C
+
+
 def cpu_baseline(short=False):
-    """The oracle (assembled CSR + unpreconditioned CG, FP64) on a bounded sample of the workload
-    statistics: a 32^3 cell with radii scaled by 1/4, 6 loads, a fixed number of CG iterations."""
-    from oracle import fem, solvers
+    """The oracle (assembled CSR + unpreconditioned CG, FP64, C/OpenMP) timed to tolerance on a bounded
+    sample of the workload: a 32^3 cell with the workload's statistics (60 periodic spheres, radii scaled
+    to 2-4 voxels, E = 100 / nu = 0.2 in E = 1 / nu = 0.3), the 6 unit Mandel strains to ||r||_2 / ||b||_2
+    <= 1e-6, on every host core; one load again on one core."""
+    from oracle import cg_native, fem
     from paper_2203_02962_gb300 import inputs
-    import scipy.sparse  # noqa: F401
 
     n = 32
-    ids = inputs.spheres3d(n, count=60, rmin=2.0, rmax=4.0, seed=0)
-    mod = np.stack([inputs.isotropic_elastic_mandel(1.0, 0.3), inputs.isotropic_elastic_mandel(100.0, 0.2)])
+    w = inputs.workload_spheres_elastic(n, seed=0, rmin=n / 16, rmax=n / 8)
     g = fem.Grid((n, n, n), "hex8_3d", "elastic")
-    K = fem.assemble_K(g, ids.ravel(), mod)
-    iters = 40 if short else 200
-    t0 = time.perf_counter()
-    total = 0
-    for e in np.eye(6):
-        b = fem.assemble_rhs(g, ids.ravel(), mod, e)
-        _, it, _ = solvers.cg(K, b, tol=1e-30, maxiter=iters)
-        total += it
-    dt = time.perf_counter() - t0
-    return {"value": g.c * g.N * total / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"32^3 elastic spheres (radii 2-4), 6 loads x {iters} unpreconditioned CG iterations "
-                      f"(scipy CSR SpMV, 1 thread), {dt:.1f} s"}
+    ids = w["ids"].ravel()
+    cores = cg_native.max_threads()
+    its, secs, _ = _oracle_solve_loads(g, ids, w["moduli"], w["loads"], 1e-6, cores)
+    its1, secs1, _ = _oracle_solve_loads(g, ids, w["moduli"], w["loads"], 1e-6, 1, which=[0])
+    dof = g.c * g.N
+    return {"value": dof * sum(its) / sum(secs), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "time_to_tol_s": sum(secs), "iterations_per_load": its,
+            "one_core": {"value": dof * its1[0] / secs1[0], "time_to_tol_s_load0": secs1[0],
+                         "iterations_load0": its1[0]},
+            "sample": f"32^3 elastic spheres (60, radii 2-4 voxels, E100/nu0.2 in E1/nu0.3), 6 unit Mandel strains, "
+                      f"assembled CSR + unpreconditioned CG (C/OpenMP) to ||r||_2/||b||_2 <= 1e-6 on {cores} threads: "
+                      f"{sum(secs):.1f} s; load 0 on 1 thread: {secs1[0]:.1f} s"}
+
+
+def oracle_timing(args):
+    """The oracle timed to tolerance on the host cores for the workloads of the benchmark table (all
+    threads, and one thread on one load), beside the GPU's FP64 and mixed solves of the same cells, with
+    the C_eff of each against a tight FP64 GPU solve (tol 1e-10).  Workloads: the 32 x 32 P1 disc
+    (2 loads, tol 1e-8); 64^3 elastic spheres standing in for the 128^3 cell (radii 4-8 voxels, 6 loads,
+    tol 1e-6; the assembled 128^3 matrix has 0.5 G entries); 64^3 thresholded GRF conductivity with
+    contrast 1000 (correlation length n/32 voxels, 3 loads, tol 1e-6).  The oracle stops on
+    ||r||_2 / ||b||_2, the GPU on the K_ref^-1 norm of the residual."""
+    import torch
+    from oracle import cg_native, fem
+    from paper_2203_02962_gb300 import fehom, inputs
+    cores = cg_native.max_threads()
+    cells = []
+    w = inputs.workload_circle2d_32()
+    cells.append(("32^2 P1 disc, k 10 in 1, 2 loads, tol 1e-8", (32, 32), w["elem"],
+                  "scalar", w["ids"], w["moduli"], w["loads"], 1e-8))
+    w = inputs.workload_spheres_elastic(64, seed=0, rmin=4.0, rmax=8.0)
+    cells.append(("64^3 hex8 elastic spheres (proxy of the 128^3 cell), 6 loads, tol 1e-6", (64, 64, 64), "hex8_3d",
+                  "elastic", w["ids"], w["moduli"], w["loads"], 1e-6))
+    w = inputs.workload_grf_scalar(64, seed=0, ell=2.0)
+    cells.append(("64^3 hex8 scalar GRF, contrast 1000, 3 loads, tol 1e-6", (64, 64, 64), "hex8_3d", "scalar",
+                   w["ids"], w["moduli"], w["loads"], 1e-6))
+    rows = []
+    for name, shape, elem, phys, ids, mod, loads, tol in cells:
+        g = fem.Grid(shape, elem, phys)
+        idf = np.ascontiguousarray(ids).ravel()
+        its, secs, C_or = _oracle_solve_loads(g, idf, mod, loads, tol, cores)
+        its1, secs1, _ = _oracle_solve_loads(g, idf, mod, loads, tol, 1, which=[0])
+        n_xyz = tuple(shape[::-1]) + (1,) * (3 - len(shape))
+        gpu = {}
+        for prec, t in (("ref", 1e-10), ("fp64", tol), ("mixed", tol)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s = fehom.Solver(elem, phys, n_xyz, ids, mod, precision="fp64" if prec == "ref" else prec)
+            s.precond_build()
+            out = s.solve(loads, tol=t, fields=None)
+            torch.cuda.synchronize()
+            gpu[prec] = (time.perf_counter() - t0, out["C_eff"], [i["iterations"] for i in out["info"]])
+            s.close()
+        Cr = gpu["ref"][1]
+        err = lambda C: float(np.abs(C - Cr).max() / np.abs(Cr).max())  # noqa: E731
+        rows.append({"workload": name, "dof": g.c * g.N,
+                     "oracle_all_cores": {"threads": cores, "time_to_tol_s": sum(secs), "iterations": its,
+                                          "C_eff_rel_err": err(C_or)},
+                     "oracle_one_core": {"threads": 1, "time_to_tol_s_load0": secs1[0], "iterations_load0": its1[0]},
+                     "gpu_fp64": {"wall_s_setup_build_solve": gpu["fp64"][0], "iterations": gpu["fp64"][2],
+                                  "C_eff_rel_err": err(gpu["fp64"][1])},
+                     "gpu_mixed": {"wall_s_setup_build_solve": gpu["mixed"][0], "inner_iterations": gpu["mixed"][2],
+                                   "C_eff_rel_err": err(gpu["mixed"][1])}})
+        print(json.dumps(rows[-1]), flush=True)
+    host = {"cores": os.cpu_count(), "machine": os.uname().machine}
+    print(json.dumps({"oracle_timing": rows, "host": host}))
 
 
 def run_reference(args):
+    """The oracle arm: each step solves one load of the 32^3 sample (cpu_baseline's cell, loads in turn)
+    to tolerance on every host core; value = DOF*iter/s over the timed steps."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    vals = []
-    for _ in range(args.warmup):
-        cpu_baseline(short=True)
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(short=True))
-    v = statistics.median(x["value"] for x in vals)
+    from oracle import cg_native, fem
+    from paper_2203_02962_gb300 import inputs
+    n = 32
+    w = inputs.workload_spheres_elastic(n, seed=0, rmin=n / 16, rmax=n / 8)
+    g = fem.Grid((n, n, n), "hex8_3d", "elastic")
+    ids = w["ids"].ravel()
+    K = cg_native.CSR(fem.assemble_K(g, ids, w["moduli"]))
+    rhs = [fem.assemble_rhs(g, ids, w["moduli"], e) for e in w["loads"]]
+    cores = cg_native.max_threads()
+    for k in range(args.warmup):
+        cg_native.cg(K, rhs[k % 6], tol=1e-6, threads=cores)
+    its, t0 = 0, time.perf_counter()
+    for k in range(args.steps):
+        its += cg_native.cg(K, rhs[k % 6], tol=1e-6, threads=cores)[1]
+    dt = time.perf_counter() - t0
+    v = g.c * g.N * its / dt
+    sample = (f"32^3 elastic spheres (60, radii 2-4 voxels), one unit Mandel strain per step, assembled CSR + "
+              f"unpreconditioned CG (C/OpenMP, {cores} threads) to ||r||_2/||b||_2 <= 1e-6; {args.steps} steps "
+              f"in {dt:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "oracle sample: 32^3 elastic spheres, 6 loads, CG"},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[-1]["sample"], "value": v},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "oracle sample: 32^3 elastic spheres, one load per step, CG to 1e-6"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": v},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -550,7 +641,12 @@ def main():
     ap.add_argument("--ncu-case", default=None, choices=["fp64", "mixed", "unet"],
                     help="run one untimed solve of the workload (for ncu kernel captures) and exit")
     ap.add_argument("--ncu-loads", type=int, default=6, help="loads of the --ncu-case solve (1-6)")
+    ap.add_argument("--oracle-timing", action="store_true",
+                    help="time the oracle to tolerance on the host cores beside the GPU solves, then exit")
     args = ap.parse_args()
+    if args.oracle_timing:
+        oracle_timing(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
