@@ -96,8 +96,11 @@ typedef struct {
                         isotropic phases on cubic voxels; see fehom_residual_update); 0 always recomputes
                         b - K x with the FP64 stiffness */
   int stencil_rows;  /* FEHOM_HEX8_3D PCG stiffness apply: node rows per tile (tiles are 32 x rows nodes), 8 or
-                        16; 0 (default) the stencil tuner times both on the first solve of a batch size and
-                        keeps the faster (with autotune = 0: 16 for FP64, 8 for FP32); see fehom_stencil_plan */
+                        16 (FP32: node planes staged by cp.async copies); 0 (default) the stencil tuner times
+                        both heights, and for FP32 both node-plane stagings (cp.async copies or one Tensor
+                        Memory Accelerator box per plane), on the first solve of a batch size and keeps the
+                        fastest (with autotune = 0: 16 rows for FP64, 8 for FP32, cp.async); see
+                        fehom_stencil_plan */
 } fehom_options;
 
 /* Kernel classes of one PCG iteration, for fehom_kernel_times. */
@@ -240,9 +243,11 @@ fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int
                             int* xy_fused);
 
 /* Stencil plan of the PCG stiffness apply of one precision (FEHOM_HEX8_3D): *rows = the node rows per
-   tile in use (8 or 16); ms[2] = the tuner's timings of one apply with 8 and 16 rows (0 if not timed,
-   -1 if the candidate failed to launch).  Either output may be NULL. */
-fehom_status fehom_stencil_plan(const fehom_ctx* ctx, int precision, int* rows, double* ms);
+   tile in use (8 or 16); *staging = the FP32 node-plane staging in use (0 cp.async copies, 3 one Tensor
+   Memory Accelerator box per plane); ms[4] = the tuner's timings of one apply with 8 and 16 rows with
+   cp.async staging, then with TMA staging (0 if not timed, -1 if the candidate failed to launch).  Any
+   output may be NULL. */
+fehom_status fehom_stencil_plan(const fehom_ctx* ctx, int precision, int* rows, int* staging, double* ms);
 
 /* Replaces the reference material (Sec. 4.1, Eq. Kref; m x m, host, symmetric positive definite) of
  * the context, e.g. when the tangent of a nonlinear problem changes (the reassembly of Sec. 5 before
@@ -340,8 +345,11 @@ fehom_status fehom_apply_precond(fehom_ctx* ctx, const void* r, void* z, int pre
  * alpha = rz / <p, K p> formed on the device.
  *   rz       <r, z> of each load (the numerator of alpha).
  *   rows     FEHOM_HEX8_3D: node rows per tile, 8 or 16 (0 = the context's plan); ignored otherwise.
- *   staging  FEHOM_HEX8_3D FP32: 0 = the solve's choice (16-byte row copies of the node planes when every
- *            x tile is full and the rows are 16-byte aligned), 1 = 4-byte copies of every plane entry.
+ *   staging  FEHOM_HEX8_3D FP32 node-plane staging: 0 = the context's plan (the stencil tuner's pick, else
+ *            cp.async copies); 1 = 4-byte cp.async copies of every entry; 2 = 16-byte cp.async row copies
+ *            (n_x a multiple of 32, rows 16-byte aligned); 3 = one Tensor Memory Accelerator box per plane,
+ *            issued by one thread, with mbarrier completion (same condition).  A staging that does not apply
+ *            to the context returns FEHOM_E_UNSUPPORTED_SIZE.
  *   pAp, alpha  NULL or host outputs.
  * Errors: FEHOM_E_INVALID, FEHOM_E_BREAKDOWN (<p, K p> not positive and finite for some load; outputs
  * still written), FEHOM_E_CUDA. */

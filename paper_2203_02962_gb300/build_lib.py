@@ -15,7 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfehom.so")
-SOURCES = ["stencil.cu", "fft.cu", "vec.cu", "api.cu", "unet.cu", "newton.cu"]
+SOURCES = ["stencil.cu", "tma_host.cu", "fft.cu", "vec.cu", "api.cu", "unet.cu", "newton.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -38,7 +38,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     """Compile and link libfehom.so; returns its path.  Raises RuntimeError on a compiler error."""
     nvcc = _nvcc()
     os.makedirs(OUT, exist_ok=True)
-    headers = [os.path.join(SRC, "fehom_internal.cuh"),
+    headers = [os.path.join(SRC, "fehom_internal.cuh"), os.path.join(SRC, "tma.cuh"),
                os.path.join(os.path.dirname(PKG), "include", "fehom.h"),
                os.path.join(os.path.dirname(PKG), "include", "fehom_unet.h")]
     jobs = []

@@ -78,8 +78,9 @@ struct fehom_ctx {
   } plan[2];                   // [0] FP64 kernels, [1] FP32 kernels
   struct StencilPlan {
     int rows = 0;         // hex8 PCG apply: node rows per tile (0 = the precision's default)
+    int staging = 0;      // FP32 node-plane staging: 0 cp.async copies, 3 tensor-memory-accelerator boxes
     int tuned_loads = 0;
-    double ms[2] = {0, 0};  // timed candidates: 8 and 16 rows
+    double ms[4] = {0, 0, 0, 0};  // timed candidates: 8 / 16 rows with cp.async, 8 / 16 rows with TMA
   } stencil[2];               // [0] FP64 kernels, [1] FP32 kernels
   PcgState* tune_st = nullptr;  // running states for the stencil tuner's PCG-apply launches
   double kms[2][FEHOM_K_COUNT] = {{0}};
@@ -324,6 +325,7 @@ StencilArgs stencil_args(fehom_ctx* ctx, bool fp32, int n_loads) {
   a.st = nullptr;
   a.red = ctx->red;
   a.tile_rows = ctx->stencil[fp32 ? 1 : 0].rows;
+  a.staging = ctx->stencil[fp32 ? 1 : 0].staging;
   return a;
 }
 
@@ -623,17 +625,20 @@ fehom_status autotune_fft(fehom_ctx* ctx, int n_loads) {
   return FEHOM_OK;
 }
 
-// Stencil tuner: times the hex8 PCG stiffness apply with 8- and 16-row tiles (both precisions) on the
-// solve's buffers, for the batch size of the solve, and keeps the faster; option stencil_rows (8 or 16)
-// fixes the choice.  The launches use running scratch states, not the solve's.
+// Stencil tuner: times the hex8 PCG stiffness apply with 8- and 16-row tiles (both precisions), and for
+// the FP32 kernels on full x tiles with both node-plane stagings (cp.async copies by every thread, or one
+// tensor-memory-accelerator box per plane), on the solve's buffers for the batch size of the solve, and
+// keeps the fastest; option stencil_rows (8 or 16) fixes the height (cp.async staging).  The launches
+// use running scratch states, not the solve's.
 template <typename T>
 fehom_status autotune_stencil(fehom_ctx* ctx, int n_loads) {
   const int prec = sizeof(T) == 4 ? 1 : 0;
   auto& sp = ctx->stencil[prec];
   if (ctx->d.elem != HEX8_3D) return FEHOM_OK;
   if (ctx->opt.stencil_rows == 8 || ctx->opt.stencil_rows == 16) {
-    if (sp.rows != ctx->opt.stencil_rows) ctx->graph_key[0] = 0;
+    if (sp.rows != ctx->opt.stencil_rows || sp.staging != 0) ctx->graph_key[0] = 0;
     sp.rows = ctx->opt.stencil_rows;
+    sp.staging = 0;
     sp.tuned_loads = n_loads;
     return FEHOM_OK;
   }
@@ -643,7 +648,7 @@ fehom_status autotune_stencil(fehom_ctx* ctx, int n_loads) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     const auto it = g_stencil_plans.find(key);
     if (it != g_stencil_plans.end()) {
-      if (sp.rows != it->second.rows) ctx->graph_key[0] = 0;
+      if (sp.rows != it->second.rows || sp.staging != it->second.staging) ctx->graph_key[0] = 0;
       sp = it->second;
       return FEHOM_OK;
     }
@@ -669,15 +674,18 @@ fehom_status autotune_stencil(fehom_ctx* ctx, int n_loads) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   double best = 1e30;
-  int rows_best = 0;
-  for (int ci = 0; ci < 2; ++ci) {
-    const int rows = ci == 0 ? 8 : 16;
+  int rows_best = 0, staging_best = 0;
+  for (int ci = 0; ci < 4; ++ci) {
+    const int rows = (ci & 1) ? 16 : 8, staging = ci < 2 ? 0 : 3;
+    sp.ms[ci] = 0.0;
+    if (staging == 3 && prec == 0) continue;  // the FP64 kernels stage nothing
     StencilArgs a = stencil_args(ctx, prec == 1, n_loads);
     a.x = pin;
     a.y = pout;
     a.st = ctx->tune_st;
     a.red.hist = nullptr;
     a.tile_rows = rows;
+    a.staging = staging;
     CK(cudaMemcpyAsync(ctx->tune_st, hs.data(), sizeof(PcgState) * n_loads, cudaMemcpyHostToDevice, s));
     double ms = -1.0;
     if (launch_stiffness<T>(a, s) == cudaSuccess) {
@@ -693,12 +701,14 @@ fehom_status autotune_stencil(fehom_ctx* ctx, int n_loads) {
     if (ms > 0 && ms < best) {
       best = ms;
       rows_best = rows;
+      staging_best = staging;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rows_best == 0) FAIL(FEHOM_E_CUDA, "stencil tuner: no candidate ran");
   sp.rows = rows_best;
+  sp.staging = staging_best;
   sp.tuned_loads = n_loads;
   ctx->graph_key[0] = 0;  // captured iterations used the previous tile
   {
@@ -712,7 +722,8 @@ template <typename T>
 fehom_status run_iterations(fehom_ctx* ctx, int n_loads, T* x, T* r, T* p, T* ap, int max_iter,
                             std::vector<PcgState>& hs) {
   cudaStream_t s = ctx->stream;
-  const long long key[8] = {(ctx->opt.profile ? 2 : 1) + 4 * ctx->stencil[sizeof(T) == 4 ? 1 : 0].rows, (long long)n_loads, (long long)(size_t)x, (long long)(size_t)r, (long long)(size_t)p,
+  const auto& spl = ctx->stencil[sizeof(T) == 4 ? 1 : 0];
+  const long long key[8] = {(ctx->opt.profile ? 2 : 1) + 4 * spl.rows + 1024 * spl.staging, (long long)n_loads, (long long)(size_t)x, (long long)(size_t)r, (long long)(size_t)p,
                             (long long)(size_t)ap, (long long)sizeof(T), (long long)(size_t)ctx->st};
   const bool prof = ctx->opt.profile != 0;
   if (prof) TRY(make_events(ctx));
@@ -1114,12 +1125,13 @@ fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int
   return FEHOM_OK;
 }
 
-fehom_status fehom_stencil_plan(const fehom_ctx* ctx, int precision, int* rows, double* ms) {
+fehom_status fehom_stencil_plan(const fehom_ctx* ctx, int precision, int* rows, int* staging, double* ms) {
   if (!ctx) return FEHOM_E_INVALID;
   const auto& sp = ctx->stencil[precision == FEHOM_MIXED ? 1 : 0];
   if (rows) *rows = sp.rows != 0 ? sp.rows : (precision == FEHOM_MIXED ? 8 : 16);
+  if (staging) *staging = sp.staging;
   if (ms)
-    for (int i = 0; i < 2; ++i) ms[i] = sp.ms[i];
+    for (int i = 0; i < 4; ++i) ms[i] = sp.ms[i];
   return FEHOM_OK;
 }
 
@@ -1764,7 +1776,7 @@ fehom_status fehom_pcg_apply_stiffness(fehom_ctx* ctx, int precision, int n_load
   if (!ctx || !p || !ap || !rz) return FEHOM_E_INVALID;
   if (n_loads < 1 || n_loads > kMaxLoads) FAIL(FEHOM_E_INVALID, "fehom_pcg_apply_stiffness: n_loads out of range");
   if (rows != 0 && rows != 8 && rows != 16) FAIL(FEHOM_E_INVALID, "fehom_pcg_apply_stiffness: rows must be 0, 8 or 16");
-  if (staging != 0 && staging != 1) FAIL(FEHOM_E_INVALID, "fehom_pcg_apply_stiffness: staging must be 0 or 1");
+  if (staging < 0 || staging > 3) FAIL(FEHOM_E_INVALID, "fehom_pcg_apply_stiffness: staging must be 0..3");
   if (precision != FEHOM_FP64 && precision != FEHOM_MIXED) FAIL(FEHOM_E_INVALID, "bad precision");
   for (int l = 0; l < n_loads; ++l)
     if (!std::isfinite(rz[l])) FAIL(FEHOM_E_INVALID, "fehom_pcg_apply_stiffness: non-finite <r, z>");
@@ -1776,9 +1788,11 @@ fehom_status fehom_pcg_apply_stiffness(fehom_ctx* ctx, int precision, int n_load
   a.st = ctx->tune_st;
   a.red.hist = nullptr;
   if (rows) a.tile_rows = rows;
-  a.narrow = staging;
-  if (fp32) CK(launch_stiffness<float>(a, ctx->stream));
-  else CK(launch_stiffness<double>(a, ctx->stream));
+  if (staging != 0) a.staging = staging;  // 0: the context's plan
+  const cudaError_t le = fp32 ? launch_stiffness<float>(a, ctx->stream) : launch_stiffness<double>(a, ctx->stream);
+  if (le == cudaErrorInvalidValue && staging != 0)
+    FAIL(FEHOM_E_UNSUPPORTED_SIZE, "fehom_pcg_apply_stiffness: this staging / tile height is not available here");
+  CK(le);
   count_launch(ctx);
   std::vector<PcgState> hs;
   TRY(op_read_states(ctx, n_loads, &hs));
@@ -1787,6 +1801,7 @@ fehom_status fehom_pcg_apply_stiffness(fehom_ctx* ctx, int precision, int n_load
     if (pAp) pAp[l] = hs[l].pAp;
     if (alpha) alpha[l] = hs[l].alpha;
     broke = broke || hs[l].state == ST_BREAK;
+    if (hs[l].err) FAIL(FEHOM_E_CUDA, "fehom_pcg_apply_stiffness: a bounded wait of the kernel gave up");
   }
   if (broke) FAIL(FEHOM_E_BREAKDOWN, "fehom_pcg_apply_stiffness: <p, K p> not positive and finite for a load");
   return FEHOM_OK;

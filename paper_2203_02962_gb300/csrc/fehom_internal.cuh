@@ -40,7 +40,7 @@ struct PcgState {
   int state;       // see ST_*
   int iter;
   int max_iter;
-  int pad;
+  int err;         // nonzero: a kernel gave up a bounded wait for this load (state is ST_BREAK)
 };
 
 // RUN: iterating; CONV / FIN_MAX: converged / out of iterations, finishing the current iteration
@@ -85,6 +85,29 @@ template <> struct DotAcc<float> {
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// The same accumulation for the real and imaginary parts of complex FP32 products at once, in packed
+// FP32x2 instructions (Blackwell FADD2 / FMUL2 / FFMA2, each rounding exactly like the scalar operation):
+// add(a, b) accumulates a.x b.x and a.y b.y.
+struct DotAcc2 {
+  float2 s = make_float2(0.0f, 0.0f), c = make_float2(0.0f, 0.0f);
+  __device__ __forceinline__ void add(float2 a, float2 b) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 p = __fmul2_rn(a, b);
+    const float2 t = __fadd2_rn(s, p);
+    const float2 z = __ffma2_rn(s, m1, t);                                            // t - s
+    const float2 e = __fadd2_rn(__ffma2_rn(__ffma2_rn(z, m1, t), m1, s), __ffma2_rn(z, m1, p));  // TwoSum error
+    c = __fadd2_rn(c, __fadd2_rn(e, __ffma2_rn(a, b, __fmul2_rn(p, m1))));            // + the product tails
+    s = t;
+  }
+  __device__ __forceinline__ void scale2() {  // exact
+    s = __fadd2_rn(s, s);
+    c = __fadd2_rn(c, c);
+  }
+  __device__ __forceinline__ double value() const {
+    return ((double)s.x + (double)c.x) + ((double)s.y + (double)c.y);
+  }
+};
+
 // ------------------------------------------------------------------------------------------------
 // stencil.cu
 // ------------------------------------------------------------------------------------------------
@@ -109,8 +132,10 @@ struct StencilArgs {
   long long load_stride;  // elements between loads in x / y
   double y_scale;         // y = y_scale * D^T W C (D x + e)
   int tile_rows;          // hex8 PCG apply: node rows per tile, 8 or 16 (0 = the precision's default)
-  int narrow;             // 1: the FP32 hex8 PCG apply stages every plane entry with 4-byte copies even
-                          // where the 16-byte row copies apply (operator-level checks of both forms)
+  int staging;            // FP32 hex8 PCG apply, node-plane staging: 0 = cp.async copies (16-byte row copies
+                          // where every x tile is full, else 4-byte), 1 = 4-byte cp.async copies, 2 = 16-byte
+                          // row copies, 3 = one tensor-memory-accelerator box per plane (2 and 3: every x
+                          // tile full, else refused)
   // fused PCG reduction <x, y> -> pAp, alpha = rz / pAp (nullptr = off)
   PcgState* st;
   RedScratch red;

@@ -37,6 +37,11 @@ template <> struct V2<float> { using t = float2; };
 template <typename C> __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) { C r; r.x = a; r.y = b; return r; }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+// FP32 complex additions as one packed FP32x2 instruction each (a - b as fma(b, -1, a): the same rounding)
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
   return mk<C>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
@@ -952,7 +957,7 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_la
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
-  DotAcc<float> dot;
+  DotAcc2 dot;
   const bool active = tid < 256;
   const int t = tid & 15, k1 = (tid >> 4) & 15;
   const int cf = cf0 + t;
@@ -975,21 +980,22 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_la
       float2 r[NC], z[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) r[c] = zr[c][k2];
+      // z = K_hat^+ r with a real symmetric block: each entry scales the real and imaginary parts alike,
+      // so the complex products are packed FP32x2 operations with the entry in both halves
+      auto kk = [](float k) { return make_float2(k, k); };
       if constexpr (NC == 1) {
-        const float k00 = ks[0];
-        z[0] = make_float2(k00 * r[0].x, k00 * r[0].y);
+        z[0] = __fmul2_rn(kk(ks[0]), r[0]);
       } else {
         constexpr int E = 128 * TCL;
-        const float k00 = ks[0], k11 = ks[E], k22 = ks[2 * E];
-        const float k12 = ks[3 * E], k02 = ks[4 * E], k01 = ks[5 * E];
-        z[0] = make_float2(fmaf(k00, r[0].x, fmaf(k01, r[1].x, k02 * r[2].x)), fmaf(k00, r[0].y, fmaf(k01, r[1].y, k02 * r[2].y)));
-        z[1] = make_float2(fmaf(k01, r[0].x, fmaf(k11, r[1].x, k12 * r[2].x)), fmaf(k01, r[0].y, fmaf(k11, r[1].y, k12 * r[2].y)));
-        z[2] = make_float2(fmaf(k02, r[0].x, fmaf(k12, r[1].x, k22 * r[2].x)), fmaf(k02, r[0].y, fmaf(k12, r[1].y, k22 * r[2].y)));
+        const float2 k00 = kk(ks[0]), k11 = kk(ks[E]), k22 = kk(ks[2 * E]);
+        const float2 k12 = kk(ks[3 * E]), k02 = kk(ks[4 * E]), k01 = kk(ks[5 * E]);
+        z[0] = __ffma2_rn(k00, r[0], __ffma2_rn(k01, r[1], __fmul2_rn(k02, r[2])));
+        z[1] = __ffma2_rn(k01, r[0], __ffma2_rn(k11, r[1], __fmul2_rn(k12, r[2])));
+        z[2] = __ffma2_rn(k02, r[0], __ffma2_rn(k12, r[1], __fmul2_rn(k22, r[2])));
       }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        dot.add(r[c].x, z[c].x);  // the column's Parseval weight is applied to the thread's sum below
-        dot.add(r[c].y, z[c].y);
+        dot.add(r[c], z[c]);  // the column's Parseval weight is applied to the thread's sum below
         zr[c][k2] = z[c];
       }
     }

@@ -25,6 +25,7 @@
 // complete its node plane (the four top corners are carried to the next layer in registers).
 // No atomics; fixed summation order.
 #include "fehom_internal.cuh"
+#include "tma.cuh"
 
 #include <algorithm>
 #include <cstdio>
@@ -335,26 +336,46 @@ constexpr int kRing = 5;  // RAW: staged node planes k .. k + 4
 // RAW elasticity packs the corner forces of an element as one float4 per corner (3 components + pad)
 template <typename T, int C, bool HAS_X>
 __host__ __device__ constexpr bool hex8_pack() { return hex8_raw<T, C, HAS_X>() && C == 3; }
-template <typename T, int C, bool HAS_X, int BYT>
+// staging of the RAW kernels' node planes: STG_CP4 4-byte cp.async copies of every entry (any grid),
+// STG_CP16 16-byte cp.async row copies (every x tile full), STG_TMA one tensor-memory-accelerator box per
+// plane issued by one thread, completion on an mbarrier per ring slot (every x tile full)
+enum { STG_CP4 = 0, STG_CP16 = 1, STG_TMA = 2 };
+// ring slot stride in elements: TMA destinations sit on 128-byte boundaries
+template <typename T, int C, int BYT, int STG>
+__host__ __device__ constexpr int hex8_slot_elems() {
+  constexpr int e = C * Hex8Tile<T, BYT>::RPLANE;
+  return STG == STG_TMA ? (int)((e * sizeof(T) + 127) / 128 * 128 / sizeof(T)) : e;
+}
+constexpr int kTmaHdr = 128;  // bytes before the TMA ring: one mbarrier per slot
+template <typename T, int C, bool HAS_X, int BYT, int STG = STG_CP4>
 __host__ __device__ constexpr size_t hex8_smem_elems() {
   using TL = Hex8Tile<T, BYT>;
   return hex8_raw<T, C, HAS_X>()
-             ? (size_t)kRing * C * TL::RPLANE + 2 * 4 * (hex8_pack<T, C, HAS_X>() ? 4 : C) * TL::NE
+             ? (size_t)kRing * hex8_slot_elems<T, C, BYT, STG>() +
+                   2 * 4 * (hex8_pack<T, C, HAS_X>() ? 4 : C) * TL::NE +
+                   (STG == STG_TMA ? (kTmaHdr + 128) / sizeof(T) : 0)
              : (size_t)2 * 4 * C * TL::NE + 2 * 4 * C * TL::NE;
 }
 
-template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED, int BYT, bool WIDE = false>
+template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED, int BYT, int STG = STG_CP4>
 __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM)
-    hex8_apply_kernel(StencilArgs a, int kz_per_cta) {
+    hex8_apply_kernel(const __grid_constant__ CUtensorMap tmap, StencilArgs a, int kz_per_cta) {
   constexpr bool RAW = hex8_raw<T, C, HAS_X>();
   constexpr bool PACK = hex8_pack<T, C, HAS_X>();
+  constexpr bool WIDE = STG != STG_CP4;
+  constexpr bool TMA = RAW && STG == STG_TMA;
   constexpr int BY = BYT, NE = Hex8Tile<T, BYT>::NE, NT = Hex8Tile<T, BYT>::NT;
   constexpr int RPLANE = Hex8Tile<T, BYT>::RPLANE;
+  constexpr int SLOTE = hex8_slot_elems<T, C, BYT, STG>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* FB = reinterpret_cast<T*>(smem_raw);  // [2 planes][4][C][NE] face butterflies (not RAW)
-  T* RW = reinterpret_cast<T*>(smem_raw);  // [kRing slots][C][BY + 2][RP] staged node planes (RAW)
+  // TMA: a 128-byte aligned base (the launch adds 128 bytes of slack), one mbarrier per ring slot first
+  unsigned char* smem_base =
+      TMA ? smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u) : smem_raw;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_base);
+  T* FB = reinterpret_cast<T*>(smem_base);  // [2 planes][4][C][NE] face butterflies (not RAW)
+  T* RW = reinterpret_cast<T*>(smem_base + (TMA ? kTmaHdr : 0));  // [kRing slots][C][BY + 2][RP] staged planes (RAW)
   // [4 corners][C][NE] face contributions to plane k; without RAW two of them, by the parity of k
-  T* FC0 = RAW ? RW + kRing * C * RPLANE : FB + 2 * 4 * C * NE;
+  T* FC0 = RAW ? RW + kRing * SLOTE : FB + 2 * 4 * C * NE;
   __shared__ double red_sh[32];
 
   const Dims d = a.d;
@@ -429,13 +450,46 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
   // 16-byte copies of the interior, one task per thread.  Otherwise every staged entry is a 4-byte copy
   // with periodic wrap (this thread: entries tid + q NT of the padded plane; pad columns skipped).
   // Source offsets are fixed per CTA.
+  // TMA: one box (x = i0 - 4 .. i0 + 35, rows j0 - 1 .. j0 + BY, the C components of the load) per plane,
+  // issued by thread 0; the box reads zeros outside the grid, so at the periodic seams the halo entries
+  // the wrap needs are patched by one load per thread (fetched a plane ahead) after the box has landed.
+  // A plane is read only after a CTA barrier that follows thread 0's wait (acquire) on its mbarrier.
   constexpr int NROW = C * (BY + 2);  // staged rows per plane
-  constexpr int NSTAGE = WIDE ? 1 : (C * RPLANE + NT - 1) / NT;
+  constexpr int NSTAGE = (WIDE || TMA) ? 1 : (C * RPLANE + NT - 1) / NT;
   int soff[NSTAGE], doff = 0;
   bool w16 = false;
 #pragma unroll
   for (int q = 0; q < NSTAGE; ++q) soff[q] = -1;
-  if constexpr (RAW && WIDE) {
+  // TMA: per slot, the parity of its next phase and whether it was ever used (thread 0 keeps them in
+  // shared memory: they are only needed to drain the ring after a failed wait)
+  [[maybe_unused]] unsigned* tma_book = reinterpret_cast<unsigned*>(full + kRing);
+  // TMA seam patch of this thread (staged entry and source offset from x), or dst < 0; recomputed where it
+  // is used instead of held in registers across the layer loop
+  [[maybe_unused]] auto seam_entry = [&](int& dst, unsigned& off) {
+    const bool ls = i0 == 0, rs = i0 + BX == d.nx, ts = j0 == 0;
+    const int rb = d.ny - j0 + 1;  // staged row of y = ny
+    const bool bs = rb <= BY + 1;
+    const int nl = ls ? C * (BY + 2) : 0, nr = rs ? C * (BY + 2) : 0;
+    const int nt = ts ? C * (BX + 2) : 0, nb = bs ? C * (BX + 2) : 0;
+    int e = tid, r = -1, j = 0, col = 0;  // col: staged column relative to RX0 (0 = x i0 - 1)
+    if (e < nl) {
+      r = e / C; j = e % C; col = 0;
+    } else if ((e -= nl) < nr) {
+      r = e / C; j = e % C; col = BX + 1;
+    } else if ((e -= nr) < nt) {
+      r = 0; j = e / (BX + 2); col = e % (BX + 2);
+    } else if ((e -= nt) < nb) {
+      r = rb; j = e / (BX + 2); col = e % (BX + 2);
+    }
+    dst = -1;
+    if (r >= 0) {
+      dst = j * RPLANE + r * RP + RX0 + col;
+      off = (unsigned)((long long)j * d.N + (long long)wrap(j0 - 1 + r, d.ny) * d.nx + wrap(i0 - 1 + col, d.nx));
+    }
+  };
+  // the CTA touches a periodic seam (then some of its threads patch entries after each box lands)
+  [[maybe_unused]] const bool seam_cta = i0 == 0 || i0 + BX == d.nx || j0 == 0 || d.ny - j0 + 1 <= BY + 1;
+  if constexpr (RAW && WIDE && !TMA) {
     if (tid < NROW * 10) {
       const int row = tid / 10, q = tid - row * 10, j = row / (BY + 2), r = row - j * (BY + 2);
       const int col = q == 0 ? 0 : (q == 9 ? BX + 1 : 1 + 4 * (q - 1));  // column relative to RX0
@@ -454,7 +508,16 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
     }
   }
   auto stage_plane = [&](int slot, int kz) {
-    if constexpr (RAW) {
+    if constexpr (TMA) {
+      if (tid == 0) {
+        tma::fence_proxy_async();
+        tma::mbar_expect_tx(&full[slot], (unsigned)(sizeof(T) * C * RPLANE));
+        tma::load_4d(RW + slot * SLOTE, &tmap, i0 - 4, j0 - 1, load * C, kz, &full[slot]);
+        tma_book[0] ^= 1u << slot;
+        tma_book[1] |= 1u << slot;
+      }
+      return;
+    } else if constexpr (RAW) {
       const T* xk = x + (long long)kz * plane;
       T* dst = RW + slot * C * RPLANE;
       if constexpr (WIDE) {
@@ -472,7 +535,7 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
   };
   // RAW: butterflies (ss, sd, ds, dd) of this thread's face in staged slot `slot`
   auto raw_face = [&](int slot, T (&f)[C][4]) {
-    const T* src = RW + slot * C * RPLANE + ej * RP + RX0 + ei;
+    const T* src = RW + slot * SLOTE + ej * RP + RX0 + ei;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
       const T* sj = src + j * RPLANE;
@@ -489,7 +552,23 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
   // B + C for element layer k (planes k: slot CUR, k + 1: slot CUR ^ 1); kzc = wrap(k).  RAW: plane k
   // sits in ring slot s0 = (k - k0 + 1) mod kRing and plane k + 4 (kz4 = wrap(k + 4)) goes to the slot
   // before it; both are carried from layer to layer instead of recomputed (no integer division)
-  auto layer = [&](auto cur_c, int k, int kzc, [[maybe_unused]] int s0, [[maybe_unused]] int kz4) {
+  // TMA: a wait that gave up (about a second) ends the launch for the whole CTA at the next barrier
+  [[maybe_unused]] bool timeout = false;
+  [[maybe_unused]] T fv = T(0);                      // seam patch of the next plane to patch
+  // the seam patch of plane p for this thread (0 when it has none)
+  [[maybe_unused]] auto fetch = [&](int p) -> T {
+    if constexpr (TMA) {
+      if (!seam_cta) return T(0);
+      int dst;
+      unsigned off = 0u;
+      seam_entry(dst, off);
+      return dst >= 0 ? __ldg(x + off + (long long)wrap(p, d.nz) * plane) : T(0);
+    } else {
+      return T(0);
+    }
+  };
+
+  auto layer = [&](auto cur_c, int k, int kzc, [[maybe_unused]] int s0, [[maybe_unused]] int kz4) -> bool {
     [[maybe_unused]] constexpr int CUR = decltype(cur_c)::value;
     [[maybe_unused]] const int s1 = s0 == kRing - 1 ? 0 : s0 + 1;
     // the face butterflies are private to their thread, and the corner buffer FC alternates with
@@ -558,12 +637,34 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
       }
     }
     // RAW: this thread's copies of plane k + 2 (issued three layers ago) have landed; the barrier
-    // makes them visible for element layer k + 1 and frees the slot of plane k - 1
-    if constexpr (RAW) cp_async_wait_group<1>();
-    __syncthreads();
-    if constexpr (RAW) {
+    // makes them visible for element layer k + 1 and frees the slot of plane k - 1.  TMA: thread 0 waits
+    // for the box of plane k + 2 and the seam entries are patched before the barrier
+    if constexpr (TMA) {
+      // plane k + 2 sits in slot s0 + 2 (mod kRing), in that slot's phase number (k - k0 + 3) / kRing
+      const int s_fix = s0 + 2 >= kRing ? s0 + 2 - kRing : s0 + 2;
+      const unsigned par_fix = (unsigned)((k - k0 + 3) / kRing) & 1u;
+      if (k + 2 <= k1) {
+        if (tid == 0 && !tma::mbar_wait(&full[s_fix], par_fix)) timeout = true;
+        if (seam_cta) {
+          int dst;
+          unsigned off = 0u;
+          seam_entry(dst, off);
+          if (dst >= 0) {
+            if (!tma::mbar_wait(&full[s_fix], par_fix)) timeout = true;
+            RW[s_fix * SLOTE + dst] = fv;
+            fv = k + 3 <= k1 ? __ldg(x + off + (long long)wrap(k + 3, d.nz) * plane) : T(0);
+          }
+        }
+      }
+      if (__syncthreads_or(timeout)) return false;
       if (k + 4 <= k1) stage_plane(s0 == 0 ? kRing - 1 : s0 - 1, kz4);
-      else cp_async_commit();  // an empty group keeps one group per layer
+    } else {
+      if constexpr (RAW) cp_async_wait_group<1>();
+      __syncthreads();
+      if constexpr (RAW) {
+        if (k + 4 <= k1) stage_plane(s0 == 0 ? kRing - 1 : s0 - 1, kz4);
+        else cp_async_commit();  // an empty group keeps one group per layer
+      }
     }
     if (node_thread && k >= k0) {
       // node (i, j) of plane k is corner (1,1) of face (i-1, j-1), (0,1) of (i, j-1),
@@ -590,7 +691,7 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
         const long long gidx = (long long)j * d.N + (long long)kzc * plane + node_off;
         if (RED != RED_SUMS) y[gidx] = val;
         if constexpr (RED == RED_PCG) {
-          if constexpr (RAW) acc_p.add(val, RW[(s0 * C + j) * RPLANE + (nj + 1) * RP + RX0 + ni + 1]);
+          if constexpr (RAW) acc_p.add(val, RW[s0 * SLOTE + j * RPLANE + (nj + 1) * RP + RX0 + ni + 1]);
           else acc_p.add(val, __ldg(x + gidx));
         }
         if (RED == RED_STATS || RED == RED_SUMS) acc_y += (double)val * (double)val;
@@ -598,10 +699,33 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
     }
     // the next layer writes the other corner buffer; plane k's slot is refilled after the barrier
     // of layer k + 1
+    return true;
   };
 
   int kz = wrap(k0 - 1, d.nz);
-  if constexpr (RAW) {  // planes k0 - 1 .. k0 + 2, one group each; the first two visible to all
+  bool ok = true;
+  if constexpr (TMA) {  // planes k0 - 1 .. k0 + 2 issued; k0 - 1 and k0 landed, patched and visible to all
+    if (tid == 0) {
+      for (int sl = 0; sl < kRing; ++sl) tma::mbar_init(&full[sl], 1);
+      tma_book[0] = tma_book[1] = 0u;
+      tma::fence_mbar_init();
+    }
+    __syncthreads();
+    for (int p = 0; p < 4; ++p)
+      if (k0 - 1 + p <= k1) stage_plane(p, wrap(k0 - 1 + p, d.nz));
+    const T fa = fetch(k0 - 1), fb = fetch(k0);
+    int dst = -1;
+    unsigned off = 0u;
+    if (seam_cta) seam_entry(dst, off);
+    if (tid == 0 || dst >= 0)
+      if (!tma::mbar_wait(&full[0], 0) || !tma::mbar_wait(&full[1], 0)) timeout = true;
+    if (dst >= 0) {
+      RW[dst] = fa;
+      RW[SLOTE + dst] = fb;
+    }
+    fv = k0 + 1 <= k1 ? fetch(k0 + 1) : T(0);
+    ok = !__syncthreads_or(timeout);
+  } else if constexpr (RAW) {  // planes k0 - 1 .. k0 + 2, one group each; the first two visible to all
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
       if (k0 - 1 + p <= k1) stage_plane(p, wrap(k0 - 1 + p, d.nz));
@@ -622,12 +746,25 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
     }
     ++k;
   };
-  while (k < k1) {
-    layer(std::integral_constant<int, 0>{}, k, kz, s0, kz4);
+  while (ok && k < k1) {
+    if (!(ok = layer(std::integral_constant<int, 0>{}, k, kz, s0, kz4))) break;
     advance();
     if (k >= k1) break;
-    layer(std::integral_constant<int, 1>{}, k, kz, s0, kz4);
+    if (!(ok = layer(std::integral_constant<int, 1>{}, k, kz, s0, kz4))) break;
     advance();
+  }
+  if constexpr (TMA) {
+    if (!ok) {  // a wait gave up: let the boxes in flight land (bounded), mark the load and leave
+      if (tid == 0) {
+        for (int sl = 0; sl < kRing; ++sl)
+          if ((tma_book[1] >> sl) & 1u) tma::mbar_wait(&full[sl], ((tma_book[0] >> sl) & 1u) ^ 1u);
+        if (a.st != nullptr) {
+          a.st[load].err = 1;
+          a.st[load].state = ST_BREAK;
+        }
+      }
+      return;
+    }
   }
 
   if (RED == RED_PCG) {
@@ -986,20 +1123,37 @@ void hex8_grid(const Dims& d, int n_loads, int* tiles, int* slabs, int* kz) {
   *slabs = (d.nz + bkz - 1) / bkz;
 }
 
+// modes: PCG (x, <x, y>), STATS (residual / right-hand side with sums), plain (x and/or e)
+// every x tile full and 16-byte aligned rows: the FP32 PCG apply stages node planes with 16-byte copies
+bool hex8_wide(const StencilArgs& a) {
+  return a.d.nx % BX == 0 && a.d.nx % 4 == 0 && a.load_stride % 4 == 0 &&
+         (reinterpret_cast<unsigned long long>(a.x) & 15) == 0;
+}
+
 template <typename T, int C, bool ISO, bool HAS_X, bool HAS_E, int RED, int BYT = hex8_default_rows<T>(),
-          bool WIDE = false>
+          int STG = STG_CP4>
 cudaError_t launch_hex8_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
   const Dims& d = a.d;
   int tiles, slabs, kz;
   hex8_grid<BYT>(d, a.n_loads, &tiles, &slabs, &kz);
   if (ctas) *ctas = tiles * slabs;
   if (RED == RED_PCG && tiles * slabs > a.red.max_blocks) return cudaErrorInvalidConfiguration;
-  const size_t smem = sizeof(T) * hex8_smem_elems<T, C, HAS_X, BYT>();
-  auto kern = hex8_apply_kernel<T, C, ISO, HAS_X, HAS_E, RED, BYT, WIDE>;
+  CUtensorMap map{};
+  if constexpr (STG == STG_TMA) {
+    // the field of every load as (x, y, component, z): a box lands as [component][row][x], the staged layout
+    const unsigned long long dims[4] = {(unsigned long long)d.nx, (unsigned long long)d.ny,
+                                        (unsigned long long)C * a.n_loads, (unsigned long long)d.nz};
+    const unsigned long long strides[3] = {(unsigned long long)d.nx * sizeof(T), (unsigned long long)d.N * sizeof(T),
+                                           (unsigned long long)d.nx * d.ny * sizeof(T)};
+    const unsigned box[4] = {RP, BYT + 2, C, 1};
+    if (!hex8_wide(a) || !encode_f32_map(&map, a.x, dims, strides, box)) return cudaErrorInvalidValue;
+  }
+  const size_t smem = sizeof(T) * hex8_smem_elems<T, C, HAS_X, BYT, STG>();
+  auto kern = hex8_apply_kernel<T, C, ISO, HAS_X, HAS_E, RED, BYT, STG>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(tiles, slabs, a.n_loads);
-  kern<<<grid, Hex8Tile<T, BYT>::NT, smem, s>>>(a, kz);
+  kern<<<grid, Hex8Tile<T, BYT>::NT, smem, s>>>(map, a, kz);
   return cudaGetLastError();
 }
 
@@ -1033,13 +1187,6 @@ cudaError_t launch_pixel_t(const StencilArgs& a, int* ctas, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// modes: PCG (x, <x, y>), STATS (residual / right-hand side with sums), plain (x and/or e)
-// every x tile full and 16-byte aligned rows: the FP32 PCG apply stages node planes with 16-byte copies
-bool hex8_wide(const StencilArgs& a) {
-  return !a.narrow && a.d.nx % BX == 0 && a.d.nx % 4 == 0 && a.load_stride % 4 == 0 &&
-         (reinterpret_cast<unsigned long long>(a.x) & 15) == 0;
-}
-
 template <typename T, int C, bool ISO>
 cudaError_t dispatch_hex8(const StencilArgs& a, int* ctas, cudaStream_t s) {
   const bool hx = a.x != nullptr, he = a.tau != nullptr;
@@ -1047,9 +1194,16 @@ cudaError_t dispatch_hex8(const StencilArgs& a, int* ctas, cudaStream_t s) {
     if (!hx || he) return cudaErrorInvalidValue;
     constexpr int R0 = hex8_default_rows<T>(), R1 = 24 - hex8_default_rows<T>();
     const bool alt = a.tile_rows != 0 && a.tile_rows != R0;
-    if (hex8_raw<T, C, true>() && hex8_wide(a)) {  // FP32: 16-byte plane staging
-      return alt ? launch_hex8_t<T, C, ISO, true, false, RED_PCG, R1, true>(a, ctas, s)
-                 : launch_hex8_t<T, C, ISO, true, false, RED_PCG, R0, true>(a, ctas, s);
+    constexpr bool raw = hex8_raw<T, C, true>();
+    const bool wide = raw && hex8_wide(a);
+    if ((a.staging == 2 || a.staging == 3) && !wide) return cudaErrorInvalidValue;
+    if constexpr (raw) {
+      if (wide && a.staging == 3)  // FP32: TMA plane staging
+        return alt ? launch_hex8_t<T, C, ISO, true, false, RED_PCG, R1, STG_TMA>(a, ctas, s)
+                   : launch_hex8_t<T, C, ISO, true, false, RED_PCG, R0, STG_TMA>(a, ctas, s);
+      if (wide && (a.staging == 0 || a.staging == 2))  // FP32: 16-byte cp.async plane staging
+        return alt ? launch_hex8_t<T, C, ISO, true, false, RED_PCG, R1, STG_CP16>(a, ctas, s)
+                   : launch_hex8_t<T, C, ISO, true, false, RED_PCG, R0, STG_CP16>(a, ctas, s);
     }
     return alt ? launch_hex8_t<T, C, ISO, true, false, RED_PCG, R1>(a, ctas, s)
                : launch_hex8_t<T, C, ISO, true, false, RED_PCG, R0>(a, ctas, s);

@@ -98,7 +98,7 @@ def load_library(path: str = LIB_PATH):
     lib.fehom_rhs.restype = i
     lib.fehom_residual_update.argtypes = [vp, vp, vp, vp, dp]
     lib.fehom_residual_update.restype = i
-    lib.fehom_stencil_plan.argtypes = [vp, i, C.POINTER(C.c_int), dp]
+    lib.fehom_stencil_plan.argtypes = [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
     lib.fehom_stencil_plan.restype = i
     lib.fehom_rhs_df.argtypes = [vp, dp, vp]
     lib.fehom_rhs_df.restype = i
@@ -292,11 +292,13 @@ class Solver:
         return b
 
     def stencil_plan(self, precision="fp64"):
-        """(rows, [ms with 8 rows, ms with 16 rows]) of the hex8 PCG stiffness apply."""
-        rows = C.c_int(0)
-        ms = np.zeros(2)
-        self._check(self.lib.fehom_stencil_plan(self.ctx, PRECISION[precision], C.byref(rows), _dptr(ms)))
-        return rows.value, ms.tolist()
+        """(rows, staging, [ms: 8 / 16 rows with cp.async staging, 8 / 16 rows with TMA staging]) of the hex8
+        PCG stiffness apply."""
+        rows, staging = C.c_int(0), C.c_int(0)
+        ms = np.zeros(4)
+        self._check(self.lib.fehom_stencil_plan(self.ctx, PRECISION[precision], C.byref(rows), C.byref(staging),
+                                                _dptr(ms)))
+        return rows.value, staging.value, ms.tolist()
 
     def residual_update(self, d, r_in, r_out=None):
         """r_out = r_in - K d with K d in double-float arithmetic (d: FP32 field, r_in / r_out: FP64 fields,

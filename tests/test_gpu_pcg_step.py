@@ -118,14 +118,30 @@ def _check_stiffness(s, g, K, precision, rows, staging, n_loads=2, seed=0):
         assert abs(alpha[l] - a_ref) <= 2.0 * tol * mag / pap_ref * a_ref
 
 
+def _staging_applies(physics, shape, kind, cubic, precision, staging, rows):
+    """Whether a staging mode of the FP32 hex8 PCG apply exists for a case (the others must be refused)."""
+    if staging in (0, 1):
+        return True
+    return precision == "mixed" and shape[2] % 32 == 0
+
+
 @pytest.mark.parametrize("elem,physics,shape,kind,cubic", STIFFNESS_CASES)
-@pytest.mark.parametrize("precision,staging", [("fp64", 0), ("mixed", 0), ("mixed", 1)])
+@pytest.mark.parametrize("precision,staging", [("fp64", 0), ("mixed", 0), ("mixed", 1), ("mixed", 2), ("mixed", 3)])
 @pytest.mark.parametrize("rows", [8, 16])
 def test_pcg_stiffness_hex8_matches_oracle(elem, physics, shape, kind, cubic, precision, staging, rows):
-    """The hex8 PCG stiffness launch: K p and the fused <p, K p> and alpha, every tile height and staging."""
+    """The hex8 PCG stiffness launch: K p and the fused <p, K p> and alpha, every tile height and staging
+    (4-byte and 16-byte cp.async copies, one tensor-memory-accelerator box per plane); a staging that does not
+    apply to the case is refused with FEHOM_E_UNSUPPORTED_SIZE."""
     ids, mod, cell, g, K = _case(elem, physics, shape, kind, cubic)
     s = _solver(elem, physics, shape, ids, mod, cell, precision=precision)
-    _check_stiffness(s, g, K, precision, rows, staging, n_loads=2, seed=rows + staging)
+    if _staging_applies(physics, shape, kind, cubic, precision, staging, rows):
+        _check_stiffness(s, g, K, precision, rows, staging, n_loads=2, seed=rows + staging)
+    else:
+        torch = _torch()
+        p = torch.zeros((1, g.c, g.N), dtype=torch.float32, device="cuda")
+        with pytest.raises(_fehom().FehomError) as ei:
+            s.pcg_apply_stiffness(p, [1.0], precision, rows=rows, staging=staging)
+        assert ei.value.status == 2
     s.close()
 
 
@@ -252,7 +268,7 @@ def test_pcg_precond_step_matches_oracle(elem, physics, shape, fft_xy, precision
 
 def test_pcg_step_full_size_benchmark_cell():
     """128^3 elastic spheres, six loads (the benchmark launch): the FP32 PCG stiffness with both tile
-    heights and both stagings on 3000 sampled rows of the oracle's K, its fused <p, K p> against the dot
+    heights and every staging on 3000 sampled rows of the oracle's K, its fused <p, K p> against the dot
     of its own output; the FP32 preconditioner passes with the register-split x-y and last-axis passes
     (the solve's plan at this size) against the oracle's FFT preconditioner, and the generic passes."""
     torch = _torch()
@@ -267,16 +283,15 @@ def test_pcg_step_full_size_benchmark_cell():
                         autotune=False)
     pt = torch.tensor(p.reshape(L, g.c, g.N), device="cuda")
     ref_rows = [fem.stiffness_rows(g, w["ids"].ravel(), w["moduli"], p[l].astype(np.float64), rows) for l in (0, L - 1)]
-    for tile_rows in (8, 16):
-        for staging in (0, 1):
-            ap, pap, _ = s.pcg_apply_stiffness(pt, np.ones(L), "mixed", rows=tile_rows, staging=staging)
-            apn = ap.double()
-            dots = (apn * pt.double()).sum(dim=(1, 2)).cpu().numpy()
-            mags = (apn.abs() * pt.double().abs()).sum(dim=(1, 2)).cpu().numpy()
-            assert np.all(np.abs(pap - dots) <= 1e-9 * mags), (tile_rows, staging)
-            apc = apn.cpu().numpy().reshape(L, -1)
-            for j, l in enumerate((0, L - 1)):
-                assert np.abs(apc[l][rows] - ref_rows[j]).max() <= 2e-5 * np.abs(ref_rows[j]).max()
+    for tile_rows, staging in ((8, 0), (8, 1), (8, 2), (8, 3), (16, 0), (16, 1), (16, 2), (16, 3)):
+        ap, pap, _ = s.pcg_apply_stiffness(pt, np.ones(L), "mixed", rows=tile_rows, staging=staging)
+        apn = ap.double()
+        dots = (apn * pt.double()).sum(dim=(1, 2)).cpu().numpy()
+        mags = (apn.abs() * pt.double().abs()).sum(dim=(1, 2)).cpu().numpy()
+        assert np.all(np.abs(pap - dots) <= 1e-9 * mags), (tile_rows, staging)
+        apc = apn.cpu().numpy().reshape(L, -1)
+        for j, l in enumerate((0, L - 1)):
+            assert np.abs(apc[l][rows] - ref_rows[j]).max() <= 2e-5 * np.abs(ref_rows[j]).max()
     s.precond_build()
     C_ref = fem.mean_material(g, w["ids"].ravel(), w["moduli"])
     Kinv = solvers.kref_pinv_symbol(solvers.kref_symbol(g, C_ref))
