@@ -70,6 +70,23 @@ template <typename C, bool INV> __device__ __forceinline__ void dft4(C& v0, C& v
   v3 = csub(b, d);
 }
 
+// FP32: the four sums and differences as packed FP32x2 instructions; the butterflies with the +-i
+// rotation mix the real and imaginary parts, so they stay scalar (the negation folds into the add)
+template <> __device__ __forceinline__ void dft4<float2, false>(float2& v0, float2& v1, float2& v2, float2& v3) {
+  const float2 a = cadd(v0, v2), b = csub(v0, v2), c = cadd(v1, v3), e = csub(v1, v3);
+  v0 = cadd(a, c);
+  v2 = csub(a, c);
+  v1 = make_float2(b.x + e.y, b.y - e.x);  // b + (-i) e
+  v3 = make_float2(b.x - e.y, b.y + e.x);
+}
+template <> __device__ __forceinline__ void dft4<float2, true>(float2& v0, float2& v1, float2& v2, float2& v3) {
+  const float2 a = cadd(v0, v2), b = csub(v0, v2), c = cadd(v1, v3), e = csub(v1, v3);
+  v0 = cadd(a, c);
+  v2 = csub(a, c);
+  v1 = make_float2(b.x - e.y, b.y + e.x);  // b + i e
+  v3 = make_float2(b.x + e.y, b.y - e.x);
+}
+
 template <typename C, int R, bool INV> struct Dft;
 template <typename C, bool INV> struct Dft<C, 2, INV> {
   __device__ static void run(C (&v)[2]) { dft2<C, INV>(v[0], v[1]); }
