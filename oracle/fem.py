@@ -285,4 +285,5 @@ def mean_material(grid: Grid, phases, moduli):
     """C_mean = (1/|Y|) sum_Q C(x_Q) w_Q (Sec. 6.2 reference-material choice)."""
     phases = np.asarray(phases).ravel()
     counts = np.bincount(phases, minlength=len(moduli)).astype(float)
-    return np.einsum("p,pij->ij", counts * grid.vp, np.asarray(moduli, float))
+    volume = grid.vp * grid.N  # |Y|: 1 on the unit cell, the cell volume when grid.h is scaled
+    return np.einsum("p,pij->ij", counts * grid.vp / volume, np.asarray(moduli, float))

@@ -596,3 +596,18 @@ def test_mean_material_of_the_disc_cell_is_exact():
     ids[:16] = 1
     mod = [_rand_spd(6, 1), _rand_spd(6, 2)]
     assert np.allclose(fem.mean_material(g3, ids, mod), 0.75 * mod[0] + 0.25 * mod[1], rtol=0, atol=1e-14)
+
+
+def test_mean_material_is_a_volume_mean_on_any_cell():
+    """Sec. 6.2 C_mean = (1/|Y|) sum_Q C(x_Q) w_Q: the same phase fractions on a scaled (non-unit) cell give
+    the same C_mean (a sum without the 1/|Y| would scale it by the cell volume)."""
+    rng = np.random.default_rng(3)
+    ids = rng.integers(0, 2, 4 * 6 * 8)
+    mod = [_rand_spd(6, 4), _rand_spd(6, 5)]
+    g = fem.Grid((4, 6, 8), "hex8_3d", "elastic")
+    unit = fem.mean_material(g, ids, mod)
+    g.h = np.array([1.0, 0.7, 0.5]) / np.array(g.n_xyz, float)
+    g.vp = float(np.prod(g.h))
+    f1 = (ids == 1).mean()
+    assert np.allclose(fem.mean_material(g, ids, mod), unit, rtol=1e-14, atol=0)
+    assert np.allclose(unit, (1 - f1) * mod[0] + f1 * mod[1], rtol=1e-14, atol=0)
