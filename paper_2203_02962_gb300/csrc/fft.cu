@@ -974,31 +974,35 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_la
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
-  DotAcc2 dot;
-  const bool active = tid < 256;
-  const int t = tid & 15, k1 = (tid >> 4) & 15;
-  const int cf = cf0 + t;
-  float2 zr[NC][8];
-  if (active) {
+  // stage 2, all threads, in place in S[c][k1][slot][t]: (a) the 8-point forward DFTs over the slot
+  // index (j -> k2) of the 16 NC (k1, c) lines of each column, two per thread for NC = 3; (b) the block
+  // solve z^ = K_hat^+ r^ / N and the Parseval sum <r, z> at every (k1, k2) of the thread's column;
+  // (c) the 8-point inverse DFTs (k2 -> j) with the conjugate twiddles W_128^(j k1) of the inverse split
+  constexpr int NT3 = last128_threads<NC>();
+  constexpr int UNITS = 16 * 16 * NC;  // (t, k1, c) lines of 8 values
+  auto line = [&](int w) { return S + ((w >> 4) * 8) * TCL + (w & 15); };  // w = (c * 16 + k1) * 16 + t
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
+  for (int w = tid; w < UNITS; w += NT3) {
+    float2* L = line(w);
+    float2 z[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) zr[c][j] = S[((c * 16 + k1) * 8 + j) * TCL + t];
+    for (int j = 0; j < 8; ++j) z[j] = L[j * TCL];
+    Dft<float2, 8, false>::run(z);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) L[k2 * TCL] = z[k2];
   }
   __syncthreads();
-  if (active) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) Dft<float2, 8, false>::run(zr[c]);
-    const int kx = cf % nxh;
-    const float wgt = (kx == 0 || kx == half) ? 1.0f : 2.0f;
-#pragma unroll
-    for (int k2 = 0; k2 < 8; ++k2) {
+  DotAcc2 dot;
+  const int t = tid & 15;  // NT3 is a multiple of 16: every point of this thread lies in column t
+  {
+    const int kx = (cf0 + t) % nxh;
+    for (int pnt = tid; pnt < 16 * 128; pnt += NT3) {
+      const int k1 = (pnt >> 4) & 15, k2 = pnt >> 8;
       const float* ks = Ssym + (k1 + 16 * k2) * TCL + t;  // entry e at ks[e * 128 * TCL]
       float2 r[NC], z[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) r[c] = zr[c][k2];
-      // z = K_hat^+ r with a real symmetric block: each entry scales the real and imaginary parts alike,
-      // so the complex products are packed FP32x2 operations with the entry in both halves
+      for (int c = 0; c < NC; ++c) r[c] = S[((c * 16 + k1) * 8 + k2) * TCL + t];
+      // a real symmetric block scales the real and imaginary parts alike: packed FP32x2 products
       auto kk = [](float k) { return make_float2(k, k); };
       if constexpr (NC == 1) {
         z[0] = __fmul2_rn(kk(ks[0]), r[0]);
@@ -1013,17 +1017,23 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_la
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         dot.add(r[c], z[c]);  // the column's Parseval weight is applied to the thread's sum below
-        zr[c][k2] = z[c];
+        S[((c * 16 + k1) * 8 + k2) * TCL + t] = z[c];
       }
     }
-    if (wgt != 1.0f) dot.scale2();
+    if (kx != 0 && kx != half) dot.scale2();
+  }
+  __syncthreads();
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      Dft<float2, 8, true>::run(zr[c]);
+  for (int w = tid; w < UNITS; w += NT3) {
+    float2* L = line(w);
+    const int k1 = (w >> 4) & 15;
+    float2 z[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        S[((c * 8 + j) * 16 + k1) * TCL + t] = j == 0 ? zr[c][0] : cmulc(zr[c][j], __ldg(tw + j * k1));
-    }
+    for (int k2 = 0; k2 < 8; ++k2) z[k2] = L[k2 * TCL];
+    Dft<float2, 8, true>::run(z);
+    L[0] = z[0];
+#pragma unroll
+    for (int j = 1; j < 8; ++j) L[j * TCL] = cmulc(z[j], __ldg(tw + j * k1));
   }
   __syncthreads();
   if (tid < 128 * NC) {  // stage 3: task (column t, subsequence j, component c): 16-point inverse DFT over k1
@@ -1031,7 +1041,7 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_la
     const int cff = cf0 + tt;
     float2 v[16];
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) v[kk] = S[((c * 8 + j) * 16 + kk) * TCL + tt];
+    for (int kk = 0; kk < 16; ++kk) v[kk] = S[((c * 16 + kk) * 8 + j) * TCL + tt];
     dft16<true>(v);
 #pragma unroll
     for (int m = 0; m < 16; ++m) spec[c * Nh + cff + (j + 8 * m) * es] = v[m];
