@@ -160,7 +160,7 @@ def kernel_model(s):
 
 FP64_INSTR_PEAK = 152 * 2 * 2.07e9     # FP64 instructions/s: 152 SMs x 2 FP64 lanes-per-clock x max clock
 # DRAM bytes (read + write) of one 6-load FP64 stiffness launch on the 128^3 workload, from ncu
-FP64_STIFFNESS_DRAM_BYTES = 324.696064e6 + 262.707200e6
+FP64_STIFFNESS_DRAM_BYTES = 324.482560e6 + 263.110144e6
 
 
 def run_ours(args):
@@ -320,8 +320,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_ops / 1e12, "peak": FP64_INSTR_PEAK / 1e12,
                      "unit": "T FP64-instr/s", "frac": achieved_ops / FP64_INSTR_PEAK,
                      "traffic": FP64_STIFFNESS_DRAM_BYTES if dom == "stiffness" else None,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 6-load launch, "
-                                       "profiles/hex8_apply_fp64_128cube_elastic.md",
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 6-load launch of the "
+                                       "current kernel, profiles/hex8_apply_fp64_128cube_elastic.md",
                      "algorithmic_bytes_per_launch": model["bytes"] * units_per_launch,
                      "peak_source": "152 SMs x 2 FP64 lanes/clk x 2.07 GHz (unit count x max clock)",
                      "avg_launch_ms": avg_ms, "launches": dom_launches,
