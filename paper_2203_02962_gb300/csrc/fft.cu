@@ -929,7 +929,7 @@ template <int NC>
 __host__ __device__ constexpr int last128_threads() { return NC == 1 ? 256 : 128 * NC; }
 template <int NC>
 __host__ __device__ constexpr size_t last128_smem() {
-  return (size_t)NC * 16 * 8 * 16 * sizeof(float2) + (size_t)(NC == 1 ? 1 : 6) * 128 * 16 * sizeof(float);
+  return (size_t)NC * 16 * 8 * 16 * sizeof(float2);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -939,13 +939,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 
 template <int NC>
-__global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_last128_kernel(FftArgs a) {
+__global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 3 : 4) fft_last128_kernel(FftArgs a) {
   constexpr int TCL = 16;
-  constexpr int NS = NC == 1 ? 1 : 6;  // packed symbol entries
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_sh[32];
   float2* S = reinterpret_cast<float2*>(smem_raw);                // NC * 16 * 8 * 16 complex
-  float* Ssym = reinterpret_cast<float*>(S + NC * 16 * 8 * TCL);  // [NS][128 kz][16 columns]
   const int load = blockIdx.x;
   if (!first_half_active(a.st, load)) return;
   float2* spec = reinterpret_cast<float2*>(a.spec) + (long long)load * a.load_stride_s;
@@ -956,11 +954,6 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_la
   const float2* tw = reinterpret_cast<const float2*>(a.tw.z);
   const float* sym = reinterpret_cast<const float*>(a.sym);
   const int tid = threadIdx.x;
-  for (int ch = tid; ch < NS * 128 * 4; ch += last128_threads<NC>()) {  // 16-byte chunks of the slice
-    const int e = ch >> 9, kz = (ch >> 2) & 127, q4 = ch & 3;
-    cp_async16(Ssym + (e * 128 + kz) * TCL + 4 * q4, sym + e * Nh + cf0 + kz * es + 4 * q4);
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
   if (tid < 128 * NC) {  // stage 1: task (column t, subsequence j, component c)
     const int t = tid & 15, j = (tid >> 4) & 7, c = tid >> 7;
     const int cf = cf0 + t;
@@ -972,7 +965,6 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_la
     for (int k1 = 0; k1 < 16; ++k1)
       S[((c * 16 + k1) * 8 + j) * TCL + t] = k1 == 0 ? v[0] : cmul(v[k1], __ldg(tw + j * k1));
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   // stage 2, all threads, in place in S[c][k1][slot][t]: (a) the 8-point forward DFTs over the slot
   // index (j -> k2) of the 16 NC (k1, c) lines of each column, two per thread for NC = 3; (b) the block
@@ -998,18 +990,19 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 2 : 4) fft_la
     const int kx = (cf0 + t) % nxh;
     for (int pnt = tid; pnt < 16 * 128; pnt += NT3) {
       const int k1 = (pnt >> 4) & 15, k2 = pnt >> 8;
-      const float* ks = Ssym + (k1 + 16 * k2) * TCL + t;  // entry e at ks[e * 128 * TCL]
+      // the symbol entries of this wavevector, read from L2 where the loads of the column group meet
+      // (the grid runs them next to each other): entry e at ks[e * Nh]
+      const float* ks = sym + cf0 + t + (long long)(k1 + 16 * k2) * es;
       float2 r[NC], z[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) r[c] = S[((c * 16 + k1) * 8 + k2) * TCL + t];
       // a real symmetric block scales the real and imaginary parts alike: packed FP32x2 products
       auto kk = [](float k) { return make_float2(k, k); };
       if constexpr (NC == 1) {
-        z[0] = __fmul2_rn(kk(ks[0]), r[0]);
+        z[0] = __fmul2_rn(kk(__ldg(ks)), r[0]);
       } else {
-        constexpr int E = 128 * TCL;
-        const float2 k00 = kk(ks[0]), k11 = kk(ks[E]), k22 = kk(ks[2 * E]);
-        const float2 k12 = kk(ks[3 * E]), k02 = kk(ks[4 * E]), k01 = kk(ks[5 * E]);
+        const float2 k00 = kk(__ldg(ks)), k11 = kk(__ldg(ks + Nh)), k22 = kk(__ldg(ks + 2 * Nh));
+        const float2 k12 = kk(__ldg(ks + 3 * Nh)), k02 = kk(__ldg(ks + 4 * Nh)), k01 = kk(__ldg(ks + 5 * Nh));
         z[0] = __ffma2_rn(k00, r[0], __ffma2_rn(k01, r[1], __fmul2_rn(k02, r[2])));
         z[1] = __ffma2_rn(k01, r[0], __ffma2_rn(k11, r[1], __fmul2_rn(k12, r[2])));
         z[2] = __ffma2_rn(k02, r[0], __ffma2_rn(k12, r[1], __fmul2_rn(k22, r[2])));
