@@ -568,6 +568,8 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
     }
   };
 
+  // phase id of this face thread's element in the next layer (the first layer is k0 - 1, plane wrap(k0 - 1))
+  int ph_n = (face_thread && a.ids != nullptr) ? a.ids[(long long)wrap(k0 - 1, d.nz) * plane + off00] : 0;
   auto layer = [&](auto cur_c, int k, int kzc, [[maybe_unused]] int s0, [[maybe_unused]] int kz4) -> bool {
     [[maybe_unused]] constexpr int CUR = decltype(cur_c)::value;
     [[maybe_unused]] const int s1 = s0 == kRing - 1 ? 0 : s0 + 1;
@@ -601,7 +603,10 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
             top[j][q] = HAS_X ? FB[(((CUR ^ 1) * 4 + q) * C + j) * NE + tid] : T(0);
           }
       }
-      const int ph = a.ids ? a.ids[(long long)kzc * plane + off00] : 0;
+      // this layer's phase id was read a layer ahead; the next layer's read is issued before the
+      // element arithmetic so that its latency hides behind this layer
+      const int ph = ph_n;
+      if (a.ids != nullptr && k + 1 < k1) ph_n = a.ids[(long long)next(kzc) * plane + off00];
       T pb[C][4], pt[C][4], t1[C][3];
       hex8_element_faces<T, C, ISO, HAS_X, HAS_E>(bot, top, mats + (long long)ph * (9 * C * C), isot + kIsoStride * ph,
                                                   HAS_E ? tau + ph * (3 * C) : nullptr, pb, pt, t1);
