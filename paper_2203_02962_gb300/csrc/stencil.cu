@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
       }
     }
   }
-  auto stage_plane = [&](int slot, int kz) {
+  auto stage_plane = [&](int slot, int kz, [[maybe_unused]] long long kzoff) {
     if constexpr (TMA) {
       if (tid == 0) {
         tma::fence_proxy_async();
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
       }
       return;
     } else if constexpr (RAW) {
-      const T* xk = x + (long long)kz * plane;
+      const T* xk = x + kzoff;  // kzoff = kz * plane
       T* dst = RW + slot * C * RPLANE;
       if constexpr (WIDE) {
         if (soff[0] >= 0) {
@@ -568,6 +568,9 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
     }
   };
 
+  // offsets kz * plane of the layer's plane and of the plane staged four ahead, carried from layer to
+  // layer (no 64-bit multiplies in the loop)
+  long long pc = (long long)wrap(k0 - 1, d.nz) * plane, p4 = RAW ? (long long)wrap(k0 + 3, d.nz) * plane : 0;
   // phase id of this face thread's element in the next layer (the first layer is k0 - 1, plane wrap(k0 - 1))
   int ph_n = (face_thread && a.ids != nullptr) ? a.ids[(long long)wrap(k0 - 1, d.nz) * plane + off00] : 0;
   auto layer = [&](auto cur_c, int k, int kzc, [[maybe_unused]] int s0, [[maybe_unused]] int kz4) -> bool {
@@ -606,7 +609,7 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
       // this layer's phase id was read a layer ahead; the next layer's read is issued before the
       // element arithmetic so that its latency hides behind this layer
       const int ph = ph_n;
-      if (a.ids != nullptr && k + 1 < k1) ph_n = a.ids[(long long)next(kzc) * plane + off00];
+      if (a.ids != nullptr && k + 1 < k1) ph_n = a.ids[(kzc + 1 == d.nz ? 0 : pc + plane) + off00];
       T pb[C][4], pt[C][4], t1[C][3];
       hex8_element_faces<T, C, ISO, HAS_X, HAS_E>(bot, top, mats + (long long)ph * (9 * C * C), isot + kIsoStride * ph,
                                                   HAS_E ? tau + ph * (3 * C) : nullptr, pb, pt, t1);
@@ -662,12 +665,12 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
         }
       }
       if (__syncthreads_or(timeout)) return false;
-      if (k + 4 <= k1) stage_plane(s0 == 0 ? kRing - 1 : s0 - 1, kz4);
+      if (k + 4 <= k1) stage_plane(s0 == 0 ? kRing - 1 : s0 - 1, kz4, p4);
     } else {
       if constexpr (RAW) cp_async_wait_group<1>();
       __syncthreads();
       if constexpr (RAW) {
-        if (k + 4 <= k1) stage_plane(s0 == 0 ? kRing - 1 : s0 - 1, kz4);
+        if (k + 4 <= k1) stage_plane(s0 == 0 ? kRing - 1 : s0 - 1, kz4, p4);
         else cp_async_commit();  // an empty group keeps one group per layer
       }
     }
@@ -693,7 +696,7 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
       for (int j = 0; j < C; ++j) {
         const T v = gv[j];
         const T val = ysc * v;
-        const long long gidx = (long long)j * d.N + (long long)kzc * plane + node_off;
+        const long long gidx = (long long)j * d.N + pc + node_off;
         if (RED != RED_SUMS) y[gidx] = val;
         if constexpr (RED == RED_PCG) {
           if constexpr (RAW) acc_p.add(val, RW[s0 * SLOTE + j * RPLANE + (nj + 1) * RP + RX0 + ni + 1]);
@@ -717,7 +720,7 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
     }
     __syncthreads();
     for (int p = 0; p < 4; ++p)
-      if (k0 - 1 + p <= k1) stage_plane(p, wrap(k0 - 1 + p, d.nz));
+      if (k0 - 1 + p <= k1) stage_plane(p, wrap(k0 - 1 + p, d.nz), (long long)wrap(k0 - 1 + p, d.nz) * plane);
     const T fa = fetch(k0 - 1), fb = fetch(k0);
     int dst = -1;
     unsigned off = 0u;
@@ -733,7 +736,7 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
   } else if constexpr (RAW) {  // planes k0 - 1 .. k0 + 2, one group each; the first two visible to all
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      if (k0 - 1 + p <= k1) stage_plane(p, wrap(k0 - 1 + p, d.nz));
+      if (k0 - 1 + p <= k1) stage_plane(p, wrap(k0 - 1 + p, d.nz), (long long)wrap(k0 - 1 + p, d.nz) * plane);
       else cp_async_commit();
     }
     cp_async_wait_group<2>();
@@ -745,8 +748,10 @@ __global__ void __launch_bounds__(Hex8Tile<T, BYT>::NT, Hex8Tile<T, BYT>::PER_SM
   int s0 = 0, kz4 = RAW ? wrap(k0 + 3, d.nz) : 0;
   auto advance = [&] {
     kz = next(kz);
+    pc = kz == 0 ? 0 : pc + plane;
     if constexpr (RAW) {
       kz4 = next(kz4);
+      p4 = kz4 == 0 ? 0 : p4 + plane;
       s0 = s0 == kRing - 1 ? 0 : s0 + 1;
     }
     ++k;
