@@ -144,10 +144,10 @@ def workload():
 # element, one node plane) for isotropic phases: in-plane butterflies of the node plane 24, z part
 # 21, closed-form duals 35, transposed z part 18, face totals 12, transposed in-plane part 24, node
 # gather and scale 12, fused <p, Ap> 3 = 149.
-def kernel_model(s):
-    c, hs = 3, 65.0 / 128.0
+def kernel_model(s, c=3):
+    hs = 65.0 / 128.0
     spec = c * hs * 2 * s              # one half-spectrum pass over the c components
-    sym = 6 * s * hs                   # packed 3x3 symmetric K_hat^+ per half-spectrum k
+    sym = c * (c + 1) // 2 * s * hs    # packed symmetric c x c K_hat^+ per half-spectrum k
     return {
         "stiffness": {"bytes": 2 * c * s + 1, "fp64_ops": 149},
         "fft_x_fwd": {"bytes": 3 * c * s + spec, "fp64_ops": 3 * 4.0 * 7 * 3.5 / 2 * 2},
@@ -381,6 +381,72 @@ def cufft_comparison(N, c, n_loads, kt32, kt64, iters32, iters64, steps):
         out[name] = {"cufft_ms_per_apply": cu_ms, "ours_ms_per_apply": ours_ms, "ratio_ours_over_cufft": ours_ms / cu_ms}
         del x, y
     return out
+
+
+def run_grf512(args):
+    """The 512^3 scalar conductivity cell (thresholded GRF, contrast 1000, three unit gradients, 134M
+    DOF, tol 1e-6): plain FP64 PCG and the mixed form (FP32 inner PCG, FP64 refinement), each timed to
+    tolerance (Algorithm 2 + solve + C_eff) after one untimed step; one JSON line."""
+    import torch
+    from paper_2203_02962_gb300 import fehom
+    from paper_2203_02962_gb300 import inputs as I
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = I.workload_grf_scalar(512)
+    n, loads, c = w["n"], w["loads"], 1
+    N = n[0] * n[1] * n[2]
+    ids_dev = torch.tensor(w["ids"].ravel(), device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    steps = max(1, min(args.steps, 2))
+    res = {}
+    for prec in ("fp64", "mixed"):
+        s = fehom.Solver("hex8_3d", "scalar", n, ids_dev, w["moduli"], precision=prec, stream=stream, profile=True)
+
+        def step():
+            s.precond_build()
+            return s.solve(loads, tol=w["tol"], fields=None)
+
+        step()
+        t_before = s.kernel_times(prec)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            ev0.record(stream)
+            outs = [step() for _ in range(steps)]
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        t_after = s.kernel_times(prec)
+        kt = {k: (t_after[k][0] - t_before[k][0], t_after[k][1] - t_before[k][1]) for k in t_after}
+        load_iters = sum(sum(i["iterations"] for i in o["info"]) for o in outs)
+        res[prec] = dict(ms=ev0.elapsed_time(ev1) / steps, out=outs[-1], clocks=clk.summary(), kt=kt,
+                         load_iters=load_iters, C_energy=s.effective_energy())
+        s.close()
+    hbm, hbm_src = peaks()
+    r64, rmx = res["fp64"], res["mixed"]
+    model, units = kernel_model(4, c), N * rmx["load_iters"]
+    roof = {}
+    for k, (ms_k, n_k) in rmx["kt"].items():
+        if n_k > 0 and ms_k > 0:
+            gbs = model[k]["bytes"] * units / (ms_k * 1e-3) / 1e9
+            roof[k] = {"achieved_gbs": gbs, "frac": gbs / hbm, "avg_launch_us": 1e3 * ms_k / n_k, "launches": int(n_k)}
+    rel = lambda A, B: float(np.abs(A - B).max() / np.abs(B).max())
+    print(json.dumps({
+        "workload": "512^3 hex8 conductivity, thresholded periodic GRF (correlation length 16 voxels, 50 % volume), "
+                    "k = 1 / 1000, 3 unit gradients, tol 1e-6, C_ref = volume mean",
+        "dof": c * N, "steps": steps, "warmup": 1,
+        "fp64": {"time_to_tol_s": r64["ms"] * 1e-3, "iterations_per_load": [i["iterations"] for i in r64["out"]["info"]],
+                 "dof_iter_per_s": c * N * r64["load_iters"] / steps / (r64["ms"] * 1e-3),
+                 "kernel_ms_per_step": {k: v[0] / steps for k, v in r64["kt"].items()}, "clocks": r64["clocks"]},
+        "mixed": {"time_to_tol_s": rmx["ms"] * 1e-3,
+                  "inner_iterations_per_load": [i["iterations"] for i in rmx["out"]["info"]],
+                  "refinements_per_load": [i["refinements"] for i in rmx["out"]["info"]],
+                  "dof_iter_per_s": c * N * rmx["load_iters"] / steps / (rmx["ms"] * 1e-3),
+                  "roofline_hbm": {"peak_gbs": hbm, "peak_source": hbm_src, "kernels": roof}, "clocks": rmx["clocks"]},
+        "speedup_mixed_vs_fp64": r64["ms"] / rmx["ms"],
+        "C_eff_rel_diff_mixed_vs_fp64": rel(rmx["out"]["C_eff"], r64["out"]["C_eff"]),
+        "C_eff_energy_rel_diff_mixed_vs_fp64": rel(rmx["C_energy"], r64["C_energy"]),
+    }))
 
 
 def run_batched(args):
@@ -690,11 +756,16 @@ def main():
     ap.add_argument("--ncu-loads", type=int, default=6, help="loads of the --ncu-case solve (1-6)")
     ap.add_argument("--ncu-rows", type=int, default=0, choices=[0, 8, 16],
                     help="stencil rows of the --ncu-case solve (0: the tuners' usual pick)")
+    ap.add_argument("--grf512", action="store_true",
+                    help="time FP64 and mixed solves of the 512^3 scalar GRF cell (134M DOF), then exit")
     ap.add_argument("--oracle-timing", action="store_true",
                     help="time the oracle to tolerance on the host cores beside the GPU solves, then exit")
     args = ap.parse_args()
     if args.oracle_timing:
         oracle_timing(args)
+        return
+    if args.grf512:
+        run_grf512(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -236,6 +236,35 @@ bool iso_elastic(const double* C, int dim, double* lam, double* mu) {
   return true;
 }
 
+// scalar conductivity C = k I (3 x 3) ?
+bool iso_scalar(const double* C, double* k) {
+  double mx = 0;
+  for (int i = 0; i < 9; ++i) mx = std::max(mx, std::fabs(C[i]));
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      if (std::fabs(C[i * 3 + j] - (i == j ? C[0] : 0.0)) > 1e-13 * mx) return false;
+  *k = C[0];
+  return true;
+}
+
+// the isotropic fast-path entry (kIsoStride values, gradient coordinates) of material C for hex8 on cubic
+// voxels, or false when C is not isotropic
+bool iso_material(const fehom_ctx* ctx, const double* C, double* out) {
+  double w, sc[3];
+  kernel_scales(ctx, &w, sc);
+  const double f = w * sc[0] * sc[0];
+  if (ctx->physics == FEHOM_ELASTIC) {
+    double lam, mu;
+    if (!iso_elastic(C, 3, &lam, &mu)) return false;
+    iso_entry(f * lam, f * mu, out);
+    return true;
+  }
+  double k;
+  if (!iso_scalar(C, &k)) return false;
+  iso_entry_scalar(f * k, out);
+  return true;
+}
+
 // symmetric Jacobi eigen-decomposition (small n), for the k = 0 pseudo-inverse
 void jacobi_eig(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& ev) {
   V.assign(n * n, 0.0);
@@ -1145,12 +1174,8 @@ fehom_status fehom_set_reference(fehom_ctx* ctx, const double* C_ref) {
   grad_material(ctx, C_ref, rm.data());
   CK(cudaMemcpyAsync(ctx->rmats64, rm.data(), rm.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   ctx->iso_ref = false;
-  double lam, mu;
-  if (ctx->iso && iso_elastic(C_ref, 3, &lam, &mu)) {
-    double w, sc[3];
-    kernel_scales(ctx, &w, sc);
-    double ri[kIsoStride];
-    iso_entry(w * sc[0] * sc[0] * lam, w * sc[0] * sc[0] * mu, ri);
+  double ri[kIsoStride];
+  if (ctx->iso && iso_material(ctx, C_ref, ri)) {
     if (!ctx->riso64) CK(cudaMalloc(&ctx->riso64, kIsoStride * sizeof(double)));
     CK(cudaMemcpyAsync(ctx->riso64, ri, kIsoStride * sizeof(double), cudaMemcpyHostToDevice, s));
     ctx->iso_ref = true;
@@ -1473,42 +1498,38 @@ static fehom_status setup_impl(fehom_ctx* ctx, int elem, int physics, const int6
   grad_material(ctx, ctx->cref.data(), rm.data());
   CK(cudaMalloc(&ctx->rmats64, rm.size() * sizeof(double)));
   CK(cudaMemcpyAsync(ctx->rmats64, rm.data(), rm.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  // isotropic fast path (hex8 elasticity on a cubic grid)
-  if (elem == FEHOM_HEX8_3D && physics == FEHOM_ELASTIC && ctx->h[0] == ctx->h[1] && ctx->h[1] == ctx->h[2]) {
+  // isotropic fast path (hex8 elasticity or conductivity on a cubic grid)
+  if (elem == FEHOM_HEX8_3D && ctx->h[0] == ctx->h[1] && ctx->h[1] == ctx->h[2]) {
     bool all = true;
     std::vector<double> iso((size_t)kIsoStride * n_phases);
-    double w, sc[3];
-    kernel_scales(ctx, &w, sc);
-    for (int p = 0; p < n_phases && all; ++p) {
-      double lam, mu;
-      all = iso_elastic(&ctx->moduli[(size_t)p * m * m], 3, &lam, &mu);
-      iso_entry(w * sc[0] * sc[0] * lam, w * sc[0] * sc[0] * mu, &iso[(size_t)kIsoStride * p]);
-    }
+    for (int p = 0; p < n_phases && all; ++p)
+      all = iso_material(ctx, &ctx->moduli[(size_t)p * m * m], &iso[(size_t)kIsoStride * p]);
     if (all) {
       ctx->iso = true;
       std::vector<float> iso32(iso.begin(), iso.end());
-      // double-float copy of the six constants, hi = fl(v), lo = fl(v - hi) (refinement residuals)
-      std::vector<float> isodf((size_t)16 * n_phases, 0.0f);
-      for (int p = 0; p < n_phases; ++p)
-        for (int i = 0; i < 6; ++i) {
-          const double v = iso[(size_t)kIsoStride * p + i];
-          const float hi = (float)v;
-          isodf[(size_t)16 * p + 2 * i] = hi;
-          isodf[(size_t)16 * p + 2 * i + 1] = (float)(v - (double)hi);
-        }
       CK(cudaMalloc(&ctx->iso64, iso.size() * sizeof(double)));
       CK(cudaMalloc(&ctx->iso32, iso.size() * sizeof(float)));
-      CK(cudaMalloc(&ctx->isodf, isodf.size() * sizeof(float)));
       CK(cudaMemcpyAsync(ctx->iso64, iso.data(), iso.size() * sizeof(double), cudaMemcpyHostToDevice, s));
       CK(cudaMemcpyAsync(ctx->iso32, iso32.data(), iso32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(ctx->isodf, isodf.data(), isodf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-      CK(cudaStreamSynchronize(s));  // the host copies above are locals
+      if (physics == FEHOM_ELASTIC) {
+        // double-float copy of the six constants, hi = fl(v), lo = fl(v - hi) (refinement residuals)
+        std::vector<float> isodf((size_t)16 * n_phases, 0.0f);
+        for (int p = 0; p < n_phases; ++p)
+          for (int i = 0; i < 6; ++i) {
+            const double v = iso[(size_t)kIsoStride * p + i];
+            const float hi = (float)v;
+            isodf[(size_t)16 * p + 2 * i] = hi;
+            isodf[(size_t)16 * p + 2 * i + 1] = (float)(v - (double)hi);
+          }
+        CK(cudaMalloc(&ctx->isodf, isodf.size() * sizeof(float)));
+        CK(cudaMemcpyAsync(ctx->isodf, isodf.data(), isodf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));  // isodf is a local
+      }
+      CK(cudaStreamSynchronize(s));  // iso and iso32 are locals
     }
-    double lam, mu;
-    if (iso_elastic(ctx->cref.data(), 3, &lam, &mu)) {
+    double ri[kIsoStride];
+    if (iso_material(ctx, ctx->cref.data(), ri)) {
       ctx->iso_ref = true;
-      double ri[kIsoStride];
-      iso_entry(w * sc[0] * sc[0] * lam, w * sc[0] * sc[0] * mu, ri);
       CK(cudaMalloc(&ctx->riso64, kIsoStride * sizeof(double)));
       CK(cudaMemcpyAsync(ctx->riso64, ri, kIsoStride * sizeof(double), cudaMemcpyHostToDevice, s));
     }

@@ -118,6 +118,12 @@ inline void iso_entry(double lam, double mu, double* out) {
   out[0] = lam; out[1] = mu; out[2] = 2.0 * mu; out[3] = lam / 3.0; out[4] = mu / 3.0;
   out[5] = (lam + 4.0 * mu) / 9.0; out[6] = 0.0; out[7] = 0.0;
 }
+// Scalar conductivity k' I (gradient coordinates): the hex8 duals are k' (q1, q2, q3), (2/3) k' (q4, q5, q6)
+// and (1/3) k' q7 (each of q4..q6 enters two linear monomials weighted 1/3, q7 three bilinear ones weighted 1/9).
+inline void iso_entry_scalar(double k, double* out) {
+  out[0] = k; out[1] = 2.0 * k / 3.0; out[2] = k / 3.0;
+  for (int i = 3; i < kIsoStride; ++i) out[i] = 0.0;
+}
 
 struct StencilArgs {
   Dims d;
@@ -125,7 +131,7 @@ struct StencilArgs {
   void* y;              // [load][c][N]
   const uint8_t* ids;   // [N]; nullptr = every voxel is phase 0 (uniform material)
   const void* mats;     // [phase][D*D] gradient-space material, T
-  const void* iso;      // [phase][kIsoStride] (iso_entry) for the isotropic cubic fast path, or nullptr
+  const void* iso;      // [phase][kIsoStride] (iso_entry / iso_entry_scalar) for the isotropic cubic fast path, or nullptr
   const double* tau;    // [load][phase][D] prestress of the macroscopic load (FP64), or nullptr
   int n_phases;
   int n_loads;

@@ -205,7 +205,24 @@ __device__ __forceinline__ void hex8_element_faces(const T (&bot)[C][4], const T
       q4[j] = top[j][3] + bot[j][3];
       q7[j] = top[j][3] - bot[j][3];
     }
-    if constexpr (ISO && C == 3) {
+    if constexpr (ISO && C == 1) {
+      // isotropic conductivity: the duals scale the modal coefficients (iso_entry_scalar)
+      T k1, k23, k3;
+      if constexpr (sizeof(T) == 4) {
+        const float4 c0 = __ldg(reinterpret_cast<const float4*>(iso));
+        k1 = c0.x; k23 = c0.y; k3 = c0.z;
+      } else {
+        const double2 c0 = __ldg(reinterpret_cast<const double2*>(iso));
+        k1 = c0.x; k23 = c0.y; k3 = __ldg(iso + 2);
+      }
+      Q1[0] = k1 * q1[0];
+      Q2[0] = k1 * q2[0];
+      Q3[0] = k1 * q3[0];
+      Q4[0] = k23 * q4[0];
+      Q5[0] = k23 * q5[0];
+      Q6[0] = k23 * q6[0];
+      Q7[0] = k3 * q7[0];
+    } else if constexpr (ISO && C == 3) {
       T lam, mu, mu2, L, M, K7;
       if constexpr (sizeof(T) == 4) {  // one entry = 8 floats, 32-byte aligned: two 16-byte loads
         const float4 c0 = __ldg(reinterpret_cast<const float4*>(iso));
@@ -1524,7 +1541,7 @@ template <typename T>
 cudaError_t launch_stiffness(const StencilArgs& a, cudaStream_t s, int* ctas) {
   const Dims& d = a.d;
   if (d.elem == HEX8_3D) {
-    if (d.c == 1) return dispatch_hex8<T, 1, false>(a, ctas, s);
+    if (d.c == 1) return a.iso ? dispatch_hex8<T, 1, true>(a, ctas, s) : dispatch_hex8<T, 1, false>(a, ctas, s);
     if (a.iso) return dispatch_hex8<T, 3, true>(a, ctas, s);
     return dispatch_hex8<T, 3, false>(a, ctas, s);
   }
