@@ -160,7 +160,7 @@ def kernel_model(s, c=3):
 
 FP64_INSTR_PEAK = 152 * 2 * 2.07e9     # FP64 instructions/s: 152 SMs x 2 FP64 lanes-per-clock x max clock
 # DRAM bytes (read + write) of one 6-load FP64 stiffness launch on the 128^3 workload, from ncu
-FP64_STIFFNESS_DRAM_BYTES = 324.482560e6 + 263.110144e6
+FP64_STIFFNESS_DRAM_BYTES = 324.537088e6 + 264.050432e6
 
 
 def run_ours(args):
