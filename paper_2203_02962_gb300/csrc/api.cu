@@ -329,7 +329,7 @@ void fill_dims_args(fehom_ctx* ctx, FftArgs& f, bool fp32, int n_loads) {
   f.herm = ctx->d.elem == P1TRI4_2D ? 1 : 0;
   f.xy = (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.xy)) && fft_xy_supported(ctx->d, fp32) ? 1 : 0;
   f.last_reg =
-      (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.last_reg)) && fft_last128_supported(ctx->d, fp32) ? 1 : 0;
+      (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.last_reg)) && fft_last_rs_supported(ctx->d, fp32) ? 1 : 0;
 }
 
 // Removes the constant null mode from every load's field: the mean of each component, or for the
@@ -524,7 +524,7 @@ fehom_status autotune_fft(fehom_ctx* ctx, int n_loads) {
   auto& pl = ctx->plan[prec];
   if (!ctx->opt.autotune || pl.tuned_loads == n_loads) return FEHOM_OK;
   // register-split passes forced on every axis: the generic passes are not used, nothing to time
-  if (prec == 1 && ctx->opt.fft_xy == 1 && fft_xy_supported(ctx->d, true) && fft_last128_supported(ctx->d, true)) {
+  if (prec == 1 && ctx->opt.fft_xy == 1 && fft_xy_supported(ctx->d, true) && fft_last_rs_supported(ctx->d, true)) {
     pl.tuned_loads = n_loads;
     return FEHOM_OK;
   }
@@ -623,7 +623,7 @@ fehom_status autotune_fft(fehom_ctx* ctx, int n_loads) {
     }
   }
   int last_reg = 0;
-  if (ctx->opt.fft_xy < 0 && fft_last128_supported(ctx->d, prec == 1)) {
+  if (ctx->opt.fft_xy < 0 && fft_last_rs_supported(ctx->d, prec == 1)) {
     const double mreg = timeit([&] {
       FftArgs f = base;
       f.last_reg = 1;
@@ -641,7 +641,7 @@ fehom_status autotune_fft(fehom_ctx* ctx, int n_loads) {
   pl.tc_y = by;
   pl.tc_last = bl;
   pl.xy = ctx->opt.fft_xy == 1 ? (fft_xy_supported(ctx->d, prec == 1) ? 1 : 0) : xy;
-  pl.last_reg = ctx->opt.fft_xy == 1 ? (fft_last128_supported(ctx->d, prec == 1) ? 1 : 0) : last_reg;
+  pl.last_reg = ctx->opt.fft_xy == 1 ? (fft_last_rs_supported(ctx->d, prec == 1) ? 1 : 0) : last_reg;
   pl.ms[0] = mp;
   pl.ms[1] = my;
   pl.ms[2] = ml;
@@ -1143,7 +1143,7 @@ fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int
   if (xy_fused) {
     const bool fp32 = precision == FEHOM_MIXED;
     const int a = (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.xy)) && fft_xy_supported(ctx->d, fp32);
-    const int b = (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.last_reg)) && fft_last128_supported(ctx->d, fp32);
+    const int b = (ctx->opt.fft_xy == 1 || (ctx->opt.fft_xy < 0 && pl.last_reg)) && fft_last_rs_supported(ctx->d, fp32);
     *xy_fused = a | (b << 1);
   }
   if (pairs) *pairs = pl.pairs;

@@ -583,29 +583,70 @@ __global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, const
 
 
 // ------------------------------------------------------------------------------------------------
-// Fused x-y passes for FP32 fields with 128 x 128 planes (3-D): one CTA transforms one z-plane of one
-// component, so the half spectrum crosses HBM once per direction instead of twice.  Each 128-point
-// transform is split 128 = 16 x 8: a 16-point DFT in registers over the stride-8 subsequence, the
-// twiddles W_128^(j k1), one shared-memory exchange, then 8-point DFTs (output index k1 + 16 k2).
+// Register-split FP32 passes for axes of N = 16 Q points (N = 32, 64, 96 or 128).  Each transform is
+// split N = 16 x Q: a 16-point DFT in registers over the stride-Q subsequence, the twiddles
+// W_N^(j k1), one shared-memory exchange, then Q-point DFTs (output index k1 + 16 k2).
+// Fused x-y passes for 3-D fields with N x N planes: one CTA transforms one z-plane of one
+// component, so the half spectrum crosses HBM once per direction instead of twice.
 //   forward: rows 2q, 2q+1 -> one complex line (fused r -= alpha Ap); the y pass splits the two half
-//            spectra on the fly; the real columns kx = 0 and kx = 64 share one complex column and are
-//            separated after the transform.
-//   inverse: columns kx = 0 and kx = 64 (whose inverse transforms are real) share one complex column;
-//            the x pass completes the Hermitian lines and applies the PCG updates of FX_PCG.
+//            spectra on the fly; the real columns kx = 0 and kx = N/2 share one complex column and
+//            are separated after the transform.
+//   inverse: columns kx = 0 and kx = N/2 (whose inverse transforms are real) share one complex
+//            column; the x pass completes the Hermitian lines and applies the PCG updates of FX_PCG.
+// Threads 4 N: the 16 N stage-2 tasks of a pass (N/2 lines or columns x 16 k1) in two rounds; the
+// N^2/32 16-point DFTs of stage 1 (N/2 lines x Q subsequences) use all of them for N = 128 and
+// 3/4, 1/2, 1/4 of them for N = 96, 64, 32.
 // ------------------------------------------------------------------------------------------------
-constexpr int XY_N = 128, XY_H = 65, XY_THREADS = 512;
-constexpr int XY_LDQ = 148;  // line stride (complex) of the x-pass buffer: [k1][9] per line, padded
-constexpr int XY_LDT = 145;  // column stride of the y-pass buffer: [k1][9] per column, padded
-constexpr int XY_LDP = 66;   // row stride of the y-inverse result plane (64 columns used)
-constexpr int XY_BUF = 64 * XY_LDQ;
-constexpr size_t XY_SMEM = (XY_BUF + XY_N) * sizeof(float2);
-// Row staging of the x passes: the 64 line pairs of a plane as two float arrays (rows 2q and 2q+1),
-// aliasing the line buffer.  Global rows move with coalesced 16-byte accesses (one warp per line
-// pair) and the stride-8 subsequences are gathered in shared memory.  Row strides: 136 floats put
-// the 4 line pairs read by a warp in the forward gather on disjoint banks; 144 does the same for the
-// 2 line pairs a warp writes in the inverse.
-constexpr int XY_LDF_F = 136, XY_LDF_I = 144;
-static_assert(2 * 64 * XY_LDF_I <= 2 * XY_BUF, "row staging must fit in the line buffer");
+template <int N>
+struct RS {
+  static_assert(N == 32 || N == 64 || N == 96 || N == 128, "register-split axis lengths: 32, 64, 96, 128");
+  static constexpr int Q = N / 16;   // the Q-point stage
+  static constexpr int H = N / 2 + 1;  // half-spectrum width
+  static constexpr int NP = N / 2;   // line pairs of the x pass, packed columns of the y pass
+  static constexpr int NT = 4 * N;   // threads of the fused x-y passes
+  static constexpr int MIN_CTAS = 1152 / NT > 2 ? 1152 / NT : 2;  // resident CTAs per SM the registers allow
+  // Shared-memory strides (complex unless noted), padded against bank conflicts (the 128 values
+  // measured, the others picked with a bank model of these access patterns):
+  //   LDQ  line stride of the x-pass buffer, [k1][Q + 1] per line
+  //   LDT  column stride of the y-pass buffer, [k1][Q + 1] per column
+  //   LDP  row stride of the y-inverse result plane (N/2 columns used)
+  //   LDF_F, LDF_I  row strides (floats) of the forward / inverse row staging, which aliases the
+  //   line buffer: the N/2 line pairs as two float arrays (rows 2q and 2q + 1)
+  static constexpr int LDQ = N == 128 ? 148 : N == 96 ? 118 : N == 64 ? 84 : 50;
+  static constexpr int LDT = N == 128 ? 145 : N == 96 ? 113 : N == 64 ? 81 : 49;
+  static constexpr int LDP = N == 128 ? 66 : N == 96 ? 50 : N == 64 ? 34 : 17;
+  static constexpr int LDF_F = N == 128 ? 136 : N == 96 ? 100 : N == 64 ? 68 : 36;
+  static constexpr int LDF_I = N == 128 ? 144 : N == 96 ? 112 : N == 64 ? 80 : 48;
+  static constexpr int BUF = NP * LDQ;
+  static constexpr size_t SMEM = (BUF + N) * sizeof(float2);
+  static_assert(LDQ >= 16 * (Q + 1) && LDT >= 16 * (Q + 1) && LDP >= NP, "strides hold their rows");
+  static_assert(LDF_F >= N && LDF_I >= N && LDF_F % 4 == 0 && LDF_I % 4 == 0, "16-byte aligned float rows");
+  static_assert(2 * NP * LDF_F <= 2 * BUF && 2 * NP * LDF_I <= 2 * BUF, "row staging fits in the line buffer");
+  static_assert(N * LDP <= BUF && NT * 2 == NP * 16, "y-inverse plane fits; two stage-2 rounds");
+};
+
+template <typename C, bool INV> struct Dft<C, 6, INV> {
+  // one radix-2 decimation-in-frequency step, then two 3-point DFTs
+  __device__ static void run(C (&v)[6]) {
+    using T = decltype(C::x);
+    const T h = T(0.5), s3 = T(0.86602540378443864676);  // W_6 = (1/2, -sin(pi/3)) forward
+    C a[3], b[3];
+#pragma unroll
+    for (int n = 0; n < 3; ++n) {
+      a[n] = cadd(v[n], v[n + 3]);
+      b[n] = csub(v[n], v[n + 3]);
+    }
+    b[1] = cmul(b[1], mk<C>(h, INV ? s3 : -s3));
+    b[2] = cmul(b[2], mk<C>(-h, INV ? s3 : -s3));
+    Dft<C, 3, INV>::run(a);
+    Dft<C, 3, INV>::run(b);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      v[2 * k] = a[k];
+      v[2 * k + 1] = b[k];
+    }
+  }
+};
 
 // 16-point DFT in registers, natural order in and out: n = n1 + 4 n2, k = 4 k1 + k2
 template <bool INV>
@@ -642,35 +683,38 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
   }
 }
 
-template <bool UPDATE>
-__global__ void __launch_bounds__(XY_THREADS, 2) fft_xy_fwd128_kernel(FftArgs a) {
+template <int N, bool UPDATE>
+__global__ void __launch_bounds__(RS<N>::NT, RS<N>::MIN_CTAS) fft_xy_fwd_rs_kernel(FftArgs a) {
+  using P = RS<N>;
+  constexpr int Q = P::Q, NP = P::NP, NT = P::NT, H = P::H;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* S = reinterpret_cast<float2*>(smem_raw);
-  float2* Cz = S + XY_BUF;
+  float2* Cz = S + P::BUF;
   const int z = blockIdx.x, comp = blockIdx.y, load = blockIdx.z;
   if (UPDATE && !first_half_active(a.st, load)) return;
-  const long long foff = (long long)load * a.load_stride_f + (long long)comp * a.d.N + (long long)z * XY_N * XY_N;
+  const long long foff = (long long)load * a.load_stride_f + (long long)comp * a.d.N + (long long)z * N * N;
   float* r = reinterpret_cast<float*>(a.f0) + foff;
   const float* ap = UPDATE ? reinterpret_cast<const float*>(a.f1) + foff : nullptr;
   float2* spec = reinterpret_cast<float2*>(a.spec) + (long long)load * a.load_stride_s + (long long)comp * a.d.Nh +
-                 (long long)z * XY_N * XY_H;
+                 (long long)z * N * H;
   const float alpha = UPDATE ? float(a.st[load].alpha) : 0.0f;
   const float2* twx = reinterpret_cast<const float2*>(a.tw.x);
   const float2* twy = reinterpret_cast<const float2*>(a.tw.y);
   const int t = threadIdx.x;
-  {  // x, stage 0: rows to shared memory (one warp per line pair, 16-byte accesses), r -= alpha Ap
+  const bool s1_thread = t < NP * Q;  // stage 1: line (or column pair index) x subsequence
+  {  // x, stage 0: rows to shared memory (16-byte accesses along each row pair), r -= alpha Ap
     float* Rre = reinterpret_cast<float*>(S);
-    float* Rim = Rre + 64 * XY_LDF_F;
+    float* Rim = Rre + NP * P::LDF_F;
 #pragma unroll
-    for (int it = 0; it < 4; ++it) {
-      const int task = t + XY_THREADS * it;
-      const int q = task >> 5, x = 4 * (task & 31);
-      float4* g0 = reinterpret_cast<float4*>(r + 2 * q * XY_N + x);
-      float4* g1 = reinterpret_cast<float4*>(r + (2 * q + 1) * XY_N + x);
+    for (int it = 0; it < N / 32; ++it) {
+      const int task = t + NT * it;
+      const int q = task / (N / 4), x = 4 * (task % (N / 4));
+      float4* g0 = reinterpret_cast<float4*>(r + 2 * q * N + x);
+      float4* g1 = reinterpret_cast<float4*>(r + (2 * q + 1) * N + x);
       float4 v0 = *g0, v1 = *g1;
       if (UPDATE) {
-        const float4 a0 = __ldg(reinterpret_cast<const float4*>(ap + 2 * q * XY_N + x));
-        const float4 a1 = __ldg(reinterpret_cast<const float4*>(ap + (2 * q + 1) * XY_N + x));
+        const float4 a0 = __ldg(reinterpret_cast<const float4*>(ap + 2 * q * N + x));
+        const float4 a1 = __ldg(reinterpret_cast<const float4*>(ap + (2 * q + 1) * N + x));
         v0 = make_float4(fmaf(-alpha, a0.x, v0.x), fmaf(-alpha, a0.y, v0.y), fmaf(-alpha, a0.z, v0.z),
                          fmaf(-alpha, a0.w, v0.w));
         v1 = make_float4(fmaf(-alpha, a1.x, v1.x), fmaf(-alpha, a1.y, v1.y), fmaf(-alpha, a1.z, v1.z),
@@ -678,193 +722,208 @@ __global__ void __launch_bounds__(XY_THREADS, 2) fft_xy_fwd128_kernel(FftArgs a)
         *g0 = v0;
         *g1 = v1;
       }
-      *reinterpret_cast<float4*>(Rre + q * XY_LDF_F + x) = v0;
-      *reinterpret_cast<float4*>(Rim + q * XY_LDF_F + x) = v1;
+      *reinterpret_cast<float4*>(Rre + q * P::LDF_F + x) = v0;
+      *reinterpret_cast<float4*>(Rim + q * P::LDF_F + x) = v1;
     }
   }
   __syncthreads();
   {  // x, stage 1: line q = rows (2q, 2q+1), subsequence j
-    const int q = t >> 3, j = t & 7;
-    const float* Rre = reinterpret_cast<const float*>(S) + q * XY_LDF_F + j;
-    const float* Rim = Rre + 64 * XY_LDF_F;
+    const int q = t / Q, j = t % Q;
     float2 v[16];
+    if (s1_thread) {
+      const float* Rre = reinterpret_cast<const float*>(S) + q * P::LDF_F + j;
+      const float* Rim = Rre + NP * P::LDF_F;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = make_float2(Rre[8 * m], Rim[8 * m]);
+      for (int m = 0; m < 16; ++m) v[m] = make_float2(Rre[Q * m], Rim[Q * m]);
+    }
     __syncthreads();  // every row has been gathered before the line buffer overwrites it
-    dft16<false>(v);
-    float2* Sq = S + q * XY_LDQ;
+    if (s1_thread) {
+      dft16<false>(v);
+      float2* Sq = S + q * P::LDQ;
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) Sq[k1 * 9 + j] = k1 == 0 ? v[0] : cmul(v[k1], __ldg(twx + j * k1));
+      for (int k1 = 0; k1 < 16; ++k1) Sq[k1 * (Q + 1) + j] = k1 == 0 ? v[0] : cmul(v[k1], __ldg(twx + j * k1));
+    }
   }
   __syncthreads();
 #pragma unroll
   for (int round = 0; round < 2; ++round) {  // x, stage 2: a warp holds both lines it rewrites
-    const int task = t + XY_THREADS * round;
+    const int task = t + NT * round;
     const int q = task >> 4, k1 = task & 15;
-    float2* Sq = S + q * XY_LDQ;
-    float2 v[8];
+    float2* Sq = S + q * P::LDQ;
+    float2 v[Q];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = Sq[k1 * 9 + j];
+    for (int j = 0; j < Q; ++j) v[j] = Sq[k1 * (Q + 1) + j];
     __syncwarp();
-    Dft<float2, 8, false>::run(v);
+    Dft<float2, Q, false>::run(v);
 #pragma unroll
-    for (int k2 = 0; k2 < 8; ++k2) Sq[k1 + 16 * k2] = v[k2];
+    for (int k2 = 0; k2 < Q; ++k2) Sq[k1 + 16 * k2] = v[k2];
     __syncwarp();
   }
   __syncthreads();
-  {  // y, stage 1: column kx (kx = 0 carries kx = 0 and kx = 64), subsequence j of the rows
-    const int kx = t & 63, j = t >> 6;
-    const int sodd = j & 1, q0 = j >> 1;
+  {  // y, stage 1: column kx (kx = 0 carries kx = 0 and kx = N/2), subsequence j of the rows
+    const int kx = t % NP, j = t / NP;
+    const int sodd = j & 1, q0 = j >> 1;  // row j + Q m = 2 (q0 + (Q/2) m) + sodd (Q is even)
     float2 v[16];
+    if (s1_thread) {
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const float2* Sq = S + (q0 + 4 * m) * XY_LDQ;
-      if (kx == 0) {
-        const float2 z0 = Sq[0], z64 = Sq[64];
-        v[m] = sodd ? make_float2(z0.y, z64.y) : make_float2(z0.x, z64.x);
-      } else {
-        const float2 zk = Sq[kx], zn = Sq[XY_N - kx];
-        v[m] = sodd ? make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x))
-                    : make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+      for (int m = 0; m < 16; ++m) {
+        const float2* Sq = S + (q0 + (Q / 2) * m) * P::LDQ;
+        if (kx == 0) {
+          const float2 z0 = Sq[0], zh = Sq[NP];
+          v[m] = sodd ? make_float2(z0.y, zh.y) : make_float2(z0.x, zh.x);
+        } else {
+          const float2 zk = Sq[kx], zn = Sq[N - kx];
+          v[m] = sodd ? make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x))
+                      : make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+        }
       }
     }
     __syncthreads();  // every line has been read before the column buffer overwrites it
-    dft16<false>(v);
-    float2* Tc = S + kx * XY_LDT;
+    if (s1_thread) {
+      dft16<false>(v);
+      float2* Tc = S + kx * P::LDT;
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) Tc[k1 * 9 + j] = k1 == 0 ? v[0] : cmul(v[k1], __ldg(twy + j * k1));
+      for (int k1 = 0; k1 < 16; ++k1) Tc[k1 * (Q + 1) + j] = k1 == 0 ? v[0] : cmul(v[k1], __ldg(twy + j * k1));
+    }
   }
   __syncthreads();
 #pragma unroll
   for (int round = 0; round < 2; ++round) {  // y, stage 2 -> half spectrum (packed column to Cz)
-    const int task = t + XY_THREADS * round;
-    const int kx = task & 63, k1 = task >> 6;
-    const float2* Tc = S + kx * XY_LDT;
-    float2 v[8];
+    const int task = t + NT * round;
+    const int kx = task % NP, k1 = task / NP;
+    const float2* Tc = S + kx * P::LDT;
+    float2 v[Q];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = Tc[k1 * 9 + j];
-    Dft<float2, 8, false>::run(v);
+    for (int j = 0; j < Q; ++j) v[j] = Tc[k1 * (Q + 1) + j];
+    Dft<float2, Q, false>::run(v);
 #pragma unroll
-    for (int k2 = 0; k2 < 8; ++k2) {
+    for (int k2 = 0; k2 < Q; ++k2) {
       const int ky = k1 + 16 * k2;
       if (kx == 0) Cz[ky] = v[k2];
-      else spec[ky * XY_H + kx] = v[k2];
+      else spec[ky * H + kx] = v[k2];
     }
   }
   __syncthreads();
-  if (t < XY_N) {  // separate the spectra of the real columns kx = 0 and kx = 64
-    const float2 c = Cz[t], cn = Cz[(XY_N - t) & (XY_N - 1)];
-    spec[t * XY_H] = make_float2(0.5f * (c.x + cn.x), 0.5f * (c.y - cn.y));
-    spec[t * XY_H + 64] = make_float2(0.5f * (c.y + cn.y), 0.5f * (cn.x - c.x));
+  if (t < N) {  // separate the spectra of the real columns kx = 0 and kx = N/2
+    const float2 c = Cz[t], cn = Cz[t == 0 ? 0 : N - t];
+    spec[t * H] = make_float2(0.5f * (c.x + cn.x), 0.5f * (c.y - cn.y));
+    spec[t * H + NP] = make_float2(0.5f * (c.y + cn.y), 0.5f * (cn.x - c.x));
   }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(XY_THREADS, 2) fft_xy_inv128_kernel(FftArgs a) {
+template <int N, int MODE>
+__global__ void __launch_bounds__(RS<N>::NT, RS<N>::MIN_CTAS) fft_xy_inv_rs_kernel(FftArgs a) {
+  using P = RS<N>;
+  constexpr int Q = P::Q, NP = P::NP, NT = P::NT, H = P::H;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_sh[32];
   float2* S = reinterpret_cast<float2*>(smem_raw);
   const int z = blockIdx.x, comp = blockIdx.y, load = blockIdx.z;
   if (MODE != FX_PLAIN && !second_half_active(a.st, load)) return;
-  const long long foff = (long long)load * a.load_stride_f + (long long)comp * a.d.N + (long long)z * XY_N * XY_N;
+  const long long foff = (long long)load * a.load_stride_f + (long long)comp * a.d.N + (long long)z * N * N;
   const float2* spec = reinterpret_cast<const float2*>(a.spec) + (long long)load * a.load_stride_s +
-                       (long long)comp * a.d.Nh + (long long)z * XY_N * XY_H;
+                       (long long)comp * a.d.Nh + (long long)z * N * H;
   const float2* twx = reinterpret_cast<const float2*>(a.tw.x);
   const float2* twy = reinterpret_cast<const float2*>(a.tw.y);
   const int t = threadIdx.x;
-  {  // y inverse, stage 1: column kx (kx = 0 carries kx = 0 and kx = 64 as real and imaginary parts)
-    const int kx = t & 63, j = t >> 6;
+  const bool s1_thread = t < NP * Q;
+  if (s1_thread) {  // y inverse, stage 1: column kx (kx = 0 carries kx = 0 and kx = N/2 as real and imaginary parts)
+    const int kx = t % NP, j = t / NP;
     float2 v[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-      const int ky = j + 8 * m;
+      const int ky = j + Q * m;
       if (kx == 0) {
-        const float2 s0 = spec[ky * XY_H], s64 = spec[ky * XY_H + 64];
-        v[m] = make_float2(s0.x - s64.y, s0.y + s64.x);
+        const float2 s0 = spec[ky * H], sh = spec[ky * H + NP];
+        v[m] = make_float2(s0.x - sh.y, s0.y + sh.x);
       } else {
-        v[m] = spec[ky * XY_H + kx];
+        v[m] = spec[ky * H + kx];
       }
     }
     dft16<true>(v);
-    float2* Tc = S + kx * XY_LDT;
+    float2* Tc = S + kx * P::LDT;
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) Tc[k1 * 9 + j] = k1 == 0 ? v[0] : cmulc(v[k1], __ldg(twy + j * k1));
+    for (int k1 = 0; k1 < 16; ++k1) Tc[k1 * (Q + 1) + j] = k1 == 0 ? v[0] : cmulc(v[k1], __ldg(twy + j * k1));
   }
   __syncthreads();
   {  // y inverse, stage 2 -> plane P[y][kx]
-    float2 w[2][8];
+    float2 w[2][Q];
 #pragma unroll
     for (int round = 0; round < 2; ++round) {
-      const int task = t + XY_THREADS * round;
-      const int kx = task & 63, k1 = task >> 6;
+      const int task = t + NT * round;
+      const int kx = task % NP, k1 = task / NP;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) w[round][j] = S[kx * XY_LDT + k1 * 9 + j];
+      for (int j = 0; j < Q; ++j) w[round][j] = S[kx * P::LDT + k1 * (Q + 1) + j];
     }
     __syncthreads();
 #pragma unroll
     for (int round = 0; round < 2; ++round) {
-      const int task = t + XY_THREADS * round;
-      const int kx = task & 63, k1 = task >> 6;
-      Dft<float2, 8, true>::run(w[round]);
+      const int task = t + NT * round;
+      const int kx = task % NP, k1 = task / NP;
+      Dft<float2, Q, true>::run(w[round]);
 #pragma unroll
-      for (int k2 = 0; k2 < 8; ++k2) S[(k1 + 16 * k2) * XY_LDP + kx] = w[round][k2];
+      for (int k2 = 0; k2 < Q; ++k2) S[(k1 + 16 * k2) * P::LDP + kx] = w[round][k2];
     }
   }
   __syncthreads();
   {  // x inverse, stage 1: line q = rows (2q, 2q+1), Hermitian completion, Z = A + i B
-    const int q = t >> 3, j = t & 7;
-    const float2* PA = S + 2 * q * XY_LDP;
-    const float2* PB = PA + XY_LDP;
+    const int q = t / Q, j = t % Q;
     float2 v[16];
+    if (s1_thread) {
+      const float2* PA = S + 2 * q * P::LDP;
+      const float2* PB = PA + P::LDP;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int k = j + 8 * m;
-      float2 A, B;
-      if (k == 0) {
-        A = make_float2(PA[0].x, 0.0f);
-        B = make_float2(PB[0].x, 0.0f);
-      } else if (k == 64) {
-        A = make_float2(PA[0].y, 0.0f);
-        B = make_float2(PB[0].y, 0.0f);
-      } else if (k < 64) {
-        A = PA[k];
-        B = PB[k];
-      } else {
-        A = PA[XY_N - k];
-        B = PB[XY_N - k];
-        A.y = -A.y;
-        B.y = -B.y;
+      for (int m = 0; m < 16; ++m) {
+        const int k = j + Q * m;
+        float2 A, B;
+        if (k == 0) {
+          A = make_float2(PA[0].x, 0.0f);
+          B = make_float2(PB[0].x, 0.0f);
+        } else if (k == NP) {
+          A = make_float2(PA[0].y, 0.0f);
+          B = make_float2(PB[0].y, 0.0f);
+        } else if (k < NP) {
+          A = PA[k];
+          B = PB[k];
+        } else {
+          A = PA[N - k];
+          B = PB[N - k];
+          A.y = -A.y;
+          B.y = -B.y;
+        }
+        v[m] = make_float2(A.x - B.y, A.y + B.x);
       }
-      v[m] = make_float2(A.x - B.y, A.y + B.x);
     }
     __syncthreads();  // the plane has been read before the line buffer overwrites it
-    dft16<true>(v);
-    float2* Sq = S + q * XY_LDQ;
+    if (s1_thread) {
+      dft16<true>(v);
+      float2* Sq = S + q * P::LDQ;
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) Sq[k1 * 9 + j] = k1 == 0 ? v[0] : cmulc(v[k1], __ldg(twx + j * k1));
+      for (int k1 = 0; k1 < 16; ++k1) Sq[k1 * (Q + 1) + j] = k1 == 0 ? v[0] : cmulc(v[k1], __ldg(twx + j * k1));
+    }
   }
   __syncthreads();
-  {  // x inverse, stage 2: 8-point DFTs, rows (2q, 2q+1) of z to the row buffers (aliasing the lines)
-    float2 w[2][8];
+  {  // x inverse, stage 2: Q-point DFTs, rows (2q, 2q+1) of z to the row buffers (aliasing the lines)
+    float2 w[2][Q];
 #pragma unroll
     for (int round = 0; round < 2; ++round) {
-      const int task = t + XY_THREADS * round;
+      const int task = t + NT * round;
       const int q = task >> 4, k1 = task & 15;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) w[round][j] = S[q * XY_LDQ + k1 * 9 + j];
+      for (int j = 0; j < Q; ++j) w[round][j] = S[q * P::LDQ + k1 * (Q + 1) + j];
     }
     __syncthreads();  // every line has been read before the row buffers overwrite it
     float* Rre = reinterpret_cast<float*>(S);
-    float* Rim = Rre + 64 * XY_LDF_I;
+    float* Rim = Rre + NP * P::LDF_I;
 #pragma unroll
     for (int round = 0; round < 2; ++round) {
-      const int task = t + XY_THREADS * round;
+      const int task = t + NT * round;
       const int q = task >> 4, k1 = task & 15;
-      Dft<float2, 8, true>::run(w[round]);
+      Dft<float2, Q, true>::run(w[round]);
 #pragma unroll
-      for (int k2 = 0; k2 < 8; ++k2) {
-        Rre[q * XY_LDF_I + k1 + 16 * k2] = w[round][k2].x;
-        Rim[q * XY_LDF_I + k1 + 16 * k2] = w[round][k2].y;
+      for (int k2 = 0; k2 < Q; ++k2) {
+        Rre[q * P::LDF_I + k1 + 16 * k2] = w[round][k2].x;
+        Rim[q * P::LDF_I + k1 + 16 * k2] = w[round][k2].y;
       }
     }
   }
@@ -874,12 +933,12 @@ __global__ void __launch_bounds__(XY_THREADS, 2) fft_xy_inv128_kernel(FftArgs a)
   const float alpha = (MODE == FX_PCG) ? float(a.st[load].alpha) : 0.0f;
   const float beta = (MODE == FX_PCG) ? float(a.st[load].beta) : 0.0f;
 #pragma unroll
-  for (int it = 0; it < 8; ++it) {  // rows to global memory (one warp per row, 16-byte accesses), PCG updates
-    const int task = t + XY_THREADS * it;
-    const int row = task >> 5, x = 4 * (task & 31);
-    const float* R = reinterpret_cast<const float*>(S) + (row & 1) * 64 * XY_LDF_I + (row >> 1) * XY_LDF_I + x;
+  for (int it = 0; it < N / 16; ++it) {  // rows to global memory (16-byte accesses along each row), PCG updates
+    const int task = t + NT * it;
+    const int row = task / (N / 4), x = 4 * (task % (N / 4));
+    const float* R = reinterpret_cast<const float*>(S) + (row & 1) * NP * P::LDF_I + (row >> 1) * P::LDF_I + x;
     const float4 zv = *reinterpret_cast<const float4*>(R);
-    const long long g = (long long)row * XY_N + x;
+    const long long g = (long long)row * N + x;
     if (MODE == FX_PLAIN) {
       *reinterpret_cast<float4*>(f0 + g) = zv;
     } else if (MODE == FX_PCG_INIT) {
@@ -912,38 +971,34 @@ __global__ void __launch_bounds__(XY_THREADS, 2) fft_xy_inv128_kernel(FftArgs a)
   }
 }
 
-
-// Last axis (z) of FP32 3-D fields with nz = 128, 16 columns x NC components per CTA, with the block
-// solve: the same 16 x 8 split as the fused x-y passes.  Stage 1: 16-point DFTs of the stride-8 z
-// subsequences read straight from the spectrum; stage 2 (one thread per column and k1): 8-point DFTs
-// giving the NC components at kz = k1 + 16 k2, the block solve and the Parseval sum in registers, and
-// the first half of the inverse (8-point inverse DFTs, conjugate twiddles); stage 3: 16-point inverse
-// DFTs written straight back.  Shared memory is touched twice per direction instead of once per
-// radix stage.
-// Threads: 128 per component for stages 1 and 3, at least 256 (16 columns x 16 k1) for stage 2.
-// The CTA's slice of the packed symbol (16 columns x 128 kz x 1 or 6 entries) is fetched into shared
-// memory by cp.async while stage 1 runs; the grid runs the loads of one column group next to each
-// other (load = blockIdx.x), so the slice is read from HBM once and from L2 by the other loads.
+// Last axis (z) of FP32 3-D fields with nz = N = 16 Q (32, 64, 96 or 128), 16 columns x NC components
+// per CTA, with the block solve: the same 16 x Q split as the fused x-y passes.  Stage 1: 16-point
+// DFTs of the stride-Q z subsequences read straight from the spectrum; stage 2, in place on every
+// thread: (a) the Q-point DFTs of the 16 NC (k1, c) lines of each column, (b) the block solve and the
+// Parseval sum at each wavevector kz = k1 + 16 k2, (c) the Q-point inverse DFTs with the conjugate
+// twiddles; stage 3: 16-point inverse DFTs written straight back.  Shared memory is touched twice per
+// direction instead of once per radix stage.  The symbol entries are read from L2 at the block
+// solve: the grid runs the loads of one column group next to each other (load = blockIdx.x), so the
+// slice comes from HBM once.
+// Threads: 16 Q NC for stages 1 and 3, at least 256 (16 columns x 16 k1) for stage 2, a multiple of 32.
 // Requires ny * nxh to be a multiple of 16 (no partial column groups).
-template <int NC>
-__host__ __device__ constexpr int last128_threads() { return NC == 1 ? 256 : 128 * NC; }
-template <int NC>
-__host__ __device__ constexpr size_t last128_smem() {
-  return (size_t)NC * 16 * 8 * 16 * sizeof(float2);
+template <int N, int NC>
+__host__ __device__ constexpr int last_rs_threads() {
+  return 16 * (N / 16) * NC > 256 ? (16 * (N / 16) * NC + 31) / 32 * 32 : 256;
+}
+template <int N, int NC>
+__host__ __device__ constexpr size_t last_rs_smem() {
+  return (size_t)NC * 16 * (N / 16) * 16 * sizeof(float2);
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(smem))),
-               "l"(gmem)
-               : "memory");
-}
-
-template <int NC>
-__global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 3 : 4) fft_last128_kernel(FftArgs a) {
-  constexpr int TCL = 16;
+template <int N, int NC>
+__global__ void __launch_bounds__(last_rs_threads<N, NC>(), 1152 / last_rs_threads<N, NC>())
+    fft_last_rs_kernel(FftArgs a) {
+  constexpr int TCL = 16, Q = N / 16;
+  constexpr int NT3 = last_rs_threads<N, NC>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_sh[32];
-  float2* S = reinterpret_cast<float2*>(smem_raw);                // NC * 16 * 8 * 16 complex
+  float2* S = reinterpret_cast<float2*>(smem_raw);  // S[c][k1][slot][t]: NC * 16 * Q * 16 complex
   const int load = blockIdx.x;
   if (!first_half_active(a.st, load)) return;
   float2* spec = reinterpret_cast<float2*>(a.spec) + (long long)load * a.load_stride_s;
@@ -954,48 +1009,47 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 3 : 4) fft_la
   const float2* tw = reinterpret_cast<const float2*>(a.tw.z);
   const float* sym = reinterpret_cast<const float*>(a.sym);
   const int tid = threadIdx.x;
-  if (tid < 128 * NC) {  // stage 1: task (column t, subsequence j, component c)
-    const int t = tid & 15, j = (tid >> 4) & 7, c = tid >> 7;
+  if (tid < 16 * Q * NC) {  // stage 1: task (column t, subsequence j, component c)
+    const int t = tid & 15, j = (tid >> 4) % Q, c = tid / (16 * Q);
     const int cf = cf0 + t;
     float2 v[16];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = spec[c * Nh + cf + (j + 8 * m) * es];
+    for (int m = 0; m < 16; ++m) v[m] = spec[c * Nh + cf + (j + Q * m) * es];
     dft16<false>(v);
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1)
-      S[((c * 16 + k1) * 8 + j) * TCL + t] = k1 == 0 ? v[0] : cmul(v[k1], __ldg(tw + j * k1));
+      S[((c * 16 + k1) * Q + j) * TCL + t] = k1 == 0 ? v[0] : cmul(v[k1], __ldg(tw + j * k1));
   }
   __syncthreads();
-  // stage 2, all threads, in place in S[c][k1][slot][t]: (a) the 8-point forward DFTs over the slot
-  // index (j -> k2) of the 16 NC (k1, c) lines of each column, two per thread for NC = 3; (b) the block
-  // solve z^ = K_hat^+ r^ / N and the Parseval sum <r, z> at every (k1, k2) of the thread's column;
-  // (c) the 8-point inverse DFTs (k2 -> j) with the conjugate twiddles W_128^(j k1) of the inverse split
-  constexpr int NT3 = last128_threads<NC>();
-  constexpr int UNITS = 16 * 16 * NC;  // (t, k1, c) lines of 8 values
-  auto line = [&](int w) { return S + ((w >> 4) * 8) * TCL + (w & 15); };  // w = (c * 16 + k1) * 16 + t
+  // stage 2, all threads, in place in S[c][k1][slot][t]: (a) the Q-point forward DFTs over the slot
+  // index (j -> k2) of the 16 NC (k1, c) lines of each column; (b) the block solve z^ = K_hat^+ r^ / N
+  // and the Parseval sum <r, z> at every (k1, k2) of the thread's column; (c) the Q-point inverse DFTs
+  // (k2 -> j) with the conjugate twiddles W_N^(j k1) of the inverse split
+  constexpr int UNITS = 16 * 16 * NC;  // (t, k1, c) lines of Q values
+  auto line = [&](int w) { return S + ((w >> 4) * Q) * TCL + (w & 15); };  // w = (c * 16 + k1) * 16 + t
 #pragma unroll
   for (int w = tid; w < UNITS; w += NT3) {
     float2* L = line(w);
-    float2 z[8];
+    float2 z[Q];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) z[j] = L[j * TCL];
-    Dft<float2, 8, false>::run(z);
+    for (int j = 0; j < Q; ++j) z[j] = L[j * TCL];
+    Dft<float2, Q, false>::run(z);
 #pragma unroll
-    for (int k2 = 0; k2 < 8; ++k2) L[k2 * TCL] = z[k2];
+    for (int k2 = 0; k2 < Q; ++k2) L[k2 * TCL] = z[k2];
   }
   __syncthreads();
   DotAcc2 dot;
   const int t = tid & 15;  // NT3 is a multiple of 16: every point of this thread lies in column t
   {
     const int kx = (cf0 + t) % nxh;
-    for (int pnt = tid; pnt < 16 * 128; pnt += NT3) {
+    for (int pnt = tid; pnt < 16 * N; pnt += NT3) {
       const int k1 = (pnt >> 4) & 15, k2 = pnt >> 8;
       // the symbol entries of this wavevector, read from L2 where the loads of the column group meet
       // (the grid runs them next to each other): entry e at ks[e * Nh]
       const float* ks = sym + cf0 + t + (long long)(k1 + 16 * k2) * es;
       float2 r[NC], z[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) r[c] = S[((c * 16 + k1) * 8 + k2) * TCL + t];
+      for (int c = 0; c < NC; ++c) r[c] = S[((c * 16 + k1) * Q + k2) * TCL + t];
       // a real symmetric block scales the real and imaginary parts alike: packed FP32x2 products
       auto kk = [](float k) { return make_float2(k, k); };
       if constexpr (NC == 1) {
@@ -1010,7 +1064,7 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 3 : 4) fft_la
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         dot.add(r[c], z[c]);  // the column's Parseval weight is applied to the thread's sum below
-        S[((c * 16 + k1) * 8 + k2) * TCL + t] = z[c];
+        S[((c * 16 + k1) * Q + k2) * TCL + t] = z[c];
       }
     }
     if (kx != 0 && kx != half) dot.scale2();
@@ -1020,24 +1074,24 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 3 : 4) fft_la
   for (int w = tid; w < UNITS; w += NT3) {
     float2* L = line(w);
     const int k1 = (w >> 4) & 15;
-    float2 z[8];
+    float2 z[Q];
 #pragma unroll
-    for (int k2 = 0; k2 < 8; ++k2) z[k2] = L[k2 * TCL];
-    Dft<float2, 8, true>::run(z);
+    for (int k2 = 0; k2 < Q; ++k2) z[k2] = L[k2 * TCL];
+    Dft<float2, Q, true>::run(z);
     L[0] = z[0];
 #pragma unroll
-    for (int j = 1; j < 8; ++j) L[j * TCL] = cmulc(z[j], __ldg(tw + j * k1));
+    for (int j = 1; j < Q; ++j) L[j * TCL] = cmulc(z[j], __ldg(tw + j * k1));
   }
   __syncthreads();
-  if (tid < 128 * NC) {  // stage 3: task (column t, subsequence j, component c): 16-point inverse DFT over k1
-    const int tt = tid & 15, j = (tid >> 4) & 7, c = tid >> 7;
+  if (tid < 16 * Q * NC) {  // stage 3: task (column t, subsequence j, component c): 16-point inverse DFT over k1
+    const int tt = tid & 15, j = (tid >> 4) % Q, c = tid / (16 * Q);
     const int cff = cf0 + tt;
     float2 v[16];
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) v[kk] = S[((c * 16 + kk) * 8 + j) * TCL + tt];
+    for (int kk = 0; kk < 16; ++kk) v[kk] = S[((c * 16 + kk) * Q + j) * TCL + tt];
     dft16<true>(v);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) spec[c * Nh + cff + (j + 8 * m) * es] = v[m];
+    for (int m = 0; m < 16; ++m) spec[c * Nh + cff + (j + Q * m) * es] = v[m];
   }
   if (a.st != nullptr) {
     const double part = block_sum(dot.value(), red_sh);
@@ -1067,6 +1121,7 @@ __global__ void __launch_bounds__(last128_threads<NC>(), NC == 3 ? 3 : 4) fft_la
     }
   }
 }
+
 
 // ------------------------------------------------------------------------------------------------
 // Algorithm 2 tail: packed symbol, checks and per-wavevector inverse
@@ -1336,19 +1391,32 @@ static cudaError_t launch_last_nc(const FftArgs& a, cudaStream_t s) {
                : launch_last_tc<T, NC, false>(a, m, TC, grid, smem, tw, s);
 }
 
-bool fft_last128_supported(const Dims& d, bool fp32) {
-  return fp32 && d.dim == 3 && d.nz == 128 && (d.c == 1 || d.c == 3) && (d.ny * d.nxh) % 16 == 0;
+static bool rs_length(int n) { return n == 32 || n == 64 || n == 96 || n == 128; }
+
+bool fft_last_rs_supported(const Dims& d, bool fp32) {
+  return fp32 && d.dim == 3 && rs_length(d.nz) && (d.c == 1 || d.c == 3) && (d.ny * d.nxh) % 16 == 0;
+}
+
+template <int N>
+static cudaError_t launch_last_rs(const FftArgs& a, dim3 grid, cudaStream_t s) {
+  if (a.d.c == 1) return launch_with_smem(fft_last_rs_kernel<N, 1>, grid, last_rs_threads<N, 1>(), last_rs_smem<N, 1>(), s, a);
+  return launch_with_smem(fft_last_rs_kernel<N, 3>, grid, last_rs_threads<N, 3>(), last_rs_smem<N, 3>(), s, a);
 }
 
 template <typename T>
 cudaError_t launch_fft_last_solve(const FftArgs& a, cudaStream_t s) {
-  if (sizeof(T) == 4 && a.last_reg && a.sym && fft_last128_supported(a.d, true)) {
+  if (sizeof(T) == 4 && a.last_reg && a.sym && fft_last_rs_supported(a.d, true)) {
     const int groups = (a.d.ny * a.d.nxh) / 16;
     if (groups > 65535) return cudaErrorInvalidConfiguration;
     const dim3 grid(a.n_loads, groups, 1);
     if (a.st != nullptr && (long long)groups > a.red.max_blocks) return cudaErrorInvalidConfiguration;
-    if (a.d.c == 1) return launch_with_smem(fft_last128_kernel<1>, grid, last128_threads<1>(), last128_smem<1>(), s, a);
-    return launch_with_smem(fft_last128_kernel<3>, grid, last128_threads<3>(), last128_smem<3>(), s, a);
+    switch (a.d.nz) {
+      case 128: return launch_last_rs<128>(a, grid, s);
+      case 96: return launch_last_rs<96>(a, grid, s);
+      case 64: return launch_last_rs<64>(a, grid, s);
+      case 32: return launch_last_rs<32>(a, grid, s);
+      default: return cudaErrorInvalidValue;
+    }
   }
   if (a.d.c == 1) return launch_last_nc<T, 1>(a, s);
   if (a.d.c == 2) return launch_last_nc<T, 2>(a, s);
@@ -1356,16 +1424,28 @@ cudaError_t launch_fft_last_solve(const FftArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+template <int N>
+static cudaError_t launch_xy_rs(const FftArgs& a, int inverse, cudaStream_t s) {
+  using P = RS<N>;
+  const dim3 grid(a.d.nz, a.d.c, a.n_loads);
+  if (!inverse && a.mode == FX_PCG) return launch_with_smem(fft_xy_fwd_rs_kernel<N, true>, grid, P::NT, P::SMEM, s, a);
+  if (!inverse) return launch_with_smem(fft_xy_fwd_rs_kernel<N, false>, grid, P::NT, P::SMEM, s, a);
+  if (a.st != nullptr && (long long)grid.x * grid.y > a.red.max_blocks) return cudaErrorInvalidConfiguration;
+  if (a.mode == FX_PCG) return launch_with_smem(fft_xy_inv_rs_kernel<N, FX_PCG>, grid, P::NT, P::SMEM, s, a);
+  if (a.mode == FX_PCG_INIT) return launch_with_smem(fft_xy_inv_rs_kernel<N, FX_PCG_INIT>, grid, P::NT, P::SMEM, s, a);
+  return launch_with_smem(fft_xy_inv_rs_kernel<N, FX_PLAIN>, grid, P::NT, P::SMEM, s, a);
+}
+
 template <>
 cudaError_t launch_fft_xy<float>(const FftArgs& a, int inverse, cudaStream_t s) {
   if (!fft_xy_supported(a.d, true)) return cudaErrorInvalidValue;
-  const dim3 grid(a.d.nz, a.d.c, a.n_loads);
-  if (!inverse && a.mode == FX_PCG) return launch_with_smem(fft_xy_fwd128_kernel<true>, grid, XY_THREADS, XY_SMEM, s, a);
-  if (!inverse) return launch_with_smem(fft_xy_fwd128_kernel<false>, grid, XY_THREADS, XY_SMEM, s, a);
-  if (a.st != nullptr && (long long)grid.x * grid.y > a.red.max_blocks) return cudaErrorInvalidConfiguration;
-  if (a.mode == FX_PCG) return launch_with_smem(fft_xy_inv128_kernel<FX_PCG>, grid, XY_THREADS, XY_SMEM, s, a);
-  if (a.mode == FX_PCG_INIT) return launch_with_smem(fft_xy_inv128_kernel<FX_PCG_INIT>, grid, XY_THREADS, XY_SMEM, s, a);
-  return launch_with_smem(fft_xy_inv128_kernel<FX_PLAIN>, grid, XY_THREADS, XY_SMEM, s, a);
+  switch (a.d.nx) {
+    case 128: return launch_xy_rs<128>(a, inverse, s);
+    case 96: return launch_xy_rs<96>(a, inverse, s);
+    case 64: return launch_xy_rs<64>(a, inverse, s);
+    case 32: return launch_xy_rs<32>(a, inverse, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <>
@@ -1374,7 +1454,7 @@ cudaError_t launch_fft_xy<double>(const FftArgs&, int, cudaStream_t) {
 }
 
 bool fft_xy_supported(const Dims& d, bool fp32) {
-  return fp32 && d.dim == 3 && d.nx == 128 && d.ny == 128 && d.nxh == 65;
+  return fp32 && d.dim == 3 && rs_length(d.nx) && d.ny == d.nx && d.nxh == d.nx / 2 + 1;
 }
 
 template cudaError_t launch_fft_x_fwd<double>(const FftArgs&, cudaStream_t);

@@ -189,6 +189,11 @@ PRECOND_CASES = [
     ("hex8_3d", "scalar", (12, 6, 48), 0),
     ("hex8_3d", "elastic", (6, 128, 128), 1),   # fused x-y passes, generic last axis
     ("hex8_3d", "scalar", (6, 128, 128), 1),
+    ("hex8_3d", "scalar", (6, 96, 96), 1),      # fused x-y passes of 96 = 16 x 6 points
+    ("hex8_3d", "elastic", (96, 16, 24), 1),    # register-split last axis (nz = 96), generic x and y
+    ("hex8_3d", "elastic", (96, 96, 96), 1),    # both register-split passes at 96, 64 and 32 points
+    ("hex8_3d", "scalar", (64, 64, 64), 1),
+    ("hex8_3d", "elastic", (32, 32, 32), 1),
     ("p1tri2_2d", "scalar", (24, 48), 0),
     ("q1_2d", "elastic", (12, 96), 0),
     ("p1tri4_2d", "scalar", (12, 48), 0),       # Hermitian 2 x 2 blocks
@@ -253,6 +258,20 @@ def _check_precond_step(s, g, Kinv, precision, n_loads, seed, expect_plan=None):
         assert (plan["xy_fused"], plan["last_reg"]) == expect_plan
 
 
+RS_LENGTHS = (32, 64, 96, 128)
+
+
+def _rs_plan(elem, shape, fft_xy, precision):
+    """(fused x-y, register-split last axis) that fft_xy = 1 must give: FP32 hex8 fields whose x-y planes
+    are n x n, and whose z axis has n points, for n = 32, 64, 96 or 128 (whole 16-column groups)."""
+    if fft_xy != 1 or precision != "mixed" or elem != "hex8_3d":
+        return (0, 0)
+    nz, ny, nx = shape
+    fused = int(nx == ny and nx in RS_LENGTHS)
+    last = int(nz in RS_LENGTHS and (ny * (nx // 2 + 1)) % 16 == 0)
+    return (fused, last)
+
+
 @pytest.mark.parametrize("elem,physics,shape,fft_xy", PRECOND_CASES)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_pcg_precond_step_matches_oracle(elem, physics, shape, fft_xy, precision):
@@ -261,8 +280,8 @@ def test_pcg_precond_step_matches_oracle(elem, physics, shape, fft_xy, precision
     s = _fehom().Solver(elem, physics, tuple(shape[::-1]), ids, mod, precision=precision, fft_xy=fft_xy,
                         autotune=False)
     s.precond_build()
-    fused = 1 if (fft_xy == 1 and precision == "mixed" and shape[1:] == (128, 128)) else 0
-    _check_precond_step(s, g, Kinv, precision, n_loads=2, seed=sum(shape), expect_plan=(fused, 0))
+    _check_precond_step(s, g, Kinv, precision, n_loads=2, seed=sum(shape),
+                        expect_plan=_rs_plan(elem, shape, fft_xy, precision))
     s.close()
 
 
