@@ -144,8 +144,8 @@ def workload():
 # element, one node plane) for isotropic phases: in-plane butterflies of the node plane 24, z part
 # 21, closed-form duals 35, transposed z part 18, face totals 12, transposed in-plane part 24, node
 # gather and scale 12, fused <p, Ap> 3 = 149.
-def kernel_model(s, c=3):
-    hs = 65.0 / 128.0
+def kernel_model(s, c=3, n=128):
+    hs = (n // 2 + 1) / n
     spec = c * hs * 2 * s              # one half-spectrum pass over the c components
     sym = c * (c + 1) // 2 * s * hs    # packed symmetric c x c K_hat^+ per half-spectrum k
     return {
@@ -447,7 +447,7 @@ def run_grf512(args):
             s.close()
     hbm, hbm_src = peaks()
     r64, rmx = res["fp64"], res["mixed"]
-    model, units = kernel_model(4, c), N * rmx["kt_load_iters"]
+    model, units = kernel_model(4, c, n[0]), N * rmx["kt_load_iters"]
     roof = {}
     for k, (ms_k, n_k) in rmx["kt"].items():
         if n_k > 0 and ms_k > 0:
@@ -748,12 +748,17 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_ncu_case(precision, n_loads=6, rows=0):
-    """One untimed solve of the benchmark workload (its first n_loads loads), for kernel captures
-    under ncu; fewer loads keep the device memory that ncu saves between replay passes small."""
+def run_ncu_case(precision, n_loads=6, rows=0, cell=0):
+    """One untimed solve of the benchmark workload (its first n_loads loads), or with cell = 32, 64 or 96
+    of the first cell of that size in the batched workload, for kernel captures under ncu; fewer loads
+    keep the device memory that ncu saves between replay passes small."""
     import torch
     from paper_2203_02962_gb300 import fehom
+    from paper_2203_02962_gb300 import inputs
     w = workload()
+    if cell:
+        c = next(x for x in inputs.workload_batched_spheres() if x["n"][0] == cell)
+        w = dict(n=c["n"], ids=c["ids"], moduli=c["moduli"], loads=inputs.unit_loads(6), tol=1e-6)
     # the FFT plan and the stencil tile height the tuners pick in the timed runs (register-split FFT
     # passes; 8-row FP32 and 16-row FP64 tiles); under ncu the tuners' own timings are serialised
     # replays and would pick differently
@@ -777,6 +782,8 @@ def main():
     ap.add_argument("--ncu-case", default=None, choices=["fp64", "mixed", "unet"],
                     help="run one untimed solve of the workload (for ncu kernel captures) and exit")
     ap.add_argument("--ncu-loads", type=int, default=6, help="loads of the --ncu-case solve (1-6)")
+    ap.add_argument("--ncu-cell", type=int, default=0, choices=[0, 32, 64, 96],
+                    help="run the --ncu-case solve on the first cell of this size of the batched workload")
     ap.add_argument("--ncu-rows", type=int, default=0, choices=[0, 8, 16],
                     help="stencil rows of the --ncu-case solve (0: the tuners' usual pick)")
     ap.add_argument("--grf512", action="store_true",
@@ -798,7 +805,7 @@ def main():
         print(json.dumps({"ncu_case": "unet", **run_unet(args)}))
         return
     if args.ncu_case:
-        run_ncu_case(args.ncu_case, args.ncu_loads, args.ncu_rows)
+        run_ncu_case(args.ncu_case, args.ncu_loads, args.ncu_rows, args.ncu_cell)
         return
     run_ours(args)
 
