@@ -87,9 +87,9 @@ typedef struct {
   int x0_scaling;    /* 1 (default): a warm start x0 (mean removed) is replaced, per load, by gamma x0 with
                         gamma = <b, x0> / <x0, K x0> (0 when <x0, K x0> = 0): the multiple of x0 closest to
                         the solution in the energy norm, never farther from it than the zero guess */
-  int fft_xy;        /* FP32 register-split FFT passes: the fused x-y passes (3-D fields with n x n planes) and
-                        the last-axis pass for nz = n (c = 1 or 3), n = 32, 64, 96 or 128: -1 (default) the
-                        tuner decides for
+  int fft_xy;        /* FP32 register-split FFT passes: the fused x-y passes (3-D fields with n x n planes,
+                        n = 32, 64, 96 or 128) and the last-axis pass (nz = 32, 64, 96, 128 or 256; c = 1 or
+                        3): -1 (default) the tuner decides for
                         each (the generic passes when autotune = 0), 0 never, 1 always when supported */
   int residual_df;   /* mixed only: 1 (default) the refinement residual is updated as r -= K d for each FP32
                         correction d, with K d evaluated in double-float arithmetic (pairs of floats, about
@@ -239,7 +239,7 @@ fehom_status fehom_eig_bounds(fehom_ctx* ctx, double* lo_values, int64_t* lo_cou
  * the device milliseconds of the chosen plans measured by the tuner (ms[3]: x passes, y passes,
  * last-axis pass; may be NULL), and the register-split FP32 passes in use as a bit mask (*xy_fused,
  * may be NULL): bit 0 = fused x-y passes (n x n planes, n = 32, 64, 96 or 128; then ms[0] times them and
- * ms[1] = 0), bit 1 = register-split last-axis pass (nz = 32, 64, 96 or 128). */
+ * ms[1] = 0), bit 1 = register-split last-axis pass (nz = 32, 64, 96, 128 or 256). */
 fehom_status fehom_fft_plan(const fehom_ctx* ctx, int precision, int* pairs, int* tc_y, int* tc_last, double* ms,
                             int* xy_fused);
 

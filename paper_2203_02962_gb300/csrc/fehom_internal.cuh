@@ -212,7 +212,7 @@ struct FftArgs {
   int pairs, tc_y, tc_last;
   int herm;      // 1: Hermitian 2 x 2 symbol blocks (two-node stencil), packed (00, 11, Re 01, Im 01)
   int xy;        // 1: fused x-y passes (launch_fft_xy) in place of the separate x and y passes
-  int last_reg;  // 1: register-split last-axis pass (FP32 3-D, nz = 32, 64, 96 or 128, c = 1 or 3) with the block solve
+  int last_reg;  // 1: register-split last-axis pass (FP32 3-D, nz = 32, 64, 96, 128 or 256, c = 1 or 3) with the block solve
 };
 
 template <typename T> cudaError_t launch_fft_x_fwd(const FftArgs& a, cudaStream_t s);

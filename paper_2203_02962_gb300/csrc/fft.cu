@@ -683,6 +683,11 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
   }
 }
 
+// the 16-point DFT as the Q-point stage of the last-axis pass for nz = 256
+template <bool INV> struct Dft<float2, 16, INV> {
+  __device__ static void run(float2 (&v)[16]) { dft16<INV>(v); }
+};
+
 template <int N, bool UPDATE>
 __global__ void __launch_bounds__(RS<N>::NT, RS<N>::MIN_CTAS) fft_xy_fwd_rs_kernel(FftArgs a) {
   using P = RS<N>;
@@ -971,7 +976,7 @@ __global__ void __launch_bounds__(RS<N>::NT, RS<N>::MIN_CTAS) fft_xy_inv_rs_kern
   }
 }
 
-// Last axis (z) of FP32 3-D fields with nz = N = 16 Q (32, 64, 96 or 128), 16 columns x NC components
+// Last axis (z) of FP32 3-D fields with nz = N = 16 Q (32, 64, 96, 128 or 256), 16 columns x NC components
 // per CTA, with the block solve: the same 16 x Q split as the fused x-y passes.  Stage 1: 16-point
 // DFTs of the stride-Q z subsequences read straight from the spectrum; stage 2, in place on every
 // thread: (a) the Q-point DFTs of the 16 NC (k1, c) lines of each column, (b) the block solve and the
@@ -992,7 +997,7 @@ __host__ __device__ constexpr size_t last_rs_smem() {
 }
 
 template <int N, int NC>
-__global__ void __launch_bounds__(last_rs_threads<N, NC>(), 1152 / last_rs_threads<N, NC>())
+__global__ void __launch_bounds__(last_rs_threads<N, NC>(), 1152 / last_rs_threads<N, NC>() > 1 ? 1152 / last_rs_threads<N, NC>() : 1)
     fft_last_rs_kernel(FftArgs a) {
   constexpr int TCL = 16, Q = N / 16;
   constexpr int NT3 = last_rs_threads<N, NC>();
@@ -1394,7 +1399,8 @@ static cudaError_t launch_last_nc(const FftArgs& a, cudaStream_t s) {
 static bool rs_length(int n) { return n == 32 || n == 64 || n == 96 || n == 128; }
 
 bool fft_last_rs_supported(const Dims& d, bool fp32) {
-  return fp32 && d.dim == 3 && rs_length(d.nz) && (d.c == 1 || d.c == 3) && (d.ny * d.nxh) % 16 == 0;
+  const bool len = rs_length(d.nz) || d.nz == 256;
+  return fp32 && d.dim == 3 && len && (d.c == 1 || d.c == 3) && (d.ny * d.nxh) % 16 == 0;
 }
 
 template <int N>
@@ -1415,6 +1421,7 @@ cudaError_t launch_fft_last_solve(const FftArgs& a, cudaStream_t s) {
       case 96: return launch_last_rs<96>(a, grid, s);
       case 64: return launch_last_rs<64>(a, grid, s);
       case 32: return launch_last_rs<32>(a, grid, s);
+      case 256: return launch_last_rs<256>(a, grid, s);
       default: return cudaErrorInvalidValue;
     }
   }

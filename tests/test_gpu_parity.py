@@ -178,12 +178,13 @@ def test_fused_xy_passes_match_oracle(physics, n):
     assert _rel(outs[1]["C_eff"], outs[0]["C_eff"]) < 1e-7
 
 
-@pytest.mark.parametrize("shape", [(128, 128, 128), (96, 96, 96), (64, 64, 64), (32, 32, 32), (96, 16, 24)])
+@pytest.mark.parametrize("shape", [(128, 128, 128), (96, 96, 96), (64, 64, 64), (32, 32, 32), (96, 16, 24),
+                                   (256, 16, 24)])
 @pytest.mark.parametrize("physics", ["elastic", "scalar"])
 def test_register_split_last_axis_pass_matches_oracle(physics, shape):
-    """The register-split last-axis pass (FP32, nz = 128, 96, 64, 32) with the fused x-y passes where the
-    planes are square: preconditioner apply against the oracle, and mixed solves with and without them
-    agree."""
+    """The register-split last-axis pass (FP32, nz = 32, 64, 96, 128, 256) with the fused x-y passes where
+    the planes are square: preconditioner apply against the oracle, and mixed solves with and without
+    them agree."""
     torch = _torch()
     g = fem.Grid(shape, "hex8_3d", physics)
     rng = np.random.default_rng(23)

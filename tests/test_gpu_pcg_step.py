@@ -194,6 +194,7 @@ PRECOND_CASES = [
     ("hex8_3d", "elastic", (96, 96, 96), 1),    # both register-split passes at 96, 64 and 32 points
     ("hex8_3d", "scalar", (64, 64, 64), 1),
     ("hex8_3d", "elastic", (32, 32, 32), 1),
+    ("hex8_3d", "elastic", (256, 16, 24), 1),   # last axis of 256 points (16 x 16)
     ("p1tri2_2d", "scalar", (24, 48), 0),
     ("q1_2d", "elastic", (12, 96), 0),
     ("p1tri4_2d", "scalar", (12, 48), 0),       # Hermitian 2 x 2 blocks
@@ -263,12 +264,14 @@ RS_LENGTHS = (32, 64, 96, 128)
 
 def _rs_plan(elem, shape, fft_xy, precision):
     """(fused x-y, register-split last axis) that fft_xy = 1 must give: FP32 hex8 fields whose x-y planes
-    are n x n, and whose z axis has n points, for n = 32, 64, 96 or 128 (whole 16-column groups)."""
+    are n x n (n = 32, 64, 96 or 128), and whose z axis has 32, 64, 96, 128 or 256 points, with whole
+    16-column groups."""
     if fft_xy != 1 or precision != "mixed" or elem != "hex8_3d":
         return (0, 0)
     nz, ny, nx = shape
     fused = int(nx == ny and nx in RS_LENGTHS)
-    last = int(nz in RS_LENGTHS and (ny * (nx // 2 + 1)) % 16 == 0)
+    z_ok = nz in RS_LENGTHS or nz == 256
+    last = int(z_ok and (ny * (nx // 2 + 1)) % 16 == 0)
     return (fused, last)
 
 
