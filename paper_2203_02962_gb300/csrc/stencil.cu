@@ -1341,7 +1341,7 @@ __device__ __forceinline__ DF operator*(DF a, DF c) {  // the lo x lo term (2^-4
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (double)a.l; }
 
 template <bool RHS>
-__global__ void __launch_bounds__(Hex8Tile<float, 8>::NT, 1)
+__global__ void __launch_bounds__(Hex8Tile<float, 8>::NT, 2)
     hex8_residual_df_kernel(StencilArgs a, const double* __restrict__ r_in, const float* __restrict__ taudf,
                             int kz_per_cta) {
   constexpr int C = 3, BY = 8, NE = Hex8Tile<float, 8>::NE;
