@@ -3,6 +3,7 @@
 #include "fehom_internal.cuh"
 
 #include <algorithm>
+#include <cstdint>
 
 namespace fehom {
 namespace {
@@ -20,6 +21,37 @@ __global__ void add_f2d_kernel(const float* __restrict__ x, double* __restrict__
   for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
     y[i] = fma(s, (double)x[i], y[i]);
 }
+
+// the same four elements at a time (16-byte accesses; both arrays 16-byte aligned); the last n mod 4
+// elements by the first threads of block 0
+__global__ void cast_d2f4_kernel(const double* __restrict__ x, float* __restrict__ y, double s, long long n) {
+  const long long n4 = n / 4;
+  const double2* x2 = reinterpret_cast<const double2*>(x);
+  float4* y4 = reinterpret_cast<float4*>(y);
+  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n4; i += (long long)gridDim.x * VT) {
+    const double2 a = x2[2 * i], b = x2[2 * i + 1];
+    y4[i] = make_float4((float)(s * a.x), (float)(s * a.y), (float)(s * b.x), (float)(s * b.y));
+  }
+  if (blockIdx.x == 0 && threadIdx.x < n - 4 * n4) y[4 * n4 + threadIdx.x] = (float)(s * x[4 * n4 + threadIdx.x]);
+}
+
+__global__ void add_f2d4_kernel(const float* __restrict__ x, double* __restrict__ y, double s, long long n) {
+  const long long n4 = n / 4;
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  double2* y2 = reinterpret_cast<double2*>(y);
+  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n4; i += (long long)gridDim.x * VT) {
+    const float4 v = x4[i];
+    const double2 a = y2[2 * i], b = y2[2 * i + 1];
+    y2[2 * i] = make_double2(fma(s, (double)v.x, a.x), fma(s, (double)v.y, a.y));
+    y2[2 * i + 1] = make_double2(fma(s, (double)v.z, b.x), fma(s, (double)v.w, b.y));
+  }
+  if (blockIdx.x == 0 && threadIdx.x < n - 4 * n4) {
+    const long long j = 4 * n4 + threadIdx.x;
+    y[j] = fma(s, (double)x[j], y[j]);
+  }
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 __device__ double block_sum(double v) {
   __shared__ double sh[32];
@@ -154,12 +186,14 @@ cudaError_t launch_impulse_scatter(const double* py, const Dims& pd, const Dims&
 }
 
 cudaError_t launch_cast_d2f(const double* x, float* y, double scale, long long n, cudaStream_t s) {
-  cast_d2f_kernel<<<grid_for(n), VT, 0, s>>>(x, y, scale, n);
+  if (aligned16(x) && aligned16(y)) cast_d2f4_kernel<<<grid_for((n + 3) / 4), VT, 0, s>>>(x, y, scale, n);
+  else cast_d2f_kernel<<<grid_for(n), VT, 0, s>>>(x, y, scale, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_add_f2d(const float* x, double* y, double scale, long long n, cudaStream_t s) {
-  add_f2d_kernel<<<grid_for(n), VT, 0, s>>>(x, y, scale, n);
+  if (aligned16(x) && aligned16(y)) add_f2d4_kernel<<<grid_for((n + 3) / 4), VT, 0, s>>>(x, y, scale, n);
+  else add_f2d_kernel<<<grid_for(n), VT, 0, s>>>(x, y, scale, n);
   return cudaGetLastError();
 }
 

@@ -296,6 +296,24 @@ def test_mixed_precision_matches_fp64():
     s32.close()
 
 
+def test_mixed_precision_matches_fp64_on_a_ragged_field_length():
+    """Mixed and FP64 solves agree where the field length c N x loads is not a multiple of 4: the 16-byte
+    precision casts of the refinement loop then finish the last elements one at a time (2-D P1
+    conductivity on a 6 x 3 grid, one load: 18 values)."""
+    shape = (3, 6)
+    ids = np.array([[0, 1, 0, 0, 1, 1], [1, 0, 0, 1, 0, 0], [0, 0, 1, 1, 0, 1]], np.uint8)
+    mod = _materials("scalar", 2, "iso")[:2]
+    out = {}
+    for prec in ("fp64", "mixed"):
+        s = _solver("p1tri2_2d", "scalar", shape, ids, mod, precision=prec)
+        s.precond_build()
+        out[prec] = s.solve(np.eye(2)[:1], tol=1e-10)
+        assert out[prec]["info"][0]["converged"]
+        s.close()
+    assert _rel(out["mixed"]["mean_flux"], out["fp64"]["mean_flux"]) < 1e-8
+    assert _rel(out["mixed"]["fields"].cpu().numpy(), out["fp64"]["fields"].cpu().numpy()) < 1e-7
+
+
 def test_graph_and_plain_launches_agree():
     n = 16
     ids, mod = _small_elastic(n, seed=8)
