@@ -710,25 +710,43 @@ __global__ void __launch_bounds__(RS<N>::NT, RS<N>::MIN_CTAS) fft_xy_fwd_rs_kern
   {  // x, stage 0: rows to shared memory (16-byte accesses along each row pair), r -= alpha Ap
     float* Rre = reinterpret_cast<float*>(S);
     float* Rim = Rre + NP * P::LDF_F;
+    // the r and Ap loads of a batch of row pieces are issued before any of its stores, so that they are
+    // in flight together
+    constexpr int IT = N / 32, B = IT < 2 ? IT : 2;
 #pragma unroll
-    for (int it = 0; it < N / 32; ++it) {
-      const int task = t + NT * it;
-      const int q = task / (N / 4), x = 4 * (task % (N / 4));
-      float4* g0 = reinterpret_cast<float4*>(r + 2 * q * N + x);
-      float4* g1 = reinterpret_cast<float4*>(r + (2 * q + 1) * N + x);
-      float4 v0 = *g0, v1 = *g1;
-      if (UPDATE) {
-        const float4 a0 = __ldg(reinterpret_cast<const float4*>(ap + 2 * q * N + x));
-        const float4 a1 = __ldg(reinterpret_cast<const float4*>(ap + (2 * q + 1) * N + x));
-        v0 = make_float4(fmaf(-alpha, a0.x, v0.x), fmaf(-alpha, a0.y, v0.y), fmaf(-alpha, a0.z, v0.z),
-                         fmaf(-alpha, a0.w, v0.w));
-        v1 = make_float4(fmaf(-alpha, a1.x, v1.x), fmaf(-alpha, a1.y, v1.y), fmaf(-alpha, a1.z, v1.z),
-                         fmaf(-alpha, a1.w, v1.w));
-        *g0 = v0;
-        *g1 = v1;
+    for (int it0 = 0; it0 < IT; it0 += B) {
+      float4 v0[B], v1[B];
+      [[maybe_unused]] float4 a0[B], a1[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        if (it0 + b < IT) {
+          const int task = t + NT * (it0 + b);
+          const int q = task / (N / 4), x = 4 * (task % (N / 4));
+          v0[b] = *reinterpret_cast<const float4*>(r + 2 * q * N + x);
+          v1[b] = *reinterpret_cast<const float4*>(r + (2 * q + 1) * N + x);
+          if (UPDATE) {
+            a0[b] = __ldg(reinterpret_cast<const float4*>(ap + 2 * q * N + x));
+            a1[b] = __ldg(reinterpret_cast<const float4*>(ap + (2 * q + 1) * N + x));
+          }
+        }
       }
-      *reinterpret_cast<float4*>(Rre + q * P::LDF_F + x) = v0;
-      *reinterpret_cast<float4*>(Rim + q * P::LDF_F + x) = v1;
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        if (it0 + b >= IT) continue;
+        const int task = t + NT * (it0 + b);
+        const int q = task / (N / 4), x = 4 * (task % (N / 4));
+        float4 w0 = v0[b], w1 = v1[b];
+        if (UPDATE) {
+          w0 = make_float4(fmaf(-alpha, a0[b].x, w0.x), fmaf(-alpha, a0[b].y, w0.y), fmaf(-alpha, a0[b].z, w0.z),
+                           fmaf(-alpha, a0[b].w, w0.w));
+          w1 = make_float4(fmaf(-alpha, a1[b].x, w1.x), fmaf(-alpha, a1[b].y, w1.y), fmaf(-alpha, a1[b].z, w1.z),
+                           fmaf(-alpha, a1[b].w, w1.w));
+          *reinterpret_cast<float4*>(r + 2 * q * N + x) = w0;
+          *reinterpret_cast<float4*>(r + (2 * q + 1) * N + x) = w1;
+        }
+        *reinterpret_cast<float4*>(Rre + q * P::LDF_F + x) = w0;
+        *reinterpret_cast<float4*>(Rim + q * P::LDF_F + x) = w1;
+      }
     }
   }
   __syncthreads();
@@ -937,25 +955,42 @@ __global__ void __launch_bounds__(RS<N>::NT, RS<N>::MIN_CTAS) fft_xy_inv_rs_kern
   float* f2 = (MODE != FX_PLAIN) ? reinterpret_cast<float*>(a.f2) + foff : nullptr;
   const float alpha = (MODE == FX_PCG) ? float(a.st[load].alpha) : 0.0f;
   const float beta = (MODE == FX_PCG) ? float(a.st[load].beta) : 0.0f;
+  // rows to global memory (16-byte accesses along each row) with the PCG updates; the x and p loads of
+  // a batch of rows are issued before any of its stores, so that they are in flight together
+  constexpr int IT = N / 16, B = IT < 4 ? IT : 4;
 #pragma unroll
-  for (int it = 0; it < N / 16; ++it) {  // rows to global memory (16-byte accesses along each row), PCG updates
-    const int task = t + NT * it;
-    const int row = task / (N / 4), x = 4 * (task % (N / 4));
-    const float* R = reinterpret_cast<const float*>(S) + (row & 1) * NP * P::LDF_I + (row >> 1) * P::LDF_I + x;
-    const float4 zv = *reinterpret_cast<const float4*>(R);
-    const long long g = (long long)row * N + x;
-    if (MODE == FX_PLAIN) {
-      *reinterpret_cast<float4*>(f0 + g) = zv;
-    } else if (MODE == FX_PCG_INIT) {
-      *reinterpret_cast<float4*>(f2 + g) = zv;
-    } else {
-      float4* xp = reinterpret_cast<float4*>(f0 + g);
-      float4* pp = reinterpret_cast<float4*>(f2 + g);
-      const float4 pv = *pp, xv = *xp;
-      *xp = make_float4(fmaf(alpha, pv.x, xv.x), fmaf(alpha, pv.y, xv.y), fmaf(alpha, pv.z, xv.z),
-                        fmaf(alpha, pv.w, xv.w));
-      *pp = make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y), fmaf(beta, pv.z, zv.z),
-                        fmaf(beta, pv.w, zv.w));
+  for (int it0 = 0; it0 < IT; it0 += B) {
+    [[maybe_unused]] float4 pv[B], xv[B];
+    if constexpr (MODE == FX_PCG) {
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        if (it0 + b < IT) {
+          const int task = t + NT * (it0 + b);
+          const long long g = (long long)(task / (N / 4)) * N + 4 * (task % (N / 4));
+          pv[b] = *reinterpret_cast<const float4*>(f2 + g);
+          xv[b] = *reinterpret_cast<const float4*>(f0 + g);
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      if (it0 + b >= IT) continue;
+      const int task = t + NT * (it0 + b);
+      const int row = task / (N / 4), x = 4 * (task % (N / 4));
+      const float* R = reinterpret_cast<const float*>(S) + (row & 1) * NP * P::LDF_I + (row >> 1) * P::LDF_I + x;
+      const float4 zv = *reinterpret_cast<const float4*>(R);
+      const long long g = (long long)row * N + x;
+      if (MODE == FX_PLAIN) {
+        *reinterpret_cast<float4*>(f0 + g) = zv;
+      } else if (MODE == FX_PCG_INIT) {
+        *reinterpret_cast<float4*>(f2 + g) = zv;
+      } else {
+        const float4 p4 = pv[b], x4 = xv[b];
+        *reinterpret_cast<float4*>(f0 + g) = make_float4(fmaf(alpha, p4.x, x4.x), fmaf(alpha, p4.y, x4.y),
+                                                         fmaf(alpha, p4.z, x4.z), fmaf(alpha, p4.w, x4.w));
+        *reinterpret_cast<float4*>(f2 + g) = make_float4(fmaf(beta, p4.x, zv.x), fmaf(beta, p4.y, zv.y),
+                                                         fmaf(beta, p4.z, zv.z), fmaf(beta, p4.w, zv.w));
+      }
     }
   }
   if (MODE != FX_PLAIN && a.st != nullptr) {
