@@ -291,26 +291,52 @@ __global__ void __launch_bounds__(XT) fft_x_fwd_kernel(FftArgs a) {
   const T alpha = UPDATE ? T(a.st[load].alpha) : T(0);
   const long long line_base = 2LL * blockIdx.x * P;
   const LineIdx li(nx);
-  for (int idx = threadIdx.x; idx < P * nx; idx += XT) {
-    int q, xx;
-    li.split(idx, q, xx);
-    const long long l0 = line_base + 2 * q;
-    T v0 = T(0), v1 = T(0);
-    if (l0 < nlines) {
-      const bool has1 = l0 + 1 < nlines;  // an odd line count leaves the last line unpaired
-      const long long g0 = l0 * nx + xx, g1 = g0 + nx;
-      v0 = r[g0];
-      if (has1) v1 = r[g1];
-      if (UPDATE) {
-        v0 = fma(-alpha, ap[g0], v0);
-        r[g0] = v0;
-        if (has1) {
-          v1 = fma(-alpha, ap[g1], v1);
-          r[g1] = v1;
+  // BL indices per step: their global loads are issued before any of their stores, so that they are in
+  // flight together (an odd line count leaves the last line unpaired)
+  constexpr int BL = 4;
+  for (int idx0 = threadIdx.x; idx0 < P * nx; idx0 += BL * XT) {
+    T v0[BL], v1[BL];
+    [[maybe_unused]] T a0[BL], a1[BL];
+#pragma unroll
+    for (int b = 0; b < BL; ++b) {
+      v0[b] = v1[b] = T(0);
+      if (UPDATE) a0[b] = a1[b] = T(0);
+      const int idx = idx0 + b * XT;
+      if (idx >= P * nx) continue;
+      int q, xx;
+      li.split(idx, q, xx);
+      const long long l0 = line_base + 2 * q;
+      if (l0 < nlines) {
+        const bool has1 = l0 + 1 < nlines;
+        const long long g0 = l0 * nx + xx, g1 = g0 + nx;
+        v0[b] = r[g0];
+        if (has1) v1[b] = r[g1];
+        if (UPDATE) {
+          a0[b] = ap[g0];
+          if (has1) a1[b] = ap[g1];
         }
       }
     }
-    b0[xx * LD + q] = mk<C>(v0, v1);
+#pragma unroll
+    for (int b = 0; b < BL; ++b) {
+      const int idx = idx0 + b * XT;
+      if (idx >= P * nx) continue;
+      int q, xx;
+      li.split(idx, q, xx);
+      const long long l0 = line_base + 2 * q;
+      T w0 = v0[b], w1 = v1[b];
+      if (UPDATE && l0 < nlines) {
+        const bool has1 = l0 + 1 < nlines;
+        const long long g0 = l0 * nx + xx, g1 = g0 + nx;
+        w0 = fma(-alpha, a0[b], w0);
+        r[g0] = w0;
+        if (has1) {
+          w1 = fma(-alpha, a1[b], w1);
+          r[g1] = w1;
+        }
+      }
+      b0[xx * LD + q] = mk<C>(w0, w1);
+    }
   }
   __syncthreads();
   const C* res = fft_smem<C, false, P, LD>(b0, b1, nx, reinterpret_cast<const C*>(a.tw.x));
@@ -373,28 +399,52 @@ __global__ void __launch_bounds__(XT) fft_x_inv_kernel(FftArgs a) {
   T* f2 = (MODE != FX_PLAIN) ? reinterpret_cast<T*>(a.f2) + foff : nullptr;
   const T alpha = (MODE == FX_PCG) ? T(a.st[load].alpha) : T(0);
   const T beta = (MODE == FX_PCG) ? T(a.st[load].beta) : T(0);
-  for (int idx = threadIdx.x; idx < P * nx; idx += XT) {
-    int q, xx;
-    li.split(idx, q, xx);
-    const long long l0 = line_base + 2 * q;
-    if (l0 >= nlines) continue;
-    const C zc = res[xx * LD + q];
-    const bool has1 = l0 + 1 < nlines;
-    const long long g0 = l0 * nx + xx, g1 = g0 + nx;
-    if (MODE == FX_PLAIN) {
-      f0[g0] = zc.x;
-      if (has1) f0[g1] = zc.y;
-    } else if (MODE == FX_PCG_INIT) {
-      f2[g0] = zc.x;
-      if (has1) f2[g1] = zc.y;
-    } else {
-      const T p0 = f2[g0];
-      f0[g0] = fma(alpha, p0, f0[g0]);
-      f2[g0] = fma(beta, p0, zc.x);
-      if (has1) {
-        const T p1 = f2[g1];
-        f0[g1] = fma(alpha, p1, f0[g1]);
-        f2[g1] = fma(beta, p1, zc.y);
+  // BL indices per step: the x and p loads of FX_PCG are issued before any of the stores
+  constexpr int BL = 4;
+  for (int idx0 = threadIdx.x; idx0 < P * nx; idx0 += BL * XT) {
+    [[maybe_unused]] T p0[BL], p1[BL], x0[BL], x1[BL];
+    if constexpr (MODE == FX_PCG) {
+#pragma unroll
+      for (int b = 0; b < BL; ++b) {
+        const int idx = idx0 + b * XT;
+        if (idx >= P * nx) continue;
+        int q, xx;
+        li.split(idx, q, xx);
+        const long long l0 = line_base + 2 * q;
+        if (l0 >= nlines) continue;
+        const long long g0 = l0 * nx + xx, g1 = g0 + nx;
+        p0[b] = f2[g0];
+        x0[b] = f0[g0];
+        if (l0 + 1 < nlines) {
+          p1[b] = f2[g1];
+          x1[b] = f0[g1];
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < BL; ++b) {
+      const int idx = idx0 + b * XT;
+      if (idx >= P * nx) continue;
+      int q, xx;
+      li.split(idx, q, xx);
+      const long long l0 = line_base + 2 * q;
+      if (l0 >= nlines) continue;
+      const C zc = res[xx * LD + q];
+      const bool has1 = l0 + 1 < nlines;
+      const long long g0 = l0 * nx + xx, g1 = g0 + nx;
+      if (MODE == FX_PLAIN) {
+        f0[g0] = zc.x;
+        if (has1) f0[g1] = zc.y;
+      } else if (MODE == FX_PCG_INIT) {
+        f2[g0] = zc.x;
+        if (has1) f2[g1] = zc.y;
+      } else {
+        f0[g0] = fma(alpha, p0[b], x0[b]);
+        f2[g0] = fma(beta, p0[b], zc.x);
+        if (has1) {
+          f0[g1] = fma(alpha, p1[b], x1[b]);
+          f2[g1] = fma(beta, p1[b], zc.y);
+        }
       }
     }
   }
