@@ -540,10 +540,20 @@ __global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, const
   const long long Nh = a.d.Nh;
   const int half = a.d.nx / 2;
   column_bases<TC>(m, a.d.nxh, blockIdx.x * TC, base, kxs);
-  for (int idx = threadIdx.x; idx < m.L * W; idx += ST) {
-    const int e = idx / W, rem = idx % W, comp = rem / TC, t = rem % TC;
-    const long long cb = base[t];
-    b0[idx] = cb >= 0 ? spec[comp * Nh + cb + (long long)e * m.estride] : mk<C>(T(0), T(0));
+  constexpr int BL = 4;  // the loads of BL elements per step are in flight together
+  for (int idx0 = threadIdx.x; idx0 < m.L * W; idx0 += BL * ST) {
+    C v[BL];
+#pragma unroll
+    for (int b = 0; b < BL; ++b) {
+      const int idx = idx0 + b * ST;
+      if (idx >= m.L * W) continue;
+      const int e = idx / W, rem = idx % W, comp = rem / TC, t = rem % TC;
+      const long long cb = base[t];
+      v[b] = cb >= 0 ? spec[comp * Nh + cb + (long long)e * m.estride] : mk<C>(T(0), T(0));
+    }
+#pragma unroll
+    for (int b = 0; b < BL; ++b)
+      if (idx0 + b * ST < m.L * W) b0[idx0 + b * ST] = v[b];
   }
   __syncthreads();
   C* res = fft_smem<C, false, W, W>(b0, b1, m.L, tw);
@@ -558,23 +568,20 @@ __global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, const
   }
   const T* sym = reinterpret_cast<const T*>(a.sym);
   DotAcc<T> dot;
-  for (int idx = threadIdx.x; idx < m.L * TC; idx += ST) {
+  // the block solve z = K_hat^+ r and the Parseval sum at one wavevector (k: the symbol entries there)
+  auto solve_point = [&](int idx, const T* k) {
     const int e = idx / TC, t = idx % TC;
-    const long long cb = base[t];
-    if (cb < 0) continue;
-    const long long ti = cb + (long long)e * m.estride;
     const int kx = kxs[t];
     const T wgt = (kx == 0 || kx == half) ? T(1) : T(2);
     C r[NC], z[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) r[c] = res[e * W + c * TC + t];
     if constexpr (NC == 1) {
-      const T k00 = sym[ti];
-      z[0] = mk<C>(k00 * r[0].x, k00 * r[0].y);
+      z[0] = mk<C>(k[0] * r[0].x, k[0] * r[0].y);
     } else if constexpr (NC == 2) {
-      const T k00 = sym[ti], k11 = sym[Nh + ti], k01 = sym[2 * Nh + ti];
+      const T k00 = k[0], k11 = k[1], k01 = k[2];
       if (a.herm) {  // z0 = k00 r0 + k01 r1, z1 = conj(k01) r0 + k11 r1 with complex k01
-        const T k01i = sym[3 * Nh + ti];
+        const T k01i = k[3];
         z[0] = mk<C>(fma(k00, r[0].x, fma(k01, r[1].x, -k01i * r[1].y)), fma(k00, r[0].y, fma(k01, r[1].y, k01i * r[1].x)));
         z[1] = mk<C>(fma(k11, r[1].x, fma(k01, r[0].x, k01i * r[0].y)), fma(k11, r[1].y, fma(k01, r[0].y, -k01i * r[0].x)));
       } else {
@@ -582,8 +589,7 @@ __global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, const
         z[1] = mk<C>(fma(k01, r[0].x, k11 * r[1].x), fma(k01, r[0].y, k11 * r[1].y));
       }
     } else {
-      const T k00 = sym[ti], k11 = sym[Nh + ti], k22 = sym[2 * Nh + ti];
-      const T k12 = sym[3 * Nh + ti], k02 = sym[4 * Nh + ti], k01 = sym[5 * Nh + ti];
+      const T k00 = k[0], k11 = k[1], k22 = k[2], k12 = k[3], k02 = k[4], k01 = k[5];
       z[0] = mk<C>(fma(k00, r[0].x, fma(k01, r[1].x, k02 * r[2].x)), fma(k00, r[0].y, fma(k01, r[1].y, k02 * r[2].y)));
       z[1] = mk<C>(fma(k01, r[0].x, fma(k11, r[1].x, k12 * r[2].x)), fma(k01, r[0].y, fma(k11, r[1].y, k12 * r[2].y)));
       z[2] = mk<C>(fma(k02, r[0].x, fma(k12, r[1].x, k22 * r[2].x)), fma(k02, r[0].y, fma(k12, r[1].y, k22 * r[2].y)));
@@ -593,6 +599,31 @@ __global__ void __launch_bounds__(ST) fft_last_kernel(FftArgs a, ColMap m, const
       dot.add(wgt * r[c].x, z[c].x);  // wgt in {1, 2}: exact
       dot.add(wgt * r[c].y, z[c].y);
       res[e * W + c * TC + t] = z[c];
+    }
+  };
+  // symbol entries per wavevector: 1, 3 (4 with the Hermitian coupling) or 6
+  constexpr int E = NC == 1 ? 1 : (NC == 2 ? 4 : 6);
+  constexpr int BS = NC == 1 ? 4 : 2;  // the symbol loads of BS points per step are in flight together
+  const int ne = NC == 2 ? (a.herm ? 4 : 3) : E;
+  for (int idx0 = threadIdx.x; idx0 < m.L * TC; idx0 += BS * ST) {
+    T k[BS][E];
+#pragma unroll
+    for (int b = 0; b < BS; ++b) {
+      const int idx = idx0 + b * ST;
+      if (idx >= m.L * TC) continue;
+      const int e = idx / TC, t = idx % TC;
+      const long long cb = base[t];
+      if (cb < 0) continue;
+      const long long ti = cb + (long long)e * m.estride;
+#pragma unroll
+      for (int j = 0; j < E; ++j)
+        if (j < ne) k[b][j] = sym[j * Nh + ti];
+    }
+#pragma unroll
+    for (int b = 0; b < BS; ++b) {
+      const int idx = idx0 + b * ST;
+      if (idx >= m.L * TC || base[idx % TC] < 0) continue;
+      solve_point(idx, k[b]);
     }
   }
   __syncthreads();
