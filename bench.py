@@ -356,7 +356,7 @@ def run_ours(args):
                                               r64["kt_load_iters"], args.steps)
     out["batched"] = run_batched(args)
     out["warm_start_unet"] = run_unet(args)
-    # the spec composite against plain FP64 on the same GPU: mixed precision with every load of a cell
+    # the composite form against plain FP64 on the same GPU: mixed precision with every load of a cell
     # batched (the 128^3 cell), and mixed + batched over the 48 cells of uneven size; the learned warm
     # start is left out (on these workloads it costs PCG iterations); C_eff in both forms beside it
     bt = out["batched"]
