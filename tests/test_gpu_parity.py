@@ -250,6 +250,46 @@ def test_solve_3d_matches_oracle(physics):
     s.close()
 
 
+@pytest.mark.parametrize("shape", [(4, 4, 1024), (4, 1024, 4), (1024, 4, 4)])
+def test_longest_axis_matches_oracle(shape):
+    """Cells with one axis at the longest supported length (1024 points; 4 x 4 across it): the FP64 and
+    FP32 stiffness, the Algorithm 2 preconditioner in both precisions and the solve of two loads
+    against the oracle.  Along such an axis the FFT passes hold fewer lines per CTA to fit shared
+    memory."""
+    torch = _torch()
+    g = fem.Grid(shape, "hex8_3d", "elastic")
+    rng = np.random.default_rng(41)
+    ids = (rng.random(shape) < 0.3).astype(np.uint8)
+    mod = _materials("elastic", 3, "iso")[:2]
+    K = fem.assemble_K(g, ids.ravel(), mod)
+    x = rng.standard_normal(g.c * g.N)
+    y_ref = K @ x
+    C_ref = fem.mean_material(g, ids.ravel(), mod)
+    Kinv = solvers.kref_pinv_symbol(solvers.kref_symbol(g, C_ref))
+    z_ref = solvers.apply_precond(g, Kinv, x)
+    s = _solver("hex8_3d", "elastic", shape, ids, mod)
+    y = s.apply_stiffness(torch.tensor(x, device="cuda"), "fp64").cpu().numpy()
+    assert np.abs(y - y_ref).max() <= 1e-12 * np.abs(y_ref).max()
+    y32 = s.apply_stiffness(torch.tensor(x, dtype=torch.float32, device="cuda"), "mixed").double().cpu().numpy()
+    assert np.abs(y32 - y_ref).max() <= 2e-5 * np.abs(K).max() * np.abs(x).max()
+    # The reference symbol's smallest nonzero modes scale like (2 pi / n)^2 along an axis of n points, so
+    # the rounding of the transforms reaches z amplified by (n / 128)^2 more than on the 128-point cells
+    # the base tolerances below are set for (the stiffness is local and keeps its tolerances).
+    f = (max(shape) / 128) ** 2
+    s.precond_build()
+    z = s.apply_precond(torch.tensor(x, device="cuda")).cpu().numpy()
+    z32 = s.apply_precond(torch.tensor(x, dtype=torch.float32, device="cuda"), "mixed").double().cpu().numpy()
+    loads = np.eye(6)[:2]
+    ref = solvers.homogenise(g, ids, mod, loads, method="pcg", tol=1e-13)  # the oracle's own PCG
+    out = s.solve(loads, tol=1e-12)
+    s.close()
+    errs = (_rel(z, z_ref), _rel(z32, z_ref), _rel(out["mean_flux"], ref["mean_flux"]),
+            _rel(out["fields"].reshape(len(loads), -1).cpu().numpy(), ref["fields"]))
+    assert all(i["converged"] for i in out["info"])
+    assert errs[0] < 1e-12 * f and errs[1] < 2e-5 * f, errs
+    assert errs[2] < 1e-10 * f and errs[3] < 1e-9 * f, errs
+
+
 def test_iteration_counts_match_oracle_pcg():
     """Same algorithm, same stopping test: the GPU and oracle PCG stop at the same iteration (+-1)."""
     n = 16
