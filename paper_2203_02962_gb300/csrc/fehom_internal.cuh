@@ -221,7 +221,8 @@ template <typename T> cudaError_t launch_fft_y(const FftArgs& a, int inverse, cu
 // last axis (z in 3-D, y in 2-D): forward FFT, z^ = K_hat^+ r^ / N, <r, z>, inverse FFT.
 // sym == nullptr: forward only (used by Algorithm 2).
 template <typename T> cudaError_t launch_fft_last_solve(const FftArgs& a, cudaStream_t s);
-// Fused x-y passes (one CTA per z-plane and component; FP32 3-D fields with 128 x 128 planes):
+// Fused x-y passes (one CTA per z-plane and component; FP32 3-D fields with n x n planes, n = 32, 64,
+// 96 or 128):
 // forward = x forward (with the FX_PCG update) + y forward; inverse = y inverse + x inverse (with the
 // FX_PCG / FX_PCG_INIT updates and the iteration bookkeeping).  cudaErrorInvalidValue when unsupported.
 template <typename T> cudaError_t launch_fft_xy(const FftArgs& a, int inverse, cudaStream_t s);
